@@ -1,0 +1,368 @@
+"""FP64 CPU oracle of the HyRes hot path (test infrastructure only).
+
+HyRes is the paper's automatic, parameter-free, low-rank, wavelet-based
+denoiser for Gaussian noise (Sec. 2.1); the paper defers its internals to the
+cited HyRes source. The stages written out here, in the order they run, are:
+
+1. Gram matrix ``R = Y^T Y`` of the ``n x p`` pixel-by-band matrix.
+2. Per-band noise level by multiple regression of each band on all the others
+   (the HySime-style estimator the paper ships, Sec. 2.1).
+3. Band whitening by those noise levels.
+4. Eigendecomposition of the whitened Gram matrix (the spectral subspace of
+   the low-rank model, Sec. 2.1 "low-rank").
+5. Projection of the whitened cube onto the leading ``r_max`` eigenvectors.
+6. Per-component 2D orthogonal Daubechies (db2) DWT (Sec. 2.1 "wavelet-based").
+7. Stein's unbiased risk estimate (SURE) of soft-thresholding each component,
+   on a grid of thresholds, and of dropping it.
+8. Choice of rank r and threshold lambda minimising the total SURE (what makes
+   the method "parameter-free", Sec. 2.1).
+9. Soft-thresholding of the detail coefficients and the inverse DWT.
+10. Back-projection to the band space and un-whitening.
+
+Readings where the paper is silent (kept identical in the CUDA path):
+periodic DWT boundary; whole-sample symmetric padding at the bottom/right to
+multiples of 2**L, cropped after the inverse transform; the LL band is never
+thresholded; one lambda shared by all kept components; lambda grid
+``k * sqrt(2 ln N) / (K - 1)``; ties go to the smallest rank, then the smallest
+lambda; regression without intercept or ridge; uncentred Gram matrix.
+
+Everything is plain float64 numpy. The input cube is float32 and is upcast
+once; the oracle never reads anything produced by the CUDA path.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------
+# Wavelet filters and transforms (stage 6 and its inverse in stage 9)
+# --------------------------------------------------------------------------
+
+def db2_filters():
+    """Daubechies' orthonormal 4-tap filter pair (two vanishing moments).
+
+    Low-pass ``h = (1+s3, 3+s3, 3-s3, 1-s3) / (4 sqrt 2)`` with ``s3 = sqrt 3``
+    (the closed form of the db2 scaling filter); high-pass is the quadrature
+    mirror ``g_m = (-1)^m h_{3-m}``. Sec. 2.1 calls HyRes "wavelet-based"; db2
+    is the orthogonal Daubechies wavelet this implementation uses.
+    """
+    s3 = np.sqrt(3.0)
+    h = np.array([1.0 + s3, 3.0 + s3, 3.0 - s3, 1.0 - s3]) / (4.0 * np.sqrt(2.0))
+    g = np.array([(-1.0) ** m * h[3 - m] for m in range(4)])
+    return h, g
+
+
+def _analysis_last_axis(x, h, g):
+    """One periodic analysis step along the last axis.
+
+    ``a_k = sum_m h_m x[(2k+m) mod M]`` and ``d_k = sum_m g_m x[(2k+m) mod M]``
+    for ``k = 0 .. M/2-1``; the output holds ``a`` then ``d``.
+    """
+    M = x.shape[-1]
+    k = np.arange(M // 2)
+    a = np.zeros(x.shape[:-1] + (M // 2,))
+    d = np.zeros(x.shape[:-1] + (M // 2,))
+    for m in range(4):
+        xm = x[..., (2 * k + m) % M]
+        a += h[m] * xm
+        d += g[m] * xm
+    return np.concatenate([a, d], axis=-1)
+
+
+def _synthesis_last_axis(c, h, g):
+    """Transpose of ``_analysis_last_axis``: scatter each ``a_k, d_k`` back
+    through the same taps, ``x[(2k+m) mod M] += h_m a_k + g_m d_k``."""
+    M = c.shape[-1]
+    half = M // 2
+    a = c[..., :half]
+    d = c[..., half:]
+    k = np.arange(half)
+    x = np.zeros(c.shape)
+    for m in range(4):
+        # for one m the targets (2k+m) mod M are distinct, so += is exact
+        x[..., (2 * k + m) % M] += h[m] * a + g[m] * d
+    return x
+
+
+def _dwt2_one_level(block, h, g):
+    # rows (W axis) first, then columns (H axis); Mallat layout: LL top-left
+    t = _analysis_last_axis(block, h, g)
+    t = np.swapaxes(_analysis_last_axis(np.swapaxes(t, -1, -2), h, g), -1, -2)
+    return t
+
+
+def _idwt2_one_level(block, h, g):
+    t = np.swapaxes(_synthesis_last_axis(np.swapaxes(block, -1, -2), h, g), -1, -2)
+    return _synthesis_last_axis(t, h, g)
+
+
+def dwt2(img, levels):
+    """L-level separable periodic db2 analysis of ``img[..., Hp, Wp]``.
+
+    Each level transforms the current LL block (top-left ``Hp>>l x Wp>>l``)
+    in place, rows then columns, so the result is in Mallat layout. ``Hp`` and
+    ``Wp`` must be multiples of ``2**levels``.
+    """
+    h, g = db2_filters()
+    C = np.array(img, dtype=np.float64, copy=True)
+    Hp, Wp = C.shape[-2:]
+    if Hp % (1 << levels) or Wp % (1 << levels):
+        raise ValueError("image sides must be multiples of 2**levels")
+    for lev in range(levels):
+        hl, wl = Hp >> lev, Wp >> lev
+        C[..., :hl, :wl] = _dwt2_one_level(C[..., :hl, :wl], h, g)
+    return C
+
+
+def idwt2(coef, levels):
+    """Inverse of ``dwt2``: the exact transpose, coarsest level first."""
+    h, g = db2_filters()
+    X = np.array(coef, dtype=np.float64, copy=True)
+    Hp, Wp = X.shape[-2:]
+    for lev in reversed(range(levels)):
+        hl, wl = Hp >> lev, Wp >> lev
+        X[..., :hl, :wl] = _idwt2_one_level(X[..., :hl, :wl], h, g)
+    return X
+
+
+def padded_shape(H, W, levels):
+    """Sides rounded up to multiples of ``2**levels``."""
+    q = 1 << levels
+    return -(-H // q) * q, -(-W // q) * q
+
+
+def pad_symmetric(img, Hp, Wp):
+    """Whole-sample symmetric extension at the bottom/right only:
+    ``x[M + j] = x[M - 2 - j]`` (the edge sample is not repeated)."""
+    H, W = img.shape[-2:]
+    if Hp - H > H - 1 or Wp - W > W - 1:
+        raise ValueError("padding longer than the image")
+    pad = [(0, 0)] * (img.ndim - 2) + [(0, Hp - H), (0, Wp - W)]
+    return np.pad(np.asarray(img, dtype=np.float64), pad, mode="reflect")
+
+
+# --------------------------------------------------------------------------
+# Stages 1-4: Gram matrix, noise estimation, whitening, eigendecomposition
+# --------------------------------------------------------------------------
+
+def gram(Y):
+    """Stage 1: uncentred Gram matrix ``R = Y^T Y`` of the ``n x p`` matrix
+    whose rows are pixels and columns are bands (input ``float[p][H][W]``)."""
+    p = Y.shape[0]
+    Yf = np.asarray(Y, dtype=np.float64).reshape(p, -1)
+    return Yf @ Yf.T
+
+
+def noise_est_regression(R, n):
+    """Stage 2, as the method states it: regress band b on all other bands
+    (least squares, no intercept) and take the residual power per pixel.
+
+    The normal equations are sliced from ``R``:
+    ``R[-b,-b] beta = R[-b,b]``, and
+    ``sigma_b^2 = (R[b,b] - R[b,-b] beta) / n`` is the residual sum of squares
+    over n. Returns ``sigma`` (float64[p]).
+    """
+    p = R.shape[0]
+    sig2 = np.empty(p)
+    for b in range(p):
+        idx = np.array([j for j in range(p) if j != b])
+        beta = np.linalg.solve(R[np.ix_(idx, idx)], R[idx, b])
+        sig2[b] = (R[b, b] - R[b, idx] @ beta) / n
+    return np.sqrt(sig2)
+
+
+def noise_est_schur(R, n):
+    """The same residual power through the Schur complement:
+    ``sigma_b^2 = 1 / (n [R^-1]_bb)``."""
+    return np.sqrt(1.0 / (n * np.diag(np.linalg.inv(R))))
+
+
+def noise_est_lstsq(Y):
+    """The same regression solved on the data matrix itself (QR/SVD based
+    ``lstsq``), without forming ``R``; used only to pin the other two."""
+    p = Y.shape[0]
+    Yf = np.asarray(Y, dtype=np.float64).reshape(p, -1).T  # n x p
+    n = Yf.shape[0]
+    sig2 = np.empty(p)
+    for b in range(p):
+        others = np.delete(Yf, b, axis=1)
+        beta, *_ = np.linalg.lstsq(others, Yf[:, b], rcond=None)
+        res = Yf[:, b] - others @ beta
+        sig2[b] = res @ res / n
+    return np.sqrt(sig2)
+
+
+def whiten_gram(R, sigma):
+    """Stage 3 applied to the Gram matrix: ``R_w = D^-1 R D^-1`` with
+    ``D = diag(sigma)``, i.e. the Gram matrix of the whitened cube
+    ``Y D^-1``."""
+    return R / np.outer(sigma, sigma)
+
+
+def eig_desc(Rw):
+    """Stage 4: symmetric eigendecomposition ``R_w = V diag(e) V^T`` with
+    eigenvalues in descending order. Sign convention: the entry of largest
+    magnitude of each eigenvector is made positive."""
+    e, V = np.linalg.eigh(Rw)
+    order = np.argsort(-e, kind="stable")
+    e = e[order]
+    V = V[:, order]
+    piv = np.argmax(np.abs(V), axis=0)
+    sgn = np.sign(V[piv, np.arange(V.shape[1])])
+    sgn[sgn == 0] = 1.0
+    return e, V * sgn
+
+
+# --------------------------------------------------------------------------
+# Stages 7-9: SURE, selection, soft threshold
+# --------------------------------------------------------------------------
+
+def soft_threshold(c, lam):
+    """``sign(c) * max(|c| - lam, 0)``: the proximal map of ``lam * |x|``."""
+    c = np.asarray(c, dtype=np.float64)
+    return np.sign(c) * np.maximum(np.abs(c) - lam, 0.0)
+
+
+def lambda_grid(N, K):
+    """Threshold candidates ``lambda_k = k * sqrt(2 ln N) / (K - 1)``,
+    ``k = 0..K-1``: a uniform grid up to the universal threshold for N
+    unit-variance coefficients."""
+    lam_max = np.sqrt(2.0 * np.log(N))
+    return np.arange(K, dtype=np.float64) * (lam_max / (K - 1))
+
+
+def _detail_mask(Hp, Wp, levels):
+    m = np.ones((Hp, Wp), dtype=bool)
+    m[: Hp >> levels, : Wp >> levels] = False
+    return m
+
+
+def sure_table(C, levels, lams):
+    """Stage 7: SURE of each component ``C[i]`` (whitened, unit noise).
+
+    For soft-thresholding the detail coefficients at ``lambda`` and keeping LL:
+    ``S_i(lambda) = N - 2 #{detail: |c| <= lambda}
+                    + sum_detail min(c^2, lambda^2)``
+    (each LL coefficient, kept as is, contributes 1). For dropping the
+    component (estimate zero): ``S_i(inf) = sum_all c^2 - N``. Evaluated by
+    direct comparison against every candidate. Returns ``(S[r][K], S_inf[r])``.
+    """
+    r, Hp, Wp = C.shape
+    N = Hp * Wp
+    mask = _detail_mask(Hp, Wp, levels)
+    S = np.empty((r, len(lams)))
+    S_inf = np.empty(r)
+    for i in range(r):
+        det = np.abs(C[i][mask])
+        det2 = det * det
+        for k, lam in enumerate(lams):
+            inside = det <= lam
+            S[i, k] = (N - 2.0 * np.count_nonzero(inside)
+                       + np.sum(np.minimum(det2, lam * lam)))
+        S_inf[i] = np.sum(C[i] * C[i]) - N
+    return S, S_inf
+
+
+def sure_rank_lambda(S, S_inf):
+    """Total SURE of keeping components ``1..r`` thresholded at ``lambda_k``
+    and dropping ``r+1..r_max``: ``T[r-1][k] = sum_{i<=r} S_i(lambda_k) +
+    sum_{r<i<=r_max} S_i(inf)``."""
+    r_max = S.shape[0]
+    head = np.cumsum(S, axis=0)
+    tail = np.array([np.sum(S_inf[r + 1:]) for r in range(r_max)])
+    return head + tail[:, None]
+
+
+def select_rank_lambda(S, S_inf):
+    """Stage 8: ``(r*, k*) = argmin T``; ties go to the smallest r, then the
+    smallest k (row-major first minimum). Returns ``(r*, k*, T, gap)`` with
+    ``gap`` the relative distance of the runner-up to the minimum."""
+    T = sure_rank_lambda(S, S_inf)
+    flat = int(np.argmin(T))
+    r_star, k_star = divmod(flat, T.shape[1])
+    vals = np.sort(T.ravel())
+    gap = (vals[1] - vals[0]) / max(abs(vals[0]), 1e-300) if vals.size > 1 else np.inf
+    return r_star + 1, k_star, T, gap
+
+
+# --------------------------------------------------------------------------
+# The whole path
+# --------------------------------------------------------------------------
+
+def hyres(Y, levels, r_max, n_lambda=64, *, sigma=None, V=None, rank=None,
+          lam=None):
+    """Run stages 1-10 on ``Y`` (``float[p][H][W]``).
+
+    Optional overrides (for checks of single stages): ``sigma`` (skip stage 2),
+    ``V`` (``p x r_max`` basis, skip stage 4), ``rank`` and ``lam`` (skip
+    stage 8). Returns a dict with the estimate ``X`` (``float64[p][H][W]``)
+    and every intermediate.
+    """
+    Y = np.asarray(Y)
+    p, H, W = Y.shape
+    n = H * W
+    if not (1 <= r_max <= p):
+        raise ValueError("need 1 <= r_max <= p")
+    Yf = Y.reshape(p, n).astype(np.float64)
+    R = Yf @ Yf.T                                               # stage 1
+    if sigma is None:
+        sigma = noise_est_regression(R, n)                      # stage 2
+    sigma = np.asarray(sigma, dtype=np.float64)
+    Rw = whiten_gram(R, sigma)                                  # stage 3
+    evals, Vfull = eig_desc(Rw)                                 # stage 4
+    if V is None:
+        V = Vfull[:, :r_max]
+    V = np.asarray(V, dtype=np.float64)
+    Z = V.T @ (Yf / sigma[:, None])                             # stage 5
+    Hp, Wp = padded_shape(H, W, levels)
+    C = dwt2(pad_symmetric(Z.reshape(r_max, H, W), Hp, Wp), levels)  # stage 6
+    N = Hp * Wp
+    lams = lambda_grid(N, n_lambda)
+    S, S_inf = sure_table(C, levels, lams)                      # stage 7
+    r_star, k_star, T, gap = select_rank_lambda(S, S_inf)       # stage 8
+    lam_star = lams[k_star]
+    if rank is not None:
+        r_star, k_star = int(rank), -1
+        lam_star = float(lam)
+    mask = _detail_mask(Hp, Wp, levels)
+    Ch = C[:r_star].copy()
+    Ch[:, mask] = soft_threshold(Ch[:, mask], lam_star)         # stage 9
+    Zh = idwt2(Ch, levels)[:, :H, :W].reshape(r_star, n)
+    Xh = sigma[:, None] * (V[:, :r_star] @ Zh)                  # stage 10
+    return dict(X=Xh.reshape(p, H, W), rank=r_star, k=k_star, lam=lam_star,
+                sigma=sigma, R=R, Rw=Rw, evals=evals, V=V, C=C, S=S,
+                S_inf=S_inf, T=T, gap=gap, lams=lams)
+
+
+# --------------------------------------------------------------------------
+# Metrics (Sec. 3 reports PSNR and SAM without formulas; these are the
+# standard definitions)
+# --------------------------------------------------------------------------
+
+def rel_l2(est, ref):
+    """``||est - ref||_F / ||ref||_F`` in float64."""
+    est = np.asarray(est, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm((est - ref).ravel()) / np.linalg.norm(ref.ravel()))
+
+
+def psnr(clean, est):
+    """Mean over bands of ``10 log10(max(clean_b)^2 / MSE_b)``."""
+    clean = np.asarray(clean, dtype=np.float64)
+    est = np.asarray(est, dtype=np.float64)
+    p = clean.shape[0]
+    c = clean.reshape(p, -1)
+    e = est.reshape(p, -1)
+    mse = np.mean((c - e) ** 2, axis=1)
+    return float(np.mean(10.0 * np.log10(np.max(c, axis=1) ** 2 / mse)))
+
+
+def sam(clean, est):
+    """Mean over pixels of the spectral angle ``arccos(<x, x^> / (|x| |x^|))``
+    in radians."""
+    p = clean.shape[0]
+    c = np.asarray(clean, dtype=np.float64).reshape(p, -1)
+    e = np.asarray(est, dtype=np.float64).reshape(p, -1)
+    cos = np.sum(c * e, axis=0) / (np.linalg.norm(c, axis=0) * np.linalg.norm(e, axis=0))
+    return float(np.mean(np.arccos(np.clip(cos, -1.0, 1.0))))

@@ -1,0 +1,339 @@
+"""Pins of the FP64 oracle against what the mathematics fixes.
+
+Each test checks the oracle against something other than itself: closed
+forms, an independent FFT route for the wavelet transform, brute force on tiny
+inputs, power iteration, a QR/SVD least-squares route, a Monte Carlo
+unbiasedness check of SURE, and special cases that reduce to a textbook
+routine (truncated SVD). None of these need a GPU.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import make_cube
+
+
+# ---------------------------------------------------------------- db2 filters
+
+def test_db2_filter_identities():
+    h, g = O.db2_filters()
+    # orthonormal scaling filter: unit norm, sum sqrt 2, double-shift orthogonal
+    assert abs(np.sum(h * h) - 1.0) < 1e-15
+    assert abs(np.sum(h) - np.sqrt(2.0)) < 1e-15
+    assert abs(h[0] * h[2] + h[1] * h[3]) < 1e-16
+    # wavelet filter: two vanishing moments, orthogonal to h at even shifts
+    m = np.arange(4)
+    assert abs(np.sum(g)) < 1e-15
+    assert abs(np.sum(m * g)) < 1e-14
+    assert abs(np.sum(h * g)) < 1e-16
+    assert abs(g[0] * h[2] + g[1] * h[3]) < 1e-16
+    assert abs(np.sum(g * g) - 1.0) < 1e-15
+
+
+def test_db2_golden_taps():
+    """Taps against the decimal values stored in tests/golden."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "db2_taps.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    gold_h = np.array([float(r[1]) for r in rows if r[0] == "h"])
+    h, g = O.db2_filters()
+    assert np.max(np.abs(h - gold_h)) < 1e-15
+
+
+# ---------------------------------------------------------------- DWT
+
+def _fft_analysis_1d(x, filt):
+    """Periodic correlation y_j = sum_m f_m x[(j+m) mod M] by FFT, then the
+    even samples: an independent route to one analysis step."""
+    M = x.shape[-1]
+    f = np.zeros(M)
+    f[: len(filt)] = filt
+    y = np.real(np.fft.ifft(np.fft.fft(x, axis=-1) * np.conj(np.fft.fft(f)), axis=-1))
+    return y[..., 0::2]
+
+
+def _fft_dwt2_one_level(img):
+    h, g = O.db2_filters()
+    rows_a = _fft_analysis_1d(img, h)
+    rows_d = _fft_analysis_1d(img, g)
+    out = np.zeros_like(img)
+    H, W = img.shape
+    for half, blk in ((0, rows_a), (1, rows_d)):
+        ca = _fft_analysis_1d(blk.T, h).T   # column low-pass
+        cd = _fft_analysis_1d(blk.T, g).T   # column high-pass
+        out[: H // 2, half * W // 2:(half + 1) * W // 2] = ca
+        out[H // 2:, half * W // 2:(half + 1) * W // 2] = cd
+    return out
+
+
+@pytest.mark.parametrize("H,W", [(8, 8), (16, 12), (6, 10), (32, 64)])
+def test_dwt_one_level_matches_fft_route(H, W):
+    rng = np.random.default_rng(H * 100 + W)
+    x = rng.standard_normal((H, W))
+    assert np.max(np.abs(O.dwt2(x, 1) - _fft_dwt2_one_level(x))) < 1e-12
+
+
+def test_dwt_multilevel_matches_fft_route():
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((32, 48))
+    ref = _fft_dwt2_one_level(x)
+    ref[:16, :24] = _fft_dwt2_one_level(ref[:16, :24])
+    ref[:8, :12] = _fft_dwt2_one_level(ref[:8, :12])
+    assert np.max(np.abs(O.dwt2(x, 3) - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("shape,L", [((64, 64), 2), ((352, 96), 5), ((3, 40, 24), 3), ((16, 8), 3)])
+def test_dwt_perfect_reconstruction_and_parseval(shape, L):
+    rng = np.random.default_rng(sum(shape) + L)
+    x = rng.standard_normal(shape) * 3.0 + 1.0
+    c = O.dwt2(x, L)
+    assert np.linalg.norm(O.idwt2(c, L) - x) / np.linalg.norm(x) < 1e-12
+    assert abs(np.sum(c * c) - np.sum(x * x)) < 1e-12 * np.sum(x * x)
+
+
+def test_dwt_matrix_is_orthogonal_brute_force():
+    H, W, L = 8, 8, 2
+    n = H * W
+    M = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        M[:, j] = O.dwt2(e.reshape(H, W), L).ravel()
+    assert np.max(np.abs(M.T @ M - np.eye(n))) < 1e-13
+    Minv = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        Minv[:, j] = O.idwt2(e.reshape(H, W), L).ravel()
+    assert np.max(np.abs(Minv - M.T)) < 1e-13   # synthesis is the transpose
+
+
+def test_dwt_delta_gives_taps():
+    """A delta at (0, 0) hits output k only through tap m = -2k mod M."""
+    h, g = O.db2_filters()
+    x = np.zeros((8, 8))
+    x[0, 0] = 1.0
+    c = O.dwt2(x, 1)
+    # row 0 only gets taps at k=0 (m=0); wrap k=3 (2*3 + 2 = 8 = 0 mod 8) gets m=2
+    assert abs(c[0, 0] - h[0] * h[0]) < 1e-15
+    assert abs(c[0, 3] - h[0] * h[2]) < 1e-15
+    assert abs(c[0, 4] - h[0] * g[0]) < 1e-15       # row detail, col low
+    assert abs(c[4, 0] - g[0] * h[0]) < 1e-15       # col detail, row low
+    assert abs(c[7, 7] - g[2] * g[2]) < 1e-15
+    assert np.count_nonzero(np.abs(c) > 1e-15) == 16
+
+
+def test_dwt_constant_and_ramp_have_no_detail():
+    L = 3
+    c = O.dwt2(np.full((32, 32), 2.5), L)
+    det = c.copy()
+    det[:4, :4] = 0
+    assert np.max(np.abs(det)) < 1e-13
+    # a linear ramp along W: row details vanish except where the filter wraps
+    x = np.tile(np.arange(32.0), (16, 1))
+    c1 = O.dwt2(x, 1)
+    row_detail = c1[:8, 16:]
+    assert np.max(np.abs(row_detail[:, :-1])) < 1e-12
+    assert np.max(np.abs(row_detail[:, -1])) > 1.0
+
+
+def test_symmetric_pad_and_shape():
+    assert O.padded_shape(349, 1905, 5) == (352, 1920)
+    assert O.padded_shape(64, 64, 2) == (64, 64)
+    x = np.arange(5.0)[None, :] * np.ones((3, 1))
+    xp = O.pad_symmetric(x, 4, 8)
+    assert np.array_equal(xp[0], [0, 1, 2, 3, 4, 3, 2, 1])
+    assert np.array_equal(xp[3], xp[1])
+
+
+# ---------------------------------------------------------------- soft threshold
+
+def test_soft_threshold_is_prox_of_l1():
+    grid = np.linspace(-6, 6, 120001)
+    for c in (-3.3, -0.4, 0.0, 0.7, 2.5):
+        for lam in (0.0, 0.5, 1.0):
+            obj = 0.5 * (grid - c) ** 2 + lam * np.abs(grid)
+            assert abs(grid[np.argmin(obj)] - O.soft_threshold(c, lam)) < 2e-4
+    c = np.linspace(-4, 4, 81)
+    assert np.array_equal(O.soft_threshold(-c, 1.3), -O.soft_threshold(c, 1.3))
+    assert np.array_equal(O.soft_threshold(c, 0.0), c)
+
+
+# ---------------------------------------------------------------- eigen
+
+def _power_deflation(A, iters=3000):
+    A = A.copy()
+    p = A.shape[0]
+    vals, vecs = [], []
+    rng = np.random.default_rng(0)
+    for _ in range(p):
+        v = rng.standard_normal(p)
+        v /= np.linalg.norm(v)
+        for _ in range(iters):
+            w = A @ v
+            v = w / np.linalg.norm(w)
+        lam = v @ A @ v
+        vals.append(lam)
+        vecs.append(v)
+        A = A - lam * np.outer(v, v)
+    return np.array(vals), np.array(vecs).T
+
+
+@pytest.mark.parametrize("p", [3, 4, 6, 8])
+def test_eig_against_power_iteration(p):
+    rng = np.random.default_rng(p)
+    Q, _ = np.linalg.qr(rng.standard_normal((p, p)))
+    lam = 10.0 * 0.6 ** np.arange(p)
+    A = (Q * lam) @ Q.T
+    e, V = O.eig_desc(A)
+    pe, pv = _power_deflation(A)
+    assert np.max(np.abs(e - pe)) < 1e-12 * lam[0]
+    for i in range(p):
+        assert abs(abs(V[:, i] @ pv[:, i]) - 1.0) < 1e-10
+    assert np.max(np.abs((V * e) @ V.T - A)) < 1e-13 * lam[0]
+    assert np.max(np.abs(V.T @ V - np.eye(p))) < 1e-13
+    assert np.all(np.diff(e) <= 0)
+    assert np.all(V[np.argmax(np.abs(V), axis=0), np.arange(p)] > 0)
+
+
+# ---------------------------------------------------------------- noise estimate
+
+def test_noise_routes_agree_c0():
+    c = make_cube(64, 64, 32, m=4, seed=1)
+    R = O.gram(c["Y"])
+    s1 = O.noise_est_regression(R, 64 * 64)
+    s2 = O.noise_est_schur(R, 64 * 64)
+    s3 = O.noise_est_lstsq(c["Y"])
+    assert np.max(np.abs(s1 / s2 - 1)) < 1e-10
+    assert np.max(np.abs(s1 / s3 - 1)) < 1e-9
+
+
+def test_noise_regression_exact_on_constructed_residual():
+    """If y_b = Y_-b beta + e with e orthogonal to the regressors, the
+    regression residual power is exactly |e|^2 / n."""
+    rng = np.random.default_rng(3)
+    n, p = 500, 6
+    for b in range(p):
+        others = rng.standard_normal((n, p - 1))
+        q, _ = np.linalg.qr(others)
+        e = rng.standard_normal(n)
+        e -= q @ (q.T @ e)
+        yb = others @ rng.standard_normal(p - 1) + e
+        Y = np.insert(others, b, yb, axis=1).T.reshape(p, 20, 25)
+        s = O.noise_est_regression(O.gram(Y), n)
+        assert abs(s[b] ** 2 - (e @ e) / n) < 1e-10 * (e @ e) / n
+
+
+def test_noise_recovers_planted_sigma():
+    """Median relative error of the planted per-band sigma within 5 %.
+
+    The regression has noisy regressors, so bands whose signal is poorly
+    predicted by the others are biased upward (errors-in-variables); the
+    estimate must never be below the truth by more than sampling error."""
+    for (H, W, p, m, seed) in [(64, 64, 32, 4, 1), (128, 128, 64, 8, 5)]:
+        c = make_cube(H, W, p, m=m, seed=seed)
+        s = O.noise_est_regression(O.gram(c["Y"]), H * W)
+        rel = s / c["sigma"] - 1.0
+        assert np.median(np.abs(rel)) < 0.05
+        assert rel.min() > -4.0 / np.sqrt(H * W) - 0.02
+
+
+# ---------------------------------------------------------------- SURE
+
+def test_sure_is_unbiased_monte_carlo():
+    """With the basis and noise levels fixed independently of the noise,
+    SURE(r, lambda) is an unbiased estimate of the whitened squared error.
+    64 noise draws; every (r, k) cell within 4.5 standard errors and 90 %
+    within 2.5."""
+    H, W, p, L, K = 32, 32, 12, 2, 16
+    base = make_cube(H, W, p, m=3, seed=11)
+    Xc = base["X"].astype(np.float64)
+    sigma = base["sigma"]
+    Xw = Xc.reshape(p, -1) / sigma[:, None]
+    _, V = O.eig_desc(Xw @ Xw.T)       # full p x p basis from the clean cube
+    rng = np.random.default_rng(12345)
+    lams = O.lambda_grid(H * W, K)
+    det_mask = np.ones((H, W), bool)
+    det_mask[: H >> L, : W >> L] = False
+    C_clean = O.dwt2((V.T @ Xw).reshape(p, H, W), L)
+    sure_vals, loss_vals = [], []
+    for _ in range(64):
+        Yw = Xw + rng.standard_normal(Xw.shape)
+        C = O.dwt2((V.T @ Yw).reshape(p, H, W), L)
+        S, S_inf = O.sure_table(C, L, lams)
+        T = O.sure_rank_lambda(S, S_inf)
+        loss = np.empty_like(T)
+        for r in range(1, p + 1):
+            for k, lam in enumerate(lams):
+                Ch = C.copy()
+                Ch[r:] = 0.0
+                Ch[:r, det_mask] = O.soft_threshold(Ch[:r, det_mask], lam)
+                loss[r - 1, k] = np.sum((Ch - C_clean) ** 2)
+        sure_vals.append(T)
+        loss_vals.append(loss)
+    diff = np.array(sure_vals) - np.array(loss_vals)
+    z = diff.mean(axis=0) / (diff.std(axis=0, ddof=1) / np.sqrt(diff.shape[0]))
+    assert np.max(np.abs(z)) < 4.5
+    assert np.mean(np.abs(z) < 2.5) > 0.9
+
+
+def test_sure_single_component_closed_form():
+    """Tiny hand case: LL = 1 coefficient, 3 detail coefficients."""
+    C = np.zeros((1, 2, 2))
+    C[0] = [[5.0, 0.5], [-2.0, 1.5]]
+    S, S_inf = O.sure_table(C, 1, np.array([0.0, 1.0, 3.0]))
+    # lam = 0: N - 2*0 + 0 = 4 (no detail coefficient is exactly 0)
+    # lam = 1: 4 - 2*1 + (0.25 + 1 + 1) = 4.25
+    # lam = 3: 4 - 2*3 + (0.25 + 4 + 2.25) = 4.5
+    assert np.allclose(S[0], [4.0, 4.25, 4.5], atol=1e-15)
+    assert abs(S_inf[0] - (25 + 0.25 + 4 + 2.25 - 4)) < 1e-14
+
+
+def test_selection_tie_break_and_layout():
+    S = np.array([[5.0, 3.0, 3.0], [1.0, 1.0, 2.0]])
+    S_inf = np.array([4.0, 0.0])
+    r, k, T, gap = O.select_rank_lambda(S, S_inf)
+    # T[0] = S[0] + S_inf[1] = [5, 3, 3]; T[1] = S[0] + S[1] = [6, 4, 5]
+    assert np.array_equal(T, [[5.0, 3.0, 3.0], [6.0, 4.0, 5.0]])
+    assert (r, k) == (1, 1) and gap == 0.0
+
+
+# ---------------------------------------------------------------- whole path
+
+def test_full_rank_zero_lambda_is_identity():
+    c = make_cube(30, 45, 10, m=3, seed=21)  # padded to 32 x 48 at L=3
+    o = O.hyres(c["Y"], 3, 10, rank=10, lam=0.0)
+    assert O.rel_l2(o["X"], c["Y"]) < 1e-12
+
+
+def test_zero_lambda_is_truncated_whitened_pca():
+    c = make_cube(40, 36, 12, m=3, seed=22)
+    p, H, W = c["Y"].shape
+    o = O.hyres(c["Y"], 2, 12, rank=4, lam=0.0)
+    Yw = c["Y"].reshape(p, -1).astype(np.float64).T / o["sigma"]
+    U, s, Wt = np.linalg.svd(Yw, full_matrices=False)
+    Xw = (U[:, :4] * s[:4]) @ Wt[:4]
+    ref = (Xw * o["sigma"]).T.reshape(p, H, W)
+    assert O.rel_l2(o["X"], ref) < 1e-10
+
+
+def test_scale_and_permutation_equivariance():
+    c = make_cube(32, 40, 16, m=4, seed=23)
+    Y = c["Y"].astype(np.float64)
+    o = O.hyres(Y, 2, 8)
+    o2 = O.hyres(3.5 * Y, 2, 8)
+    assert (o2["rank"], o2["k"]) == (o["rank"], o["k"])
+    assert O.rel_l2(o2["X"], 3.5 * o["X"]) < 1e-10
+    perm = np.random.default_rng(0).permutation(16)
+    o3 = O.hyres(Y[perm], 2, 8)
+    assert (o3["rank"], o3["k"]) == (o["rank"], o["k"])
+    assert O.rel_l2(o3["X"], o["X"][perm]) < 1e-10
+
+
+def test_c0_selects_planted_rank_and_denoises():
+    c = make_cube(64, 64, 32, m=4, seed=1)
+    o = O.hyres(c["Y"], 2, 8)
+    assert o["rank"] == 4
+    assert O.psnr(c["X"], o["X"]) > O.psnr(c["X"], c["Y"]) + 10.0
+    assert O.sam(c["X"], o["X"]) < O.sam(c["X"], c["Y"])
