@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 HyRes path.
+
+One step = one full HyRes denoise (all stages: Gram, noise regression,
+eigensolver, projection, DWT, SURE selection, threshold + inverse DWT,
+back-projection) of a 349 x 1905 x 144 float32 cube (the Houston-2013 shape
+of the paper's experiments, Sec. 3) with 5 db2 levels, r <= 20 and K = 64
+threshold candidates. The metric is Mvoxel/s (input voxels per second).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank denoises its own
+cube (independent replicas, no collective on the data path: weak scaling);
+``value`` is all ranks' voxels over the slowest rank's time.
+
+The reference arm (``--impl reference``) times the FP64 CPU oracle on a
+bounded column slice of the same cube on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HyRes Mvoxel/s on 1 GB300 (plain vs batched/mixed, ≤1e-3 rel err); % HBM roofline"
+UNIT = "Mvoxel/s"
+WORKLOAD = dict(H=349, W=1905, p=144, m=12, snr_db=10.0, seed=2, levels=5, r_max=20, n_lambda=64)
+L2_BYTES = 129 * 1024 * 1024
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FMA/clk x 2 x max clock
+PAPER_A100_MVOXEL_S = 302.0   # 95.7 Mvoxel / 0.317 s (HyRes, A100, FP32, Houston 20 dB)
+
+
+def _measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), bf16_tflops=float(d["bf16_tflops"]),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, source="fallback")
+
+
+def _config(n_gpus: int) -> dict:
+    w = WORKLOAD
+    return {
+        "workload": (f"HyRes denoise of a {w['H']}x{w['W']}x{w['p']} float32 synthetic cube "
+                     f"(Houston-2013 shape, {w['m']} endmembers, SNR {w['snr_db']:.0f} dB), db2 "
+                     f"L={w['levels']}, r<={w['r_max']}, K={w['n_lambda']}"),
+        "H": w["H"], "W": w["W"], "p": w["p"], "levels": w["levels"], "r_max": w["r_max"],
+        "n_lambda": w["n_lambda"], "precision": "fp32",
+        "l2": "input 383 MB > L2, and a 256 MB buffer is written between timed steps",
+        "parallelism": f"replicas x{n_gpus}",
+    }
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def _oracle_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads", 0) for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_sample_rate(cube, cols: int, runs: int) -> dict:
+    """Time the FP64 oracle on the first ``cols`` columns of the cube."""
+    import oracle as O
+    w = WORKLOAD
+    Ys = cube["Y"][:, :, :cols].copy()
+    vox = Ys.size
+    ts = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        O.hyres(Ys, w["levels"], w["r_max"], w["n_lambda"])
+        ts.append(time.perf_counter() - t0)
+    return dict(value=vox / 1e6 / statistics.mean(ts), times=ts, voxels=vox,
+                sample=f"oracle on the {w['H']}x{cols}x{w['p']} column slice "
+                       f"({vox / 1e6:.1f} Mvoxel), {runs} runs, mean time")
+
+
+# --------------------------------------------------------------- bench
+
+def _dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+        return dist, world, rank, local
+    return None, 1, 0, local
+
+
+def _stage_bytes(r_star: int) -> dict:
+    w = WORKLOAD
+    n = w["H"] * w["W"]
+    q = 1 << w["levels"]
+    N = (-(-w["H"] // q) * q) * (-(-w["W"] // q) * q)
+    p, r = w["p"], w["r_max"]
+    return {
+        "gram": 4 * n * p,
+        "project": 4 * n * p + 4 * r * N,
+        "dwt": 8 * r * N,
+        "sure": 4 * r * N,
+        "idwt": 4 * r_star * N + 4 * r_star * n,
+        "backproject": 4 * r_star * n + 4 * p * n,
+    }
+
+
+def run_gb300(args) -> None:
+    import numpy as np
+    import torch
+    from paper_2204_06979_gb300 import api, _lib
+    from synth import make_cube
+
+    dist, world, rank, local = _dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOAD
+    cube = make_cube(w["H"], w["W"], w["p"], m=w["m"], snr_db=w["snr_db"], seed=w["seed"])
+    p, H, W = w["p"], w["H"], w["W"]
+    n = H * W
+    voxels = p * n
+    Yd = torch.from_numpy(cube["Y"]).to(dev)
+    Xd = torch.empty_like(Yd)
+    h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev)
+    lib = _lib.load()
+    launches_per_step = lib.hyde_hyres_kernel_launches(h.params)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 0)):
+        h(Yd, Xd)
+    torch.cuda.synchronize(dev)
+    info = h.result_info()
+
+    # ---- device-timed steps (each step between its own events, L2 flushed between)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    wall0 = time.perf_counter()
+    with clocks:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            h(Yd, Xd)
+            ev[i][1].record(stream)
+        barrier()
+    wall = time.perf_counter() - wall0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * voxels * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- per-stage timing through the timed entry point (same launches)
+    nst = _lib.N_STAGES
+    stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
+                for _ in range(args.steps)]
+    import ctypes
+    stage_ms = {name: [] for name in _lib.STAGE_NAMES}
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        arr = (ctypes.c_void_p * (nst + 1))(*[e.cuda_event for e in stage_ev[i]])
+        code = lib.hyde_hyres_denoise_timed(
+            Yd.data_ptr(), Xd.data_ptr(), p, H, W, ctypes.byref(h.params), h.info.data_ptr(),
+            h.ws.data_ptr(), h.ws.numel(), stream.cuda_stream, arr)
+        if code != 0:
+            raise RuntimeError(f"hyde_hyres_denoise_timed failed: {code}")
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        for s, name in enumerate(_lib.STAGE_NAMES):
+            stage_ms[name].append(stage_ev[i][s].elapsed_time(stage_ev[i][s + 1]))
+    stage_avg = {k: statistics.mean(v) for k, v in stage_ms.items()}
+    info = h.result_info()
+    r_star = int(info["rank"])
+    peaks = _measured_peaks()
+    sbytes = _stage_bytes(r_star)
+    dominant = max(stage_avg, key=stage_avg.get)
+    if dominant == "gram":
+        flops = n * p * (p + 1)   # the symmetric product computed: n p (p+1)/2 FMAs
+        achieved = flops / (stage_avg["gram"] / 1e3) / 1e12
+        roofline = {"kernel": "gram (gram_partial + gram_reduce)", "bound": "alu",
+                    "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz",
+                    "algorithmic": f"{flops:.4g} flop per launch"}
+    elif dominant in sbytes:
+        bts = sbytes[dominant]
+        achieved = bts / (stage_avg[dominant] / 1e3) / 1e9
+        roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": peaks["source"],
+                    "algorithmic": f"{bts} bytes per launch"}
+    else:
+        roofline = {"kernel": dominant, "bound": "latency", "achieved": None, "peak": None,
+                    "unit": None, "frac": None, "traffic": None}
+    hbm_stages = {}
+    for k, bts in sbytes.items():
+        gbs = bts / (stage_avg[k] / 1e3) / 1e9
+        hbm_stages[k] = {"ms": round(stage_avg[k], 4), "GB/s": round(gbs, 1),
+                         "frac_hbm": round(gbs / peaks["hbm_gbs"], 3)}
+
+    # ---- end to end through the public call with host buffers
+    Yh = torch.from_numpy(cube["Y"]).pin_memory()
+    Xh = torch.empty_like(Yh).pin_memory()
+    info_h = torch.empty(h.info.numel(), dtype=torch.uint8).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for _ in range(2):
+        Yd.copy_(Yh, non_blocking=True)
+        h(Yd, Xd)
+        Xh.copy_(Xd, non_blocking=True)
+        info_h.copy_(h.info, non_blocking=True)
+    barrier()
+    for i in range(args.steps):
+        e2e_ev[i][0].record(stream)
+        Yd.copy_(Yh, non_blocking=True)
+        h(Yd, Xd)
+        Xh.copy_(Xd, non_blocking=True)
+        info_h.copy_(h.info, non_blocking=True)
+        e2e_ev[i][1].record(stream)
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * voxels * args.steps / (e2e_ms / 1e3) / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample_rate(cube, cols=args.cpu_cols, runs=args.cpu_runs)
+        cpu = {"value": round(s["value"], 3), "unit": UNIT, "cores": _oracle_threads(),
+               "kind": "oracle", "sample": s["sample"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": _config(world),
+            "roofline": roofline,
+            "stages": hbm_stages | {k: {"ms": round(v, 4)} for k, v in stage_avg.items()
+                                    if k not in hbm_stages},
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": int(Yh.numel() * 4),
+                    "d2h_bytes_per_step": int(Xh.numel() * 4 + info_h.numel())},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+            "selection": {"rank": r_star, "lambda_index": info["lambda_index"],
+                          "status": info["status"]},
+            "wall_s_timed": round(wall, 3),
+            "context": {"paper_a100_fp32_mvoxel_s": PAPER_A100_MVOXEL_S,
+                        "note": "paper: HyRes on the real Houston cube at 20 dB on an A100 "
+                                "(0.317 s); context only"},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    _ = np
+
+
+def run_reference(args) -> None:
+    from synth import make_cube
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOAD
+    cube = make_cube(w["H"], w["W"], w["p"], m=w["m"], snr_db=w["snr_db"], seed=w["seed"])
+    import oracle as O
+    Ys = cube["Y"][:, :, :args.cpu_cols].copy()
+    for _ in range(max(args.warmup, 0)):
+        O.hyres(Ys, w["levels"], w["r_max"], w["n_lambda"])
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.hyres(Ys, w["levels"], w["r_max"], w["n_lambda"])
+        ts.append(time.perf_counter() - t0)
+    vox = Ys.size
+    value = vox * len(ts) / sum(ts) / 1e6
+    sample = (f"FP64 numpy oracle on the {w['H']}x{args.cpu_cols}x{w['p']} column slice "
+              f"({vox / 1e6:.1f} Mvoxel) of the cube, one slice per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(ts) / len(ts), 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(world),
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": _oracle_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
+    ap.add_argument("--cpu-cols", type=int, default=384,
+                    help="columns of the cube in the CPU oracle sample")
+    ap.add_argument("--cpu-runs", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * hyde.h -- C ABI of the GB300 HyRes library (libhyde.so).
+ *
+ * HyRes is the automatic, parameter-free, low-rank, wavelet-based Gaussian
+ * denoiser for hyperspectral images packaged by HyDe (arXiv 2204.06979,
+ * Sec. 2.1). This library runs its data-parallel path on one GPU:
+ *
+ *   Gram matrix -> per-band noise level by multiple regression -> whitening
+ *   -> eigendecomposition (spectral subspace) -> rank-r_max projection ->
+ *   per-component 2D db2 DWT -> SURE table over (rank, lambda) -> selection
+ *   -> soft threshold + inverse DWT -> back-projection and un-whitening.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Cubes are band-major (BSQ): float[p][H][W], C-contiguous, in DEVICE
+ *   memory. A pixel is one (y, x); n = H * W. The library reads the cube as
+ *   the n x p matrix Y whose rows are pixels and columns are bands.
+ * - Every pointer argument is device memory owned by the caller unless the
+ *   comment says otherwise. The library never allocates or frees memory;
+ *   scratch space is a caller-provided workspace whose size comes from the
+ *   matching *_workspace_size query. Workspaces must be 256-byte aligned and
+ *   must not be shared by calls that can run concurrently.
+ * - Work is enqueued asynchronously on the given stream (0 = the legacy
+ *   default stream); no entry point synchronises the host or reads device
+ *   memory back. Results are valid once the stream has reached them.
+ * - Argument errors detectable on the host return a status immediately and
+ *   enqueue nothing. Errors only the device can see (NaN/Inf input, a Gram
+ *   matrix that is not positive definite, a non-positive noise level) are
+ *   written to a status word (hyde_hyres_info.status, or the status output of
+ *   the stage call); the host reads it after synchronising.
+ * - Sizes: 2 <= p <= 256 bands for the Gram and noise stages; the
+ *   eigensolver and noise solve hold a p x p float matrix in one SM's shared
+ *   memory, which bounds p (about 208 at r_max = 20, see hyde_workspace_size).
+ *   1 <= levels <= 10; the padded sides H_p, W_p (H, W rounded up to
+ *   multiples of 2^levels) need H_p - H <= H - 1 and W_p - W <= W - 1 (the
+ *   reflection must stay inside the image).
+ */
+#ifndef HYDE_H
+#define HYDE_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HYDE_OK = 0,
+    HYDE_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, misaligned buffer */
+    HYDE_ERR_SHAPE = 2,         /* sizes outside the supported range        */
+    HYDE_ERR_NUMERIC = 3,       /* NaN/Inf, non-SPD Gram, sigma <= 0        */
+    HYDE_ERR_NOT_CONVERGED = 4, /* eigensolver iteration limit               */
+    HYDE_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up        */
+    HYDE_ERR_CUDA = 6,          /* a CUDA runtime call or launch failed      */
+    HYDE_ERR_WORKSPACE = 7      /* workspace missing or too small            */
+} hyde_status;
+
+typedef enum {
+    HYDE_PREC_FP32 = 0,    /* plain FP32 SIMT arithmetic                      */
+    HYDE_PREC_TF32X3 = 1,  /* reserved: split-TF32 tensor-core contractions   */
+    HYDE_PREC_BF16X3 = 2   /* reserved: split-BF16 tensor-core contractions   */
+} hyde_precision;
+
+/* Parameters of one HyRes run. */
+typedef struct {
+    int wavelet;    /* number of vanishing moments of the Daubechies filter;
+                       2 (db2) is the only supported value                  */
+    int levels;     /* DWT levels L, 1..10                                  */
+    int r_max;      /* largest rank tried, 1..min(p, 32)                    */
+    int n_lambda;   /* K threshold candidates, 2..256; 64 is the default    */
+    int precision;  /* hyde_precision                                       */
+    int reserved[3];/* must be zero                                         */
+} hyde_hyres_params;
+
+/* Outcome of one HyRes run, written by the device into caller memory. */
+typedef struct {
+    int status;        /* hyde_status seen on the device (HYDE_OK if none)   */
+    int rank;          /* selected rank r*, 1..r_max                          */
+    int lambda_index;  /* selected candidate k*, 0..K-1                       */
+    int reserved;
+    double lambda;     /* selected threshold lambda_{k*} (whitened units)     */
+    double sure_min;   /* minimum total SURE                                  */
+    double sure_gap;   /* (runner-up - minimum) / |minimum|                   */
+} hyde_hyres_info;
+
+/* Byte offsets of the intermediates hyde_hyres_denoise leaves in its
+ * workspace (for inspection after the stream has finished). */
+typedef struct {
+    size_t total;      /* workspace bytes needed                            */
+    size_t R;          /* double[p][p]   Gram matrix Y^T Y                  */
+    size_t sigma;      /* double[p]      per-band noise std                  */
+    size_t evals;      /* double[r_max]  leading eigenvalues of D^-1 R D^-1  */
+    size_t V;          /* double[p][r_max] eigenvectors, row b = band b      */
+    size_t coef;       /* float[r_max][H_p][W_p] wavelet coefficients        */
+    size_t sure;       /* double[r_max][K] SURE of thresholding component i  */
+    size_t sure_inf;   /* double[r_max]  SURE of dropping component i        */
+    size_t sure_total; /* double[r_max][K] total SURE of rank r=i+1, lambda_k */
+    size_t status;     /* int            device status word                  */
+} hyde_ws_layout;
+
+/* Human-readable name of a status code (static storage). */
+const char* hyde_status_string(hyde_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int hyde_version(void);
+
+/* ------------------------------------------------------------------ Gram
+ * R = Y^T Y, the uncentred p x p Gram (covariance) matrix of the n x p
+ * pixel-by-band matrix; the spectral statistics of the low-rank model
+ * (Sec. 2.1, "low-rank"). Y is float[p][n] band-major (ld = n); R is
+ * double[p][p] row-major, full symmetric. Per-block float partial sums are
+ * combined in double. precision must be HYDE_PREC_FP32.
+ */
+hyde_status hyde_gram_workspace_size(int p, long long n, int precision,
+                                     size_t* bytes);
+hyde_status hyde_gram(const float* Y, int p, long long n, int precision,
+                      double* R, void* ws, size_t ws_bytes,
+                      cudaStream_t stream);
+
+/* ------------------------------------------------------------ noise level
+ * Per-band noise standard deviation by multiple regression of each band on
+ * all other bands (least squares, no intercept): sigma_b^2 is the residual
+ * sum of squares over n, i.e. 1 / (n [R^-1]_bb) (the HySime-style estimator
+ * of Sec. 2.1). Y is float[p][H][W]; sigma is double[p]. The inverse is
+ * formed in float by Gauss-Jordan on the diagonally scaled matrix and its
+ * diagonal is corrected by one double-precision Newton step. status (device
+ * int, may be NULL) receives HYDE_ERR_NUMERIC if R is not positive definite
+ * or a sigma_b^2 is not positive.
+ */
+hyde_status hyde_noise_est_workspace_size(int p, int H, int W, size_t* bytes);
+hyde_status hyde_noise_est(const float* Y, int p, int H, int W, double* sigma,
+                           int* status, void* ws, size_t ws_bytes,
+                           cudaStream_t stream);
+
+/* ----------------------------------------------------------- eigenvectors
+ * Leading r eigenpairs of a symmetric positive semi-definite p x p matrix A
+ * (double, row-major): the spectral subspace of the low-rank model
+ * (Sec. 2.1). evals (double[r]) are in descending order; V is double[p][r]
+ * (column i = eigenvector i); the entry of largest magnitude of each
+ * eigenvector is positive. Householder tridiagonalisation, multisection for
+ * the eigenvalues, twisted-factorisation eigenvectors and a Gram-Schmidt
+ * pass, all in float in one thread block. status as above.
+ */
+hyde_status hyde_eig_sym_top(const double* A, int p, int r, double* evals,
+                             double* V, int* status, cudaStream_t stream);
+
+/* -------------------------------------------------------------------- DWT
+ * L-level separable 2D periodic db2 analysis of a batch of images.
+ * in: float[batch][H][W]; each image is first extended at the bottom and
+ * right to H_p x W_p by whole-sample symmetric reflection
+ * (x[M + j] = x[M - 2 - j]). coef: float[batch][H_p][W_p] in Mallat layout
+ * (LL of the last level top-left; at each level the row-detail band is right
+ * of LL, the column-detail band below it, the diagonal band diagonally).
+ * One level: a_k = sum_m h_m x[(2k+m) mod M], d_k = sum_m g_m x[(2k+m) mod M]
+ * along rows, then along columns, g_m = (-1)^m h_{3-m}.
+ * hyde_idwt2 is the exact transpose (the inverse of the periodic transform)
+ * followed by cropping to H x W. wavelet must be 2.
+ */
+hyde_status hyde_dwt_workspace_size(int batch, int H, int W, int levels,
+                                    size_t* bytes);
+hyde_status hyde_dwt2(const float* in, float* coef, int batch, int H, int W,
+                      int wavelet, int levels, void* ws, size_t ws_bytes,
+                      cudaStream_t stream);
+hyde_status hyde_idwt2(const float* coef, float* out, int batch, int H, int W,
+                       int wavelet, int levels, void* ws, size_t ws_bytes,
+                       cudaStream_t stream);
+
+/* --------------------------------------------------------------- SURE
+ * Stein's unbiased risk estimate of soft-thresholding each coefficient image
+ * (unit noise variance), on the candidate grid
+ * lambda_k = k sqrt(2 ln N) / (K - 1), k = 0..K-1, N = H_p W_p:
+ *   S[i][k] = N - 2 #{detail : |c| <= lambda_k}
+ *             + sum_detail min(c^2, lambda_k^2)
+ * (the LL band of the last level is kept and contributes 1 per coefficient),
+ * and S_inf[i] = sum_all c^2 - N (the risk of dropping image i).
+ * coef: float[batch][H_p][W_p] Mallat layout; S: double[batch][K];
+ * S_inf: double[batch]. Counts are exact integers; sums of squares are
+ * accumulated in float per thread and in double across blocks.
+ */
+hyde_status hyde_sure_workspace_size(int batch, int K, size_t* bytes);
+hyde_status hyde_sure_table(const float* coef, int batch, int Hp, int Wp,
+                            int levels, int K, double* S, double* S_inf,
+                            void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------- whole HyRes
+ * Denoise Y (float[p][H][W]) into X (float[p][H][W]; may not alias Y).
+ * Rank r* in 1..r_max and threshold lambda_{k*} minimise the total SURE
+ *   T(r, k) = sum_{i<=r} S_i(lambda_k) + sum_{r<i<=r_max} S_i(inf)
+ * (ties: smallest r, then smallest k). info (device) receives the choice
+ * and the device status; NULL is allowed.
+ */
+hyde_status hyde_workspace_size(int p, int H, int W,
+                                const hyde_hyres_params* params,
+                                size_t* bytes);
+hyde_status hyde_workspace_layout(int p, int H, int W,
+                                  const hyde_hyres_params* params,
+                                  hyde_ws_layout* layout);
+hyde_status hyde_hyres_denoise(const float* Y, float* X, int p, int H, int W,
+                               const hyde_hyres_params* params,
+                               hyde_hyres_info* info, void* ws,
+                               size_t ws_bytes, cudaStream_t stream);
+
+/* Stage boundaries of hyde_hyres_denoise_timed, in enqueue order. */
+#define HYDE_N_STAGES 8   /* gram, noise, eig+weights, projection, DWT,
+                             SURE+selection, threshold+IDWT, back-projection */
+
+/* Same as hyde_hyres_denoise, and records events[0] before the first stage
+ * and events[s+1] after stage s (HYDE_N_STAGES + 1 events created by the
+ * caller) on the stream, so the caller can time each stage with
+ * cudaEventElapsedTime after synchronising. For measurement only. */
+hyde_status hyde_hyres_denoise_timed(const float* Y, float* X, int p, int H,
+                                     int W, const hyde_hyres_params* params,
+                                     hyde_hyres_info* info, void* ws,
+                                     size_t ws_bytes, cudaStream_t stream,
+                                     cudaEvent_t* events);
+
+/* Number of kernels one hyde_hyres_denoise call launches (10 + 2 * levels;
+ * the workspace clear is a memset, not counted), or -1 for bad params. */
+int hyde_hyres_kernel_launches(const hyde_hyres_params* params);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDE_H */

@@ -1,0 +1,242 @@
+"""PyTorch-facing binding of libhyde (argument marshalling only).
+
+Every function takes CUDA tensors, allocates outputs and workspaces with
+torch's allocator, and calls the matching C entry point on the current torch
+stream. All arithmetic runs in the library's CUDA kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import struct
+
+import torch
+
+from . import _lib
+from ._lib import HydeParams, HydeWsLayout, INFO_BYTES, INFO_FORMAT
+
+HYDE_OK = 0
+PREC_FP32 = 0
+
+
+class HydeError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.load().hyde_status_string(code).decode()
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+def _check(code: int, where: str) -> None:
+    if code != HYDE_OK:
+        raise HydeError(code, where)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _cuda_f32(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    return x.contiguous()
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator returns blocks aligned to at least 512 bytes
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def padded_shape(H: int, W: int, levels: int) -> tuple[int, int]:
+    q = 1 << levels
+    return -(-H // q) * q, -(-W // q) * q
+
+
+def params(levels: int, r_max: int, n_lambda: int = 64, precision: int = PREC_FP32) -> HydeParams:
+    p = HydeParams()
+    p.wavelet = 2
+    p.levels = levels
+    p.r_max = r_max
+    p.n_lambda = n_lambda
+    p.precision = precision
+    return p
+
+
+def version() -> int:
+    return _lib.load().hyde_version()
+
+
+# ------------------------------------------------------------------ stages
+
+def gram(Y: torch.Tensor) -> torch.Tensor:
+    """R = Y^T Y of a cube ``Y[p, ...]`` (float32, CUDA) as float64 ``[p, p]``."""
+    lib = _lib.load()
+    Y = _cuda_f32(Y, "Y")
+    p = Y.shape[0]
+    n = Y.numel() // p
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_gram_workspace_size(p, n, PREC_FP32, ctypes.byref(sz)), "hyde_gram_workspace_size")
+    ws = _workspace(sz.value, Y.device)
+    R = torch.empty((p, p), dtype=torch.float64, device=Y.device)
+    _check(lib.hyde_gram(_ptr(Y), p, n, PREC_FP32, _ptr(R), _ptr(ws), ws.numel(), _stream()),
+           "hyde_gram")
+    return R
+
+
+def noise_est(Y: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+    """Per-band noise std of ``Y[p, H, W]`` by multiple regression.
+    Returns ``(sigma float64[p], status int32[1])``."""
+    lib = _lib.load()
+    Y = _cuda_f32(Y, "Y")
+    p, H, W = Y.shape
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_noise_est_workspace_size(p, H, W, ctypes.byref(sz)), "hyde_noise_est_workspace_size")
+    ws = _workspace(sz.value, Y.device)
+    sigma = torch.empty(p, dtype=torch.float64, device=Y.device)
+    status = torch.zeros(1, dtype=torch.int32, device=Y.device)
+    _check(lib.hyde_noise_est(_ptr(Y), p, H, W, _ptr(sigma), _ptr(status), _ptr(ws), ws.numel(),
+                              _stream()), "hyde_noise_est")
+    return sigma, status
+
+
+def eig_sym_top(A: torch.Tensor, r: int) -> tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+    """Leading r eigenpairs of a symmetric float64 CUDA matrix.
+    Returns ``(evals[r], V[p, r], status[1])``."""
+    lib = _lib.load()
+    if not A.is_cuda or A.dtype != torch.float64:
+        raise ValueError("A must be a float64 CUDA tensor")
+    A = A.contiguous()
+    p = A.shape[0]
+    evals = torch.empty(r, dtype=torch.float64, device=A.device)
+    V = torch.empty((p, r), dtype=torch.float64, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib.hyde_eig_sym_top(_ptr(A), p, r, _ptr(evals), _ptr(V), _ptr(status), _stream()),
+           "hyde_eig_sym_top")
+    return evals, V, status
+
+
+def dwt2(x: torch.Tensor, levels: int) -> torch.Tensor:
+    """Periodic db2 analysis of ``x[B, H, W]`` -> Mallat ``coef[B, Hp, Wp]``."""
+    lib = _lib.load()
+    x = _cuda_f32(x, "x")
+    B, H, W = x.shape
+    Hp, Wp = padded_shape(H, W, levels)
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_dwt_workspace_size(B, H, W, levels, ctypes.byref(sz)), "hyde_dwt_workspace_size")
+    ws = _workspace(sz.value, x.device)
+    coef = torch.empty((B, Hp, Wp), dtype=torch.float32, device=x.device)
+    _check(lib.hyde_dwt2(_ptr(x), _ptr(coef), B, H, W, 2, levels, _ptr(ws), ws.numel(), _stream()),
+           "hyde_dwt2")
+    return coef
+
+
+def idwt2(coef: torch.Tensor, H: int, W: int, levels: int) -> torch.Tensor:
+    """Inverse of ``dwt2``: ``coef[B, Hp, Wp]`` -> ``x[B, H, W]``."""
+    lib = _lib.load()
+    coef = _cuda_f32(coef, "coef")
+    B = coef.shape[0]
+    if tuple(coef.shape[1:]) != padded_shape(H, W, levels):
+        raise ValueError("coef shape does not match (H, W, levels)")
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_dwt_workspace_size(B, H, W, levels, ctypes.byref(sz)), "hyde_dwt_workspace_size")
+    ws = _workspace(sz.value, coef.device)
+    out = torch.empty((B, H, W), dtype=torch.float32, device=coef.device)
+    _check(lib.hyde_idwt2(_ptr(coef), _ptr(out), B, H, W, 2, levels, _ptr(ws), ws.numel(),
+                          _stream()), "hyde_idwt2")
+    return out
+
+
+def sure_table(coef: torch.Tensor, levels: int, K: int = 64) -> tuple[torch.Tensor, torch.Tensor]:
+    """SURE of soft-thresholding each image of ``coef[B, Hp, Wp]`` on the
+    K-point grid, and of dropping it: ``(S[B, K], S_inf[B])`` float64."""
+    lib = _lib.load()
+    coef = _cuda_f32(coef, "coef")
+    B, Hp, Wp = coef.shape
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_sure_workspace_size(B, K, ctypes.byref(sz)), "hyde_sure_workspace_size")
+    ws = _workspace(sz.value, coef.device)
+    S = torch.empty((B, K), dtype=torch.float64, device=coef.device)
+    S_inf = torch.empty(B, dtype=torch.float64, device=coef.device)
+    _check(lib.hyde_sure_table(_ptr(coef), B, Hp, Wp, levels, K, _ptr(S), _ptr(S_inf), _ptr(ws),
+                               ws.numel(), _stream()), "hyde_sure_table")
+    return S, S_inf
+
+
+# ------------------------------------------------------------ whole path
+
+def parse_info(info: torch.Tensor) -> dict:
+    raw = bytes(info.cpu().numpy().tobytes())
+    st, rank, k, _, lam, smin, gap = struct.unpack(INFO_FORMAT, raw[:INFO_BYTES])
+    return dict(status=st, rank=rank, lambda_index=k, lam=lam, sure_min=smin, sure_gap=gap)
+
+
+class HyRes:
+    """Reusable HyRes denoiser for cubes of one shape: owns the workspace and
+    the device info record; ``__call__`` enqueues one denoise on the current
+    stream."""
+
+    def __init__(self, p: int, H: int, W: int, levels: int, r_max: int, n_lambda: int = 64,
+                 device="cuda"):
+        self.lib = _lib.load()
+        self.shape = (p, H, W)
+        self.params = params(levels, r_max, n_lambda)
+        sz = ctypes.c_size_t()
+        _check(self.lib.hyde_workspace_size(p, H, W, ctypes.byref(self.params), ctypes.byref(sz)),
+               "hyde_workspace_size")
+        self.layout = HydeWsLayout()
+        _check(self.lib.hyde_workspace_layout(p, H, W, ctypes.byref(self.params),
+                                              ctypes.byref(self.layout)), "hyde_workspace_layout")
+        self.device = torch.device(device)
+        self.ws = _workspace(sz.value, self.device)
+        self.info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=self.device)
+
+    def __call__(self, Y: torch.Tensor, X: torch.Tensor | None = None) -> torch.Tensor:
+        Y = _cuda_f32(Y, "Y")
+        if tuple(Y.shape) != self.shape:
+            raise ValueError(f"expected a cube of shape {self.shape}")
+        if X is None:
+            X = torch.empty_like(Y)
+        p, H, W = self.shape
+        _check(self.lib.hyde_hyres_denoise(_ptr(Y), _ptr(X), p, H, W, ctypes.byref(self.params),
+                                           _ptr(self.info), _ptr(self.ws), self.ws.numel(),
+                                           _stream()), "hyde_hyres_denoise")
+        return X
+
+    def result_info(self) -> dict:
+        return parse_info(self.info)
+
+    def _view(self, off: int, count: int, dtype: torch.dtype) -> torch.Tensor:
+        es = torch.tensor([], dtype=dtype).element_size()
+        return self.ws[off: off + count * es].view(dtype)
+
+    def intermediates(self) -> dict:
+        """Views into the workspace of the last call's intermediates."""
+        p, H, W = self.shape
+        r, K = self.params.r_max, self.params.n_lambda
+        Hp, Wp = padded_shape(H, W, self.params.levels)
+        L = self.layout
+        return dict(
+            R=self._view(L.R, p * p, torch.float64).view(p, p),
+            sigma=self._view(L.sigma, p, torch.float64),
+            evals=self._view(L.evals, r, torch.float64),
+            V=self._view(L.V, p * r, torch.float64).view(p, r),
+            coef=self._view(L.coef, r * Hp * Wp, torch.float32).view(r, Hp, Wp),
+            S=self._view(L.sure, r * K, torch.float64).view(r, K),
+            S_inf=self._view(L.sure_inf, r, torch.float64),
+            T=self._view(L.sure_total, r * K, torch.float64).view(r, K),
+            status=self._view(L.status, 1, torch.int32),
+        )
+
+
+def hyres_denoise(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64):
+    """One-shot HyRes on ``Y[p, H, W]``; returns ``(X, info dict)``
+    (synchronises the current stream to read the info record)."""
+    p, H, W = Y.shape
+    h = HyRes(p, H, W, levels, r_max, n_lambda, device=Y.device)
+    X = h(Y)
+    return X, h.result_info()

@@ -1,0 +1,399 @@
+// extern "C" entry points of libhyde (declared in include/hyde.h): argument
+// checks, workspace carving and the launch sequence of the HyRes path
+// (arXiv 2204.06979, Sec. 2.1). No entry point allocates, frees or
+// synchronises; everything is enqueued on the caller's stream.
+#include <math.h>
+#include <string.h>
+
+#include "hyde_internal.cuh"
+
+namespace hyde {
+
+int device_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    static int cache[64] = {0};
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64) cache[dev] = v;
+    return v;
+}
+
+cudaError_t ensure_smem_limit(const void* func, int bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    // dynamic + static shared memory may not exceed the opt-in limit
+    const int room = optin - (int)fa.sharedSizeBytes;
+    if (bytes > room) return cudaErrorInvalidValue;
+    // the largest value is always safe to set; concurrent callers agree on it
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+}
+
+namespace {
+
+inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+inline int rank_pad(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
+
+bool padded(int H, int W, int levels, int* Hp, int* Wp) {
+    if (levels < 1 || levels > kMaxLevels || H < 1 || W < 1) return false;
+    const int q = 1 << levels;
+    const long long hp = ((long long)H + q - 1) / q * q, wp = ((long long)W + q - 1) / q * q;
+    if (hp > (1 << 30) || wp > (1 << 30)) return false;
+    if (hp - H > H - 1 || wp - W > W - 1) return false;
+    *Hp = (int)hp;
+    *Wp = (int)wp;
+    return true;
+}
+
+// Bump allocator over the caller's workspace (offsets only).
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes, kAlign);
+        return o;
+    }
+};
+
+struct HyresLayout {
+    int Hp, Wp, RM, K;
+    long long N, n;
+    GramPlan gram;
+    hyde_ws_layout pub;
+    size_t rank_dev, lam_dev, counts, sums, sum_all, P, Q, noise, partials, zp, scratch;
+    size_t zero_begin, zero_end;
+};
+
+hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, HyresLayout* L) {
+    if (!pr) return HYDE_ERR_INVALID_ARG;
+    if (pr->wavelet != 2 || pr->precision != HYDE_PREC_FP32) return HYDE_ERR_INVALID_ARG;
+    if (pr->reserved[0] || pr->reserved[1] || pr->reserved[2]) return HYDE_ERR_INVALID_ARG;
+    if (p < 2 || p > kMaxBandsGram) return HYDE_ERR_SHAPE;
+    if (pr->r_max < 1 || pr->r_max > kMaxRank || pr->r_max > p) return HYDE_ERR_SHAPE;
+    if (pr->n_lambda < 2 || pr->n_lambda > kMaxLambda) return HYDE_ERR_SHAPE;
+    int Hp, Wp;
+    if (!padded(H, W, pr->levels, &Hp, &Wp)) return HYDE_ERR_SHAPE;
+    const long long n = (long long)H * W;
+    if (n < p) return HYDE_ERR_SHAPE;
+    if (eig_smem_bytes(p, pr->r_max) > 227 * 1024) return HYDE_ERR_SHAPE;
+    if (((size_t)p * p + 2 * p) * sizeof(float) > 227 * 1024) return HYDE_ERR_SHAPE;
+    HyresLayout l;
+    l.Hp = Hp; l.Wp = Wp; l.RM = rank_pad(pr->r_max); l.K = pr->n_lambda;
+    l.N = (long long)Hp * Wp; l.n = n;
+    hyde_status st = gram_plan(p, n, &l.gram);
+    if (st != HYDE_OK) return st;
+    const int r = pr->r_max, K = pr->n_lambda;
+    Carver c;
+    memset(&l.pub, 0, sizeof(l.pub));
+    // zero-initialised block first: status, rank, lambda, SURE accumulators
+    l.zero_begin = c.off;
+    l.pub.status = c.take(sizeof(int));
+    l.rank_dev = c.take(sizeof(int));
+    l.lam_dev = c.take(sizeof(double));
+    l.counts = c.take((size_t)r * K * sizeof(unsigned int));
+    l.sums = c.take((size_t)r * K * sizeof(double));
+    l.sum_all = c.take((size_t)r * sizeof(double));
+    l.zero_end = c.off;
+    l.pub.R = c.take((size_t)p * p * sizeof(double));
+    l.pub.sigma = c.take((size_t)p * sizeof(double));
+    l.pub.evals = c.take((size_t)r * sizeof(double));
+    l.pub.V = c.take((size_t)p * r * sizeof(double));
+    l.pub.sure = c.take((size_t)r * K * sizeof(double));
+    l.pub.sure_inf = c.take((size_t)r * sizeof(double));
+    l.pub.sure_total = c.take((size_t)r * K * sizeof(double));
+    l.P = c.take((size_t)p * l.RM * sizeof(float));
+    l.Q = c.take((size_t)p * l.RM * sizeof(float));
+    l.noise = c.take(noise_ws_bytes(p));
+    l.partials = c.take(l.gram.partial_bytes);
+    l.zp = c.take((size_t)r * l.N * sizeof(float));
+    l.pub.coef = c.take((size_t)r * l.N * sizeof(float));
+    l.scratch = c.take((size_t)r * dwt_scratch_floats(Hp, Wp) * sizeof(float));
+    l.pub.total = c.off;
+    *L = l;
+    return HYDE_OK;
+}
+
+template <typename T>
+inline T* at(void* ws, size_t off) {
+    return reinterpret_cast<T*>(reinterpret_cast<char*>(ws) + off);
+}
+
+}  // namespace
+}  // namespace hyde
+
+using namespace hyde;
+
+extern "C" {
+
+const char* hyde_status_string(hyde_status s) {
+    switch (s) {
+        case HYDE_OK: return "ok";
+        case HYDE_ERR_INVALID_ARG: return "invalid argument";
+        case HYDE_ERR_SHAPE: return "unsupported shape";
+        case HYDE_ERR_NUMERIC: return "numerical failure (NaN/Inf input or non-SPD Gram matrix)";
+        case HYDE_ERR_NOT_CONVERGED: return "eigensolver did not converge";
+        case HYDE_ERR_TIMEOUT: return "bounded device wait gave up";
+        case HYDE_ERR_CUDA: return "CUDA runtime error";
+        case HYDE_ERR_WORKSPACE: return "workspace missing or too small";
+    }
+    return "unknown status";
+}
+
+int hyde_version(void) { return 100; }
+
+// ------------------------------------------------------------------ Gram
+hyde_status hyde_gram_workspace_size(int p, long long n, int precision, size_t* bytes) {
+    if (!bytes) return HYDE_ERR_INVALID_ARG;
+    if (precision != HYDE_PREC_FP32) return HYDE_ERR_INVALID_ARG;
+    GramPlan g;
+    hyde_status st = gram_plan(p, n, &g);
+    if (st != HYDE_OK) return st;
+    *bytes = align_up(g.partial_bytes, kAlign);
+    return HYDE_OK;
+}
+
+hyde_status hyde_gram(const float* Y, int p, long long n, int precision, double* R, void* ws,
+                      size_t ws_bytes, cudaStream_t stream) {
+    if (!Y || !R) return HYDE_ERR_INVALID_ARG;
+    if (precision != HYDE_PREC_FP32) return HYDE_ERR_INVALID_ARG;
+    GramPlan g;
+    hyde_status st = gram_plan(p, n, &g);
+    if (st != HYDE_OK) return st;
+    if (!ws || !aligned(ws, kAlign) || ws_bytes < g.partial_bytes) return HYDE_ERR_WORKSPACE;
+    return launch_gram(Y, p, n, g, reinterpret_cast<float*>(ws), R, nullptr, stream);
+}
+
+// ------------------------------------------------------------ noise level
+hyde_status hyde_noise_est_workspace_size(int p, int H, int W, size_t* bytes) {
+    if (!bytes) return HYDE_ERR_INVALID_ARG;
+    if (p < 2 || H < 1 || W < 1) return HYDE_ERR_SHAPE;
+    long long n = (long long)H * W;
+    if (n < p) return HYDE_ERR_SHAPE;
+    GramPlan g;
+    hyde_status st = gram_plan(p, n, &g);
+    if (st != HYDE_OK) return st;
+    *bytes = align_up(g.partial_bytes, kAlign) + align_up((size_t)p * p * sizeof(double), kAlign) +
+             noise_ws_bytes(p);
+    return HYDE_OK;
+}
+
+hyde_status hyde_noise_est(const float* Y, int p, int H, int W, double* sigma, int* status,
+                           void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!Y || !sigma) return HYDE_ERR_INVALID_ARG;
+    size_t need = 0;
+    hyde_status st = hyde_noise_est_workspace_size(p, H, W, &need);
+    if (st != HYDE_OK) return st;
+    if (((size_t)p * p + 2 * p) * sizeof(float) > 227 * 1024) return HYDE_ERR_SHAPE;
+    if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return HYDE_ERR_WORKSPACE;
+    long long n = (long long)H * W;
+    GramPlan g;
+    gram_plan(p, n, &g);
+    char* w = reinterpret_cast<char*>(ws);
+    float* partials = reinterpret_cast<float*>(w);
+    double* R = reinterpret_cast<double*>(w + align_up(g.partial_bytes, kAlign));
+    void* nws = w + align_up(g.partial_bytes, kAlign) + align_up((size_t)p * p * sizeof(double), kAlign);
+    st = launch_gram(Y, p, n, g, partials, R, status, stream);
+    if (st != HYDE_OK) return st;
+    return launch_noise_from_gram(R, p, n, sigma, nws, status, stream);
+}
+
+// ----------------------------------------------------------- eigenvectors
+hyde_status hyde_eig_sym_top(const double* A, int p, int r, double* evals, double* V,
+                             int* status, cudaStream_t stream) {
+    if (!A || !evals || !V) return HYDE_ERR_INVALID_ARG;
+    if (p < 1 || r < 1 || r > p || r > kMaxRank) return HYDE_ERR_SHAPE;
+    return launch_eig_top(A, nullptr, p, r, evals, V, status, stream);
+}
+
+// -------------------------------------------------------------------- DWT
+hyde_status hyde_dwt_workspace_size(int batch, int H, int W, int levels, size_t* bytes) {
+    if (!bytes) return HYDE_ERR_INVALID_ARG;
+    int Hp, Wp;
+    if (batch < 1 || batch > 65535 || !padded(H, W, levels, &Hp, &Wp)) return HYDE_ERR_SHAPE;
+    *bytes = align_up((size_t)batch * dwt_scratch_floats(Hp, Wp) * sizeof(float), kAlign);
+    return HYDE_OK;
+}
+
+static hyde_status dwt_common(const void* a, const void* b, int batch, int H, int W, int wavelet,
+                              int levels, void* ws, size_t ws_bytes, int* Hp, int* Wp) {
+    if (!a || !b || wavelet != 2) return HYDE_ERR_INVALID_ARG;
+    size_t need = 0;
+    hyde_status st = hyde_dwt_workspace_size(batch, H, W, levels, &need);
+    if (st != HYDE_OK) return st;
+    padded(H, W, levels, Hp, Wp);
+    if (levels > 1 && (!ws || !aligned(ws, kAlign) || ws_bytes < need)) return HYDE_ERR_WORKSPACE;
+    return HYDE_OK;
+}
+
+hyde_status hyde_dwt2(const float* in, float* coef, int batch, int H, int W, int wavelet,
+                      int levels, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    int Hp, Wp;
+    hyde_status st = dwt_common(in, coef, batch, H, W, wavelet, levels, ws, ws_bytes, &Hp, &Wp);
+    if (st != HYDE_OK) return st;
+    DwtSrc src{in, (long long)H * W, W, H, W};
+    return launch_dwt2(src, coef, batch, Hp, Wp, levels, reinterpret_cast<float*>(ws), stream);
+}
+
+hyde_status hyde_idwt2(const float* coef, float* out, int batch, int H, int W, int wavelet,
+                       int levels, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    int Hp, Wp;
+    hyde_status st = dwt_common(coef, out, batch, H, W, wavelet, levels, ws, ws_bytes, &Hp, &Wp);
+    if (st != HYDE_OK) return st;
+    return launch_idwt2(coef, out, batch, Hp, Wp, H, W, levels, reinterpret_cast<float*>(ws),
+                        nullptr, nullptr, stream);
+}
+
+// ------------------------------------------------------------------- SURE
+hyde_status hyde_sure_workspace_size(int batch, int K, size_t* bytes) {
+    if (!bytes) return HYDE_ERR_INVALID_ARG;
+    if (batch < 1 || batch > 65535 || K < 2 || K > kMaxLambda) return HYDE_ERR_SHAPE;
+    *bytes = sure_accum_bytes(batch, K);
+    return HYDE_OK;
+}
+
+hyde_status hyde_sure_table(const float* coef, int batch, int Hp, int Wp, int levels, int K,
+                            double* S, double* S_inf, void* ws, size_t ws_bytes,
+                            cudaStream_t stream) {
+    if (!coef || !S || !S_inf) return HYDE_ERR_INVALID_ARG;
+    size_t need = 0;
+    hyde_status st = hyde_sure_workspace_size(batch, K, &need);
+    if (st != HYDE_OK) return st;
+    if (levels < 1 || levels > kMaxLevels || Hp < 2 || Wp < 2 || (Hp % (1 << levels)) ||
+        (Wp % (1 << levels)))
+        return HYDE_ERR_SHAPE;
+    if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return HYDE_ERR_WORKSPACE;
+    char* w = reinterpret_cast<char*>(ws);
+    SureBufs b;
+    b.counts = reinterpret_cast<unsigned int*>(w);
+    b.sums = reinterpret_cast<double*>(w + align_up((size_t)batch * K * sizeof(unsigned int), kAlign));
+    b.sum_all = reinterpret_cast<double*>(reinterpret_cast<char*>(b.sums) +
+                                          align_up((size_t)batch * K * sizeof(double), kAlign));
+    if (cudaMemsetAsync(ws, 0, need, stream) != cudaSuccess) return HYDE_ERR_CUDA;
+    const long long N = (long long)Hp * Wp;
+    const long long N_det = N - (long long)(Hp >> levels) * (Wp >> levels);
+    const double delta = sqrt(2.0 * log((double)N)) / (K - 1);
+    st = launch_sure_hist(coef, batch, Hp, Wp, levels, K, delta, b, stream);
+    if (st != HYDE_OK) return st;
+    return launch_sure_select(b, batch, K, N, N_det, delta, S, S_inf, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, stream);
+}
+
+// ---------------------------------------------------------- whole HyRes
+hyde_status hyde_workspace_size(int p, int H, int W, const hyde_hyres_params* params,
+                                size_t* bytes) {
+    if (!bytes) return HYDE_ERR_INVALID_ARG;
+    HyresLayout L;
+    hyde_status st = hyres_layout(p, H, W, params, &L);
+    if (st != HYDE_OK) return st;
+    *bytes = L.pub.total;
+    return HYDE_OK;
+}
+
+hyde_status hyde_workspace_layout(int p, int H, int W, const hyde_hyres_params* params,
+                                  hyde_ws_layout* layout) {
+    if (!layout) return HYDE_ERR_INVALID_ARG;
+    HyresLayout L;
+    hyde_status st = hyres_layout(p, H, W, params, &L);
+    if (st != HYDE_OK) return st;
+    *layout = L.pub;
+    return HYDE_OK;
+}
+
+static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
+                                 const hyde_hyres_params* params, hyde_hyres_info* info,
+                                 void* ws, size_t ws_bytes, cudaStream_t stream,
+                                 cudaEvent_t* ev) {
+    if (!Y || !X || Y == X) return HYDE_ERR_INVALID_ARG;
+    HyresLayout L;
+    hyde_status st = hyres_layout(p, H, W, params, &L);
+    if (st != HYDE_OK) return st;
+    if (!ws || !aligned(ws, kAlign) || ws_bytes < L.pub.total) return HYDE_ERR_WORKSPACE;
+    const int r = params->r_max, K = params->n_lambda, lev = params->levels;
+    int* status = at<int>(ws, L.pub.status);
+    int* rank_dev = at<int>(ws, L.rank_dev);
+    double* lam_dev = at<double>(ws, L.lam_dev);
+    double* R = at<double>(ws, L.pub.R);
+    double* sigma = at<double>(ws, L.pub.sigma);
+    double* evals = at<double>(ws, L.pub.evals);
+    double* V = at<double>(ws, L.pub.V);
+    float* P = at<float>(ws, L.P);
+    float* Q = at<float>(ws, L.Q);
+    float* zp = at<float>(ws, L.zp);
+    float* coef = at<float>(ws, L.pub.coef);
+    float* scratch = at<float>(ws, L.scratch);
+    SureBufs sb{at<unsigned int>(ws, L.counts), at<double>(ws, L.sums), at<double>(ws, L.sum_all)};
+    int mark = 0;
+    auto stage = [&]() -> hyde_status {
+        if (!ev) return HYDE_OK;
+        return cuda_status(cudaEventRecord(ev[mark++], stream));
+    };
+#define HYDE_TRY(x) do { hyde_status s_ = (x); if (s_ != HYDE_OK) return s_; } while (0)
+    HYDE_TRY(stage());
+    if (cudaMemsetAsync(at<char>(ws, L.zero_begin), 0, L.zero_end - L.zero_begin, stream) !=
+        cudaSuccess)
+        return HYDE_ERR_CUDA;
+    // 1. Gram matrix
+    HYDE_TRY(launch_gram(Y, p, L.n, L.gram, at<float>(ws, L.partials), R, status, stream));
+    HYDE_TRY(stage());
+    // 2. noise level by regression
+    HYDE_TRY(launch_noise_from_gram(R, p, L.n, sigma, at<void>(ws, L.noise), status, stream));
+    HYDE_TRY(stage());
+    // 3-4. whitened Gram matrix, leading eigenpairs, float weights
+    HYDE_TRY(launch_eig_top(R, sigma, p, r, evals, V, status, stream));
+    HYDE_TRY(launch_weights(V, sigma, p, r, L.RM, P, Q, stream));
+    HYDE_TRY(stage());
+    // 5. projection into padded component images
+    HYDE_TRY(launch_project_pad(Y, p, H, W, P, r, L.RM, zp, L.Hp, L.Wp, stream));
+    HYDE_TRY(stage());
+    // 6. wavelet analysis
+    DwtSrc src{zp, L.N, L.Wp, L.Hp, L.Wp};
+    HYDE_TRY(launch_dwt2(src, coef, r, L.Hp, L.Wp, lev, scratch, stream));
+    HYDE_TRY(stage());
+    // 7-8. SURE table and (rank, lambda) selection
+    const long long N_det = L.N - (long long)(L.Hp >> lev) * (L.Wp >> lev);
+    const double delta = sqrt(2.0 * log((double)L.N)) / (K - 1);
+    HYDE_TRY(launch_sure_hist(coef, r, L.Hp, L.Wp, lev, K, delta, sb, stream));
+    HYDE_TRY(launch_sure_select(sb, r, K, L.N, N_det, delta, at<double>(ws, L.pub.sure),
+                                at<double>(ws, L.pub.sure_inf), at<double>(ws, L.pub.sure_total),
+                                info, rank_dev, lam_dev, status, stream));
+    HYDE_TRY(stage());
+    // 9. soft threshold + inverse DWT of the kept components (into zp, H x W)
+    HYDE_TRY(launch_idwt2(coef, zp, r, L.Hp, L.Wp, H, W, lev, scratch, lam_dev, rank_dev, stream));
+    HYDE_TRY(stage());
+    // 10. back-projection and un-whitening
+    HYDE_TRY(launch_backproject(zp, L.n, Q, p, r, L.RM, rank_dev, X, stream));
+    HYDE_TRY(stage());
+#undef HYDE_TRY
+    return HYDE_OK;
+}
+
+hyde_status hyde_hyres_denoise(const float* Y, float* X, int p, int H, int W,
+                               const hyde_hyres_params* params, hyde_hyres_info* info, void* ws,
+                               size_t ws_bytes, cudaStream_t stream) {
+    return hyres_enqueue(Y, X, p, H, W, params, info, ws, ws_bytes, stream, nullptr);
+}
+
+hyde_status hyde_hyres_denoise_timed(const float* Y, float* X, int p, int H, int W,
+                                     const hyde_hyres_params* params, hyde_hyres_info* info,
+                                     void* ws, size_t ws_bytes, cudaStream_t stream,
+                                     cudaEvent_t* events) {
+    if (!events) return HYDE_ERR_INVALID_ARG;
+    return hyres_enqueue(Y, X, p, H, W, params, info, ws, ws_bytes, stream, events);
+}
+
+int hyde_hyres_kernel_launches(const hyde_hyres_params* params) {
+    if (!params || params->levels < 1 || params->levels > kMaxLevels) return -1;
+    // gram 2, noise 2, eig 1, weights 1, projection 1, DWT L, SURE 2, IDWT L, back 1
+    return 10 + 2 * params->levels;
+}
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+// Separable periodic db2 wavelet transform of a batch of images (the spatial
+// sparsifying basis of HyRes, "wavelet-based", arXiv 2204.06979 Sec. 2.1),
+// and its transpose with the soft threshold fused into the coefficient load.
+//
+// One level of analysis on an h x w image:
+//   rows:    a_k = sum_m h_m x[(2k+m) mod w],  d_k = sum_m g_m x[(2k+m) mod w]
+//   columns: the same filters along y on both row outputs,
+// giving LL (top-left), the row-detail band (top-right), the column-detail
+// band (bottom-left) and the diagonal band. LL is recursed on.
+//
+// Each block computes a 16 x 32 tile of every subband from a 34 x 66 input
+// tile staged in shared memory (the +2 halo wraps periodically). Details go
+// straight to their Mallat position in the coefficient image; LL goes to a
+// compact ping-pong buffer (or, at the last level, into the coefficient
+// image), so no level reads what another block of the same launch writes.
+#include "hyde_internal.cuh"
+
+namespace hyde {
+namespace {
+
+constexpr int TH = 16, TW = 32;            // coefficient tile per subband
+constexpr int IH = 2 * TH + 2, IW = 2 * TW + 2;
+constexpr int kThreads = 256;
+
+template <bool REFLECT>
+__global__ void __launch_bounds__(kThreads)
+dwt_level_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int hv,
+                 int wv, int h, int w, float* __restrict__ coef, long long coef_bs,
+                 int coef_ld, float* __restrict__ ll, long long ll_bs, int ll_ld) {
+    __shared__ float in[IH][IW + 1];
+    __shared__ float ra[IH][TW + 1];
+    __shared__ float rd[IH][TW + 1];
+    const int b = blockIdx.z;
+    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+    const int hh = h >> 1, wh = w >> 1;
+    const float* s = src + (long long)b * src_bs;
+    for (int e = threadIdx.x; e < IH * IW; e += kThreads) {
+        const int r = e / IW, c = e - (e / IW) * IW;
+        int y = (2 * ty0 + r) % h;
+        int x = (2 * tx0 + c) % w;
+        if (REFLECT) {
+            if (y >= hv) y = 2 * hv - 2 - y;
+            if (x >= wv) x = 2 * wv - 2 - x;
+        }
+        in[r][c] = __ldg(s + (long long)y * src_ld + x);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < IH * TW; e += kThreads) {
+        const int r = e / TW, k = e % TW;
+        const float x0 = in[r][2 * k], x1 = in[r][2 * k + 1];
+        const float x2 = in[r][2 * k + 2], x3 = in[r][2 * k + 3];
+        ra[r][k] = kH0 * x0 + kH1 * x1 + kH2 * x2 + kH3 * x3;
+        rd[r][k] = kG0 * x0 + kG1 * x1 + kG2 * x2 + kG3 * x3;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TH * TW; e += kThreads) {
+        const int j = e / TW, k = e % TW;
+        const int J = ty0 + j, K = tx0 + k;
+        if (J >= hh || K >= wh) continue;
+        const float a0 = ra[2 * j][k], a1 = ra[2 * j + 1][k];
+        const float a2 = ra[2 * j + 2][k], a3 = ra[2 * j + 3][k];
+        const float d0 = rd[2 * j][k], d1 = rd[2 * j + 1][k];
+        const float d2 = rd[2 * j + 2][k], d3 = rd[2 * j + 3][k];
+        const float LL = kH0 * a0 + kH1 * a1 + kH2 * a2 + kH3 * a3;
+        const float LH = kG0 * a0 + kG1 * a1 + kG2 * a2 + kG3 * a3;   // column detail
+        const float HL = kH0 * d0 + kH1 * d1 + kH2 * d2 + kH3 * d3;   // row detail
+        const float HH = kG0 * d0 + kG1 * d1 + kG2 * d2 + kG3 * d3;
+        float* cb = coef + (long long)b * coef_bs;
+        ll[(long long)b * ll_bs + (long long)J * ll_ld + K] = LL;
+        cb[(long long)J * coef_ld + wh + K] = HL;
+        cb[(long long)(hh + J) * coef_ld + K] = LH;
+        cb[(long long)(hh + J) * coef_ld + wh + K] = HH;
+    }
+}
+
+__device__ __forceinline__ float soft(float c, float lam) {
+    return copysignf(fmaxf(fabsf(c) - lam, 0.f), c);
+}
+
+// Synthesis of one level: coefficients of an (h/2 x w/2) x 4 layout -> an
+// h x w image, written only where y < ho and x < wo (crop at the last level).
+// Output rows 2j and 2j+1 draw on coefficient rows j and j-1 (mod h/2):
+//   x[2j]   = h0 a_j + g0 d_j + h2 a_{j-1} + g2 d_{j-1}
+//   x[2j+1] = h1 a_j + g1 d_j + h3 a_{j-1} + g3 d_{j-1}
+__global__ void __launch_bounds__(kThreads)
+idwt_level_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
+                  const float* __restrict__ coef, long long coef_bs, int coef_ld, int h,
+                  int w, const double* __restrict__ lam, const int* __restrict__ rank,
+                  float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo) {
+    __shared__ float sLL[TH + 1][TW + 2], sLH[TH + 1][TW + 2];
+    __shared__ float sHL[TH + 1][TW + 2], sHH[TH + 1][TW + 2];
+    __shared__ float tl[2 * TH][TW + 2], th[2 * TH][TW + 2];
+    const int b = blockIdx.z;
+    if (rank && b >= *rank) return;
+    const float lv = lam ? (float)(*lam) : 0.f;
+    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+    const int hh = h >> 1, wh = w >> 1;
+    const float* L = llsrc + (long long)b * ll_bs;
+    const float* C = coef + (long long)b * coef_bs;
+    for (int e = threadIdx.x; e < (TH + 1) * (TW + 1); e += kThreads) {
+        const int j = e / (TW + 1), k = e % (TW + 1);
+        const int J = (ty0 + j - 1 + hh) % hh;
+        const int K = (tx0 + k - 1 + wh) % wh;
+        sLL[j][k] = L[(long long)J * ll_ld + K];
+        const float hl = C[(long long)J * coef_ld + wh + K];
+        const float lh = C[(long long)(hh + J) * coef_ld + K];
+        const float hhv = C[(long long)(hh + J) * coef_ld + wh + K];
+        sHL[j][k] = soft(hl, lv);
+        sLH[j][k] = soft(lh, lv);
+        sHH[j][k] = soft(hhv, lv);
+    }
+    __syncthreads();
+    // columns: local output row y (0..2TH-1) from coefficient rows y/2 (+1 in smem)
+    for (int e = threadIdx.x; e < 2 * TH * (TW + 1); e += kThreads) {
+        const int y = e / (TW + 1), k = e % (TW + 1);
+        const int j = (y >> 1) + 1;
+        float l, hgh;
+        if ((y & 1) == 0) {
+            l = kH0 * sLL[j][k] + kG0 * sLH[j][k] + kH2 * sLL[j - 1][k] + kG2 * sLH[j - 1][k];
+            hgh = kH0 * sHL[j][k] + kG0 * sHH[j][k] + kH2 * sHL[j - 1][k] + kG2 * sHH[j - 1][k];
+        } else {
+            l = kH1 * sLL[j][k] + kG1 * sLH[j][k] + kH3 * sLL[j - 1][k] + kG3 * sLH[j - 1][k];
+            hgh = kH1 * sHL[j][k] + kG1 * sHH[j][k] + kH3 * sHL[j - 1][k] + kG3 * sHH[j - 1][k];
+        }
+        tl[y][k] = l;
+        th[y][k] = hgh;
+    }
+    __syncthreads();
+    float* O = out + (long long)b * out_bs;
+    for (int e = threadIdx.x; e < 2 * TH * 2 * TW; e += kThreads) {
+        const int y = e / (2 * TW), x = e % (2 * TW);
+        const int Y = 2 * ty0 + y, X = 2 * tx0 + x;
+        if (Y >= ho || X >= wo) continue;
+        const int k = (x >> 1) + 1;
+        float v;
+        if ((x & 1) == 0)
+            v = kH0 * tl[y][k] + kG0 * th[y][k] + kH2 * tl[y][k - 1] + kG2 * th[y][k - 1];
+        else
+            v = kH1 * tl[y][k] + kG1 * th[y][k] + kH3 * tl[y][k - 1] + kG3 * th[y][k - 1];
+        O[(long long)Y * out_ld + X] = v;
+    }
+}
+
+}  // namespace
+
+size_t dwt_scratch_floats(int Hp, int Wp) {
+    size_t N = (size_t)Hp * Wp;
+    return N / 4 + N / 16;
+}
+
+// LL of level j (1-based, size (Hp>>j) x (Wp>>j)) lives in half A (odd j)
+// or half B (even j) of the per-image scratch.
+static inline float* ll_buf(float* scratch, int batch, int Hp, int Wp, int j,
+                            long long* bs) {
+    size_t N = (size_t)Hp * Wp;
+    if (j & 1) { *bs = (long long)(N / 4); return scratch; }
+    *bs = (long long)(N / 16);
+    return scratch + (size_t)batch * (N / 4);
+}
+
+hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int Wp,
+                        int levels, float* scratch, cudaStream_t s) {
+    const long long cbs = (long long)Hp * Wp;
+    for (int lev = 1; lev <= levels; ++lev) {
+        const int h = Hp >> (lev - 1), w = Wp >> (lev - 1);
+        const float* sp;
+        long long sbs;
+        int sld, hv, wv;
+        if (lev == 1) {
+            sp = src.ptr; sbs = src.bstride; sld = src.ld; hv = src.hv; wv = src.wv;
+        } else {
+            sp = ll_buf(scratch, batch, Hp, Wp, lev - 1, &sbs);
+            sld = w; hv = h; wv = w;
+        }
+        float* lp;
+        long long lbs;
+        int lld;
+        if (lev == levels) { lp = coef; lbs = cbs; lld = Wp; }
+        else { lp = ll_buf(scratch, batch, Hp, Wp, lev, &lbs); lld = w / 2; }
+        dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
+        if (hv < h || wv < w)
+            dwt_level_kernel<true><<<grid, kThreads, 0, s>>>(sp, sbs, sld, hv, wv, h, w, coef,
+                                                             cbs, Wp, lp, lbs, lld);
+        else
+            dwt_level_kernel<false><<<grid, kThreads, 0, s>>>(sp, sbs, sld, hv, wv, h, w, coef,
+                                                              cbs, Wp, lp, lbs, lld);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int Wp, int H,
+                         int W, int levels, float* scratch, const double* lam,
+                         const int* rank, cudaStream_t s) {
+    const long long cbs = (long long)Hp * Wp;
+    for (int lev = levels; lev >= 1; --lev) {
+        const int h = Hp >> (lev - 1), w = Wp >> (lev - 1);
+        const float* lp;
+        long long lbs;
+        int lld;
+        if (lev == levels) { lp = coef; lbs = cbs; lld = Wp; }
+        else {
+            lp = ll_buf(scratch, batch, Hp, Wp, lev, &lbs);
+            lld = w / 2;
+        }
+        float* op;
+        long long obs;
+        int old, ho, wo;
+        if (lev == 1) { op = out; obs = (long long)H * W; old = W; ho = H; wo = W; }
+        else {
+            op = ll_buf(scratch, batch, Hp, Wp, lev - 1, &obs);
+            old = w; ho = h; wo = w;
+        }
+        dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
+        idwt_level_kernel<<<grid, kThreads, 0, s>>>(lp, lbs, lld, coef, cbs, Wp, h, w, lam,
+                                                    rank, op, obs, old, ho, wo);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace hyde

@@ -1,0 +1,199 @@
+// Gram matrix R = Y^T Y of the n x p pixel-by-band matrix (the spectral
+// statistics of HyRes's low-rank model, arXiv 2204.06979 Sec. 2.1).
+//
+// Plain FP32 SIMT design. The symmetric p x p result is cut into 8 x 8 tiles;
+// one thread owns one tile of the upper triangle (PT(PT+1)/2 tiles for
+// PT = ceil(p/8)), so each thread does 64 FMAs per pixel from 16 float4
+// shared-memory loads. A block walks a contiguous range of 32-pixel chunks
+// through a 3-stage cp.async pipeline (a warp copies one band's 32
+// consecutive pixels) into a swizzled shared buffer, so that the 8 rows a
+// thread reads are spread over all 32 banks. Each block writes its float
+// partial; a second kernel sums the partials in double and mirrors the
+// triangle.
+#include "hyde_internal.cuh"
+
+namespace hyde {
+namespace {
+
+constexpr int KC = 32;        // pixels per chunk
+constexpr int STAGES = 3;     // cp.async pipeline depth
+constexpr int kGramMaxThreads = 544;
+
+__device__ __forceinline__ void tile_of(int t, int PT, int& ti, int& tj) {
+    // row-major enumeration of the upper triangle: row ti holds PT - ti tiles
+    int row = 0, rem = t, len = PT;
+    while (rem >= len) { rem -= len; ++row; --len; }
+    ti = row;
+    tj = row + rem;
+}
+
+// Shared layout: band b occupies one 128-byte row of 8 float4 (32 pixels);
+// logical float4 column q is stored at q ^ ((b >> 3) & 7).
+__device__ __forceinline__ int swz(int b, int q) { return b * 8 + (q ^ ((b >> 3) & 7)); }
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 4 : 0;   // zero-fill outside the cube
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Rows of Y are only 4-byte aligned when n is odd, so the copies are 4-byte
+// cp.async (a warp still covers one band's 32 consecutive pixels: 128 B).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT <= 256 ? 2 : 1))
+gram_partial_kernel(const float* __restrict__ Y, int p, long long n, int PT,
+                    int ntiles, long long chunks_per_block,
+                    float* __restrict__ partials) {
+    extern __shared__ float4 sm4[];
+    const int p8 = PT * 8;
+    const int t = threadIdx.x;
+    const int T = blockDim.x;
+
+    // padded bands p..p8-1 stay zero in every stage
+    for (int i = t; i < (p8 - p) * 8 * STAGES; i += T) {
+        const int st = i / ((p8 - p) * 8), o = i % ((p8 - p) * 8);
+        sm4[st * p8 * 8 + p * 8 + o] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+
+    const long long nchunks = (n + KC - 1) / KC;
+    const long long c0 = (long long)blockIdx.x * chunks_per_block;
+    const long long c1 = min(c0 + chunks_per_block, nchunks);
+    const int nelem = p * KC;
+
+    auto issue = [&](long long c, int st) {
+        float* d = reinterpret_cast<float*>(sm4 + st * p8 * 8);
+        for (int e = t; e < nelem; e += T) {
+            const int b = e / KC, k = e % KC;
+            const long long pix = c * KC + k;
+            const bool ok = pix < n;
+            cp_async4(d + swz(b, k >> 2) * 4 + (k & 3), Y + (long long)b * n + (ok ? pix : 0), ok);
+        }
+    };
+
+    const bool active = t < ntiles;
+    int ti = 0, tj = 0;
+    if (active) tile_of(t, PT, ti, tj);
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (c0 + s < c1) issue(c0 + s, s);
+        cp_async_commit();
+    }
+    for (long long c = c0; c < c1; ++c) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();   // chunk c visible to all; stage (c-1)%STAGES is free
+        const long long nxt = c + STAGES - 1;
+        if (nxt < c1) issue(nxt, (int)(nxt - c0) % STAGES);
+        cp_async_commit();
+        if (active) {
+            const float4* B = sm4 + ((int)(c - c0) % STAGES) * p8 * 8;
+#pragma unroll 1
+            for (int q = 0; q < 8; ++q) {
+                float4 a[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] = B[swz(8 * ti + i, q)];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 bv = B[swz(8 * tj + j, q)];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        acc[i][j] = fmaf(a[i].x, bv.x, acc[i][j]);
+                        acc[i][j] = fmaf(a[i].y, bv.y, acc[i][j]);
+                        acc[i][j] = fmaf(a[i].z, bv.z, acc[i][j]);
+                        acc[i][j] = fmaf(a[i].w, bv.w, acc[i][j]);
+                    }
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+
+    if (active) {
+        float4* out = reinterpret_cast<float4*>(
+            partials + ((long long)blockIdx.x * ntiles + t) * 64);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            out[2 * i] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            out[2 * i + 1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+        }
+    }
+}
+
+__global__ void gram_reduce_kernel(const float* __restrict__ partials, int nblocks,
+                                   int p, int PT, int ntiles, double* __restrict__ R,
+                                   int* status) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)ntiles * 64) return;
+    const int t = (int)(idx / 64), e = (int)(idx % 64);
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += (double)partials[(long long)b * ntiles * 64 + idx];
+    int ti, tj;
+    tile_of(t, PT, ti, tj);
+    const int i = 8 * ti + e / 8, j = 8 * tj + e % 8;
+    if (i < p && j < p) {
+        if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
+        R[(long long)i * p + j] = s;
+        R[(long long)j * p + i] = s;
+    }
+}
+
+}  // namespace
+
+template <int MAXT>
+static hyde_status plan_for(GramPlan& g, long long n) {
+    cudaError_t e = ensure_smem_limit((const void*)gram_partial_kernel<MAXT>, (int)g.smem);
+    if (e != cudaSuccess) return HYDE_ERR_CUDA;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_partial_kernel<MAXT>,
+                                                      g.threads, g.smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    long long nchunks = (n + KC - 1) / KC;
+    long long blocks = (long long)sms * per_sm;
+    if (blocks > nchunks) blocks = nchunks;
+    g.blocks = (int)blocks;
+    return HYDE_OK;
+}
+
+hyde_status gram_plan(int p, long long n, GramPlan* plan) {
+    if (p < 1 || p > kMaxBandsGram || n < 1) return HYDE_ERR_SHAPE;
+    GramPlan g;
+    g.PT = (p + 7) / 8;
+    g.ntiles = g.PT * (g.PT + 1) / 2;
+    g.threads = (g.ntiles + 31) / 32 * 32;
+    if (g.threads > kGramMaxThreads) return HYDE_ERR_SHAPE;
+    g.smem = (size_t)STAGES * g.PT * 8 * KC * sizeof(float);
+    hyde_status st = g.threads <= 256 ? plan_for<256>(g, n) : plan_for<kGramMaxThreads>(g, n);
+    if (st != HYDE_OK) return st;
+    g.partial_bytes = (size_t)g.blocks * g.ntiles * 64 * sizeof(float);
+    *plan = g;
+    return HYDE_OK;
+}
+
+hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
+                        float* partials, double* R, int* status, cudaStream_t s) {
+    long long nchunks = (n + KC - 1) / KC;
+    long long per = (nchunks + g.blocks - 1) / g.blocks;
+    if (g.threads <= 256)
+        gram_partial_kernel<256><<<g.blocks, g.threads, g.smem, s>>>(Y, p, n, g.PT, g.ntiles,
+                                                                     per, partials);
+    else
+        gram_partial_kernel<kGramMaxThreads><<<g.blocks, g.threads, g.smem, s>>>(
+            Y, p, n, g.PT, g.ntiles, per, partials);
+    long long tot = (long long)g.ntiles * 64;
+    gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        partials, g.blocks, p, g.PT, g.ntiles, R, status);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace hyde

@@ -1,0 +1,140 @@
+// Internal declarations shared by the libhyde translation units.
+// Every kernel of the HyRes path (arXiv 2204.06979, Sec. 2.1) is launched
+// through one of the host launchers declared here; the extern "C" layer in
+// abi.cu validates arguments, carves the caller's workspace and calls them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hyde.h"
+
+namespace hyde {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxBandsGram = 256;   // p bound of the Gram kernel (8x8 tiles)
+constexpr int kMaxRank = 32;         // r_max bound (one warp per eigenpair)
+constexpr int kMaxLambda = 256;      // K bound of the SURE table
+constexpr int kMaxLevels = 10;
+constexpr size_t kAlign = 256;       // workspace carve alignment
+
+// ------------------------------------------------------- db2 filter taps
+// Daubechies' orthonormal scaling filter with two vanishing moments, from its
+// closed form h = (1+r3, 3+r3, 3-r3, 1-r3) / (4 r2); wavelet filter
+// g_m = (-1)^m h_{3-m}.
+constexpr double kR3 = 1.7320508075688772935274463;
+constexpr double kR2 = 1.4142135623730950488016887;
+constexpr float kH0 = (float)((1.0 + kR3) / (4.0 * kR2));
+constexpr float kH1 = (float)((3.0 + kR3) / (4.0 * kR2));
+constexpr float kH2 = (float)((3.0 - kR3) / (4.0 * kR2));
+constexpr float kH3 = (float)((1.0 - kR3) / (4.0 * kR2));
+constexpr float kG0 = kH3;
+constexpr float kG1 = -kH2;
+constexpr float kG2 = kH1;
+constexpr float kG3 = -kH0;
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ inline size_t align_up(size_t x, size_t a) {
+    return (x + a - 1) / a * a;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// Number of SMs of the current device (cached per device).
+int device_sm_count();
+
+// Sets the dynamic shared-memory limit of a kernel once per device.
+cudaError_t ensure_smem_limit(const void* func, int bytes);
+
+inline hyde_status cuda_status(cudaError_t e) {
+    return e == cudaSuccess ? HYDE_OK : HYDE_ERR_CUDA;
+}
+
+// ----------------------------------------------------------------- Gram
+struct GramPlan {
+    int PT;          // 8-band tile rows
+    int ntiles;      // upper-triangle 8x8 tiles
+    int threads;     // threads per block
+    int blocks;      // blocks in the grid
+    size_t smem;     // dynamic shared memory per block
+    size_t partial_bytes;
+};
+hyde_status gram_plan(int p, long long n, GramPlan* plan);
+hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& plan,
+                        float* partials, double* R, int* status,
+                        cudaStream_t s);
+
+// ------------------------------------------------------- small dense LA
+size_t noise_ws_bytes(int p);
+hyde_status launch_noise_from_gram(const double* R, int p, long long n,
+                                   double* sigma, void* ws, int* status,
+                                   cudaStream_t s);
+size_t eig_smem_bytes(int p, int r);
+hyde_status launch_eig_top(const double* A, const double* wsig, int p,
+                           int r, double* evals, double* V, int* status,
+                           cudaStream_t s);
+// P[b][i] = V[b][i] / sigma_b and Q[b][i] = V[b][i] * sigma_b (float,
+// row stride ldw, zero for i >= r)
+hyde_status launch_weights(const double* V, const double* sigma, int p, int r,
+                           int ldw, float* P, float* Q, cudaStream_t s);
+
+// ------------------------------------------------- projection / back
+hyde_status launch_project_pad(const float* Y, int p, int H, int W,
+                               const float* P, int r, int ldw, float* Zp,
+                               int Hp, int Wp, cudaStream_t s);
+hyde_status launch_backproject(const float* Zh, long long n, const float* Q,
+                               int p, int r_max, int ldw, const int* rank,
+                               float* X, cudaStream_t s);
+
+// ------------------------------------------------------------------ DWT
+// Source of the first analysis level: the image is read at (y, x) of the
+// padded domain through whole-sample symmetric reflection at hv, wv.
+struct DwtSrc {
+    const float* ptr;
+    long long bstride;
+    int ld;
+    int hv, wv;
+};
+size_t dwt_scratch_floats(int Hp, int Wp);   // per image, both ping-pong halves
+hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp,
+                        int Wp, int levels, float* scratch, cudaStream_t s);
+// Synthesis with optional soft threshold of detail coefficients at *lam and
+// an optional rank limit (*rank images are processed; NULL = all).
+hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp,
+                         int Wp, int H, int W, int levels, float* scratch,
+                         const double* lam, const int* rank, cudaStream_t s);
+
+// ----------------------------------------------------------------- SURE
+struct SureBufs {
+    unsigned int* counts;   // [batch][K]
+    double* sums;           // [batch][K]
+    double* sum_all;        // [batch]
+};
+size_t sure_accum_bytes(int batch, int K);
+hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp,
+                             int levels, int K, double delta,
+                             const SureBufs& b, cudaStream_t s);
+// Builds S, S_inf (and, when T != NULL, the (rank, lambda) table plus the
+// selection written to info/rank_out/lam_out).
+hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
+                               long long N_det, double delta, double* S,
+                               double* S_inf, double* T,
+                               hyde_hyres_info* info, int* rank_out,
+                               double* lam_out, const int* status,
+                               cudaStream_t s);
+
+}  // namespace hyde

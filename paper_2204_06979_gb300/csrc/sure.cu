@@ -1,0 +1,198 @@
+// Stein's unbiased risk estimate (SURE) of soft-thresholding whitened wavelet
+// coefficients, for every component and every threshold candidate, and the
+// choice of (rank, lambda) that minimises the total risk: what makes HyRes
+// "parameter-free" (arXiv 2204.06979, Sec. 2.1).
+//
+// For unit-variance noise, soft-thresholding the detail coefficients of
+// component i at lambda (keeping LL) has risk
+//   S_i(lambda) = N - 2 #{detail: |c| <= lambda} + sum_detail min(c^2, lambda^2),
+// and dropping the component has risk S_i(inf) = sum_all c^2 - N.
+// On the uniform grid lambda_k = k * delta both counts and clipped sums come
+// from one histogram pass: bin k collects the coefficients with
+// lambda_{k-1} < |c| <= lambda_k (bin 0: c == 0), so prefix sums give
+//   #{|c| <= lambda_k} and sum_{|c| <= lambda_k} c^2
+// and coefficients above lambda_{K-1} contribute lambda_k^2 each.
+#include <float.h>
+
+#include "hyde_internal.cuh"
+
+namespace hyde {
+namespace {
+
+constexpr int kHistThreads = 256;
+constexpr int kHistWarps = kHistThreads / 32;
+
+__global__ void __launch_bounds__(kHistThreads)
+sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl, int K,
+                 float inv_delta, int rows_per_block, unsigned int* __restrict__ counts,
+                 double* __restrict__ sums, double* __restrict__ sum_all) {
+    extern __shared__ unsigned char smraw[];
+    unsigned int* hc = reinterpret_cast<unsigned int*>(smraw);      // [warps][K]
+    float* hs = reinterpret_cast<float*>(hc + kHistWarps * K);      // [warps][K]
+    const int i = blockIdx.y;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < kHistWarps * K; e += kHistThreads) { hc[e] = 0u; hs[e] = 0.f; }
+    __syncthreads();
+    const int y0 = blockIdx.x * rows_per_block;
+    const int y1 = min(y0 + rows_per_block, Hp);
+    const float* base = coef + (long long)i * Hp * Wp;
+    unsigned int* mc = hc + wid * K;
+    float* ms = hs + wid * K;
+    const float kmax = (float)(K - 1);
+    float all = 0.f;
+    auto one = [&](float c, bool in_ll) {
+        const float c2 = c * c;
+        all += c2;
+        if (in_ll) return;
+        const float t = ceilf(fabsf(c) * inv_delta);
+        if (t <= kmax) {
+            const int k = (int)t;
+            atomicAdd(&mc[k], 1u);
+            atomicAdd(&ms[k], c2);
+        }
+    };
+    if ((Wp & 3) == 0) {
+        const int W4 = Wp >> 2;
+        for (int y = y0 + wid; y < y1; y += kHistWarps) {
+            const float4* row = reinterpret_cast<const float4*>(base + (long long)y * Wp);
+            const bool yll = y < hl;
+            for (int x4 = lane; x4 < W4; x4 += 32) {
+                const float4 v = __ldg(row + x4);
+                const int x = x4 * 4;
+                one(v.x, yll && x < wl);
+                one(v.y, yll && x + 1 < wl);
+                one(v.z, yll && x + 2 < wl);
+                one(v.w, yll && x + 3 < wl);
+            }
+        }
+    } else {
+        for (int y = y0 + wid; y < y1; y += kHistWarps) {
+            const float* row = base + (long long)y * Wp;
+            const bool yll = y < hl;
+            for (int x = lane; x < Wp; x += 32) one(__ldg(row + x), yll && x < wl);
+        }
+    }
+    all = warp_sum(all);
+    if (lane == 0 && all != 0.f) atomicAdd(&sum_all[i], (double)all);
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += kHistThreads) {
+        unsigned int c = 0;
+        double sacc = 0.0;
+        for (int w = 0; w < kHistWarps; ++w) { c += hc[w * K + k]; sacc += (double)hs[w * K + k]; }
+        if (c) {
+            atomicAdd(&counts[(long long)i * K + k], c);
+            atomicAdd(&sums[(long long)i * K + k], sacc);
+        }
+    }
+}
+
+// One block. S[i][k], S_inf[i]; with T: the total-SURE table, its first
+// minimum in row-major (rank, lambda) order, and the relative gap to the
+// runner-up.
+__global__ void __launch_bounds__(256)
+sure_select_kernel(const unsigned int* __restrict__ counts, const double* __restrict__ sums,
+                   const double* __restrict__ sum_all, int batch, int K, long long N,
+                   long long N_det, double delta, double* __restrict__ S,
+                   double* __restrict__ S_inf, double* __restrict__ T,
+                   hyde_hyres_info* info, int* rank_out, double* lam_out,
+                   const int* status) {
+    __shared__ double tail[kMaxRank + 1];
+    const int t = threadIdx.x;
+    for (int i = t; i < batch; i += blockDim.x) {
+        double cle = 0.0, sle = 0.0;
+        for (int k = 0; k < K; ++k) {
+            cle += (double)counts[(long long)i * K + k];
+            sle += sums[(long long)i * K + k];
+            const double lam = k * delta;
+            S[(long long)i * K + k] = (double)N - 2.0 * cle + sle + lam * lam * ((double)N_det - cle);
+        }
+        S_inf[i] = sum_all[i] - (double)N;
+    }
+    if (T == nullptr) return;
+    __syncthreads();
+    if (t == 0) {
+        double acc = 0.0;
+        tail[batch] = 0.0;
+        for (int r = batch - 1; r >= 0; --r) { tail[r] = acc; acc += S_inf[r]; }
+        // tail[r] = sum_{i > r} S_inf[i] (0-based r = rank - 1)
+    }
+    __syncthreads();
+    for (int k = t; k < K; k += blockDim.x) {
+        double head = 0.0;
+        for (int r = 0; r < batch; ++r) {
+            head += S[(long long)r * K + k];
+            T[(long long)r * K + k] = head + tail[r];
+        }
+    }
+    __syncthreads();
+    if (t < 32) {
+        const int tot = batch * K;
+        double m1 = DBL_MAX, m2 = DBL_MAX;
+        int i1 = 0x7fffffff;
+        for (int e = t; e < tot; e += 32) {
+            const double v = T[e];
+            if (v < m1 || (v == m1 && e < i1)) { m2 = fmin(m2, m1); m1 = v; i1 = e; }
+            else m2 = fmin(m2, v);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double om1 = __shfl_xor_sync(0xffffffffu, m1, o);
+            const double om2 = __shfl_xor_sync(0xffffffffu, m2, o);
+            const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
+            double n1, n2;
+            int ni;
+            if (om1 < m1 || (om1 == m1 && oi1 < i1)) { n1 = om1; ni = oi1; n2 = fmin(m1, om2); }
+            else { n1 = m1; ni = i1; n2 = fmin(m2, om1); }
+            m1 = n1; m2 = n2; i1 = ni;
+        }
+        if (t == 0) {
+            const int r = i1 / K, k = i1 % K;
+            if (rank_out) *rank_out = r + 1;
+            if (lam_out) *lam_out = k * delta;
+            if (info) {
+                info->status = status ? *status : 0;
+                info->rank = r + 1;
+                info->lambda_index = k;
+                info->reserved = 0;
+                info->lambda = k * delta;
+                info->sure_min = m1;
+                info->sure_gap = (tot > 1) ? (m2 - m1) / fmax(fabs(m1), 1e-300) : 0.0;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+size_t sure_accum_bytes(int batch, int K) {
+    return align_up((size_t)batch * K * sizeof(unsigned int), kAlign) +
+           align_up((size_t)batch * K * sizeof(double), kAlign) +
+           align_up((size_t)batch * sizeof(double), kAlign);
+}
+
+hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int levels, int K,
+                             double delta, const SureBufs& b, cudaStream_t s) {
+    int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    int per_comp = (4 * sms + batch - 1) / batch;
+    if (per_comp > Hp) per_comp = Hp;
+    if (per_comp < 1) per_comp = 1;
+    int rows = (Hp + per_comp - 1) / per_comp;
+    per_comp = (Hp + rows - 1) / rows;
+    size_t smem = (size_t)kHistWarps * K * (sizeof(unsigned int) + sizeof(float));
+    dim3 grid(per_comp, batch);
+    sure_hist_kernel<<<grid, kHistThreads, smem, s>>>(coef, Hp, Wp, Hp >> levels, Wp >> levels, K,
+                                                     (float)(1.0 / delta), rows, b.counts,
+                                                     b.sums, b.sum_all);
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
+                               long long N_det, double delta, double* S, double* S_inf,
+                               double* T, hyde_hyres_info* info, int* rank_out,
+                               double* lam_out, const int* status, cudaStream_t s) {
+    sure_select_kernel<<<1, 256, 0, s>>>(b.counts, b.sums, b.sum_all, batch, K, N, N_det, delta,
+                                         S, S_inf, T, info, rank_out, lam_out, status);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace hyde

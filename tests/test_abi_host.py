@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/hyde.h declares, and rejects bad
+arguments before touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hyde.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hyde_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2204_06979_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("hyde_noise_est", "hyde_dwt2", "hyde_idwt2", "hyde_gram",
+                 "hyde_hyres_denoise", "hyde_workspace_size", "hyde_sure_table",
+                 "hyde_eig_sym_top"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2204_06979_gb300 import _lib
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks a signature for {name}"
+
+
+def test_status_strings_and_version(lib):
+    assert lib.hyde_version() >= 100
+    for code in range(8):
+        assert lib.hyde_status_string(code)
+    assert lib.hyde_status_string(99) == b"unknown status"
+
+
+def test_bad_arguments_rejected_on_host(lib):
+    from paper_2204_06979_gb300._lib import HydeParams
+    sz = ctypes.c_size_t()
+    # DWT: padding longer than the image, bad batch, bad levels
+    assert lib.hyde_dwt_workspace_size(1, 3, 40, 3, ctypes.byref(sz)) == 2
+    assert lib.hyde_dwt_workspace_size(0, 32, 32, 2, ctypes.byref(sz)) == 2
+    assert lib.hyde_dwt_workspace_size(1, 32, 32, 11, ctypes.byref(sz)) == 2
+    assert lib.hyde_dwt_workspace_size(1, 32, 32, 2, None) == 1
+    # DWT with null pointers / wrong wavelet
+    assert lib.hyde_dwt2(None, None, 1, 32, 32, 2, 2, None, 0, None) == 1
+    assert lib.hyde_dwt2(1, 2, 1, 32, 32, 4, 2, None, 0, None) == 1
+    # SURE sizes
+    assert lib.hyde_sure_workspace_size(1, 1, ctypes.byref(sz)) == 2
+    assert lib.hyde_sure_workspace_size(1, 300, ctypes.byref(sz)) == 2
+    # whole path: invalid params
+    p = HydeParams()
+    p.wavelet, p.levels, p.r_max, p.n_lambda, p.precision = 2, 2, 8, 64, 0
+    assert lib.hyde_hyres_denoise(None, None, 32, 64, 64, ctypes.byref(p), None, None, 0, None) == 1
+    p.wavelet = 3
+    assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
+    p.wavelet, p.r_max = 2, 40
+    assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 2
+    p.r_max, p.n_lambda = 8, 1
+    assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 2
+    p.n_lambda, p.reserved[0] = 64, 1
+    assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
+    p.reserved[0] = 0
+    assert lib.hyde_workspace_size(1, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 2
+    assert lib.hyde_eig_sym_top(None, 4, 2, None, None, None, None) == 1
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2204_06979_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_lib, "_LIB", None)
+    with pytest.raises(ImportError):
+        _lib.load()
