@@ -234,6 +234,10 @@ def run_gb300(args) -> None:
     nst = _lib.N_STAGES
     stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
                 for _ in range(args.steps)]
+    for row in stage_ev:          # torch creates the CUDA event on first record
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize(dev)
     import ctypes
     stage_ms = {name: [] for name in _lib.STAGE_NAMES}
     for i in range(args.steps):

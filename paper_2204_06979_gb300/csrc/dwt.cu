@@ -22,6 +22,13 @@ constexpr int TH = 16, TW = 32;            // coefficient tile per subband
 constexpr int IH = 2 * TH + 2, IW = 2 * TW + 2;
 constexpr int kThreads = 256;
 
+// v in [0, m + tile) -> v mod m, with the division only for tiny images
+__device__ __forceinline__ int wrap(int v, int m) {
+    if (v < m) return v;
+    v -= m;
+    return v < m ? v : v % m;
+}
+
 template <bool REFLECT>
 __global__ void __launch_bounds__(kThreads)
 dwt_level_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int hv,
@@ -34,15 +41,18 @@ dwt_level_kernel(const float* __restrict__ src, long long src_bs, int src_ld, in
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     const int hh = h >> 1, wh = w >> 1;
     const float* s = src + (long long)b * src_bs;
-    for (int e = threadIdx.x; e < IH * IW; e += kThreads) {
-        const int r = e / IW, c = e - (e / IW) * IW;
-        int y = (2 * ty0 + r) % h;
-        int x = (2 * tx0 + c) % w;
-        if (REFLECT) {
-            if (y >= hv) y = 2 * hv - 2 - y;
-            if (x >= wv) x = 2 * wv - 2 - x;
+    // one warp per input row; the periodic wrap is a subtraction except on
+    // images smaller than a tile
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int r = wid; r < IH; r += kThreads / 32) {
+        int y = wrap(2 * ty0 + r, h);
+        if (REFLECT && y >= hv) y = 2 * hv - 2 - y;
+        const float* row = s + (long long)y * src_ld;
+        for (int c = lane; c < IW; c += 32) {
+            int x = wrap(2 * tx0 + c, w);
+            if (REFLECT && x >= wv) x = 2 * wv - 2 - x;
+            in[r][c] = __ldg(row + x);
         }
-        in[r][c] = __ldg(s + (long long)y * src_ld + x);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < IH * TW; e += kThreads) {
@@ -99,8 +109,8 @@ idwt_level_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
     const float* C = coef + (long long)b * coef_bs;
     for (int e = threadIdx.x; e < (TH + 1) * (TW + 1); e += kThreads) {
         const int j = e / (TW + 1), k = e % (TW + 1);
-        const int J = (ty0 + j - 1 + hh) % hh;
-        const int K = (tx0 + k - 1 + wh) % wh;
+        const int J = ty0 + j == 0 ? hh - 1 : wrap(ty0 + j - 1, hh);
+        const int K = tx0 + k == 0 ? wh - 1 : wrap(tx0 + k - 1, wh);
         sLL[j][k] = L[(long long)J * ll_ld + K];
         const float hl = C[(long long)J * coef_ld + wh + K];
         const float lh = C[(long long)(hh + J) * coef_ld + K];

@@ -31,19 +31,22 @@ noise_gj_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
     extern __shared__ float sm[];
     float* A = sm;                  // p * p
     float* colk = A + p * p;        // p
-    float* rowk = colk + p;         // p
+    float* rowk = colk + p;         // p   (first holds 1 / S in float)
     const int t = threadIdx.x;
+    const int lane0 = t & 31, wid0 = t >> 5;
+    // FP64 is slow on this part: p square roots in double, the p^2 scaling in float
     for (int i = t; i < p; i += blockDim.x) {
         double d = R[(long long)i * p + i];
         if (!(d > 0.0) || !isfinite(d)) set_status(status, HYDE_ERR_NUMERIC);
-        S[i] = d > 0.0 ? sqrt(d) : 1.0;
+        const double s = d > 0.0 ? sqrt(d) : 1.0;
+        S[i] = s;
+        rowk[i] = (float)(1.0 / s);
     }
     __syncthreads();
-    for (int e = t; e < p * p; e += blockDim.x) {
-        int i = e / p, j = e % p;
-        double di = R[(long long)i * p + i], dj = R[(long long)j * p + j];
-        double si = di > 0.0 ? sqrt(di) : 1.0, sj = dj > 0.0 ? sqrt(dj) : 1.0;
-        A[e] = (float)(R[(long long)i * p + j] / (si * sj));
+    for (int i = wid0; i < p; i += 32) {
+        const float si = rowk[i];
+        for (int j = lane0; j < p; j += 32)
+            A[i * p + j] = (float)R[(long long)i * p + j] * si * rowk[j];
     }
     __syncthreads();
     for (int k = 0; k < p; ++k) {
@@ -155,7 +158,7 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
     int c = q < 0.f;
     for (int i = 1; i < p; ++i) {
         if (fabsf(q) < pivmin) q = -pivmin;
-        q = (d[i] - x) - e2[i - 1] / q;
+        q = (d[i] - x) - __fdividef(e2[i - 1], q);
         c += q < 0.f;
     }
     return c;
@@ -170,13 +173,17 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int lda = S.lda;
 
-    // ---- load (optionally whitened) matrix, scaled by 1 / max |diag|
+    // ---- load (optionally whitened) matrix, scaled by 1 / max |diag|;
+    // FP64 only for the p diagonal entries, the p^2 scaling in float
     __shared__ float s_scale;
+    float* iw = S.v;   // 1 / wsig (float), reused as the Householder vector later
     if (t < 32) {
         double mx = 0.0;
         for (int i = lane; i < p; i += 32) {
             double a = Ain[(long long)i * p + i];
-            if (wsig) a /= wsig[i] * wsig[i];
+            double w = wsig ? 1.0 / wsig[i] : 1.0;
+            iw[i] = (float)w;
+            a *= w * w;
             if (!isfinite(a)) set_status(status, HYDE_ERR_NUMERIC);
             mx = fmax(mx, fabs(a));
         }
@@ -185,11 +192,10 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     }
     __syncthreads();
     const float scale = s_scale;
-    for (int e = t; e < p * p; e += blockDim.x) {
-        int i = e / p, j = e % p;
-        double a = Ain[e];
-        if (wsig) a /= wsig[i] * wsig[j];
-        S.A[i * lda + j] = (float)a * scale;
+    for (int i = wid; i < p; i += 32) {
+        const float si = iw[i] * scale;
+        for (int j = lane; j < p; j += 32)
+            S.A[i * lda + j] = (float)Ain[(long long)i * p + j] * si * iw[j];
     }
     __syncthreads();
 

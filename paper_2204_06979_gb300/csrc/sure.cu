@@ -19,25 +19,25 @@
 namespace hyde {
 namespace {
 
-constexpr int kHistThreads = 256;
-constexpr int kHistWarps = kHistThreads / 32;
-
-__global__ void __launch_bounds__(kHistThreads)
+// Every thread owns a private column of the block's histogram (layout
+// [bin][thread], so a thread's updates never conflict with another's and
+// need no atomics); the block reduces the columns and adds them to the
+// global table with one atomic per bin.
+__global__ void __launch_bounds__(256)
 sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl, int K,
                  float inv_delta, int rows_per_block, unsigned int* __restrict__ counts,
                  double* __restrict__ sums, double* __restrict__ sum_all) {
     extern __shared__ unsigned char smraw[];
-    unsigned int* hc = reinterpret_cast<unsigned int*>(smraw);      // [warps][K]
-    float* hs = reinterpret_cast<float*>(hc + kHistWarps * K);      // [warps][K]
+    const int T = blockDim.x, tid = threadIdx.x;
+    unsigned int* hc = reinterpret_cast<unsigned int*>(smraw);     // [K][T]
+    float* hs = reinterpret_cast<float*>(hc + (size_t)K * T);      // [K][T]
     const int i = blockIdx.y;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < kHistWarps * K; e += kHistThreads) { hc[e] = 0u; hs[e] = 0.f; }
+    const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
+    for (int e = tid; e < K * T; e += T) { hc[e] = 0u; hs[e] = 0.f; }
     __syncthreads();
     const int y0 = blockIdx.x * rows_per_block;
     const int y1 = min(y0 + rows_per_block, Hp);
     const float* base = coef + (long long)i * Hp * Wp;
-    unsigned int* mc = hc + wid * K;
-    float* ms = hs + wid * K;
     const float kmax = (float)(K - 1);
     float all = 0.f;
     auto one = [&](float c, bool in_ll) {
@@ -47,13 +47,13 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
         const float t = ceilf(fabsf(c) * inv_delta);
         if (t <= kmax) {
             const int k = (int)t;
-            atomicAdd(&mc[k], 1u);
-            atomicAdd(&ms[k], c2);
+            hc[k * T + tid] += 1u;
+            hs[k * T + tid] += c2;
         }
     };
     if ((Wp & 3) == 0) {
         const int W4 = Wp >> 2;
-        for (int y = y0 + wid; y < y1; y += kHistWarps) {
+        for (int y = y0 + wid; y < y1; y += nw) {
             const float4* row = reinterpret_cast<const float4*>(base + (long long)y * Wp);
             const bool yll = y < hl;
             for (int x4 = lane; x4 < W4; x4 += 32) {
@@ -66,7 +66,7 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
             }
         }
     } else {
-        for (int y = y0 + wid; y < y1; y += kHistWarps) {
+        for (int y = y0 + wid; y < y1; y += nw) {
             const float* row = base + (long long)y * Wp;
             const bool yll = y < hl;
             for (int x = lane; x < Wp; x += 32) one(__ldg(row + x), yll && x < wl);
@@ -75,13 +75,17 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
     all = warp_sum(all);
     if (lane == 0 && all != 0.f) atomicAdd(&sum_all[i], (double)all);
     __syncthreads();
-    for (int k = threadIdx.x; k < K; k += kHistThreads) {
+    for (int k = wid; k < K; k += nw) {
         unsigned int c = 0;
-        double sacc = 0.0;
-        for (int w = 0; w < kHistWarps; ++w) { c += hc[w * K + k]; sacc += (double)hs[w * K + k]; }
-        if (c) {
+        float sacc = 0.f;
+        for (int q = lane; q < T; q += 32) { c += hc[k * T + q]; sacc += hs[k * T + q]; }
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        }
+        if (lane == 0 && c) {
             atomicAdd(&counts[(long long)i * K + k], c);
-            atomicAdd(&sums[(long long)i * K + k], sacc);
+            atomicAdd(&sums[(long long)i * K + k], (double)sacc);
         }
     }
 }
@@ -178,9 +182,16 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int l
     if (per_comp < 1) per_comp = 1;
     int rows = (Hp + per_comp - 1) / per_comp;
     per_comp = (Hp + rows - 1) / rows;
-    size_t smem = (size_t)kHistWarps * K * (sizeof(unsigned int) + sizeof(float));
+    // threads per block: the private histograms (8 bytes per bin and thread)
+    // stay within 96 KB so that two blocks share an SM
+    int threads = (int)((96 * 1024) / (8 * (size_t)K)) / 32 * 32;
+    if (threads > 256) threads = 256;
+    if (threads < 32) threads = 32;
+    size_t smem = (size_t)K * threads * 8;
+    if (ensure_smem_limit((const void*)sure_hist_kernel, (int)smem) != cudaSuccess)
+        return HYDE_ERR_CUDA;
     dim3 grid(per_comp, batch);
-    sure_hist_kernel<<<grid, kHistThreads, smem, s>>>(coef, Hp, Wp, Hp >> levels, Wp >> levels, K,
+    sure_hist_kernel<<<grid, threads, smem, s>>>(coef, Hp, Wp, Hp >> levels, Wp >> levels, K,
                                                      (float)(1.0 / delta), rows, b.counts,
                                                      b.sums, b.sum_all);
     return cuda_status(cudaGetLastError());
