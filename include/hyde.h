@@ -118,6 +118,27 @@ hyde_status hyde_gram(const float* Y, int p, long long n, int precision,
                       double* R, void* ws, size_t ws_bytes,
                       cudaStream_t stream);
 
+/* Allocation-free Gram matrix, for callers that cannot allocate device
+ * memory: code running where cudaMalloc is unavailable or forbidden (inside
+ * a memory-budgeted host framework that owns every allocation, a real-time
+ * loop that must not allocate) and that therefore cannot supply the
+ * workspace hyde_gram needs. The paper has no counterpart; this is an
+ * interface convenience. Same inputs and output as hyde_gram with
+ * precision HYDE_PREC_FP32; the float partial sums go to one fixed
+ * 16 MiB array in device global memory (hyde_gram_noalloc_scratch_bytes)
+ * that every GPU loading the library holds until the process exits. The
+ * grid is capped so the partials fit (fewer blocks for large p, never
+ * fewer than one); p > 256 is rejected with HYDE_ERR_SHAPE. The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress,
+ * no allocation), so make that first call before any stream capture. All
+ * calls share the one array: calls that can overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+size_t hyde_gram_noalloc_scratch_bytes(void);
+hyde_status hyde_gram_noalloc(const float* Y, int p, long long n, double* R,
+                              cudaStream_t stream);
+
 /* ------------------------------------------------------------ noise level
  * Per-band noise standard deviation by multiple regression of each band on
  * all other bands (least squares, no intercept): sigma_b^2 is the residual

@@ -41,6 +41,8 @@ SIGNATURES = {
     "hyde_version": (c_int, []),
     "hyde_gram_workspace_size": (c_int, [c_int, c_ll, c_int, c_size_p]),
     "hyde_gram": (c_int, [c_vp, c_int, c_ll, c_int, c_vp, c_vp, c_size, c_vp]),
+    "hyde_gram_noalloc_scratch_bytes": (c_size, []),
+    "hyde_gram_noalloc": (c_int, [c_vp, c_int, c_ll, c_vp, c_vp]),
     "hyde_noise_est_workspace_size": (c_int, [c_int, c_int, c_int, c_size_p]),
     "hyde_noise_est": (c_int, [c_vp, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_size, c_vp]),
     "hyde_eig_sym_top": (c_int, [c_vp, c_int, c_int, c_vp, c_vp, c_vp, c_vp]),

@@ -10,6 +10,8 @@
 // thread reads are spread over all 32 banks. Each block writes its float
 // partial; a second kernel sums the partials in double and mirrors the
 // triangle.
+#include <mutex>
+
 #include "hyde_internal.cuh"
 
 namespace hyde {
@@ -197,3 +199,64 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
 }
 
 }  // namespace hyde
+
+// --------------------------------------------------------------------------
+// Allocation-free variant of hyde_gram.
+//
+// The float partial sums of the Gram kernel live in a fixed array in device
+// global memory, reserved when the module is loaded onto a GPU and held by
+// every GPU that loads the library until the process exits. Host code cannot
+// use the array's name as a device pointer (it names a host-side shadow), so
+// the device address is looked up once per device with that device current.
+// --------------------------------------------------------------------------
+namespace hyde {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_gram_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+hyde_status gram_scratch_for_current_device(float** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HYDE_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* addr = nullptr;
+        if (cudaGetSymbolAddress(&addr, g_gram_scratch) != cudaSuccess || !addr)
+            return HYDE_ERR_CUDA;
+        g_scratch_addr[dev] = addr;
+    }
+    *out = reinterpret_cast<float*>(g_scratch_addr[dev]);
+    return HYDE_OK;
+}
+
+}  // namespace
+}  // namespace hyde
+
+extern "C" size_t hyde_gram_noalloc_scratch_bytes(void) { return hyde::kNoAllocScratchBytes; }
+
+extern "C" hyde_status hyde_gram_noalloc(const float* Y, int p, long long n, double* R,
+                                         cudaStream_t stream) {
+    using namespace hyde;
+    if (!Y || !R) return HYDE_ERR_INVALID_ARG;
+    GramPlan g;
+    hyde_status st = gram_plan(p, n, &g);
+    if (st != HYDE_OK) return st;
+    // each block writes ntiles * 64 floats of partials; use as many blocks as
+    // the fixed scratch holds (never more than the occupancy-sized grid)
+    const size_t per_block = (size_t)g.ntiles * 64 * sizeof(float);
+    const size_t max_blocks = kNoAllocScratchBytes / per_block;
+    if (max_blocks < 1) return HYDE_ERR_SHAPE;
+    if ((size_t)g.blocks > max_blocks) g.blocks = (int)max_blocks;
+    g.partial_bytes = (size_t)g.blocks * per_block;
+    float* scratch = nullptr;
+    st = gram_scratch_for_current_device(&scratch);
+    if (st != HYDE_OK) return st;
+    // every block overwrites its whole partial slot, so nothing needs clearing
+    return launch_gram(Y, p, n, g, scratch, R, nullptr, stream);
+}
+
