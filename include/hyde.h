@@ -236,8 +236,9 @@ hyde_status hyde_hyres_denoise_timed(const float* Y, float* X, int p, int H,
                                      size_t ws_bytes, cudaStream_t stream,
                                      cudaEvent_t* events);
 
-/* Number of kernels one hyde_hyres_denoise call launches (10 + 2 * levels;
- * the workspace clear is a memset, not counted), or -1 for bad params. */
+/* Number of kernels one hyde_hyres_denoise call launches (11 + 2 * levels;
+ * the two memsets that clear the workspace header and R are not counted),
+ * or -1 for bad params. */
 int hyde_hyres_kernel_launches(const hyde_hyres_params* params);
 
 #ifdef __cplusplus

@@ -41,7 +41,7 @@ namespace {
 
 inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-inline int rank_pad(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
+inline int rank_pad(int r) { return (r + 3) / 4 * 4; }   // weights row stride: r rounded up to 4
 
 bool padded(int H, int W, int levels, int* Hp, int* Wp) {
     if (levels < 1 || levels > kMaxLevels || H < 1 || W < 1) return false;
@@ -85,7 +85,7 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     const long long n = (long long)H * W;
     if (n < p) return HYDE_ERR_SHAPE;
     if (eig_smem_bytes(p, pr->r_max) > 227 * 1024) return HYDE_ERR_SHAPE;
-    if (((size_t)p * p + 2 * p) * sizeof(float) > 227 * 1024) return HYDE_ERR_SHAPE;
+    if (noise_smem_bytes(p) > 227 * 1024) return HYDE_ERR_SHAPE;
     HyresLayout l;
     l.Hp = Hp; l.Wp = Wp; l.RM = rank_pad(pr->r_max); l.K = pr->n_lambda;
     l.N = (long long)Hp * Wp; l.n = n;
@@ -192,7 +192,7 @@ hyde_status hyde_noise_est(const float* Y, int p, int H, int W, double* sigma, i
     size_t need = 0;
     hyde_status st = hyde_noise_est_workspace_size(p, H, W, &need);
     if (st != HYDE_OK) return st;
-    if (((size_t)p * p + 2 * p) * sizeof(float) > 227 * 1024) return HYDE_ERR_SHAPE;
+    if (noise_smem_bytes(p) > 227 * 1024) return HYDE_ERR_SHAPE;
     if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return HYDE_ERR_WORKSPACE;
     long long n = (long long)H * W;
     GramPlan g;
@@ -392,8 +392,8 @@ hyde_status hyde_hyres_denoise_timed(const float* Y, float* X, int p, int H, int
 
 int hyde_hyres_kernel_launches(const hyde_hyres_params* params) {
     if (!params || params->levels < 1 || params->levels > kMaxLevels) return -1;
-    // gram 2, noise 2, eig 1, weights 1, projection 1, DWT L, SURE 2, IDWT L, back 1
-    return 10 + 2 * params->levels;
+    // gram 2, noise 2, eig 1, weights 1, projection 1, DWT L, SURE 3, IDWT L, back 1
+    return 11 + 2 * params->levels;
 }
 
 }  // extern "C"

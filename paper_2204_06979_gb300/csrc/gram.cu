@@ -130,21 +130,32 @@ gram_partial_kernel(const float* __restrict__ Y, int p, long long n, int PT,
     }
 }
 
+// Block partials -> R in double. Each thread sums one element over a segment
+// of kReduceSeg blocks (independent loads, double accumulation) and adds the
+// segment total to R with a double atomic; R is cleared beforehand.
+constexpr int kReduceSeg = 16;
+
 __global__ void gram_reduce_kernel(const float* __restrict__ partials, int nblocks,
                                    int p, int PT, int ntiles, double* __restrict__ R,
                                    int* status) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)ntiles * 64) return;
-    const int t = (int)(idx / 64), e = (int)(idx % 64);
+    const int b0 = blockIdx.y * kReduceSeg;
+    const int b1 = min(b0 + kReduceSeg, nblocks);
+    if (b0 >= b1) return;
+    const long long stride = (long long)ntiles * 64;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += (double)partials[(long long)b * ntiles * 64 + idx];
+#pragma unroll 4
+    for (int b = b0; b < b1; ++b) s += (double)__ldg(partials + (long long)b * stride + idx);
+    const int t = (int)(idx / 64), e = (int)(idx % 64);
     int ti, tj;
     tile_of(t, PT, ti, tj);
     const int i = 8 * ti + e / 8, j = 8 * tj + e % 8;
     if (i < p && j < p) {
         if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
-        R[(long long)i * p + j] = s;
-        R[(long long)j * p + i] = s;
+        atomicAdd(&R[(long long)i * p + j], s);
+        // a diagonal tile holds both (i, j) and (j, i): no mirror there
+        if (ti != tj) atomicAdd(&R[(long long)j * p + i], s);
     }
 }
 
@@ -193,8 +204,10 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
         gram_partial_kernel<kGramMaxThreads><<<g.blocks, g.threads, g.smem, s>>>(
             Y, p, n, g.PT, g.ntiles, per, partials);
     long long tot = (long long)g.ntiles * 64;
-    gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-        partials, g.blocks, p, g.PT, g.ntiles, R, status);
+    if (cudaMemsetAsync(R, 0, (size_t)p * p * sizeof(double), s) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    dim3 rgrid((unsigned)((tot + 255) / 256), (g.blocks + kReduceSeg - 1) / kReduceSeg);
+    gram_reduce_kernel<<<rgrid, 256, 0, s>>>(partials, g.blocks, p, g.PT, g.ntiles, R, status);
     return cuda_status(cudaGetLastError());
 }
 

@@ -84,6 +84,7 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n,
                                    double* sigma, void* ws, int* status,
                                    cudaStream_t s);
 size_t eig_smem_bytes(int p, int r);
+size_t noise_smem_bytes(int p);   // dynamic smem of the Gauss-Jordan kernel (0 = registers)
 hyde_status launch_eig_top(const double* A, const double* wsig, int p,
                            int r, double* evals, double* V, int* status,
                            cudaStream_t s);

@@ -7,10 +7,18 @@
 //    subspace of the low-rank model);
 //  * the float projection / back-projection weights V/sigma and V*sigma.
 //
-// GB300 runs FP64 at a small fraction of its FP32 rate, so the O(p^3) work is
-// done in FP32 inside one thread block (the p x p matrix lives in shared
-// memory) and FP64 is used where it buys accuracy cheaply: the diagonal of the
-// inverse gets one Newton correction in double, spread over p blocks.
+// GB300 runs FP64 at 1/64 of its FP32 rate, so the O(p^3) work is done in
+// FP32 inside one thread block and FP64 is used where it buys accuracy
+// cheaply: the diagonal of the inverse gets one Newton correction in double,
+// spread over p blocks.
+//
+// The p-step recurrences (Gauss-Jordan, Householder) are latency- and
+// issue-bound on one SM, so for p <= 192 the matrix lives in registers: the
+// 1024 threads form a 32 x 32 grid and thread (w, l) owns the T x T tile of
+// rows w*T.. and columns l*T.. (T = ceil(p/32)). A step then costs T^2 FMAs
+// per thread plus one to three barriers; the row and column of the current
+// step are published through small double-buffered shared vectors. Larger p
+// falls back to kernels that keep the matrix in shared memory.
 #include <float.h>
 
 #include "hyde_internal.cuh"
@@ -18,34 +26,133 @@
 namespace hyde {
 namespace {
 
-constexpr int kLA = 1024;   // threads of the single-block kernels
+constexpr int kLA = 1024;     // threads of the single-block kernels
+constexpr int kMaxRegT = 6;   // register tiles up to 6 x 6 (p <= 192)
 
 // --------------------------------------------------------------------------
 // Noise level, part 1: Gauss-Jordan inverse (no pivoting: the matrix is SPD)
-// of As = S^-1 R S^-1, S = sqrt(diag R), in float. Writes As^-1 (p x p) and
-// S (double[p]).
+// of As = S^-1 R S^-1, S = sqrt(diag R), in float; writes As^-1 and S.
+// Pivots of the unit-diagonal matrix are Schur complements >= its smallest
+// eigenvalue; below ~16 ulp the float inverse is meaningless (exactly
+// collinear bands give ~1 ulp), which is reported as HYDE_ERR_NUMERIC.
 // --------------------------------------------------------------------------
+constexpr float kPivotFloor = 2e-6f;
+
+template <int T>
 __global__ void __launch_bounds__(kLA, 1)
-noise_gj_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
-                double* __restrict__ S, int* status) {
+noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
+                    double* __restrict__ S, int* status) {
+    __shared__ float s_inv[32 * T];
+    __shared__ float s_row[2][32 * T];
+    __shared__ float s_col[2][32 * T];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int r0 = wid * T, c0 = lane * T;
+    for (int i = t; i < 32 * T; i += kLA) {
+        float inv = 0.f;
+        if (i < p) {
+            const double d = R[(long long)i * p + i];
+            if (!(d > 0.0) || !isfinite(d)) set_status(status, HYDE_ERR_NUMERIC);
+            const double sd = d > 0.0 ? sqrt(d) : 1.0;
+            S[i] = sd;
+            inv = (float)(1.0 / sd);
+        }
+        s_inv[i] = inv;
+    }
+    __syncthreads();
+    float a[T][T];
+#pragma unroll
+    for (int ii = 0; ii < T; ++ii) {
+        const int i = r0 + ii;
+#pragma unroll
+        for (int jj = 0; jj < T; ++jj) {
+            const int j = c0 + jj;
+            float v = (i == j) ? 1.f : 0.f;      // identity on the padding
+            if (i < p && j < p) v = (float)R[(long long)i * p + j] * s_inv[i] * s_inv[j];
+            a[ii][jj] = v;
+        }
+    }
+    for (int k = 0; k < p; ++k) {
+        const int buf = k & 1;
+        const int kt = k / T, ko = k - kt * T;
+        if (wid == kt) {
+#pragma unroll
+            for (int ii = 0; ii < T; ++ii)
+                if (ii == ko) {
+#pragma unroll
+                    for (int jj = 0; jj < T; ++jj) s_row[buf][c0 + jj] = a[ii][jj];
+                }
+        }
+        if (lane == kt) {
+#pragma unroll
+            for (int jj = 0; jj < T; ++jj)
+                if (jj == ko) {
+#pragma unroll
+                    for (int ii = 0; ii < T; ++ii) s_col[buf][r0 + ii] = a[ii][jj];
+                }
+        }
+        __syncthreads();   // one barrier per step: the vectors are double-buffered
+        const float pk = s_col[buf][k];
+        if (t == 0 && !(pk > kPivotFloor)) set_status(status, HYDE_ERR_NUMERIC);
+        const float piv = 1.0f / pk;
+        float rk[T], ck[T];
+#pragma unroll
+        for (int q = 0; q < T; ++q) {
+            rk[q] = s_row[buf][c0 + q];
+            ck[q] = s_col[buf][r0 + q] * piv;
+        }
+#pragma unroll
+        for (int ii = 0; ii < T; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < T; ++jj) a[ii][jj] = fmaf(-ck[ii], rk[jj], a[ii][jj]);
+        if (wid == kt) {   // row k: a_kj * piv
+#pragma unroll
+            for (int ii = 0; ii < T; ++ii)
+                if (ii == ko) {
+#pragma unroll
+                    for (int jj = 0; jj < T; ++jj) a[ii][jj] = rk[jj] * piv;
+                }
+        }
+        if (lane == kt) {  // column k: -a_ik * piv, and the pivot itself
+#pragma unroll
+            for (int jj = 0; jj < T; ++jj)
+                if (jj == ko) {
+#pragma unroll
+                    for (int ii = 0; ii < T; ++ii)
+                        a[ii][jj] = (wid == kt && ii == ko) ? piv : -ck[ii];
+                }
+        }
+    }
+#pragma unroll
+    for (int ii = 0; ii < T; ++ii) {
+        const int i = r0 + ii;
+#pragma unroll
+        for (int jj = 0; jj < T; ++jj) {
+            const int j = c0 + jj;
+            if (i < p && j < p) Ainv[(long long)i * p + j] = a[ii][jj];
+        }
+    }
+}
+
+// Shared-memory Gauss-Jordan for p > 192 (same arithmetic, matrix in smem).
+__global__ void __launch_bounds__(kLA, 1)
+noise_gj_smem_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
+                     double* __restrict__ S, int* status) {
     extern __shared__ float sm[];
     float* A = sm;                  // p * p
     float* colk = A + p * p;        // p
     float* rowk = colk + p;         // p   (first holds 1 / S in float)
-    const int t = threadIdx.x;
-    const int lane0 = t & 31, wid0 = t >> 5;
-    // FP64 is slow on this part: p square roots in double, the p^2 scaling in float
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int i = t; i < p; i += blockDim.x) {
         double d = R[(long long)i * p + i];
         if (!(d > 0.0) || !isfinite(d)) set_status(status, HYDE_ERR_NUMERIC);
-        const double s = d > 0.0 ? sqrt(d) : 1.0;
-        S[i] = s;
-        rowk[i] = (float)(1.0 / s);
+        const double sd = d > 0.0 ? sqrt(d) : 1.0;
+        S[i] = sd;
+        rowk[i] = (float)(1.0 / sd);
     }
     __syncthreads();
-    for (int i = wid0; i < p; i += 32) {
+    for (int i = wid; i < p; i += 32) {
         const float si = rowk[i];
-        for (int j = lane0; j < p; j += 32)
+        for (int j = lane; j < p; j += 32)
             A[i * p + j] = (float)R[(long long)i * p + j] * si * rowk[j];
     }
     __syncthreads();
@@ -56,12 +163,8 @@ noise_gj_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
         }
         __syncthreads();
         const float pk = colk[k];
-        // pivots of the unit-diagonal matrix are Schur complements >= its
-        // smallest eigenvalue; below ~16 ulp the float inverse is meaningless
-        // (exactly collinear bands give ~1 ulp)
-        if (t == 0 && !(pk > 2e-6f)) set_status(status, HYDE_ERR_NUMERIC);
+        if (t == 0 && !(pk > kPivotFloor)) set_status(status, HYDE_ERR_NUMERIC);
         const float piv = 1.0f / pk;
-        const int lane = t & 31, wid = t >> 5;
         for (int i = wid; i < p; i += 32) {
             const float ci = -colk[i] * piv;
             for (int j = lane; j < p; j += 32) {
@@ -89,8 +192,9 @@ noise_refine_kernel(const double* __restrict__ R, const float* __restrict__ Ainv
     extern __shared__ double xs[];   // p
     __shared__ double red[8];
     const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const double sb = S[b];
     for (int i = t; i < p; i += blockDim.x)
-        xs[i] = (double)Ainv[(long long)i * p + b] / (S[i] * S[b]);
+        xs[i] = (double)Ainv[(long long)i * p + b] / (S[i] * sb);
     __syncthreads();
     double part = 0.0;
     for (int i = w; i < p; i += 8) {
@@ -116,41 +220,36 @@ noise_refine_kernel(const double* __restrict__ R, const float* __restrict__ Ainv
 
 // --------------------------------------------------------------------------
 // Leading r eigenpairs of a symmetric p x p matrix (one block, 1024 threads),
-// optionally whitened on load: A_ij / (wsig_i wsig_j).
-// 1. Householder tridiagonalisation in float (A = Q T Q^T, reflectors kept
-//    below the diagonal).
+// optionally whitened on load (A_ij / (wsig_i wsig_j)) and scaled by
+// 1 / max |diag|.
+// 1. Householder tridiagonalisation in float (A = Q T Q^T); the reflectors
+//    v_k (v_k[0] = 1) are kept for step 5.
 // 2. Eigenvalues of T by multisection: one warp per wanted eigenvalue, each
 //    lane counts eigenvalues below one of 32 points (Sturm sequence).
 // 3. Eigenvectors of T from a twisted factorisation at each eigenvalue.
 // 4. Classical Gram-Schmidt, twice, over the r vectors (orthogonality inside
 //    clusters of close eigenvalues).
-// 5. Back-transformation by the reflectors (one warp per vector).
+// 5. Back-transformation by the reflectors (one warp per vector), sign rule
+//    (largest-magnitude entry positive), write-out in double.
 // --------------------------------------------------------------------------
-struct EigSmem {
-    float* A; float* tau; float* d; float* e; float* e2; float* v; float* pv;
-    float* red; float* lam; float* X; float* Dp; float* Dm; float* dots;
-    int lda;
+struct EigTail {
+    float* d; float* e; float* e2; float* tau; float* lam; float* X; float* Dp; float* Dm;
+    float* dots;
 };
 
-__device__ inline EigSmem eig_carve(float* base, int p, int r) {
-    EigSmem m;
-    m.lda = p + 1;
-    float* q = base;
-    m.A = q;   q += p * m.lda;
-    m.tau = q; q += p;
-    m.d = q;   q += p;
-    m.e = q;   q += p;
-    m.e2 = q;  q += p;
-    m.v = q;   q += p;
-    m.pv = q;  q += p;
-    m.red = q; q += 64;
-    m.lam = q; q += 32;
-    m.dots = q; q += 32;
-    m.X = q;   q += p * r;
-    m.Dp = q;  q += p * r;
-    m.Dm = q;  q += p * r;
-    return m;
-}
+// reflector k as (first element, stride); element i is v_k[i], i < p-k-1
+struct ReflInPlace {
+    const float* A; int lda;
+    __device__ const float* base(int k) const { return A + (k + 1) * lda + k; }
+    __device__ int stride() const { return lda; }
+};
+struct ReflPacked {
+    const float* V; int p;
+    __device__ const float* base(int k) const {
+        return V + (size_t)k * (p - 1) - (size_t)k * (k - 1) / 2;
+    }
+    __device__ int stride() const { return 1; }
+};
 
 __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int p,
                                            float x, float pivmin) {
@@ -164,114 +263,17 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
     return c;
 }
 
-__global__ void __launch_bounds__(kLA, 1)
-eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
-               int p, int r, double* __restrict__ evals, double* __restrict__ V,
-               int* status) {
-    extern __shared__ float sm[];
-    EigSmem S = eig_carve(sm, p, r);
+// Stages 2-5 on the tridiagonal (d, e) in shared memory; all 1024 threads.
+template <class Refl>
+__device__ void eig_tail(const EigTail& S, const Refl& refl, int p, int r, float scale,
+                         double* __restrict__ evals, double* __restrict__ V, int* status) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int lda = S.lda;
-
-    // ---- load (optionally whitened) matrix, scaled by 1 / max |diag|;
-    // FP64 only for the p diagonal entries, the p^2 scaling in float
-    __shared__ float s_scale;
-    float* iw = S.v;   // 1 / wsig (float), reused as the Householder vector later
-    if (t < 32) {
-        double mx = 0.0;
-        for (int i = lane; i < p; i += 32) {
-            double a = Ain[(long long)i * p + i];
-            double w = wsig ? 1.0 / wsig[i] : 1.0;
-            iw[i] = (float)w;
-            a *= w * w;
-            if (!isfinite(a)) set_status(status, HYDE_ERR_NUMERIC);
-            mx = fmax(mx, fabs(a));
-        }
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) s_scale = mx > 0.0 ? (float)(1.0 / mx) : 1.0f;
-    }
-    __syncthreads();
-    const float scale = s_scale;
-    for (int i = wid; i < p; i += 32) {
-        const float si = iw[i] * scale;
-        for (int j = lane; j < p; j += 32)
-            S.A[i * lda + j] = (float)Ain[(long long)i * p + j] * si * iw[j];
-    }
-    __syncthreads();
-
-    // ---- 1. Householder tridiagonalisation
-    for (int k = 0; k + 2 < p; ++k) {
-        const int m = p - k - 1;
-        float* col = S.A + (k + 1) * lda + k;   // col[i * lda] = A[k+1+i][k]
-        if (wid == 0) {
-            float ss = 0.f;
-            for (int i = 1 + lane; i < m; i += 32) { float x = col[i * lda]; ss = fmaf(x, x, ss); }
-            ss = warp_sum(ss);
-            const float alpha = col[0];
-            __syncwarp();   // every lane has read col[] before lane 0 rewrites it
-            float tau = 0.f, beta = alpha, sc = 0.f;
-            if (ss > 0.f) {
-                const float nrm = sqrtf(fmaf(alpha, alpha, ss));
-                beta = alpha >= 0.f ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                sc = 1.0f / (alpha - beta);
-            }
-            for (int i = lane; i < m; i += 32) {
-                float vi = (i == 0) ? 1.0f : col[i * lda] * sc;
-                if (ss == 0.f) vi = (i == 0) ? 1.0f : 0.f;
-                S.v[i] = vi;
-                col[i * lda] = vi;       // reflector kept for step 5
-            }
-            if (lane == 0) { S.tau[k] = tau; S.d[k] = S.A[k * lda + k]; S.e[k] = beta; }
-        }
-        __syncthreads();
-        const float tau = S.tau[k];
-        if (tau != 0.f) {
-            // p = tau * A22 v, one warp per row; K partials per warp
-            float kpart = 0.f;
-            for (int i = wid; i < m; i += 32) {
-                const float* row = S.A + (k + 1 + i) * lda + (k + 1);
-                float u = 0.f;
-                for (int j = lane; j < m; j += 32) u = fmaf(row[j], S.v[j], u);
-                u = warp_sum(u) * tau;
-                if (lane == 0) S.pv[i] = u;
-                kpart = fmaf(u, S.v[i], kpart);
-            }
-            if (lane == 0) S.red[wid] = kpart;
-            __syncthreads();
-            float K = 0.f;
-#pragma unroll
-            for (int w = 0; w < 32; ++w) K += S.red[w];
-            K *= 0.5f * tau;
-            // A22 -= v w^T + w v^T, w = p - K v
-            for (int i = wid; i < m; i += 32) {
-                float* row = S.A + (k + 1 + i) * lda + (k + 1);
-                const float vi = S.v[i], wi = fmaf(-K, vi, S.pv[i]);
-                for (int j = lane; j < m; j += 32) {
-                    const float vj = S.v[j], wj = fmaf(-K, vj, S.pv[j]);
-                    row[j] = fmaf(-vi, wj, fmaf(-wi, vj, row[j]));
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if (t == 0) {
-        if (p >= 2) {
-            S.d[p - 2] = S.A[(p - 2) * lda + (p - 2)];
-            S.e[p - 2] = S.A[(p - 1) * lda + (p - 2)];
-            S.tau[p - 2] = 0.f;
-        }
-        S.d[p - 1] = S.A[(p - 1) * lda + (p - 1)];
-        S.e[p - 1] = 0.f;
-    }
-    __syncthreads();
     for (int i = t; i < p; i += blockDim.x) {
         S.e2[i] = S.e[i] * S.e[i];
         if (!isfinite(S.d[i]) || !isfinite(S.e[i])) set_status(status, HYDE_ERR_NUMERIC);
     }
     __syncthreads();
 
-    // ---- Gershgorin interval and pivot guard (warp 0)
     __shared__ float s_lo, s_hi, s_pivmin;
     if (wid == 0) {
         float lo = FLT_MAX, hi = -FLT_MAX, emax = 0.f;
@@ -295,7 +297,7 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     }
     __syncthreads();
 
-    // ---- 2. multisection, warp j finds the (j+1)-th largest eigenvalue
+    // 2. multisection, warp j finds the (j+1)-th largest eigenvalue
     if (wid < r) {
         const int target = p - 1 - wid;       // ascending index
         float lo = s_lo, hi = s_hi;
@@ -316,7 +318,7 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     }
     __syncthreads();
 
-    // ---- 3. twisted factorisation eigenvector of T for each eigenvalue
+    // 3. twisted factorisation eigenvector of T for each eigenvalue
     if (wid < r) {
         const float lam = S.lam[wid];
         float* Dp = S.Dp + wid * p;
@@ -328,7 +330,7 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
             if (fabsf(q) < pm) q = -pm;
             Dp[0] = q;
             for (int i = 1; i < p; ++i) {
-                q = (S.d[i] - lam) - S.e2[i - 1] / q;
+                q = (S.d[i] - lam) - __fdividef(S.e2[i - 1], q);
                 if (fabsf(q) < pm) q = -pm;
                 Dp[i] = q;
             }
@@ -337,7 +339,7 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
             if (fabsf(q) < pm) q = -pm;
             Dm[p - 1] = q;
             for (int i = p - 2; i >= 0; --i) {
-                q = (S.d[i] - lam) - S.e2[i] / q;
+                q = (S.d[i] - lam) - __fdividef(S.e2[i], q);
                 if (fabsf(q) < pm) q = -pm;
                 Dm[i] = q;
             }
@@ -359,10 +361,10 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
         if (lane == 0) {
             z[kt] = 1.0f;
             float zz = 1.0f;
-            for (int i = kt - 1; i >= 0; --i) { zz = -(S.e[i] / Dp[i]) * zz; z[i] = zz; }
+            for (int i = kt - 1; i >= 0; --i) { zz = -__fdividef(S.e[i], Dp[i]) * zz; z[i] = zz; }
         } else if (lane == 1) {
             float zz = 1.0f;
-            for (int i = kt + 1; i < p; ++i) { zz = -(S.e[i - 1] / Dm[i]) * zz; z[i] = zz; }
+            for (int i = kt + 1; i < p; ++i) { zz = -__fdividef(S.e[i - 1], Dm[i]) * zz; z[i] = zz; }
         }
         __syncwarp();
         float ss = 0.f;
@@ -373,7 +375,7 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     }
     __syncthreads();
 
-    // ---- 4. classical Gram-Schmidt, two passes, in descending order
+    // 4. classical Gram-Schmidt, two passes, in descending order
     for (int j = 1; j < r; ++j) {
         float* zj = S.X + j * p;
         for (int pass = 0; pass < 2; ++pass) {
@@ -402,21 +404,21 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
         __syncthreads();
     }
 
-    // ---- 5. back-transformation x <- H_0 ... H_{p-3} x, one warp per vector
+    // 5. back-transformation x <- H_0 ... H_{p-3} x, one warp per vector
     if (wid < r) {
         float* x = S.X + wid * p;
+        const int st = refl.stride();
         for (int k = p - 3; k >= 0; --k) {
             const float tau = S.tau[k];
             if (tau == 0.f) continue;
             const int m = p - k - 1;
-            const float* col = S.A + (k + 1) * lda + k;
+            const float* col = refl.base(k);
             float dt = 0.f;
-            for (int i = lane; i < m; i += 32) dt = fmaf(col[i * lda], x[k + 1 + i], dt);
+            for (int i = lane; i < m; i += 32) dt = fmaf(col[i * st], x[k + 1 + i], dt);
             dt = warp_sum(dt) * tau;
-            for (int i = lane; i < m; i += 32) x[k + 1 + i] = fmaf(-dt, col[i * lda], x[k + 1 + i]);
+            for (int i = lane; i < m; i += 32) x[k + 1 + i] = fmaf(-dt, col[i * st], x[k + 1 + i]);
             __syncwarp();
         }
-        // sign: entry of largest magnitude positive (smallest index on ties)
         float best = -1.f;
         int bi = 0;
         for (int i = lane; i < p; i += 32) {
@@ -434,6 +436,304 @@ eig_top_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     }
 }
 
+// Shared-memory layout of the register-tile eigensolver.
+struct EigRegSmem {
+    float *Vh, *d, *e, *e2, *tau, *iw, *lam, *dots, *X, *Dp, *Dm, *red;
+    float *xb, *vb, *pv;   // [2][32T] each
+};
+
+__device__ inline EigRegSmem eig_reg_carve(float* q, int p, int r, int T) {
+    EigRegSmem m;
+    const int P = 32 * T;
+    m.Vh = q;   q += (p * (p - 1)) / 2 + 1;
+    m.d = q;    q += P;
+    m.e = q;    q += P;
+    m.e2 = q;   q += P;
+    m.tau = q;  q += P;
+    m.iw = q;   q += P;
+    m.lam = q;  q += 32;
+    m.dots = q; q += 32;
+    m.red = q;  q += 64;
+    m.xb = q;   q += 2 * P;
+    m.vb = q;   q += 2 * P;
+    m.pv = q;   q += 2 * P;
+    m.X = q;    q += p * r;
+    m.Dp = q;   q += p * r;
+    m.Dm = q;   q += p * r;
+    return m;
+}
+
+size_t eig_reg_smem_floats(int p, int r, int T) {
+    const size_t P = 32 * (size_t)T;
+    return (size_t)(p * (p - 1)) / 2 + 1 + 5 * P + 128 + 6 * P + 3 * (size_t)p * r;
+}
+
+template <int T>
+__global__ void __launch_bounds__(kLA, 1)
+eig_reg_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p, int r,
+               double* __restrict__ evals, double* __restrict__ V, int* status) {
+    extern __shared__ float sm[];
+    EigRegSmem S = eig_reg_carve(sm, p, r, T);
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int r0 = wid * T, c0 = lane * T;
+    constexpr int P = 32 * T;
+
+    __shared__ float s_scale;
+    if (t < 32) {
+        double mx = 0.0;
+        for (int i = lane; i < P; i += 32) {
+            float w = 0.f;
+            if (i < p) {
+                double a = Ain[(long long)i * p + i];
+                const double wd = wsig ? 1.0 / wsig[i] : 1.0;
+                w = (float)wd;
+                a *= wd * wd;
+                if (!isfinite(a)) set_status(status, HYDE_ERR_NUMERIC);
+                mx = fmax(mx, fabs(a));
+            }
+            S.iw[i] = w;
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_scale = mx > 0.0 ? (float)(1.0 / mx) : 1.0f;
+    }
+    __syncthreads();
+    const float scale = s_scale;
+    float a[T][T];
+#pragma unroll
+    for (int ii = 0; ii < T; ++ii) {
+        const int i = r0 + ii;
+#pragma unroll
+        for (int jj = 0; jj < T; ++jj) {
+            const int j = c0 + jj;
+            a[ii][jj] = (i < p && j < p)
+                            ? (float)Ain[(long long)i * p + j] * (S.iw[i] * scale) * S.iw[j]
+                            : 0.f;
+        }
+    }
+
+    // ---- 1. Householder tridiagonalisation, matrix in registers
+    for (int k = 0; k + 2 < p; ++k) {
+        const int buf = k & 1;
+        float* xb = S.xb + buf * P;
+        float* vb = S.vb + buf * P;
+        float* pv = S.pv + buf * P;
+        float* red = S.red + buf * 32;
+        const int kt = k / T, ko = k - kt * T;
+        if (lane == kt) {                     // publish column k
+#pragma unroll
+            for (int jj = 0; jj < T; ++jj)
+                if (jj == ko) {
+#pragma unroll
+                    for (int ii = 0; ii < T; ++ii) xb[r0 + ii] = a[ii][jj];
+                }
+        }
+        __syncthreads();
+        if (wid == 0) {                       // reflector from x = A[k+1..p-1][k]
+            float ss = 0.f;
+            for (int i = k + 2 + lane; i < p; i += 32) ss = fmaf(xb[i], xb[i], ss);
+            ss = warp_sum(ss);
+            const float alpha = xb[k + 1];
+            float tau = 0.f, beta = alpha, sc = 0.f;
+            if (ss > 0.f) {
+                const float nrm = sqrtf(fmaf(alpha, alpha, ss));
+                beta = alpha >= 0.f ? -nrm : nrm;
+                tau = (beta - alpha) / beta;
+                sc = 1.0f / (alpha - beta);
+            }
+            float* vh = S.Vh + (size_t)k * (p - 1) - (size_t)k * (k - 1) / 2;
+            for (int i = lane; i < P; i += 32) {
+                float vi = 0.f;
+                if (i == k + 1) vi = 1.0f;
+                else if (i > k + 1 && i < p && ss > 0.f) vi = xb[i] * sc;
+                vb[i] = vi;
+                if (i > k && i < p) vh[i - k - 1] = vi;
+            }
+            if (lane == 0) { S.tau[k] = tau; S.d[k] = xb[k]; S.e[k] = beta; }
+        }
+        __syncthreads();
+        const float tau = S.tau[k];
+        const bool active = (r0 + T - 1 > k) && tau != 0.f;   // warp owns rows beyond k
+        float vr[T], vc[T];
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < T; ++q) { vr[q] = vb[r0 + q]; vc[q] = vb[c0 + q]; }
+            float kpart = 0.f;
+#pragma unroll
+            for (int ii = 0; ii < T; ++ii) {
+                float s = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < T; ++jj) s = fmaf(a[ii][jj], vc[jj], s);
+                s = warp_sum(s) * tau;
+                if (r0 + ii <= k) s = 0.f;     // rows already reduced take no update
+                if (lane == 0) pv[r0 + ii] = s;
+                kpart = fmaf(s, vr[ii], kpart);
+            }
+            if (lane == 0) red[wid] = kpart;
+        } else if (lane == 0) {
+            red[wid] = 0.f;
+#pragma unroll
+            for (int q = 0; q < T; ++q) pv[r0 + q] = 0.f;
+        }
+        __syncthreads();
+        if (active) {
+            const float K = 0.5f * tau * warp_sum(red[lane]);
+            float wr[T], wc[T];
+#pragma unroll
+            for (int q = 0; q < T; ++q) {
+                wr[q] = fmaf(-K, vr[q], pv[r0 + q]);
+                wc[q] = fmaf(-K, vc[q], pv[c0 + q]);
+            }
+#pragma unroll
+            for (int ii = 0; ii < T; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < T; ++jj)
+                    a[ii][jj] = fmaf(-vr[ii], wc[jj], fmaf(-wr[ii], vc[jj], a[ii][jj]));
+        }
+    }
+    // last 2 x 2 block: publish columns p-2 and p-1
+    {
+        float* xb0 = S.xb;
+        float* xb1 = S.xb + P;
+        __syncthreads();
+        const int k0 = p >= 2 ? p - 2 : 0, k1 = p - 1;
+        const int kt0 = k0 / T, ko0 = k0 - kt0 * T, kt1 = k1 / T, ko1 = k1 - kt1 * T;
+#pragma unroll
+        for (int jj = 0; jj < T; ++jj) {
+            if (lane == kt0 && jj == ko0) {
+#pragma unroll
+                for (int ii = 0; ii < T; ++ii) xb0[r0 + ii] = a[ii][jj];
+            }
+            if (lane == kt1 && jj == ko1) {
+#pragma unroll
+                for (int ii = 0; ii < T; ++ii) xb1[r0 + ii] = a[ii][jj];
+            }
+        }
+        __syncthreads();
+        if (t == 0) {
+            if (p >= 2) {
+                S.d[p - 2] = xb0[p - 2];
+                S.e[p - 2] = xb0[p - 1];
+                S.tau[p - 2] = 0.f;
+            }
+            S.d[p - 1] = xb1[p - 1];
+            S.e[p - 1] = 0.f;
+        }
+        __syncthreads();
+    }
+    EigTail tail{S.d, S.e, S.e2, S.tau, S.lam, S.X, S.Dp, S.Dm, S.dots};
+    eig_tail(tail, ReflPacked{S.Vh, p}, p, r, scale, evals, V, status);
+}
+
+// Shared-memory eigensolver for p > 192 (matrix and reflectors in smem).
+__global__ void __launch_bounds__(kLA, 1)
+eig_smem_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p, int r,
+                double* __restrict__ evals, double* __restrict__ V, int* status) {
+    extern __shared__ float sm[];
+    const int lda = p + 1;
+    float* q = sm;
+    float* A = q;    q += p * lda;
+    float* tauv = q; q += p;
+    float* dv = q;   q += p;
+    float* ev = q;   q += p;
+    float* e2v = q;  q += p;
+    float* v = q;    q += p;
+    float* pvv = q;  q += p;
+    float* red = q;  q += 64;
+    float* lamv = q; q += 32;
+    float* dots = q; q += 32;
+    float* X = q;    q += p * r;
+    float* Dp = q;   q += p * r;
+    float* Dm = q;   q += p * r;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+
+    __shared__ float s_scale;
+    float* iw = v;
+    if (t < 32) {
+        double mx = 0.0;
+        for (int i = lane; i < p; i += 32) {
+            double a = Ain[(long long)i * p + i];
+            double w = wsig ? 1.0 / wsig[i] : 1.0;
+            iw[i] = (float)w;
+            a *= w * w;
+            if (!isfinite(a)) set_status(status, HYDE_ERR_NUMERIC);
+            mx = fmax(mx, fabs(a));
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_scale = mx > 0.0 ? (float)(1.0 / mx) : 1.0f;
+    }
+    __syncthreads();
+    const float scale = s_scale;
+    for (int i = wid; i < p; i += 32) {
+        const float si = iw[i] * scale;
+        for (int j = lane; j < p; j += 32)
+            A[i * lda + j] = (float)Ain[(long long)i * p + j] * si * iw[j];
+    }
+    __syncthreads();
+
+    for (int k = 0; k + 2 < p; ++k) {
+        const int m = p - k - 1;
+        float* col = A + (k + 1) * lda + k;
+        if (wid == 0) {
+            float ss = 0.f;
+            for (int i = 1 + lane; i < m; i += 32) { float x = col[i * lda]; ss = fmaf(x, x, ss); }
+            ss = warp_sum(ss);
+            const float alpha = col[0];
+            __syncwarp();   // every lane has read col[] before it is rewritten
+            float tau = 0.f, beta = alpha, sc = 0.f;
+            if (ss > 0.f) {
+                const float nrm = sqrtf(fmaf(alpha, alpha, ss));
+                beta = alpha >= 0.f ? -nrm : nrm;
+                tau = (beta - alpha) / beta;
+                sc = 1.0f / (alpha - beta);
+            }
+            for (int i = lane; i < m; i += 32) {
+                float vi = (i == 0) ? 1.0f : col[i * lda] * sc;
+                if (ss == 0.f) vi = (i == 0) ? 1.0f : 0.f;
+                v[i] = vi;
+                col[i * lda] = vi;
+            }
+            if (lane == 0) { tauv[k] = tau; dv[k] = A[k * lda + k]; ev[k] = beta; }
+        }
+        __syncthreads();
+        const float tau = tauv[k];
+        if (tau != 0.f) {
+            float kpart = 0.f;
+            for (int i = wid; i < m; i += 32) {
+                const float* row = A + (k + 1 + i) * lda + (k + 1);
+                float u = 0.f;
+                for (int j = lane; j < m; j += 32) u = fmaf(row[j], v[j], u);
+                u = warp_sum(u) * tau;
+                if (lane == 0) pvv[i] = u;
+                kpart = fmaf(u, v[i], kpart);
+            }
+            if (lane == 0) red[wid] = kpart;
+            __syncthreads();
+            const float K = 0.5f * tau * warp_sum(red[lane]);
+            for (int i = wid; i < m; i += 32) {
+                float* row = A + (k + 1 + i) * lda + (k + 1);
+                const float vi = v[i], wi = fmaf(-K, vi, pvv[i]);
+                for (int j = lane; j < m; j += 32) {
+                    const float vj = v[j], wj = fmaf(-K, vj, pvv[j]);
+                    row[j] = fmaf(-vi, wj, fmaf(-wi, vj, row[j]));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (p >= 2) {
+            dv[p - 2] = A[(p - 2) * lda + (p - 2)];
+            ev[p - 2] = A[(p - 1) * lda + (p - 2)];
+            tauv[p - 2] = 0.f;
+        }
+        dv[p - 1] = A[(p - 1) * lda + (p - 1)];
+        ev[p - 1] = 0.f;
+    }
+    __syncthreads();
+    EigTail tail{dv, ev, e2v, tauv, lamv, X, Dp, Dm, dots};
+    eig_tail(tail, ReflInPlace{A, lda}, p, r, scale, evals, V, status);
+}
+
 __global__ void weights_kernel(const double* __restrict__ V, const double* __restrict__ sigma,
                                int p, int r, int ldw, float* __restrict__ P,
                                float* __restrict__ Q) {
@@ -446,6 +746,21 @@ __global__ void weights_kernel(const double* __restrict__ V, const double* __res
     }
 }
 
+template <int T>
+hyde_status launch_eig_reg(const double* A, const double* wsig, int p, int r, double* evals,
+                           double* V, int* status, cudaStream_t s) {
+    const size_t smem = eig_reg_smem_floats(p, r, T) * sizeof(float);
+    if (ensure_smem_limit((const void*)eig_reg_kernel<T>, (int)smem) != cudaSuccess)
+        return HYDE_ERR_SHAPE;
+    eig_reg_kernel<T><<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);
+    return HYDE_OK;
+}
+
+size_t eig_smem_old_bytes(int p, int r) {
+    return ((size_t)p * (p + 1) + 6 * (size_t)p + 64 + 32 + 32 + 3 * (size_t)p * r) *
+           sizeof(float);
+}
+
 }  // namespace
 
 size_t noise_ws_bytes(int p) {
@@ -453,32 +768,62 @@ size_t noise_ws_bytes(int p) {
            align_up((size_t)p * sizeof(double), kAlign);
 }
 
+size_t noise_smem_bytes(int p) {
+    const int T = (p + 31) / 32;
+    return T <= kMaxRegT ? 0 : ((size_t)p * p + 2 * p) * sizeof(float);
+}
+
 hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* sigma,
                                    void* ws, int* status, cudaStream_t s) {
     float* Ainv = reinterpret_cast<float*>(ws);
     double* Sd = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) +
                                            align_up((size_t)p * p * sizeof(float), kAlign));
-    size_t smem = ((size_t)p * p + 2 * p) * sizeof(float);
-    if (smem > 227 * 1024) return HYDE_ERR_SHAPE;
-    if (ensure_smem_limit((const void*)noise_gj_kernel, (int)smem) != cudaSuccess)
-        return HYDE_ERR_CUDA;
-    noise_gj_kernel<<<1, kLA, smem, s>>>(R, p, Ainv, Sd, status);
+    const int T = (p + 31) / 32;
+    switch (T) {
+        case 1: noise_gj_reg_kernel<1><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
+        case 2: noise_gj_reg_kernel<2><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
+        case 3: noise_gj_reg_kernel<3><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
+        case 4: noise_gj_reg_kernel<4><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
+        case 5: noise_gj_reg_kernel<5><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
+        case 6: noise_gj_reg_kernel<6><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
+        default: {
+            size_t smem = noise_smem_bytes(p);
+            if (ensure_smem_limit((const void*)noise_gj_smem_kernel, (int)smem) != cudaSuccess)
+                return HYDE_ERR_SHAPE;
+            noise_gj_smem_kernel<<<1, kLA, smem, s>>>(R, p, Ainv, Sd, status);
+        }
+    }
     noise_refine_kernel<<<p, 256, p * sizeof(double), s>>>(R, Ainv, Sd, p, n, sigma, status);
     return cuda_status(cudaGetLastError());
 }
 
 size_t eig_smem_bytes(int p, int r) {
-    return ((size_t)p * (p + 1) + 6 * (size_t)p + 64 + 32 + 32 + 3 * (size_t)p * r) *
-           sizeof(float);
+    const int T = (p + 31) / 32;
+    if (T <= kMaxRegT) return eig_reg_smem_floats(p, r, T) * sizeof(float);
+    return eig_smem_old_bytes(p, r);
 }
 
-hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r,
-                           double* evals, double* V, int* status, cudaStream_t s) {
-    size_t smem = eig_smem_bytes(p, r);
-    if (smem > 227 * 1024 || r > 32 || r < 1 || r > p) return HYDE_ERR_SHAPE;
-    if (ensure_smem_limit((const void*)eig_top_kernel, (int)smem) != cudaSuccess)
-        return HYDE_ERR_CUDA;
-    eig_top_kernel<<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);
+hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, double* evals,
+                           double* V, int* status, cudaStream_t s) {
+    if (r > 32 || r < 1 || r > p) return HYDE_ERR_SHAPE;
+    if (eig_smem_bytes(p, r) > 227 * 1024) return HYDE_ERR_SHAPE;
+    const int T = (p + 31) / 32;
+    hyde_status st = HYDE_OK;
+    switch (T) {
+        case 1: st = launch_eig_reg<1>(A, wsig, p, r, evals, V, status, s); break;
+        case 2: st = launch_eig_reg<2>(A, wsig, p, r, evals, V, status, s); break;
+        case 3: st = launch_eig_reg<3>(A, wsig, p, r, evals, V, status, s); break;
+        case 4: st = launch_eig_reg<4>(A, wsig, p, r, evals, V, status, s); break;
+        case 5: st = launch_eig_reg<5>(A, wsig, p, r, evals, V, status, s); break;
+        case 6: st = launch_eig_reg<6>(A, wsig, p, r, evals, V, status, s); break;
+        default: {
+            const size_t smem = eig_smem_old_bytes(p, r);
+            if (ensure_smem_limit((const void*)eig_smem_kernel, (int)smem) != cudaSuccess)
+                return HYDE_ERR_SHAPE;
+            eig_smem_kernel<<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);
+        }
+    }
+    if (st != HYDE_OK) return st;
     return cuda_status(cudaGetLastError());
 }
 

@@ -90,35 +90,57 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
     }
 }
 
-// One block. S[i][k], S_inf[i]; with T: the total-SURE table, its first
-// minimum in row-major (rank, lambda) order, and the relative gap to the
-// runner-up.
+// S[i][k] and S_inf[i]: one warp per component; the prefix sums over the
+// bins are warp scans (K/32 chunks of shuffles), not a K-long serial chain.
 __global__ void __launch_bounds__(256)
-sure_select_kernel(const unsigned int* __restrict__ counts, const double* __restrict__ sums,
-                   const double* __restrict__ sum_all, int batch, int K, long long N,
-                   long long N_det, double delta, double* __restrict__ S,
-                   double* __restrict__ S_inf, double* __restrict__ T,
-                   hyde_hyres_info* info, int* rank_out, double* lam_out,
-                   const int* status) {
-    __shared__ double tail[kMaxRank + 1];
-    const int t = threadIdx.x;
-    for (int i = t; i < batch; i += blockDim.x) {
-        double cle = 0.0, sle = 0.0;
-        for (int k = 0; k < K; ++k) {
-            cle += (double)counts[(long long)i * K + k];
-            sle += sums[(long long)i * K + k];
+sure_table_kernel(const unsigned int* __restrict__ counts, const double* __restrict__ sums,
+                  const double* __restrict__ sum_all, int batch, int K, long long N,
+                  long long N_det, double delta, double* __restrict__ S,
+                  double* __restrict__ S_inf) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= batch) return;
+    double ccarry = 0.0, scarry = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = k0 + lane;
+        double c = k < K ? (double)counts[(long long)i * K + k] : 0.0;
+        double q = k < K ? sums[(long long)i * K + k] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double c2 = __shfl_up_sync(0xffffffffu, c, o);
+            const double q2 = __shfl_up_sync(0xffffffffu, q, o);
+            if (lane >= o) { c += c2; q += q2; }
+        }
+        const double cle = c + ccarry, sle = q + scarry;
+        if (k < K) {
             const double lam = k * delta;
             S[(long long)i * K + k] = (double)N - 2.0 * cle + sle + lam * lam * ((double)N_det - cle);
         }
-        S_inf[i] = sum_all[i] - (double)N;
+        ccarry = __shfl_sync(0xffffffffu, cle, 31);
+        scarry = __shfl_sync(0xffffffffu, sle, 31);
     }
-    if (T == nullptr) return;
-    __syncthreads();
-    if (t == 0) {
-        double acc = 0.0;
-        tail[batch] = 0.0;
-        for (int r = batch - 1; r >= 0; --r) { tail[r] = acc; acc += S_inf[r]; }
-        // tail[r] = sum_{i > r} S_inf[i] (0-based r = rank - 1)
+    if (lane == 0) S_inf[i] = sum_all[i] - (double)N;
+}
+
+// One block: the total-SURE table T(r, k) = sum_{i<=r} S_i(lambda_k) +
+// sum_{r<i<=r_max} S_i(inf), its first minimum in row-major (rank, lambda)
+// order, and the relative gap to the runner-up.
+__global__ void __launch_bounds__(256)
+sure_select_kernel(const double* __restrict__ S, const double* __restrict__ S_inf, int batch,
+                   int K, double delta, double* __restrict__ T, hyde_hyres_info* info,
+                   int* rank_out, double* lam_out, const int* status) {
+    __shared__ double tail[kMaxRank + 1];
+    const int t = threadIdx.x;
+    if (t < 32) {   // tail[r] = sum_{i > r} S_inf[i] by a reversed warp scan
+        const int i = batch - 1 - t;
+        double v = (i >= 0) ? S_inf[i] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, v, o);
+            if (t >= o) v += u;
+        }
+        // v = sum_{j >= i} S_inf[j]; tail[i] = v - S_inf[i]
+        if (i >= 0) tail[i] = v - S_inf[i];
     }
     __syncthreads();
     for (int k = t; k < K; k += blockDim.x) {
@@ -201,8 +223,13 @@ hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
                                long long N_det, double delta, double* S, double* S_inf,
                                double* T, hyde_hyres_info* info, int* rank_out,
                                double* lam_out, const int* status, cudaStream_t s) {
-    sure_select_kernel<<<1, 256, 0, s>>>(b.counts, b.sums, b.sum_all, batch, K, N, N_det, delta,
-                                         S, S_inf, T, info, rank_out, lam_out, status);
+    sure_table_kernel<<<(batch + 7) / 8, 256, 0, s>>>(b.counts, b.sums, b.sum_all, batch, K, N,
+                                                       N_det, delta, S, S_inf);
+    if (T != nullptr) {
+        if (batch > kMaxRank) return HYDE_ERR_SHAPE;
+        sure_select_kernel<<<1, 256, 0, s>>>(S, S_inf, batch, K, delta, T, info, rank_out,
+                                             lam_out, status);
+    }
     return cuda_status(cudaGetLastError());
 }
 
