@@ -15,5 +15,6 @@ from .hyres import (  # noqa: F401
     whiten_gram, eig_desc, padded_shape, pad_symmetric, dwt2, idwt2,
     soft_threshold, lambda_grid, sure_table, sure_rank_lambda,
     select_rank_lambda, hyres,
-    rel_l2, psnr, sam,
+    rel_l2, psnr, sam, level_map, hyres_scaled, hyres_scaled_grad, mse_loss,
+    sure_loss_scaled,
 )

@@ -366,3 +366,106 @@ def sam(clean, est):
     e = np.asarray(est, dtype=np.float64).reshape(p, -1)
     cos = np.sum(c * e, axis=0) / (np.linalg.norm(c, axis=0) * np.linalg.norm(e, axis=0))
     return float(np.mean(np.arccos(np.clip(cos, -1.0, 1.0))))
+
+
+# --------------------------------------------------------------------------
+# Differentiation form: learnable per-(component, level) threshold scales.
+# The paper's package makes several conventional methods differentiable with
+# PyTorch autograd and puts a trainable HyRes step in front of a DNN
+# (Sec. 2.1, Sec. 2.2). Here the rank r* and base threshold lambda* are chosen
+# by SURE at s = 1 and held fixed; the detail coefficients of component i at
+# level l are thresholded at lambda* s[i][l].
+# --------------------------------------------------------------------------
+
+def level_map(Hp, Wp, levels):
+    """Level (1..L) of every Mallat position; 0 for the final LL band."""
+    lev = np.zeros((Hp, Wp), dtype=np.int64)
+    for l in range(levels, 0, -1):
+        hl, wl = Hp >> (l - 1), Wp >> (l - 1)
+        blk = np.zeros((Hp, Wp), dtype=bool)
+        blk[:hl, :wl] = True
+        blk[: Hp >> l, : Wp >> l] = False
+        lev[blk] = l
+    return lev
+
+
+def hyres_scaled(Y, levels, r_max, scale, n_lambda=64):
+    """Forward of the differentiation form. ``scale`` is ``[p or r_max][L]``
+    (rows >= r* unused). Returns the dict of ``hyres`` plus ``X_scaled``."""
+    o = hyres(Y, levels, r_max, n_lambda)
+    p, H, W = np.asarray(Y).shape
+    r = o["rank"]
+    C = o["C"][:r]
+    Hp, Wp = C.shape[-2:]
+    lev = level_map(Hp, Wp, levels)
+    scale = np.asarray(scale, dtype=np.float64)
+    Ch = C.copy()
+    for i in range(r):
+        for l in range(1, levels + 1):
+            m = lev == l
+            Ch[i][m] = soft_threshold(C[i][m], o["lam"] * scale[i, l - 1])
+    Zh = idwt2(Ch, levels)[:, :H, :W].reshape(r, H * W)
+    Xs = o["sigma"][:, None] * (o["V"][:, :r] @ Zh)
+    o = dict(o)
+    o["X_scaled"] = Xs.reshape(p, H, W)
+    o["level_map"] = lev
+    return o
+
+
+def hyres_scaled_grad(Y, G, levels, r_max, scale, n_lambda=64):
+    """Analytic gradient dL/ds of a loss with dL/dX_hat = G (``[p][H][W]``),
+    by the adjoint chain: G -> V_r^T D G (transpose of the back-projection)
+    -> zero-embed in H_p x W_p (transpose of the crop) -> DWT (the inverse DWT
+    is orthogonal, so its transpose is the forward transform) -> times
+    d soft(c, lam)/d lam = -sign(c) [|c| > lam] -> summed per (component,
+    level) -> times lambda*. Returns ``dscale`` shaped like ``scale``."""
+    o = hyres_scaled(Y, levels, r_max, scale, n_lambda)
+    p, H, W = np.asarray(Y).shape
+    r = o["rank"]
+    Gf = np.asarray(G, dtype=np.float64).reshape(p, H * W)
+    dZ = o["V"][:, :r].T @ (o["sigma"][:, None] * Gf)          # r x n
+    Hp, Wp = o["C"].shape[-2:]
+    dZp = np.zeros((r, Hp, Wp))
+    dZp[:, :H, :W] = dZ.reshape(r, H, W)
+    dC = dwt2(dZp, levels)
+    lev = o["level_map"]
+    C = o["C"][:r]
+    scale = np.asarray(scale, dtype=np.float64)
+    ds = np.zeros_like(scale)
+    for i in range(r):
+        for l in range(1, levels + 1):
+            m = lev == l
+            lam = o["lam"] * scale[i, l - 1]
+            c = C[i][m]
+            ds[i, l - 1] = o["lam"] * np.sum(dC[i][m] * (-np.sign(c)) * (np.abs(c) > lam))
+    return ds, o
+
+
+def mse_loss(Xh, Xc):
+    """Mean squared error to the clean cube, ``||X_hat - X||^2 / numel``."""
+    d = np.asarray(Xh, dtype=np.float64) - np.asarray(Xc, dtype=np.float64)
+    return float(np.sum(d * d) / d.size)
+
+
+def sure_loss_scaled(o, levels, scale):
+    """SURE of the kept components with per-level thresholds lambda* s[i][l]:
+    sum_i [N - sum_l (2 #{|c| <= lam_il} - sum min(c^2, lam_il^2))] over the
+    detail coefficients of level l (LL kept). Returns (value, gradient) with
+    the almost-everywhere gradient: d/dlam sum min(c^2, lam^2) =
+    2 lam #{|c| > lam}, the count term being piecewise constant."""
+    r = o["rank"]
+    C = o["C"][:r]
+    lev = o["level_map"]
+    N = C.shape[-1] * C.shape[-2]
+    scale = np.asarray(scale, dtype=np.float64)
+    val = 0.0
+    ds = np.zeros_like(scale)
+    for i in range(r):
+        val += N
+        for l in range(1, levels + 1):
+            m = lev == l
+            lam = o["lam"] * scale[i, l - 1]
+            c = np.abs(C[i][m])
+            val += -2.0 * np.count_nonzero(c <= lam) + np.sum(np.minimum(c * c, lam * lam))
+            ds[i, l - 1] = o["lam"] * 2.0 * lam * np.count_nonzero(c > lam)
+    return float(val), ds

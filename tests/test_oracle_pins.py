@@ -337,3 +337,102 @@ def test_c0_selects_planted_rank_and_denoises():
     assert o["rank"] == 4
     assert O.psnr(c["X"], o["X"]) > O.psnr(c["X"], c["Y"]) + 10.0
     assert O.sam(c["X"], o["X"]) < O.sam(c["X"], c["Y"])
+
+
+# ---------------------------------------------------------------- gradient form
+
+def _frozen_mask_loss(o, Y_shape, Xc, levels, scale, mask):
+    """MSE with the threshold mask frozen: a soft threshold whose kept set is
+    fixed is affine in lambda, so the loss is quadratic in the scales."""
+    p, H, W = Y_shape
+    r = o["rank"]
+    C = o["C"][:r]
+    lev = o["level_map"]
+    Ch = C.copy()
+    for i in range(r):
+        for l in range(1, levels + 1):
+            m = lev == l
+            lam = o["lam"] * scale[i, l - 1]
+            c = C[i][m]
+            Ch[i][m] = np.where(mask[i][m], c - lam * np.sign(c), 0.0)
+    Zh = O.idwt2(Ch, levels)[:, :H, :W].reshape(r, H * W)
+    Xh = (o["sigma"][:, None] * (o["V"][:, :r] @ Zh)).reshape(p, H, W)
+    return O.mse_loss(Xh, Xc)
+
+
+def test_scaled_forward_at_unit_scale_is_hyres():
+    c = make_cube(40, 48, 12, m=3, seed=51)
+    o = O.hyres_scaled(c["Y"], 2, 6, np.ones((12, 2)))
+    assert O.rel_l2(o["X_scaled"], o["X"]) < 1e-13
+
+
+def test_level_map_counts():
+    lev = O.level_map(32, 48, 3)
+    assert np.count_nonzero(lev == 0) == 4 * 6
+    assert np.count_nonzero(lev == 1) == 32 * 48 * 3 // 4
+    assert np.count_nonzero(lev == 3) == 3 * 4 * 6
+
+
+def test_mse_gradient_against_frozen_mask_finite_differences():
+    """With the kept set frozen the loss is exactly quadratic in s, so central
+    differences (h = 1e-3) equal the analytic adjoint to rounding."""
+    c = make_cube(48, 40, 16, m=3, seed=41)
+    levels, r_max = 2, 8
+    rng = np.random.default_rng(0)
+    s = 1.0 + 0.2 * rng.standard_normal((16, levels))
+    o = O.hyres_scaled(c["Y"], levels, r_max, s)
+    G = 2.0 * (o["X_scaled"] - c["X"]) / c["X"].size
+    g, _ = O.hyres_scaled_grad(c["Y"], G, levels, r_max, s)
+    r = o["rank"]
+    mask = np.zeros(o["C"][:r].shape, dtype=bool)
+    for i in range(r):
+        for l in range(1, levels + 1):
+            m = o["level_map"] == l
+            mask[i][m] = np.abs(o["C"][i][m]) > o["lam"] * s[i, l - 1]
+    h = 1e-3
+    fd = np.zeros_like(s)
+    for i in range(r):
+        for l in range(levels):
+            e = np.zeros_like(s)
+            e[i, l] = h
+            fd[i, l] = (_frozen_mask_loss(o, c["Y"].shape, c["X"], levels, s + e, mask)
+                        - _frozen_mask_loss(o, c["Y"].shape, c["X"], levels, s - e, mask)) / (2 * h)
+    assert np.max(np.abs(fd[:r] - g[:r])) < 1e-7 * max(1.0, np.max(np.abs(g[:r])))
+    assert np.all(g[r:] == 0.0)
+    # mask free: the kinks move only a few coefficients, so raw differences
+    # still agree to about 1 %
+    raw = np.zeros_like(s)
+    for i in range(r):
+        for l in range(levels):
+            e = np.zeros_like(s)
+            e[i, l] = h
+            raw[i, l] = (O.mse_loss(O.hyres_scaled(c["Y"], levels, r_max, s + e)["X_scaled"], c["X"])
+                         - O.mse_loss(O.hyres_scaled(c["Y"], levels, r_max, s - e)["X_scaled"], c["X"])) / (2 * h)
+    assert np.linalg.norm(raw[:r] - g[:r]) <= 1e-2 * np.linalg.norm(g[:r])
+
+
+def test_sure_loss_gradient_continuous_part():
+    """The SURE loss is piecewise smooth in s: its count term jumps, the rest
+    is sum min(c^2, lam^2). Central differences of that continuous part match
+    the stated gradient 2 lam* lam #{|c| > lam}."""
+    c = make_cube(48, 40, 16, m=3, seed=42)
+    levels, r_max = 2, 8
+    s = np.full((16, levels), 1.1)
+    o = O.hyres_scaled(c["Y"], levels, r_max, s)
+    val, g = O.sure_loss_scaled(o, levels, s)
+    r = o["rank"]
+    h = 1e-4
+    for i in range(r):
+        for l in range(levels):
+            m = o["level_map"] == l + 1
+            cc = np.abs(o["C"][i][m])
+
+            def cont(si):
+                lam = o["lam"] * si
+                return np.sum(np.minimum(cc * cc, lam * lam))
+            fd = (cont(s[i, l] + h) - cont(s[i, l] - h)) / (2 * h)
+            assert abs(fd - g[i, l]) <= 1e-6 * max(1.0, abs(g[i, l]))
+    # at s = 1 the per-level SURE equals the selection table's entry for (r*, k*)
+    o1 = O.hyres_scaled(c["Y"], levels, r_max, np.ones((16, levels)))
+    v1, _ = O.sure_loss_scaled(o1, levels, np.ones((16, levels)))
+    assert abs(v1 - np.sum(o1["S"][: o1["rank"], o1["k"]])) < 1e-6 * abs(v1)
