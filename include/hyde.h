@@ -236,6 +236,49 @@ hyde_status hyde_hyres_denoise_timed(const float* Y, float* X, int p, int H,
                                      size_t ws_bytes, cudaStream_t stream,
                                      cudaEvent_t* events);
 
+/* ------------------------------------------------- differentiation form
+ * HyRes with learnable threshold scales: the paper's package makes several
+ * conventional methods differentiable with autograd and puts a trainable
+ * HyRes step in front of a DNN (Sec. 2.1, Sec. 2.2). The rank r* and base
+ * threshold lambda* are chosen by SURE at scale = 1 and held fixed (no
+ * gradient through the selection); the detail coefficients of component i
+ * at level l are soft-thresholded at lambda* * scale[i][l].
+ * scale: float[r_max][levels] device (row i = component i, rows >= r*
+ * unused). Otherwise identical to hyde_hyres_denoise, including the
+ * workspace, which the backward then reads.
+ */
+hyde_status hyde_hyres_denoise_scaled(const float* Y, float* X, int p, int H,
+                                      int W, const hyde_hyres_params* params,
+                                      const float* scale, hyde_hyres_info* info,
+                                      void* ws, size_t ws_bytes,
+                                      cudaStream_t stream);
+
+/* Gradient with respect to the scales, by the hand-written adjoint. fws is
+ * the workspace of the preceding hyde_hyres_denoise(_scaled) call on the same
+ * Y and params (read only: weights, rank, lambda*); bws is a separate scratch
+ * (hyde_backward_workspace_size). The forward wavelet coefficients are
+ * recomputed from Y, not stored.
+ *   loss = 0: dX (float[p][H][W] device) is dL/dX_hat;
+ *             dscale[i][l] = lambda* sum dC (-sign C) [|C| > lambda_il] over the
+ *             level-l detail coefficients of component i, dC = DWT of the
+ *             zero-embedded V^T D dX (the inverse DWT is orthogonal).
+ *   loss = 1: the SURE of the kept components with per-level thresholds,
+ *             sum_i [N - sum_l (2 #{|c| <= lambda_il} - sum min(c^2, lambda_il^2))],
+ *             is written to *sure_value (device double, may be NULL) and
+ *             dscale[i][l] = lambda* 2 lambda_il #{|c| > lambda_il} (the count
+ *             term is piecewise constant; dX is ignored).
+ * dscale: float[r_max][levels] device; rows >= r* are zero.
+ */
+hyde_status hyde_backward_workspace_size(int p, int H, int W,
+                                         const hyde_hyres_params* params,
+                                         size_t* bytes);
+hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H,
+                                int W, const hyde_hyres_params* params,
+                                const float* scale, int loss, float* dscale,
+                                double* sure_value, const void* fws,
+                                size_t fws_bytes, void* bws, size_t bws_bytes,
+                                cudaStream_t stream);
+
 /* Number of kernels one hyde_hyres_denoise call launches (11 + 2 * levels;
  * the two memsets that clear the workspace header and R are not counted),
  * or -1 for bad params. */

@@ -61,6 +61,13 @@ SIGNATURES = {
                                          ctypes.POINTER(HydeParams), c_vp, c_vp, c_size, c_vp,
                                          c_vp]),
     "hyde_hyres_kernel_launches": (c_int, [ctypes.POINTER(HydeParams)]),
+    "hyde_hyres_denoise_scaled": (c_int, [c_vp, c_vp, c_int, c_int, c_int,
+                                          ctypes.POINTER(HydeParams), c_vp, c_vp, c_vp, c_size,
+                                          c_vp]),
+    "hyde_backward_workspace_size": (c_int, [c_int, c_int, c_int, ctypes.POINTER(HydeParams),
+                                             c_size_p]),
+    "hyde_hyres_backward": (c_int, [c_vp, c_vp, c_int, c_int, c_int, ctypes.POINTER(HydeParams),
+                                    c_vp, c_int, c_vp, c_vp, c_vp, c_size, c_vp, c_size, c_vp]),
 }
 
 N_STAGES = 8

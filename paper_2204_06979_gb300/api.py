@@ -240,3 +240,106 @@ def hyres_denoise(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64):
     h = HyRes(p, H, W, levels, r_max, n_lambda, device=Y.device)
     X = h(Y)
     return X, h.result_info()
+
+
+# ------------------------------------------------------ differentiation form
+
+def _scale_rows(scale: torch.Tensor, r_max: int, levels: int) -> torch.Tensor:
+    if not scale.is_cuda or scale.dtype != torch.float32 or scale.dim() != 2:
+        raise ValueError("scale must be a float32 CUDA matrix [rows >= r_max, levels]")
+    if scale.shape[0] < r_max or scale.shape[1] != levels:
+        raise ValueError(f"scale must have >= {r_max} rows and {levels} columns")
+    return scale[:r_max].contiguous()
+
+
+class HyResGrad(HyRes):
+    """HyRes with per-(component, level) threshold scales and the hand-written
+    backward. Owns a forward workspace (which the backward reads) and a
+    backward workspace; use one instance per cube of a batch."""
+
+    def __init__(self, p, H, W, levels, r_max, n_lambda=64, device="cuda"):
+        super().__init__(p, H, W, levels, r_max, n_lambda, device)
+        sz = ctypes.c_size_t()
+        _check(self.lib.hyde_backward_workspace_size(p, H, W, ctypes.byref(self.params),
+                                                     ctypes.byref(sz)),
+               "hyde_backward_workspace_size")
+        self.bws = _workspace(sz.value, self.device)
+        self.sure_value = torch.zeros(1, dtype=torch.float64, device=self.device)
+
+    def forward_scaled(self, Y: torch.Tensor, scale: torch.Tensor) -> torch.Tensor:
+        Y = _cuda_f32(Y, "Y")
+        s = _scale_rows(scale, self.params.r_max, self.params.levels)
+        X = torch.empty_like(Y)
+        p, H, W = self.shape
+        _check(self.lib.hyde_hyres_denoise_scaled(
+            _ptr(Y), _ptr(X), p, H, W, ctypes.byref(self.params), _ptr(s), _ptr(self.info),
+            _ptr(self.ws), self.ws.numel(), _stream()), "hyde_hyres_denoise_scaled")
+        return X
+
+    def backward_scaled(self, Y: torch.Tensor, dX: torch.Tensor | None, scale: torch.Tensor,
+                        loss: int = 0) -> torch.Tensor:
+        """dL/dscale as float32 [r_max, levels] (loss 0: dX = dL/dX_hat;
+        loss 1: the SURE loss, value left in ``self.sure_value``)."""
+        Y = _cuda_f32(Y, "Y")
+        s = _scale_rows(scale, self.params.r_max, self.params.levels)
+        ds = torch.empty((self.params.r_max, self.params.levels), dtype=torch.float32,
+                         device=self.device)
+        p, H, W = self.shape
+        dptr = None
+        if loss == 0:
+            dX = _cuda_f32(dX, "dX")
+            dptr = _ptr(dX)
+        _check(self.lib.hyde_hyres_backward(
+            _ptr(Y), dptr, p, H, W, ctypes.byref(self.params), _ptr(s), loss, _ptr(ds),
+            _ptr(self.sure_value), _ptr(self.ws), self.ws.numel(), _ptr(self.bws),
+            self.bws.numel(), _stream()), "hyde_hyres_backward")
+        return ds
+
+
+def _pad_rows(ds: torch.Tensor, like: torch.Tensor) -> torch.Tensor:
+    out = torch.zeros_like(like)
+    out[: ds.shape[0]] = ds
+    return out
+
+
+class HyResScaledFn(torch.autograd.Function):
+    """X_hat = HyRes_s(Y): differentiable in the threshold scales only (the
+    cube is data; the rank and base threshold are stop-gradient)."""
+
+    @staticmethod
+    def forward(ctx, Y, scale, model):
+        X = model.forward_scaled(Y, scale)
+        ctx.model = model
+        ctx.save_for_backward(Y, scale)
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        Y, scale = ctx.saved_tensors
+        ds = ctx.model.backward_scaled(Y, gX.contiguous(), scale, loss=0)
+        return None, _pad_rows(ds, scale), None
+
+
+class HyResSureFn(torch.autograd.Function):
+    """SURE of the kept components with thresholds lambda* scale (a scalar,
+    float64), with its almost-everywhere gradient in the scales."""
+
+    @staticmethod
+    def forward(ctx, Y, scale, model):
+        model.forward_scaled(Y, scale)            # rank, lambda* and weights
+        ds = model.backward_scaled(Y, None, scale, loss=1)
+        ctx.save_for_backward(_pad_rows(ds, scale))
+        return model.sure_value.clone().reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        (ds,) = ctx.saved_tensors
+        return None, ds * g.to(ds.dtype), None
+
+
+def hyres_scaled(Y: torch.Tensor, scale: torch.Tensor, model: HyResGrad) -> torch.Tensor:
+    return HyResScaledFn.apply(Y, scale, model)
+
+
+def hyres_sure_loss(Y: torch.Tensor, scale: torch.Tensor, model: HyResGrad) -> torch.Tensor:
+    return HyResSureFn.apply(Y, scale, model)

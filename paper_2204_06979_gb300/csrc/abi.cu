@@ -311,7 +311,7 @@ hyde_status hyde_workspace_layout(int p, int H, int W, const hyde_hyres_params* 
 static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
                                  const hyde_hyres_params* params, hyde_hyres_info* info,
                                  void* ws, size_t ws_bytes, cudaStream_t stream,
-                                 cudaEvent_t* ev) {
+                                 cudaEvent_t* ev, const float* scale = nullptr) {
     if (!Y || !X || Y == X) return HYDE_ERR_INVALID_ARG;
     HyresLayout L;
     hyde_status st = hyres_layout(p, H, W, params, &L);
@@ -367,7 +367,8 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
                                 info, rank_dev, lam_dev, status, stream));
     HYDE_TRY(stage());
     // 9. soft threshold + inverse DWT of the kept components (into zp, H x W)
-    HYDE_TRY(launch_idwt2(coef, zp, r, L.Hp, L.Wp, H, W, lev, scratch, lam_dev, rank_dev, stream));
+    HYDE_TRY(launch_idwt2(coef, zp, r, L.Hp, L.Wp, H, W, lev, scratch, lam_dev, rank_dev, stream,
+                          scale, lev));
     HYDE_TRY(stage());
     // 10. back-projection and un-whitening
     HYDE_TRY(launch_backproject(zp, L.n, Q, p, r, L.RM, rank_dev, X, stream));
@@ -388,6 +389,91 @@ hyde_status hyde_hyres_denoise_timed(const float* Y, float* X, int p, int H, int
                                      cudaEvent_t* events) {
     if (!events) return HYDE_ERR_INVALID_ARG;
     return hyres_enqueue(Y, X, p, H, W, params, info, ws, ws_bytes, stream, events);
+}
+
+hyde_status hyde_hyres_denoise_scaled(const float* Y, float* X, int p, int H, int W,
+                                      const hyde_hyres_params* params, const float* scale,
+                                      hyde_hyres_info* info, void* ws, size_t ws_bytes,
+                                      cudaStream_t stream) {
+    if (!scale) return HYDE_ERR_INVALID_ARG;
+    return hyres_enqueue(Y, X, p, H, W, params, info, ws, ws_bytes, stream, nullptr, scale);
+}
+
+// Backward workspace: recomputed coefficients C, their adjoint dC, one padded
+// image buffer, the DWT scratch, and the (component, level) accumulators.
+struct BackLayout {
+    size_t C, dC, zp, scratch, acc, sure_acc, total;
+};
+
+static hyde_status back_layout(const HyresLayout& L, int r, int levels, BackLayout* B) {
+    Carver c;
+    BackLayout b;
+    b.acc = c.take((size_t)r * levels * sizeof(double));
+    b.sure_acc = c.take(sizeof(double));
+    b.C = c.take((size_t)r * L.N * sizeof(float));
+    b.dC = c.take((size_t)r * L.N * sizeof(float));
+    b.zp = c.take((size_t)r * L.N * sizeof(float));
+    b.scratch = c.take((size_t)r * dwt_scratch_floats(L.Hp, L.Wp) * sizeof(float));
+    b.total = c.off;
+    *B = b;
+    return HYDE_OK;
+}
+
+hyde_status hyde_backward_workspace_size(int p, int H, int W, const hyde_hyres_params* params,
+                                         size_t* bytes) {
+    if (!bytes) return HYDE_ERR_INVALID_ARG;
+    HyresLayout L;
+    hyde_status st = hyres_layout(p, H, W, params, &L);
+    if (st != HYDE_OK) return st;
+    BackLayout B;
+    back_layout(L, params->r_max, params->levels, &B);
+    *bytes = B.total;
+    return HYDE_OK;
+}
+
+hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H, int W,
+                                const hyde_hyres_params* params, const float* scale, int loss,
+                                float* dscale, double* sure_value, const void* fws,
+                                size_t fws_bytes, void* bws, size_t bws_bytes,
+                                cudaStream_t stream) {
+    if (!Y || !scale || !dscale || (loss != 0 && loss != 1)) return HYDE_ERR_INVALID_ARG;
+    if (loss == 0 && !dX) return HYDE_ERR_INVALID_ARG;
+    HyresLayout L;
+    hyde_status st = hyres_layout(p, H, W, params, &L);
+    if (st != HYDE_OK) return st;
+    BackLayout B;
+    back_layout(L, params->r_max, params->levels, &B);
+    if (!fws || !aligned(fws, kAlign) || fws_bytes < L.pub.total) return HYDE_ERR_WORKSPACE;
+    if (!bws || !aligned(bws, kAlign) || bws_bytes < B.total) return HYDE_ERR_WORKSPACE;
+    void* f = const_cast<void*>(fws);
+    const int r = params->r_max, lev = params->levels;
+    const float* P = at<float>(f, L.P);
+    const float* Q = at<float>(f, L.Q);
+    const int* rank_dev = at<int>(f, L.rank_dev);
+    const double* lam_dev = at<double>(f, L.lam_dev);
+    float* C = at<float>(bws, B.C);
+    float* dC = at<float>(bws, B.dC);
+    float* zp = at<float>(bws, B.zp);
+    float* scratch = at<float>(bws, B.scratch);
+    double* acc = at<double>(bws, B.acc);
+    double* sacc = at<double>(bws, B.sure_acc);
+#define HYDE_TRY(x) do { hyde_status s_ = (x); if (s_ != HYDE_OK) return s_; } while (0)
+    if (cudaMemsetAsync(bws, 0, B.C, stream) != cudaSuccess) return HYDE_ERR_CUDA;
+    // recompute the forward coefficients C = DWT(pad(Y P))
+    HYDE_TRY(launch_project_pad(Y, p, H, W, P, r, L.RM, zp, L.Hp, L.Wp, stream));
+    DwtSrc src{zp, L.N, L.Wp, L.Hp, L.Wp};
+    HYDE_TRY(launch_dwt2(src, C, r, L.Hp, L.Wp, lev, scratch, stream));
+    if (loss == 0) {
+        // adjoint of back-projection, crop and inverse DWT: dC = DWT(zero-embed(Q^T dX))
+        HYDE_TRY(launch_project_pad(dX, p, H, W, Q, r, L.RM, zp, L.Hp, L.Wp, stream, true));
+        HYDE_TRY(launch_dwt2(src, dC, r, L.Hp, L.Wp, lev, scratch, stream));
+    }
+    HYDE_TRY(launch_scale_grad(C, loss == 0 ? dC : nullptr, r, L.Hp, L.Wp, lev, rank_dev, lam_dev,
+                               scale, lev, loss, acc, sacc, stream));
+    HYDE_TRY(launch_scale_grad_finish(acc, r, lev, rank_dev, lam_dev, dscale, lev, loss, L.N,
+                                      sacc, sure_value, stream));
+#undef HYDE_TRY
+    return HYDE_OK;
 }
 
 int hyde_hyres_kernel_launches(const hyde_hyres_params* params) {

@@ -95,14 +95,17 @@ __device__ __forceinline__ float soft(float c, float lam) {
 __global__ void __launch_bounds__(kThreads)
 idwt_level_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
                   const float* __restrict__ coef, long long coef_bs, int coef_ld, int h,
-                  int w, const double* __restrict__ lam, const int* __restrict__ rank,
+                  int w, const double* __restrict__ lam, const float* __restrict__ scale,
+                  int scale_ld, int lev, const int* __restrict__ rank,
                   float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo) {
     __shared__ float sLL[TH + 1][TW + 2], sLH[TH + 1][TW + 2];
     __shared__ float sHL[TH + 1][TW + 2], sHH[TH + 1][TW + 2];
     __shared__ float tl[2 * TH][TW + 2], th[2 * TH][TW + 2];
     const int b = blockIdx.z;
     if (rank && b >= *rank) return;
-    const float lv = lam ? (float)(*lam) : 0.f;
+    // threshold of this level's detail bands: lambda (* scale[image][level])
+    float lv = lam ? (float)(*lam) : 0.f;
+    if (lam && scale) lv *= scale[(long long)b * scale_ld + (lev - 1)];
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     const int hh = h >> 1, wh = w >> 1;
     const float* L = llsrc + (long long)b * ll_bs;
@@ -200,7 +203,7 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
 
 hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int Wp, int H,
                          int W, int levels, float* scratch, const double* lam,
-                         const int* rank, cudaStream_t s) {
+                         const int* rank, cudaStream_t s, const float* scale, int scale_ld) {
     const long long cbs = (long long)Hp * Wp;
     for (int lev = levels; lev >= 1; --lev) {
         const int h = Hp >> (lev - 1), w = Wp >> (lev - 1);
@@ -222,7 +225,8 @@ hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int W
         }
         dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
         idwt_level_kernel<<<grid, kThreads, 0, s>>>(lp, lbs, lld, coef, cbs, Wp, h, w, lam,
-                                                    rank, op, obs, old, ho, wo);
+                                                    scale, scale_ld, lev, rank, op, obs, old,
+                                                    ho, wo);
     }
     return cuda_status(cudaGetLastError());
 }

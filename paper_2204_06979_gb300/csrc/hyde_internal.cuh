@@ -94,9 +94,11 @@ hyde_status launch_weights(const double* V, const double* sigma, int p, int r,
                            int ldw, float* P, float* Q, cudaStream_t s);
 
 // ------------------------------------------------- projection / back
+// zero_pad: the padding is zero (the transpose of cropping) instead of the
+// symmetric reflection of the image
 hyde_status launch_project_pad(const float* Y, int p, int H, int W,
                                const float* P, int r, int ldw, float* Zp,
-                               int Hp, int Wp, cudaStream_t s);
+                               int Hp, int Wp, cudaStream_t s, bool zero_pad = false);
 hyde_status launch_backproject(const float* Zh, long long n, const float* Q,
                                int p, int r_max, int ldw, const int* rank,
                                float* X, cudaStream_t s);
@@ -113,11 +115,31 @@ struct DwtSrc {
 size_t dwt_scratch_floats(int Hp, int Wp);   // per image, both ping-pong halves
 hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp,
                         int Wp, int levels, float* scratch, cudaStream_t s);
-// Synthesis with optional soft threshold of detail coefficients at *lam and
-// an optional rank limit (*rank images are processed; NULL = all).
+// Synthesis with optional soft threshold of detail coefficients at *lam
+// (times scale[image * scale_ld + level - 1] when scale != NULL) and an
+// optional rank limit (*rank images are processed; NULL = all).
 hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp,
                          int Wp, int H, int W, int levels, float* scratch,
-                         const double* lam, const int* rank, cudaStream_t s);
+                         const double* lam, const int* rank, cudaStream_t s,
+                         const float* scale = nullptr, int scale_ld = 0);
+
+// ------------------------------------------------- differentiation form
+// acc[i][l] (double, zeroed by the caller) += per-(component, level) sums over
+// the detail coefficients of components i < *rank:
+//   mode 0: dC * (-sign C) * [|C| > lam_il]         (needs dC)
+//   mode 1: 2 lam_il [|C| > lam_il]; sure_acc += -2 [|C| <= lam_il] + min(C^2, lam_il^2)
+// with lam_il = *lam * scale[i * scale_ld + l - 1].
+hyde_status launch_scale_grad(const float* C, const float* dC, int r_max, int Hp, int Wp,
+                              int levels, const int* rank, const double* lam,
+                              const float* scale, int scale_ld, int mode, double* acc,
+                              double* sure_acc, cudaStream_t s);
+// dscale[i][l] = (float)(lam * acc[i][l]) for i < rank, 0 otherwise; in mode 1
+// *sure_value = rank * N + sure_acc.
+hyde_status launch_scale_grad_finish(const double* acc, int r_max, int levels,
+                                     const int* rank, const double* lam, float* dscale,
+                                     int dscale_ld, int mode, long long N,
+                                     const double* sure_acc, double* sure_value,
+                                     cudaStream_t s);
 
 // ----------------------------------------------------------------- SURE
 struct SureBufs {

@@ -23,7 +23,7 @@ template <int RM>
 __global__ void __launch_bounds__(kThreads)
 project_pad_kernel(const float* __restrict__ Y, int p, int H, int W,
                    const float* __restrict__ P, int r, float* __restrict__ Zp, int Hp,
-                   int Wp) {
+                   int Wp, int zero_pad) {
     extern __shared__ float4 Ps4[];   // p * RM / 4
     float* Ps = reinterpret_cast<float*>(Ps4);
     for (int e = threadIdx.x; e < p * RM; e += kThreads) Ps[e] = P[e];
@@ -32,6 +32,12 @@ project_pad_kernel(const float* __restrict__ Y, int p, int H, int W,
     for (long long pix = (long long)blockIdx.x * kThreads + threadIdx.x; pix < N;
          pix += (long long)gridDim.x * kThreads) {
         int y = (int)(pix / Wp), x = (int)(pix - (long long)(pix / Wp) * Wp);
+        if (zero_pad && (y >= H || x >= W)) {
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+                if (i < r) Zp[(long long)i * N + pix] = 0.f;
+            continue;
+        }
         if (y >= H) y = 2 * H - 2 - y;
         if (x >= W) x = 2 * W - 2 - x;
         const float* yp = Y + (long long)y * W + x;
@@ -132,7 +138,8 @@ int grid_for(long long items, int per_block, int blocks_per_sm) {
 }  // namespace
 
 hyde_status launch_project_pad(const float* Y, int p, int H, int W, const float* P, int r,
-                               int ldw, float* Zp, int Hp, int Wp, cudaStream_t s) {
+                               int ldw, float* Zp, int Hp, int Wp, cudaStream_t s,
+                               bool zero_pad) {
     const long long N = (long long)Hp * Wp;
     const int grid = grid_for(N, kThreads, 8);
     const size_t smem = (size_t)p * ldw * sizeof(float);
@@ -142,7 +149,8 @@ hyde_status launch_project_pad(const float* Y, int p, int H, int W, const float*
     case RMV:                                                                                  \
         if (ensure_smem_limit((const void*)project_pad_kernel<RMV>, (int)smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                              \
-        project_pad_kernel<RMV><<<grid, kThreads, smem, s>>>(Y, p, H, W, P, r, Zp, Hp, Wp);   \
+        project_pad_kernel<RMV><<<grid, kThreads, smem, s>>>(Y, p, H, W, P, r, Zp, Hp, Wp, \
+                                                             zero_pad ? 1 : 0);                 \
         break;
         HYDE_PROJ(4) HYDE_PROJ(8) HYDE_PROJ(12) HYDE_PROJ(16)
         HYDE_PROJ(20) HYDE_PROJ(24) HYDE_PROJ(28) HYDE_PROJ(32)
