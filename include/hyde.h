@@ -279,6 +279,40 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H,
                                 size_t fws_bytes, void* bws, size_t bws_bytes,
                                 cudaStream_t stream);
 
+/* ------------------------------------------------------- sliding windows
+ * Batched form: the scene Y (float[p][H][W]) is cut into windows, each
+ * denoised with its own noise levels, subspace, rank and threshold, and X
+ * takes every pixel from the window whose core holds it. The paper denoises
+ * images too large for one pass by slicing them into tiles and reassembling
+ * the results (Sec. 2.2.2). win (HOST memory) lists the windows; the cores
+ * must tile the scene (not checked: pixels outside every core are left
+ * untouched in X). info (device, may be NULL) receives one record per
+ * window. Windows go round-robin to n_slots slots; slot s works on
+ * streams[s] (caller-created) with its own part of ws
+ * (hyde_windows_workspace_size). events holds n_slots + 1 caller-created
+ * events used to fork the slot streams from `stream` and join them back, so
+ * the call behaves as one operation on `stream` and can be captured into a
+ * single CUDA graph.
+ */
+typedef struct {
+    int y0, x0, h, w;       /* window in scene pixels                       */
+    int cy0, cx0, ch, cw;   /* its core (inside the window)                 */
+} hyde_window;
+
+hyde_status hyde_windows_workspace_size(int p, int H, int W,
+                                        const hyde_window* win, int n_win,
+                                        const hyde_hyres_params* params,
+                                        int n_slots, size_t* bytes);
+hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
+                                       int W, const hyde_window* win,
+                                       int n_win,
+                                       const hyde_hyres_params* params,
+                                       hyde_hyres_info* info, void* ws,
+                                       size_t ws_bytes,
+                                       const cudaStream_t* streams,
+                                       int n_slots, cudaEvent_t* events,
+                                       cudaStream_t stream);
+
 /* Number of kernels one hyde_hyres_denoise call launches (11 + 2 * levels;
  * the two memsets that clear the workspace header and R are not counted),
  * or -1 for bad params. */

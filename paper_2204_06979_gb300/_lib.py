@@ -26,6 +26,10 @@ class HydeParams(ctypes.Structure):
                 ("reserved", c_int * 3)]
 
 
+class HydeWindow(ctypes.Structure):
+    _fields_ = [(name, c_int) for name in ("y0", "x0", "h", "w", "cy0", "cx0", "ch", "cw")]
+
+
 class HydeWsLayout(ctypes.Structure):
     _fields_ = [(name, c_size) for name in
                 ("total", "R", "sigma", "evals", "V", "coef", "sure", "sure_inf",
@@ -68,6 +72,11 @@ SIGNATURES = {
                                              c_size_p]),
     "hyde_hyres_backward": (c_int, [c_vp, c_vp, c_int, c_int, c_int, ctypes.POINTER(HydeParams),
                                     c_vp, c_int, c_vp, c_vp, c_vp, c_size, c_vp, c_size, c_vp]),
+    "hyde_windows_workspace_size": (c_int, [c_int, c_int, c_int, c_vp, c_int,
+                                            ctypes.POINTER(HydeParams), c_int, c_size_p]),
+    "hyde_hyres_denoise_windows": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_vp, c_int,
+                                           ctypes.POINTER(HydeParams), c_vp, c_vp, c_size, c_vp,
+                                           c_int, c_vp, c_vp]),
 }
 
 N_STAGES = 8

@@ -343,3 +343,67 @@ def hyres_scaled(Y: torch.Tensor, scale: torch.Tensor, model: HyResGrad) -> torc
 
 def hyres_sure_loss(Y: torch.Tensor, scale: torch.Tensor, model: HyResGrad) -> torch.Tensor:
     return HyResSureFn.apply(Y, scale, model)
+
+
+# ------------------------------------------------------- sliding windows
+
+class HyResWindows:
+    """Sliding-window HyRes over a scene of fixed shape and window table
+    (``int32[n][8]``: window y0, x0, h, w and core y0, x0, h, w). Owns the
+    slot streams, fork/join events, workspace and per-window info records.
+    ``__call__`` enqueues the whole scene on the current stream;
+    ``capture``/``replay`` record it once into a CUDA graph and relaunch it."""
+
+    def __init__(self, p, H, W, table, levels, r_max, n_lambda=64, n_slots=64, device="cuda"):
+        from ._lib import HydeWindow
+        self.lib = _lib.load()
+        self.shape = (p, H, W)
+        self.params = params(levels, r_max, n_lambda)
+        self.device = torch.device(device)
+        rows = [tuple(int(v) for v in r) for r in table]
+        self.n_win = len(rows)
+        self.win = (HydeWindow * self.n_win)(*[HydeWindow(*r) for r in rows])
+        self.n_slots = min(n_slots, self.n_win)
+        sz = ctypes.c_size_t()
+        _check(self.lib.hyde_windows_workspace_size(p, H, W, self.win, self.n_win,
+                                                    ctypes.byref(self.params), self.n_slots,
+                                                    ctypes.byref(sz)),
+               "hyde_windows_workspace_size")
+        self.ws = _workspace(sz.value, self.device)
+        self.info = torch.zeros(self.n_win * INFO_BYTES, dtype=torch.uint8, device=self.device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.n_slots)]
+        self.events = [torch.cuda.Event() for _ in range(self.n_slots + 1)]
+        for e in self.events:      # torch creates the CUDA event on first record
+            e.record(torch.cuda.current_stream(self.device))
+        torch.cuda.synchronize(self.device)
+        self._streams_arr = (ctypes.c_void_p * self.n_slots)(*[s.cuda_stream for s in self.streams])
+        self._events_arr = (ctypes.c_void_p * (self.n_slots + 1))(*[e.cuda_event for e in self.events])
+        self.graph = None
+
+    def __call__(self, Y: torch.Tensor, X: torch.Tensor | None = None) -> torch.Tensor:
+        Y = _cuda_f32(Y, "Y")
+        if tuple(Y.shape) != self.shape:
+            raise ValueError(f"expected a scene of shape {self.shape}")
+        if X is None:
+            X = torch.empty_like(Y)
+        p, H, W = self.shape
+        _check(self.lib.hyde_hyres_denoise_windows(
+            _ptr(Y), _ptr(X), p, H, W, self.win, self.n_win, ctypes.byref(self.params),
+            _ptr(self.info), _ptr(self.ws), self.ws.numel(), self._streams_arr, self.n_slots,
+            self._events_arr, _stream()), "hyde_hyres_denoise_windows")
+        return X
+
+    def capture(self, Y: torch.Tensor, X: torch.Tensor) -> None:
+        """Record one scene denoise (reading Y, writing X) into a CUDA graph."""
+        self(Y, X)                 # first call: function attributes, caches
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            self(Y, X)
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+    def infos(self) -> list[dict]:
+        raw = self.info.cpu()
+        return [parse_info(raw[k * INFO_BYTES:(k + 1) * INFO_BYTES]) for k in range(self.n_win)]

@@ -476,6 +476,101 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H, i
     return HYDE_OK;
 }
 
+// ------------------------------------------------------- sliding windows
+static hyde_status window_valid(const hyde_window& wn, int H, int W) {
+    if (wn.h < 1 || wn.w < 1 || wn.y0 < 0 || wn.x0 < 0 || wn.y0 + wn.h > H || wn.x0 + wn.w > W)
+        return HYDE_ERR_SHAPE;
+    if (wn.ch < 1 || wn.cw < 1 || wn.cy0 < wn.y0 || wn.cx0 < wn.x0 ||
+        wn.cy0 + wn.ch > wn.y0 + wn.h || wn.cx0 + wn.cw > wn.x0 + wn.w)
+        return HYDE_ERR_SHAPE;
+    return HYDE_OK;
+}
+
+struct SlotLayout {
+    size_t cube_in, cube_out, hyres, stride;
+};
+
+static hyde_status slot_layout(int p, const hyde_window* win, int n_win,
+                               const hyde_hyres_params* params, SlotLayout* S) {
+    size_t max_cube = 0, max_ws = 0;
+    for (int k = 0; k < n_win; ++k) {
+        HyresLayout L;
+        hyde_status st = hyres_layout(p, win[k].h, win[k].w, params, &L);
+        if (st != HYDE_OK) return st;
+        if (L.pub.total > max_ws) max_ws = L.pub.total;
+        const size_t cube = (size_t)p * win[k].h * win[k].w * sizeof(float);
+        if (cube > max_cube) max_cube = cube;
+    }
+    Carver c;
+    SlotLayout s;
+    s.cube_in = c.take(max_cube);
+    s.cube_out = c.take(max_cube);
+    s.hyres = c.take(max_ws);
+    s.stride = c.off;
+    *S = s;
+    return HYDE_OK;
+}
+
+hyde_status hyde_windows_workspace_size(int p, int H, int W, const hyde_window* win, int n_win,
+                                        const hyde_hyres_params* params, int n_slots,
+                                        size_t* bytes) {
+    if (!win || !bytes || n_win < 1 || n_slots < 1) return HYDE_ERR_INVALID_ARG;
+    for (int k = 0; k < n_win; ++k) {
+        hyde_status st = window_valid(win[k], H, W);
+        if (st != HYDE_OK) return st;
+    }
+    SlotLayout S;
+    hyde_status st = slot_layout(p, win, n_win, params, &S);
+    if (st != HYDE_OK) return st;
+    const int slots = n_slots < n_win ? n_slots : n_win;
+    *bytes = S.stride * (size_t)slots;
+    return HYDE_OK;
+}
+
+hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H, int W,
+                                       const hyde_window* win, int n_win,
+                                       const hyde_hyres_params* params,
+                                       hyde_hyres_info* info, void* ws, size_t ws_bytes,
+                                       const cudaStream_t* streams, int n_slots,
+                                       cudaEvent_t* events, cudaStream_t stream) {
+    if (!Y || !X || Y == X || !win || !streams || !events || n_win < 1 || n_slots < 1)
+        return HYDE_ERR_INVALID_ARG;
+    size_t need = 0;
+    hyde_status st = hyde_windows_workspace_size(p, H, W, win, n_win, params, n_slots, &need);
+    if (st != HYDE_OK) return st;
+    if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return HYDE_ERR_WORKSPACE;
+    SlotLayout S;
+    slot_layout(p, win, n_win, params, &S);
+    const int slots = n_slots < n_win ? n_slots : n_win;
+    // fork: every slot stream waits for the work already on the caller's stream
+    if (cudaEventRecord(events[slots], stream) != cudaSuccess) return HYDE_ERR_CUDA;
+    for (int s = 0; s < slots; ++s)
+        if (cudaStreamWaitEvent(streams[s], events[slots], 0) != cudaSuccess) return HYDE_ERR_CUDA;
+    for (int k = 0; k < n_win; ++k) {
+        const int s = k % slots;
+        cudaStream_t ss = streams[s];
+        char* base = reinterpret_cast<char*>(ws) + S.stride * (size_t)s;
+        float* cin = reinterpret_cast<float*>(base + S.cube_in);
+        float* cout = reinterpret_cast<float*>(base + S.cube_out);
+        void* hws = base + S.hyres;
+        const hyde_window& wn = win[k];
+        st = launch_gather_window(Y, H, W, wn.y0, wn.x0, wn.h, wn.w, p, cin, ss);
+        if (st != HYDE_OK) return st;
+        st = hyres_enqueue(cin, cout, p, wn.h, wn.w, params, info ? info + k : nullptr, hws,
+                           S.stride - S.hyres, ss, nullptr);
+        if (st != HYDE_OK) return st;
+        st = launch_scatter_core(cout, wn.h, wn.w, wn.y0, wn.x0, wn.cy0, wn.cx0, wn.ch, wn.cw, p,
+                                 H, W, X, ss);
+        if (st != HYDE_OK) return st;
+    }
+    // join
+    for (int s = 0; s < slots; ++s) {
+        if (cudaEventRecord(events[s], streams[s]) != cudaSuccess) return HYDE_ERR_CUDA;
+        if (cudaStreamWaitEvent(stream, events[s], 0) != cudaSuccess) return HYDE_ERR_CUDA;
+    }
+    return HYDE_OK;
+}
+
 int hyde_hyres_kernel_launches(const hyde_hyres_params* params) {
     if (!params || params->levels < 1 || params->levels > kMaxLevels) return -1;
     // gram 2, noise 2, eig 1, weights 1, projection 1, DWT L, SURE 3, IDWT L, back 1

@@ -141,6 +141,13 @@ hyde_status launch_scale_grad_finish(const double* acc, int r_max, int levels,
                                      const double* sure_acc, double* sure_value,
                                      cudaStream_t s);
 
+// ------------------------------------------------------- sliding windows
+hyde_status launch_gather_window(const float* Y, int H, int W, int y0, int x0, int h, int w,
+                                 int p, float* out, cudaStream_t s);
+hyde_status launch_scatter_core(const float* cube, int h, int w, int y0, int x0, int cy0,
+                                int cx0, int ch, int cw, int p, int H, int W, float* X,
+                                cudaStream_t s);
+
 // ----------------------------------------------------------------- SURE
 struct SureBufs {
     unsigned int* counts;   // [batch][K]

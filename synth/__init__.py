@@ -7,5 +7,5 @@ Gram, no wavelet, no threshold), so both the CUDA path and the FP64 oracle can
 consume its output without sharing any of the method's code.
 """
 
-from .cube import make_cube, cube_config, CONFIGS  # noqa: F401
+from .cube import make_cube, make_scene, cube_config, CONFIGS  # noqa: F401
 from .windows import make_window_table  # noqa: F401

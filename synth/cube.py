@@ -113,8 +113,13 @@ def make_cube(H: int, W: int, p: int, m: int = 4, snr_db: float = 10.0,
     E = _endmembers(rng, m, p)
     A = _abundances(rng, m, H, W)
     n = H * W
-    # clean cube, band-major: X[b] = sum_j E[j, b] * A[j]
-    X = (E.T @ A.reshape(m, n)).astype(np.float32).reshape(p, H, W)
+    # clean cube, band-major: X[b] = sum_j E[j, b] * A[j] (float64 for
+    # cubes up to ~10^8 voxels, float32 beyond to bound host memory)
+    if p * n <= 10 ** 8:
+        X = (E.T @ A.reshape(m, n)).astype(np.float32).reshape(p, H, W)
+    else:
+        X = (E.T.astype(np.float32) @ A.reshape(m, n).astype(np.float32)).reshape(p, H, W)
+    del A
     u = rng.uniform(1.0, spread, size=p)
     sig_pow = float(np.sum(X.astype(np.float64) ** 2))
     s2 = sig_pow / (n * float(np.sum(u ** 2)) * 10.0 ** (snr_db / 10.0))
@@ -128,3 +133,21 @@ def make_cube(H: int, W: int, p: int, m: int = 4, snr_db: float = 10.0,
     return dict(Y=np.ascontiguousarray(Y, dtype=np.float32),
                 X=np.ascontiguousarray(X, dtype=np.float32),
                 sigma=sigma, E=E)
+
+
+def make_scene(H: int, W: int, p: int, table: np.ndarray, m: int = 12,
+               snr_range: tuple = (5.0, 20.0), seed: int = 4) -> dict:
+    """A scene for the sliding-window form: ``make_cube`` at 10 dB whole-cube
+    SNR, with the noise of every window core scaled so that its own SNR is
+    about ``U[snr_range]`` dB (the factor ``10^((10 - SNR_core) / 20)``
+    multiplies sigma_b over the core). Returns the cube dict plus
+    ``core_snr_db``."""
+    rng = np.random.default_rng(seed + 1000)
+    snr = rng.uniform(snr_range[0], snr_range[1], size=len(table))
+    sigma_map = np.ones((H, W), dtype=np.float32)
+    for (row, s_db) in zip(table, snr):
+        cy, cx, ch, cw = (int(v) for v in row[4:8])
+        sigma_map[cy:cy + ch, cx:cx + cw] = 10.0 ** ((10.0 - s_db) / 20.0)
+    cube = make_cube(H, W, p, m=m, snr_db=10.0, seed=seed, sigma_map=sigma_map)
+    cube["core_snr_db"] = snr
+    return cube
