@@ -56,7 +56,7 @@ def _config(n_gpus: int) -> dict:
                      f"(Houston-2013 shape, {w['m']} endmembers, SNR {w['snr_db']:.0f} dB), db2 "
                      f"L={w['levels']}, r<={w['r_max']}, K={w['n_lambda']}"),
         "H": w["H"], "W": w["W"], "p": w["p"], "levels": w["levels"], "r_max": w["r_max"],
-        "n_lambda": w["n_lambda"], "precision": "fp32",
+        "n_lambda": w["n_lambda"], "precision": "fp32",  # replaced for --precision bf16x3
         "l2": "input 383 MB > L2, and a 256 MB buffer is written between timed steps",
         "parallelism": f"replicas x{n_gpus}",
     }
@@ -191,7 +191,8 @@ def run_gb300(args) -> None:
     voxels = p * n
     Yd = torch.from_numpy(cube["Y"]).to(dev)
     Xd = torch.empty_like(Yd)
-    h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev)
+    prec = api.PREC_BF16X3 if args.precision == "bf16x3" else api.PREC_FP32
+    h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev, precision=prec)
     lib = _lib.load()
     launches_per_step = lib.hyde_hyres_kernel_launches(h.params)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -258,7 +259,16 @@ def run_gb300(args) -> None:
     peaks = _measured_peaks()
     sbytes = _stage_bytes(r_star)
     dominant = max(stage_avg, key=stage_avg.get)
-    if dominant == "gram":
+    if dominant == "gram" and args.precision == "bf16x3":
+        flops = 3 * 2 * n * p * p   # three bf16 products per entry (hi hi, hi lo, lo hi)
+        tc_peak = peaks["bf16_tflops"]
+        achieved = flops / (stage_avg["gram"] / 1e3) / 1e12
+        roofline = {"kernel": "gram_tc (tcgen05 split-BF16) + reduce", "bound": "tensor",
+                    "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                    "frac": achieved / tc_peak, "traffic": None,
+                    "peak_source": peaks["source"] + " bf16 dense (burst)",
+                    "algorithmic": f"{flops:.4g} flop per launch (3 products of 2np^2)"}
+    elif dominant == "gram":
         flops = n * p * (p + 1)   # the symmetric product computed: n p (p+1)/2 FMAs
         achieved = flops / (stage_avg["gram"] / 1e3) / 1e12
         roofline = {"kernel": "gram (gram_partial + gram_reduce)", "bound": "alu",
@@ -317,11 +327,16 @@ def run_gb300(args) -> None:
                "kind": "oracle", "sample": s["sample"]}
 
     if rank == 0:
+        cfg = _config(world)
+        if args.precision == "bf16x3":
+            cfg["precision"] = "bf16x3 (Gram on tcgen05, split-BF16 compensated)"
+            cfg["workload"] += ", precision form"
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic", "config": _config(world),
+            "dtype": "f32" if args.precision == "fp32" else "bf16x3+f32",
+            "data": "synthetic", "config": cfg,
             "roofline": roofline,
             "stages": hbm_stages | {k: {"ms": round(v, 4)} for k, v in stage_avg.items()
                                     if k not in hbm_stages},
@@ -488,6 +503,8 @@ def main() -> None:
     ap.add_argument("--form", choices=("plain", "windows", "diff"), default="plain",
                     help="plain: the headline workload; windows / diff: secondary forms")
     ap.add_argument("--slots", type=int, default=64, help="window slots (--form windows)")
+    ap.add_argument("--precision", choices=("fp32", "bf16x3"), default="fp32",
+                    help="fp32: plain form (headline); bf16x3: Gram on the tensor cores")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3

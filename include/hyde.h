@@ -58,8 +58,12 @@ typedef enum {
 
 typedef enum {
     HYDE_PREC_FP32 = 0,    /* plain FP32 SIMT arithmetic                      */
-    HYDE_PREC_TF32X3 = 1,  /* reserved: split-TF32 tensor-core contractions   */
-    HYDE_PREC_BF16X3 = 2   /* reserved: split-BF16 tensor-core contractions   */
+    HYDE_PREC_TF32X3 = 1,  /* reserved (rejected): split-TF32 contractions    */
+    HYDE_PREC_BF16X3 = 2   /* Gram matrix on the tensor cores: each float is
+                              split into bf16 hi + lo and y_a y_b is taken as
+                              hi hi + hi lo + lo hi (tcgen05.mma, FP32
+                              accumulation in TMEM, double across SMs); the
+                              other stages as in HYDE_PREC_FP32             */
 } hyde_precision;
 
 /* Parameters of one HyRes run. */
@@ -110,7 +114,8 @@ int hyde_version(void);
  * pixel-by-band matrix; the spectral statistics of the low-rank model
  * (Sec. 2.1, "low-rank"). Y is float[p][n] band-major (ld = n); R is
  * double[p][p] row-major, full symmetric. Per-block float partial sums are
- * combined in double. precision must be HYDE_PREC_FP32.
+ * combined in double. precision: HYDE_PREC_FP32 (FP32 FMA) or
+ * HYDE_PREC_BF16X3 (split-BF16 products on the tensor cores).
  */
 hyde_status hyde_gram_workspace_size(int p, long long n, int precision,
                                      size_t* bytes);

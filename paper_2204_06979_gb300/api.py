@@ -17,6 +17,7 @@ from ._lib import HydeParams, HydeWsLayout, INFO_BYTES, INFO_FORMAT
 
 HYDE_OK = 0
 PREC_FP32 = 0
+PREC_BF16X3 = 2
 
 
 class HydeError(RuntimeError):
@@ -73,17 +74,18 @@ def version() -> int:
 
 # ------------------------------------------------------------------ stages
 
-def gram(Y: torch.Tensor) -> torch.Tensor:
-    """R = Y^T Y of a cube ``Y[p, ...]`` (float32, CUDA) as float64 ``[p, p]``."""
+def gram(Y: torch.Tensor, precision: int = PREC_FP32) -> torch.Tensor:
+    """R = Y^T Y of a cube ``Y[p, ...]`` (float32, CUDA) as float64 ``[p, p]``
+    (``precision`` PREC_FP32, or PREC_BF16X3 for the tensor-core form)."""
     lib = _lib.load()
     Y = _cuda_f32(Y, "Y")
     p = Y.shape[0]
     n = Y.numel() // p
     sz = ctypes.c_size_t()
-    _check(lib.hyde_gram_workspace_size(p, n, PREC_FP32, ctypes.byref(sz)), "hyde_gram_workspace_size")
+    _check(lib.hyde_gram_workspace_size(p, n, precision, ctypes.byref(sz)), "hyde_gram_workspace_size")
     ws = _workspace(sz.value, Y.device)
     R = torch.empty((p, p), dtype=torch.float64, device=Y.device)
-    _check(lib.hyde_gram(_ptr(Y), p, n, PREC_FP32, _ptr(R), _ptr(ws), ws.numel(), _stream()),
+    _check(lib.hyde_gram(_ptr(Y), p, n, precision, _ptr(R), _ptr(ws), ws.numel(), _stream()),
            "hyde_gram")
     return R
 
@@ -181,10 +183,10 @@ class HyRes:
     stream."""
 
     def __init__(self, p: int, H: int, W: int, levels: int, r_max: int, n_lambda: int = 64,
-                 device="cuda"):
+                 device="cuda", precision: int = PREC_FP32):
         self.lib = _lib.load()
         self.shape = (p, H, W)
-        self.params = params(levels, r_max, n_lambda)
+        self.params = params(levels, r_max, n_lambda, precision)
         sz = ctypes.c_size_t()
         _check(self.lib.hyde_workspace_size(p, H, W, ctypes.byref(self.params), ctypes.byref(sz)),
                "hyde_workspace_size")
@@ -233,11 +235,12 @@ class HyRes:
         )
 
 
-def hyres_denoise(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64):
+def hyres_denoise(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64,
+                  precision: int = PREC_FP32):
     """One-shot HyRes on ``Y[p, H, W]``; returns ``(X, info dict)``
     (synchronises the current stream to read the info record)."""
     p, H, W = Y.shape
-    h = HyRes(p, H, W, levels, r_max, n_lambda, device=Y.device)
+    h = HyRes(p, H, W, levels, r_max, n_lambda, device=Y.device, precision=precision)
     X = h(Y)
     return X, h.result_info()
 

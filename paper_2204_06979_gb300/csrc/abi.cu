@@ -75,7 +75,9 @@ struct HyresLayout {
 
 hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, HyresLayout* L) {
     if (!pr) return HYDE_ERR_INVALID_ARG;
-    if (pr->wavelet != 2 || pr->precision != HYDE_PREC_FP32) return HYDE_ERR_INVALID_ARG;
+    if (pr->wavelet != 2) return HYDE_ERR_INVALID_ARG;
+    if (pr->precision != HYDE_PREC_FP32 && pr->precision != HYDE_PREC_BF16X3)
+        return HYDE_ERR_INVALID_ARG;
     if (pr->reserved[0] || pr->reserved[1] || pr->reserved[2]) return HYDE_ERR_INVALID_ARG;
     if (p < 2 || p > kMaxBandsGram) return HYDE_ERR_SHAPE;
     if (pr->r_max < 1 || pr->r_max > kMaxRank || pr->r_max > p) return HYDE_ERR_SHAPE;
@@ -91,6 +93,12 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.N = (long long)Hp * Wp; l.n = n;
     hyde_status st = gram_plan(p, n, &l.gram);
     if (st != HYDE_OK) return st;
+    if (pr->precision == HYDE_PREC_BF16X3) {
+        size_t tcb = 0;
+        st = gram_tc_partial_bytes(p, &tcb);
+        if (st != HYDE_OK) return st;
+        l.gram.partial_bytes = tcb;
+    }
     const int r = pr->r_max, K = pr->n_lambda;
     Carver c;
     memset(&l.pub, 0, sizeof(l.pub));
@@ -153,6 +161,14 @@ int hyde_version(void) { return 100; }
 // ------------------------------------------------------------------ Gram
 hyde_status hyde_gram_workspace_size(int p, long long n, int precision, size_t* bytes) {
     if (!bytes) return HYDE_ERR_INVALID_ARG;
+    if (precision == HYDE_PREC_BF16X3) {
+        if (n < 1) return HYDE_ERR_SHAPE;
+        size_t b = 0;
+        hyde_status st = gram_tc_partial_bytes(p, &b);
+        if (st != HYDE_OK) return st;
+        *bytes = align_up(b, kAlign);
+        return HYDE_OK;
+    }
     if (precision != HYDE_PREC_FP32) return HYDE_ERR_INVALID_ARG;
     GramPlan g;
     hyde_status st = gram_plan(p, n, &g);
@@ -164,11 +180,14 @@ hyde_status hyde_gram_workspace_size(int p, long long n, int precision, size_t* 
 hyde_status hyde_gram(const float* Y, int p, long long n, int precision, double* R, void* ws,
                       size_t ws_bytes, cudaStream_t stream) {
     if (!Y || !R) return HYDE_ERR_INVALID_ARG;
-    if (precision != HYDE_PREC_FP32) return HYDE_ERR_INVALID_ARG;
-    GramPlan g;
-    hyde_status st = gram_plan(p, n, &g);
+    size_t need = 0;
+    hyde_status st = hyde_gram_workspace_size(p, n, precision, &need);
     if (st != HYDE_OK) return st;
-    if (!ws || !aligned(ws, kAlign) || ws_bytes < g.partial_bytes) return HYDE_ERR_WORKSPACE;
+    if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return HYDE_ERR_WORKSPACE;
+    if (precision == HYDE_PREC_BF16X3)
+        return launch_gram_tc(Y, p, n, reinterpret_cast<float*>(ws), R, nullptr, stream);
+    GramPlan g;
+    gram_plan(p, n, &g);
     return launch_gram(Y, p, n, g, reinterpret_cast<float*>(ws), R, nullptr, stream);
 }
 
@@ -341,8 +360,11 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     if (cudaMemsetAsync(at<char>(ws, L.zero_begin), 0, L.zero_end - L.zero_begin, stream) !=
         cudaSuccess)
         return HYDE_ERR_CUDA;
-    // 1. Gram matrix
-    HYDE_TRY(launch_gram(Y, p, L.n, L.gram, at<float>(ws, L.partials), R, status, stream));
+    // 1. Gram matrix (float SIMT, or split-BF16 on the tensor cores)
+    if (params->precision == HYDE_PREC_BF16X3)
+        HYDE_TRY(launch_gram_tc(Y, p, L.n, at<float>(ws, L.partials), R, status, stream));
+    else
+        HYDE_TRY(launch_gram(Y, p, L.n, L.gram, at<float>(ws, L.partials), R, status, stream));
     HYDE_TRY(stage());
     // 2. noise level by regression
     HYDE_TRY(launch_noise_from_gram(R, p, L.n, sigma, at<void>(ws, L.noise), status, stream));

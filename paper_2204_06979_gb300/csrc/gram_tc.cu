@@ -1,0 +1,339 @@
+// Gram matrix R = Y^T Y on the 5th-generation tensor cores (precision form of
+// HyRes, arXiv 2204.06979 Sec. 2.1 "low-rank"; the paper runs in FP32 and
+// compares against FP64 references, Sec. 3).
+//
+// Split-BF16 compensated product: every float y is split into
+// hi = bf16(y) and lo = bf16(y - hi); y_a y_b is taken as
+// hi_a hi_b + hi_a lo_b + lo_a hi_b (the lo*lo term, ~2^-18 relative, is
+// dropped), three tcgen05.mma kind::f16 (BF16 x BF16 -> FP32) per K step with
+// the accumulator in TMEM.
+//
+// One CTA per SM walks a contiguous range of 64-pixel chunks. Per chunk all
+// 8 warps load one band row each (a warp reads 64 consecutive pixels of one
+// band), split it and store hi and lo into the 128-byte-swizzled K-major
+// layout the UMMA shared-memory descriptors expect; one thread then issues
+// the MMAs of the chunk and commits them to the chunk's stage mbarrier, and
+// the stage is refilled only after that barrier flips. Rows of the
+// accumulator: bands [0, 128) (M-tile 0, all N = Np columns) and, for
+// p > 128, bands [Np - 128, Np) against columns [128, Np) (M-tile 1). Each
+// CTA writes its float partial; a second kernel sums them in double.
+//
+// Every wait on an mbarrier is bounded in time (a status flag is set and the
+// kernel winds down: it waits, again bounded, for its MMAs in flight and
+// frees its TMEM).
+#include <cuda_bf16.h>
+
+#include "hyde_internal.cuh"
+
+namespace hyde {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcMaxStages = 4;
+constexpr int kChunk = 64;                      // pixels per chunk = one 128 B row of bf16
+constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// K-major operand, 128-byte swizzle, 8-row atoms of 1024 bytes (SBO = 1024).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // SWIZZLE_128B
+    return d;
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1);
+    v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+    v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5);
+    v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b, uint32_t* lo_out) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+    const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+    *lo_out = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+    return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+}
+
+// byte offset of the 4-byte pair (elements 2*lane, 2*lane+1) of row `row`
+// in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw128_offset(int row, int lane) {
+    const int r = row & 7, atom = row >> 3, c = lane >> 2;
+    return (uint32_t)(atom * 1024 + r * 128 + ((c ^ r) << 4) + ((lane & 3) << 2));
+}
+
+struct TcPlan {
+    int Np;        // rows in shared memory (p rounded up to 16, at least 128)
+    int nmt;       // M tiles (1 or 2)
+    int m1_row0;   // first band of M-tile 1
+    int n1;        // columns of M-tile 1 (bands [128, Np))
+    int d1_col;    // TMEM column of M-tile 1
+    int tmem_cols; // allocated TMEM columns
+    int stages;    // shared-memory stages (<= kTcMaxStages)
+    size_t stage_bytes, smem;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
+               long long chunks_per_cta, float* __restrict__ partials, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t mbar[kTcMaxStages];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // 1024-byte aligned stage area (the swizzle atoms must not straddle)
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t half = (uint32_t)P.Np * 128u;   // hi tile, then lo tile
+
+    // zero every stage once: rows p..Np-1 stay zero
+    const int S = P.stages;
+    for (size_t e = tid; e < (size_t)S * P.stage_bytes / 16; e += kTcThreads)
+        reinterpret_cast<uint4*>(gbase)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(smem_u32(&mbar[q]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_s)),
+                     "r"((uint32_t)P.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    const long long nchunks = (n + kChunk - 1) / kChunk;
+    const long long c0 = (long long)blockIdx.x * chunks_per_cta;
+    const long long c1 = min(c0 + chunks_per_cta, nchunks);
+    const long long iters = c1 > c0 ? c1 - c0 : 0;
+    const uint32_t id0 = idesc_bf16(128, P.Np);
+    const uint32_t id1 = idesc_bf16(128, P.n1 > 0 ? P.n1 : 16);
+
+    long long issued = 0;   // iterations whose MMAs were committed
+    for (long long it = 0; it < iters; ++it) {
+        const int s = (int)(it % S);
+        const uint32_t sbase = base + (uint32_t)s * (uint32_t)P.stage_bytes;
+        if (it >= S) {
+            // the MMAs that last read this stage (iteration it - S) are done
+            const uint32_t par = (uint32_t)((it / S - 1) & 1);
+            if (!mbar_wait_bounded(smem_u32(&mbar[s]), par)) atomicExch(&abort_s, 1);
+        }
+        __syncthreads();
+        if (abort_s) break;
+        const long long pix = (c0 + it) * kChunk + 2 * lane;
+        uint8_t* st = gbase + (sbase - base);
+        for (int b = warp; b < p; b += kTcThreads / 32) {
+            const float* yr = Y + (long long)b * n;
+            const float v0 = pix < n ? __ldg(yr + pix) : 0.f;
+            const float v1 = pix + 1 < n ? __ldg(yr + pix + 1) : 0.f;
+            uint32_t lo;
+            const uint32_t hi = pack_bf16(v0, v1, &lo);
+            const uint32_t off = sw128_offset(b, lane);
+            *reinterpret_cast<uint32_t*>(st + off) = hi;
+            *reinterpret_cast<uint32_t*>(st + half + off) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t hi0 = sbase, lo0 = sbase + half;
+#pragma unroll
+            for (int kk = 0; kk < kChunk / 16; ++kk) {
+                const uint32_t ko = (uint32_t)kk * 32u;   // 16 bf16 along K
+                const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
+                // M-tile 0: bands [0,128) x all Np columns
+                umma_bf16(tmem, sw128_desc(hi0 + ko), sw128_desc(hi0 + ko), id0, acc0);
+                umma_bf16(tmem, sw128_desc(hi0 + ko), sw128_desc(lo0 + ko), id0, 1u);
+                umma_bf16(tmem, sw128_desc(lo0 + ko), sw128_desc(hi0 + ko), id0, 1u);
+                if (P.nmt == 2) {
+                    // M-tile 1: bands [Np-128, Np) x columns [128, Np)
+                    const uint32_t ao = (uint32_t)P.m1_row0 * 128u, bo = 128u * 128u;
+                    const uint32_t d1 = tmem + (uint32_t)P.d1_col;
+                    umma_bf16(d1, sw128_desc(hi0 + ao + ko), sw128_desc(hi0 + bo + ko), id1, acc0);
+                    umma_bf16(d1, sw128_desc(hi0 + ao + ko), sw128_desc(lo0 + bo + ko), id1, 1u);
+                    umma_bf16(d1, sw128_desc(lo0 + ao + ko), sw128_desc(hi0 + bo + ko), id1, 1u);
+                }
+            }
+            umma_commit(smem_u32(&mbar[s]));
+        }
+        issued = it + 1;
+    }
+    // drain: wait for the commits still outstanding (bounded)
+    {
+        const long long first = issued > S ? issued - S : 0;
+        for (long long it = first; it < issued; ++it) {
+            const int s = (int)(it % S);
+            const uint32_t par = (uint32_t)((it / S) & 1);
+            if (!mbar_wait_bounded(smem_u32(&mbar[s]), par)) atomicExch(&abort_s, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (abort_s && tid == 0) set_status(status, HYDE_ERR_TIMEOUT);
+
+    // epilogue: warp w % 4 reads TMEM lanes 32 (w % 4) .. + 31
+    float* out = partials + (long long)blockIdx.x * p * p;
+    const int quad = warp & 3;
+    const uint32_t lane_addr = (uint32_t)(32 * quad) << 16;
+    if (warp < 4) {
+        const int row = 32 * quad + lane;           // band of M-tile 0
+        for (int j = 0; j < P.Np; j += 8) {
+            float v[8];
+            if (iters > 0 && !abort_s) tmem_ld8(tmem + lane_addr + (uint32_t)j, v);
+            else for (int q = 0; q < 8; ++q) v[q] = 0.f;
+            if (row < p)
+                for (int q = 0; q < 8; ++q)
+                    if (j + q < p) out[(long long)row * p + j + q] = v[q];
+        }
+    } else if (P.nmt == 2) {
+        const int row = P.m1_row0 + 32 * quad + lane;   // band of M-tile 1
+        for (int j = 0; j < P.n1; j += 8) {
+            float v[8];
+            if (iters > 0 && !abort_s) tmem_ld8(tmem + lane_addr + (uint32_t)(P.d1_col + j), v);
+            else for (int q = 0; q < 8; ++q) v[q] = 0.f;
+            if (row >= 128 && row < p)
+                for (int q = 0; q < 8; ++q)
+                    if (128 + j + q < p) out[(long long)row * p + 128 + j + q] = v[q];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)P.tmem_cols));
+    }
+}
+
+// R[i][j] = R[j][i] = sum over CTAs of the partial (i <= j): rows < 128 come
+// from M-tile 0, rows >= 128 (then j >= 128) from M-tile 1.
+__global__ void gram_tc_reduce_kernel(const float* __restrict__ partials, int nblocks, int p,
+                                      double* __restrict__ R, int* status) {
+    const long long tot = (long long)p * p;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / p), j = (int)(e % p);
+        if (j < i) continue;
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += (double)partials[(long long)b * tot + e];
+        if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
+        R[(long long)i * p + j] = s;
+        R[(long long)j * p + i] = s;
+    }
+}
+
+TcPlan tc_plan(int p) {
+    TcPlan P;
+    int np16 = (p + 15) / 16 * 16;
+    P.Np = np16 < 128 ? 128 : np16;
+    P.nmt = P.Np > 128 ? 2 : 1;
+    P.m1_row0 = P.Np - 128;
+    P.n1 = P.nmt == 2 ? P.Np - 128 : 0;
+    P.d1_col = (P.Np + 31) / 32 * 32;
+    const int cols = P.d1_col + P.n1;
+    P.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+    P.stage_bytes = (size_t)P.Np * 128 * 2;
+    const size_t room = 227 * 1024 - 1024 - 256;   // alignment slack, static smem
+    P.stages = (int)(room / P.stage_bytes);
+    if (P.stages > kTcMaxStages) P.stages = kTcMaxStages;
+    P.smem = (size_t)P.stages * P.stage_bytes + 1024;
+    return P;
+}
+
+}  // namespace
+
+hyde_status gram_tc_partial_bytes(int p, size_t* bytes) {
+    if (p < 1 || p > kMaxBandsGram) return HYDE_ERR_SHAPE;
+    const int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    *bytes = (size_t)sms * p * p * sizeof(float);
+    return HYDE_OK;
+}
+
+hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, double* R,
+                           int* status, cudaStream_t s) {
+    if (p < 1 || p > kMaxBandsGram || n < 1) return HYDE_ERR_SHAPE;
+    const TcPlan P = tc_plan(p);
+    if (P.stages < 2 || P.smem > 227 * 1024 || P.tmem_cols > 512) return HYDE_ERR_SHAPE;
+    const int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    if (ensure_smem_limit((const void*)gram_tc_kernel, (int)P.smem) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    const long long nchunks = (n + kChunk - 1) / kChunk;
+    const int blocks = sms;
+    const long long per = (nchunks + blocks - 1) / blocks;
+    gram_tc_kernel<<<blocks, kTcThreads, P.smem, s>>>(Y, p, n, P, per, partials, status);
+    gram_tc_reduce_kernel<<<(p * p + 255) / 256, 256, 0, s>>>(partials, blocks, p, R, status);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace hyde

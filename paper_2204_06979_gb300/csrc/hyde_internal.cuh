@@ -78,6 +78,12 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& plan
                         float* partials, double* R, int* status,
                         cudaStream_t s);
 
+// Split-BF16 (hi*hi + hi*lo + lo*hi) Gram on the tensor cores (tcgen05.mma,
+// accumulators in TMEM); per-SM float partials p x p, summed in double.
+hyde_status gram_tc_partial_bytes(int p, size_t* bytes);
+hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, double* R,
+                           int* status, cudaStream_t s);
+
 // ------------------------------------------------------- small dense LA
 size_t noise_ws_bytes(int p);
 hyde_status launch_noise_from_gram(const double* R, int p, long long n,

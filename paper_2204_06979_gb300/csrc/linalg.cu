@@ -237,20 +237,6 @@ struct EigTail {
     float* dots;
 };
 
-// reflector k as (first element, stride); element i is v_k[i], i < p-k-1
-struct ReflInPlace {
-    const float* A; int lda;
-    __device__ const float* base(int k) const { return A + (k + 1) * lda + k; }
-    __device__ int stride() const { return lda; }
-};
-struct ReflPacked {
-    const float* V; int p;
-    __device__ const float* base(int k) const {
-        return V + (size_t)k * (p - 1) - (size_t)k * (k - 1) / 2;
-    }
-    __device__ int stride() const { return 1; }
-};
-
 __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int p,
                                            float x, float pivmin) {
     float q = d[0] - x;
@@ -264,9 +250,7 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
 }
 
 // Stages 2-5 on the tridiagonal (d, e) in shared memory; all 1024 threads.
-template <class Refl>
-__device__ void eig_tail(const EigTail& S, const Refl& refl, int p, int r, float scale,
-                         double* __restrict__ evals, double* __restrict__ V, int* status) {
+__device__ void eig_tail_stages234(const EigTail& S, int p, int r, int* status) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int i = t; i < p; i += blockDim.x) {
         S.e2[i] = S.e[i] * S.e[i];
@@ -403,230 +387,21 @@ __device__ void eig_tail(const EigTail& S, const Refl& refl, int p, int r, float
         }
         __syncthreads();
     }
-
-    // 5. back-transformation x <- H_0 ... H_{p-3} x, one warp per vector
-    if (wid < r) {
-        float* x = S.X + wid * p;
-        const int st = refl.stride();
-        for (int k = p - 3; k >= 0; --k) {
-            const float tau = S.tau[k];
-            if (tau == 0.f) continue;
-            const int m = p - k - 1;
-            const float* col = refl.base(k);
-            float dt = 0.f;
-            for (int i = lane; i < m; i += 32) dt = fmaf(col[i * st], x[k + 1 + i], dt);
-            dt = warp_sum(dt) * tau;
-            for (int i = lane; i < m; i += 32) x[k + 1 + i] = fmaf(-dt, col[i * st], x[k + 1 + i]);
-            __syncwarp();
-        }
-        float best = -1.f;
-        int bi = 0;
-        for (int i = lane; i < p; i += 32) {
-            float a = fabsf(x[i]);
-            if (a > best) { best = a; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        const float sg = x[bi] < 0.f ? -1.f : 1.f;
-        for (int i = lane; i < p; i += 32) V[(long long)i * r + wid] = (double)(sg * x[i]);
-        if (lane == 0) evals[wid] = (double)S.lam[wid] / (double)scale;
-    }
 }
 
-// Shared-memory layout of the register-tile eigensolver.
-struct EigRegSmem {
-    float *Vh, *d, *e, *e2, *tau, *iw, *lam, *dots, *X, *Dp, *Dm, *red;
-    float *xb, *vb, *pv;   // [2][32T] each
-};
-
-__device__ inline EigRegSmem eig_reg_carve(float* q, int p, int r, int T) {
-    EigRegSmem m;
-    const int P = 32 * T;
-    m.Vh = q;   q += (p * (p - 1)) / 2 + 1;
-    m.d = q;    q += P;
-    m.e = q;    q += P;
-    m.e2 = q;   q += P;
-    m.tau = q;  q += P;
-    m.iw = q;   q += P;
-    m.lam = q;  q += 32;
-    m.dots = q; q += 32;
-    m.red = q;  q += 64;
-    m.xb = q;   q += 2 * P;
-    m.vb = q;   q += 2 * P;
-    m.pv = q;   q += 2 * P;
-    m.X = q;    q += p * r;
-    m.Dp = q;   q += p * r;
-    m.Dm = q;   q += p * r;
-    return m;
-}
-
-size_t eig_reg_smem_floats(int p, int r, int T) {
-    const size_t P = 32 * (size_t)T;
-    return (size_t)(p * (p - 1)) / 2 + 1 + 5 * P + 128 + 6 * P + 3 * (size_t)p * r;
-}
-
-template <int T>
+// --------------------------------------------------------------------------
+// Eigensolver with the matrix in shared memory and the per-step vectors in
+// registers (one block, 1024 threads; NB = ceil(p/32) column chunks per
+// lane). Warp w owns rows i = w (mod 32) of the trailing matrix, lane l owns
+// columns j = l + 32b, and caches v_j and w_j of those columns in registers,
+// so a matrix element costs one load and one FMA in the matvec and one
+// load, two FMAs and one store in the rank-2 update; K = tau/2 v^T p is one
+// warp shuffle-sum per warp. The back-transformation keeps each eigenvector
+// in registers (lane l holds entries l + 32b).
+// --------------------------------------------------------------------------
+template <int NB>
 __global__ void __launch_bounds__(kLA, 1)
-eig_reg_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p, int r,
-               double* __restrict__ evals, double* __restrict__ V, int* status) {
-    extern __shared__ float sm[];
-    EigRegSmem S = eig_reg_carve(sm, p, r, T);
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int r0 = wid * T, c0 = lane * T;
-    constexpr int P = 32 * T;
-
-    __shared__ float s_scale;
-    if (t < 32) {
-        double mx = 0.0;
-        for (int i = lane; i < P; i += 32) {
-            float w = 0.f;
-            if (i < p) {
-                double a = Ain[(long long)i * p + i];
-                const double wd = wsig ? 1.0 / wsig[i] : 1.0;
-                w = (float)wd;
-                a *= wd * wd;
-                if (!isfinite(a)) set_status(status, HYDE_ERR_NUMERIC);
-                mx = fmax(mx, fabs(a));
-            }
-            S.iw[i] = w;
-        }
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) s_scale = mx > 0.0 ? (float)(1.0 / mx) : 1.0f;
-    }
-    __syncthreads();
-    const float scale = s_scale;
-    float a[T][T];
-#pragma unroll
-    for (int ii = 0; ii < T; ++ii) {
-        const int i = r0 + ii;
-#pragma unroll
-        for (int jj = 0; jj < T; ++jj) {
-            const int j = c0 + jj;
-            a[ii][jj] = (i < p && j < p)
-                            ? (float)Ain[(long long)i * p + j] * (S.iw[i] * scale) * S.iw[j]
-                            : 0.f;
-        }
-    }
-
-    // ---- 1. Householder tridiagonalisation, matrix in registers
-    for (int k = 0; k + 2 < p; ++k) {
-        const int buf = k & 1;
-        float* xb = S.xb + buf * P;
-        float* vb = S.vb + buf * P;
-        float* pv = S.pv + buf * P;
-        float* red = S.red + buf * 32;
-        const int kt = k / T, ko = k - kt * T;
-        if (lane == kt) {                     // publish column k
-#pragma unroll
-            for (int jj = 0; jj < T; ++jj)
-                if (jj == ko) {
-#pragma unroll
-                    for (int ii = 0; ii < T; ++ii) xb[r0 + ii] = a[ii][jj];
-                }
-        }
-        __syncthreads();
-        if (wid == 0) {                       // reflector from x = A[k+1..p-1][k]
-            float ss = 0.f;
-            for (int i = k + 2 + lane; i < p; i += 32) ss = fmaf(xb[i], xb[i], ss);
-            ss = warp_sum(ss);
-            const float alpha = xb[k + 1];
-            float tau = 0.f, beta = alpha, sc = 0.f;
-            if (ss > 0.f) {
-                const float nrm = sqrtf(fmaf(alpha, alpha, ss));
-                beta = alpha >= 0.f ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                sc = 1.0f / (alpha - beta);
-            }
-            float* vh = S.Vh + (size_t)k * (p - 1) - (size_t)k * (k - 1) / 2;
-            for (int i = lane; i < P; i += 32) {
-                float vi = 0.f;
-                if (i == k + 1) vi = 1.0f;
-                else if (i > k + 1 && i < p && ss > 0.f) vi = xb[i] * sc;
-                vb[i] = vi;
-                if (i > k && i < p) vh[i - k - 1] = vi;
-            }
-            if (lane == 0) { S.tau[k] = tau; S.d[k] = xb[k]; S.e[k] = beta; }
-        }
-        __syncthreads();
-        const float tau = S.tau[k];
-        const bool active = (r0 + T - 1 > k) && tau != 0.f;   // warp owns rows beyond k
-        float vr[T], vc[T];
-        if (active) {
-#pragma unroll
-            for (int q = 0; q < T; ++q) { vr[q] = vb[r0 + q]; vc[q] = vb[c0 + q]; }
-            float kpart = 0.f;
-#pragma unroll
-            for (int ii = 0; ii < T; ++ii) {
-                float s = 0.f;
-#pragma unroll
-                for (int jj = 0; jj < T; ++jj) s = fmaf(a[ii][jj], vc[jj], s);
-                s = warp_sum(s) * tau;
-                if (r0 + ii <= k) s = 0.f;     // rows already reduced take no update
-                if (lane == 0) pv[r0 + ii] = s;
-                kpart = fmaf(s, vr[ii], kpart);
-            }
-            if (lane == 0) red[wid] = kpart;
-        } else if (lane == 0) {
-            red[wid] = 0.f;
-#pragma unroll
-            for (int q = 0; q < T; ++q) pv[r0 + q] = 0.f;
-        }
-        __syncthreads();
-        if (active) {
-            const float K = 0.5f * tau * warp_sum(red[lane]);
-            float wr[T], wc[T];
-#pragma unroll
-            for (int q = 0; q < T; ++q) {
-                wr[q] = fmaf(-K, vr[q], pv[r0 + q]);
-                wc[q] = fmaf(-K, vc[q], pv[c0 + q]);
-            }
-#pragma unroll
-            for (int ii = 0; ii < T; ++ii)
-#pragma unroll
-                for (int jj = 0; jj < T; ++jj)
-                    a[ii][jj] = fmaf(-vr[ii], wc[jj], fmaf(-wr[ii], vc[jj], a[ii][jj]));
-        }
-    }
-    // last 2 x 2 block: publish columns p-2 and p-1
-    {
-        float* xb0 = S.xb;
-        float* xb1 = S.xb + P;
-        __syncthreads();
-        const int k0 = p >= 2 ? p - 2 : 0, k1 = p - 1;
-        const int kt0 = k0 / T, ko0 = k0 - kt0 * T, kt1 = k1 / T, ko1 = k1 - kt1 * T;
-#pragma unroll
-        for (int jj = 0; jj < T; ++jj) {
-            if (lane == kt0 && jj == ko0) {
-#pragma unroll
-                for (int ii = 0; ii < T; ++ii) xb0[r0 + ii] = a[ii][jj];
-            }
-            if (lane == kt1 && jj == ko1) {
-#pragma unroll
-                for (int ii = 0; ii < T; ++ii) xb1[r0 + ii] = a[ii][jj];
-            }
-        }
-        __syncthreads();
-        if (t == 0) {
-            if (p >= 2) {
-                S.d[p - 2] = xb0[p - 2];
-                S.e[p - 2] = xb0[p - 1];
-                S.tau[p - 2] = 0.f;
-            }
-            S.d[p - 1] = xb1[p - 1];
-            S.e[p - 1] = 0.f;
-        }
-        __syncthreads();
-    }
-    EigTail tail{S.d, S.e, S.e2, S.tau, S.lam, S.X, S.Dp, S.Dm, S.dots};
-    eig_tail(tail, ReflPacked{S.Vh, p}, p, r, scale, evals, V, status);
-}
-
-// Shared-memory eigensolver for p > 192 (matrix and reflectors in smem).
-__global__ void __launch_bounds__(kLA, 1)
-eig_smem_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p, int r,
+eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p, int r,
                 double* __restrict__ evals, double* __restrict__ V, int* status) {
     extern __shared__ float sm[];
     const int lda = p + 1;
@@ -636,7 +411,7 @@ eig_smem_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     float* dv = q;   q += p;
     float* ev = q;   q += p;
     float* e2v = q;  q += p;
-    float* v = q;    q += p;
+    float* vf = q;   q += p;     // current reflector, full length
     float* pvv = q;  q += p;
     float* red = q;  q += 64;
     float* lamv = q; q += 32;
@@ -647,7 +422,7 @@ eig_smem_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 
     __shared__ float s_scale;
-    float* iw = v;
+    float* iw = vf;
     if (t < 32) {
         double mx = 0.0;
         for (int i = lane; i < p; i += 32) {
@@ -671,11 +446,11 @@ eig_smem_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     __syncthreads();
 
     for (int k = 0; k + 2 < p; ++k) {
+        float* col = A + (k + 1) * lda + k;     // col[i * lda] = A[k+1+i][k]
         const int m = p - k - 1;
-        float* col = A + (k + 1) * lda + k;
         if (wid == 0) {
             float ss = 0.f;
-            for (int i = 1 + lane; i < m; i += 32) { float x = col[i * lda]; ss = fmaf(x, x, ss); }
+            for (int i = 1 + lane; i < m; i += 32) { const float x = col[i * lda]; ss = fmaf(x, x, ss); }
             ss = warp_sum(ss);
             const float alpha = col[0];
             __syncwarp();   // every lane has read col[] before it is rewritten
@@ -683,38 +458,79 @@ eig_smem_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
             if (ss > 0.f) {
                 const float nrm = sqrtf(fmaf(alpha, alpha, ss));
                 beta = alpha >= 0.f ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                sc = 1.0f / (alpha - beta);
+                tau = __fdividef(beta - alpha, beta);
+                sc = __fdividef(1.0f, alpha - beta);
             }
-            for (int i = lane; i < m; i += 32) {
-                float vi = (i == 0) ? 1.0f : col[i * lda] * sc;
-                if (ss == 0.f) vi = (i == 0) ? 1.0f : 0.f;
-                v[i] = vi;
-                col[i * lda] = vi;
+            for (int i = lane; i < p; i += 32) {
+                float vi = 0.f;
+                if (i == k + 1) vi = 1.0f;
+                else if (i > k + 1 && ss > 0.f) vi = col[(i - k - 1) * lda] * sc;
+                vf[i] = vi;
             }
+            __syncwarp();
+            for (int i = lane; i < m; i += 32) col[i * lda] = vf[k + 1 + i];   // kept for step 5
             if (lane == 0) { tauv[k] = tau; dv[k] = A[k * lda + k]; ev[k] = beta; }
         }
         __syncthreads();
         const float tau = tauv[k];
         if (tau != 0.f) {
+            float vreg[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int j = lane + 32 * b;
+                vreg[b] = (j > k && j < p) ? vf[j] : 0.f;
+            }
+            // all rows of this warp at once (rows i0 + 32a), so the NB row
+            // reductions overlap instead of running one after another
+            const int i0 = k + 1 + ((wid - (k + 1)) & 31);
+            float s[NB];
+#pragma unroll
+            for (int a = 0; a < NB; ++a) {
+                const int i = i0 + 32 * a;
+                s[a] = 0.f;
+                if (i < p) {
+                    const float* row = A + i * lda;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const int j = lane + 32 * b;
+                        if (j < p) s[a] = fmaf(row[j], vreg[b], s[a]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int a = 0; a < NB; ++a) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
             float kpart = 0.f;
-            for (int i = wid; i < m; i += 32) {
-                const float* row = A + (k + 1 + i) * lda + (k + 1);
-                float u = 0.f;
-                for (int j = lane; j < m; j += 32) u = fmaf(row[j], v[j], u);
-                u = warp_sum(u) * tau;
-                if (lane == 0) pvv[i] = u;
-                kpart = fmaf(u, v[i], kpart);
+#pragma unroll
+            for (int a = 0; a < NB; ++a) {
+                const int i = i0 + 32 * a;
+                if (i < p) {
+                    const float pi = s[a] * tau;
+                    if (lane == a) pvv[i] = pi;
+                    kpart = fmaf(pi, vf[i], kpart);
+                }
             }
             if (lane == 0) red[wid] = kpart;
             __syncthreads();
             const float K = 0.5f * tau * warp_sum(red[lane]);
-            for (int i = wid; i < m; i += 32) {
-                float* row = A + (k + 1 + i) * lda + (k + 1);
-                const float vi = v[i], wi = fmaf(-K, vi, pvv[i]);
-                for (int j = lane; j < m; j += 32) {
-                    const float vj = v[j], wj = fmaf(-K, vj, pvv[j]);
-                    row[j] = fmaf(-vi, wj, fmaf(-wi, vj, row[j]));
+            float wreg[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int j = lane + 32 * b;
+                wreg[b] = (j > k && j < p) ? fmaf(-K, vreg[b], pvv[j]) : 0.f;
+            }
+#pragma unroll
+            for (int a = 0; a < NB; ++a) {
+                const int i = i0 + 32 * a;
+                if (i < p) {
+                    float* row = A + i * lda;
+                    const float vi = vf[i], wi = fmaf(-K, vi, pvv[i]);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const int j = lane + 32 * b;
+                        if (j > k && j < p) row[j] = fmaf(-vi, wreg[b], fmaf(-wi, vreg[b], row[j]));
+                    }
                 }
             }
         }
@@ -731,7 +547,58 @@ eig_smem_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     }
     __syncthreads();
     EigTail tail{dv, ev, e2v, tauv, lamv, X, Dp, Dm, dots};
-    eig_tail(tail, ReflInPlace{A, lda}, p, r, scale, evals, V, status);
+    eig_tail_stages234(tail, p, r, status);
+    // 5. back-transformation with the vector in registers, one warp per vector
+    if (wid < r) {
+        float x[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int i = lane + 32 * b;
+            x[b] = i < p ? X[wid * p + i] : 0.f;
+        }
+        for (int k = p - 3; k >= 0; --k) {
+            const float tau = tauv[k];
+            if (tau == 0.f) continue;
+            const float* cl = A + k;          // column k; entry i (> k) at cl[i * lda]
+            float dt = 0.f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int i = lane + 32 * b;
+                if (i > k && i < p) dt = fmaf(cl[i * lda], x[b], dt);
+            }
+            dt = warp_sum(dt) * tau;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int i = lane + 32 * b;
+                if (i > k && i < p) x[b] = fmaf(-dt, cl[i * lda], x[b]);
+            }
+        }
+        float best = -1.f;
+        int bi = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int i = lane + 32 * b;
+            if (i < p && fabsf(x[b]) > best) { best = fabsf(x[b]); bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        const int owner = bi & 31;
+        float xb = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (b == (bi >> 5)) xb = x[b];
+        xb = __shfl_sync(0xffffffffu, xb, owner);
+        const float sg = xb < 0.f ? -1.f : 1.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int i = lane + 32 * b;
+            if (i < p) V[(long long)i * r + wid] = (double)(sg * x[b]);
+        }
+        if (lane == 0) evals[wid] = (double)lamv[wid] / (double)scale;
+    }
 }
 
 __global__ void weights_kernel(const double* __restrict__ V, const double* __restrict__ sigma,
@@ -746,17 +613,7 @@ __global__ void weights_kernel(const double* __restrict__ V, const double* __res
     }
 }
 
-template <int T>
-hyde_status launch_eig_reg(const double* A, const double* wsig, int p, int r, double* evals,
-                           double* V, int* status, cudaStream_t s) {
-    const size_t smem = eig_reg_smem_floats(p, r, T) * sizeof(float);
-    if (ensure_smem_limit((const void*)eig_reg_kernel<T>, (int)smem) != cudaSuccess)
-        return HYDE_ERR_SHAPE;
-    eig_reg_kernel<T><<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);
-    return HYDE_OK;
-}
-
-size_t eig_smem_old_bytes(int p, int r) {
+size_t eig_fast_bytes(int p, int r) {
     return ((size_t)p * (p + 1) + 6 * (size_t)p + 64 + 32 + 32 + 3 * (size_t)p * r) *
            sizeof(float);
 }
@@ -797,33 +654,26 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
     return cuda_status(cudaGetLastError());
 }
 
-size_t eig_smem_bytes(int p, int r) {
-    const int T = (p + 31) / 32;
-    if (T <= kMaxRegT) return eig_reg_smem_floats(p, r, T) * sizeof(float);
-    return eig_smem_old_bytes(p, r);
-}
+size_t eig_smem_bytes(int p, int r) { return eig_fast_bytes(p, r); }
 
 hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, double* evals,
                            double* V, int* status, cudaStream_t s) {
-    if (r > 32 || r < 1 || r > p) return HYDE_ERR_SHAPE;
-    if (eig_smem_bytes(p, r) > 227 * 1024) return HYDE_ERR_SHAPE;
-    const int T = (p + 31) / 32;
-    hyde_status st = HYDE_OK;
-    switch (T) {
-        case 1: st = launch_eig_reg<1>(A, wsig, p, r, evals, V, status, s); break;
-        case 2: st = launch_eig_reg<2>(A, wsig, p, r, evals, V, status, s); break;
-        case 3: st = launch_eig_reg<3>(A, wsig, p, r, evals, V, status, s); break;
-        case 4: st = launch_eig_reg<4>(A, wsig, p, r, evals, V, status, s); break;
-        case 5: st = launch_eig_reg<5>(A, wsig, p, r, evals, V, status, s); break;
-        case 6: st = launch_eig_reg<6>(A, wsig, p, r, evals, V, status, s); break;
-        default: {
-            const size_t smem = eig_smem_old_bytes(p, r);
-            if (ensure_smem_limit((const void*)eig_smem_kernel, (int)smem) != cudaSuccess)
-                return HYDE_ERR_SHAPE;
-            eig_smem_kernel<<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);
-        }
+    if (r > 32 || r < 1 || r > p || p > 256) return HYDE_ERR_SHAPE;
+    const size_t smem = eig_fast_bytes(p, r);
+    if (smem > 227 * 1024) return HYDE_ERR_SHAPE;
+    const int NB = (p + 31) / 32;
+    switch (NB) {
+#define HYDE_EIG(NBV)                                                                          \
+    case NBV:                                                                                  \
+        if (ensure_smem_limit((const void*)eig_fast_kernel<NBV>, (int)smem) != cudaSuccess)    \
+            return HYDE_ERR_SHAPE;                                                             \
+        eig_fast_kernel<NBV><<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);           \
+        break;
+        HYDE_EIG(1) HYDE_EIG(2) HYDE_EIG(3) HYDE_EIG(4)
+        HYDE_EIG(5) HYDE_EIG(6) HYDE_EIG(7) HYDE_EIG(8)
+#undef HYDE_EIG
+        default: return HYDE_ERR_SHAPE;
     }
-    if (st != HYDE_OK) return st;
     return cuda_status(cudaGetLastError());
 }
 
