@@ -136,6 +136,49 @@ struct TcPlan {
     size_t stage_bytes, smem;
 };
 
+// Chunk loads are double-buffered in registers: each thread holds RPW band
+// rows x 2 pixels of two chunks, so all of a chunk's loads are in flight
+// while the previous chunk is converted, stored and multiplied.
+template <int RPW>
+struct ChunkRegs {
+    float v[RPW][2];
+};
+
+template <int RPW>
+__device__ __forceinline__ void load_chunk(ChunkRegs<RPW>& R, const float* __restrict__ Y, int p,
+                                           long long n, long long chunk, int warp, int lane) {
+    const long long pix = chunk * kChunk + 2 * lane;
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        const int b = warp + q * (kTcThreads / 32);
+        float v0 = 0.f, v1 = 0.f;
+        if (b < p) {
+            const float* yr = Y + (long long)b * n;
+            if (pix < n) v0 = __ldg(yr + pix);
+            if (pix + 1 < n) v1 = __ldg(yr + pix + 1);
+        }
+        R.v[q][0] = v0;
+        R.v[q][1] = v1;
+    }
+}
+
+template <int RPW>
+__device__ __forceinline__ void store_chunk(const ChunkRegs<RPW>& R, uint8_t* st, uint32_t half,
+                                            int p, int warp, int lane) {
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        const int b = warp + q * (kTcThreads / 32);
+        if (b < p) {
+            uint32_t lo;
+            const uint32_t hi = pack_bf16(R.v[q][0], R.v[q][1], &lo);
+            const uint32_t off = sw128_offset(b, lane);
+            *reinterpret_cast<uint32_t*>(st + off) = hi;
+            *reinterpret_cast<uint32_t*>(st + half + off) = lo;
+        }
+    }
+}
+
+template <int RPW>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
                long long chunks_per_cta, float* __restrict__ partials, int* status) {
@@ -177,6 +220,10 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
     const uint32_t id0 = idesc_bf16(128, P.Np);
     const uint32_t id1 = idesc_bf16(128, P.n1 > 0 ? P.n1 : 16);
 
+    ChunkRegs<RPW> ra, rb;
+    if (iters > 0) load_chunk(ra, Y, p, n, c0, warp, lane);
+    if (iters > 1) load_chunk(rb, Y, p, n, c0 + 1, warp, lane);
+
     long long issued = 0;   // iterations whose MMAs were committed
     for (long long it = 0; it < iters; ++it) {
         const int s = (int)(it % S);
@@ -188,17 +235,14 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
         }
         __syncthreads();
         if (abort_s) break;
-        const long long pix = (c0 + it) * kChunk + 2 * lane;
         uint8_t* st = gbase + (sbase - base);
-        for (int b = warp; b < p; b += kTcThreads / 32) {
-            const float* yr = Y + (long long)b * n;
-            const float v0 = pix < n ? __ldg(yr + pix) : 0.f;
-            const float v1 = pix + 1 < n ? __ldg(yr + pix + 1) : 0.f;
-            uint32_t lo;
-            const uint32_t hi = pack_bf16(v0, v1, &lo);
-            const uint32_t off = sw128_offset(b, lane);
-            *reinterpret_cast<uint32_t*>(st + off) = hi;
-            *reinterpret_cast<uint32_t*>(st + half + off) = lo;
+        // store chunk it, then reuse its registers for chunk it + 2
+        if ((it & 1) == 0) {
+            store_chunk(ra, st, half, p, warp, lane);
+            if (it + 2 < iters) load_chunk(ra, Y, p, n, c0 + it + 2, warp, lane);
+        } else {
+            store_chunk(rb, st, half, p, warp, lane);
+            if (it + 2 < iters) load_chunk(rb, Y, p, n, c0 + it + 2, warp, lane);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -326,12 +370,22 @@ hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, 
     if (P.stages < 2 || P.smem > 227 * 1024 || P.tmem_cols > 512) return HYDE_ERR_SHAPE;
     const int sms = device_sm_count();
     if (sms <= 0) return HYDE_ERR_CUDA;
-    if (ensure_smem_limit((const void*)gram_tc_kernel, (int)P.smem) != cudaSuccess)
-        return HYDE_ERR_CUDA;
     const long long nchunks = (n + kChunk - 1) / kChunk;
     const int blocks = sms;
     const long long per = (nchunks + blocks - 1) / blocks;
-    gram_tc_kernel<<<blocks, kTcThreads, P.smem, s>>>(Y, p, n, P, per, partials, status);
+    const int rpw = (p + kTcThreads / 32 - 1) / (kTcThreads / 32);   // band rows per warp
+    switch ((rpw + 7) / 8) {
+#define HYDE_TC(G)                                                                            \
+    case G:                                                                                   \
+        if (ensure_smem_limit((const void*)gram_tc_kernel<8 * G>, (int)P.smem) != cudaSuccess) \
+            return HYDE_ERR_CUDA;                                                             \
+        gram_tc_kernel<8 * G><<<blocks, kTcThreads, P.smem, s>>>(Y, p, n, P, per, partials,  \
+                                                                  status);                    \
+        break;
+        HYDE_TC(1) HYDE_TC(2) HYDE_TC(3) HYDE_TC(4)
+#undef HYDE_TC
+        default: return HYDE_ERR_SHAPE;
+    }
     gram_tc_reduce_kernel<<<(p * p + 255) / 256, 256, 0, s>>>(partials, blocks, p, R, status);
     return cuda_status(cudaGetLastError());
 }

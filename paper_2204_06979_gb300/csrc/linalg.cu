@@ -389,6 +389,27 @@ __device__ void eig_tail_stages234(const EigTail& S, int p, int r, int* status) 
     }
 }
 
+// Scalars of Householder reflector kr from column kr of A (row-major, leading
+// dimension lda): alpha = A[kr+1][kr], ss = sum of squares below it. The
+// reflector is v = e_{kr+1} + sc * (A[kr+2..][kr]), H = I - tau v v^T, and it
+// maps the column onto beta e_{kr+1}. ss == 0 gives the identity (tau = 0).
+__device__ __forceinline__ void hh_scalars(const float* A, int lda, int kr, float ss,
+                                           float& tau, float& sc, float& beta) {
+    const float alpha = A[(kr + 1) * lda + kr];
+    tau = 0.f; beta = alpha; sc = 0.f;
+    if (ss > 0.f) {
+        const float nrm = sqrtf(fmaf(alpha, alpha, ss));
+        beta = alpha >= 0.f ? -nrm : nrm;
+        tau = __fdividef(beta - alpha, beta);
+        sc = __fdividef(1.0f, alpha - beta);
+    }
+}
+
+// Entry i of reflector kr (see hh_scalars).
+__device__ __forceinline__ float hh_coef(const float* A, int lda, int p, int kr, float sc, int i) {
+    return i == kr + 1 ? 1.0f : ((i > kr + 1 && i < p) ? A[i * lda + kr] * sc : 0.f);
+}
+
 // --------------------------------------------------------------------------
 // Eigensolver with the matrix in shared memory and the per-step vectors in
 // registers (one block, 1024 threads; NB = ceil(p/32) column chunks per
@@ -411,8 +432,8 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     float* dv = q;   q += p;
     float* ev = q;   q += p;
     float* e2v = q;  q += p;
-    float* vf = q;   q += p;     // current reflector, full length
-    float* pvv = q;  q += p;
+    float* vf = q;   q += p;     // reflector buffer 0, full length
+    float* pvv = q;  q += 2 * p; // p = tau A v, then reflector buffer 1
     float* red = q;  q += 64;
     float* lamv = q; q += 32;
     float* dots = q; q += 32;
@@ -445,95 +466,145 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     }
     __syncthreads();
 
-    for (int k = 0; k + 2 < p; ++k) {
-        float* col = A + (k + 1) * lda + k;     // col[i * lda] = A[k+1+i][k]
-        const int m = p - k - 1;
-        if (wid == 0) {
-            float ss = 0.f;
-            for (int i = 1 + lane; i < m; i += 32) { const float x = col[i * lda]; ss = fmaf(x, x, ss); }
-            ss = warp_sum(ss);
-            const float alpha = col[0];
-            __syncwarp();   // every lane has read col[] before it is rewritten
-            float tau = 0.f, beta = alpha, sc = 0.f;
-            if (ss > 0.f) {
-                const float nrm = sqrtf(fmaf(alpha, alpha, ss));
-                beta = alpha >= 0.f ? -nrm : nrm;
-                tau = __fdividef(beta - alpha, beta);
-                sc = __fdividef(1.0f, alpha - beta);
-            }
-            for (int i = lane; i < p; i += 32) {
-                float vi = 0.f;
-                if (i == k + 1) vi = 1.0f;
-                else if (i > k + 1 && ss > 0.f) vi = col[(i - k - 1) * lda] * sc;
-                vf[i] = vi;
-            }
-            __syncwarp();
-            for (int i = lane; i < m; i += 32) col[i * lda] = vf[k + 1 + i];   // kept for step 5
-            if (lane == 0) { tauv[k] = tau; dv[k] = A[k * lda + k]; ev[k] = beta; }
-        }
-        __syncthreads();
-        const float tau = tauv[k];
-        if (tau != 0.f) {
-            float vreg[NB];
+    // Fused steps. Reflector k is kept as (column k of A, scale sc_k):
+    // v_k[i] = 1 at i = k+1, A[i][k] sc_k beyond. Per step: K from the block
+    // partials; the owner lanes update column k+1 and sum the squares of its
+    // entries below k+2; after one barrier every thread forms reflector k+1's
+    // scalars itself; then one sweep over the trailing matrix applies update
+    // k and accumulates p' = A' v_{k+1} of step k+1 from the new values. Two
+    // barriers per step, one read and one write of each trailing element.
+    float* const scv = vf;           // reflector scales (vf is free after the load)
+    // prologue: reflector 0 (scalars in every warp) and p_0 = tau_0 A v_0
+    float tau_k = 0.f, sc_k = 0.f;
+    float vreg[NB];
+    if (p >= 3) {
+        float ss = 0.f;
+        for (int i = 2 + lane; i < p; i += 32) { const float x = A[i * lda]; ss = fmaf(x, x, ss); }
+        ss = warp_sum(ss);
+        float beta;
+        hh_scalars(A, lda, 0, ss, tau_k, sc_k, beta);
+        if (t == 0) { tauv[0] = tau_k; scv[0] = sc_k; dv[0] = A[0]; ev[0] = beta; }
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const int j = lane + 32 * b;
-                vreg[b] = (j > k && j < p) ? vf[j] : 0.f;
+        for (int b = 0; b < NB; ++b) vreg[b] = hh_coef(A, lda, p, 0, sc_k, lane + 32 * b);
+        const int i0 = 1 + ((wid - 1) & 31);
+        float sacc[NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) {
+            const int i = i0 + 32 * a;
+            sacc[a] = 0.f;
+            if (i < p) {
+                const float* row = A + i * lda;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int j = lane + 32 * b;
+                    if (j < p) sacc[a] = fmaf(row[j], vreg[b], sacc[a]);
+                }
             }
-            // all rows of this warp at once (rows i0 + 32a), so the NB row
-            // reductions overlap instead of running one after another
-            const int i0 = k + 1 + ((wid - (k + 1)) & 31);
-            float s[NB];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int a = 0; a < NB; ++a) sacc[a] += __shfl_xor_sync(0xffffffffu, sacc[a], o);
+        float kpart = 0.f;
+#pragma unroll
+        for (int a = 0; a < NB; ++a) {
+            const int i = i0 + 32 * a;
+            if (i < p) {
+                const float pi = sacc[a] * tau_k;
+                if (lane == a) pvv[i] = pi;
+                kpart = fmaf(pi, hh_coef(A, lda, p, 0, sc_k, i), kpart);
+            }
+        }
+        if (lane == 0) red[wid] = kpart;
+    }
+    __syncthreads();
+    for (int k = 0; k + 2 < p; ++k) {
+        const float* pc = pvv + (k & 1) * p;
+        float* pn = pvv + ((k + 1) & 1) * p;
+        const bool has_next = k + 4 <= p;
+        const float K = 0.5f * tau_k * warp_sum(red[lane]);
+        float wreg[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int j = lane + 32 * b;
+            wreg[b] = (j > k && j < p) ? fmaf(-K, vreg[b], pc[j]) : 0.f;
+        }
+        const int i0 = k + 1 + ((wid - (k + 1)) & 31);
+        // column k+1 (owner lane of each warp) and the squares for reflector k+1
+        const int jn = k + 1;
+        float ssp = 0.f;
+        if (lane == (jn & 31)) {
+            const float wjn = pc[jn] - K;
 #pragma unroll
             for (int a = 0; a < NB; ++a) {
                 const int i = i0 + 32 * a;
-                s[a] = 0.f;
                 if (i < p) {
-                    const float* row = A + i * lda;
+                    const float vi = hh_coef(A, lda, p, k, sc_k, i), wi = fmaf(-K, vi, pc[i]);
+                    float* e = A + i * lda + jn;          // v_k[jn] = 1
+                    const float x = fmaf(-vi, wjn, *e - wi);
+                    *e = x;
+                    if (i >= k + 3) ssp = fmaf(x, x, ssp);
+                }
+            }
+            red[32 + wid] = ssp;
+        }
+        __syncthreads();
+        float tau_n = 0.f, sc_n = 0.f;
+        float vn[NB];
+        if (has_next) {
+            float beta;
+            hh_scalars(A, lda, k + 1, warp_sum(red[32 + lane]), tau_n, sc_n, beta);
+            if (t == 0) {
+                tauv[k + 1] = tau_n; scv[k + 1] = sc_n;
+                dv[k + 1] = A[(k + 1) * lda + (k + 1)]; ev[k + 1] = beta;
+            }
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const int j = lane + 32 * b;
-                        if (j < p) s[a] = fmaf(row[j], vreg[b], s[a]);
+            for (int b = 0; b < NB; ++b) vn[b] = hh_coef(A, lda, p, k + 1, sc_n, lane + 32 * b);
+        } else {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) vn[b] = 0.f;
+        }
+        // fused sweep: update k on rows > k+1, columns > k+1; accumulate p' rows
+        float sacc[NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) {
+            const int i = i0 + 32 * a;
+            sacc[a] = 0.f;
+            if (i > k + 1 && i < p) {
+                float* row = A + i * lda;
+                const float vi = hh_coef(A, lda, p, k, sc_k, i), wi = fmaf(-K, vi, pc[i]);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int j = lane + 32 * b;
+                    if (j > k + 1 && j < p) {
+                        const float x = fmaf(-vi, wreg[b], fmaf(-wi, vreg[b], row[j]));
+                        row[j] = x;
+                        sacc[a] = fmaf(x, vn[b], sacc[a]);
                     }
                 }
             }
+        }
+        if (has_next) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                for (int a = 0; a < NB; ++a) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
+                for (int a = 0; a < NB; ++a) sacc[a] += __shfl_xor_sync(0xffffffffu, sacc[a], o);
             float kpart = 0.f;
 #pragma unroll
             for (int a = 0; a < NB; ++a) {
                 const int i = i0 + 32 * a;
-                if (i < p) {
-                    const float pi = s[a] * tau;
-                    if (lane == a) pvv[i] = pi;
-                    kpart = fmaf(pi, vf[i], kpart);
+                if (i > k + 1 && i < p) {
+                    const float pi = sacc[a] * tau_n;
+                    if (lane == a) pn[i] = pi;
+                    kpart = fmaf(pi, hh_coef(A, lda, p, k + 1, sc_n, i), kpart);
                 }
             }
             if (lane == 0) red[wid] = kpart;
-            __syncthreads();
-            const float K = 0.5f * tau * warp_sum(red[lane]);
-            float wreg[NB];
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const int j = lane + 32 * b;
-                wreg[b] = (j > k && j < p) ? fmaf(-K, vreg[b], pvv[j]) : 0.f;
-            }
-#pragma unroll
-            for (int a = 0; a < NB; ++a) {
-                const int i = i0 + 32 * a;
-                if (i < p) {
-                    float* row = A + i * lda;
-                    const float vi = vf[i], wi = fmaf(-K, vi, pvv[i]);
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const int j = lane + 32 * b;
-                        if (j > k && j < p) row[j] = fmaf(-vi, wreg[b], fmaf(-wi, vreg[b], row[j]));
-                    }
-                }
-            }
         }
+        tau_k = tau_n;
+        sc_k = sc_n;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) vreg[b] = vn[b];
         __syncthreads();
     }
     if (t == 0) {
@@ -559,19 +630,19 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
         for (int k = p - 3; k >= 0; --k) {
             const float tau = tauv[k];
             if (tau == 0.f) continue;
-            const float* cl = A + k;          // column k; entry i (> k) at cl[i * lda]
+            const float* cl = A + k;          // column k; v_k[i] = cl[i * lda] * sc (i > k+1)
+            const float scr = vf[k];
+            float vk[NB];
             float dt = 0.f;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const int i = lane + 32 * b;
-                if (i > k && i < p) dt = fmaf(cl[i * lda], x[b], dt);
+                vk[b] = i == k + 1 ? 1.0f : ((i > k + 1 && i < p) ? cl[i * lda] * scr : 0.f);
+                dt = fmaf(vk[b], x[b], dt);
             }
             dt = warp_sum(dt) * tau;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const int i = lane + 32 * b;
-                if (i > k && i < p) x[b] = fmaf(-dt, cl[i * lda], x[b]);
-            }
+            for (int b = 0; b < NB; ++b) x[b] = fmaf(-dt, vk[b], x[b]);
         }
         float best = -1.f;
         int bi = 0;
@@ -614,7 +685,7 @@ __global__ void weights_kernel(const double* __restrict__ V, const double* __res
 }
 
 size_t eig_fast_bytes(int p, int r) {
-    return ((size_t)p * (p + 1) + 6 * (size_t)p + 64 + 32 + 32 + 3 * (size_t)p * r) *
+    return ((size_t)p * (p + 1) + 7 * (size_t)p + 64 + 32 + 32 + 3 * (size_t)p * r) *
            sizeof(float);
 }
 
