@@ -37,6 +37,30 @@ WORKLOAD = dict(H=349, W=1905, p=144, m=12, snr_db=10.0, seed=2, levels=5, r_max
 L2_BYTES = 129 * 1024 * 1024
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FMA/clk x 2 x max clock
 PAPER_A100_MVOXEL_S = 302.0   # 95.7 Mvoxel / 0.317 s (HyRes, A100, FP32, Houston 20 dB)
+FP32_SM_PEAK_TFLOPS = 128 * 2 * 2.070e9 / 1e12         # one SM, for single-block kernels
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, from one ncu capture of the 349 x 1905 x 144 cube; keyed by
+# (stage, precision). profiles/ holds the capture summaries; an entry is
+# removed when its kernel changes.
+NCU_TRAFFIC: dict = {
+    # gram_partial 390.01 + 5.38 MB, gram_reduce 13.48 MB
+    ("gram", "fp32"): 408.87e6,
+    # gram_tc 385.74 + 3.75 MB, gram_tc_reduce 8.27 MB
+    ("gram", "bf16x3"): 397.76e6,
+    # eig_fast (one thread block) 0.25 MB
+    ("eig", "fp32"): 0.25e6,
+    ("eig", "bf16x3"): 0.25e6,
+}
+
+
+def _small_dense_flops(stage: str, p: int, r: int) -> float:
+    """Algorithmic flops of the single-block stages: Householder
+    tridiagonalisation 4p^3/3 + back-transformation of r vectors 4p^2 r
+    (eig); Gauss-Jordan inverse 2p^3 (noise)."""
+    if stage == "eig":
+        return 4.0 * p ** 3 / 3.0 + 4.0 * p * p * r
+    return 2.0 * p ** 3
 
 
 def _measured_peaks() -> dict:
@@ -265,7 +289,7 @@ def run_gb300(args) -> None:
         achieved = flops / (stage_avg["gram"] / 1e3) / 1e12
         roofline = {"kernel": "gram_tc (tcgen05 split-BF16) + reduce", "bound": "tensor",
                     "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": achieved / tc_peak, "traffic": None,
+                    "frac": achieved / tc_peak,
                     "peak_source": peaks["source"] + " bf16 dense (burst)",
                     "algorithmic": f"{flops:.4g} flop per launch (3 products of 2np^2)"}
     elif dominant == "gram":
@@ -273,7 +297,7 @@ def run_gb300(args) -> None:
         achieved = flops / (stage_avg["gram"] / 1e3) / 1e12
         roofline = {"kernel": "gram (gram_partial + gram_reduce)", "bound": "alu",
                     "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS,
                     "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz",
                     "algorithmic": f"{flops:.4g} flop per launch"}
     elif dominant in sbytes:
@@ -281,12 +305,23 @@ def run_gb300(args) -> None:
         achieved = bts / (stage_avg[dominant] / 1e3) / 1e9
         roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "frac": achieved / peaks["hbm_gbs"],
                     "peak_source": peaks["source"],
                     "algorithmic": f"{bts} bytes per launch"}
     else:
-        roofline = {"kernel": dominant, "bound": "latency", "achieved": None, "peak": None,
-                    "unit": None, "frac": None, "traffic": None}
+        # eig / noise: one thread block by construction (a p x p problem),
+        # bound by the dependent chain of its p steps, so the ceiling that
+        # applies is one SM's FP32 rate; the whole-GPU fraction is also given
+        flops = _small_dense_flops(dominant, p, w["r_max"])
+        achieved = flops / (stage_avg[dominant] / 1e3) / 1e12
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved,
+                    "peak": FP32_SM_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_SM_PEAK_TFLOPS,
+                    "frac_of_gpu": achieved / FP32_SIMT_PEAK_TFLOPS,
+                    "peak_source": "derived: 1 SM x 128 FP32 FMA/clk x 2 x 2070 MHz "
+                                   "(single-block kernel)",
+                    "algorithmic": f"{flops:.4g} flop per launch"}
+    roofline["traffic"] = NCU_TRAFFIC.get((dominant, args.precision))
     hbm_stages = {}
     for k, bts in sbytes.items():
         gbs = bts / (stage_avg[k] / 1e3) / 1e9
