@@ -23,10 +23,15 @@
 
 #include "hyde_internal.cuh"
 
+#ifndef HYDE_EIG_WARPS
+#define HYDE_EIG_WARPS 16
+#endif
+
 namespace hyde {
 namespace {
 
 constexpr int kLA = 1024;     // threads of the single-block kernels
+constexpr int kEigWarps = HYDE_EIG_WARPS;   // warps of the tridiagonalisation
 constexpr int kMaxRegT = 6;   // register tiles up to 6 x 6 (p <= 192)
 
 // --------------------------------------------------------------------------
@@ -237,6 +242,49 @@ struct EigTail {
     float* dots;
 };
 
+// Barrier among warps 0..NW-1 only (named barrier 1); the other warps of the
+// block do not take part and wait at the next __syncthreads.
+template <int NW>
+__device__ __forceinline__ void bar_sync_warps() {
+    if (NW == 32) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"n"(NW * 32) : "memory");
+}
+
+// Warp sums of NB <= 32 per-lane values at once (reduce-scatter): the
+// values are padded to G = 1, 2, 4, ..., 32 slots; each butterfly level with G > 1 slots
+// left sends half of them to the partner lane and keeps the other half, so
+// sum a is complete after ~G + 4 shuffles instead of 5 NB. Returns the total
+// of value `a` (set on return) in every lane; lanes with the same a form
+// groups of 32/G consecutive lanes.
+__host__ __device__ constexpr int rows_groups(int nb) {
+    return nb <= 1 ? 1 : nb <= 2 ? 2 : nb <= 4 ? 4 : nb <= 8 ? 8 : nb <= 16 ? 16 : 32;
+}
+
+template <int NB>
+__device__ __forceinline__ float rows_reduce_scatter(const float (&s)[NB], int lane, int& a) {
+    constexpr int G = rows_groups(NB);
+    float x[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) x[q] = q < NB ? s[q] : 0.f;
+    int idx = 0, off = 16;
+#pragma unroll
+    for (int half = G / 2; half >= 1; half >>= 1) {
+        const bool hi = (lane & off) != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            const float send = hi ? x[q] : x[q + half];
+            const float keep = hi ? x[q + half] : x[q];
+            x[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+        if (hi) idx += half;
+        off >>= 1;
+    }
+    float v = x[0];
+    for (; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    a = idx;
+    return v;
+}
+
 __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int p,
                                            float x, float pivmin) {
     float q = d[0] - x;
@@ -250,7 +298,8 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
 }
 
 // Stages 2-5 on the tridiagonal (d, e) in shared memory; all 1024 threads.
-__device__ void eig_tail_stages234(const EigTail& S, int p, int r, int* status) {
+template <int NBV>
+__device__ __forceinline__ void eig_tail_stages234(const EigTail& S, int p, int r, int* status) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int i = t; i < p; i += blockDim.x) {
         S.e2[i] = S.e[i] * S.e[i];
@@ -309,23 +358,23 @@ __device__ void eig_tail_stages234(const EigTail& S, int p, int r, int* status) 
         float* Dm = S.Dm + wid * p;
         float* z = S.X + wid * p;
         const float pm = s_pivmin;
-        if (lane == 0) {
-            float q = S.d[0] - lam;
+        // the two factorisations run in lockstep in lanes 0 (L D L^T from the
+        // top) and 1 (U D U^T from the bottom): one instruction stream, no
+        // divergent branches
+        if (lane < 2) {
+            const bool fwd = lane == 0;
+            float* D = fwd ? Dp : Dm;
+            int i = fwd ? 0 : p - 1;
+            const int step = fwd ? 1 : -1;
+            float q = S.d[i] - lam;
             if (fabsf(q) < pm) q = -pm;
-            Dp[0] = q;
-            for (int i = 1; i < p; ++i) {
-                q = (S.d[i] - lam) - __fdividef(S.e2[i - 1], q);
+            D[i] = q;
+            for (int s2 = 1; s2 < p; ++s2) {
+                i += step;
+                const float e2 = S.e2[fwd ? i - 1 : i];
+                q = (S.d[i] - lam) - __fdividef(e2, q);
                 if (fabsf(q) < pm) q = -pm;
-                Dp[i] = q;
-            }
-        } else if (lane == 1) {
-            float q = S.d[p - 1] - lam;
-            if (fabsf(q) < pm) q = -pm;
-            Dm[p - 1] = q;
-            for (int i = p - 2; i >= 0; --i) {
-                q = (S.d[i] - lam) - __fdividef(S.e2[i], q);
-                if (fabsf(q) < pm) q = -pm;
-                Dm[i] = q;
+                D[i] = q;
             }
         }
         __syncwarp();
@@ -342,13 +391,24 @@ __device__ void eig_tail_stages234(const EigTail& S, int p, int r, int* status) 
             if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
         const int kt = bi;
-        if (lane == 0) {
-            z[kt] = 1.0f;
+        // z from the twist outwards, lane 0 upwards (rows kt-1..0, from L D L^T)
+        // and lane 1 downwards (rows kt+1..p-1, from U D U^T), in lockstep
+        if (lane < 2) {
+            const bool up = lane == 0;
+            const int len = up ? kt : p - 1 - kt;
+            const int steps = max(kt, p - 1 - kt);
+            if (up) z[kt] = 1.0f;
+            int i = kt;
             float zz = 1.0f;
-            for (int i = kt - 1; i >= 0; --i) { zz = -__fdividef(S.e[i], Dp[i]) * zz; z[i] = zz; }
-        } else if (lane == 1) {
-            float zz = 1.0f;
-            for (int i = kt + 1; i < p; ++i) { zz = -__fdividef(S.e[i - 1], Dm[i]) * zz; z[i] = zz; }
+            for (int s2 = 0; s2 < steps; ++s2) {
+                if (s2 < len) {
+                    i += up ? -1 : 1;
+                    const float num = S.e[up ? i : i - 1];
+                    const float den = up ? Dp[i] : Dm[i];
+                    zz = -__fdividef(num, den) * zz;
+                    z[i] = zz;
+                }
+            }
         }
         __syncwarp();
         float ss = 0.f;
@@ -420,7 +480,7 @@ __device__ __forceinline__ float hh_coef(const float* A, int lda, int p, int kr,
 // warp shuffle-sum per warp. The back-transformation keeps each eigenvector
 // in registers (lane l holds entries l + 32b).
 // --------------------------------------------------------------------------
-template <int NB>
+template <int NB, int NW>
 __global__ void __launch_bounds__(kLA, 1)
 eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p, int r,
                 double* __restrict__ evals, double* __restrict__ V, int* status) {
@@ -467,13 +527,16 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     __syncthreads();
 
     // Fused steps. Reflector k is kept as (column k of A, scale sc_k):
-    // v_k[i] = 1 at i = k+1, A[i][k] sc_k beyond. Per step: K from the block
-    // partials; the owner lanes update column k+1 and sum the squares of its
-    // entries below k+2; after one barrier every thread forms reflector k+1's
-    // scalars itself; then one sweep over the trailing matrix applies update
-    // k and accumulates p' = A' v_{k+1} of step k+1 from the new values. Two
+    // v_k[i] = 1 at i = k+1, A[i][k] sc_k beyond. Per step: K = tau/2 v^T p
+    // in every warp from p in shared memory; the owner lanes update column
+    // k+1 and sum the squares of its entries below k+2; after one barrier
+    // every warp forms reflector k+1's scalars itself; then one sweep over
+    // the trailing matrix applies update k and accumulates p' = A' v_{k+1} of
+    // step k+1 from the new values (row sums by a reduce-scatter). Two
     // barriers per step, one read and one write of each trailing element.
     float* const scv = vf;           // reflector scales (vf is free after the load)
+    constexpr int NA = (32 * NB + NW - 1) / NW;   // trailing rows per warp
+    if (wid < NW) {
     // prologue: reflector 0 (scalars in every warp) and p_0 = tau_0 A v_0
     float tau_k = 0.f, sc_k = 0.f;
     float vreg[NB];
@@ -486,11 +549,11 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
         if (t == 0) { tauv[0] = tau_k; scv[0] = sc_k; dv[0] = A[0]; ev[0] = beta; }
 #pragma unroll
         for (int b = 0; b < NB; ++b) vreg[b] = hh_coef(A, lda, p, 0, sc_k, lane + 32 * b);
-        const int i0 = 1 + ((wid - 1) & 31);
-        float sacc[NB];
+        const int i0 = 1 + ((wid - 1) & (NW - 1));
+        float sacc[NA];
 #pragma unroll
-        for (int a = 0; a < NB; ++a) {
-            const int i = i0 + 32 * a;
+        for (int a = 0; a < NA; ++a) {
+            const int i = i0 + NW * a;
             sacc[a] = 0.f;
             if (i < p) {
                 const float* row = A + i * lda;
@@ -501,59 +564,65 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
                 }
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int a = 0; a < NB; ++a) sacc[a] += __shfl_xor_sync(0xffffffffu, sacc[a], o);
-        float kpart = 0.f;
-#pragma unroll
-        for (int a = 0; a < NB; ++a) {
-            const int i = i0 + 32 * a;
-            if (i < p) {
-                const float pi = sacc[a] * tau_k;
-                if (lane == a) pvv[i] = pi;
-                kpart = fmaf(pi, hh_coef(A, lda, p, 0, sc_k, i), kpart);
-            }
-        }
-        if (lane == 0) red[wid] = kpart;
+        int a_own;
+        const float tot = rows_reduce_scatter<NA>(sacc, lane, a_own);
+        const int i = i0 + NW * a_own;
+        if (a_own < NA && (lane & (32 / rows_groups(NA) - 1)) == 0 && i < p) pvv[i] = tot * tau_k;
     }
-    __syncthreads();
+    bar_sync_warps<NW>();
     for (int k = 0; k + 2 < p; ++k) {
         const float* pc = pvv + (k & 1) * p;
         float* pn = pvv + ((k + 1) & 1) * p;
         const bool has_next = k + 4 <= p;
-        const float K = 0.5f * tau_k * warp_sum(red[lane]);
-        float wreg[NB];
+        // K = tau/2 v^T p and w = p - K v (v_k, p_k nonzero on rows > k)
+        float pj[NB];
+        float kp = 0.f;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int j = lane + 32 * b;
-            wreg[b] = (j > k && j < p) ? fmaf(-K, vreg[b], pc[j]) : 0.f;
+            pj[b] = (j > k && j < p) ? pc[j] : 0.f;
+            kp = fmaf(vreg[b], pj[b], kp);
         }
-        const int i0 = k + 1 + ((wid - (k + 1)) & 31);
+        const float K = 0.5f * tau_k * warp_sum(kp);
+        float wreg[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) wreg[b] = fmaf(-K, vreg[b], pj[b]);
+        const int i0 = k + 1 + ((wid - (k + 1)) & (NW - 1));
         // column k+1 (owner lane of each warp) and the squares for reflector k+1
         const int jn = k + 1;
-        float ssp = 0.f;
         if (lane == (jn & 31)) {
-            const float wjn = pc[jn] - K;
+            const float wjn = pc[jn] - K;          // v_k[jn] = 1
+            float ssp = 0.f;
 #pragma unroll
-            for (int a = 0; a < NB; ++a) {
-                const int i = i0 + 32 * a;
-                if (i < p) {
-                    const float vi = hh_coef(A, lda, p, k, sc_k, i), wi = fmaf(-K, vi, pc[i]);
-                    float* e = A + i * lda + jn;          // v_k[jn] = 1
-                    const float x = fmaf(-vi, wjn, *e - wi);
-                    *e = x;
-                    if (i >= k + 3) ssp = fmaf(x, x, ssp);
+            for (int a0 = 0; a0 < NA; a0 += 4) {   // loads of 4 rows before their stores
+                float vi[4], pi[4], e[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + NW * (a0 + u);
+                    const bool ok = a0 + u < NA && i < p;
+                    vi[u] = ok ? hh_coef(A, lda, p, k, sc_k, i) : 0.f;
+                    pi[u] = ok ? pc[i] : 0.f;
+                    e[u] = ok ? A[i * lda + jn] : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + NW * (a0 + u);
+                    if (a0 + u < NA && i < p) {
+                        const float x = fmaf(-vi[u], wjn, e[u] - fmaf(-K, vi[u], pi[u]));
+                        A[i * lda + jn] = x;
+                        if (i >= k + 3) ssp = fmaf(x, x, ssp);
+                    }
                 }
             }
             red[32 + wid] = ssp;
         }
-        __syncthreads();
+        bar_sync_warps<NW>();
         float tau_n = 0.f, sc_n = 0.f;
         float vn[NB];
         if (has_next) {
             float beta;
-            hh_scalars(A, lda, k + 1, warp_sum(red[32 + lane]), tau_n, sc_n, beta);
+            hh_scalars(A, lda, k + 1, warp_sum(lane < NW ? red[32 + lane] : 0.f), tau_n, sc_n,
+                       beta);
             if (t == 0) {
                 tauv[k + 1] = tau_n; scv[k + 1] = sc_n;
                 dv[k + 1] = A[(k + 1) * lda + (k + 1)]; ev[k + 1] = beta;
@@ -565,47 +634,49 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
             for (int b = 0; b < NB; ++b) vn[b] = 0.f;
         }
         // fused sweep: update k on rows > k+1, columns > k+1; accumulate p' rows
-        float sacc[NB];
+        // Columns j <= k have v = w = 0 and are rewritten unchanged; column
+        // k+1 was updated by its owner lane and is not stored again; only the
+        // last column block can reach past p (p > 32 (NB - 1)).
+        float sacc[NA];
 #pragma unroll
-        for (int a = 0; a < NB; ++a) {
-            const int i = i0 + 32 * a;
+        for (int a = 0; a < NA; ++a) {
+            const int i = i0 + NW * a;
             sacc[a] = 0.f;
             if (i > k + 1 && i < p) {
                 float* row = A + i * lda;
-                const float vi = hh_coef(A, lda, p, k, sc_k, i), wi = fmaf(-K, vi, pc[i]);
+                const float vi = row[k] * sc_k, wi = fmaf(-K, vi, pc[i]);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     const int j = lane + 32 * b;
-                    if (j > k + 1 && j < p) {
+                    if (b < NB - 1 || j < p) {
                         const float x = fmaf(-vi, wreg[b], fmaf(-wi, vreg[b], row[j]));
-                        row[j] = x;
+                        if (j != k + 1) row[j] = x;
                         sacc[a] = fmaf(x, vn[b], sacc[a]);
                     }
                 }
             }
         }
         if (has_next) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int a = 0; a < NB; ++a) sacc[a] += __shfl_xor_sync(0xffffffffu, sacc[a], o);
-            float kpart = 0.f;
-#pragma unroll
-            for (int a = 0; a < NB; ++a) {
-                const int i = i0 + 32 * a;
-                if (i > k + 1 && i < p) {
-                    const float pi = sacc[a] * tau_n;
-                    if (lane == a) pn[i] = pi;
-                    kpart = fmaf(pi, hh_coef(A, lda, p, k + 1, sc_n, i), kpart);
-                }
-            }
-            if (lane == 0) red[wid] = kpart;
+            int a_own;
+            const float tot = rows_reduce_scatter<NA>(sacc, lane, a_own);
+            const int i = i0 + NW * a_own;
+            if (a_own < NA && (lane & (32 / rows_groups(NA) - 1)) == 0 && i > k + 1 && i < p)
+                pn[i] = tot * tau_n;
         }
         tau_k = tau_n;
         sc_k = sc_n;
 #pragma unroll
         for (int b = 0; b < NB; ++b) vreg[b] = vn[b];
-        __syncthreads();
+        bar_sync_warps<NW>();
+    }
+    }   // wid < NW
+    __syncthreads();
+    // reflector k as an explicit vector in column k: 0 above row k+1, 1 at
+    // k+1, x * scale below (the back-transformation then reads it directly)
+    for (int e = t; e < p * (p - 2 > 0 ? p - 2 : 0); e += blockDim.x) {
+        const int i = e / (p - 2), k = e - i * (p - 2);
+        float* a = A + i * lda + k;
+        *a = i <= k ? 0.f : (i == k + 1 ? 1.0f : *a * scv[k]);
     }
     if (t == 0) {
         if (p >= 2) {
@@ -618,7 +689,7 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     }
     __syncthreads();
     EigTail tail{dv, ev, e2v, tauv, lamv, X, Dp, Dm, dots};
-    eig_tail_stages234(tail, p, r, status);
+    eig_tail_stages234<NB>(tail, p, r, status);
     // 5. back-transformation with the vector in registers, one warp per vector
     if (wid < r) {
         float x[NB];
@@ -627,19 +698,34 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
             const int i = lane + 32 * b;
             x[b] = i < p ? X[wid * p + i] : 0.f;
         }
-        for (int k = p - 3; k >= 0; --k) {
-            const float tau = tauv[k];
-            if (tau == 0.f) continue;
-            const float* cl = A + k;          // column k; v_k[i] = cl[i * lda] * sc (i > k+1)
-            const float scr = vf[k];
-            float vk[NB];
-            float dt = 0.f;
+        // reflector k is column k of A (explicit); the next reflector's tau
+        // and column are loaded while this one's warp sum runs
+        float tau_c = 0.f, col[NB];
+        if (p >= 3) {
+            tau_c = tauv[p - 3];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const int i = lane + 32 * b;
-                vk[b] = i == k + 1 ? 1.0f : ((i > k + 1 && i < p) ? cl[i * lda] * scr : 0.f);
-                dt = fmaf(vk[b], x[b], dt);
+                col[b] = (b < NB - 1 || i < p) ? A[i * lda + (p - 3)] : 0.f;
             }
+        }
+        for (int k = p - 3; k >= 0; --k) {
+            const float tau = tau_c;
+            float vk[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) vk[b] = col[b];
+            if (k > 0) {
+                tau_c = tauv[k - 1];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int i = lane + 32 * b;
+                    col[b] = (b < NB - 1 || i < p) ? A[i * lda + (k - 1)] : 0.f;
+                }
+            }
+            if (tau == 0.f) continue;
+            float dt = 0.f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) dt = fmaf(vk[b], x[b], dt);
             dt = warp_sum(dt) * tau;
 #pragma unroll
             for (int b = 0; b < NB; ++b) x[b] = fmaf(-dt, vk[b], x[b]);
@@ -736,9 +822,10 @@ hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, do
     switch (NB) {
 #define HYDE_EIG(NBV)                                                                          \
     case NBV:                                                                                  \
-        if (ensure_smem_limit((const void*)eig_fast_kernel<NBV>, (int)smem) != cudaSuccess)    \
+        if (ensure_smem_limit((const void*)eig_fast_kernel<NBV, kEigWarps>, (int)smem) !=      \
+            cudaSuccess)    \
             return HYDE_ERR_SHAPE;                                                             \
-        eig_fast_kernel<NBV><<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);           \
+        eig_fast_kernel<NBV, kEigWarps><<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);           \
         break;
         HYDE_EIG(1) HYDE_EIG(2) HYDE_EIG(3) HYDE_EIG(4)
         HYDE_EIG(5) HYDE_EIG(6) HYDE_EIG(7) HYDE_EIG(8)

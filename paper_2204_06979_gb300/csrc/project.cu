@@ -4,21 +4,56 @@
 //   Z_i(pixel) = sum_b Y_b(pixel) P[b][i],  P = D^-1 V   (D = diag(sigma))
 //   X_b(pixel) = sum_{i < r*} Q[b][i] Zh_i(pixel),  Q = D V
 // Both are skinny contractions (<= 32 outputs or inputs per pixel) at about
-// the FP32/HBM balance point, so they stay on the FP32 pipes: one thread per
-// pixel, weights in shared memory read as broadcast float4, the cube streamed
-// band by band with coalesced accesses. The projection keeps 8 bands of loads
-// in flight per thread and writes straight into the padded H_p x W_p
+// the FP32/HBM balance point, so they stay on the FP32 pipes, with weights in
+// shared memory read as broadcast float4 and the cube streamed band by band
+// with coalesced accesses. The projection takes two pixels per thread (one
+// weight load feeds eight FMAs), keeps two groups of 8 bands x 2 pixels of
+// loads in flight per thread and writes straight into the padded H_p x W_p
 // component images (whole-sample symmetric reflection at the bottom/right),
-// so the DWT never sees an unpadded image. The back-projection unrolls to
-// ceil(r*/4)*4 terms, r* read on the device.
+// so the DWT never sees an unpadded image. The back-projection (one pixel per
+// thread) unrolls to ceil(r*/4)*4 terms, r* read on the device.
 #include "hyde_internal.cuh"
 
 namespace hyde {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 constexpr int kBandGroup = 8;
+constexpr int kPix = 2;   // pixels per thread: each broadcast weight feeds kPix FMAs
+// The back-projection is bound by its stores (one per band and pixel):
+// one pixel per thread and 256-thread blocks keep more warps resident.
+constexpr int kBpThreads = 256;
 
+// Source address of padded pixel pix (whole-sample reflection at the bottom
+// and right edges); false for a padding pixel that is zero-filled instead.
+__device__ __forceinline__ bool padded_source(long long pix, int H, int W, int Wp,
+                                              int zero_pad, long long& src) {
+    int y = (int)(pix / Wp), x = (int)(pix - (long long)(pix / Wp) * Wp);
+    if (zero_pad && (y >= H || x >= W)) { src = 0; return false; }
+    if (y >= H) y = 2 * H - 2 - y;
+    if (x >= W) x = 2 * W - 2 - x;
+    src = (long long)y * W + x;
+    return true;
+}
+
+template <int RM>
+__device__ __forceinline__ void project_fma(float (&acc)[kPix][RM], const float (&v)[kPix],
+                                            const float4* __restrict__ w4) {
+#pragma unroll
+    for (int q = 0; q < RM / 4; ++q) {
+        const float4 w = w4[q];
+#pragma unroll
+        for (int u = 0; u < kPix; ++u) {
+            acc[u][4 * q + 0] = fmaf(v[u], w.x, acc[u][4 * q + 0]);
+            acc[u][4 * q + 1] = fmaf(v[u], w.y, acc[u][4 * q + 1]);
+            acc[u][4 * q + 2] = fmaf(v[u], w.z, acc[u][4 * q + 2]);
+            acc[u][4 * q + 3] = fmaf(v[u], w.w, acc[u][4 * q + 3]);
+        }
+    }
+}
+
+// Each thread projects kPix pixels (pix and pix + kThreads of its block's
+// tile); the loads of band group g+1 are issued before the FMAs of group g.
 template <int RM>
 __global__ void __launch_bounds__(kThreads)
 project_pad_kernel(const float* __restrict__ Y, int p, int H, int W,
@@ -29,54 +64,61 @@ project_pad_kernel(const float* __restrict__ Y, int p, int H, int W,
     for (int e = threadIdx.x; e < p * RM; e += kThreads) Ps[e] = P[e];
     __syncthreads();
     const long long N = (long long)Hp * Wp, n = (long long)H * W;
-    for (long long pix = (long long)blockIdx.x * kThreads + threadIdx.x; pix < N;
-         pix += (long long)gridDim.x * kThreads) {
-        int y = (int)(pix / Wp), x = (int)(pix - (long long)(pix / Wp) * Wp);
-        if (zero_pad && (y >= H || x >= W)) {
+    const long long tile = (long long)kThreads * kPix;
+    for (long long base = (long long)blockIdx.x * tile; base < N;
+         base += (long long)gridDim.x * tile) {
+        long long src[kPix];
+        bool live[kPix], data[kPix];
+#pragma unroll
+        for (int u = 0; u < kPix; ++u) {
+            const long long pix = base + threadIdx.x + (long long)u * kThreads;
+            live[u] = pix < N;
+            data[u] = live[u] && padded_source(pix, H, W, Wp, zero_pad, src[u]);
+            if (!data[u]) src[u] = 0;           // a valid address; the result is dropped
+        }
+        float acc[kPix][RM];
+#pragma unroll
+        for (int u = 0; u < kPix; ++u)
+#pragma unroll
+            for (int i = 0; i < RM; ++i) acc[u][i] = 0.f;
+        const int pg = p - p % kBandGroup;      // bands in whole groups
+        float v[kBandGroup][kPix];
+        if (pg > 0) {
+#pragma unroll
+            for (int g = 0; g < kBandGroup; ++g)
+#pragma unroll
+                for (int u = 0; u < kPix; ++u) v[g][u] = __ldg(Y + (long long)g * n + src[u]);
+        }
+        for (int b = 0; b < pg; b += kBandGroup) {
+            float nv[kBandGroup][kPix];
+            const int bn = b + kBandGroup < pg ? b + kBandGroup : b;   // last group: reload
+#pragma unroll
+            for (int g = 0; g < kBandGroup; ++g)
+#pragma unroll
+                for (int u = 0; u < kPix; ++u)
+                    nv[g][u] = __ldg(Y + (long long)(bn + g) * n + src[u]);
+#pragma unroll
+            for (int g = 0; g < kBandGroup; ++g)
+                project_fma<RM>(acc, v[g], Ps4 + (b + g) * (RM / 4));
+#pragma unroll
+            for (int g = 0; g < kBandGroup; ++g)
+#pragma unroll
+                for (int u = 0; u < kPix; ++u) v[g][u] = nv[g][u];
+        }
+        for (int b = pg; b < p; ++b) {
+            float vt[kPix];
+#pragma unroll
+            for (int u = 0; u < kPix; ++u) vt[u] = __ldg(Y + (long long)b * n + src[u]);
+            project_fma<RM>(acc, vt, Ps4 + b * (RM / 4));
+        }
+#pragma unroll
+        for (int u = 0; u < kPix; ++u) {
+            if (!live[u]) continue;
+            const long long pix = base + threadIdx.x + (long long)u * kThreads;
 #pragma unroll
             for (int i = 0; i < RM; ++i)
-                if (i < r) Zp[(long long)i * N + pix] = 0.f;
-            continue;
+                if (i < r) Zp[(long long)i * N + pix] = data[u] ? acc[u][i] : 0.f;
         }
-        if (y >= H) y = 2 * H - 2 - y;
-        if (x >= W) x = 2 * W - 2 - x;
-        const float* yp = Y + (long long)y * W + x;
-        float acc[RM];
-#pragma unroll
-        for (int i = 0; i < RM; ++i) acc[i] = 0.f;
-        int b = 0;
-        for (; b + kBandGroup <= p; b += kBandGroup) {
-            float v[kBandGroup];
-#pragma unroll
-            for (int u = 0; u < kBandGroup; ++u) v[u] = __ldg(yp + (long long)(b + u) * n);
-#pragma unroll
-            for (int u = 0; u < kBandGroup; ++u) {
-                const float4* w4 = Ps4 + (b + u) * (RM / 4);
-#pragma unroll
-                for (int q = 0; q < RM / 4; ++q) {
-                    const float4 w = w4[q];
-                    acc[4 * q + 0] = fmaf(v[u], w.x, acc[4 * q + 0]);
-                    acc[4 * q + 1] = fmaf(v[u], w.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(v[u], w.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(v[u], w.w, acc[4 * q + 3]);
-                }
-            }
-        }
-        for (; b < p; ++b) {
-            const float v = __ldg(yp + (long long)b * n);
-            const float4* w4 = Ps4 + b * (RM / 4);
-#pragma unroll
-            for (int q = 0; q < RM / 4; ++q) {
-                const float4 w = w4[q];
-                acc[4 * q + 0] = fmaf(v, w.x, acc[4 * q + 0]);
-                acc[4 * q + 1] = fmaf(v, w.y, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(v, w.z, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(v, w.w, acc[4 * q + 3]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < RM; ++i)
-            if (i < r) Zp[(long long)i * N + pix] = acc[i];
     }
 }
 
@@ -104,17 +146,17 @@ __device__ __forceinline__ void backproject_pixel(const float* __restrict__ Zh, 
 }
 
 template <int RM>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kBpThreads)
 backproject_kernel(const float* __restrict__ Zh, long long n, const float* __restrict__ Q,
                    int p, const int* __restrict__ rank, float* __restrict__ X) {
     extern __shared__ float4 Qs4[];
     float* Qs = reinterpret_cast<float*>(Qs4);
-    for (int e = threadIdx.x; e < p * RM; e += kThreads) Qs[e] = Q[e];
+    for (int e = threadIdx.x; e < p * RM; e += kBpThreads) Qs[e] = Q[e];
     __syncthreads();
     const int r = min(*rank, RM);
     const int groups = (r + 3) / 4;
-    for (long long pix = (long long)blockIdx.x * kThreads + threadIdx.x; pix < n;
-         pix += (long long)gridDim.x * kThreads) {
+    for (long long pix = (long long)blockIdx.x * kBpThreads + threadIdx.x; pix < n;
+         pix += (long long)gridDim.x * kBpThreads) {
         switch (groups) {
 #define HYDE_BP_CASE(G) \
     case G: if (4 * G <= RM) backproject_pixel<4 * G, RM>(Zh, n, Qs4, p, r, pix, X); break;
@@ -126,13 +168,17 @@ backproject_kernel(const float* __restrict__ Zh, long long n, const float* __res
     }
 }
 
-int grid_for(long long items, int per_block, int blocks_per_sm) {
-    int sms = device_sm_count();
-    long long need = (items + per_block - 1) / per_block;
-    long long cap = (long long)sms * blocks_per_sm;
-    if (need > cap) need = cap;
-    if (need < 1) need = 1;
-    return (int)need;
+// Grid of a grid-stride kernel: the blocks that fit on the device at once
+// (occupancy of this kernel at this shared-memory size), fewer if the work
+// has fewer tiles; small tiles (256 pixels) keep the last wave short.
+int resident_grid(const void* func, int threads, size_t smem, long long tiles) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    long long cap = (long long)device_sm_count() * per_sm;
+    if (tiles < cap) cap = tiles;
+    return cap < 1 ? 1 : (int)cap;
 }
 
 }  // namespace
@@ -141,7 +187,7 @@ hyde_status launch_project_pad(const float* Y, int p, int H, int W, const float*
                                int ldw, float* Zp, int Hp, int Wp, cudaStream_t s,
                                bool zero_pad) {
     const long long N = (long long)Hp * Wp;
-    const int grid = grid_for(N, kThreads, 8);
+    const long long tiles = (N + kThreads * kPix - 1) / (kThreads * kPix);
     const size_t smem = (size_t)p * ldw * sizeof(float);
     if (smem > 227 * 1024) return HYDE_ERR_SHAPE;
     switch (ldw) {
@@ -149,8 +195,10 @@ hyde_status launch_project_pad(const float* Y, int p, int H, int W, const float*
     case RMV:                                                                                  \
         if (ensure_smem_limit((const void*)project_pad_kernel<RMV>, (int)smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                              \
-        project_pad_kernel<RMV><<<grid, kThreads, smem, s>>>(Y, p, H, W, P, r, Zp, Hp, Wp, \
-                                                             zero_pad ? 1 : 0);                 \
+        project_pad_kernel<RMV><<<resident_grid((const void*)project_pad_kernel<RMV>,          \
+                                                kThreads, smem, tiles),                        \
+                                  kThreads, smem, s>>>(Y, p, H, W, P, r, Zp, Hp, Wp,           \
+                                                       zero_pad ? 1 : 0);                      \
         break;
         HYDE_PROJ(4) HYDE_PROJ(8) HYDE_PROJ(12) HYDE_PROJ(16)
         HYDE_PROJ(20) HYDE_PROJ(24) HYDE_PROJ(28) HYDE_PROJ(32)
@@ -163,7 +211,7 @@ hyde_status launch_project_pad(const float* Y, int p, int H, int W, const float*
 hyde_status launch_backproject(const float* Zh, long long n, const float* Q, int p, int r_max,
                                int ldw, const int* rank, float* X, cudaStream_t s) {
     (void)r_max;
-    const int grid = grid_for(n, kThreads, 8);
+    const long long tiles = (n + kBpThreads - 1) / kBpThreads;
     const size_t smem = (size_t)p * ldw * sizeof(float);
     if (smem > 227 * 1024) return HYDE_ERR_SHAPE;
     switch (ldw) {
@@ -171,7 +219,9 @@ hyde_status launch_backproject(const float* Zh, long long n, const float* Q, int
     case RMV:                                                                                  \
         if (ensure_smem_limit((const void*)backproject_kernel<RMV>, (int)smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                              \
-        backproject_kernel<RMV><<<grid, kThreads, smem, s>>>(Zh, n, Q, p, rank, X);            \
+        backproject_kernel<RMV><<<resident_grid((const void*)backproject_kernel<RMV>,          \
+                                                kBpThreads, smem, tiles),                      \
+                                  kBpThreads, smem, s>>>(Zh, n, Q, p, rank, X);                \
         break;
         HYDE_BACK(4) HYDE_BACK(8) HYDE_BACK(12) HYDE_BACK(16)
         HYDE_BACK(20) HYDE_BACK(24) HYDE_BACK(28) HYDE_BACK(32)
