@@ -5,9 +5,10 @@
 // one thread owns one tile of the upper triangle (PT(PT+1)/2 tiles for
 // PT = ceil(p/8)), so each thread does 64 FMAs per pixel from 16 float4
 // shared-memory loads. A block walks a contiguous range of 32-pixel chunks
-// through a 3-stage cp.async pipeline (a warp copies one band's 32
-// consecutive pixels) into a swizzled shared buffer, so that the 8 rows a
-// thread reads are spread over all 32 banks. Each block writes its float
+// through a 3-stage cp.async pipeline (each warp copies a fixed set of
+// bands, one band's 32 consecutive pixels per copy instruction) into a
+// swizzled shared buffer, so that the 8 rows a thread reads are spread over
+// all 32 banks. Each block writes its float
 // partial; a second kernel sums the partials in double and mirrors the
 // triangle.
 #include <mutex>
@@ -31,7 +32,6 @@ __device__ __forceinline__ void tile_of(int t, int PT, int& ti, int& tj) {
 
 // Shared layout: band b occupies one 128-byte row of 8 float4 (32 pixels);
 // logical float4 column q is stored at q ^ ((b >> 3) & 7).
-__device__ __forceinline__ int swz(int b, int q) { return b * 8 + (q ^ ((b >> 3) & 7)); }
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -61,18 +61,25 @@ gram_partial_kernel(const float* __restrict__ Y, int p, long long n, int PT,
     }
 
     const long long nchunks = (n + KC - 1) / KC;
-    const long long c0 = (long long)blockIdx.x * chunks_per_block;
-    const long long c1 = min(c0 + chunks_per_block, nchunks);
-    const int nelem = p * KC;
+    // even split: block b takes chunks [b N / G, (b + 1) N / G)
+    const long long c0 = (long long)blockIdx.x * nchunks / gridDim.x;
+    const long long c1 = (long long)(blockIdx.x + 1) * nchunks / gridDim.x;
+    (void)chunks_per_block;
 
+    // Copy of one chunk: warp w copies bands w, w + nw, ...; lane k copies
+    // pixel k of each (128 contiguous bytes per band), so the source pointer
+    // just advances by nw bands and the destination offset needs the band's
+    // swizzle only.
+    const int lane = t & 31, wrp = t >> 5, nw = T >> 5;
+    const int kq = lane >> 2, kr = lane & 3;
+    const long long bstride = (long long)nw * n;
     auto issue = [&](long long c, int st) {
         float* d = reinterpret_cast<float*>(sm4 + st * p8 * 8);
-        for (int e = t; e < nelem; e += T) {
-            const int b = e / KC, k = e % KC;
-            const long long pix = c * KC + k;
-            const bool ok = pix < n;
-            cp_async4(d + swz(b, k >> 2) * 4 + (k & 3), Y + (long long)b * n + (ok ? pix : 0), ok);
-        }
+        const long long pix = c * KC + lane;
+        const bool ok = pix < n;
+        const float* src = Y + (long long)wrp * n + (ok ? pix : 0);
+        for (int b = wrp; b < p; b += nw, src += bstride)
+            cp_async4(d + b * 32 + ((kq ^ ((b >> 3) & 7)) << 2) + kr, src, ok);
     };
 
     const bool active = t < ntiles;
@@ -97,15 +104,21 @@ gram_partial_kernel(const float* __restrict__ Y, int p, long long n, int PT,
         if (nxt < c1) issue(nxt, (int)(nxt - c0) % STAGES);
         cp_async_commit();
         if (active) {
+            // rows 8ti.. and 8tj.. of the stage; logical float4 column q sits
+            // at q ^ (ti & 7) and q ^ (tj & 7) respectively
             const float4* B = sm4 + ((int)(c - c0) % STAGES) * p8 * 8;
+            const float4* Ba = B + 64 * ti;
+            const float4* Bb = B + 64 * tj;
+            const int xa = ti & 7, xb = tj & 7;
 #pragma unroll 1
             for (int q = 0; q < 8; ++q) {
+                const int qa = q ^ xa, qb = q ^ xb;
                 float4 a[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) a[i] = B[swz(8 * ti + i, q)];
+                for (int i = 0; i < 8; ++i) a[i] = Ba[8 * i + qa];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float4 bv = B[swz(8 * tj + j, q)];
+                    const float4 bv = Bb[8 * j + qb];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         acc[i][j] = fmaf(a[i].x, bv.x, acc[i][j]);
@@ -186,7 +199,9 @@ hyde_status gram_plan(int p, long long n, GramPlan* plan) {
     g.threads = (g.ntiles + 31) / 32 * 32;
     if (g.threads > kGramMaxThreads) return HYDE_ERR_SHAPE;
     g.smem = (size_t)STAGES * g.PT * 8 * KC * sizeof(float);
-    hyde_status st = g.threads <= 256 ? plan_for<256>(g, n) : plan_for<kGramMaxThreads>(g, n);
+    hyde_status st = g.threads <= 256   ? plan_for<256>(g, n)
+                     : g.threads <= 384 ? plan_for<384>(g, n)
+                                        : plan_for<kGramMaxThreads>(g, n);
     if (st != HYDE_OK) return st;
     g.partial_bytes = (size_t)g.blocks * g.ntiles * 64 * sizeof(float);
     *plan = g;
@@ -199,6 +214,9 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
     long long per = (nchunks + g.blocks - 1) / g.blocks;
     if (g.threads <= 256)
         gram_partial_kernel<256><<<g.blocks, g.threads, g.smem, s>>>(Y, p, n, g.PT, g.ntiles,
+                                                                     per, partials);
+    else if (g.threads <= 384)
+        gram_partial_kernel<384><<<g.blocks, g.threads, g.smem, s>>>(Y, p, n, g.PT, g.ntiles,
                                                                      per, partials);
     else
         gram_partial_kernel<kGramMaxThreads><<<g.blocks, g.threads, g.smem, s>>>(

@@ -8,12 +8,13 @@
 // dropped), three tcgen05.mma kind::f16 (BF16 x BF16 -> FP32) per K step with
 // the accumulator in TMEM.
 //
-// One CTA per SM walks a contiguous range of 64-pixel chunks. Per chunk all
-// 8 warps load one band row each (a warp reads 64 consecutive pixels of one
-// band), split it and store hi and lo into the 128-byte-swizzled K-major
-// layout the UMMA shared-memory descriptors expect; one thread then issues
-// the MMAs of the chunk and commits them to the chunk's stage mbarrier, and
-// the stage is refilled only after that barrier flips. Rows of the
+// One CTA per SM walks a contiguous range of 64-pixel chunks through a ring
+// of shared-memory stages. Eight producer warps load the chunk (a warp reads
+// 64 consecutive pixels of a band), split it and store hi and lo into the
+// 128-byte-swizzled K-major layout the UMMA shared-memory descriptors
+// expect, then arrive on the stage's "full" mbarrier; a ninth warp waits on
+// it, issues the chunk's MMAs and commits them to the stage's "empty"
+// mbarrier, which the producers wait on before refilling the stage. Rows of the
 // accumulator: bands [0, 128) (M-tile 0, all N = Np columns) and, for
 // p > 128, bands [Np - 128, Np) against columns [128, Np) (M-tile 1). Each
 // CTA writes its float partial; a second kernel sums them in double.
@@ -28,7 +29,6 @@
 namespace hyde {
 namespace {
 
-constexpr int kTcThreads = 256;
 constexpr int kTcMaxStages = 4;
 constexpr int kChunk = 64;                      // pixels per chunk = one 128 B row of bf16
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s
@@ -136,54 +136,75 @@ struct TcPlan {
     size_t stage_bytes, smem;
 };
 
-// Chunk loads are double-buffered in registers: each thread holds RPW band
-// rows x 2 pixels of two chunks, so all of a chunk's loads are in flight
-// while the previous chunk is converted, stored and multiplied.
+// Producer warps 0..7 convert; warp 8 issues the MMAs. Each producer thread
+// owns band rows b = warp + 8q (q < RPW) and the pixel pair (2 lane,
+// 2 lane + 1) of every chunk, double-buffered in registers: chunk it + 2 is
+// loaded while chunk it is split and stored. All of a thread's rows share
+// b & 7 = warp, so in the 128-byte-swizzled layout row b sits at
+// q * 1024 + (a per-thread offset).
+constexpr int kProducerWarps = 8;
+constexpr int kTcThreadsWs = (kProducerWarps + 1) * 32;
+
 template <int RPW>
 struct ChunkRegs {
     float v[RPW][2];
 };
 
 template <int RPW>
-__device__ __forceinline__ void load_chunk(ChunkRegs<RPW>& R, const float* __restrict__ Y, int p,
-                                           long long n, long long chunk, int warp, int lane) {
-    const long long pix = chunk * kChunk + 2 * lane;
+__device__ __forceinline__ void load_chunk(ChunkRegs<RPW>& R, const float* __restrict__ yb,
+                                           long long bstride, int p, long long n,
+                                           long long pix, int warp) {
+    const bool full = pix + 1 < n;     // both pixels of the pair inside the cube
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-        const int b = warp + q * (kTcThreads / 32);
         float v0 = 0.f, v1 = 0.f;
-        if (b < p) {
-            const float* yr = Y + (long long)b * n;
-            if (pix < n) v0 = __ldg(yr + pix);
-            if (pix + 1 < n) v1 = __ldg(yr + pix + 1);
+        if (warp + kProducerWarps * q < p) {
+            const float* yr = yb + q * bstride;
+            if (full) {
+                v0 = __ldg(yr);
+                v1 = __ldg(yr + 1);
+            } else if (pix < n) {
+                v0 = __ldg(yr);
+            }
         }
         R.v[q][0] = v0;
         R.v[q][1] = v1;
     }
 }
 
+// hi = bf16(y) and lo = bf16(y - hi) for the pair, packed two per word
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
 template <int RPW>
 __device__ __forceinline__ void store_chunk(const ChunkRegs<RPW>& R, uint8_t* st, uint32_t half,
-                                            int p, int warp, int lane) {
+                                            uint32_t toff, int p, int warp) {
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-        const int b = warp + q * (kTcThreads / 32);
-        if (b < p) {
-            uint32_t lo;
-            const uint32_t hi = pack_bf16(R.v[q][0], R.v[q][1], &lo);
-            const uint32_t off = sw128_offset(b, lane);
-            *reinterpret_cast<uint32_t*>(st + off) = hi;
-            *reinterpret_cast<uint32_t*>(st + half + off) = lo;
+        if (warp + kProducerWarps * q < p) {
+            uint32_t hi, lo;
+            split_pair(R.v[q][0], R.v[q][1], hi, lo);
+            *reinterpret_cast<uint32_t*>(st + q * 1024 + toff) = hi;
+            *reinterpret_cast<uint32_t*>(st + half + q * 1024 + toff) = lo;
         }
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 template <int RPW>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreadsWs, 1)
 gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
                long long chunks_per_cta, float* __restrict__ partials, int* status) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t mbar[kTcMaxStages];
+    __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -192,63 +213,85 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - raw);
     const uint32_t half = (uint32_t)P.Np * 128u;   // hi tile, then lo tile
+    volatile int* abort_v = &abort_s;
 
     // zero every stage once: rows p..Np-1 stay zero
     const int S = P.stages;
-    for (size_t e = tid; e < (size_t)S * P.stage_bytes / 16; e += kTcThreads)
+    for (size_t e = tid; e < (size_t)S * P.stage_bytes / 16; e += kTcThreadsWs)
         reinterpret_cast<uint4*>(gbase)[e] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
-        for (int q = 0; q < S; ++q) mbar_init(smem_u32(&mbar[q]), 1);
+        for (int q = 0; q < S; ++q) {
+            mbar_init(smem_u32(&full_bar[q]), kProducerWarps * 32);
+            mbar_init(smem_u32(&empty_bar[q]), 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
     }
-    if (warp == 0) {
+    if (warp == kProducerWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_s)),
                      "r"((uint32_t)P.tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    // the zeroed stages are read by the tensor cores (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
 
     const long long nchunks = (n + kChunk - 1) / kChunk;
-    const long long c0 = (long long)blockIdx.x * chunks_per_cta;
-    const long long c1 = min(c0 + chunks_per_cta, nchunks);
+    // even split: block b takes chunks [b N / G, (b + 1) N / G)
+    const long long c0 = (long long)blockIdx.x * nchunks / gridDim.x;
+    const long long c1 = (long long)(blockIdx.x + 1) * nchunks / gridDim.x;
+    (void)chunks_per_cta;
     const long long iters = c1 > c0 ? c1 - c0 : 0;
-    const uint32_t id0 = idesc_bf16(128, P.Np);
-    const uint32_t id1 = idesc_bf16(128, P.n1 > 0 ? P.n1 : 16);
 
-    ChunkRegs<RPW> ra, rb;
-    if (iters > 0) load_chunk(ra, Y, p, n, c0, warp, lane);
-    if (iters > 1) load_chunk(rb, Y, p, n, c0 + 1, warp, lane);
-
-    long long issued = 0;   // iterations whose MMAs were committed
-    for (long long it = 0; it < iters; ++it) {
-        const int s = (int)(it % S);
-        const uint32_t sbase = base + (uint32_t)s * (uint32_t)P.stage_bytes;
-        if (it >= S) {
-            // the MMAs that last read this stage (iteration it - S) are done
-            const uint32_t par = (uint32_t)((it / S - 1) & 1);
-            if (!mbar_wait_bounded(smem_u32(&mbar[s]), par)) atomicExch(&abort_s, 1);
+    if (warp < kProducerWarps) {
+        // ---------------- producers
+        const uint32_t toff = (uint32_t)(warp * 128 + (((lane >> 2) ^ warp) << 4) +
+                                         ((lane & 3) << 2));
+        const long long bstride = (long long)kProducerWarps * n;
+        const float* yw = Y + (long long)warp * n + 2 * lane;
+        ChunkRegs<RPW> ra, rb;
+        if (iters > 0) load_chunk(ra, yw + c0 * kChunk, bstride, p, n, c0 * kChunk + 2 * lane, warp);
+        if (iters > 1)
+            load_chunk(rb, yw + (c0 + 1) * kChunk, bstride, p, n, (c0 + 1) * kChunk + 2 * lane,
+                       warp);
+        for (long long it = 0; it < iters; ++it) {
+            const int s = (int)(it % S);
+            if (it >= S) {
+                // the MMAs that last read this stage (iteration it - S) are done
+                const uint32_t par = (uint32_t)((it / S - 1) & 1);
+                if (!mbar_wait_bounded(smem_u32(&empty_bar[s]), par)) *abort_v = 1;
+            }
+            if (*abort_v) break;
+            uint8_t* st = gbase + (size_t)s * P.stage_bytes;
+            const long long cn = c0 + it + 2;
+            if ((it & 1) == 0) {
+                store_chunk(ra, st, half, toff, p, warp);
+                if (it + 2 < iters) load_chunk(ra, yw + cn * kChunk, bstride, p, n, cn * kChunk + 2 * lane, warp);
+            } else {
+                store_chunk(rb, st, half, toff, p, warp);
+                if (it + 2 < iters) load_chunk(rb, yw + cn * kChunk, bstride, p, n, cn * kChunk + 2 * lane, warp);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&full_bar[s]));
         }
-        __syncthreads();
-        if (abort_s) break;
-        uint8_t* st = gbase + (sbase - base);
-        // store chunk it, then reuse its registers for chunk it + 2
-        if ((it & 1) == 0) {
-            store_chunk(ra, st, half, p, warp, lane);
-            if (it + 2 < iters) load_chunk(ra, Y, p, n, c0 + it + 2, warp, lane);
-        } else {
-            store_chunk(rb, st, half, p, warp, lane);
-            if (it + 2 < iters) load_chunk(rb, Y, p, n, c0 + it + 2, warp, lane);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else if (lane == 0) {
+        // ---------------- MMA issuer (one thread)
+        const uint32_t id0 = idesc_bf16(128, P.Np);
+        const uint32_t id1 = idesc_bf16(128, P.n1 > 0 ? P.n1 : 16);
+        long long issued = 0;
+        for (long long it = 0; it < iters; ++it) {
+            const int s = (int)(it % S);
+            if (!mbar_wait_bounded(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1))) {
+                *abort_v = 1;
+                break;
+            }
+            if (*abort_v) break;
             tc_fence_after();
-            const uint32_t hi0 = sbase, lo0 = sbase + half;
+            const uint32_t hi0 = base + (uint32_t)s * (uint32_t)P.stage_bytes, lo0 = hi0 + half;
 #pragma unroll
             for (int kk = 0; kk < kChunk / 16; ++kk) {
                 const uint32_t ko = (uint32_t)kk * 32u;   // 16 bf16 along K
@@ -266,22 +309,21 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
                     umma_bf16(d1, sw128_desc(lo0 + ao + ko), sw128_desc(hi0 + bo + ko), id1, 1u);
                 }
             }
-            umma_commit(smem_u32(&mbar[s]));
+            umma_commit(smem_u32(&empty_bar[s]));
+            issued = it + 1;
         }
-        issued = it + 1;
-    }
-    // drain: wait for the commits still outstanding (bounded)
-    {
-        const long long first = issued > S ? issued - S : 0;
-        for (long long it = first; it < issued; ++it) {
-            const int s = (int)(it % S);
-            const uint32_t par = (uint32_t)((it / S) & 1);
-            if (!mbar_wait_bounded(smem_u32(&mbar[s]), par)) atomicExch(&abort_s, 1);
+        // MMAs complete in order: the last commit covers all of them (bounded)
+        if (issued > 0) {
+            const long long last = issued - 1;
+            if (!mbar_wait_bounded(smem_u32(&empty_bar[(int)(last % S)]),
+                                   (uint32_t)((last / S) & 1)))
+                *abort_v = 1;
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    const bool ok = iters > 0 && !abort_s;
     if (abort_s && tid == 0) set_status(status, HYDE_ERR_TIMEOUT);
 
     // epilogue: warp w % 4 reads TMEM lanes 32 (w % 4) .. + 31
@@ -292,17 +334,17 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
         const int row = 32 * quad + lane;           // band of M-tile 0
         for (int j = 0; j < P.Np; j += 8) {
             float v[8];
-            if (iters > 0 && !abort_s) tmem_ld8(tmem + lane_addr + (uint32_t)j, v);
+            if (ok) tmem_ld8(tmem + lane_addr + (uint32_t)j, v);
             else for (int q = 0; q < 8; ++q) v[q] = 0.f;
             if (row < p)
                 for (int q = 0; q < 8; ++q)
                     if (j + q < p) out[(long long)row * p + j + q] = v[q];
         }
-    } else if (P.nmt == 2) {
+    } else if (warp < 8 && P.nmt == 2) {
         const int row = P.m1_row0 + 32 * quad + lane;   // band of M-tile 1
         for (int j = 0; j < P.n1; j += 8) {
             float v[8];
-            if (iters > 0 && !abort_s) tmem_ld8(tmem + lane_addr + (uint32_t)(P.d1_col + j), v);
+            if (ok) tmem_ld8(tmem + lane_addr + (uint32_t)(P.d1_col + j), v);
             else for (int q = 0; q < 8; ++q) v[q] = 0.f;
             if (row >= 128 && row < p)
                 for (int q = 0; q < 8; ++q)
@@ -311,7 +353,7 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kProducerWarps) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"((uint32_t)P.tmem_cols));
@@ -319,20 +361,26 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
 }
 
 // R[i][j] = R[j][i] = sum over CTAs of the partial (i <= j): rows < 128 come
-// from M-tile 0, rows >= 128 (then j >= 128) from M-tile 1.
+// from M-tile 0, rows >= 128 (then j >= 128) from M-tile 1. Thread (e, y)
+// sums the partials of CTAs [16 y, 16 y + 16) for element e (coalesced over
+// e, independent loads) and adds the segment total with a double atomic to R,
+// which is cleared beforehand.
+constexpr int kTcReduceSeg = 16;
+
 __global__ void gram_tc_reduce_kernel(const float* __restrict__ partials, int nblocks, int p,
                                       double* __restrict__ R, int* status) {
     const long long tot = (long long)p * p;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / p), j = (int)(e % p);
-        if (j < i) continue;
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += (double)partials[(long long)b * tot + e];
-        if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
-        R[(long long)i * p + j] = s;
-        R[(long long)j * p + i] = s;
-    }
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= tot) return;
+    const int i = (int)(e / p), j = (int)(e % p);
+    if (j < i) return;
+    const int b0 = blockIdx.y * kTcReduceSeg, b1 = min(b0 + kTcReduceSeg, nblocks);
+    double s = 0.0;
+#pragma unroll 4
+    for (int b = b0; b < b1; ++b) s += (double)__ldg(partials + (long long)b * tot + e);
+    if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
+    atomicAdd(&R[(long long)i * p + j], s);
+    if (i != j) atomicAdd(&R[(long long)j * p + i], s);
 }
 
 TcPlan tc_plan(int p) {
@@ -373,20 +421,23 @@ hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, 
     const long long nchunks = (n + kChunk - 1) / kChunk;
     const int blocks = sms;
     const long long per = (nchunks + blocks - 1) / blocks;
-    const int rpw = (p + kTcThreads / 32 - 1) / (kTcThreads / 32);   // band rows per warp
+    const int rpw = (p + kProducerWarps - 1) / kProducerWarps;   // band rows per producer warp
     switch ((rpw + 7) / 8) {
 #define HYDE_TC(G)                                                                            \
     case G:                                                                                   \
         if (ensure_smem_limit((const void*)gram_tc_kernel<8 * G>, (int)P.smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                             \
-        gram_tc_kernel<8 * G><<<blocks, kTcThreads, P.smem, s>>>(Y, p, n, P, per, partials,  \
-                                                                  status);                    \
+        gram_tc_kernel<8 * G><<<blocks, kTcThreadsWs, P.smem, s>>>(Y, p, n, P, per, partials, \
+                                                                    status);                  \
         break;
         HYDE_TC(1) HYDE_TC(2) HYDE_TC(3) HYDE_TC(4)
 #undef HYDE_TC
         default: return HYDE_ERR_SHAPE;
     }
-    gram_tc_reduce_kernel<<<(p * p + 255) / 256, 256, 0, s>>>(partials, blocks, p, R, status);
+    if (cudaMemsetAsync(R, 0, (size_t)p * p * sizeof(double), s) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    dim3 rgrid((unsigned)((p * p + 255) / 256), (blocks + kTcReduceSeg - 1) / kTcReduceSeg);
+    gram_tc_reduce_kernel<<<rgrid, 256, 0, s>>>(partials, blocks, p, R, status);
     return cuda_status(cudaGetLastError());
 }
 

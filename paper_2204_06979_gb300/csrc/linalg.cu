@@ -465,6 +465,18 @@ __device__ __forceinline__ void hh_scalars(const float* A, int lda, int kr, floa
     }
 }
 
+// The same scalars from alpha and ss given directly.
+__device__ __forceinline__ void hh_scalars_of(float alpha, float ss, float& tau, float& sc,
+                                              float& beta) {
+    tau = 0.f; beta = alpha; sc = 0.f;
+    if (ss > 0.f) {
+        const float nrm = sqrtf(fmaf(alpha, alpha, ss));
+        beta = alpha >= 0.f ? -nrm : nrm;
+        tau = __fdividef(beta - alpha, beta);
+        sc = __fdividef(1.0f, alpha - beta);
+    }
+}
+
 // Entry i of reflector kr (see hh_scalars).
 __device__ __forceinline__ float hh_coef(const float* A, int lda, int p, int kr, float sc, int i) {
     return i == kr + 1 ? 1.0f : ((i > kr + 1 && i < p) ? A[i * lda + kr] * sc : 0.f);
@@ -535,6 +547,7 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     // step k+1 from the new values (row sums by a reduce-scatter). Two
     // barriers per step, one read and one write of each trailing element.
     float* const scv = vf;           // reflector scales (vf is free after the load)
+    float* const cvec = e2v;         // updated column k+1 (e2v is filled by the tail)
     constexpr int NA = (32 * NB + NW - 1) / NW;   // trailing rows per warp
     if (wid < NW) {
     // prologue: reflector 0 (scalars in every warp) and p_0 = tau_0 A v_0
@@ -588,55 +601,49 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
 #pragma unroll
         for (int b = 0; b < NB; ++b) wreg[b] = fmaf(-K, vreg[b], pj[b]);
         const int i0 = k + 1 + ((wid - (k + 1)) & (NW - 1));
-        // column k+1 (owner lane of each warp) and the squares for reflector k+1
+        // column k+1 by warp 0 alone (lane l: rows k+1+l+32b), written to
+        // cvec (A keeps the old values: the sweep updates the column in
+        // place), and the sum of squares below row k+2 for reflector k+1
         const int jn = k + 1;
-        if (lane == (jn & 31)) {
+        if (wid == 0) {
             const float wjn = pc[jn] - K;          // v_k[jn] = 1
             float ssp = 0.f;
 #pragma unroll
-            for (int a0 = 0; a0 < NA; a0 += 4) {   // loads of 4 rows before their stores
-                float vi[4], pi[4], e[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = i0 + NW * (a0 + u);
-                    const bool ok = a0 + u < NA && i < p;
-                    vi[u] = ok ? hh_coef(A, lda, p, k, sc_k, i) : 0.f;
-                    pi[u] = ok ? pc[i] : 0.f;
-                    e[u] = ok ? A[i * lda + jn] : 0.f;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = i0 + NW * (a0 + u);
-                    if (a0 + u < NA && i < p) {
-                        const float x = fmaf(-vi[u], wjn, e[u] - fmaf(-K, vi[u], pi[u]));
-                        A[i * lda + jn] = x;
-                        if (i >= k + 3) ssp = fmaf(x, x, ssp);
-                    }
+            for (int b = 0; b < NB; ++b) {
+                const int i = jn + lane + 32 * b;
+                if (i < p) {
+                    const float vi = hh_coef(A, lda, p, k, sc_k, i);
+                    const float x = fmaf(-vi, wjn, A[i * lda + jn] - fmaf(-K, vi, pc[i]));
+                    cvec[i] = x;
+                    if (i >= k + 3) ssp = fmaf(x, x, ssp);
                 }
             }
-            red[32 + wid] = ssp;
+            ssp = warp_sum(ssp);
+            if (lane == 0) red[32] = ssp;
         }
         bar_sync_warps<NW>();
         float tau_n = 0.f, sc_n = 0.f;
         float vn[NB];
         if (has_next) {
             float beta;
-            hh_scalars(A, lda, k + 1, warp_sum(lane < NW ? red[32 + lane] : 0.f), tau_n, sc_n,
-                       beta);
+            hh_scalars_of(cvec[k + 2], red[32], tau_n, sc_n, beta);
             if (t == 0) {
                 tauv[k + 1] = tau_n; scv[k + 1] = sc_n;
-                dv[k + 1] = A[(k + 1) * lda + (k + 1)]; ev[k + 1] = beta;
+                dv[k + 1] = cvec[k + 1]; ev[k + 1] = beta;
             }
 #pragma unroll
-            for (int b = 0; b < NB; ++b) vn[b] = hh_coef(A, lda, p, k + 1, sc_n, lane + 32 * b);
+            for (int b = 0; b < NB; ++b) {
+                const int j = lane + 32 * b;
+                vn[b] = j == k + 2 ? 1.0f : ((j > k + 2 && j < p) ? cvec[j] * sc_n : 0.f);
+            }
         } else {
 #pragma unroll
             for (int b = 0; b < NB; ++b) vn[b] = 0.f;
         }
         // fused sweep: update k on rows > k+1, columns > k+1; accumulate p' rows
         // Columns j <= k have v = w = 0 and are rewritten unchanged; column
-        // k+1 was updated by its owner lane and is not stored again; only the
-        // last column block can reach past p (p > 32 (NB - 1)).
+        // k+1 gets the same value warp 0 put in cvec; only the last column
+        // block can reach past p (p > 32 (NB - 1)).
         float sacc[NA];
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
@@ -650,7 +657,7 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
                     const int j = lane + 32 * b;
                     if (b < NB - 1 || j < p) {
                         const float x = fmaf(-vi, wreg[b], fmaf(-wi, vreg[b], row[j]));
-                        if (j != k + 1) row[j] = x;
+                        row[j] = x;
                         sacc[a] = fmaf(x, vn[b], sacc[a]);
                     }
                 }
@@ -679,10 +686,16 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
         *a = i <= k ? 0.f : (i == k + 1 ? 1.0f : *a * scv[k]);
     }
     if (t == 0) {
-        if (p >= 2) {
-            dv[p - 2] = A[(p - 2) * lda + (p - 2)];
-            ev[p - 2] = A[(p - 1) * lda + (p - 2)];
+        // with p >= 3 the last step left column p-2 in cvec (row p-2 of A is
+        // not updated by the sweep); A[p-1][p-1] is current
+        if (p >= 3) {
+            dv[p - 2] = cvec[p - 2];
+            ev[p - 2] = cvec[p - 1];
             tauv[p - 2] = 0.f;
+        } else if (p == 2) {
+            dv[0] = A[0];
+            ev[0] = A[lda];
+            tauv[0] = 0.f;
         }
         dv[p - 1] = A[(p - 1) * lda + (p - 1)];
         ev[p - 1] = 0.f;
