@@ -318,7 +318,7 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
                                        int n_slots, cudaEvent_t* events,
                                        cudaStream_t stream);
 
-/* Number of kernels one hyde_hyres_denoise call launches (11 + 2 * levels;
+/* Number of kernels one hyde_hyres_denoise call launches (10 + 2 * levels;
  * the two memsets that clear the workspace header and R are not counted),
  * or -1 for bad params. */
 int hyde_hyres_kernel_launches(const hyde_hyres_params* params);

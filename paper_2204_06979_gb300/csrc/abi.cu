@@ -595,8 +595,8 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H, i
 
 int hyde_hyres_kernel_launches(const hyde_hyres_params* params) {
     if (!params || params->levels < 1 || params->levels > kMaxLevels) return -1;
-    // gram 2, noise 2, eig 1, weights 1, projection 1, DWT L, SURE 3, IDWT L, back 1
-    return 11 + 2 * params->levels;
+    // gram 2, noise 2, eig 1, weights 1, projection 1, DWT L, SURE 2, IDWT L, back 1
+    return 10 + 2 * params->levels;
 }
 
 }  // extern "C"

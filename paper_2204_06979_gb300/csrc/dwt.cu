@@ -44,14 +44,26 @@ dwt_level_kernel(const float* __restrict__ src, long long src_bs, int src_ld, in
     // one warp per input row; the periodic wrap is a subtraction except on
     // images smaller than a tile
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int r = wid; r < IH; r += kThreads / 32) {
-        int y = wrap(2 * ty0 + r, h);
-        if (REFLECT && y >= hv) y = 2 * hv - 2 - y;
-        const float* row = s + (long long)y * src_ld;
-        for (int c = lane; c < IW; c += 32) {
-            int x = wrap(2 * tx0 + c, w);
-            if (REFLECT && x >= wv) x = 2 * wv - 2 - x;
-            in[r][c] = __ldg(row + x);
+    // fixed trip counts (rows wid + 8 rr, columns lane + 32 cc), unrolled, so
+    // that all of a thread's loads are in flight before the first store
+    constexpr int kRowSteps = (IH + kThreads / 32 - 1) / (kThreads / 32);
+    constexpr int kColSteps = (IW + 31) / 32;
+#pragma unroll
+    for (int rr = 0; rr < kRowSteps; ++rr) {
+        const int r = wid + rr * (kThreads / 32);
+        if (r < IH) {
+            int y = wrap(2 * ty0 + r, h);
+            if (REFLECT && y >= hv) y = 2 * hv - 2 - y;
+            const float* row = s + (long long)y * src_ld;
+#pragma unroll
+            for (int cc = 0; cc < kColSteps; ++cc) {
+                const int c = lane + 32 * cc;
+                if (c < IW) {
+                    int x = wrap(2 * tx0 + c, w);
+                    if (REFLECT && x >= wv) x = 2 * wv - 2 - x;
+                    in[r][c] = __ldg(row + x);
+                }
+            }
         }
     }
     __syncthreads();
@@ -110,7 +122,11 @@ idwt_level_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
     const int hh = h >> 1, wh = w >> 1;
     const float* L = llsrc + (long long)b * ll_bs;
     const float* C = coef + (long long)b * coef_bs;
-    for (int e = threadIdx.x; e < (TH + 1) * (TW + 1); e += kThreads) {
+    constexpr int kLoadSteps = ((TH + 1) * (TW + 1) + kThreads - 1) / kThreads;
+#pragma unroll
+    for (int q = 0; q < kLoadSteps; ++q) {
+        const int e = threadIdx.x + q * kThreads;
+        if (e >= (TH + 1) * (TW + 1)) break;
         const int j = e / (TW + 1), k = e % (TW + 1);
         const int J = ty0 + j == 0 ? hh - 1 : wrap(ty0 + j - 1, hh);
         const int K = tx0 + k == 0 ? wh - 1 : wrap(tx0 + k - 1, wh);

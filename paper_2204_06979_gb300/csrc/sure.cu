@@ -56,13 +56,25 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
         for (int y = y0 + wid; y < y1; y += nw) {
             const float4* row = reinterpret_cast<const float4*>(base + (long long)y * Wp);
             const bool yll = y < hl;
-            for (int x4 = lane; x4 < W4; x4 += 32) {
-                const float4 v = __ldg(row + x4);
-                const int x = x4 * 4;
-                one(v.x, yll && x < wl);
-                one(v.y, yll && x + 1 < wl);
-                one(v.z, yll && x + 2 < wl);
-                one(v.w, yll && x + 3 < wl);
+            // four float4 loads in flight per lane, then their 16 values
+            for (int x40 = lane; x40 < W4; x40 += 128) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int x4 = x40 + 32 * u;
+                    v[u] = x4 < W4 ? __ldg(row + x4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int x4 = x40 + 32 * u;
+                    if (x4 < W4) {
+                        const int x = x4 * 4;
+                        one(v[u].x, yll && x < wl);
+                        one(v[u].y, yll && x + 1 < wl);
+                        one(v[u].z, yll && x + 2 < wl);
+                        one(v[u].w, yll && x + 3 < wl);
+                    }
+                }
             }
         }
     } else {
@@ -122,55 +134,109 @@ sure_table_kernel(const unsigned int* __restrict__ counts, const double* __restr
     if (lane == 0) S_inf[i] = sum_all[i] - (double)N;
 }
 
-// One block: the total-SURE table T(r, k) = sum_{i<=r} S_i(lambda_k) +
-// sum_{r<i<=r_max} S_i(inf), its first minimum in row-major (rank, lambda)
-// order, and the relative gap to the runner-up.
-__global__ void __launch_bounds__(256)
-sure_select_kernel(const double* __restrict__ S, const double* __restrict__ S_inf, int batch,
-                   int K, double delta, double* __restrict__ T, hyde_hyres_info* info,
-                   int* rank_out, double* lam_out, const int* status) {
-    __shared__ double tail[kMaxRank + 1];
-    const int t = threadIdx.x;
-    if (t < 32) {   // tail[r] = sum_{i > r} S_inf[i] by a reversed warp scan
-        const int i = batch - 1 - t;
-        double v = (i >= 0) ? S_inf[i] : 0.0;
+// Table and choice in one block of 32 * batch threads, everything in shared
+// memory: warp i forms S_i(lambda_k) by warp scans over the bins; warp 0 the
+// suffix sums of S_inf; T(r, k) = sum_{i<=r} S_i(lambda_k) + sum_{i>r} S_inf[i]
+// by scans across lanes (lane = rank) per column k; then a block-wide first
+// minimum in row-major (rank, lambda) order and the runner-up for the gap.
+__global__ void __launch_bounds__(32 * kMaxRank)
+sure_table_select_kernel(const unsigned int* __restrict__ counts,
+                         const double* __restrict__ sums, const double* __restrict__ sum_all,
+                         int batch, int K, long long N, long long N_det, double delta,
+                         double* __restrict__ S, double* __restrict__ S_inf,
+                         double* __restrict__ T, hyde_hyres_info* info, int* rank_out,
+                         double* lam_out, const int* status) {
+    extern __shared__ double shd[];
+    double* Ss = shd;                       // [batch][K]
+    double* Ts = shd + (size_t)batch * K;   // [batch][K]
+    __shared__ double sinf[kMaxRank], tail[kMaxRank];
+    __shared__ double wm1[kMaxRank], wm2[kMaxRank];
+    __shared__ int wi1[kMaxRank];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    if (wid < batch) {
+        const int i = wid;
+        double ccarry = 0.0, scarry = 0.0;
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            const int k = k0 + lane;
+            double c = k < K ? (double)counts[(long long)i * K + k] : 0.0;
+            double q = k < K ? sums[(long long)i * K + k] : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double c2 = __shfl_up_sync(0xffffffffu, c, o);
+                const double q2 = __shfl_up_sync(0xffffffffu, q, o);
+                if (lane >= o) { c += c2; q += q2; }
+            }
+            const double cle = c + ccarry, sle = q + scarry;
+            if (k < K) {
+                const double lam = k * delta;
+                const double v = (double)N - 2.0 * cle + sle + lam * lam * ((double)N_det - cle);
+                Ss[i * K + k] = v;
+                S[(long long)i * K + k] = v;
+            }
+            ccarry = __shfl_sync(0xffffffffu, cle, 31);
+            scarry = __shfl_sync(0xffffffffu, sle, 31);
+        }
+        if (lane == 0) {
+            const double v = sum_all[i] - (double)N;
+            sinf[i] = v;
+            S_inf[i] = v;
+        }
+    }
+    __syncthreads();
+    if (wid == 0) {   // tail[r] = sum_{i > r} S_inf[i] by a reversed warp scan
+        const int i = batch - 1 - lane;
+        double v = (i >= 0) ? sinf[i] : 0.0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const double u = __shfl_up_sync(0xffffffffu, v, o);
-            if (t >= o) v += u;
+            if (lane >= o) v += u;
         }
-        // v = sum_{j >= i} S_inf[j]; tail[i] = v - S_inf[i]
-        if (i >= 0) tail[i] = v - S_inf[i];
+        if (i >= 0) tail[i] = v - sinf[i];
     }
     __syncthreads();
-    for (int k = t; k < K; k += blockDim.x) {
-        double head = 0.0;
-        for (int r = 0; r < batch; ++r) {
-            head += S[(long long)r * K + k];
-            T[(long long)r * K + k] = head + tail[r];
+    for (int k = wid; k < K; k += nw) {   // lane = rank r - 1
+        double v = lane < batch ? Ss[lane * K + k] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane < batch) {
+            const double tv = v + tail[lane];
+            Ts[lane * K + k] = tv;
+            if (T) T[(long long)lane * K + k] = tv;
         }
     }
     __syncthreads();
-    if (t < 32) {
-        const int tot = batch * K;
-        double m1 = DBL_MAX, m2 = DBL_MAX;
-        int i1 = 0x7fffffff;
-        for (int e = t; e < tot; e += 32) {
-            const double v = T[e];
-            if (v < m1 || (v == m1 && e < i1)) { m2 = fmin(m2, m1); m1 = v; i1 = e; }
-            else m2 = fmin(m2, v);
-        }
+    const int tot = batch * K;
+    double m1 = DBL_MAX, m2 = DBL_MAX;
+    int i1 = 0x7fffffff;
+    for (int e = t; e < tot; e += blockDim.x) {
+        const double v = Ts[e];
+        if (v < m1 || (v == m1 && e < i1)) { m2 = fmin(m2, m1); m1 = v; i1 = e; }
+        else m2 = fmin(m2, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double om1 = __shfl_xor_sync(0xffffffffu, m1, o);
+        const double om2 = __shfl_xor_sync(0xffffffffu, m2, o);
+        const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
+        if (om1 < m1 || (om1 == m1 && oi1 < i1)) { m2 = fmin(m1, om2); m1 = om1; i1 = oi1; }
+        else m2 = fmin(m2, om1);
+    }
+    if (lane == 0) { wm1[wid] = m1; wm2[wid] = m2; wi1[wid] = i1; }
+    __syncthreads();
+    if (wid == 0) {
+        m1 = lane < nw ? wm1[lane] : DBL_MAX;
+        m2 = lane < nw ? wm2[lane] : DBL_MAX;
+        i1 = lane < nw ? wi1[lane] : 0x7fffffff;
         for (int o = 16; o > 0; o >>= 1) {
             const double om1 = __shfl_xor_sync(0xffffffffu, m1, o);
             const double om2 = __shfl_xor_sync(0xffffffffu, m2, o);
             const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
-            double n1, n2;
-            int ni;
-            if (om1 < m1 || (om1 == m1 && oi1 < i1)) { n1 = om1; ni = oi1; n2 = fmin(m1, om2); }
-            else { n1 = m1; ni = i1; n2 = fmin(m2, om1); }
-            m1 = n1; m2 = n2; i1 = ni;
+            if (om1 < m1 || (om1 == m1 && oi1 < i1)) { m2 = fmin(m1, om2); m1 = om1; i1 = oi1; }
+            else m2 = fmin(m2, om1);
         }
-        if (t == 0) {
+        if (lane == 0) {
             const int r = i1 / K, k = i1 % K;
             if (rank_out) *rank_out = r + 1;
             if (lam_out) *lam_out = k * delta;
@@ -223,12 +289,17 @@ hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
                                long long N_det, double delta, double* S, double* S_inf,
                                double* T, hyde_hyres_info* info, int* rank_out,
                                double* lam_out, const int* status, cudaStream_t s) {
-    sure_table_kernel<<<(batch + 7) / 8, 256, 0, s>>>(b.counts, b.sums, b.sum_all, batch, K, N,
-                                                       N_det, delta, S, S_inf);
-    if (T != nullptr) {
+    if (T == nullptr) {   // the tables only
+        sure_table_kernel<<<(batch + 7) / 8, 256, 0, s>>>(b.counts, b.sums, b.sum_all, batch, K,
+                                                           N, N_det, delta, S, S_inf);
+    } else {
         if (batch > kMaxRank) return HYDE_ERR_SHAPE;
-        sure_select_kernel<<<1, 256, 0, s>>>(S, S_inf, batch, K, delta, T, info, rank_out,
-                                             lam_out, status);
+        const size_t smem = 2 * (size_t)batch * K * sizeof(double);
+        if (ensure_smem_limit((const void*)sure_table_select_kernel, (int)smem) != cudaSuccess)
+            return HYDE_ERR_CUDA;
+        sure_table_select_kernel<<<1, 32 * batch, smem, s>>>(b.counts, b.sums, b.sum_all, batch,
+                                                             K, N, N_det, delta, S, S_inf, T,
+                                                             info, rank_out, lam_out, status);
     }
     return cuda_status(cudaGetLastError());
 }
