@@ -43,16 +43,71 @@ constexpr int kMaxRegT = 6;   // register tiles up to 6 x 6 (p <= 192)
 // --------------------------------------------------------------------------
 constexpr float kPivotFloor = 2e-6f;
 
+// Row or column ko of a T x T register tile (ko uniform across the block):
+// a switch selects one of T straight-line cases instead of T^2 predicated
+// moves.
+#define HYDE_CASES10(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9)
+
 template <int T>
-__global__ void __launch_bounds__(kLA, 1)
+__device__ __forceinline__ void tile_row_out(const float (&a)[T][T], int ko, float* dst) {
+    switch (ko) {
+#define HYDE_ROW(C) \
+    case C: if (C < T) { _Pragma("unroll") for (int jj = 0; jj < T; ++jj) dst[jj] = a[C < T ? C : 0][jj]; } break;
+        HYDE_CASES10(HYDE_ROW)
+#undef HYDE_ROW
+        default: break;
+    }
+}
+template <int T>
+__device__ __forceinline__ void tile_col_out(const float (&a)[T][T], int ko, float* dst) {
+    switch (ko) {
+#define HYDE_COL(C) \
+    case C: if (C < T) { _Pragma("unroll") for (int ii = 0; ii < T; ++ii) dst[ii] = a[ii][C < T ? C : 0]; } break;
+        HYDE_CASES10(HYDE_COL)
+#undef HYDE_COL
+        default: break;
+    }
+}
+template <int T>
+__device__ __forceinline__ void tile_row_set(float (&a)[T][T], int ko, const float (&v)[T], float s) {
+    switch (ko) {
+#define HYDE_RSET(C) \
+    case C: if (C < T) { _Pragma("unroll") for (int jj = 0; jj < T; ++jj) a[C < T ? C : 0][jj] = v[jj] * s; } break;
+        HYDE_CASES10(HYDE_RSET)
+#undef HYDE_RSET
+        default: break;
+    }
+}
+template <int T>
+__device__ __forceinline__ void tile_col_set(float (&a)[T][T], int ko, const float (&v)[T], int diag,
+                                             float piv) {
+    // column ko := -v; entry (diag, ko) := piv when diag >= 0
+    switch (ko) {
+#define HYDE_CSET(C) \
+    case C: if (C < T) { _Pragma("unroll") for (int ii = 0; ii < T; ++ii) a[ii][C < T ? C : 0] = ii == diag ? piv : -v[ii]; } break;
+        HYDE_CASES10(HYDE_CSET)
+#undef HYDE_CSET
+        default: break;
+    }
+}
+
+// The G x G threads form a grid over the matrix: thread (ty, tx) owns the
+// T x T tile of rows ty T.. and columns tx T.. in registers. A step costs T^2
+// FMAs and 2T shared loads per thread plus one barrier; the pivot row and
+// column are published through double-buffered shared vectors. G = 16 (256
+// threads, up to 10 x 10 tiles) keeps the per-thread work of a step high and
+// the number of warps that repeat the pivot arithmetic low; G = 32 covers
+// p <= 192 with smaller tiles.
+template <int T, int G>
+__global__ void __launch_bounds__(G * G, 1)
 noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
                     double* __restrict__ S, int* status) {
-    __shared__ float s_inv[32 * T];
-    __shared__ float s_row[2][32 * T];
-    __shared__ float s_col[2][32 * T];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int r0 = wid * T, c0 = lane * T;
-    for (int i = t; i < 32 * T; i += kLA) {
+    __shared__ float s_inv[G * T];
+    __shared__ float s_row[2][G * T];
+    __shared__ float s_col[2][G * T];
+    const int t = threadIdx.x, tx = t % G, ty = t / G;
+    const int r0 = ty * T, c0 = tx * T;
+    for (int i = t; i < G * T; i += G * G) {
         float inv = 0.f;
         if (i < p) {
             const double d = R[(long long)i * p + i];
@@ -79,22 +134,8 @@ noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ain
     for (int k = 0; k < p; ++k) {
         const int buf = k & 1;
         const int kt = k / T, ko = k - kt * T;
-        if (wid == kt) {
-#pragma unroll
-            for (int ii = 0; ii < T; ++ii)
-                if (ii == ko) {
-#pragma unroll
-                    for (int jj = 0; jj < T; ++jj) s_row[buf][c0 + jj] = a[ii][jj];
-                }
-        }
-        if (lane == kt) {
-#pragma unroll
-            for (int jj = 0; jj < T; ++jj)
-                if (jj == ko) {
-#pragma unroll
-                    for (int ii = 0; ii < T; ++ii) s_col[buf][r0 + ii] = a[ii][jj];
-                }
-        }
+        if (ty == kt) tile_row_out<T>(a, ko, &s_row[buf][c0]);
+        if (tx == kt) tile_col_out<T>(a, ko, &s_col[buf][r0]);
         __syncthreads();   // one barrier per step: the vectors are double-buffered
         const float pk = s_col[buf][k];
         if (t == 0 && !(pk > kPivotFloor)) set_status(status, HYDE_ERR_NUMERIC);
@@ -109,23 +150,8 @@ noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ain
         for (int ii = 0; ii < T; ++ii)
 #pragma unroll
             for (int jj = 0; jj < T; ++jj) a[ii][jj] = fmaf(-ck[ii], rk[jj], a[ii][jj]);
-        if (wid == kt) {   // row k: a_kj * piv
-#pragma unroll
-            for (int ii = 0; ii < T; ++ii)
-                if (ii == ko) {
-#pragma unroll
-                    for (int jj = 0; jj < T; ++jj) a[ii][jj] = rk[jj] * piv;
-                }
-        }
-        if (lane == kt) {  // column k: -a_ik * piv, and the pivot itself
-#pragma unroll
-            for (int jj = 0; jj < T; ++jj)
-                if (jj == ko) {
-#pragma unroll
-                    for (int ii = 0; ii < T; ++ii)
-                        a[ii][jj] = (wid == kt && ii == ko) ? piv : -ck[ii];
-                }
-        }
+        if (ty == kt) tile_row_set<T>(a, ko, rk, piv);                 // row k: a_kj * piv
+        if (tx == kt) tile_col_set<T>(a, ko, ck, ty == kt ? ko : -1, piv);   // column k, pivot
     }
 #pragma unroll
     for (int ii = 0; ii < T; ++ii) {
@@ -201,13 +227,21 @@ noise_refine_kernel(const double* __restrict__ R, const float* __restrict__ Ainv
     for (int i = t; i < p; i += blockDim.x)
         xs[i] = (double)Ainv[(long long)i * p + b] / (S[i] * sb);
     __syncthreads();
+    // x^T R x = sum_i x_i sum_j R_ij x_j: each lane keeps its own share of
+    // the double sum (rows w + 8m, columns lane + 32q); one warp sum at the end
     double part = 0.0;
     for (int i = w; i < p; i += 8) {
+        const double* Ri = R + (long long)i * p;
         double u = 0.0;
-        for (int j = lane; j < p; j += 32) u = fma(R[(long long)i * p + j], xs[j], u);
-        u = warp_sum_d(u);
-        part = fma(xs[i], u, part);   // identical in all lanes
+#pragma unroll 8
+        for (int q = 0; q < 8; ++q) {
+            const int j = lane + 32 * q;
+            if (j < p) u = fma(__ldg(Ri + j), xs[j], u);
+        }
+        for (int j = lane + 256; j < p; j += 32) u = fma(__ldg(Ri + j), xs[j], u);
+        part = fma(xs[i], u, part);
     }
+    part = warp_sum_d(part);
     if (lane == 0) red[w] = part;
     __syncthreads();
     if (t == 0) {
@@ -805,20 +839,26 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
     float* Ainv = reinterpret_cast<float*>(ws);
     double* Sd = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) +
                                            align_up((size_t)p * p * sizeof(float), kAlign));
-    const int T = (p + 31) / 32;
-    switch (T) {
-        case 1: noise_gj_reg_kernel<1><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
-        case 2: noise_gj_reg_kernel<2><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
-        case 3: noise_gj_reg_kernel<3><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
-        case 4: noise_gj_reg_kernel<4><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
-        case 5: noise_gj_reg_kernel<5><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
-        case 6: noise_gj_reg_kernel<6><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
-        default: {
-            size_t smem = noise_smem_bytes(p);
-            if (ensure_smem_limit((const void*)noise_gj_smem_kernel, (int)smem) != cudaSuccess)
-                return HYDE_ERR_SHAPE;
-            noise_gj_smem_kernel<<<1, kLA, smem, s>>>(R, p, Ainv, Sd, status);
+    const int T16 = (p + 15) / 16, T32 = (p + 31) / 32;
+    if (T16 <= 10) {
+        switch (T16) {
+#define HYDE_GJ16(TV) \
+    case TV: noise_gj_reg_kernel<TV, 16><<<1, 256, 0, s>>>(R, p, Ainv, Sd, status); break;
+            HYDE_GJ16(1) HYDE_GJ16(2) HYDE_GJ16(3) HYDE_GJ16(4) HYDE_GJ16(5)
+            HYDE_GJ16(6) HYDE_GJ16(7) HYDE_GJ16(8) HYDE_GJ16(9) HYDE_GJ16(10)
+#undef HYDE_GJ16
+            default: return HYDE_ERR_SHAPE;
         }
+    } else if (T32 <= kMaxRegT) {
+        switch (T32) {
+            case 6: noise_gj_reg_kernel<6, 32><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
+            default: return HYDE_ERR_SHAPE;   // p in (160, 192] has T32 = 6
+        }
+    } else {
+        size_t smem = noise_smem_bytes(p);
+        if (ensure_smem_limit((const void*)noise_gj_smem_kernel, (int)smem) != cudaSuccess)
+            return HYDE_ERR_SHAPE;
+        noise_gj_smem_kernel<<<1, kLA, smem, s>>>(R, p, Ainv, Sd, status);
     }
     noise_refine_kernel<<<p, 256, p * sizeof(double), s>>>(R, Ainv, Sd, p, n, sigma, status);
     return cuda_status(cudaGetLastError());
