@@ -374,7 +374,11 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     HYDE_TRY(launch_weights(V, sigma, p, r, L.RM, P, Q, stream));
     HYDE_TRY(stage());
     // 5. projection into padded component images
-    HYDE_TRY(launch_project_pad(Y, p, H, W, P, r, L.RM, zp, L.Hp, L.Wp, stream));
+    const bool tc_proj = params->precision == HYDE_PREC_BF16X3 && project_tc_supported(p, r);
+    if (tc_proj)
+        HYDE_TRY(launch_project_pad_tc(Y, p, H, W, P, r, L.RM, zp, L.Hp, L.Wp, status, stream));
+    else
+        HYDE_TRY(launch_project_pad(Y, p, H, W, P, r, L.RM, zp, L.Hp, L.Wp, stream));
     HYDE_TRY(stage());
     // 6. wavelet analysis
     DwtSrc src{zp, L.N, L.Wp, L.Hp, L.Wp};
@@ -393,7 +397,10 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
                           scale, lev));
     HYDE_TRY(stage());
     // 10. back-projection and un-whitening
-    HYDE_TRY(launch_backproject(zp, L.n, Q, p, r, L.RM, rank_dev, X, stream));
+    if (tc_proj)
+        HYDE_TRY(launch_backproject_tc(zp, L.n, Q, p, L.RM, rank_dev, X, status, stream));
+    else
+        HYDE_TRY(launch_backproject(zp, L.n, Q, p, r, L.RM, rank_dev, X, stream));
     HYDE_TRY(stage());
 #undef HYDE_TRY
     return HYDE_OK;

@@ -108,6 +108,14 @@ hyde_status launch_project_pad(const float* Y, int p, int H, int W,
 hyde_status launch_backproject(const float* Zh, long long n, const float* Q,
                                int p, int r_max, int ldw, const int* rank,
                                float* X, cudaStream_t s);
+// Split-BF16 tcgen05 versions (precision form): the same contractions with
+// the pixels on the MMA's M. Supported for p <= 256 and r_max <= 32.
+bool project_tc_supported(int p, int r_max);
+hyde_status launch_project_pad_tc(const float* Y, int p, int H, int W, const float* P, int r,
+                                  int ldw, float* Zp, int Hp, int Wp, int* status,
+                                  cudaStream_t s);
+hyde_status launch_backproject_tc(const float* Zh, long long n, const float* Q, int p, int ldw,
+                                  const int* rank, float* X, int* status, cudaStream_t s);
 
 // ------------------------------------------------------------------ DWT
 // Source of the first analysis level: the image is read at (y, x) of the
