@@ -28,7 +28,16 @@ constexpr int kBpThreads = 256;
 // and right edges); false for a padding pixel that is zero-filled instead.
 __device__ __forceinline__ bool padded_source(long long pix, int H, int W, int Wp,
                                               int zero_pad, long long& src) {
-    int y = (int)(pix / Wp), x = (int)(pix - (long long)(pix / Wp) * Wp);
+    // 32-bit division when the padded image is below 2^31 pixels
+    int y, x;
+    if (pix < 0x7fffffffLL) {
+        const int pi = (int)pix;
+        y = pi / Wp;
+        x = pi - y * Wp;
+    } else {
+        y = (int)(pix / Wp);
+        x = (int)(pix - (long long)y * Wp);
+    }
     if (zero_pad && (y >= H || x >= W)) { src = 0; return false; }
     if (y >= H) y = 2 * H - 2 - y;
     if (x >= W) x = 2 * W - 2 - x;

@@ -63,7 +63,8 @@ __device__ __forceinline__ bool pad_src(long long pix, long long N, int H, int W
                                         int zero_pad, long long& src) {
     src = 0;
     if (pix >= N) return false;
-    int y = (int)(pix / Wp), x = (int)(pix - (long long)(pix / Wp) * Wp);
+    const int pi = (int)pix;               // N < 2^31 (checked by the launcher)
+    int y = pi / Wp, x = pi - y * Wp;
     if (zero_pad && (y >= H || x >= W)) return false;
     if (y >= H) y = 2 * H - 2 - y;
     if (x >= W) x = 2 * W - 2 - x;
@@ -98,30 +99,45 @@ constexpr int kPjN = 32;        // components (MMA N); r_max <= 32
 constexpr int kPjStages = 5;    // (tile, K block) stages of 32 KB
 constexpr int kPjEpiWarps = 4;
 constexpr int kPjThreads = (kProdWarps + 1 + kPjEpiWarps) * 32;
-constexpr int kPjPairs = 16;    // K pairs per producer thread and stage
+constexpr int kPjSlots = 16;    // (row, K pair) slots per producer thread and stage
 
+// Producer thread mapping of one 128-row x 64-K stage: warp w covers the
+// 8-row atoms w and w + 8, lane l row (l & 7) of the atom and K pairs
+// 4 j + (l >> 3), j < 8. The 32 lanes of a store then hit one 16-byte chunk
+// position per row (8 rows) and four words within it: 32 distinct banks.
 struct PjRegs {
-    float v[kPjPairs][2];
+    float v[kPjSlots][2];
 };
 
-__device__ __forceinline__ void pj_load(PjRegs& R, const float* __restrict__ Y, long long n, int p,
-                                        int kb, int g, long long src, bool data) {
+// element offsets (32 bit: p * n < 2^31) of band pair (b, b + 1) at pixel src
+__device__ __forceinline__ void pj_load(PjRegs& R, const float* __restrict__ Y, unsigned n, int p,
+                                        int kb, int pq, const unsigned (&src)[2],
+                                        const bool (&data)[2]) {
 #pragma unroll
-    for (int q = 0; q < kPjPairs; ++q) {
-        const int b = kb * 64 + 2 * (g + 2 * q);
-        R.v[q][0] = (data && b < p) ? __ldg(Y + (long long)b * n + src) : 0.f;
-        R.v[q][1] = (data && b + 1 < p) ? __ldg(Y + (long long)(b + 1) * n + src) : 0.f;
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int b = kb * 64 + 2 * (4 * j + pq);
+            const unsigned off = (unsigned)b * n + src[a];
+            R.v[a * 8 + j][0] = (data[a] && b < p) ? __ldg(Y + off) : 0.f;
+            R.v[a * 8 + j][1] = (data[a] && b + 1 < p) ? __ldg(Y + off + n) : 0.f;
+        }
     }
 }
 
-__device__ __forceinline__ void pj_store(const PjRegs& R, uint8_t* hi, uint8_t* lo, int m, int g) {
+__device__ __forceinline__ void pj_store(const PjRegs& R, uint8_t* hi, uint8_t* lo, int warp,
+                                         int rr, int pq) {
 #pragma unroll
-    for (int q = 0; q < kPjPairs; ++q) {
-        uint32_t h, l;
-        split_pair(R.v[q][0], R.v[q][1], h, l);
-        const uint32_t off = sw128_pair_offset(m, 2 * (g + 2 * q));
-        *reinterpret_cast<uint32_t*>(hi + off) = h;
-        *reinterpret_cast<uint32_t*>(lo + off) = l;
+    for (int a = 0; a < 2; ++a) {
+        const int row = 8 * (warp + 8 * a) + rr;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            uint32_t h, l;
+            split_pair(R.v[a * 8 + j][0], R.v[a * 8 + j][1], h, l);
+            const uint32_t off = sw128_pair_offset(row, 2 * (4 * j + pq));
+            *reinterpret_cast<uint32_t*>(hi + off) = h;
+            *reinterpret_cast<uint32_t*>(lo + off) = l;
+        }
     }
 }
 
@@ -181,15 +197,25 @@ project_tc_kernel(const float* __restrict__ Y, int p, int H, int W, const float*
     const long long nstage = ntile * KB;
 
     if (warp < kProdWarps) {
-        // ---- producers: thread = (pixel m, K-pair parity g)
-        const int m = tid & (kTileM - 1), g = tid >> 7;
+        // ---- producers (mapping above)
+        const int rr = lane & 7, pq = lane >> 3;
         PjRegs ra, rb;
+        // source pixels of the tile being loaded (the same for its K blocks)
+        unsigned src[2] = {0u, 0u};
+        bool data[2] = {false, false};
         auto prep = [&](long long u, PjRegs& R) {
-            const long long tl = t0 + u / KB;
             const int kb = (int)(u % KB);
-            long long src;
-            const bool data = pad_src(tl * kTileM + m, N, H, W, Wp, zero_pad, src);
-            pj_load(R, Y, n, p, kb, g, src, data);
+            if (kb == 0) {
+                const long long tl = t0 + u / KB;
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    long long sp;
+                    data[a] = pad_src(tl * kTileM + 8 * (warp + 8 * a) + rr, N, H, W, Wp,
+                                      zero_pad, sp);
+                    src[a] = (unsigned)sp;
+                }
+            }
+            pj_load(R, Y, (unsigned)n, p, kb, pq, src, data);
         };
         if (nstage > 0) prep(0, ra);
         if (nstage > 1) prep(1, rb);
@@ -201,10 +227,10 @@ project_tc_kernel(const float* __restrict__ Y, int p, int H, int W, const float*
             if (*abort_v) break;
             uint8_t* hi = gbase + stage0 + (uint32_t)s * stage_bytes;
             if ((u & 1) == 0) {
-                pj_store(ra, hi, hi + kKBlockBytes, m, g);
+                pj_store(ra, hi, hi + kKBlockBytes, warp, rr, pq);
                 if (u + 2 < nstage) prep(u + 2, ra);
             } else {
-                pj_store(rb, hi, hi + kKBlockBytes, m, g);
+                pj_store(rb, hi, hi + kKBlockBytes, warp, rr, pq);
                 if (u + 2 < nstage) prep(u + 2, rb);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -280,9 +306,10 @@ project_tc_kernel(const float* __restrict__ Y, int p, int H, int W, const float*
             mbar_arrive(smem_u32(&tempty_bar[buf]));
             const long long pix = (t0 + tl) * kTileM + m;
             if (pix < N) {
+                unsigned off = (unsigned)pix;
 #pragma unroll
-                for (int i = 0; i < kPjN; ++i)
-                    if (i < r) Zp[(long long)i * N + pix] = v[i];
+                for (int i = 0; i < kPjN; ++i, off += (unsigned)N)
+                    if (i < r) Zp[off] = v[i];
             }
         }
     }
@@ -300,32 +327,45 @@ constexpr int kBpK = 32;          // components (MMA K, two steps of 16)
 constexpr int kBpStages = 3;      // tiles of 32 KB (hi + lo, one 64-wide K block)
 constexpr int kBpEpiWarps = 8;    // two per TMEM lane quadrant (column halves)
 constexpr int kBpThreads = (kProdWarps + 1 + kBpEpiWarps) * 32;
-constexpr int kBpPairs = 8;       // K pairs per producer thread (16 components)
+constexpr int kBpSlots = 8;       // (row, K pair) slots per producer thread: K = 32
 constexpr uint32_t kBpAccCols = 256;   // TMEM columns per accumulator (N <= 256)
 
+// Producer mapping for a 128-row x 32-K tile (16 K pairs): warp w covers the
+// 8-row atoms w and w + 8, lane l row (l & 7) and K pairs 4 j + (l >> 3),
+// j < 4 (conflict-free stores as in the projection).
 struct BpRegs {
-    float v[kBpPairs][2];
+    float v[kBpSlots][2];
 };
 
-__device__ __forceinline__ void bp_load(BpRegs& R, const float* __restrict__ Zh, long long n, int r,
-                                        int g, long long pix) {
-    const bool live = pix < n;
+__device__ __forceinline__ void bp_load(BpRegs& R, const float* __restrict__ Zh, unsigned n, int r,
+                                        int warp, int rr, int pq, long long tile) {
 #pragma unroll
-    for (int q = 0; q < kBpPairs; ++q) {
-        const int i = 2 * (g + 2 * q);
-        R.v[q][0] = (live && i < r) ? __ldg(Zh + (long long)i * n + pix) : 0.f;
-        R.v[q][1] = (live && i + 1 < r) ? __ldg(Zh + (long long)(i + 1) * n + pix) : 0.f;
+    for (int a = 0; a < 2; ++a) {
+        const long long pix = tile * kTileM + 8 * (warp + 8 * a) + rr;
+        const bool live = pix < (long long)n;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = 2 * (4 * j + pq);
+            const unsigned off = (unsigned)i * n + (unsigned)pix;
+            R.v[a * 4 + j][0] = (live && i < r) ? __ldg(Zh + off) : 0.f;
+            R.v[a * 4 + j][1] = (live && i + 1 < r) ? __ldg(Zh + off + n) : 0.f;
+        }
     }
 }
 
-__device__ __forceinline__ void bp_store(const BpRegs& R, uint8_t* hi, uint8_t* lo, int m, int g) {
+__device__ __forceinline__ void bp_store(const BpRegs& R, uint8_t* hi, uint8_t* lo, int warp,
+                                         int rr, int pq) {
 #pragma unroll
-    for (int q = 0; q < kBpPairs; ++q) {
-        uint32_t h, l;
-        split_pair(R.v[q][0], R.v[q][1], h, l);
-        const uint32_t off = sw128_pair_offset(m, 2 * (g + 2 * q));
-        *reinterpret_cast<uint32_t*>(hi + off) = h;
-        *reinterpret_cast<uint32_t*>(lo + off) = l;
+    for (int a = 0; a < 2; ++a) {
+        const int row = 8 * (warp + 8 * a) + rr;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t h, l;
+            split_pair(R.v[a * 4 + j][0], R.v[a * 4 + j][1], h, l);
+            const uint32_t off = sw128_pair_offset(row, 2 * (4 * j + pq));
+            *reinterpret_cast<uint32_t*>(hi + off) = h;
+            *reinterpret_cast<uint32_t*>(lo + off) = l;
+        }
     }
 }
 
@@ -400,10 +440,11 @@ backproject_tc_kernel(const float* __restrict__ Zh, long long n, const float* __
     const long long ntile = t1 - t0;
 
     if (warp < kProdWarps) {
-        const int m = tid & (kTileM - 1), g = tid >> 7;
+        const int rr = lane & 7, pq = lane >> 3;
+        const unsigned nu = (unsigned)n;
         BpRegs ra, rb;
-        if (ntile > 0) bp_load(ra, Zh, n, r, g, t0 * kTileM + m);
-        if (ntile > 1) bp_load(rb, Zh, n, r, g, (t0 + 1) * kTileM + m);
+        if (ntile > 0) bp_load(ra, Zh, nu, r, warp, rr, pq, t0);
+        if (ntile > 1) bp_load(rb, Zh, nu, r, warp, rr, pq, t0 + 1);
         for (long long u = 0; u < ntile; ++u) {
             const int s = (int)(u % kBpStages);
             if (u >= kBpStages &&
@@ -412,11 +453,11 @@ backproject_tc_kernel(const float* __restrict__ Zh, long long n, const float* __
             if (*abort_v) break;
             uint8_t* hi = gbase + stage0 + (uint32_t)s * stage_bytes;
             if ((u & 1) == 0) {
-                bp_store(ra, hi, hi + kKBlockBytes, m, g);
-                if (u + 2 < ntile) bp_load(ra, Zh, n, r, g, (t0 + u + 2) * kTileM + m);
+                bp_store(ra, hi, hi + kKBlockBytes, warp, rr, pq);
+                if (u + 2 < ntile) bp_load(ra, Zh, nu, r, warp, rr, pq, t0 + u + 2);
             } else {
-                bp_store(rb, hi, hi + kKBlockBytes, m, g);
-                if (u + 2 < ntile) bp_load(rb, Zh, n, r, g, (t0 + u + 2) * kTileM + m);
+                bp_store(rb, hi, hi + kKBlockBytes, warp, rr, pq);
+                if (u + 2 < ntile) bp_load(rb, Zh, nu, r, warp, rr, pq, t0 + u + 2);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&full_bar[s]));
@@ -477,14 +518,21 @@ backproject_tc_kernel(const float* __restrict__ Zh, long long n, const float* __
             if (*abort_v) break;
             tc_fence_after();
             const long long pix = (t0 + u) * kTileM + m;
+            const unsigned nu = (unsigned)n;
             for (int c = c_begin; c < c_end; c += 16) {
                 float v[16];
                 tmem_ld16(tmem + lane_addr + (uint32_t)buf * kBpAccCols + (uint32_t)c, v);
                 tmem_wait_ld();
                 if (pix < n) {
+                    unsigned off = (unsigned)c * nu + (unsigned)pix;
+                    if (c + 16 <= p) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        if (c + q < p) X[(long long)(c + q) * n + pix] = v[q];
+                        for (int q = 0; q < 16; ++q, off += nu) X[off] = v[q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q, off += nu)
+                            if (c + q < p) X[off] = v[q];
+                    }
                 }
             }
             tc_fence_before();
@@ -518,10 +566,15 @@ bool project_tc_supported(int p, int r_max) {
            project_tc_smem(p) <= 227 * 1024 && backproject_tc_smem(p) <= 227 * 1024;
 }
 
+// the kernels index with 32-bit element offsets
+static bool offsets_fit(long long elems) { return elems > 0 && elems < (1LL << 31); }
+
 hyde_status launch_project_pad_tc(const float* Y, int p, int H, int W, const float* P, int r,
                                   int ldw, float* Zp, int Hp, int Wp, int* status,
                                   cudaStream_t s) {
     if (!project_tc_supported(p, r)) return HYDE_ERR_SHAPE;
+    if (!offsets_fit((long long)p * H * W) || !offsets_fit((long long)kPjN * Hp * Wp))
+        return HYDE_ERR_SHAPE;
     const size_t smem = project_tc_smem(p);
     if (ensure_smem_limit((const void*)project_tc_kernel, (int)smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
@@ -537,6 +590,7 @@ hyde_status launch_project_pad_tc(const float* Y, int p, int H, int W, const flo
 hyde_status launch_backproject_tc(const float* Zh, long long n, const float* Q, int p, int ldw,
                                   const int* rank, float* X, int* status, cudaStream_t s) {
     if (!project_tc_supported(p, ldw > kBpK ? kBpK : ldw)) return HYDE_ERR_SHAPE;
+    if (!offsets_fit((long long)(p > kBpK ? p : kBpK) * n)) return HYDE_ERR_SHAPE;
     const size_t smem = backproject_tc_smem(p);
     if (ensure_smem_limit((const void*)backproject_tc_kernel, (int)smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
