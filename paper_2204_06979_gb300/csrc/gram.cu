@@ -143,32 +143,143 @@ gram_partial_kernel(const float* __restrict__ Y, int p, long long n, int PT,
     }
 }
 
+// Variant with 8 x 4 tiles (rows 8ti.., columns 4tj.., tj >= 2ti: PT (PT+1)
+// tiles) and paired FP32 FMAs: fma.rn.f32x2 updates an (even pixel, odd
+// pixel) accumulator pair of one (i, j) from the (x, y) or (z, w) halves of
+// the float4 operands, so 128 FMAs of four pixels take 64 instructions. The
+// stage rows are swizzled by (b >> 2) & 7 so that the 4-row B tiles of a
+// warp's lanes fall on different float4 columns.
+__device__ __forceinline__ void fma_f32x2(float& c0, float& c1, float a0, float a1, float b0,
+                                          float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%0, %1};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+__device__ __forceinline__ void tile84_of(int t, int PT, int& ti, int& tj) {
+    // row ti holds the 2 PT - 2 ti tiles tj = 2 ti .. 2 PT - 1
+    int row = 0, rem = t, len = 2 * PT;
+    while (rem >= len) { rem -= len; ++row; len -= 2; }
+    ti = row;
+    tj = 2 * row + rem;
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+gram_partial84_kernel(const float* __restrict__ Y, int p, long long n, int PT, int ntiles,
+                      float* __restrict__ partials) {
+    extern __shared__ float4 sm4[];
+    const int p8 = PT * 8;
+    const int t = threadIdx.x;
+    const int T = blockDim.x;
+    for (int i = t; i < (p8 - p) * 8 * STAGES; i += T) {
+        const int st = i / ((p8 - p) * 8), o = i % ((p8 - p) * 8);
+        sm4[st * p8 * 8 + p * 8 + o] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const long long nchunks = (n + KC - 1) / KC;
+    const long long c0 = (long long)blockIdx.x * nchunks / gridDim.x;
+    const long long c1 = (long long)(blockIdx.x + 1) * nchunks / gridDim.x;
+    const int lane = t & 31, wrp = t >> 5, nw = T >> 5;
+    const int kq = lane >> 2, kr = lane & 3;
+    const long long bstride = (long long)nw * n;
+    auto issue = [&](long long c, int st) {
+        float* d = reinterpret_cast<float*>(sm4 + st * p8 * 8);
+        const long long pix = c * KC + lane;
+        const bool ok = pix < n;
+        const float* src = Y + (long long)wrp * n + (ok ? pix : 0);
+        for (int b = wrp; b < p; b += nw, src += bstride)
+            cp_async4(d + b * 32 + ((kq ^ ((b >> 2) & 7)) << 2) + kr, src, ok);
+    };
+    const bool active = t < ntiles;
+    int ti = 0, tj = 0;
+    if (active) tile84_of(t, PT, ti, tj);
+    float ae[8][4], ao[8][4];   // even / odd pixel accumulators
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ae[i][j] = ao[i][j] = 0.f;
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (c0 + s < c1) issue(c0 + s, s);
+        cp_async_commit();
+    }
+    for (long long c = c0; c < c1; ++c) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();
+        const long long nxt = c + STAGES - 1;
+        if (nxt < c1) issue(nxt, (int)(nxt - c0) % STAGES);
+        cp_async_commit();
+        if (active) {
+            const float4* B = sm4 + ((int)(c - c0) % STAGES) * p8 * 8;
+            const float4* Ba = B + 64 * ti;   // rows 8ti .. 8ti+7
+            const float4* Bb = B + 32 * tj;   // rows 4tj .. 4tj+3
+            const int xa0 = (2 * ti) & 7, xa1 = (2 * ti + 1) & 7, xb = tj & 7;
+#pragma unroll 1
+            for (int q = 0; q < 8; ++q) {
+                float4 a[8], b[4];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] = Ba[8 * i + (q ^ (i < 4 ? xa0 : xa1))];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bb[8 * j + (q ^ xb)];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        fma_f32x2(ae[i][j], ao[i][j], a[i].x, a[i].y, b[j].x, b[j].y);
+                        fma_f32x2(ae[i][j], ao[i][j], a[i].z, a[i].w, b[j].z, b[j].w);
+                    }
+            }
+        }
+    }
+    cp_async_wait<0>();
+    if (active) {
+        float4* out = reinterpret_cast<float4*>(partials + ((long long)blockIdx.x * ntiles + t) * 32);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            out[i] = make_float4(ae[i][0] + ao[i][0], ae[i][1] + ao[i][1], ae[i][2] + ao[i][2],
+                                 ae[i][3] + ao[i][3]);
+    }
+}
+
 // Block partials -> R in double. Each thread sums one element over a segment
 // of kReduceSeg blocks (independent loads, double accumulation) and adds the
 // segment total to R with a double atomic; R is cleared beforehand.
 constexpr int kReduceSeg = 16;
 
 __global__ void gram_reduce_kernel(const float* __restrict__ partials, int nblocks,
-                                   int p, int PT, int ntiles, double* __restrict__ R,
+                                   int p, int PT, int ntiles, int mode, double* __restrict__ R,
                                    int* status) {
+    const int te = mode == 0 ? 64 : 32;   // elements per tile
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)ntiles * 64) return;
+    if (idx >= (long long)ntiles * te) return;
     const int b0 = blockIdx.y * kReduceSeg;
     const int b1 = min(b0 + kReduceSeg, nblocks);
     if (b0 >= b1) return;
-    const long long stride = (long long)ntiles * 64;
+    const long long stride = (long long)ntiles * te;
     double s = 0.0;
 #pragma unroll 4
     for (int b = b0; b < b1; ++b) s += (double)__ldg(partials + (long long)b * stride + idx);
-    const int t = (int)(idx / 64), e = (int)(idx % 64);
-    int ti, tj;
-    tile_of(t, PT, ti, tj);
-    const int i = 8 * ti + e / 8, j = 8 * tj + e % 8;
-    if (i < p && j < p) {
+    const int t = (int)(idx / te), e = (int)(idx % te);
+    int ti, tj, i, j;
+    if (mode == 0) {
+        tile_of(t, PT, ti, tj);
+        i = 8 * ti + e / 8;
+        j = 8 * tj + e % 8;
+    } else {
+        tile84_of(t, PT, ti, tj);
+        i = 8 * ti + e / 4;
+        j = 4 * tj + e % 4;
+    }
+    // tiles on the diagonal hold both (i, j) and (j, i): take i <= j only
+    if (i < p && j < p && i <= j) {
         if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
         atomicAdd(&R[(long long)i * p + j], s);
-        // a diagonal tile holds both (i, j) and (j, i): no mirror there
-        if (ti != tj) atomicAdd(&R[(long long)j * p + i], s);
+        if (i != j) atomicAdd(&R[(long long)j * p + i], s);
     }
 }
 
@@ -191,19 +302,46 @@ static hyde_status plan_for(GramPlan& g, long long n) {
     return HYDE_OK;
 }
 
+template <int MAXT>
+static hyde_status plan_for84(GramPlan& g, long long n) {
+    cudaError_t e = ensure_smem_limit((const void*)gram_partial84_kernel<MAXT>, (int)g.smem);
+    if (e != cudaSuccess) return HYDE_ERR_CUDA;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_partial84_kernel<MAXT>,
+                                                      g.threads, g.smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    long long nchunks = (n + KC - 1) / KC;
+    long long blocks = (long long)sms * per_sm;
+    if (blocks > nchunks) blocks = nchunks;
+    g.blocks = (int)blocks;
+    return HYDE_OK;
+}
+
 hyde_status gram_plan(int p, long long n, GramPlan* plan) {
     if (p < 1 || p > kMaxBandsGram || n < 1) return HYDE_ERR_SHAPE;
     GramPlan g;
     g.PT = (p + 7) / 8;
-    g.ntiles = g.PT * (g.PT + 1) / 2;
-    g.threads = (g.ntiles + 31) / 32 * 32;
-    if (g.threads > kGramMaxThreads) return HYDE_ERR_SHAPE;
     g.smem = (size_t)STAGES * g.PT * 8 * KC * sizeof(float);
-    hyde_status st = g.threads <= 256   ? plan_for<256>(g, n)
-                     : g.threads <= 384 ? plan_for<384>(g, n)
-                                        : plan_for<kGramMaxThreads>(g, n);
+    hyde_status st;
+    if (g.PT * (g.PT + 1) <= 384) {
+        // 8 x 4 tiles with paired FMAs, one block of up to 384 threads per SM
+        g.mode = 1;
+        g.ntiles = g.PT * (g.PT + 1);
+        g.threads = (g.ntiles + 31) / 32 * 32;
+        st = plan_for84<384>(g, n);
+    } else {
+        g.mode = 0;
+        g.ntiles = g.PT * (g.PT + 1) / 2;
+        g.threads = (g.ntiles + 31) / 32 * 32;
+        if (g.threads > kGramMaxThreads) return HYDE_ERR_SHAPE;
+        st = g.threads <= 256   ? plan_for<256>(g, n)
+             : g.threads <= 384 ? plan_for<384>(g, n)
+                                : plan_for<kGramMaxThreads>(g, n);
+    }
     if (st != HYDE_OK) return st;
-    g.partial_bytes = (size_t)g.blocks * g.ntiles * 64 * sizeof(float);
+    g.partial_bytes = (size_t)g.blocks * g.ntiles * (g.mode == 0 ? 64 : 32) * sizeof(float);
     *plan = g;
     return HYDE_OK;
 }
@@ -212,7 +350,10 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
                         float* partials, double* R, int* status, cudaStream_t s) {
     long long nchunks = (n + KC - 1) / KC;
     long long per = (nchunks + g.blocks - 1) / g.blocks;
-    if (g.threads <= 256)
+    if (g.mode == 1)
+        gram_partial84_kernel<384><<<g.blocks, g.threads, g.smem, s>>>(Y, p, n, g.PT, g.ntiles,
+                                                                       partials);
+    else if (g.threads <= 256)
         gram_partial_kernel<256><<<g.blocks, g.threads, g.smem, s>>>(Y, p, n, g.PT, g.ntiles,
                                                                      per, partials);
     else if (g.threads <= 384)
@@ -221,11 +362,12 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
     else
         gram_partial_kernel<kGramMaxThreads><<<g.blocks, g.threads, g.smem, s>>>(
             Y, p, n, g.PT, g.ntiles, per, partials);
-    long long tot = (long long)g.ntiles * 64;
+    long long tot = (long long)g.ntiles * (g.mode == 0 ? 64 : 32);
     if (cudaMemsetAsync(R, 0, (size_t)p * p * sizeof(double), s) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 rgrid((unsigned)((tot + 255) / 256), (g.blocks + kReduceSeg - 1) / kReduceSeg);
-    gram_reduce_kernel<<<rgrid, 256, 0, s>>>(partials, g.blocks, p, g.PT, g.ntiles, R, status);
+    gram_reduce_kernel<<<rgrid, 256, 0, s>>>(partials, g.blocks, p, g.PT, g.ntiles, g.mode, R,
+                                             status);
     return cuda_status(cudaGetLastError());
 }
 
@@ -277,9 +419,9 @@ extern "C" hyde_status hyde_gram_noalloc(const float* Y, int p, long long n, dou
     GramPlan g;
     hyde_status st = gram_plan(p, n, &g);
     if (st != HYDE_OK) return st;
-    // each block writes ntiles * 64 floats of partials; use as many blocks as
+    // each block writes one partial per tile element; use as many blocks as
     // the fixed scratch holds (never more than the occupancy-sized grid)
-    const size_t per_block = (size_t)g.ntiles * 64 * sizeof(float);
+    const size_t per_block = (size_t)g.ntiles * (g.mode == 0 ? 64 : 32) * sizeof(float);
     const size_t max_blocks = kNoAllocScratchBytes / per_block;
     if (max_blocks < 1) return HYDE_ERR_SHAPE;
     if ((size_t)g.blocks > max_blocks) g.blocks = (int)max_blocks;

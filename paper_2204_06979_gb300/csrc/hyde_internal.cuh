@@ -66,8 +66,9 @@ inline hyde_status cuda_status(cudaError_t e) {
 
 // ----------------------------------------------------------------- Gram
 struct GramPlan {
+    int mode;        // 0: 8x8 tiles, FFMA; 1: 8x4 tiles, paired FP32 FMA (f32x2)
     int PT;          // 8-band tile rows
-    int ntiles;      // upper-triangle 8x8 tiles
+    int ntiles;      // upper-triangle tiles
     int threads;     // threads per block
     int blocks;      // blocks in the grid
     size_t smem;     // dynamic shared memory per block
