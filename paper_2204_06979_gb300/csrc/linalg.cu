@@ -43,54 +43,6 @@ constexpr int kMaxRegT = 6;   // register tiles up to 6 x 6 (p <= 192)
 // --------------------------------------------------------------------------
 constexpr float kPivotFloor = 2e-6f;
 
-// Row or column ko of a T x T register tile (ko uniform across the block):
-// a switch selects one of T straight-line cases instead of T^2 predicated
-// moves.
-#define HYDE_CASES10(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9)
-
-template <int T>
-__device__ __forceinline__ void tile_row_out(const float (&a)[T][T], int ko, float* dst) {
-    switch (ko) {
-#define HYDE_ROW(C) \
-    case C: if (C < T) { _Pragma("unroll") for (int jj = 0; jj < T; ++jj) dst[jj] = a[C < T ? C : 0][jj]; } break;
-        HYDE_CASES10(HYDE_ROW)
-#undef HYDE_ROW
-        default: break;
-    }
-}
-template <int T>
-__device__ __forceinline__ void tile_col_out(const float (&a)[T][T], int ko, float* dst) {
-    switch (ko) {
-#define HYDE_COL(C) \
-    case C: if (C < T) { _Pragma("unroll") for (int ii = 0; ii < T; ++ii) dst[ii] = a[ii][C < T ? C : 0]; } break;
-        HYDE_CASES10(HYDE_COL)
-#undef HYDE_COL
-        default: break;
-    }
-}
-template <int T>
-__device__ __forceinline__ void tile_row_set(float (&a)[T][T], int ko, const float (&v)[T], float s) {
-    switch (ko) {
-#define HYDE_RSET(C) \
-    case C: if (C < T) { _Pragma("unroll") for (int jj = 0; jj < T; ++jj) a[C < T ? C : 0][jj] = v[jj] * s; } break;
-        HYDE_CASES10(HYDE_RSET)
-#undef HYDE_RSET
-        default: break;
-    }
-}
-template <int T>
-__device__ __forceinline__ void tile_col_set(float (&a)[T][T], int ko, const float (&v)[T], int diag,
-                                             float piv) {
-    // column ko := -v; entry (diag, ko) := piv when diag >= 0
-    switch (ko) {
-#define HYDE_CSET(C) \
-    case C: if (C < T) { _Pragma("unroll") for (int ii = 0; ii < T; ++ii) a[ii][C < T ? C : 0] = ii == diag ? piv : -v[ii]; } break;
-        HYDE_CASES10(HYDE_CSET)
-#undef HYDE_CSET
-        default: break;
-    }
-}
-
 // The G x G threads form a grid over the matrix: thread (ty, tx) owns the
 // T x T tile of rows ty T.. and columns tx T.. in registers. A step costs T^2
 // FMAs and 2T shared loads per thread plus one barrier; the pivot row and
@@ -131,27 +83,47 @@ noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ain
             a[ii][jj] = v;
         }
     }
-    for (int k = 0; k < p; ++k) {
-        const int buf = k & 1;
-        const int kt = k / T, ko = k - kt * T;
-        if (ty == kt) tile_row_out<T>(a, ko, &s_row[buf][c0]);
-        if (tx == kt) tile_col_out<T>(a, ko, &s_col[buf][r0]);
-        __syncthreads();   // one barrier per step: the vectors are double-buffered
-        const float pk = s_col[buf][k];
-        if (t == 0 && !(pk > kPivotFloor)) set_status(status, HYDE_ERR_NUMERIC);
-        const float piv = 1.0f / pk;
-        float rk[T], ck[T];
+    // Steps k = kt T + ko with ko unrolled: the pivot row and column of the
+    // register tile are compile-time indices (no runtime selection).
+    for (int kt = 0; kt * T < p; ++kt) {
 #pragma unroll
-        for (int q = 0; q < T; ++q) {
-            rk[q] = s_row[buf][c0 + q];
-            ck[q] = s_col[buf][r0 + q] * piv;
+        for (int ko = 0; ko < T; ++ko) {
+            const int k = kt * T + ko;
+            if (k < p) {
+                const int buf = k & 1;
+                if (ty == kt) {
+#pragma unroll
+                    for (int jj = 0; jj < T; ++jj) s_row[buf][c0 + jj] = a[ko][jj];
+                }
+                if (tx == kt) {
+#pragma unroll
+                    for (int ii = 0; ii < T; ++ii) s_col[buf][r0 + ii] = a[ii][ko];
+                }
+                __syncthreads();   // one barrier per step: the vectors are double-buffered
+                const float pk = s_col[buf][k];
+                if (t == 0 && !(pk > kPivotFloor)) set_status(status, HYDE_ERR_NUMERIC);
+                // ~1 ulp reciprocal: the FP64 Newton step on the diagonal follows
+                const float piv = __fdividef(1.0f, pk);
+                float rk[T], ck[T];
+#pragma unroll
+                for (int q = 0; q < T; ++q) {
+                    rk[q] = s_row[buf][c0 + q];
+                    ck[q] = s_col[buf][r0 + q] * piv;
+                }
+#pragma unroll
+                for (int ii = 0; ii < T; ++ii)
+#pragma unroll
+                    for (int jj = 0; jj < T; ++jj) a[ii][jj] = fmaf(-ck[ii], rk[jj], a[ii][jj]);
+                if (ty == kt) {   // row k: a_kj * piv
+#pragma unroll
+                    for (int jj = 0; jj < T; ++jj) a[ko][jj] = rk[jj] * piv;
+                }
+                if (tx == kt) {   // column k: -a_ik * piv, and the pivot itself
+#pragma unroll
+                    for (int ii = 0; ii < T; ++ii) a[ii][ko] = (ty == kt && ii == ko) ? piv : -ck[ii];
+                }
+            }
         }
-#pragma unroll
-        for (int ii = 0; ii < T; ++ii)
-#pragma unroll
-            for (int jj = 0; jj < T; ++jj) a[ii][jj] = fmaf(-ck[ii], rk[jj], a[ii][jj]);
-        if (ty == kt) tile_row_set<T>(a, ko, rk, piv);                 // row k: a_kj * piv
-        if (tx == kt) tile_col_set<T>(a, ko, ck, ty == kt ? ko : -1, piv);   // column k, pivot
     }
 #pragma unroll
     for (int ii = 0; ii < T; ++ii) {
@@ -719,6 +691,16 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
         float* a = A + i * lda + k;
         *a = i <= k ? 0.f : (i == k + 1 ? 1.0f : *a * scv[k]);
     }
+    __syncthreads();
+    // cpair[k] = v_{k-1} . v_k (k >= 1) for the paired back-transformation;
+    // the reflector scales are no longer needed, so their array holds it
+    float* const cpair = vf;
+    for (int k = 1 + wid; k <= p - 3; k += 32) {
+        float s2 = 0.f;
+        for (int i = k + lane; i < p; i += 32) s2 = fmaf(A[i * lda + k - 1], A[i * lda + k], s2);
+        s2 = warp_sum(s2);
+        if (lane == 0) cpair[k] = s2;
+    }
     if (t == 0) {
         // with p >= 3 the last step left column p-2 in cvec (row p-2 of A is
         // not updated by the sweep); A[p-1][p-1] is current
@@ -745,37 +727,49 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
             const int i = lane + 32 * b;
             x[b] = i < p ? X[wid * p + i] : 0.f;
         }
-        // reflector k is column k of A (explicit); the next reflector's tau
-        // and column are loaded while this one's warp sum runs
-        float tau_c = 0.f, col[NB];
-        if (p >= 3) {
-            tau_c = tauv[p - 3];
+        // Reflectors k (column k of A, explicit) in pairs (k, k-1): both dot
+        // products come from one pass and two interleaved warp sums;
+        // H_{k-1} H_k x = x - d_a v_k - d_b v_{k-1} with d_a = tau_k v_k.x and
+        // d_b = tau_{k-1} (v_{k-1}.x - d_a v_{k-1}.v_k) (cpair[k]). The next
+        // pair's columns are loaded while this pair's sums run.
+        auto load_col = [&](int k, float (&c)[NB]) {
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const int i = lane + 32 * b;
-                col[b] = (b < NB - 1 || i < p) ? A[i * lda + (p - 3)] : 0.f;
+                c[b] = (b < NB - 1 || i < p) ? A[i * lda + k] : 0.f;
             }
+        };
+        float ca[NB], cb[NB];
+        int k = p - 3;
+        if (k >= 1) { load_col(k, ca); load_col(k - 1, cb); }
+        for (; k >= 1; k -= 2) {
+            float va[NB], vb[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) { va[b] = ca[b]; vb[b] = cb[b]; }
+            const float ta = tauv[k], tb = tauv[k - 1], cab = cpair[k];
+            if (k >= 3) { load_col(k - 2, ca); load_col(k - 3, cb); }
+            float sa = 0.f, sb = 0.f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) { sa = fmaf(va[b], x[b], sa); sb = fmaf(vb[b], x[b], sb); }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            }
+            const float da = ta * sa;
+            const float db = tb * fmaf(-da, cab, sb);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) x[b] = fmaf(-db, vb[b], fmaf(-da, va[b], x[b]));
         }
-        for (int k = p - 3; k >= 0; --k) {
-            const float tau = tau_c;
-            float vk[NB];
+        if (k == 0) {   // an odd count leaves reflector 0
+            float v0[NB];
+            load_col(0, v0);
+            float s0 = 0.f;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) vk[b] = col[b];
-            if (k > 0) {
-                tau_c = tauv[k - 1];
+            for (int b = 0; b < NB; ++b) s0 = fmaf(v0[b], x[b], s0);
+            const float d0 = tauv[0] * warp_sum(s0);
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const int i = lane + 32 * b;
-                    col[b] = (b < NB - 1 || i < p) ? A[i * lda + (k - 1)] : 0.f;
-                }
-            }
-            if (tau == 0.f) continue;
-            float dt = 0.f;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) dt = fmaf(vk[b], x[b], dt);
-            dt = warp_sum(dt) * tau;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) x[b] = fmaf(-dt, vk[b], x[b]);
+            for (int b = 0; b < NB; ++b) x[b] = fmaf(-d0, v0[b], x[b]);
         }
         float best = -1.f;
         int bi = 0;
