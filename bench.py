@@ -43,7 +43,15 @@ FP32_SM_PEAK_TFLOPS = 128 * 2 * 2.070e9 / 1e12         # one SM, for single-bloc
 # dominant kernel, from one ncu capture of the 349 x 1905 x 144 cube; keyed by
 # (stage, precision). profiles/ holds the capture summaries; an entry is
 # removed when its kernel changes.
-NCU_TRAFFIC: dict = {}
+NCU_TRAFFIC: dict = {
+    # gram_partial84 385.69 + 3.24 MB, gram_reduce 6.83 MB
+    ("gram", "fp32"): 395.76e6,
+    # gram_tc 385.73 + 3.27 MB, gram_tc_reduce 8.42 MB
+    ("gram", "bf16x3"): 397.42e6,
+    # eig_fast (one thread block) 0.25 MB
+    ("eig", "fp32"): 0.25e6,
+    ("eig", "bf16x3"): 0.25e6,
+}
 
 
 def _small_dense_flops(stage: str, p: int, r: int) -> float:
