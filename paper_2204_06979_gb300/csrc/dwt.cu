@@ -95,6 +95,146 @@ dwt_level_kernel(const float* __restrict__ src, long long src_bs, int src_ld, in
     }
 }
 
+// --------------------------------------------------------------------------
+// Analysis level for a source that is already padded (no reflection), as a
+// persistent pipeline: block (g, image) walks tiles g, g + G, ... of one
+// image, 16 x 64 coefficients per subband each, from a 34 x 132 input tile.
+// The next tile streams into the other half of a double buffer with cp.async
+// (16-byte copies where the row is 16-byte aligned and the chunk does not
+// reach the image edge, 4-byte copies with the periodic wrap elsewhere)
+// while the current one is filtered: the row pass reads 10 inputs and writes
+// 4 outputs per thread as float4, the column pass forms the four subbands of
+// 4 coefficients per thread and stores them as float4 rows.
+// --------------------------------------------------------------------------
+constexpr int FTH = 16, FTW = 64;           // coefficients per subband per tile
+constexpr int FIH = 2 * FTH + 2;            // input rows
+constexpr int FIW = 2 * FTW + 4;            // input columns (2 FTW + 2 used, multiple of 4)
+constexpr int kFThreads = 256;
+
+__device__ __forceinline__ void cpa16(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cpa4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__global__ void __launch_bounds__(kFThreads)
+dwt_level_pipe_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int h, int w,
+                      float* __restrict__ coef, long long coef_bs, int coef_ld,
+                      float* __restrict__ ll, long long ll_bs, int ll_ld) {
+    extern __shared__ float4 fsm4[];
+    float* inb = reinterpret_cast<float*>(fsm4);     // [2][FIH][FIW]
+    float* ra = inb + 2 * FIH * FIW;                  // [FIH][FTW]
+    float* rd = ra + FIH * FTW;                       // [FIH][FTW]
+    const int tid = threadIdx.x;
+    const int b = blockIdx.y, G = gridDim.x;
+    const int hh = h >> 1, wh = w >> 1;
+    const int tiles_x = (wh + FTW - 1) / FTW, tiles_y = (hh + FTH - 1) / FTH;
+    const int ntiles = tiles_x * tiles_y;
+    const float* S = src + (long long)b * src_bs;
+    float* CB = coef + (long long)b * coef_bs;
+    float* LB = ll + (long long)b * ll_bs;
+    const bool vin = (src_ld & 3) == 0 && ((reinterpret_cast<uintptr_t>(S) & 15) == 0);
+    const bool vout = (wh & 3) == 0 && (coef_ld & 3) == 0 && (ll_ld & 3) == 0 &&
+                      ((reinterpret_cast<uintptr_t>(CB) & 15) == 0) &&
+                      ((reinterpret_cast<uintptr_t>(LB) & 15) == 0);
+
+    auto load_tile = [&](int t, int buf) {
+        const int ty0 = (t / tiles_x) * FTH, tx0 = (t % tiles_x) * FTW;
+        float* in = inb + buf * FIH * FIW;
+        for (int e = tid; e < FIH * (FIW / 4); e += kFThreads) {
+            const int r = e / (FIW / 4), cq = e - r * (FIW / 4);
+            const int y = wrap(2 * ty0 + r, h);
+            const float* row = S + (long long)y * src_ld;
+            const int x0 = 2 * tx0 + 4 * cq;
+            float* d = in + r * FIW + 4 * cq;
+            if (vin && x0 + 3 < w) {
+                cpa16(d, row + x0);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cpa4(d + u, row + wrap(x0 + u, w));
+            }
+        }
+    };
+
+    int t = blockIdx.x;
+    if (t < ntiles) load_tile(t, 0);
+    cpa_commit();
+    for (int it = 0; t < ntiles; ++it, t += G) {
+        const int buf = it & 1;
+        if (t + G < ntiles) load_tile(t + G, buf ^ 1);
+        cpa_commit();
+        cpa_wait<1>();
+        __syncthreads();   // tile t landed; the previous column pass is done
+        const float* in = inb + buf * FIH * FIW;
+        for (int e = tid; e < FIH * (FTW / 4); e += kFThreads) {
+            const int r = e / (FTW / 4), kq = e - r * (FTW / 4);
+            const float* ir = in + r * FIW + 8 * kq;
+            const float4 v0 = *reinterpret_cast<const float4*>(ir);
+            const float4 v1 = *reinterpret_cast<const float4*>(ir + 4);
+            const float2 v2 = *reinterpret_cast<const float2*>(ir + 8);
+            const float x[10] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
+            float a[4], d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = kH0 * x[2 * u] + kH1 * x[2 * u + 1] + kH2 * x[2 * u + 2] + kH3 * x[2 * u + 3];
+                d[u] = kG0 * x[2 * u] + kG1 * x[2 * u + 1] + kG2 * x[2 * u + 2] + kG3 * x[2 * u + 3];
+            }
+            *reinterpret_cast<float4*>(ra + r * FTW + 4 * kq) = make_float4(a[0], a[1], a[2], a[3]);
+            *reinterpret_cast<float4*>(rd + r * FTW + 4 * kq) = make_float4(d[0], d[1], d[2], d[3]);
+        }
+        __syncthreads();   // row outputs complete; buffer `buf` may be refilled
+        const int ty0 = (t / tiles_x) * FTH, tx0 = (t % tiles_x) * FTW;
+        const int j = tid / (FTW / 4), kq = tid - j * (FTW / 4);
+        const int J = ty0 + j, Kc = tx0 + 4 * kq;
+        if (J < hh && Kc < wh) {
+            float4 A[4], D[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                A[m] = *reinterpret_cast<const float4*>(ra + (2 * j + m) * FTW + 4 * kq);
+                D[m] = *reinterpret_cast<const float4*>(rd + (2 * j + m) * FTW + 4 * kq);
+            }
+            auto comb = [](const float4 (&V)[4], float c0, float c1, float c2, float c3) {
+                return make_float4(c0 * V[0].x + c1 * V[1].x + c2 * V[2].x + c3 * V[3].x,
+                                   c0 * V[0].y + c1 * V[1].y + c2 * V[2].y + c3 * V[3].y,
+                                   c0 * V[0].z + c1 * V[1].z + c2 * V[2].z + c3 * V[3].z,
+                                   c0 * V[0].w + c1 * V[1].w + c2 * V[2].w + c3 * V[3].w);
+            };
+            const float4 LL = comb(A, kH0, kH1, kH2, kH3);
+            const float4 LH = comb(A, kG0, kG1, kG2, kG3);   // column detail
+            const float4 HL = comb(D, kH0, kH1, kH2, kH3);   // row detail
+            const float4 HH = comb(D, kG0, kG1, kG2, kG3);
+            float* pLL = LB + (long long)J * ll_ld + Kc;
+            float* pHL = CB + (long long)J * coef_ld + wh + Kc;
+            float* pLH = CB + (long long)(hh + J) * coef_ld + Kc;
+            float* pHH = CB + (long long)(hh + J) * coef_ld + wh + Kc;
+            if (vout) {
+                *reinterpret_cast<float4*>(pLL) = LL;
+                *reinterpret_cast<float4*>(pHL) = HL;
+                *reinterpret_cast<float4*>(pLH) = LH;
+                *reinterpret_cast<float4*>(pHH) = HH;
+            } else {
+                const float ll4[4] = {LL.x, LL.y, LL.z, LL.w}, hl4[4] = {HL.x, HL.y, HL.z, HL.w};
+                const float lh4[4] = {LH.x, LH.y, LH.z, LH.w}, hh4[4] = {HH.x, HH.y, HH.z, HH.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (Kc + q < wh) {
+                        pLL[q] = ll4[q];
+                        pHL[q] = hl4[q];
+                        pLH[q] = lh4[q];
+                        pHH[q] = hh4[q];
+                    }
+            }
+        }
+    }
+    cpa_wait<0>();
+}
+
 __device__ __forceinline__ float soft(float c, float lam) {
     return copysignf(fmaxf(fabsf(c) - lam, 0.f), c);
 }
@@ -190,6 +330,16 @@ static inline float* ll_buf(float* scratch, int batch, int Hp, int Wp, int j,
 hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int Wp,
                         int levels, float* scratch, cudaStream_t s) {
     const long long cbs = (long long)Hp * Wp;
+    const size_t pipe_smem = (size_t)(2 * FIH * FIW + 2 * FIH * FTW) * sizeof(float);
+    if (ensure_smem_limit((const void*)dwt_level_pipe_kernel, (int)pipe_smem) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    const int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    int pipe_per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pipe_per_sm, dwt_level_pipe_kernel,
+                                                      kFThreads, pipe_smem) != cudaSuccess ||
+        pipe_per_sm < 1)
+        pipe_per_sm = 1;
     for (int lev = 1; lev <= levels; ++lev) {
         const int h = Hp >> (lev - 1), w = Wp >> (lev - 1);
         const float* sp;
@@ -207,12 +357,18 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
         if (lev == levels) { lp = coef; lbs = cbs; lld = Wp; }
         else { lp = ll_buf(scratch, batch, Hp, Wp, lev, &lbs); lld = w / 2; }
         dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
-        if (hv < h || wv < w)
+        if (hv < h || wv < w) {
             dwt_level_kernel<true><<<grid, kThreads, 0, s>>>(sp, sbs, sld, hv, wv, h, w, coef,
                                                              cbs, Wp, lp, lbs, lld);
-        else
-            dwt_level_kernel<false><<<grid, kThreads, 0, s>>>(sp, sbs, sld, hv, wv, h, w, coef,
-                                                              cbs, Wp, lp, lbs, lld);
+        } else {
+            // padded source: the pipelined kernel, a few tiles per block
+            const int ntiles = ((w / 2 + FTW - 1) / FTW) * ((h / 2 + FTH - 1) / FTH);
+            int G = (pipe_per_sm * sms + batch - 1) / batch;
+            if (G > ntiles) G = ntiles;
+            if (G < 1) G = 1;
+            dwt_level_pipe_kernel<<<dim3(G, batch), kFThreads, pipe_smem, s>>>(
+                sp, sbs, sld, h, w, coef, cbs, Wp, lp, lbs, lld);
+        }
     }
     return cuda_status(cudaGetLastError());
 }

@@ -21,19 +21,24 @@ namespace {
 
 // Every thread owns a private column of the block's histogram (layout
 // [bin][thread], so a thread's updates never conflict with another's and
-// need no atomics); the block reduces the columns and adds them to the
-// global table with one atomic per bin.
+// need no atomics): 16-bit counts (the launcher bounds the values a thread
+// sees below 2^16) and float sums, 6 bytes per bin and thread, so that a
+// 256-thread block fits in 96 KB. The block reduces the columns and adds them
+// to the global table with one atomic per bin. Each lane keeps eight float4
+// loads in flight.
+constexpr int kHistUnroll = 8;
+
 __global__ void __launch_bounds__(256)
 sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl, int K,
                  float inv_delta, int rows_per_block, unsigned int* __restrict__ counts,
                  double* __restrict__ sums, double* __restrict__ sum_all) {
     extern __shared__ unsigned char smraw[];
     const int T = blockDim.x, tid = threadIdx.x;
-    unsigned int* hc = reinterpret_cast<unsigned int*>(smraw);     // [K][T]
-    float* hs = reinterpret_cast<float*>(hc + (size_t)K * T);      // [K][T]
+    float* hs = reinterpret_cast<float*>(smraw);                         // [K][T]
+    unsigned short* hc = reinterpret_cast<unsigned short*>(hs + (size_t)K * T);   // [K][T]
     const int i = blockIdx.y;
     const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
-    for (int e = tid; e < K * T; e += T) { hc[e] = 0u; hs[e] = 0.f; }
+    for (int e = tid; e < K * T; e += T) { hc[e] = 0; hs[e] = 0.f; }
     __syncthreads();
     const int y0 = blockIdx.x * rows_per_block;
     const int y1 = min(y0 + rows_per_block, Hp);
@@ -47,7 +52,7 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
         const float t = ceilf(fabsf(c) * inv_delta);
         if (t <= kmax) {
             const int k = (int)t;
-            hc[k * T + tid] += 1u;
+            hc[k * T + tid] += 1;
             hs[k * T + tid] += c2;
         }
     };
@@ -56,16 +61,15 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
         for (int y = y0 + wid; y < y1; y += nw) {
             const float4* row = reinterpret_cast<const float4*>(base + (long long)y * Wp);
             const bool yll = y < hl;
-            // four float4 loads in flight per lane, then their 16 values
-            for (int x40 = lane; x40 < W4; x40 += 128) {
-                float4 v[4];
+            for (int x40 = lane; x40 < W4; x40 += 32 * kHistUnroll) {
+                float4 v[kHistUnroll];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kHistUnroll; ++u) {
                     const int x4 = x40 + 32 * u;
                     v[u] = x4 < W4 ? __ldg(row + x4) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kHistUnroll; ++u) {
                     const int x4 = x40 + 32 * u;
                     if (x4 < W4) {
                         const int x = x4 * 4;
@@ -265,23 +269,29 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int l
                              double delta, const SureBufs& b, cudaStream_t s) {
     int sms = device_sm_count();
     if (sms <= 0) return HYDE_ERR_CUDA;
+    // threads per block: the private histograms (6 bytes per bin and thread)
+    // stay within 96 KB so that two blocks share an SM
+    int threads = (int)((96 * 1024) / (6 * (size_t)K)) / 32 * 32;
+    if (threads > 256) threads = 256;
+    if (threads < 32) threads = 32;
     int per_comp = (4 * sms + batch - 1) / batch;
+    // a thread must see fewer than 2^16 values (16-bit bin counts)
+    const long long per_thread_cap = 60000;
+    const long long min_blocks = ((long long)Hp * Wp + per_thread_cap * threads - 1) /
+                                 (per_thread_cap * threads);
+    if (per_comp < min_blocks) per_comp = (int)min_blocks;
     if (per_comp > Hp) per_comp = Hp;
     if (per_comp < 1) per_comp = 1;
     int rows = (Hp + per_comp - 1) / per_comp;
     per_comp = (Hp + rows - 1) / rows;
-    // threads per block: the private histograms (8 bytes per bin and thread)
-    // stay within 96 KB so that two blocks share an SM
-    int threads = (int)((96 * 1024) / (8 * (size_t)K)) / 32 * 32;
-    if (threads > 256) threads = 256;
-    if (threads < 32) threads = 32;
-    size_t smem = (size_t)K * threads * 8;
+    if ((long long)rows * Wp > per_thread_cap * threads) return HYDE_ERR_SHAPE;
+    size_t smem = (size_t)K * threads * 6;
     if (ensure_smem_limit((const void*)sure_hist_kernel, (int)smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 grid(per_comp, batch);
     sure_hist_kernel<<<grid, threads, smem, s>>>(coef, Hp, Wp, Hp >> levels, Wp >> levels, K,
-                                                     (float)(1.0 / delta), rows, b.counts,
-                                                     b.sums, b.sum_all);
+                                                 (float)(1.0 / delta), rows, b.counts, b.sums,
+                                                 b.sum_all);
     return cuda_status(cudaGetLastError());
 }
 
