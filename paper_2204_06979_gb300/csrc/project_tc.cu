@@ -240,7 +240,6 @@ project_tc_kernel(const float* __restrict__ Y, int p, int H, int W, const float*
         if (lane == 0) {
             // ---- MMA issuer
             const uint32_t idesc = idesc_bf16(kTileM, kPjN);
-            long long committed = -1;   // last tile whose accumulator was committed
             long long issued = 0;
             for (long long u = 0; u < nstage; ++u) {
                 const long long tl = u / KB;
@@ -270,10 +269,7 @@ project_tc_kernel(const float* __restrict__ Y, int p, int H, int W, const float*
                     umma_bf16(d, sw128_desc(alo + ko), sw128_desc(bhi + ko), idesc, 1u);
                 }
                 umma_commit(smem_u32(&empty_bar[s]));
-                if (kb == KB - 1) {
-                    umma_commit(smem_u32(&tfull_bar[buf]));
-                    committed = tl;
-                }
+                if (kb == KB - 1) umma_commit(smem_u32(&tfull_bar[buf]));
                 issued = u + 1;
             }
             // the MMAs complete in order: wait for the last commit (bounded)
@@ -283,7 +279,6 @@ project_tc_kernel(const float* __restrict__ Y, int p, int H, int W, const float*
                                        (uint32_t)((last / kPjStages) & 1)))
                     *abort_v = 1;
             }
-            (void)committed;
         }
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (pixels)

@@ -43,15 +43,15 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
     const int y0 = blockIdx.x * rows_per_block;
     const int y1 = min(y0 + rows_per_block, Hp);
     const float* base = coef + (long long)i * Hp * Wp;
-    const float kmax = (float)(K - 1);
     float all = 0.f;
+    // bin ceil(|c| / delta) by one float-to-int conversion rounding up; the
+    // value is clamped below 2^24 so the conversion is exact and cannot wrap
     auto one = [&](float c, bool in_ll) {
         const float c2 = c * c;
         all += c2;
         if (in_ll) return;
-        const float t = ceilf(fabsf(c) * inv_delta);
-        if (t <= kmax) {
-            const int k = (int)t;
+        const int k = __float2int_ru(fminf(fabsf(c) * inv_delta, 16777216.f));
+        if (k < K) {
             hc[k * T + tid] += 1;
             hs[k * T + tid] += c2;
         }
@@ -72,11 +72,18 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
                 for (int u = 0; u < kHistUnroll; ++u) {
                     const int x4 = x40 + 32 * u;
                     if (x4 < W4) {
-                        const int x = x4 * 4;
-                        one(v[u].x, yll && x < wl);
-                        one(v[u].y, yll && x + 1 < wl);
-                        one(v[u].z, yll && x + 2 < wl);
-                        one(v[u].w, yll && x + 3 < wl);
+                        if (yll) {   // rows holding the final LL band
+                            const int x = x4 * 4;
+                            one(v[u].x, x < wl);
+                            one(v[u].y, x + 1 < wl);
+                            one(v[u].z, x + 2 < wl);
+                            one(v[u].w, x + 3 < wl);
+                        } else {
+                            one(v[u].x, false);
+                            one(v[u].y, false);
+                            one(v[u].z, false);
+                            one(v[u].w, false);
+                        }
                     }
                 }
             }
