@@ -69,7 +69,7 @@ struct HyresLayout {
     long long N, n;
     GramPlan gram;
     hyde_ws_layout pub;
-    size_t rank_dev, lam_dev, counts, sums, sum_all, P, Q, noise, partials, zp, scratch;
+    size_t rank_dev, lam_dev, counts, sums, sum_all, done, P, Q, noise, partials, zp, scratch;
     size_t zero_begin, zero_end;
 };
 
@@ -110,6 +110,7 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.counts = c.take((size_t)r * K * sizeof(unsigned int));
     l.sums = c.take((size_t)r * K * sizeof(double));
     l.sum_all = c.take((size_t)r * sizeof(double));
+    l.done = c.take(sizeof(unsigned int));
     l.zero_end = c.off;
     l.pub.R = c.take((size_t)p * p * sizeof(double));
     l.pub.sigma = c.take((size_t)p * sizeof(double));
@@ -296,6 +297,7 @@ hyde_status hyde_sure_table(const float* coef, int batch, int Hp, int Wp, int le
     b.sums = reinterpret_cast<double*>(w + align_up((size_t)batch * K * sizeof(unsigned int), kAlign));
     b.sum_all = reinterpret_cast<double*>(reinterpret_cast<char*>(b.sums) +
                                           align_up((size_t)batch * K * sizeof(double), kAlign));
+    b.done = nullptr;   // the table-only path has no selection
     if (cudaMemsetAsync(ws, 0, need, stream) != cudaSuccess) return HYDE_ERR_CUDA;
     const long long N = (long long)Hp * Wp;
     const long long N_det = N - (long long)(Hp >> levels) * (Wp >> levels);
@@ -349,7 +351,8 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     float* zp = at<float>(ws, L.zp);
     float* coef = at<float>(ws, L.pub.coef);
     float* scratch = at<float>(ws, L.scratch);
-    SureBufs sb{at<unsigned int>(ws, L.counts), at<double>(ws, L.sums), at<double>(ws, L.sum_all)};
+    SureBufs sb{at<unsigned int>(ws, L.counts), at<double>(ws, L.sums), at<double>(ws, L.sum_all),
+                at<unsigned int>(ws, L.done)};
     int mark = 0;
     auto stage = [&]() -> hyde_status {
         if (!ev) return HYDE_OK;

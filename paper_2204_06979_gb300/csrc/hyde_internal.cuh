@@ -168,6 +168,7 @@ struct SureBufs {
     unsigned int* counts;   // [batch][K]
     double* sums;           // [batch][K]
     double* sum_all;        // [batch]
+    unsigned int* done;     // blocks finished (selection kernel); cleared with the rest
 };
 size_t sure_accum_bytes(int batch, int K);
 hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp,

@@ -145,27 +145,28 @@ sure_table_kernel(const unsigned int* __restrict__ counts, const double* __restr
     if (lane == 0) S_inf[i] = sum_all[i] - (double)N;
 }
 
-// Table and choice in one block of 32 * batch threads, everything in shared
-// memory: warp i forms S_i(lambda_k) by warp scans over the bins; warp 0 the
-// suffix sums of S_inf; T(r, k) = sum_{i<=r} S_i(lambda_k) + sum_{i>r} S_inf[i]
-// by scans across lanes (lane = rank) per column k; then a block-wide first
-// minimum in row-major (rank, lambda) order and the runner-up for the gap.
-__global__ void __launch_bounds__(32 * kMaxRank)
-sure_table_select_kernel(const unsigned int* __restrict__ counts,
-                         const double* __restrict__ sums, const double* __restrict__ sum_all,
-                         int batch, int K, long long N, long long N_det, double delta,
-                         double* __restrict__ S, double* __restrict__ S_inf,
-                         double* __restrict__ T, hyde_hyres_info* info, int* rank_out,
-                         double* lam_out, const int* status) {
-    extern __shared__ double shd[];
-    double* Ss = shd;                       // [batch][K]
-    double* Ts = shd + (size_t)batch * K;   // [batch][K]
-    __shared__ double sinf[kMaxRank], tail[kMaxRank];
-    __shared__ double wm1[kMaxRank], wm2[kMaxRank];
-    __shared__ int wi1[kMaxRank];
+// Table and choice over the grid: block i (one warp of work) forms
+// S_i(lambda_k) by warp scans over the bins and S_inf[i], so the FP64 work is
+// spread over `batch` SMs (FP64 runs at a small fraction of the FP32 rate on
+// this part); the last block to finish (a counter in the zeroed workspace)
+// forms T(r, k) = sum_{i<=r} S_i(lambda_k) + sum_{i>r} S_inf[i] with one
+// thread per column k walking r upwards (a sequential prefix: fewer FP64
+// instructions than scans), keeps each column's first minimum and runner-up,
+// and reduces them: the first minimum in row-major (rank, lambda) order and
+// the relative gap to the runner-up.
+__global__ void __launch_bounds__(256)
+sure_select_kernel(const unsigned int* __restrict__ counts, const double* __restrict__ sums,
+                   const double* __restrict__ sum_all, int batch, int K, long long N,
+                   long long N_det, double delta, double* __restrict__ S,
+                   double* __restrict__ S_inf, double* __restrict__ T, unsigned int* done,
+                   hyde_hyres_info* info, int* rank_out, double* lam_out, const int* status) {
+    __shared__ double tail[kMaxRank];
+    __shared__ double wm1[8], wm2[8];
+    __shared__ int wi1[8];
+    __shared__ int s_last;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
-    if (wid < batch) {
-        const int i = wid;
+    const int i = blockIdx.x;
+    if (wid == 0) {
         double ccarry = 0.0, scarry = 0.0;
         for (int k0 = 0; k0 < K; k0 += 32) {
             const int k = k0 + lane;
@@ -180,52 +181,43 @@ sure_table_select_kernel(const unsigned int* __restrict__ counts,
             const double cle = c + ccarry, sle = q + scarry;
             if (k < K) {
                 const double lam = k * delta;
-                const double v = (double)N - 2.0 * cle + sle + lam * lam * ((double)N_det - cle);
-                Ss[i * K + k] = v;
-                S[(long long)i * K + k] = v;
+                S[(long long)i * K + k] =
+                    (double)N - 2.0 * cle + sle + lam * lam * ((double)N_det - cle);
             }
             ccarry = __shfl_sync(0xffffffffu, cle, 31);
             scarry = __shfl_sync(0xffffffffu, sle, 31);
         }
-        if (lane == 0) {
-            const double v = sum_all[i] - (double)N;
-            sinf[i] = v;
-            S_inf[i] = v;
+        if (lane == 0) S_inf[i] = sum_all[i] - (double)N;
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = atomicAdd(done, 1u) == (unsigned)gridDim.x - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // every block's S row, copied once with coalesced loads (L2, not L1)
+    extern __shared__ double Ssh[];   // [batch][K]
+    for (int e = t; e < batch * K; e += blockDim.x) Ssh[e] = __ldcg(S + e);
+    if (t == 0) {   // tail[r] = sum_{i > r} S_inf[i]
+        double acc = 0.0;
+        for (int r = batch - 1; r >= 0; --r) {
+            tail[r] = acc;
+            acc += __ldcg(S_inf + r);
         }
     }
     __syncthreads();
-    if (wid == 0) {   // tail[r] = sum_{i > r} S_inf[i] by a reversed warp scan
-        const int i = batch - 1 - lane;
-        double v = (i >= 0) ? sinf[i] : 0.0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        if (i >= 0) tail[i] = v - sinf[i];
-    }
-    __syncthreads();
-    for (int k = wid; k < K; k += nw) {   // lane = rank r - 1
-        double v = lane < batch ? Ss[lane * K + k] : 0.0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        if (lane < batch) {
-            const double tv = v + tail[lane];
-            Ts[lane * K + k] = tv;
-            if (T) T[(long long)lane * K + k] = tv;
-        }
-    }
-    __syncthreads();
-    const int tot = batch * K;
     double m1 = DBL_MAX, m2 = DBL_MAX;
     int i1 = 0x7fffffff;
-    for (int e = t; e < tot; e += blockDim.x) {
-        const double v = Ts[e];
-        if (v < m1 || (v == m1 && e < i1)) { m2 = fmin(m2, m1); m1 = v; i1 = e; }
-        else m2 = fmin(m2, v);
+    for (int k = t; k < K; k += blockDim.x) {
+        double head = 0.0;
+        for (int r = 0; r < batch; ++r) {
+            head += Ssh[r * K + k];
+            const double v = head + tail[r];
+            if (T) T[(long long)r * K + k] = v;
+            const int e = r * K + k;
+            if (v < m1 || (v == m1 && e < i1)) { m2 = fmin(m2, m1); m1 = v; i1 = e; }
+            else m2 = fmin(m2, v);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double om1 = __shfl_xor_sync(0xffffffffu, m1, o);
@@ -236,30 +228,27 @@ sure_table_select_kernel(const unsigned int* __restrict__ counts,
     }
     if (lane == 0) { wm1[wid] = m1; wm2[wid] = m2; wi1[wid] = i1; }
     __syncthreads();
-    if (wid == 0) {
-        m1 = lane < nw ? wm1[lane] : DBL_MAX;
-        m2 = lane < nw ? wm2[lane] : DBL_MAX;
-        i1 = lane < nw ? wi1[lane] : 0x7fffffff;
-        for (int o = 16; o > 0; o >>= 1) {
-            const double om1 = __shfl_xor_sync(0xffffffffu, m1, o);
-            const double om2 = __shfl_xor_sync(0xffffffffu, m2, o);
-            const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
-            if (om1 < m1 || (om1 == m1 && oi1 < i1)) { m2 = fmin(m1, om2); m1 = om1; i1 = oi1; }
-            else m2 = fmin(m2, om1);
-        }
-        if (lane == 0) {
-            const int r = i1 / K, k = i1 % K;
-            if (rank_out) *rank_out = r + 1;
-            if (lam_out) *lam_out = k * delta;
-            if (info) {
-                info->status = status ? *status : 0;
-                info->rank = r + 1;
-                info->lambda_index = k;
-                info->reserved = 0;
-                info->lambda = k * delta;
-                info->sure_min = m1;
-                info->sure_gap = (tot > 1) ? (m2 - m1) / fmax(fabs(m1), 1e-300) : 0.0;
+    if (t == 0) {
+        m1 = wm1[0]; m2 = wm2[0]; i1 = wi1[0];
+        for (int q = 1; q < nw; ++q) {
+            if (wm1[q] < m1 || (wm1[q] == m1 && wi1[q] < i1)) {
+                m2 = fmin(m1, wm2[q]); m1 = wm1[q]; i1 = wi1[q];
+            } else {
+                m2 = fmin(m2, wm1[q]);
             }
+        }
+        const int tot = batch * K;
+        const int r = i1 / K, k = i1 % K;
+        if (rank_out) *rank_out = r + 1;
+        if (lam_out) *lam_out = k * delta;
+        if (info) {
+            info->status = status ? *status : 0;
+            info->rank = r + 1;
+            info->lambda_index = k;
+            info->reserved = 0;
+            info->lambda = k * delta;
+            info->sure_min = m1;
+            info->sure_gap = (tot > 1) ? (m2 - m1) / fmax(fabs(m1), 1e-300) : 0.0;
         }
     }
 }
@@ -310,13 +299,15 @@ hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
         sure_table_kernel<<<(batch + 7) / 8, 256, 0, s>>>(b.counts, b.sums, b.sum_all, batch, K,
                                                            N, N_det, delta, S, S_inf);
     } else {
-        if (batch > kMaxRank) return HYDE_ERR_SHAPE;
-        const size_t smem = 2 * (size_t)batch * K * sizeof(double);
-        if (ensure_smem_limit((const void*)sure_table_select_kernel, (int)smem) != cudaSuccess)
+        if (batch > kMaxRank || b.done == nullptr) return HYDE_ERR_SHAPE;
+        int threads = (K + 31) / 32 * 32;
+        if (threads > 256) threads = 256;
+        const size_t smem = (size_t)batch * K * sizeof(double);
+        if (ensure_smem_limit((const void*)sure_select_kernel, (int)smem) != cudaSuccess)
             return HYDE_ERR_CUDA;
-        sure_table_select_kernel<<<1, 32 * batch, smem, s>>>(b.counts, b.sums, b.sum_all, batch,
-                                                             K, N, N_det, delta, S, S_inf, T,
-                                                             info, rank_out, lam_out, status);
+        sure_select_kernel<<<batch, threads, smem, s>>>(b.counts, b.sums, b.sum_all, batch, K, N,
+                                                     N_det, delta, S, S_inf, T, b.done, info,
+                                                     rank_out, lam_out, status);
     }
     return cuda_status(cudaGetLastError());
 }
