@@ -340,8 +340,62 @@ class HyResSureFn(torch.autograd.Function):
         return None, ds * g.to(ds.dtype), None
 
 
+class HyResScaledBatchFn(torch.autograd.Function):
+    """A batch of cubes through the scaled HyRes with shared threshold scales:
+    each cube's forward and backward run on their own stream, forked from
+    the caller's stream and joined back to it, so the cubes' pipelines (each
+    latency-bound on a few SMs) overlap on the GPU. dL/dscale is the sum over
+    the cubes."""
+
+    @staticmethod
+    def forward(ctx, scale, models, streams, *Ys):
+        cur = torch.cuda.current_stream(scale.device)
+        outs = []
+        for Y, m, st in zip(Ys, models, streams):
+            st.wait_stream(cur)
+            Y.record_stream(st)
+            scale.record_stream(st)
+            with torch.cuda.stream(st):
+                outs.append(m.forward_scaled(Y, scale))
+        for X, st in zip(outs, streams):
+            cur.wait_stream(st)
+            X.record_stream(cur)
+        ctx.models, ctx.streams = models, streams
+        ctx.save_for_backward(scale, *Ys)
+        return tuple(outs)
+
+    @staticmethod
+    def backward(ctx, *gXs):
+        scale, *Ys = ctx.saved_tensors
+        cur = torch.cuda.current_stream(scale.device)
+        dss = []
+        for Y, g, m, st in zip(Ys, gXs, ctx.models, ctx.streams):
+            st.wait_stream(cur)
+            g = g.contiguous()
+            g.record_stream(st)
+            Y.record_stream(st)
+            with torch.cuda.stream(st):
+                dss.append(m.backward_scaled(Y, g, scale, loss=0))
+        total = torch.zeros_like(scale)
+        for ds, st in zip(dss, ctx.streams):
+            cur.wait_stream(st)
+            ds.record_stream(cur)
+            total[: ds.shape[0]] += ds
+        return (total, None, None) + (None,) * len(Ys)
+
+
 def hyres_scaled(Y: torch.Tensor, scale: torch.Tensor, model: HyResGrad) -> torch.Tensor:
     return HyResScaledFn.apply(Y, scale, model)
+
+
+def hyres_scaled_batch(Ys, scale: torch.Tensor, models, streams=None):
+    """``[HyRes_s(Y) for Y in Ys]`` with each cube on its own stream (one
+    HyResGrad per cube; ``streams`` default to new ones)."""
+    if len(Ys) != len(models):
+        raise ValueError("one model per cube")
+    if streams is None:
+        streams = [torch.cuda.Stream(scale.device) for _ in Ys]
+    return list(HyResScaledBatchFn.apply(scale, list(models), list(streams), *Ys))
 
 
 def hyres_sure_loss(Y: torch.Tensor, scale: torch.Tensor, model: HyResGrad) -> torch.Tensor:

@@ -123,3 +123,29 @@ def test_autograd_sure_loss_and_batch_sum(hyde):
     assert abs(total.item() - ref_val) <= 1e-5 * abs(ref_val) + 24.0
     got = s.grad.cpu().numpy()
     assert np.linalg.norm(got - ref_grad) <= 1e-4 * np.linalg.norm(ref_grad)
+
+
+def test_batched_streams_match_sequential(hyde):
+    """The batch on one stream per cube gives the same outputs and the same
+    summed gradient as the cubes one after another."""
+    H, W, p, L, r = 64, 64, 16, 3, 6
+    cubes = [make_cube(H, W, p, m=3, seed=90 + b) for b in range(4)]
+    Ys = [_t(cb["Y"]) for cb in cubes]
+    Xc = [_t(cb["X"]) for cb in cubes]
+    s0 = torch.from_numpy(_scale(p, L, 9)).cuda()
+
+    seq_models = [hyde.HyResGrad(p, H, W, L, r) for _ in cubes]
+    s_seq = s0.clone().requires_grad_(True)
+    outs_seq = [hyde.hyres_scaled(Y, s_seq, m) for Y, m in zip(Ys, seq_models)]
+    sum(torch.mean((X - C) ** 2) for X, C in zip(outs_seq, Xc)).backward()
+
+    bat_models = [hyde.HyResGrad(p, H, W, L, r) for _ in cubes]
+    s_bat = s0.clone().requires_grad_(True)
+    outs_bat = hyde.hyres_scaled_batch(Ys, s_bat, bat_models)
+    sum(torch.mean((X - C) ** 2) for X, C in zip(outs_bat, Xc)).backward()
+    torch.cuda.synchronize()
+
+    for a, b in zip(outs_seq, outs_bat):
+        assert O.rel_l2(b.detach().cpu().numpy(), a.detach().cpu().numpy()) < 1e-6
+    gs, gb = s_seq.grad.cpu().numpy(), s_bat.grad.cpu().numpy()
+    assert np.linalg.norm(gb - gs) <= 1e-5 * np.linalg.norm(gs)
