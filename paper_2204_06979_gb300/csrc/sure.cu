@@ -14,102 +14,122 @@
 // and coefficients above lambda_{K-1} contribute lambda_k^2 each.
 #include <float.h>
 
+#include <cmath>
+
 #include "hyde_internal.cuh"
 
 namespace hyde {
 namespace {
 
-// Every thread owns a private column of the block's histogram (layout
-// [bin][thread], so a thread's updates never conflict with another's and
-// need no atomics): 16-bit counts (the launcher bounds the values a thread
-// sees below 2^16) and float sums, 6 bytes per bin and thread, so that a
-// 256-thread block fits in 96 KB. The block reduces the columns and adds them
-// to the global table with one atomic per bin. Each lane keeps eight float4
-// loads in flight.
-constexpr int kHistUnroll = 8;
+// The block's histogram has one column per lane index, [bin][lane], shared by
+// all of its warps through shared-memory atomics whose result is unused (no
+// thread waits on a read-modify-write, and lane l of every warp hits bank l):
+// 32-bit counts and 32-bit fixed-point sums of c^2 in units of 2^-s. The
+// launcher picks s and the rows per block so that no column can overflow.
+// Integer sums make the table independent of the order of the additions; the
+// block adds its columns to the global table with one atomic per bin, as
+// doubles holding exact multiples of 2^-s.
+//
+// Both integers come from one FMA onto 1.5 * 2^23, where the float spacing
+// is 1: rounded upwards it gives ceil(|c| / delta), rounded to nearest
+// rn(c^2 * 2^s), in the low mantissa bits (exact below 2^22; larger |c|,
+// inf and NaN give bit patterns above every bin).
+constexpr int kHistThreads = 256;
+constexpr int kHistUnroll = 4;
+constexpr float kMagic = 12582912.f;   // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kHistThreads)
 sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl, int K,
-                 float inv_delta, int rows_per_block, unsigned int* __restrict__ counts,
-                 double* __restrict__ sums, double* __restrict__ sum_all) {
-    extern __shared__ unsigned char smraw[];
-    const int T = blockDim.x, tid = threadIdx.x;
-    float* hs = reinterpret_cast<float*>(smraw);                         // [K][T]
-    unsigned short* hc = reinterpret_cast<unsigned short*>(hs + (size_t)K * T);   // [K][T]
-    const int i = blockIdx.y;
-    const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
-    for (int e = tid; e < K * T; e += T) { hc[e] = 0; hs[e] = 0.f; }
+                 float inv_delta, float qscale, double inv_qscale, int rows_per_block,
+                 unsigned int* __restrict__ counts, double* __restrict__ sums,
+                 double* __restrict__ sum_all) {
+    extern __shared__ unsigned int hsm[];   // counts [K][32], then sums [K][32]
+    __shared__ double wall[kHistThreads / 32];
+    unsigned int* hc = hsm;
+    unsigned int* hq = hsm + K * 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int nw = kHistThreads / 32;
+    for (int e = tid; e < 2 * K * 32; e += kHistThreads) hsm[e] = 0u;
     __syncthreads();
+    const int i = blockIdx.y;
     const int y0 = blockIdx.x * rows_per_block;
     const int y1 = min(y0 + rows_per_block, Hp);
     const float* base = coef + (long long)i * Hp * Wp;
     float all = 0.f;
-    // bin ceil(|c| / delta) by one float-to-int conversion rounding up; the
-    // value is clamped below 2^24 so the conversion is exact and cannot wrap
     auto one = [&](float c, bool in_ll) {
         const float c2 = c * c;
         all += c2;
         if (in_ll) return;
-        const int k = __float2int_ru(fminf(fabsf(c) * inv_delta, 16777216.f));
-        if (k < K) {
-            hc[k * T + tid] += 1;
-            hs[k * T + tid] += c2;
+        const unsigned k =
+            (unsigned)(__float_as_int(__fmaf_ru(fabsf(c), inv_delta, kMagic)) - kMagicBits);
+        if (k < (unsigned)K) {
+            const unsigned q = (unsigned)(__float_as_int(fmaf(c2, qscale, kMagic)) - kMagicBits);
+            atomicAdd(hc + k * 32 + lane, 1u);
+            atomicAdd(hq + k * 32 + lane, q);
         }
     };
-    if ((Wp & 3) == 0) {
-        const int W4 = Wp >> 2;
-        for (int y = y0 + wid; y < y1; y += nw) {
-            const float4* row = reinterpret_cast<const float4*>(base + (long long)y * Wp);
-            const bool yll = y < hl;
-            for (int x40 = lane; x40 < W4; x40 += 32 * kHistUnroll) {
+    if (y0 < y1) {
+        if ((Wp & 3) == 0) {
+            // the block's rows as one run of float4s
+            const int W4 = Wp >> 2;
+            const float4* b4 = reinterpret_cast<const float4*>(base) + (long long)y0 * W4;
+            const int nf = (y1 - y0) * W4;
+            const bool has_ll = y0 < hl;   // only the first rows hold the final LL band
+            for (int f = tid; f < nf; f += kHistThreads * kHistUnroll) {
                 float4 v[kHistUnroll];
 #pragma unroll
                 for (int u = 0; u < kHistUnroll; ++u) {
-                    const int x4 = x40 + 32 * u;
-                    v[u] = x4 < W4 ? __ldg(row + x4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int fu = f + u * kHistThreads;
+                    v[u] = fu < nf ? __ldg(b4 + fu) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
                 for (int u = 0; u < kHistUnroll; ++u) {
-                    const int x4 = x40 + 32 * u;
-                    if (x4 < W4) {
-                        if (yll) {   // rows holding the final LL band
-                            const int x = x4 * 4;
-                            one(v[u].x, x < wl);
-                            one(v[u].y, x + 1 < wl);
-                            one(v[u].z, x + 2 < wl);
-                            one(v[u].w, x + 3 < wl);
-                        } else {
-                            one(v[u].x, false);
-                            one(v[u].y, false);
-                            one(v[u].z, false);
-                            one(v[u].w, false);
-                        }
+                    const int fu = f + u * kHistThreads;
+                    if (fu >= nf) continue;
+                    if (has_ll) {
+                        const int yy = fu / W4;
+                        const int x = (fu - yy * W4) * 4;
+                        const bool yll = y0 + yy < hl;
+                        one(v[u].x, yll && x < wl);
+                        one(v[u].y, yll && x + 1 < wl);
+                        one(v[u].z, yll && x + 2 < wl);
+                        one(v[u].w, yll && x + 3 < wl);
+                    } else {
+                        one(v[u].x, false);
+                        one(v[u].y, false);
+                        one(v[u].z, false);
+                        one(v[u].w, false);
                     }
                 }
             }
-        }
-    } else {
-        for (int y = y0 + wid; y < y1; y += nw) {
-            const float* row = base + (long long)y * Wp;
-            const bool yll = y < hl;
-            for (int x = lane; x < Wp; x += 32) one(__ldg(row + x), yll && x < wl);
+        } else {
+            for (int y = y0 + wid; y < y1; y += nw) {
+                const float* row = base + (long long)y * Wp;
+                const bool yll = y < hl;
+                for (int x = lane; x < Wp; x += 32) one(__ldg(row + x), yll && x < wl);
+            }
         }
     }
     all = warp_sum(all);
-    if (lane == 0 && all != 0.f) atomicAdd(&sum_all[i], (double)all);
+    if (lane == 0) wall[wid] = (double)all;
     __syncthreads();
     for (int k = wid; k < K; k += nw) {
-        unsigned int c = 0;
-        float sacc = 0.f;
-        for (int q = lane; q < T; q += 32) { c += hc[k * T + q]; sacc += hs[k * T + q]; }
+        unsigned int c = hc[k * 32 + lane];
+        unsigned long long q = hq[k * 32 + lane];
         for (int o = 16; o > 0; o >>= 1) {
             c += __shfl_xor_sync(0xffffffffu, c, o);
-            sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            q += __shfl_xor_sync(0xffffffffu, q, o);
         }
         if (lane == 0 && c) {
             atomicAdd(&counts[(long long)i * K + k], c);
-            atomicAdd(&sums[(long long)i * K + k], (double)sacc);
+            atomicAdd(&sums[(long long)i * K + k], (double)q * inv_qscale);
         }
+    }
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w) tot += wall[w];
+        if (tot != 0.0) atomicAdd(&sum_all[i], tot);
     }
 }
 
@@ -263,31 +283,37 @@ size_t sure_accum_bytes(int batch, int K) {
 
 hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int levels, int K,
                              double delta, const SureBufs& b, cudaStream_t s) {
-    int sms = device_sm_count();
+    const int sms = device_sm_count();
     if (sms <= 0) return HYDE_ERR_CUDA;
-    // threads per block: the private histograms (6 bytes per bin and thread)
-    // stay within 96 KB so that two blocks share an SM
-    int threads = (int)((96 * 1024) / (6 * (size_t)K)) / 32 * 32;
-    if (threads > 256) threads = 256;
-    if (threads < 32) threads = 32;
-    int per_comp = (4 * sms + batch - 1) / batch;
-    // a thread must see fewer than 2^16 values (16-bit bin counts)
-    const long long per_thread_cap = 60000;
-    const long long min_blocks = ((long long)Hp * Wp + per_thread_cap * threads - 1) /
-                                 (per_thread_cap * threads);
-    if (per_comp < min_blocks) per_comp = (int)min_blocks;
+    if (K < 1 || !(delta > 0.0)) return HYDE_ERR_INVALID_ARG;
+    const size_t smem = (size_t)2 * K * 32 * sizeof(unsigned int);
+    if (smem > 200 * 1024) return HYDE_ERR_SHAPE;
+    const float inv_delta = (float)(1.0 / delta);
+    // largest c^2 that lands in a bin below K (ceil(|c| * inv_delta) <= K - 1), with margin
+    const double q = (K - 1) / (double)inv_delta;
+    const double c2max = q * q * 1.001 + 1e-300;
+    // fixed-point unit 2^-s: rn(c^2 * 2^s) must stay below 2^22 (the FMA trick)
+    int sh = 16;
+    while (sh > 0 && c2max * std::ldexp(1.0, sh) >= 4194304.0) --sh;
+    if (c2max * std::ldexp(1.0, sh) >= 4194304.0) return HYDE_ERR_SHAPE;
+    const double qmax = std::floor(c2max * std::ldexp(1.0, sh)) + 1.0;
+    // values one lane column can receive per row, and the rows that keep its sum below 2^32
+    const double per_row = 4.0 * (double)(((long long)Wp + 127) / 128);
+    const long long rows_cap = (long long)(4294967295.0 / (qmax * per_row));
+    if (rows_cap < 1) return HYDE_ERR_SHAPE;
+    // about eight 256-thread blocks per SM
+    int per_comp = (8 * sms + batch - 1) / batch;
     if (per_comp > Hp) per_comp = Hp;
     if (per_comp < 1) per_comp = 1;
-    int rows = (Hp + per_comp - 1) / per_comp;
-    per_comp = (Hp + rows - 1) / rows;
-    if ((long long)rows * Wp > per_thread_cap * threads) return HYDE_ERR_SHAPE;
-    size_t smem = (size_t)K * threads * 6;
+    long long rows = (Hp + per_comp - 1) / per_comp;
+    if (rows > rows_cap) rows = rows_cap;
+    per_comp = (int)((Hp + rows - 1) / rows);
     if (ensure_smem_limit((const void*)sure_hist_kernel, (int)smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 grid(per_comp, batch);
-    sure_hist_kernel<<<grid, threads, smem, s>>>(coef, Hp, Wp, Hp >> levels, Wp >> levels, K,
-                                                 (float)(1.0 / delta), rows, b.counts, b.sums,
-                                                 b.sum_all);
+    sure_hist_kernel<<<grid, kHistThreads, smem, s>>>(
+        coef, Hp, Wp, Hp >> levels, Wp >> levels, K, inv_delta, (float)std::ldexp(1.0, sh),
+        std::ldexp(1.0, -sh), (int)rows, b.counts, b.sums, b.sum_all);
     return cuda_status(cudaGetLastError());
 }
 
