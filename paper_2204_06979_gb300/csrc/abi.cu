@@ -9,6 +9,8 @@
 
 namespace hyde {
 
+thread_local bool tl_pdl = true;
+
 int device_sm_count() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -574,6 +576,7 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H, i
     SlotLayout S;
     slot_layout(p, win, n_win, params, &S);
     const int slots = n_slots < n_win ? n_slots : n_win;
+    const PdlOff plain_launches;   // concurrent slot streams: ordinary stream order
     // fork: every slot stream waits for the work already on the caller's stream
     if (cudaEventRecord(events[slots], stream) != cudaSuccess) return HYDE_ERR_CUDA;
     for (int s = 0; s < slots; ++s)

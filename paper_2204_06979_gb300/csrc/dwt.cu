@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(kThreads)
 dwt_level_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int hv,
                  int wv, int h, int w, float* __restrict__ coef, long long coef_bs,
                  int coef_ld, float* __restrict__ ll, long long ll_bs, int ll_ld) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float in[IH][IW + 1];
     __shared__ float ra[IH][TW + 1];
     __shared__ float rd[IH][TW + 1];
@@ -134,6 +136,8 @@ __global__ void __launch_bounds__(kFThreads)
 dwt_level_pipe_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int h, int w,
                       float* __restrict__ coef, long long coef_bs, int coef_ld,
                       float* __restrict__ ll, long long ll_bs, int ll_ld) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float4 fsm4[];
     float* inb = reinterpret_cast<float*>(fsm4);     // [2][FIH][FIW]
     float* ra = inb + 2 * FIH * FIW;                  // [FIH][FTW]
@@ -257,6 +261,8 @@ idwt_level_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
                   int w, const double* __restrict__ lam, const float* __restrict__ scale,
                   int scale_ld, int lev, const int* __restrict__ rank,
                   float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float sLL[TH + 1][TW + 2], sLH[TH + 1][TW + 2];
     __shared__ float sHL[TH + 1][TW + 2], sHH[TH + 1][TW + 2];
     __shared__ float tl[2 * TH][TW + 2], th[2 * TH][TW + 2];
@@ -317,6 +323,146 @@ idwt_level_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
     }
 }
 
+// --------------------------------------------------------------------------
+// Synthesis of one level, register form: lane l of a warp owns coefficient
+// columns k0 = 128 s + 4 l .. k0 + 3 of a 128-column strip s and walks
+// kSynRows coefficient rows down it, keeping the previous row's four bands in
+// registers, so every coefficient is loaded once (float4, soft threshold on
+// load) and column k0 - 1 comes from the left lane by a shuffle (lane 0
+// loads it). Per coefficient row j the lane forms output rows 2j and 2j + 1
+// at columns 2 k0 .. 2 k0 + 7. Output rows that are 16-byte aligned take
+// float4 stores; otherwise (the cropped last level, row length W) the two
+// rows go through a per-warp shared buffer so that each store instruction
+// writes 32 consecutive floats.
+// --------------------------------------------------------------------------
+constexpr int kSynRows = 4;
+constexpr int kSynThreads = 256;
+constexpr int kSynWarps = kSynThreads / 32;
+
+__device__ __forceinline__ float4 soft4(float4 v, float lam) {
+    return make_float4(soft(v.x, lam), soft(v.y, lam), soft(v.z, lam), soft(v.w, lam));
+}
+
+__global__ void __launch_bounds__(kSynThreads)
+idwt_level_vec_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
+                      const float* __restrict__ coef, long long coef_bs, int coef_ld, int h,
+                      int w, const double* __restrict__ lam, const float* __restrict__ scale,
+                      int scale_ld, int lev, const int* __restrict__ rank,
+                      float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo,
+                      int vout) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ float4 stage4[kSynWarps][2][64];   // two output rows of 256 floats per warp
+    const int b = blockIdx.y;
+    if (rank && b >= *rank) return;
+    float lv = lam ? (float)(*lam) : 0.f;
+    if (lam && scale) lv *= scale[(long long)b * scale_ld + (lev - 1)];
+    const int hh = h >> 1, wh = w >> 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nstrips = (wh + 127) >> 7;
+    const int nruns = (hh + kSynRows - 1) / kSynRows;
+    const int u = blockIdx.x * kSynWarps + wid;
+    if (u >= nstrips * nruns) return;   // whole warp
+    const int strip = u % nstrips, run = u / nstrips;
+    const int k0 = strip * 128 + 4 * lane;
+    const bool active = k0 < wh;        // wh is a multiple of 4: the lane's 4 columns exist
+    const int kc = active ? k0 : 0;
+    const int km1 = (strip == 0 ? wh : strip * 128) - 1;
+    const float* L = llsrc + (long long)b * ll_bs;
+    const float* C = coef + (long long)b * coef_bs;
+    // bands in the order LL, LH (column detail), HL (row detail), HH
+    auto load_row = [&](int J, float4 (&v)[4], float (&left)[4]) {
+        const long long rl = (long long)J * ll_ld, rt = (long long)J * coef_ld,
+                        rb = (long long)(hh + J) * coef_ld;
+        v[0] = __ldg(reinterpret_cast<const float4*>(L + rl + kc));
+        v[1] = soft4(__ldg(reinterpret_cast<const float4*>(C + rb + kc)), lv);
+        v[2] = soft4(__ldg(reinterpret_cast<const float4*>(C + rt + wh + kc)), lv);
+        v[3] = soft4(__ldg(reinterpret_cast<const float4*>(C + rb + wh + kc)), lv);
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
+        if (lane == 0) {
+            e0 = __ldg(L + rl + km1);
+            e1 = soft(__ldg(C + rb + km1), lv);
+            e2 = soft(__ldg(C + rt + wh + km1), lv);
+            e3 = soft(__ldg(C + rb + wh + km1), lv);
+        }
+        left[0] = __shfl_up_sync(0xffffffffu, v[0].w, 1);
+        left[1] = __shfl_up_sync(0xffffffffu, v[1].w, 1);
+        left[2] = __shfl_up_sync(0xffffffffu, v[2].w, 1);
+        left[3] = __shfl_up_sync(0xffffffffu, v[3].w, 1);
+        if (lane == 0) { left[0] = e0; left[1] = e1; left[2] = e2; left[3] = e3; }
+    };
+    const int j0 = run * kSynRows;
+    float4 pv[4];
+    float pl[4];
+    load_row(j0 == 0 ? hh - 1 : j0 - 1, pv, pl);
+    float* O = out + (long long)b * out_bs;
+    const int X0 = 2 * k0;
+#pragma unroll
+    for (int s = 0; s < kSynRows; ++s) {
+        const int j = j0 + s;
+        if (j >= hh) break;   // warp-uniform
+        float4 cv[4];
+        float cl[4];
+        load_row(j, cv, cl);
+        // column pass on the five columns k0 - 1 .. k0 + 3
+        float le[5], lo[5], he[5], hq[5];
+        auto col = [&](int c, float cLL, float cLH, float cHL, float cHH, float pLL, float pLH,
+                       float pHL, float pHH) {
+            le[c] = kH0 * cLL + kG0 * cLH + kH2 * pLL + kG2 * pLH;
+            lo[c] = kH1 * cLL + kG1 * cLH + kH3 * pLL + kG3 * pLH;
+            he[c] = kH0 * cHL + kG0 * cHH + kH2 * pHL + kG2 * pHH;
+            hq[c] = kH1 * cHL + kG1 * cHH + kH3 * pHL + kG3 * pHH;
+        };
+        col(0, cl[0], cl[1], cl[2], cl[3], pl[0], pl[1], pl[2], pl[3]);
+        col(1, cv[0].x, cv[1].x, cv[2].x, cv[3].x, pv[0].x, pv[1].x, pv[2].x, pv[3].x);
+        col(2, cv[0].y, cv[1].y, cv[2].y, cv[3].y, pv[0].y, pv[1].y, pv[2].y, pv[3].y);
+        col(3, cv[0].z, cv[1].z, cv[2].z, cv[3].z, pv[0].z, pv[1].z, pv[2].z, pv[3].z);
+        col(4, cv[0].w, cv[1].w, cv[2].w, cv[3].w, pv[0].w, pv[1].w, pv[2].w, pv[3].w);
+        // row pass: outputs 2k and 2k + 1 for k = k0 .. k0 + 3 (column index c = k - k0 + 1)
+        float oe[8], oo[8];
+#pragma unroll
+        for (int c = 1; c <= 4; ++c) {
+            oe[2 * c - 2] = kH0 * le[c] + kG0 * he[c] + kH2 * le[c - 1] + kG2 * he[c - 1];
+            oe[2 * c - 1] = kH1 * le[c] + kG1 * he[c] + kH3 * le[c - 1] + kG3 * he[c - 1];
+            oo[2 * c - 2] = kH0 * lo[c] + kG0 * hq[c] + kH2 * lo[c - 1] + kG2 * hq[c - 1];
+            oo[2 * c - 1] = kH1 * lo[c] + kG1 * hq[c] + kH3 * lo[c - 1] + kG3 * hq[c - 1];
+        }
+        const int Y = 2 * j;
+        if (vout) {
+            if (active) {
+                float* r0 = O + (long long)Y * out_ld + X0;
+                float* r1 = r0 + out_ld;
+                *reinterpret_cast<float4*>(r0) = make_float4(oe[0], oe[1], oe[2], oe[3]);
+                *reinterpret_cast<float4*>(r0 + 4) = make_float4(oe[4], oe[5], oe[6], oe[7]);
+                *reinterpret_cast<float4*>(r1) = make_float4(oo[0], oo[1], oo[2], oo[3]);
+                *reinterpret_cast<float4*>(r1 + 4) = make_float4(oo[4], oo[5], oo[6], oo[7]);
+            }
+        } else {
+            float4* st0 = stage4[wid][0];
+            float4* st1 = stage4[wid][1];
+            st0[2 * lane] = make_float4(oe[0], oe[1], oe[2], oe[3]);
+            st0[2 * lane + 1] = make_float4(oe[4], oe[5], oe[6], oe[7]);
+            st1[2 * lane] = make_float4(oo[0], oo[1], oo[2], oo[3]);
+            st1[2 * lane + 1] = make_float4(oo[4], oo[5], oo[6], oo[7]);
+            __syncwarp();
+            const float* f0 = reinterpret_cast<const float*>(st0);
+            const float* f1 = reinterpret_cast<const float*>(st1);
+            const int xs = 256 * strip;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int X = xs + 32 * q + lane;
+                if (X < wo) {
+                    if (Y < ho) O[(long long)Y * out_ld + X] = f0[32 * q + lane];
+                    if (Y + 1 < ho) O[(long long)(Y + 1) * out_ld + X] = f1[32 * q + lane];
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { pv[q] = cv[q]; pl[q] = cl[q]; }
+    }
+}
+
 }  // namespace
 
 size_t dwt_scratch_floats(int Hp, int Wp) {
@@ -365,7 +511,7 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
         else { lp = ll_buf(scratch, batch, Hp, Wp, lev, &lbs); lld = w / 2; }
         dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
         if (hv < h || wv < w) {
-            dwt_level_kernel<true><<<grid, kThreads, 0, s>>>(sp, sbs, sld, hv, wv, h, w, coef,
+            launch_pdl(dwt_level_kernel<true>, grid, kThreads, 0, s, sp, sbs, sld, hv, wv, h, w, coef,
                                                              cbs, Wp, lp, lbs, lld);
         } else {
             // padded source: the pipelined kernel, a few tiles per block
@@ -373,7 +519,7 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
             int G = (pipe_per_sm * sms + batch - 1) / batch;
             if (G > ntiles) G = ntiles;
             if (G < 1) G = 1;
-            dwt_level_pipe_kernel<<<dim3(G, batch), kFThreads, pipe_smem, s>>>(
+            launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s, 
                 sp, sbs, sld, h, w, coef, cbs, Wp, lp, lbs, lld);
         }
     }
@@ -402,8 +548,22 @@ hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int W
             op = ll_buf(scratch, batch, Hp, Wp, lev - 1, &obs);
             old = w; ho = h; wo = w;
         }
+        const int wh = w / 2, hh = h / 2;
+        const bool vin = (Wp & 3) == 0 && (wh & 3) == 0 && (lld & 3) == 0 && (lbs & 3) == 0 &&
+                         (cbs & 3) == 0 && (reinterpret_cast<uintptr_t>(lp) & 15) == 0 &&
+                         (reinterpret_cast<uintptr_t>(coef) & 15) == 0;
+        if (vin) {
+            // every output row inside the crop; float4 stores when rows are 16-byte aligned
+            const bool vout = (old & 3) == 0 && (obs & 3) == 0 && ho == h && wo == w &&
+                              (reinterpret_cast<uintptr_t>(op) & 15) == 0;
+            const long long units = (long long)((wh + 127) / 128) * ((hh + kSynRows - 1) / kSynRows);
+            launch_pdl(idwt_level_vec_kernel, dim3((unsigned)((units + kSynWarps - 1) / kSynWarps), batch),
+                       kSynThreads, 0, s, lp, lbs, lld, coef, cbs, Wp, h, w, lam, scale, scale_ld,
+                       lev, rank, op, obs, old, ho, wo, vout ? 1 : 0);
+            continue;
+        }
         dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
-        idwt_level_kernel<<<grid, kThreads, 0, s>>>(lp, lbs, lld, coef, cbs, Wp, h, w, lam,
+        launch_pdl(idwt_level_kernel, grid, kThreads, 0, s, lp, lbs, lld, coef, cbs, Wp, h, w, lam,
                                                     scale, scale_ld, lev, rank, op, obs, old,
                                                     ho, wo);
     }

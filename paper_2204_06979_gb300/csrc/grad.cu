@@ -31,6 +31,8 @@ scale_grad_kernel(const float* __restrict__ C, const float* __restrict__ dC, int
                   int L, const int* __restrict__ rank, const double* __restrict__ lam,
                   const float* __restrict__ scale, int scale_ld, int mode, int rows_per_block,
                   double* __restrict__ acc, double* __restrict__ sure_acc) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float s_lam[kMaxLevels];
     __shared__ float s_part[kMaxLevels][kThreads];   // private column per thread
     const int i = blockIdx.y;
@@ -85,6 +87,8 @@ __global__ void scale_grad_finish_kernel(const double* __restrict__ acc, int r_m
                                          float* __restrict__ dscale, int ld, int mode,
                                          long long N, const double* __restrict__ sure_acc,
                                          double* __restrict__ sure_value) {
+    pdl_wait();
+    pdl_trigger();
     const int r = *rank;
     for (int e = threadIdx.x; e < r_max * L; e += blockDim.x) {
         const int i = e / L, l = e % L;
@@ -109,7 +113,7 @@ hyde_status launch_scale_grad(const float* C, const float* dC, int r_max, int Hp
     const int rows = (Hp + per - 1) / per;
     per = (Hp + rows - 1) / rows;
     dim3 grid(per, r_max);
-    scale_grad_kernel<<<grid, kThreads, 0, s>>>(C, dC, Hp, Wp, levels, rank, lam, scale,
+    launch_pdl(scale_grad_kernel, grid, kThreads, 0, s, C, dC, Hp, Wp, levels, rank, lam, scale,
                                                 scale_ld, mode, rows, acc, sure_acc);
     return cuda_status(cudaGetLastError());
 }
@@ -118,7 +122,7 @@ hyde_status launch_scale_grad_finish(const double* acc, int r_max, int levels, c
                                      const double* lam, float* dscale, int dscale_ld, int mode,
                                      long long N, const double* sure_acc, double* sure_value,
                                      cudaStream_t s) {
-    scale_grad_finish_kernel<<<1, 256, 0, s>>>(acc, r_max, levels, rank, lam, dscale, dscale_ld,
+    launch_pdl(scale_grad_finish_kernel, 1, 256, 0, s, acc, r_max, levels, rank, lam, dscale, dscale_ld,
                                                mode, N, sure_acc, sure_value);
     return cuda_status(cudaGetLastError());
 }

@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 ? 2 : 1))
 gram_partial_kernel(const float* __restrict__ Y, int p, long long n, int PT,
                     int ntiles, long long chunks_per_block,
                     float* __restrict__ partials) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float4 sm4[];
     const int p8 = PT * 8;
     const int t = threadIdx.x;
@@ -173,6 +175,8 @@ template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1)
 gram_partial84_kernel(const float* __restrict__ Y, int p, long long n, int PT, int ntiles,
                       float* __restrict__ partials) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float4 sm4[];
     const int p8 = PT * 8;
     const int t = threadIdx.x;
@@ -254,6 +258,8 @@ constexpr int kReduceSeg = 16;
 __global__ void gram_reduce_kernel(const float* __restrict__ partials, int nblocks,
                                    int p, int PT, int ntiles, int mode, double* __restrict__ R,
                                    int* status) {
+    pdl_wait();
+    pdl_trigger();
     const int te = mode == 0 ? 64 : 32;   // elements per tile
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)ntiles * te) return;
@@ -351,22 +357,22 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
     long long nchunks = (n + KC - 1) / KC;
     long long per = (nchunks + g.blocks - 1) / g.blocks;
     if (g.mode == 1)
-        gram_partial84_kernel<384><<<g.blocks, g.threads, g.smem, s>>>(Y, p, n, g.PT, g.ntiles,
+        launch_pdl(gram_partial84_kernel<384>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT, g.ntiles,
                                                                        partials);
     else if (g.threads <= 256)
-        gram_partial_kernel<256><<<g.blocks, g.threads, g.smem, s>>>(Y, p, n, g.PT, g.ntiles,
+        launch_pdl(gram_partial_kernel<256>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT, g.ntiles,
                                                                      per, partials);
     else if (g.threads <= 384)
-        gram_partial_kernel<384><<<g.blocks, g.threads, g.smem, s>>>(Y, p, n, g.PT, g.ntiles,
+        launch_pdl(gram_partial_kernel<384>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT, g.ntiles,
                                                                      per, partials);
     else
-        gram_partial_kernel<kGramMaxThreads><<<g.blocks, g.threads, g.smem, s>>>(
+        launch_pdl(gram_partial_kernel<kGramMaxThreads>, g.blocks, g.threads, g.smem, s, 
             Y, p, n, g.PT, g.ntiles, per, partials);
     long long tot = (long long)g.ntiles * (g.mode == 0 ? 64 : 32);
     if (cudaMemsetAsync(R, 0, (size_t)p * p * sizeof(double), s) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 rgrid((unsigned)((tot + 255) / 256), (g.blocks + kReduceSeg - 1) / kReduceSeg);
-    gram_reduce_kernel<<<rgrid, 256, 0, s>>>(partials, g.blocks, p, g.PT, g.ntiles, g.mode, R,
+    launch_pdl(gram_reduce_kernel, rgrid, 256, 0, s, partials, g.blocks, p, g.PT, g.ntiles, g.mode, R,
                                              status);
     return cuda_status(cudaGetLastError());
 }

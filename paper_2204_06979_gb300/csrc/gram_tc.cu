@@ -98,6 +98,8 @@ template <int RPW>
 __global__ void __launch_bounds__(kTcThreadsWs, 1)
 gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
                long long chunks_per_cta, float* __restrict__ partials, int* status) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages];
     __shared__ uint32_t tmem_base_s;
@@ -264,6 +266,8 @@ constexpr int kTcReduceSeg = 16;
 
 __global__ void gram_tc_reduce_kernel(const float* __restrict__ partials, int nblocks, int p,
                                       double* __restrict__ R, int* status) {
+    pdl_wait();
+    pdl_trigger();
     const long long tot = (long long)p * p;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= tot) return;
@@ -322,7 +326,7 @@ hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, 
     case G:                                                                                   \
         if (ensure_smem_limit((const void*)gram_tc_kernel<8 * G>, (int)P.smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                             \
-        gram_tc_kernel<8 * G><<<blocks, kTcThreadsWs, P.smem, s>>>(Y, p, n, P, per, partials, \
+        launch_pdl(gram_tc_kernel<8 * G>, blocks, kTcThreadsWs, P.smem, s, Y, p, n, P, per, partials, \
                                                                     status);                  \
         break;
         HYDE_TC(1) HYDE_TC(2) HYDE_TC(3) HYDE_TC(4)
@@ -332,7 +336,7 @@ hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, 
     if (cudaMemsetAsync(R, 0, (size_t)p * p * sizeof(double), s) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 rgrid((unsigned)((p * p + 255) / 256), (blocks + kTcReduceSeg - 1) / kTcReduceSeg);
-    gram_tc_reduce_kernel<<<rgrid, 256, 0, s>>>(partials, blocks, p, R, status);
+    launch_pdl(gram_tc_reduce_kernel, rgrid, 256, 0, s, partials, blocks, p, R, status);
     return cuda_status(cudaGetLastError());
 }
 

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/hyde.h"
 
 namespace hyde {
@@ -52,6 +54,48 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------- programmatic dependent launch
+// Every kernel is launched with programmatic stream serialisation: its blocks
+// may be scheduled while the previous kernel on the stream is still running,
+// which hides the launch and ramp-up between the dependent kernels of the
+// path. Each kernel therefore begins with pdl_wait(), which returns once the
+// previous grid has completed and its writes are visible (at once when there
+// is none), before it touches global memory; pdl_trigger() then lets the next
+// kernel's blocks be scheduled. Because the trigger comes after the wait, at
+// most one grid waits behind a running one, and that running grid has every
+// block resident, so the waiting blocks cannot hold resources it needs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches from one host thread use the attribute unless a PdlOff guard is
+// alive on that thread: the sliding-window form runs dozens of small
+// pipelines on concurrent streams, where blocks resident ahead of their
+// predecessor take SM room from the other streams' running kernels.
+extern thread_local bool tl_pdl;
+struct PdlOff {
+    bool prev;
+    PdlOff() : prev(tl_pdl) { tl_pdl = false; }
+    ~PdlOff() { tl_pdl = prev; }
+};
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = tl_pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Number of SMs of the current device (cached per device).

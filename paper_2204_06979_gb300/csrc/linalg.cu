@@ -54,6 +54,8 @@ template <int T, int G>
 __global__ void __launch_bounds__(G * G, 1)
 noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
                     double* __restrict__ S, int* status) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float s_inv[G * T];
     __shared__ float s_row[2][G * T];
     __shared__ float s_col[2][G * T];
@@ -140,6 +142,8 @@ noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ain
 __global__ void __launch_bounds__(kLA, 1)
 noise_gj_smem_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
                      double* __restrict__ S, int* status) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float sm[];
     float* A = sm;                  // p * p
     float* colk = A + p * p;        // p
@@ -192,6 +196,8 @@ __global__ void __launch_bounds__(256)
 noise_refine_kernel(const double* __restrict__ R, const float* __restrict__ Ainv,
                     const double* __restrict__ S, int p, long long n,
                     double* __restrict__ sigma, int* status) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ double xs[];   // p
     __shared__ double red[8];
     const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -502,6 +508,8 @@ template <int NB, int NW>
 __global__ void __launch_bounds__(kLA, 1)
 eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p, int r,
                 double* __restrict__ evals, double* __restrict__ V, int* status) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float sm[];
     const int lda = p + 1;
     float* q = sm;
@@ -802,6 +810,8 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
 __global__ void weights_kernel(const double* __restrict__ V, const double* __restrict__ sigma,
                                int p, int r, int ldw, float* __restrict__ P,
                                float* __restrict__ Q) {
+    pdl_wait();
+    pdl_trigger();
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * ldw;
          e += gridDim.x * blockDim.x) {
         int b = e / ldw, i = e % ldw;
@@ -837,7 +847,7 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
     if (T16 <= 10) {
         switch (T16) {
 #define HYDE_GJ16(TV) \
-    case TV: noise_gj_reg_kernel<TV, 16><<<1, 256, 0, s>>>(R, p, Ainv, Sd, status); break;
+    case TV: launch_pdl(noise_gj_reg_kernel<TV, 16>, 1, 256, 0, s, R, p, Ainv, Sd, status); break;
             HYDE_GJ16(1) HYDE_GJ16(2) HYDE_GJ16(3) HYDE_GJ16(4) HYDE_GJ16(5)
             HYDE_GJ16(6) HYDE_GJ16(7) HYDE_GJ16(8) HYDE_GJ16(9) HYDE_GJ16(10)
 #undef HYDE_GJ16
@@ -845,16 +855,16 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
         }
     } else if (T32 <= kMaxRegT) {
         switch (T32) {
-            case 6: noise_gj_reg_kernel<6, 32><<<1, kLA, 0, s>>>(R, p, Ainv, Sd, status); break;
+            case 6: launch_pdl(noise_gj_reg_kernel<6, 32>, 1, kLA, 0, s, R, p, Ainv, Sd, status); break;
             default: return HYDE_ERR_SHAPE;   // p in (160, 192] has T32 = 6
         }
     } else {
         size_t smem = noise_smem_bytes(p);
         if (ensure_smem_limit((const void*)noise_gj_smem_kernel, (int)smem) != cudaSuccess)
             return HYDE_ERR_SHAPE;
-        noise_gj_smem_kernel<<<1, kLA, smem, s>>>(R, p, Ainv, Sd, status);
+        launch_pdl(noise_gj_smem_kernel, 1, kLA, smem, s, R, p, Ainv, Sd, status);
     }
-    noise_refine_kernel<<<p, 256, p * sizeof(double), s>>>(R, Ainv, Sd, p, n, sigma, status);
+    launch_pdl(noise_refine_kernel, p, 256, p * sizeof(double), s, R, Ainv, Sd, p, n, sigma, status);
     return cuda_status(cudaGetLastError());
 }
 
@@ -872,7 +882,7 @@ hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, do
         if (ensure_smem_limit((const void*)eig_fast_kernel<NBV, kEigWarps>, (int)smem) !=      \
             cudaSuccess)    \
             return HYDE_ERR_SHAPE;                                                             \
-        eig_fast_kernel<NBV, kEigWarps><<<1, kLA, smem, s>>>(A, wsig, p, r, evals, V, status);           \
+        launch_pdl(eig_fast_kernel<NBV, kEigWarps>, 1, kLA, smem, s, A, wsig, p, r, evals, V, status);           \
         break;
         HYDE_EIG(1) HYDE_EIG(2) HYDE_EIG(3) HYDE_EIG(4)
         HYDE_EIG(5) HYDE_EIG(6) HYDE_EIG(7) HYDE_EIG(8)
@@ -885,7 +895,7 @@ hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, do
 hyde_status launch_weights(const double* V, const double* sigma, int p, int r, int ldw,
                            float* P, float* Q, cudaStream_t s) {
     int tot = p * ldw;
-    weights_kernel<<<(tot + 255) / 256, 256, 0, s>>>(V, sigma, p, r, ldw, P, Q);
+    launch_pdl(weights_kernel, (tot + 255) / 256, 256, 0, s, V, sigma, p, r, ldw, P, Q);
     return cuda_status(cudaGetLastError());
 }
 

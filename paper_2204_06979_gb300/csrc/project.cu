@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(kThreads)
 project_pad_kernel(const float* __restrict__ Y, int p, int H, int W,
                    const float* __restrict__ P, int r, float* __restrict__ Zp, int Hp,
                    int Wp, int zero_pad) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float4 Ps4[];   // p * RM / 4
     float* Ps = reinterpret_cast<float*>(Ps4);
     for (int e = threadIdx.x; e < p * RM; e += kThreads) Ps[e] = P[e];
@@ -158,6 +160,8 @@ template <int RM>
 __global__ void __launch_bounds__(kBpThreads)
 backproject_kernel(const float* __restrict__ Zh, long long n, const float* __restrict__ Q,
                    int p, const int* __restrict__ rank, float* __restrict__ X) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float4 Qs4[];
     float* Qs = reinterpret_cast<float*>(Qs4);
     for (int e = threadIdx.x; e < p * RM; e += kBpThreads) Qs[e] = Q[e];
@@ -204,9 +208,9 @@ hyde_status launch_project_pad(const float* Y, int p, int H, int W, const float*
     case RMV:                                                                                  \
         if (ensure_smem_limit((const void*)project_pad_kernel<RMV>, (int)smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                              \
-        project_pad_kernel<RMV><<<resident_grid((const void*)project_pad_kernel<RMV>,          \
+        launch_pdl(project_pad_kernel<RMV>, resident_grid((const void*)project_pad_kernel<RMV>,          \
                                                 kThreads, smem, tiles),                        \
-                                  kThreads, smem, s>>>(Y, p, H, W, P, r, Zp, Hp, Wp,           \
+                                  kThreads, smem, s, Y, p, H, W, P, r, Zp, Hp, Wp,           \
                                                        zero_pad ? 1 : 0);                      \
         break;
         HYDE_PROJ(4) HYDE_PROJ(8) HYDE_PROJ(12) HYDE_PROJ(16)
@@ -228,9 +232,9 @@ hyde_status launch_backproject(const float* Zh, long long n, const float* Q, int
     case RMV:                                                                                  \
         if (ensure_smem_limit((const void*)backproject_kernel<RMV>, (int)smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                              \
-        backproject_kernel<RMV><<<resident_grid((const void*)backproject_kernel<RMV>,          \
+        launch_pdl(backproject_kernel<RMV>, resident_grid((const void*)backproject_kernel<RMV>,          \
                                                 kBpThreads, smem, tiles),                      \
-                                  kBpThreads, smem, s>>>(Zh, n, Q, p, rank, X);                \
+                                  kBpThreads, smem, s, Zh, n, Q, p, rank, X);                \
         break;
         HYDE_BACK(4) HYDE_BACK(8) HYDE_BACK(12) HYDE_BACK(16)
         HYDE_BACK(20) HYDE_BACK(24) HYDE_BACK(28) HYDE_BACK(32)

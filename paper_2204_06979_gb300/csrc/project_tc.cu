@@ -145,6 +145,8 @@ __global__ void __launch_bounds__(kPjThreads, 1)
 project_tc_kernel(const float* __restrict__ Y, int p, int H, int W, const float* __restrict__ P,
                   int r, int ldw, float* __restrict__ Zp, int Hp, int Wp, int zero_pad,
                   int* status) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kPjStages], empty_bar[kPjStages];
     __shared__ uint64_t tfull_bar[2], tempty_bar[2];
@@ -368,6 +370,8 @@ __global__ void __launch_bounds__(kBpThreads, 1)
 backproject_tc_kernel(const float* __restrict__ Zh, long long n, const float* __restrict__ Q,
                       int p, int ldw, const int* __restrict__ rank, float* __restrict__ X,
                       int* status) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kBpStages], empty_bar[kBpStages];
     __shared__ uint64_t tfull_bar[2], tempty_bar[2];
@@ -577,7 +581,7 @@ hyde_status launch_project_pad_tc(const float* Y, int p, int H, int W, const flo
     long long grid = device_sm_count();
     if (grid <= 0) return HYDE_ERR_CUDA;
     if (grid > tiles) grid = tiles;
-    project_tc_kernel<<<(int)grid, kPjThreads, smem, s>>>(Y, p, H, W, P, r, ldw, Zp, Hp, Wp, 0,
+    launch_pdl(project_tc_kernel, (int)grid, kPjThreads, smem, s, Y, p, H, W, P, r, ldw, Zp, Hp, Wp, 0,
                                                           status);
     return cuda_status(cudaGetLastError());
 }
@@ -593,7 +597,7 @@ hyde_status launch_backproject_tc(const float* Zh, long long n, const float* Q, 
     long long grid = device_sm_count();
     if (grid <= 0) return HYDE_ERR_CUDA;
     if (grid > tiles) grid = tiles;
-    backproject_tc_kernel<<<(int)grid, kBpThreads, smem, s>>>(Zh, n, Q, p, ldw, rank, X, status);
+    launch_pdl(backproject_tc_kernel, (int)grid, kBpThreads, smem, s, Zh, n, Q, p, ldw, rank, X, status);
     return cuda_status(cudaGetLastError());
 }
 

@@ -44,6 +44,8 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
                  float inv_delta, float qscale, double inv_qscale, int rows_per_block,
                  unsigned int* __restrict__ counts, double* __restrict__ sums,
                  double* __restrict__ sum_all) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ unsigned int hsm[];   // counts [K][32], then sums [K][32]
     __shared__ double wall[kHistThreads / 32];
     unsigned int* hc = hsm;
@@ -140,6 +142,8 @@ sure_table_kernel(const unsigned int* __restrict__ counts, const double* __restr
                   const double* __restrict__ sum_all, int batch, int K, long long N,
                   long long N_det, double delta, double* __restrict__ S,
                   double* __restrict__ S_inf) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= batch) return;
@@ -180,6 +184,8 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
                    long long N_det, double delta, double* __restrict__ S,
                    double* __restrict__ S_inf, double* __restrict__ T, unsigned int* done,
                    hyde_hyres_info* info, int* rank_out, double* lam_out, const int* status) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double tail[kMaxRank];
     __shared__ double wm1[8], wm2[8];
     __shared__ int wi1[8];
@@ -311,7 +317,7 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int l
     if (ensure_smem_limit((const void*)sure_hist_kernel, (int)smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 grid(per_comp, batch);
-    sure_hist_kernel<<<grid, kHistThreads, smem, s>>>(
+    launch_pdl(sure_hist_kernel, grid, kHistThreads, smem, s, 
         coef, Hp, Wp, Hp >> levels, Wp >> levels, K, inv_delta, (float)std::ldexp(1.0, sh),
         std::ldexp(1.0, -sh), (int)rows, b.counts, b.sums, b.sum_all);
     return cuda_status(cudaGetLastError());
@@ -322,7 +328,7 @@ hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
                                double* T, hyde_hyres_info* info, int* rank_out,
                                double* lam_out, const int* status, cudaStream_t s) {
     if (T == nullptr) {   // the tables only
-        sure_table_kernel<<<(batch + 7) / 8, 256, 0, s>>>(b.counts, b.sums, b.sum_all, batch, K,
+        launch_pdl(sure_table_kernel, (batch + 7) / 8, 256, 0, s, b.counts, b.sums, b.sum_all, batch, K,
                                                            N, N_det, delta, S, S_inf);
     } else {
         if (batch > kMaxRank || b.done == nullptr) return HYDE_ERR_SHAPE;
@@ -331,7 +337,7 @@ hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
         const size_t smem = (size_t)batch * K * sizeof(double);
         if (ensure_smem_limit((const void*)sure_select_kernel, (int)smem) != cudaSuccess)
             return HYDE_ERR_CUDA;
-        sure_select_kernel<<<batch, threads, smem, s>>>(b.counts, b.sums, b.sum_all, batch, K, N,
+        launch_pdl(sure_select_kernel, batch, threads, smem, s, b.counts, b.sums, b.sum_all, batch, K, N,
                                                      N_det, delta, S, S_inf, T, b.done, info,
                                                      rank_out, lam_out, status);
     }

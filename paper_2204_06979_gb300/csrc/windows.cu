@@ -18,6 +18,8 @@ namespace {
 // scene [p][H][W] -> cube [p][h][w] of the window at (y0, x0)
 __global__ void gather_window_kernel(const float* __restrict__ Y, int H, int W, int y0, int x0,
                                      int h, int w, int p, float* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const long long n = (long long)h * w, tot = n * p;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
          e += (long long)gridDim.x * blockDim.x) {
@@ -32,6 +34,8 @@ __global__ void gather_window_kernel(const float* __restrict__ Y, int H, int W, 
 __global__ void scatter_core_kernel(const float* __restrict__ cube, int h, int w, int y0, int x0,
                                     int cy0, int cx0, int ch, int cw, int p, int H, int W,
                                     float* __restrict__ X) {
+    pdl_wait();
+    pdl_trigger();
     const long long n = (long long)ch * cw, tot = n * p;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
          e += (long long)gridDim.x * blockDim.x) {
@@ -52,7 +56,7 @@ hyde_status launch_gather_window(const float* Y, int H, int W, int y0, int x0, i
     const int sms = device_sm_count();
     long long blocks = (tot + 255) / 256;
     if (blocks > 8LL * sms) blocks = 8LL * sms;
-    gather_window_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, H, W, y0, x0, h, w, p, out);
+    launch_pdl(gather_window_kernel, (unsigned)blocks, 256, 0, s, Y, H, W, y0, x0, h, w, p, out);
     return cuda_status(cudaGetLastError());
 }
 
@@ -63,7 +67,7 @@ hyde_status launch_scatter_core(const float* cube, int h, int w, int y0, int x0,
     const int sms = device_sm_count();
     long long blocks = (tot + 255) / 256;
     if (blocks > 8LL * sms) blocks = 8LL * sms;
-    scatter_core_kernel<<<(unsigned)blocks, 256, 0, s>>>(cube, h, w, y0, x0, cy0, cx0, ch, cw, p,
+    launch_pdl(scatter_core_kernel, (unsigned)blocks, 256, 0, s, cube, h, w, y0, x0, cy0, cx0, ch, cw, p,
                                                          H, W, X);
     return cuda_status(cudaGetLastError());
 }
