@@ -343,44 +343,35 @@ __device__ __forceinline__ float4 soft4(float4 v, float lam) {
     return make_float4(soft(v.x, lam), soft(v.y, lam), soft(v.z, lam), soft(v.w, lam));
 }
 
-__global__ void __launch_bounds__(kSynThreads)
-idwt_level_vec_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
-                      const float* __restrict__ coef, long long coef_bs, int coef_ld, int h,
-                      int w, const double* __restrict__ lam, const float* __restrict__ scale,
-                      int scale_ld, int lev, const int* __restrict__ rank,
-                      float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo,
-                      int vout) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ float4 stage4[kSynWarps][2][64];   // two output rows of 256 floats per warp
-    const int b = blockIdx.y;
-    if (rank && b >= *rank) return;
-    float lv = lam ? (float)(*lam) : 0.f;
-    if (lam && scale) lv *= scale[(long long)b * scale_ld + (lev - 1)];
-    const int hh = h >> 1, wh = w >> 1;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nstrips = (wh + 127) >> 7;
-    const int nruns = (hh + kSynRows - 1) / kSynRows;
-    const int u = blockIdx.x * kSynWarps + wid;
-    if (u >= nstrips * nruns) return;   // whole warp
-    const int strip = u % nstrips, run = u / nstrips;
+// One (strip, run) unit of the register-form synthesis for the calling warp.
+// L is the LL band (global memory when LLG, else shared memory), C the
+// component's coefficient image; st0/st1 the warp's staging rows (used when
+// !vout).
+template <bool LLG, int ROWS>
+__device__ __forceinline__ void syn_unit(const float* L, int ll_ld, const float* __restrict__ C,
+                                         int coef_ld, int hh, int wh, float lv, int strip,
+                                         int run, float* O, int out_ld, int ho, int wo,
+                                         bool vout, float4* st0, float4* st1, int lane) {
     const int k0 = strip * 128 + 4 * lane;
     const bool active = k0 < wh;        // wh is a multiple of 4: the lane's 4 columns exist
     const int kc = active ? k0 : 0;
     const int km1 = (strip == 0 ? wh : strip * 128) - 1;
-    const float* L = llsrc + (long long)b * ll_bs;
-    const float* C = coef + (long long)b * coef_bs;
+    auto ldl4 = [&](long long off) {
+        return LLG ? __ldg(reinterpret_cast<const float4*>(L + off))
+                   : *reinterpret_cast<const float4*>(L + off);
+    };
+    auto ldl1 = [&](long long off) { return LLG ? __ldg(L + off) : L[off]; };
     // bands in the order LL, LH (column detail), HL (row detail), HH
     auto load_row = [&](int J, float4 (&v)[4], float (&left)[4]) {
         const long long rl = (long long)J * ll_ld, rt = (long long)J * coef_ld,
                         rb = (long long)(hh + J) * coef_ld;
-        v[0] = __ldg(reinterpret_cast<const float4*>(L + rl + kc));
+        v[0] = ldl4(rl + kc);
         v[1] = soft4(__ldg(reinterpret_cast<const float4*>(C + rb + kc)), lv);
         v[2] = soft4(__ldg(reinterpret_cast<const float4*>(C + rt + wh + kc)), lv);
         v[3] = soft4(__ldg(reinterpret_cast<const float4*>(C + rb + wh + kc)), lv);
         float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
         if (lane == 0) {
-            e0 = __ldg(L + rl + km1);
+            e0 = ldl1(rl + km1);
             e1 = soft(__ldg(C + rb + km1), lv);
             e2 = soft(__ldg(C + rt + wh + km1), lv);
             e3 = soft(__ldg(C + rb + wh + km1), lv);
@@ -391,14 +382,13 @@ idwt_level_vec_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_l
         left[3] = __shfl_up_sync(0xffffffffu, v[3].w, 1);
         if (lane == 0) { left[0] = e0; left[1] = e1; left[2] = e2; left[3] = e3; }
     };
-    const int j0 = run * kSynRows;
+    const int j0 = run * ROWS;
     float4 pv[4];
     float pl[4];
     load_row(j0 == 0 ? hh - 1 : j0 - 1, pv, pl);
-    float* O = out + (long long)b * out_bs;
     const int X0 = 2 * k0;
 #pragma unroll
-    for (int s = 0; s < kSynRows; ++s) {
+    for (int s = 0; s < ROWS; ++s) {
         const int j = j0 + s;
         if (j >= hh) break;   // warp-uniform
         float4 cv[4];
@@ -438,8 +428,6 @@ idwt_level_vec_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_l
                 *reinterpret_cast<float4*>(r1 + 4) = make_float4(oo[4], oo[5], oo[6], oo[7]);
             }
         } else {
-            float4* st0 = stage4[wid][0];
-            float4* st1 = stage4[wid][1];
             st0[2 * lane] = make_float4(oe[0], oe[1], oe[2], oe[3]);
             st0[2 * lane + 1] = make_float4(oe[4], oe[5], oe[6], oe[7]);
             st1[2 * lane] = make_float4(oo[0], oo[1], oo[2], oo[3]);
@@ -463,6 +451,144 @@ idwt_level_vec_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_l
     }
 }
 
+__global__ void __launch_bounds__(kSynThreads)
+idwt_level_vec_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
+                      const float* __restrict__ coef, long long coef_bs, int coef_ld, int h,
+                      int w, const double* __restrict__ lam, const float* __restrict__ scale,
+                      int scale_ld, int lev, const int* __restrict__ rank,
+                      float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo,
+                      int vout) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ float4 stage4[kSynWarps][2][64];   // two output rows of 256 floats per warp
+    const int b = blockIdx.y;
+    if (rank && b >= *rank) return;
+    float lv = lam ? (float)(*lam) : 0.f;
+    if (lam && scale) lv *= scale[(long long)b * scale_ld + (lev - 1)];
+    const int hh = h >> 1, wh = w >> 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nstrips = (wh + 127) >> 7;
+    const int nruns = (hh + kSynRows - 1) / kSynRows;
+    const int u = blockIdx.x * kSynWarps + wid;
+    if (u >= nstrips * nruns) return;   // whole warp
+    syn_unit<true, kSynRows>(llsrc + (long long)b * ll_bs, ll_ld,
+                             coef + (long long)b * coef_bs, coef_ld, hh, wh, lv, u % nstrips,
+                             u / nstrips, out + (long long)b * out_bs, out_ld, ho, wo, vout != 0,
+                             stage4[wid][0], stage4[wid][1], lane);
+}
+
+// --------------------------------------------------------------------------
+// The coarse levels in one block per component. Below a few tens of
+// thousands of coefficients a level is all launch and ramp: one launch per
+// level leaves most SMs idle while each of its blocks waits on its first
+// load. These kernels run levels lo..hi of one component in one block (1024
+// threads for the analysis, 768 for the synthesis), the intermediate LL bands
+// in shared memory.
+// --------------------------------------------------------------------------
+constexpr int kTailThreads = 1024;
+constexpr int kTailSynThreads = 768;   // 24 warps: the synthesis unit needs ~73 registers
+// The tail starts at the first level with at most this many input values
+// (analysis) or output values (synthesis) per component: below it a level on
+// one SM costs less than a launch of its own (at C1, levels 4-5: the level-3
+// input, 42k values, took 13.7 us on one SM against 4.5 us as its own launch).
+constexpr int kTailMaxFloats = 12288;
+
+// Analysis, levels lo..hi: the input LL_{lo-1} (h0 x w0) is loaded once; each
+// thread forms the four subbands of one coefficient, consecutive lanes taking
+// consecutive columns (float2 shared loads, no bank conflicts), the row filter
+// recomputed for each of its 4 input rows (no row-pass buffer).
+__global__ void __launch_bounds__(kTailThreads, 1)
+dwt_tail_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int Hp, int Wp,
+                int lo, int hi, float* __restrict__ coef, long long coef_bs, int coef_ld) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ float4 tail4[];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int h0 = Hp >> (lo - 1), w0 = Wp >> (lo - 1);
+    float* A = reinterpret_cast<float*>(tail4);   // h0 x w0
+    float* B = A + h0 * w0;                        // h0/2 x w0/2
+    const float* S = src + (long long)b * src_bs;
+    const int w4 = w0 >> 2;
+    for (int e = tid; e < h0 * w4; e += kTailThreads) {
+        const int y = e / w4, x4 = e - y * w4;
+        reinterpret_cast<float4*>(A)[e] =
+            __ldg(reinterpret_cast<const float4*>(S + (long long)y * src_ld) + x4);
+    }
+    __syncthreads();
+    float* CB = coef + (long long)b * coef_bs;
+    for (int l = lo; l <= hi; ++l) {
+        const int h = Hp >> (l - 1), w = Wp >> (l - 1), hh = h >> 1, wh = w >> 1;
+        const float* in = ((l - lo) & 1) ? B : A;
+        float* ob = ((l - lo) & 1) ? A : B;
+        for (int e = tid; e < hh * wh; e += kTailThreads) {
+            const int J = e / wh, K = e - J * wh;
+            const int x0 = 2 * K, x2 = (2 * K + 2 >= w) ? 2 * K + 2 - w : 2 * K + 2;
+            float a[4], d[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                int y = 2 * J + m;
+                if (y >= h) y -= h;
+                const float* row = in + y * w;
+                const float2 u = *reinterpret_cast<const float2*>(row + x0);
+                const float2 v = *reinterpret_cast<const float2*>(row + x2);
+                a[m] = kH0 * u.x + kH1 * u.y + kH2 * v.x + kH3 * v.y;
+                d[m] = kG0 * u.x + kG1 * u.y + kG2 * v.x + kG3 * v.y;
+            }
+            const float LL = kH0 * a[0] + kH1 * a[1] + kH2 * a[2] + kH3 * a[3];
+            const float LH = kG0 * a[0] + kG1 * a[1] + kG2 * a[2] + kG3 * a[3];
+            const float HL = kH0 * d[0] + kH1 * d[1] + kH2 * d[2] + kH3 * d[3];
+            const float HH = kG0 * d[0] + kG1 * d[1] + kG2 * d[2] + kG3 * d[3];
+            float* pt = CB + (long long)J * coef_ld;
+            float* pb = CB + (long long)(hh + J) * coef_ld;
+            pt[wh + K] = HL;
+            pb[K] = LH;
+            pb[wh + K] = HH;
+            if (l == hi) pt[K] = LL;
+            else ob[J * wh + K] = LL;
+        }
+        __syncthreads();
+    }
+}
+
+// Synthesis, levels hi..lo: the LL band of level l > lo goes to shared memory
+// (level lo+1 into A, then alternating), level lo writes LL_{lo-1} to `out`
+// (row stride Wp >> (lo-1), 16-byte aligned rows). Warps take the (strip,
+// run) units of a level in turn, one coefficient row each.
+__global__ void __launch_bounds__(kTailSynThreads, 1)
+idwt_tail_kernel(const float* __restrict__ coef, long long coef_bs, int coef_ld, int Hp, int Wp,
+                 int lo, int hi, const double* __restrict__ lam, const float* __restrict__ scale,
+                 int scale_ld, const int* __restrict__ rank, float* __restrict__ out,
+                 long long out_bs) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ float4 tail4[];
+    const int b = blockIdx.x;
+    if (rank && b >= *rank) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* A = reinterpret_cast<float*>(tail4);          // (Hp >> lo) x (Wp >> lo)
+    float* B = A + (Hp >> lo) * (Wp >> lo);               // a quarter of A
+    const float* C = coef + (long long)b * coef_bs;
+    const float lam0 = lam ? (float)(*lam) : 0.f;
+    for (int l = hi; l >= lo; --l) {
+        const int h = Hp >> (l - 1), w = Wp >> (l - 1), hh = h >> 1, wh = w >> 1;
+        float lv = lam0;
+        if (lam && scale) lv *= scale[(long long)b * scale_ld + (l - 1)];
+        float* O = (l == lo) ? out + (long long)b * out_bs : (((l - lo) & 1) ? A : B);
+        const int nstrips = (wh + 127) >> 7;
+        const int units = nstrips * hh;   // one coefficient row per unit: more warps busy
+        for (int u = wid; u < units; u += kTailSynThreads / 32) {
+            if (l == hi)
+                syn_unit<true, 1>(C, coef_ld, C, coef_ld, hh, wh, lv, u % nstrips, u / nstrips, O, w,
+                               h, w, true, nullptr, nullptr, lane);
+            else
+                syn_unit<false, 1>(((l + 1 - lo) & 1) ? A : B, wh, C, coef_ld, hh, wh, lv,
+                                u % nstrips, u / nstrips, O, w, h, w, true, nullptr, nullptr,
+                                lane);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 size_t dwt_scratch_floats(int Hp, int Wp) {
@@ -480,6 +606,21 @@ static inline float* ll_buf(float* scratch, int batch, int Hp, int Wp, int j,
     return scratch + (size_t)batch * (N / 4);
 }
 
+// First level of the fused coarse tail: the smallest lo >= 2 whose level-lo
+// input (analysis) / output (synthesis), (Hp >> (lo-1)) x (Wp >> (lo-1)),
+// has at most kTailMaxFloats values, provided every tail level keeps its
+// half-width a multiple of 4 (float4 rows); levels + 1 when there is none.
+static int tail_first_level(int Hp, int Wp, int levels) {
+    if (levels < 2 || (Wp & 3) != 0 || ((Wp >> levels) & 3) != 0) return levels + 1;
+    for (int lo = 2; lo <= levels; ++lo)
+        if ((long long)(Hp >> (lo - 1)) * (Wp >> (lo - 1)) <= kTailMaxFloats) return lo;
+    return levels + 1;
+}
+
+static inline bool aligned16(const void* p) {
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
 hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int Wp,
                         int levels, float* scratch, cudaStream_t s) {
     const long long cbs = (long long)Hp * Wp;
@@ -493,7 +634,14 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
                                                       kFThreads, pipe_smem) != cudaSuccess ||
         pipe_per_sm < 1)
         pipe_per_sm = 1;
-    for (int lev = 1; lev <= levels; ++lev) {
+    int lo = tail_first_level(Hp, Wp, levels);
+    if (lo <= levels) {
+        long long bs;
+        const float* tin = ll_buf(scratch, batch, Hp, Wp, lo - 1, &bs);
+        if (!aligned16(tin) || !aligned16(coef) || (bs & 3) != 0 || (cbs & 3) != 0)
+            lo = levels + 1;
+    }
+    for (int lev = 1; lev <= levels && lev < lo; ++lev) {
         const int h = Hp >> (lev - 1), w = Wp >> (lev - 1);
         const float* sp;
         long long sbs;
@@ -519,9 +667,19 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
             int G = (pipe_per_sm * sms + batch - 1) / batch;
             if (G > ntiles) G = ntiles;
             if (G < 1) G = 1;
-            launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s, 
+            launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s,
                 sp, sbs, sld, h, w, coef, cbs, Wp, lp, lbs, lld);
         }
+    }
+    if (lo <= levels) {
+        long long bs;
+        const float* tin = ll_buf(scratch, batch, Hp, Wp, lo - 1, &bs);
+        const size_t smem =
+            (size_t)(Hp >> (lo - 1)) * (Wp >> (lo - 1)) * 5 / 4 * sizeof(float);
+        if (ensure_smem_limit((const void*)dwt_tail_kernel, (int)smem) != cudaSuccess)
+            return HYDE_ERR_CUDA;
+        launch_pdl(dwt_tail_kernel, batch, kTailThreads, smem, s, tin, bs, Wp >> (lo - 1), Hp,
+                   Wp, lo, levels, coef, cbs, Wp);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -530,7 +688,21 @@ hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int W
                          int W, int levels, float* scratch, const double* lam,
                          const int* rank, cudaStream_t s, const float* scale, int scale_ld) {
     const long long cbs = (long long)Hp * Wp;
-    for (int lev = levels; lev >= 1; --lev) {
+    int lo = tail_first_level(Hp, Wp, levels);
+    if (lo <= levels) {
+        long long bs;
+        float* tout = ll_buf(scratch, batch, Hp, Wp, lo - 1, &bs);
+        if (!aligned16(tout) || !aligned16(coef) || (bs & 3) != 0 || (cbs & 3) != 0) {
+            lo = levels + 1;
+        } else {
+            const size_t smem = (size_t)(Hp >> lo) * (Wp >> lo) * 5 / 4 * sizeof(float);
+            if (ensure_smem_limit((const void*)idwt_tail_kernel, (int)smem) != cudaSuccess)
+                return HYDE_ERR_CUDA;
+            launch_pdl(idwt_tail_kernel, batch, kTailSynThreads, smem, s, coef, cbs, Wp, Hp, Wp, lo,
+                       levels, lam, scale, scale_ld, rank, tout, bs);
+        }
+    }
+    for (int lev = (lo <= levels ? lo - 1 : levels); lev >= 1; --lev) {
         const int h = Hp >> (lev - 1), w = Wp >> (lev - 1);
         const float* lp;
         long long lbs;

@@ -223,7 +223,7 @@ gram_partial84_kernel(const float* __restrict__ Y, int p, long long n, int PT, i
             const float4* Ba = B + 64 * ti;   // rows 8ti .. 8ti+7
             const float4* Bb = B + 32 * tj;   // rows 4tj .. 4tj+3
             const int xa0 = (2 * ti) & 7, xa1 = (2 * ti + 1) & 7, xb = tj & 7;
-#pragma unroll 1
+#pragma unroll 2
             for (int q = 0; q < 8; ++q) {
                 float4 a[8], b[4];
 #pragma unroll
@@ -366,7 +366,7 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
         launch_pdl(gram_partial_kernel<384>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT, g.ntiles,
                                                                      per, partials);
     else
-        launch_pdl(gram_partial_kernel<kGramMaxThreads>, g.blocks, g.threads, g.smem, s, 
+        launch_pdl(gram_partial_kernel<kGramMaxThreads>, g.blocks, g.threads, g.smem, s,
             Y, p, n, g.PT, g.ntiles, per, partials);
     long long tot = (long long)g.ntiles * (g.mode == 0 ? 64 : 32);
     if (cudaMemsetAsync(R, 0, (size_t)p * p * sizeof(double), s) != cudaSuccess)

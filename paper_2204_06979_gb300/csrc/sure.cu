@@ -317,7 +317,7 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int l
     if (ensure_smem_limit((const void*)sure_hist_kernel, (int)smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 grid(per_comp, batch);
-    launch_pdl(sure_hist_kernel, grid, kHistThreads, smem, s, 
+    launch_pdl(sure_hist_kernel, grid, kHistThreads, smem, s,
         coef, Hp, Wp, Hp >> levels, Wp >> levels, K, inv_delta, (float)std::ldexp(1.0, sh),
         std::ldexp(1.0, -sh), (int)rows, b.counts, b.sums, b.sum_all);
     return cuda_status(cudaGetLastError());
