@@ -151,17 +151,6 @@ gram_partial_kernel(const float* __restrict__ Y, int p, long long n, int PT,
 // the float4 operands, so 128 FMAs of four pixels take 64 instructions. The
 // stage rows are swizzled by (b >> 2) & 7 so that the 4-row B tiles of a
 // warp's lanes fall on different float4 columns.
-__device__ __forceinline__ void fma_f32x2(float& c0, float& c1, float a0, float a1, float b0,
-                                          float b1) {
-    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
-        "mov.b64 ra, {%2, %3};\n\t"
-        "mov.b64 rb, {%4, %5};\n\t"
-        "mov.b64 rc, {%0, %1};\n\t"
-        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
-        "mov.b64 {%0, %1}, rc;\n\t}"
-        : "+f"(c0), "+f"(c1)
-        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
-}
 
 __device__ __forceinline__ void tile84_of(int t, int PT, int& ti, int& tj) {
     // row ti holds the 2 PT - 2 ti tiles tj = 2 ti .. 2 PT - 1

@@ -52,6 +52,20 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// Two FP32 FMAs in one instruction (c0 += a0 b0, c1 += a1 b1, each rounded
+// once): halves the issue slots of the FMA-heavy loops.
+__device__ __forceinline__ void fma_f32x2(float& c0, float& c1, float a0, float a1, float b0,
+                                          float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%0, %1};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

@@ -10,8 +10,11 @@
 // weight load feeds eight FMAs), keeps two groups of 8 bands x 2 pixels of
 // loads in flight per thread and writes straight into the padded H_p x W_p
 // component images (whole-sample symmetric reflection at the bottom/right),
-// so the DWT never sees an unpadded image. The back-projection (one pixel per
-// thread) unrolls to ceil(r*/4)*4 terms, r* read on the device.
+// so the DWT never sees an unpadded image; its two pixels per thread share
+// each weight in one fma.rn.f32x2. The back-projection (one pixel per thread)
+// unrolls to ceil(r*/4)*4 terms, r* read on the device; two pixels per thread
+// there (paired FMAs, half the weight loads) measured slower, 113 against
+// 109 us at C1: the extra registers cost a third of the resident warps.
 #include "hyde_internal.cuh"
 
 namespace hyde {
@@ -45,19 +48,18 @@ __device__ __forceinline__ bool padded_source(long long pix, int H, int W, int W
     return true;
 }
 
+// The two pixels of a thread share each weight: one paired FMA per component.
+static_assert(kPix == 2, "the projection pairs its two pixels in fma.rn.f32x2");
 template <int RM>
 __device__ __forceinline__ void project_fma(float (&acc)[kPix][RM], const float (&v)[kPix],
                                             const float4* __restrict__ w4) {
 #pragma unroll
     for (int q = 0; q < RM / 4; ++q) {
         const float4 w = w4[q];
-#pragma unroll
-        for (int u = 0; u < kPix; ++u) {
-            acc[u][4 * q + 0] = fmaf(v[u], w.x, acc[u][4 * q + 0]);
-            acc[u][4 * q + 1] = fmaf(v[u], w.y, acc[u][4 * q + 1]);
-            acc[u][4 * q + 2] = fmaf(v[u], w.z, acc[u][4 * q + 2]);
-            acc[u][4 * q + 3] = fmaf(v[u], w.w, acc[u][4 * q + 3]);
-        }
+        fma_f32x2(acc[0][4 * q + 0], acc[1][4 * q + 0], v[0], v[1], w.x, w.x);
+        fma_f32x2(acc[0][4 * q + 1], acc[1][4 * q + 1], v[0], v[1], w.y, w.y);
+        fma_f32x2(acc[0][4 * q + 2], acc[1][4 * q + 2], v[0], v[1], w.z, w.z);
+        fma_f32x2(acc[0][4 * q + 3], acc[1][4 * q + 3], v[0], v[1], w.w, w.w);
     }
 }
 
