@@ -71,7 +71,8 @@ struct HyresLayout {
     long long N, n;
     GramPlan gram;
     hyde_ws_layout pub;
-    size_t rank_dev, lam_dev, counts, sums, sum_all, done, P, Q, noise, partials, zp, scratch;
+    size_t rank_dev, lam_dev, counts, sums, sum_all, done, sint, P, Q, noise, partials, zp,
+        scratch;
     size_t zero_begin, zero_end;
 };
 
@@ -121,6 +122,7 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.pub.sure = c.take((size_t)r * K * sizeof(double));
     l.pub.sure_inf = c.take((size_t)r * sizeof(double));
     l.pub.sure_total = c.take((size_t)r * K * sizeof(double));
+    l.sint = c.take((size_t)2 * r * K * sizeof(long long));
     l.P = c.take((size_t)p * l.RM * sizeof(float));
     l.Q = c.take((size_t)p * l.RM * sizeof(float));
     l.noise = c.take(noise_ws_bytes(p));
@@ -300,6 +302,7 @@ hyde_status hyde_sure_table(const float* coef, int batch, int Hp, int Wp, int le
     b.sum_all = reinterpret_cast<double*>(reinterpret_cast<char*>(b.sums) +
                                           align_up((size_t)batch * K * sizeof(double), kAlign));
     b.done = nullptr;   // the table-only path has no selection
+    b.sint = nullptr;
     if (cudaMemsetAsync(ws, 0, need, stream) != cudaSuccess) return HYDE_ERR_CUDA;
     const long long N = (long long)Hp * Wp;
     const long long N_det = N - (long long)(Hp >> levels) * (Wp >> levels);
@@ -354,7 +357,7 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     float* coef = at<float>(ws, L.pub.coef);
     float* scratch = at<float>(ws, L.scratch);
     SureBufs sb{at<unsigned int>(ws, L.counts), at<double>(ws, L.sums), at<double>(ws, L.sum_all),
-                at<unsigned int>(ws, L.done)};
+                at<unsigned int>(ws, L.done), at<long long>(ws, L.sint)};
     int mark = 0;
     auto stage = [&]() -> hyde_status {
         if (!ev) return HYDE_OK;

@@ -227,6 +227,7 @@ struct SureBufs {
     double* sums;           // [batch][K]
     double* sum_all;        // [batch]
     unsigned int* done;     // blocks finished (selection kernel); cleared with the rest
+    long long* sint;        // [2][batch][K] integer prefix rows (selection kernel)
 };
 size_t sure_accum_bytes(int batch, int K);
 hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp,

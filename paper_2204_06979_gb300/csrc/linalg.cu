@@ -206,18 +206,37 @@ noise_refine_kernel(const double* __restrict__ R, const float* __restrict__ Ainv
         xs[i] = (double)Ainv[(long long)i * p + b] / (S[i] * sb);
     __syncthreads();
     // x^T R x = sum_i x_i sum_j R_ij x_j: each lane keeps its own share of
-    // the double sum (rows w + 8m, columns lane + 32q); one warp sum at the end
+    // the double sum (rows w + 8m, columns lane + 32q); one warp sum at the end.
+    // Rows go in groups of kRefRows whose loads are all issued before the
+    // first FMA, so the warp waits on L2 once per group, not once per row.
+    constexpr int kRefRows = 4;
     double part = 0.0;
-    for (int i = w; i < p; i += 8) {
-        const double* Ri = R + (long long)i * p;
-        double u = 0.0;
-#pragma unroll 8
-        for (int q = 0; q < 8; ++q) {
-            const int j = lane + 32 * q;
-            if (j < p) u = fma(__ldg(Ri + j), xs[j], u);
+    for (int i0 = w; i0 < p; i0 += 8 * kRefRows) {
+        double rv[kRefRows][8];
+#pragma unroll
+        for (int m = 0; m < kRefRows; ++m) {
+            const int i = i0 + 8 * m;
+            const double* Ri = R + (long long)(i < p ? i : 0) * p;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = lane + 32 * q;
+                rv[m][q] = (i < p && j < p) ? __ldg(Ri + j) : 0.0;
+            }
         }
-        for (int j = lane + 256; j < p; j += 32) u = fma(__ldg(Ri + j), xs[j], u);
-        part = fma(xs[i], u, part);
+#pragma unroll
+        for (int m = 0; m < kRefRows; ++m) {
+            const int i = i0 + 8 * m;
+            if (i >= p) break;
+            const double* Ri = R + (long long)i * p;
+            double u = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = lane + 32 * q;
+                if (j < p) u = fma(rv[m][q], xs[j], u);
+            }
+            for (int j = lane + 256; j < p; j += 32) u = fma(__ldg(Ri + j), xs[j], u);
+            part = fma(xs[i], u, part);
+        }
     }
     part = warp_sum_d(part);
     if (lane == 0) red[w] = part;

@@ -169,51 +169,96 @@ sure_table_kernel(const unsigned int* __restrict__ counts, const double* __restr
     if (lane == 0) S_inf[i] = sum_all[i] - (double)N;
 }
 
-// Table and choice over the grid: block i (one warp of work) forms
-// S_i(lambda_k) by warp scans over the bins and S_inf[i], so the FP64 work is
-// spread over `batch` SMs (FP64 runs at a small fraction of the FP32 rate on
-// this part); the last block to finish (a counter in the zeroed workspace)
-// forms T(r, k) = sum_{i<=r} S_i(lambda_k) + sum_{i>r} S_inf[i] with one
-// thread per column k walking r upwards (a sequential prefix: fewer FP64
-// instructions than scans), keeps each column's first minimum and runner-up,
-// and reduces them: the first minimum in row-major (rank, lambda) order and
-// the relative gap to the runner-up.
-__global__ void __launch_bounds__(256)
+// Table and choice over the grid. FP64 runs at a small fraction of the FP32
+// rate on this part and a dependent FP64 instruction costs many cycles, so
+// the counts and clipped sums are prefixed as integers: the histogram sums
+// are exact multiples of 2^-16 (the fixed-point unit of the histogram, or a
+// coarser power of two), so with c the count and q the sum in units of
+// 2^-16, both cumulated over the bins up to k,
+//   A_ik = (N - 2 c) 2^16 + q,   B_ik = N_det - c   (64-bit integers)
+// give S_i(lambda_k) = A_ik 2^-16 + lambda_k^2 B_ik exactly but for the final
+// rounding. Block i forms row i of A and B (block-wide integer scans) and of
+// S, and S_inf[i]; the last block to finish (a counter in the zeroed
+// workspace) prefixes A and B over the components, which gives
+//   T(r, k) = sum_{i<=r} S_i(lambda_k) + sum_{i>r} S_inf[i]
+//           = PA_rk 2^-16 + lambda_k^2 PB_rk + sum_{i>r} S_inf[i],
+// forms every T with a few FP64 operations spread over the block, and finds
+// the first minimum in row-major (rank, lambda) order and the runner-up on
+// order-preserving integer keys.
+constexpr int kSelThreads = 256;
+
+__device__ __forceinline__ long long ord_key(double v) {
+    const long long bits = __double_as_longlong(v);
+    return bits >= 0 ? bits : bits ^ 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ double key_value(long long k) {
+    return __longlong_as_double(k >= 0 ? k : k ^ 0x7fffffffffffffffLL);
+}
+
+// inclusive block scan of (c, q) over threads 0..blockDim-1 (kSelThreads)
+__device__ __forceinline__ void block_scan2(long long& c, long long& q, long long* wc,
+                                            long long* wq) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long c2 = __shfl_up_sync(0xffffffffu, c, o);
+        const long long q2 = __shfl_up_sync(0xffffffffu, q, o);
+        if (lane >= o) { c += c2; q += q2; }
+    }
+    if (lane == 31) { wc[wid] = c; wq[wid] = q; }
+    __syncthreads();
+    long long oc = 0, oq = 0;
+    for (int w = 0; w < wid; ++w) { oc += wc[w]; oq += wq[w]; }
+    c += oc;
+    q += oq;
+}
+
+__device__ __forceinline__ void keep_min2(long long kv, int e, long long& m1, long long& m2,
+                                          int& i1) {
+    if (kv < m1 || (kv == m1 && e < i1)) {
+        m2 = min(m2, m1);
+        m1 = kv;
+        i1 = e;
+    } else {
+        m2 = min(m2, kv);
+    }
+}
+
+__global__ void __launch_bounds__(kSelThreads)
 sure_select_kernel(const unsigned int* __restrict__ counts, const double* __restrict__ sums,
                    const double* __restrict__ sum_all, int batch, int K, long long N,
                    long long N_det, double delta, double* __restrict__ S,
-                   double* __restrict__ S_inf, double* __restrict__ T, unsigned int* done,
-                   hyde_hyres_info* info, int* rank_out, double* lam_out, const int* status) {
+                   double* __restrict__ S_inf, double* __restrict__ T, long long* sint,
+                   unsigned int* done, hyde_hyres_info* info, int* rank_out, double* lam_out,
+                   const int* status) {
     pdl_wait();
     pdl_trigger();
-    __shared__ double tail[kMaxRank];
-    __shared__ double wm1[8], wm2[8];
-    __shared__ int wi1[8];
+    __shared__ long long wc[kSelThreads / 32], wq[kSelThreads / 32];
+    __shared__ double tail[kMaxRank], sinf[kMaxRank];
+    __shared__ double lam2[kMaxLambda];
+    __shared__ long long wm1[kSelThreads / 32], wm2[kSelThreads / 32];
+    __shared__ int wi1[kSelThreads / 32];
     __shared__ int s_last;
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    constexpr int nw = kSelThreads / 32;
     const int i = blockIdx.x;
-    if (wid == 0) {
-        double ccarry = 0.0, scarry = 0.0;
-        for (int k0 = 0; k0 < K; k0 += 32) {
-            const int k = k0 + lane;
-            double c = k < K ? (double)counts[(long long)i * K + k] : 0.0;
-            double q = k < K ? sums[(long long)i * K + k] : 0.0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const double c2 = __shfl_up_sync(0xffffffffu, c, o);
-                const double q2 = __shfl_up_sync(0xffffffffu, q, o);
-                if (lane >= o) { c += c2; q += q2; }
-            }
-            const double cle = c + ccarry, sle = q + scarry;
-            if (k < K) {
-                const double lam = k * delta;
-                S[(long long)i * K + k] =
-                    (double)N - 2.0 * cle + sle + lam * lam * ((double)N_det - cle);
-            }
-            ccarry = __shfl_sync(0xffffffffu, cle, 31);
-            scarry = __shfl_sync(0xffffffffu, sle, 31);
+    long long* A = sint;                       // [batch][K]
+    long long* B = sint + (long long)batch * K;
+    {   // row i: integer scans over the bins (K <= kSelThreads)
+        long long c = 0, q = 0;
+        if (t < K) {
+            c = counts[(long long)i * K + t];
+            q = (long long)(sums[(long long)i * K + t] * 65536.0);   // exact
         }
-        if (lane == 0) S_inf[i] = sum_all[i] - (double)N;
+        block_scan2(c, q, wc, wq);
+        if (t < K) {
+            const long long a = (N - 2 * c) * 65536LL + q, bb = N_det - c;
+            A[(long long)i * K + t] = a;
+            B[(long long)i * K + t] = bb;
+            const double lam = t * delta;
+            S[(long long)i * K + t] = fma(lam * lam, (double)bb, (double)a * (1.0 / 65536.0));
+        }
+        if (t == 0) S_inf[i] = sum_all[i] - (double)N;
     }
     __threadfence();
     __syncthreads();
@@ -221,36 +266,50 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // every block's S row, copied once with coalesced loads (L2, not L1)
-    extern __shared__ double Ssh[];   // [batch][K]
-    for (int e = t; e < batch * K; e += blockDim.x) Ssh[e] = __ldcg(S + e);
-    if (t == 0) {   // tail[r] = sum_{i > r} S_inf[i]
+    // every block's rows of A and B (L2, not L1), prefixed over the components in place
+    extern __shared__ long long Psh[];   // PA [batch][K], then PB [batch][K]
+    long long* PA = Psh;
+    long long* PB = Psh + batch * K;
+    for (int e = t; e < batch * K; e += kSelThreads) {
+        PA[e] = __ldcg(A + e);
+        PB[e] = __ldcg(B + e);
+    }
+    if (t < batch) sinf[t] = __ldcg(S_inf + t);
+    for (int k = t; k < K; k += kSelThreads) {
+        const double lam = k * delta;
+        lam2[k] = lam * lam;
+    }
+    __syncthreads();
+    if (t < batch) {   // tail[r] = sum_{i > r} S_inf[i], added from i = batch - 1 down
         double acc = 0.0;
-        for (int r = batch - 1; r >= 0; --r) {
-            tail[r] = acc;
-            acc += __ldcg(S_inf + r);
+        for (int r = batch - 1; r > t; --r) acc += sinf[r];
+        tail[t] = acc;
+    }
+    for (int k = t; k < K; k += kSelThreads) {
+        long long pa = 0, pb = 0;
+        for (int r = 0; r < batch; ++r) {
+            pa += PA[r * K + k];
+            pb += PB[r * K + k];
+            PA[r * K + k] = pa;
+            PB[r * K + k] = pb;
         }
     }
     __syncthreads();
-    double m1 = DBL_MAX, m2 = DBL_MAX;
+    long long m1 = 0x7fffffffffffffffLL, m2 = 0x7fffffffffffffffLL;
     int i1 = 0x7fffffff;
-    for (int k = t; k < K; k += blockDim.x) {
-        double head = 0.0;
-        for (int r = 0; r < batch; ++r) {
-            head += Ssh[r * K + k];
-            const double v = head + tail[r];
-            if (T) T[(long long)r * K + k] = v;
-            const int e = r * K + k;
-            if (v < m1 || (v == m1 && e < i1)) { m2 = fmin(m2, m1); m1 = v; i1 = e; }
-            else m2 = fmin(m2, v);
-        }
+    for (int e = t; e < batch * K; e += kSelThreads) {
+        const int r = e / K, k = e - r * K;
+        const double v =
+            fma(lam2[k], (double)PB[e], (double)PA[e] * (1.0 / 65536.0)) + tail[r];
+        if (T) T[e] = v;
+        keep_min2(ord_key(v), e, m1, m2, i1);
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const double om1 = __shfl_xor_sync(0xffffffffu, m1, o);
-        const double om2 = __shfl_xor_sync(0xffffffffu, m2, o);
+        const long long om1 = __shfl_xor_sync(0xffffffffu, m1, o);
+        const long long om2 = __shfl_xor_sync(0xffffffffu, m2, o);
         const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
-        if (om1 < m1 || (om1 == m1 && oi1 < i1)) { m2 = fmin(m1, om2); m1 = om1; i1 = oi1; }
-        else m2 = fmin(m2, om1);
+        if (om1 < m1 || (om1 == m1 && oi1 < i1)) { m2 = min(m1, om2); m1 = om1; i1 = oi1; }
+        else m2 = min(m2, om1);
     }
     if (lane == 0) { wm1[wid] = m1; wm2[wid] = m2; wi1[wid] = i1; }
     __syncthreads();
@@ -258,13 +317,14 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
         m1 = wm1[0]; m2 = wm2[0]; i1 = wi1[0];
         for (int q = 1; q < nw; ++q) {
             if (wm1[q] < m1 || (wm1[q] == m1 && wi1[q] < i1)) {
-                m2 = fmin(m1, wm2[q]); m1 = wm1[q]; i1 = wi1[q];
+                m2 = min(m1, wm2[q]); m1 = wm1[q]; i1 = wi1[q];
             } else {
-                m2 = fmin(m2, wm1[q]);
+                m2 = min(m2, wm1[q]);
             }
         }
         const int tot = batch * K;
         const int r = i1 / K, k = i1 % K;
+        const double v1 = key_value(m1), v2 = key_value(m2);
         if (rank_out) *rank_out = r + 1;
         if (lam_out) *lam_out = k * delta;
         if (info) {
@@ -273,8 +333,8 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
             info->lambda_index = k;
             info->reserved = 0;
             info->lambda = k * delta;
-            info->sure_min = m1;
-            info->sure_gap = (tot > 1) ? (m2 - m1) / fmax(fabs(m1), 1e-300) : 0.0;
+            info->sure_min = v1;
+            info->sure_gap = (tot > 1) ? (v2 - v1) / fmax(fabs(v1), 1e-300) : 0.0;
         }
     }
 }
@@ -331,15 +391,14 @@ hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
         launch_pdl(sure_table_kernel, (batch + 7) / 8, 256, 0, s, b.counts, b.sums, b.sum_all, batch, K,
                                                            N, N_det, delta, S, S_inf);
     } else {
-        if (batch > kMaxRank || b.done == nullptr) return HYDE_ERR_SHAPE;
-        int threads = (K + 31) / 32 * 32;
-        if (threads > 256) threads = 256;
-        const size_t smem = (size_t)batch * K * sizeof(double);
+        if (batch > kMaxRank || K > kSelThreads || b.done == nullptr || b.sint == nullptr)
+            return HYDE_ERR_SHAPE;
+        const size_t smem = (size_t)2 * batch * K * sizeof(long long);
         if (ensure_smem_limit((const void*)sure_select_kernel, (int)smem) != cudaSuccess)
             return HYDE_ERR_CUDA;
-        launch_pdl(sure_select_kernel, batch, threads, smem, s, b.counts, b.sums, b.sum_all, batch, K, N,
-                                                     N_det, delta, S, S_inf, T, b.done, info,
-                                                     rank_out, lam_out, status);
+        launch_pdl(sure_select_kernel, batch, kSelThreads, smem, s, b.counts, b.sums,
+                   b.sum_all, batch, K, N, N_det, delta, S, S_inf, T, b.sint, b.done, info,
+                   rank_out, lam_out, status);
     }
     return cuda_status(cudaGetLastError());
 }
