@@ -30,6 +30,23 @@ def _scale(rows, L, seed):
     return (1.0 + 0.2 * rng.standard_normal((rows, L))).astype(np.float32)
 
 
+def _flip_allowance(o, L, s, rel=1e-5):
+    """The a.e. SURE gradient 2 lam* lam_il #{|c| > lam_il} is piecewise
+    constant in the coefficients: each detail coefficient that float
+    arithmetic may put on the other side of its threshold (the oracle's lies
+    within ``rel`` of it) can move entry (i, l) by 2 lam* lam_il."""
+    r = o["rank"]
+    C, lev = o["C"][:r], o["level_map"]
+    allow = np.zeros(s.shape, dtype=np.float64)
+    for i in range(r):
+        for l in range(1, L + 1):
+            lam = o["lam"] * float(s[i, l - 1])
+            c = np.abs(C[i][lev == l])
+            near = np.count_nonzero(np.abs(c - lam) <= rel * lam)
+            allow[i, l - 1] = near * 2.0 * o["lam"] * lam
+    return allow
+
+
 @pytest.mark.parametrize("H,W,p,m,L,r,seed", CASES)
 def test_scaled_forward_matches_oracle(hyde, H, W, p, m, L, r, seed):
     c = make_cube(H, W, p, m=m, seed=seed)
@@ -73,7 +90,9 @@ def test_sure_loss_and_gradient_match_oracle(hyde, H, W, p, m, L, r, seed):
     got = float(g.sure_value.item())
     rk = o["rank"]
     assert abs(got - val) <= 1e-5 * abs(val) + 8.0
-    assert np.linalg.norm(ds[:rk] - ref[:rk]) <= 1e-4 * np.linalg.norm(ref[:rk])
+    allow = _flip_allowance(o, L, s)
+    assert np.linalg.norm(ds[:rk] - ref[:rk]) <= (1e-4 * np.linalg.norm(ref[:rk]) +
+                                                  np.linalg.norm(allow[:rk]))
 
 
 def test_autograd_mse_against_finite_differences(hyde):
