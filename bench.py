@@ -44,13 +44,15 @@ FP32_SM_PEAK_TFLOPS = 128 * 2 * 2.070e9 / 1e12         # one SM, for single-bloc
 # (stage, precision). profiles/ holds the capture summaries; an entry is
 # removed when its kernel changes.
 NCU_TRAFFIC: dict = {
-    # gram_partial84 385.69 + 3.24 MB, gram_reduce 6.83 MB
-    ("gram", "fp32"): 395.76e6,
-    # gram_tc 385.73 + 3.27 MB, gram_tc_reduce 8.42 MB
-    ("gram", "bf16x3"): 397.42e6,
+    # gram_partial84 385.67 + 3.63 MB, gram_reduce 6.83 MB
+    ("gram", "fp32"): 396.13e6,
+    # gram_tc 385.77 + 3.68 MB, gram_tc_reduce 8.42 MB
+    ("gram", "bf16x3"): 397.87e6,
+    ("gram", "bf16x3_all"): 397.87e6,
     # eig_fast (one thread block) 0.25 MB
     ("eig", "fp32"): 0.25e6,
     ("eig", "bf16x3"): 0.25e6,
+    ("eig", "bf16x3_all"): 0.25e6,
 }
 
 
@@ -215,7 +217,8 @@ def run_gb300(args) -> None:
     voxels = p * n
     Yd = torch.from_numpy(cube["Y"]).to(dev)
     Xd = torch.empty_like(Yd)
-    prec = api.PREC_BF16X3 if args.precision == "bf16x3" else api.PREC_FP32
+    prec = {"fp32": api.PREC_FP32, "bf16x3": api.PREC_BF16X3,
+            "bf16x3_all": api.PREC_BF16X3_ALL}[args.precision]
     h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev, precision=prec)
     lib = _lib.load()
     launches_per_step = lib.hyde_hyres_kernel_launches(h.params)
@@ -283,7 +286,7 @@ def run_gb300(args) -> None:
     peaks = _measured_peaks()
     sbytes = _stage_bytes(r_star)
     dominant = max(stage_avg, key=stage_avg.get)
-    if dominant == "gram" and args.precision == "bf16x3":
+    if dominant == "gram" and args.precision != "fp32":
         flops = 3 * 2 * n * p * p   # three bf16 products per entry (hi hi, hi lo, lo hi)
         tc_peak = peaks["bf16_tflops"]
         achieved = flops / (stage_avg["gram"] / 1e3) / 1e12
@@ -366,6 +369,10 @@ def run_gb300(args) -> None:
         if args.precision == "bf16x3":
             cfg["precision"] = "bf16x3 (Gram on tcgen05, split-BF16 compensated)"
             cfg["workload"] += ", precision form"
+        elif args.precision == "bf16x3_all":
+            cfg["precision"] = ("bf16x3_all (Gram, projection and back-projection on tcgen05, "
+                                "split-BF16 compensated)")
+            cfg["workload"] += ", precision form (all contractions on the tensor cores)"
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -555,8 +562,9 @@ def main() -> None:
     ap.add_argument("--form", choices=("plain", "windows", "diff"), default="plain",
                     help="plain: the headline workload; windows / diff: secondary forms")
     ap.add_argument("--slots", type=int, default=64, help="window slots (--form windows)")
-    ap.add_argument("--precision", choices=("fp32", "bf16x3"), default="fp32",
-                    help="fp32: plain form (headline); bf16x3: Gram on the tensor cores")
+    ap.add_argument("--precision", choices=("fp32", "bf16x3", "bf16x3_all"), default="fp32",
+                    help="fp32: plain form (headline); bf16x3: Gram on the tensor cores; "
+                         "bf16x3_all: the projections there too")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3

@@ -59,11 +59,15 @@ typedef enum {
 typedef enum {
     HYDE_PREC_FP32 = 0,    /* plain FP32 SIMT arithmetic                      */
     HYDE_PREC_TF32X3 = 1,  /* reserved (rejected): split-TF32 contractions    */
-    HYDE_PREC_BF16X3 = 2   /* Gram matrix on the tensor cores: each float is
+    HYDE_PREC_BF16X3 = 2,  /* Gram matrix on the tensor cores: each float is
                               split into bf16 hi + lo and y_a y_b is taken as
                               hi hi + hi lo + lo hi (tcgen05.mma, FP32
                               accumulation in TMEM, double across SMs); the
                               other stages as in HYDE_PREC_FP32             */
+    HYDE_PREC_BF16X3_ALL = 3 /* as HYDE_PREC_BF16X3, and the projection and
+                              back-projection also as split-BF16 products on
+                              the tensor cores (both are HBM-bound at ~10
+                              flop/B, where the FP32 forms measure faster)   */
 } hyde_precision;
 
 /* Parameters of one HyRes run. */

@@ -17,7 +17,8 @@ from ._lib import HydeParams, HydeWsLayout, INFO_BYTES, INFO_FORMAT
 
 HYDE_OK = 0
 PREC_FP32 = 0
-PREC_BF16X3 = 2
+PREC_BF16X3 = 2       # Gram on the tensor cores (split-BF16)
+PREC_BF16X3_ALL = 3   # Gram, projection and back-projection on the tensor cores
 
 
 class HydeError(RuntimeError):

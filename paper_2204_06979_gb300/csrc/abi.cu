@@ -79,7 +79,8 @@ struct HyresLayout {
 hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, HyresLayout* L) {
     if (!pr) return HYDE_ERR_INVALID_ARG;
     if (pr->wavelet != 2) return HYDE_ERR_INVALID_ARG;
-    if (pr->precision != HYDE_PREC_FP32 && pr->precision != HYDE_PREC_BF16X3)
+    if (pr->precision != HYDE_PREC_FP32 && pr->precision != HYDE_PREC_BF16X3 &&
+        pr->precision != HYDE_PREC_BF16X3_ALL)
         return HYDE_ERR_INVALID_ARG;
     if (pr->reserved[0] || pr->reserved[1] || pr->reserved[2]) return HYDE_ERR_INVALID_ARG;
     if (p < 2 || p > kMaxBandsGram) return HYDE_ERR_SHAPE;
@@ -96,7 +97,7 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.N = (long long)Hp * Wp; l.n = n;
     hyde_status st = gram_plan(p, n, &l.gram);
     if (st != HYDE_OK) return st;
-    if (pr->precision == HYDE_PREC_BF16X3) {
+    if (pr->precision != HYDE_PREC_FP32) {   // split-BF16 Gram on the tensor cores
         size_t tcb = 0;
         st = gram_tc_partial_bytes(p, &tcb);
         if (st != HYDE_OK) return st;
@@ -369,7 +370,7 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
         cudaSuccess)
         return HYDE_ERR_CUDA;
     // 1. Gram matrix (float SIMT, or split-BF16 on the tensor cores)
-    if (params->precision == HYDE_PREC_BF16X3)
+    if (params->precision != HYDE_PREC_FP32)
         HYDE_TRY(launch_gram_tc(Y, p, L.n, at<float>(ws, L.partials), R, status, stream));
     else
         HYDE_TRY(launch_gram(Y, p, L.n, L.gram, at<float>(ws, L.partials), R, status, stream));
@@ -382,7 +383,8 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     HYDE_TRY(launch_weights(V, sigma, p, r, L.RM, P, Q, stream));
     HYDE_TRY(stage());
     // 5. projection into padded component images
-    const bool tc_proj = params->precision == HYDE_PREC_BF16X3 && project_tc_supported(p, r);
+    const bool tc_proj =
+        params->precision == HYDE_PREC_BF16X3_ALL && project_tc_supported(p, r);
     if (tc_proj)
         HYDE_TRY(launch_project_pad_tc(Y, p, H, W, P, r, L.RM, zp, L.Hp, L.Wp, status, stream));
     else

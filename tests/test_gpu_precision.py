@@ -1,9 +1,10 @@
-"""GPU parity of the precision form: the Gram matrix, the projection and the
-back-projection on the tensor cores with split-BF16 compensated products
-(hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM, double across SMs for the
-Gram matrix), everything else as in the FP32 path. Held to the precision
-form's bar: relative error <= 1e-3 and PSNR within 0.05 dB of the FP64
-oracle; the error of every stage is checked and reported."""
+"""GPU parity of the precision form: the Gram matrix on the tensor cores with
+split-BF16 compensated products (hi*hi + hi*lo + lo*hi, FP32 accumulation in
+TMEM, double across SMs), everything else as in the FP32 path; and of the
+all-tensor-core variant, which also takes the projection and back-projection
+as split-BF16 products. Held to the precision form's bar: relative error
+<= 1e-3 and PSNR within 0.05 dB of the FP64 oracle; the error of every stage
+is checked and reported."""
 
 import numpy as np
 import pytest
@@ -34,14 +35,16 @@ def test_tc_gram_matches_oracle(hyde, p, H, W):
     assert err < 3e-5, err
 
 
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x3_all"])
 @pytest.mark.parametrize("cfg", ["c0", "c1", "ragged"])
-def test_precision_form_against_oracle(hyde, cfg):
+def test_precision_form_against_oracle(hyde, cfg, mode):
     shapes = {"c0": (64, 64, 32, 4, 1, 2, 8), "c1": (349, 1905, 144, 12, 2, 5, 20),
               "ragged": (77, 131, 24, 3, 31, 3, 6)}
     H, W, p, m, seed, L, r = shapes[cfg]
     c = make_cube(H, W, p, m=m, seed=seed)
     o = O.hyres(c["Y"], L, r)
-    h = hyde.HyRes(p, H, W, L, r, precision=hyde.PREC_BF16X3)
+    prec = hyde.PREC_BF16X3 if mode == "bf16x3" else hyde.PREC_BF16X3_ALL
+    h = hyde.HyRes(p, H, W, L, r, precision=prec)
     X = h(_t(c["Y"])).cpu().numpy()
     info = h.result_info()
     mid = h.intermediates()
@@ -57,7 +60,7 @@ def test_precision_form_against_oracle(hyde, cfg):
     lead = min(info["rank"], o["rank"])
     coef = mid["coef"].cpu().numpy()[:lead]
     coef_err = max(O.rel_l2(coef[i], o["C"][i]) for i in range(lead))
-    print(f"{cfg}: gram {gram_err:.2e} sigma {sig_err:.2e} coef {coef_err:.2e} "
+    print(f"{cfg} {mode}: gram {gram_err:.2e} sigma {sig_err:.2e} coef {coef_err:.2e} "
           f"output {out_err:.2e} dPSNR {dpsnr:.4f} dB rank {info['rank']}/{o['rank']} "
           f"k {info['lambda_index']}/{o['k']}")
     assert gram_err < 3e-5
