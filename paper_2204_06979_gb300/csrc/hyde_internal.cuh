@@ -66,6 +66,24 @@ __device__ __forceinline__ void fma_f32x2(float& c0, float& c1, float a0, float 
         : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
+// double -> float from the IEEE-754 bit fields on the integer pipes (FP64
+// arithmetic and conversions run at a small fraction of the FP32 rate on
+// this part): sign, exponent rebased from 1023 to 127, the top 23 of the 52
+// mantissa bits rounded to nearest (ties away from zero; a carry into the
+// exponent is the correct result). Values below the float normal range give
+// a signed zero, values above it (and inf, NaN) give inf.
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    unsigned bits = ((unsigned)e << 23) + m + ((lo >> 28) & 1u);
+    if (e <= 0) bits = 0u;
+    if (e >= 255 || bits >= 0x7f800000u) bits = 0x7f800000u;
+    return __int_as_float((int)(sign | bits));
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

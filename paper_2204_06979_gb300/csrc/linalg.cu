@@ -547,27 +547,32 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     float* Dm = q;   q += p * r;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 
+    // Whitening weights 1/sigma and the largest whitened diagonal entry in
+    // float over all threads, the matrix converted on the integer pipes: no
+    // FP64 arithmetic on this one SM.
     __shared__ float s_scale;
+    __shared__ int s_mx;
     float* iw = vf;
-    if (t < 32) {
-        double mx = 0.0;
-        for (int i = lane; i < p; i += 32) {
-            double a = Ain[(long long)i * p + i];
-            double w = wsig ? 1.0 / wsig[i] : 1.0;
-            iw[i] = (float)w;
-            a *= w * w;
-            if (!isfinite(a)) set_status(status, HYDE_ERR_NUMERIC);
-            mx = fmax(mx, fabs(a));
-        }
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) s_scale = mx > 0.0 ? (float)(1.0 / mx) : 1.0f;
+    if (t == 0) s_mx = 0;
+    __syncthreads();
+    for (int i = t; i < p; i += blockDim.x) {
+        const float w = wsig ? 1.0f / d2f_bits(wsig[i]) : 1.0f;
+        iw[i] = w;
+        const float a = d2f_bits(Ain[(long long)i * p + i]) * w * w;
+        if (!isfinite(a)) set_status(status, HYDE_ERR_NUMERIC);
+        atomicMax(&s_mx, __float_as_int(fabsf(a)));   // non-negative floats order as ints
+    }
+    __syncthreads();
+    if (t == 0) {
+        const float mx = __int_as_float(s_mx);
+        s_scale = mx > 0.f && isfinite(mx) ? 1.0f / mx : 1.0f;
     }
     __syncthreads();
     const float scale = s_scale;
     for (int i = wid; i < p; i += 32) {
         const float si = iw[i] * scale;
         for (int j = lane; j < p; j += 32)
-            A[i * lda + j] = (float)Ain[(long long)i * p + j] * si * iw[j];
+            A[i * lda + j] = d2f_bits(Ain[(long long)i * p + j]) * si * iw[j];
     }
     __syncthreads();
 
@@ -713,10 +718,11 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
     __syncthreads();
     // reflector k as an explicit vector in column k: 0 above row k+1, 1 at
     // k+1, x * scale below (the back-transformation then reads it directly)
-    for (int e = t; e < p * (p - 2 > 0 ? p - 2 : 0); e += blockDim.x) {
-        const int i = e / (p - 2), k = e - i * (p - 2);
-        float* a = A + i * lda + k;
-        *a = i <= k ? 0.f : (i == k + 1 ? 1.0f : *a * scv[k]);
+    for (int i = wid; i < p; i += 32) {
+        for (int k = lane; k < p - 2; k += 32) {
+            float* a = A + i * lda + k;
+            *a = i <= k ? 0.f : (i == k + 1 ? 1.0f : *a * scv[k]);
+        }
     }
     __syncthreads();
     // cpair[k] = v_{k-1} . v_k (k >= 1) for the paired back-transformation;
@@ -822,7 +828,7 @@ eig_fast_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig,
             const int i = lane + 32 * b;
             if (i < p) V[(long long)i * r + wid] = (double)(sg * x[b]);
         }
-        if (lane == 0) evals[wid] = (double)lamv[wid] / (double)scale;
+        if (lane == 0) evals[wid] = (double)(lamv[wid] / scale);
     }
 }
 
