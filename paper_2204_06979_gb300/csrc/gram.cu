@@ -19,6 +19,7 @@ namespace hyde {
 namespace {
 
 constexpr int KC = 32;        // pixels per chunk
+constexpr int KC84 = 64;      // pixels per chunk of the 8 x 4 kernel (one barrier each)
 constexpr int STAGES = 3;     // cp.async pipeline depth
 constexpr int kGramMaxThreads = 544;
 
@@ -170,23 +171,31 @@ gram_partial84_kernel(const float* __restrict__ Y, int p, long long n, int PT, i
     const int p8 = PT * 8;
     const int t = threadIdx.x;
     const int T = blockDim.x;
-    for (int i = t; i < (p8 - p) * 8 * STAGES; i += T) {
-        const int st = i / ((p8 - p) * 8), o = i % ((p8 - p) * 8);
-        sm4[st * p8 * 8 + p * 8 + o] = make_float4(0.f, 0.f, 0.f, 0.f);
+    constexpr int RQ = KC84 / 4;   // float4 per stage row
+    for (int i = t; i < (p8 - p) * RQ * STAGES; i += T) {
+        const int st = i / ((p8 - p) * RQ), o = i % ((p8 - p) * RQ);
+        sm4[st * p8 * RQ + p * RQ + o] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const long long nchunks = (n + KC - 1) / KC;
+    const long long nchunks = (n + KC84 - 1) / KC84;
     const long long c0 = (long long)blockIdx.x * nchunks / gridDim.x;
     const long long c1 = (long long)(blockIdx.x + 1) * nchunks / gridDim.x;
     const int lane = t & 31, wrp = t >> 5, nw = T >> 5;
     const int kq = lane >> 2, kr = lane & 3;
     const long long bstride = (long long)nw * n;
+    // a warp copies 32 + 32 consecutive pixels of each of its bands; float4
+    // column kq of a row is stored at kq ^ ((b >> 2) & 7) (the XOR keeps each
+    // half of the row in place)
     auto issue = [&](long long c, int st) {
-        float* d = reinterpret_cast<float*>(sm4 + st * p8 * 8);
-        const long long pix = c * KC + lane;
-        const bool ok = pix < n;
-        const float* src = Y + (long long)wrp * n + (ok ? pix : 0);
-        for (int b = wrp; b < p; b += nw, src += bstride)
-            cp_async4(d + b * 32 + ((kq ^ ((b >> 2) & 7)) << 2) + kr, src, ok);
+        float* d = reinterpret_cast<float*>(sm4 + st * p8 * RQ);
+        const long long pix = c * KC84 + lane;
+        const bool ok0 = pix < n, ok1 = pix + 32 < n;
+        const float* src0 = Y + (long long)wrp * n + (ok0 ? pix : 0);
+        const float* src1 = Y + (long long)wrp * n + (ok1 ? pix + 32 : 0);
+        for (int b = wrp; b < p; b += nw, src0 += bstride, src1 += bstride) {
+            float* row = d + b * KC84 + (((kq ^ ((b >> 2) & 7))) << 2) + kr;
+            cp_async4(row, src0, ok0);
+            cp_async4(row + 32, src1, ok1);
+        }
     };
     const bool active = t < ntiles;
     int ti = 0, tj = 0;
@@ -208,17 +217,17 @@ gram_partial84_kernel(const float* __restrict__ Y, int p, long long n, int PT, i
         if (nxt < c1) issue(nxt, (int)(nxt - c0) % STAGES);
         cp_async_commit();
         if (active) {
-            const float4* B = sm4 + ((int)(c - c0) % STAGES) * p8 * 8;
-            const float4* Ba = B + 64 * ti;   // rows 8ti .. 8ti+7
-            const float4* Bb = B + 32 * tj;   // rows 4tj .. 4tj+3
+            const float4* B = sm4 + ((int)(c - c0) % STAGES) * p8 * RQ;
+            const float4* Ba = B + 8 * RQ * ti;   // rows 8ti .. 8ti+7
+            const float4* Bb = B + 4 * RQ * tj;   // rows 4tj .. 4tj+3
             const int xa0 = (2 * ti) & 7, xa1 = (2 * ti + 1) & 7, xb = tj & 7;
 #pragma unroll 2
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < RQ; ++q) {
                 float4 a[8], b[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) a[i] = Ba[8 * i + (q ^ (i < 4 ? xa0 : xa1))];
+                for (int i = 0; i < 8; ++i) a[i] = Ba[RQ * i + (q ^ (i < 4 ? xa0 : xa1))];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = Bb[8 * j + (q ^ xb)];
+                for (int j = 0; j < 4; ++j) b[j] = Bb[RQ * j + (q ^ xb)];
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -307,7 +316,7 @@ static hyde_status plan_for84(GramPlan& g, long long n) {
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     int sms = device_sm_count();
     if (sms <= 0) return HYDE_ERR_CUDA;
-    long long nchunks = (n + KC - 1) / KC;
+    long long nchunks = (n + KC84 - 1) / KC84;
     long long blocks = (long long)sms * per_sm;
     if (blocks > nchunks) blocks = nchunks;
     g.blocks = (int)blocks;
@@ -323,6 +332,7 @@ hyde_status gram_plan(int p, long long n, GramPlan* plan) {
     if (g.PT * (g.PT + 1) <= 384) {
         // 8 x 4 tiles with paired FMAs, one block of up to 384 threads per SM
         g.mode = 1;
+        g.smem = (size_t)STAGES * g.PT * 8 * KC84 * sizeof(float);
         g.ntiles = g.PT * (g.PT + 1);
         g.threads = (g.ntiles + 31) / 32 * 32;
         st = plan_for84<384>(g, n);
