@@ -19,7 +19,9 @@ namespace hyde {
 namespace {
 
 constexpr int KC = 32;        // pixels per chunk
-constexpr int KC84 = 64;      // pixels per chunk of the 8 x 4 kernel (one barrier each)
+constexpr int KC84 = 64;      // pixels per chunk of the 8 x 4 kernel (one barrier each);
+                              // the copy below fills it as two 32-pixel halves
+static_assert(KC84 == 64, "gram_partial84_kernel copies a chunk as two 32-pixel halves");
 constexpr int STAGES = 3;     // cp.async pipeline depth
 constexpr int kGramMaxThreads = 544;
 
