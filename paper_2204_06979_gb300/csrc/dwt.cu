@@ -659,16 +659,16 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
         else { lp = ll_buf(scratch, batch, Hp, Wp, lev, &lbs); lld = w / 2; }
         dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
         if (hv < h || wv < w) {
-            launch_pdl(dwt_level_kernel<true>, grid, kThreads, 0, s, sp, sbs, sld, hv, wv, h, w, coef,
-                                                             cbs, Wp, lp, lbs, lld);
+            launch_pdl(dwt_level_kernel<true>, grid, kThreads, 0, s, sp, sbs, sld, hv, wv, h, w,
+                       coef, cbs, Wp, lp, lbs, lld);
         } else {
             // padded source: the pipelined kernel, a few tiles per block
             const int ntiles = ((w / 2 + FTW - 1) / FTW) * ((h / 2 + FTH - 1) / FTH);
             int G = (pipe_per_sm * sms + batch - 1) / batch;
             if (G > ntiles) G = ntiles;
             if (G < 1) G = 1;
-            launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s,
-                sp, sbs, sld, h, w, coef, cbs, Wp, lp, lbs, lld);
+            launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s, sp, sbs,
+                       sld, h, w, coef, cbs, Wp, lp, lbs, lld);
         }
     }
     if (lo <= levels) {
@@ -728,16 +728,17 @@ hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int W
             // every output row inside the crop; float4 stores when rows are 16-byte aligned
             const bool vout = (old & 3) == 0 && (obs & 3) == 0 && ho == h && wo == w &&
                               (reinterpret_cast<uintptr_t>(op) & 15) == 0;
-            const long long units = (long long)((wh + 127) / 128) * ((hh + kSynRows - 1) / kSynRows);
-            launch_pdl(idwt_level_vec_kernel, dim3((unsigned)((units + kSynWarps - 1) / kSynWarps), batch),
-                       kSynThreads, 0, s, lp, lbs, lld, coef, cbs, Wp, h, w, lam, scale, scale_ld,
-                       lev, rank, op, obs, old, ho, wo, vout ? 1 : 0);
+            const long long units =
+                (long long)((wh + 127) / 128) * ((hh + kSynRows - 1) / kSynRows);
+            const dim3 vgrid((unsigned)((units + kSynWarps - 1) / kSynWarps), batch);
+            launch_pdl(idwt_level_vec_kernel, vgrid, kSynThreads, 0, s, lp, lbs, lld, coef, cbs,
+                       Wp, h, w, lam, scale, scale_ld, lev, rank, op, obs, old, ho, wo,
+                       vout ? 1 : 0);
             continue;
         }
         dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
-        launch_pdl(idwt_level_kernel, grid, kThreads, 0, s, lp, lbs, lld, coef, cbs, Wp, h, w, lam,
-                                                    scale, scale_ld, lev, rank, op, obs, old,
-                                                    ho, wo);
+        launch_pdl(idwt_level_kernel, grid, kThreads, 0, s, lp, lbs, lld, coef, cbs, Wp, h, w,
+                   lam, scale, scale_ld, lev, rank, op, obs, old, ho, wo);
     }
     return cuda_status(cudaGetLastError());
 }

@@ -114,7 +114,7 @@ hyde_status launch_scale_grad(const float* C, const float* dC, int r_max, int Hp
     per = (Hp + rows - 1) / rows;
     dim3 grid(per, r_max);
     launch_pdl(scale_grad_kernel, grid, kThreads, 0, s, C, dC, Hp, Wp, levels, rank, lam, scale,
-                                                scale_ld, mode, rows, acc, sure_acc);
+               scale_ld, mode, rows, acc, sure_acc);
     return cuda_status(cudaGetLastError());
 }
 
@@ -122,8 +122,8 @@ hyde_status launch_scale_grad_finish(const double* acc, int r_max, int levels, c
                                      const double* lam, float* dscale, int dscale_ld, int mode,
                                      long long N, const double* sure_acc, double* sure_value,
                                      cudaStream_t s) {
-    launch_pdl(scale_grad_finish_kernel, 1, 256, 0, s, acc, r_max, levels, rank, lam, dscale, dscale_ld,
-                                               mode, N, sure_acc, sure_value);
+    launch_pdl(scale_grad_finish_kernel, 1, 256, 0, s, acc, r_max, levels, rank, lam, dscale,
+               dscale_ld, mode, N, sure_acc, sure_value);
     return cuda_status(cudaGetLastError());
 }
 

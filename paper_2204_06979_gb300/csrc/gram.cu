@@ -358,23 +358,23 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
     long long nchunks = (n + KC - 1) / KC;
     long long per = (nchunks + g.blocks - 1) / g.blocks;
     if (g.mode == 1)
-        launch_pdl(gram_partial84_kernel<384>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT, g.ntiles,
-                                                                       partials);
+        launch_pdl(gram_partial84_kernel<384>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT,
+                   g.ntiles, partials);
     else if (g.threads <= 256)
-        launch_pdl(gram_partial_kernel<256>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT, g.ntiles,
-                                                                     per, partials);
+        launch_pdl(gram_partial_kernel<256>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT,
+                   g.ntiles, per, partials);
     else if (g.threads <= 384)
-        launch_pdl(gram_partial_kernel<384>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT, g.ntiles,
-                                                                     per, partials);
+        launch_pdl(gram_partial_kernel<384>, g.blocks, g.threads, g.smem, s, Y, p, n, g.PT,
+                   g.ntiles, per, partials);
     else
-        launch_pdl(gram_partial_kernel<kGramMaxThreads>, g.blocks, g.threads, g.smem, s,
-            Y, p, n, g.PT, g.ntiles, per, partials);
+        launch_pdl(gram_partial_kernel<kGramMaxThreads>, g.blocks, g.threads, g.smem, s, Y, p, n,
+                   g.PT, g.ntiles, per, partials);
     long long tot = (long long)g.ntiles * (g.mode == 0 ? 64 : 32);
     if (cudaMemsetAsync(R, 0, (size_t)p * p * sizeof(double), s) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 rgrid((unsigned)((tot + 255) / 256), (g.blocks + kReduceSeg - 1) / kReduceSeg);
-    launch_pdl(gram_reduce_kernel, rgrid, 256, 0, s, partials, g.blocks, p, g.PT, g.ntiles, g.mode, R,
-                                             status);
+    launch_pdl(gram_reduce_kernel, rgrid, 256, 0, s, partials, g.blocks, p, g.PT, g.ntiles,
+               g.mode, R, status);
     return cuda_status(cudaGetLastError());
 }
 

@@ -326,8 +326,8 @@ hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, 
     case G:                                                                                   \
         if (ensure_smem_limit((const void*)gram_tc_kernel<8 * G>, (int)P.smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                             \
-        launch_pdl(gram_tc_kernel<8 * G>, blocks, kTcThreadsWs, P.smem, s, Y, p, n, P, per, partials, \
-                                                                    status);                  \
+        launch_pdl(gram_tc_kernel<8 * G>, blocks, kTcThreadsWs, P.smem, s, Y, p, n, P, per,   \
+                   partials, status);                                                         \
         break;
         HYDE_TC(1) HYDE_TC(2) HYDE_TC(3) HYDE_TC(4)
 #undef HYDE_TC

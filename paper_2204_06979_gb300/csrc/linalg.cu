@@ -872,7 +872,8 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
     if (T16 <= 10) {
         switch (T16) {
 #define HYDE_GJ16(TV) \
-    case TV: launch_pdl(noise_gj_reg_kernel<TV, 16>, 1, 256, 0, s, R, p, Ainv, Sd, status); break;
+    case TV: launch_pdl(noise_gj_reg_kernel<TV, 16>, 1, 256, 0, s, R, p, Ainv, Sd, status); \
+        break;
             HYDE_GJ16(1) HYDE_GJ16(2) HYDE_GJ16(3) HYDE_GJ16(4) HYDE_GJ16(5)
             HYDE_GJ16(6) HYDE_GJ16(7) HYDE_GJ16(8) HYDE_GJ16(9) HYDE_GJ16(10)
 #undef HYDE_GJ16
@@ -880,7 +881,9 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
         }
     } else if (T32 <= kMaxRegT) {
         switch (T32) {
-            case 6: launch_pdl(noise_gj_reg_kernel<6, 32>, 1, kLA, 0, s, R, p, Ainv, Sd, status); break;
+            case 6:
+                launch_pdl(noise_gj_reg_kernel<6, 32>, 1, kLA, 0, s, R, p, Ainv, Sd, status);
+                break;
             default: return HYDE_ERR_SHAPE;   // p in (160, 192] has T32 = 6
         }
     } else {
@@ -889,7 +892,8 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
             return HYDE_ERR_SHAPE;
         launch_pdl(noise_gj_smem_kernel, 1, kLA, smem, s, R, p, Ainv, Sd, status);
     }
-    launch_pdl(noise_refine_kernel, p, 256, p * sizeof(double), s, R, Ainv, Sd, p, n, sigma, status);
+    launch_pdl(noise_refine_kernel, p, 256, p * sizeof(double), s, R, Ainv, Sd, p, n, sigma,
+               status);
     return cuda_status(cudaGetLastError());
 }
 
@@ -907,7 +911,8 @@ hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, do
         if (ensure_smem_limit((const void*)eig_fast_kernel<NBV, kEigWarps>, (int)smem) !=      \
             cudaSuccess)    \
             return HYDE_ERR_SHAPE;                                                             \
-        launch_pdl(eig_fast_kernel<NBV, kEigWarps>, 1, kLA, smem, s, A, wsig, p, r, evals, V, status);           \
+        launch_pdl(eig_fast_kernel<NBV, kEigWarps>, 1, kLA, smem, s, A, wsig, p, r, evals, V, \
+                   status);                                                                   \
         break;
         HYDE_EIG(1) HYDE_EIG(2) HYDE_EIG(3) HYDE_EIG(4)
         HYDE_EIG(5) HYDE_EIG(6) HYDE_EIG(7) HYDE_EIG(8)

@@ -210,10 +210,9 @@ hyde_status launch_project_pad(const float* Y, int p, int H, int W, const float*
     case RMV:                                                                                  \
         if (ensure_smem_limit((const void*)project_pad_kernel<RMV>, (int)smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                              \
-        launch_pdl(project_pad_kernel<RMV>, resident_grid((const void*)project_pad_kernel<RMV>,          \
-                                                kThreads, smem, tiles),                        \
-                                  kThreads, smem, s, Y, p, H, W, P, r, Zp, Hp, Wp,           \
-                                                       zero_pad ? 1 : 0);                      \
+        launch_pdl(project_pad_kernel<RMV>,                                                    \
+                   resident_grid((const void*)project_pad_kernel<RMV>, kThreads, smem, tiles), \
+                   kThreads, smem, s, Y, p, H, W, P, r, Zp, Hp, Wp, zero_pad ? 1 : 0);          \
         break;
         HYDE_PROJ(4) HYDE_PROJ(8) HYDE_PROJ(12) HYDE_PROJ(16)
         HYDE_PROJ(20) HYDE_PROJ(24) HYDE_PROJ(28) HYDE_PROJ(32)
@@ -234,9 +233,9 @@ hyde_status launch_backproject(const float* Zh, long long n, const float* Q, int
     case RMV:                                                                                  \
         if (ensure_smem_limit((const void*)backproject_kernel<RMV>, (int)smem) != cudaSuccess) \
             return HYDE_ERR_CUDA;                                                              \
-        launch_pdl(backproject_kernel<RMV>, resident_grid((const void*)backproject_kernel<RMV>,          \
-                                                kBpThreads, smem, tiles),                      \
-                                  kBpThreads, smem, s, Zh, n, Q, p, rank, X);                \
+        launch_pdl(backproject_kernel<RMV>,                                                    \
+                   resident_grid((const void*)backproject_kernel<RMV>, kBpThreads, smem, tiles), \
+                   kBpThreads, smem, s, Zh, n, Q, p, rank, X);                                  \
         break;
         HYDE_BACK(4) HYDE_BACK(8) HYDE_BACK(12) HYDE_BACK(16)
         HYDE_BACK(20) HYDE_BACK(24) HYDE_BACK(28) HYDE_BACK(32)

@@ -581,8 +581,8 @@ hyde_status launch_project_pad_tc(const float* Y, int p, int H, int W, const flo
     long long grid = device_sm_count();
     if (grid <= 0) return HYDE_ERR_CUDA;
     if (grid > tiles) grid = tiles;
-    launch_pdl(project_tc_kernel, (int)grid, kPjThreads, smem, s, Y, p, H, W, P, r, ldw, Zp, Hp, Wp, 0,
-                                                          status);
+    launch_pdl(project_tc_kernel, (int)grid, kPjThreads, smem, s, Y, p, H, W, P, r, ldw, Zp, Hp,
+               Wp, 0, status);
     return cuda_status(cudaGetLastError());
 }
 
@@ -597,7 +597,8 @@ hyde_status launch_backproject_tc(const float* Zh, long long n, const float* Q, 
     long long grid = device_sm_count();
     if (grid <= 0) return HYDE_ERR_CUDA;
     if (grid > tiles) grid = tiles;
-    launch_pdl(backproject_tc_kernel, (int)grid, kBpThreads, smem, s, Zh, n, Q, p, ldw, rank, X, status);
+    launch_pdl(backproject_tc_kernel, (int)grid, kBpThreads, smem, s, Zh, n, Q, p, ldw, rank, X,
+               status);
     return cuda_status(cudaGetLastError());
 }
 

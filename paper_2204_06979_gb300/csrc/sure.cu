@@ -377,9 +377,9 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int l
     if (ensure_smem_limit((const void*)sure_hist_kernel, (int)smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 grid(per_comp, batch);
-    launch_pdl(sure_hist_kernel, grid, kHistThreads, smem, s,
-        coef, Hp, Wp, Hp >> levels, Wp >> levels, K, inv_delta, (float)std::ldexp(1.0, sh),
-        std::ldexp(1.0, -sh), (int)rows, b.counts, b.sums, b.sum_all);
+    launch_pdl(sure_hist_kernel, grid, kHistThreads, smem, s, coef, Hp, Wp, Hp >> levels,
+               Wp >> levels, K, inv_delta, (float)std::ldexp(1.0, sh), std::ldexp(1.0, -sh),
+               (int)rows, b.counts, b.sums, b.sum_all);
     return cuda_status(cudaGetLastError());
 }
 
@@ -388,8 +388,8 @@ hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
                                double* T, hyde_hyres_info* info, int* rank_out,
                                double* lam_out, const int* status, cudaStream_t s) {
     if (T == nullptr) {   // the tables only
-        launch_pdl(sure_table_kernel, (batch + 7) / 8, 256, 0, s, b.counts, b.sums, b.sum_all, batch, K,
-                                                           N, N_det, delta, S, S_inf);
+        launch_pdl(sure_table_kernel, (batch + 7) / 8, 256, 0, s, b.counts, b.sums, b.sum_all,
+                   batch, K, N, N_det, delta, S, S_inf);
     } else {
         if (batch > kMaxRank || K > kSelThreads || b.done == nullptr || b.sint == nullptr)
             return HYDE_ERR_SHAPE;

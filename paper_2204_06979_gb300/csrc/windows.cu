@@ -67,8 +67,8 @@ hyde_status launch_scatter_core(const float* cube, int h, int w, int y0, int x0,
     const int sms = device_sm_count();
     long long blocks = (tot + 255) / 256;
     if (blocks > 8LL * sms) blocks = 8LL * sms;
-    launch_pdl(scatter_core_kernel, (unsigned)blocks, 256, 0, s, cube, h, w, y0, x0, cy0, cx0, ch, cw, p,
-                                                         H, W, X);
+    launch_pdl(scatter_core_kernel, (unsigned)blocks, 256, 0, s, cube, h, w, y0, x0, cy0, cx0, ch,
+               cw, p, H, W, X);
     return cuda_status(cudaGetLastError());
 }
 

@@ -30,6 +30,7 @@ def _t(a):
     (2, 349, 1905, 5),   # C1 component size
     (1, 5, 7, 2),        # tiny: tiles larger than the image, wrap inside a tile
     (4, 33, 65, 1),      # single level, odd sides
+    (2, 128, 256, 4),    # levels 2-4 fused in one block per image (both shared buffers)
 ])
 def test_dwt2_matches_oracle(hyde, B, H, W, L):
     rng = np.random.default_rng(B * 1000 + H + W)
@@ -43,7 +44,8 @@ def test_dwt2_matches_oracle(hyde, B, H, W, L):
     assert np.max(np.abs(got - ref)) < 1e-5 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("B,H,W,L", [(2, 64, 64, 2), (3, 100, 150, 3), (1, 349, 1905, 5)])
+@pytest.mark.parametrize("B,H,W,L", [(2, 64, 64, 2), (3, 100, 150, 3), (1, 349, 1905, 5),
+                                     (2, 128, 256, 4), (1, 120, 250, 4)])
 def test_idwt2_matches_oracle_and_inverts(hyde, B, H, W, L):
     rng = np.random.default_rng(7 + H)
     Hp, Wp = O.padded_shape(H, W, L)
