@@ -231,6 +231,31 @@ hyde_status hyde_hyres_denoise(const float* Y, float* X, int p, int H, int W,
                                hyde_hyres_info* info, void* ws,
                                size_t ws_bytes, cudaStream_t stream);
 
+/* A stream of cubes in host memory: denoises count cubes Y_host[s] ->
+ * X_host[s] (float[p][H][W] each, page-locked for the copies to overlap),
+ * copying cube s+1 in and cube s-1 out while cube s is denoised. The copies
+ * run on h2d and d2h (one cudaMemcpyAsync per cube and direction), the
+ * denoise of every cube on `stream`, in order, with the one workspace ws
+ * (as for hyde_hyres_denoise). dev: four device cubes owned by the caller,
+ * input buffers dev[0], dev[1] and output buffers dev[2], dev[3], used in
+ * turn; info_dev: two device info records; info_host: count page-locked
+ * records that receive each cube's hyde_hyres_info, or NULL. events: seven
+ * caller-created events (copy-in done, denoise done, copy-out done for each
+ * buffer pair, and one fork event); a buffer is refilled only after the
+ * work that read it has completed. The call forks the copy streams from
+ * `stream` and joins them back to it: work queued on `stream` before the
+ * call precedes all of it, and everything the call enqueues, copies
+ * included, precedes later work on `stream`. Asynchronous; X_host[s] may
+ * repeat when the caller does not read it in between. Returns the status
+ * codes of hyde_hyres_denoise, or HYDE_ERR_CUDA if a copy or an event call
+ * fails. (Sec. 2.1's HyRes per cube; the overlap is this library's.) */
+hyde_status hyde_hyres_denoise_host(const float* const* Y_host, float* const* X_host,
+                                    hyde_hyres_info* info_host, int count, int p, int H,
+                                    int W, const hyde_hyres_params* params,
+                                    float* const* dev, hyde_hyres_info* info_dev, void* ws,
+                                    size_t ws_bytes, cudaStream_t stream, cudaStream_t h2d,
+                                    cudaStream_t d2h, cudaEvent_t* events);
+
 /* Stage boundaries of hyde_hyres_denoise_timed, in enqueue order. */
 #define HYDE_N_STAGES 8   /* gram, noise, eig+weights, projection, DWT,
                              SURE+selection, threshold+IDWT, back-projection */

@@ -213,6 +213,43 @@ class HyRes:
     def result_info(self) -> dict:
         return parse_info(self.info)
 
+    def denoise_host(self, Ys, Xs, infos: torch.Tensor | None = None) -> None:
+        """Denoises the host cubes ``Ys[s]`` into ``Xs[s]`` (contiguous float32
+        CPU tensors of this shape, page-locked for the copies to overlap) with
+        ``hyde_hyres_denoise_host``: cube s+1 is copied in and cube s-1 out
+        while cube s is denoised. Enqueued on the current stream (synchronise
+        before reading ``Xs``). ``infos``: optional page-locked uint8 tensor of
+        ``len(Ys) * INFO_BYTES`` bytes for the per-cube records."""
+        n = len(Ys)
+        if n < 1 or len(Xs) != n:
+            raise ValueError("Ys and Xs must be equally long and non-empty")
+        for t in list(Ys) + list(Xs):
+            if (t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous()
+                    or tuple(t.shape) != self.shape):
+                raise ValueError(f"host cubes must be contiguous float32 CPU tensors of shape "
+                                 f"{self.shape}")
+        if infos is not None and (infos.device.type != "cpu" or infos.numel() < n * INFO_BYTES):
+            raise ValueError("infos must be a CPU uint8 tensor of len(Ys) * INFO_BYTES bytes")
+        if not hasattr(self, "_host_dev"):
+            self._host_bufs = [torch.empty(self.shape, dtype=torch.float32, device=self.device)
+                               for _ in range(4)]
+            self._host_info = torch.zeros(2 * INFO_BYTES, dtype=torch.uint8, device=self.device)
+            self._host_streams = [torch.cuda.Stream(device=self.device) for _ in range(2)]
+            self._host_events = [torch.cuda.Event() for _ in range(7)]
+            for e in self._host_events:   # torch creates the CUDA event on first record
+                e.record(torch.cuda.current_stream(self.device))
+            torch.cuda.synchronize(self.device)
+            self._host_dev = (ctypes.c_void_p * 4)(*[t.data_ptr() for t in self._host_bufs])
+            self._host_ev = (ctypes.c_void_p * 7)(*[e.cuda_event for e in self._host_events])
+        Yp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Ys])
+        Xp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Xs])
+        p, H, W = self.shape
+        _check(self.lib.hyde_hyres_denoise_host(
+            Yp, Xp, _ptr(infos), n, p, H, W, ctypes.byref(self.params), self._host_dev,
+            _ptr(self._host_info), _ptr(self.ws), self.ws.numel(), _stream(),
+            self._host_streams[0].cuda_stream, self._host_streams[1].cuda_stream,
+            self._host_ev), "hyde_hyres_denoise_host")
+
     def _view(self, off: int, count: int, dtype: torch.dtype) -> torch.Tensor:
         es = torch.tensor([], dtype=dtype).element_size()
         return self.ws[off: off + count * es].view(dtype)

@@ -422,6 +422,61 @@ hyde_status hyde_hyres_denoise(const float* Y, float* X, int p, int H, int W,
     return hyres_enqueue(Y, X, p, H, W, params, info, ws, ws_bytes, stream, nullptr);
 }
 
+hyde_status hyde_hyres_denoise_host(const float* const* Y_host, float* const* X_host,
+                                    hyde_hyres_info* info_host, int count, int p, int H,
+                                    int W, const hyde_hyres_params* params,
+                                    float* const* dev, hyde_hyres_info* info_dev, void* ws,
+                                    size_t ws_bytes, cudaStream_t stream, cudaStream_t h2d,
+                                    cudaStream_t d2h, cudaEvent_t* events) {
+    if (!Y_host || !X_host || !dev || !info_dev || !events || count < 1 || !params)
+        return HYDE_ERR_INVALID_ARG;
+    for (int q = 0; q < 4; ++q)
+        if (!dev[q]) return HYDE_ERR_INVALID_ARG;
+    for (int q = 0; q < 7; ++q)
+        if (!events[q]) return HYDE_ERR_INVALID_ARG;
+    for (int s = 0; s < count; ++s)
+        if (!Y_host[s] || !X_host[s]) return HYDE_ERR_INVALID_ARG;
+    HyresLayout L;
+    hyde_status st = hyres_layout(p, H, W, params, &L);
+    if (st != HYDE_OK) return st;
+    const size_t bytes = (size_t)p * H * W * sizeof(float);
+    cudaEvent_t* in_done = events;          // per input buffer
+    cudaEvent_t* comp_done = events + 2;    // per buffer pair
+    cudaEvent_t* out_done = events + 4;     // per output buffer
+#define HYDE_CU(x) do { if ((x) != cudaSuccess) return HYDE_ERR_CUDA; } while (0)
+    // fork: the copies follow what is already queued on `stream`
+    HYDE_CU(cudaEventRecord(events[6], stream));
+    HYDE_CU(cudaStreamWaitEvent(h2d, events[6], 0));
+    HYDE_CU(cudaStreamWaitEvent(d2h, events[6], 0));
+    for (int s = 0; s < count; ++s) {
+        const int b = s & 1;
+        float* Yd = dev[b];
+        float* Xd = dev[2 + b];
+        // copy in once the denoise of cube s - 2 has read the buffer
+        if (s >= 2) HYDE_CU(cudaStreamWaitEvent(h2d, comp_done[b], 0));
+        HYDE_CU(cudaMemcpyAsync(Yd, Y_host[s], bytes, cudaMemcpyHostToDevice, h2d));
+        HYDE_CU(cudaEventRecord(in_done[b], h2d));
+        // denoise once the input is in and cube s - 2's output is out
+        HYDE_CU(cudaStreamWaitEvent(stream, in_done[b], 0));
+        if (s >= 2) HYDE_CU(cudaStreamWaitEvent(stream, out_done[b], 0));
+        st = hyres_enqueue(Yd, Xd, p, H, W, params, info_dev + b, ws, ws_bytes, stream, nullptr);
+        if (st != HYDE_OK) return st;
+        HYDE_CU(cudaEventRecord(comp_done[b], stream));
+        // copy out
+        HYDE_CU(cudaStreamWaitEvent(d2h, comp_done[b], 0));
+        HYDE_CU(cudaMemcpyAsync(X_host[s], Xd, bytes, cudaMemcpyDeviceToHost, d2h));
+        if (info_host)
+            HYDE_CU(cudaMemcpyAsync(info_host + s, info_dev + b, sizeof(hyde_hyres_info),
+                                    cudaMemcpyDeviceToHost, d2h));
+        HYDE_CU(cudaEventRecord(out_done[b], d2h));
+    }
+    // join: the last copy-out ends the d2h stream's work; the h2d stream's
+    // last copy was already waited for by the last denoise
+    HYDE_CU(cudaStreamWaitEvent(stream, out_done[(count - 1) & 1], 0));
+#undef HYDE_CU
+    return HYDE_OK;
+}
+
 hyde_status hyde_hyres_denoise_timed(const float* Y, float* X, int p, int H, int W,
                                      const hyde_hyres_params* params, hyde_hyres_info* info,
                                      void* ws, size_t ws_bytes, cudaStream_t stream,

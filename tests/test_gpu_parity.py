@@ -214,3 +214,30 @@ def test_hyres_rejects_bad_shapes(hyde):
         hyde.HyRes(32, 64, 64, 2, 40)
     with pytest.raises(hyde.HydeError):
         hyde.HyRes(32, 3, 64, 3, 8)     # padding longer than the image
+
+
+# ------------------------------------------------------ host cube stream
+
+@pytest.mark.parametrize("count", [1, 3, 4])
+def test_denoise_host_stream_matches_device_calls(hyde, count):
+    """hyde_hyres_denoise_host (copies of cube s+1 in and s-1 out overlapping
+    the denoise of cube s, device buffers reused in turn) gives each cube the
+    result and the (rank, lambda) choice of a plain device call."""
+    cubes = [make_cube(64, 64, 32, m=4, seed=40 + s)["Y"] for s in range(count)]
+    h = hyde.HyRes(32, 64, 64, 2, 8)
+    refs, choices = [], []
+    for Y in cubes:
+        refs.append(h(_t(Y)).cpu().numpy())
+        info = h.result_info()
+        choices.append((info["rank"], info["lambda_index"]))
+    Ys = [torch.from_numpy(Y).pin_memory() for Y in cubes]
+    Xs = [torch.full_like(Ys[0], float("nan")).pin_memory() for _ in cubes]
+    nb = hyde.INFO_BYTES
+    infos = torch.zeros(count * nb, dtype=torch.uint8).pin_memory()
+    h.denoise_host(Ys, Xs, infos)
+    torch.cuda.synchronize()
+    for s in range(count):
+        assert O.rel_l2(Xs[s].numpy(), refs[s]) < 1e-6
+        info = hyde.parse_info(infos[s * nb:(s + 1) * nb])
+        assert info["status"] == 0
+        assert (info["rank"], info["lambda_index"]) == choices[s]
