@@ -32,7 +32,6 @@ namespace {
 
 constexpr int kLA = 1024;     // threads of the single-block kernels
 constexpr int kEigWarps = HYDE_EIG_WARPS;   // warps of the tridiagonalisation
-constexpr int kMaxRegT = 6;   // register tiles up to 6 x 6 (p <= 192)
 
 // --------------------------------------------------------------------------
 // Noise level, part 1: Gauss-Jordan inverse (no pivoting: the matrix is SPD)
@@ -48,12 +47,12 @@ constexpr float kPivotFloor = 2e-6f;
 // FMAs and 2T shared loads per thread plus one barrier; the pivot row and
 // column are published through double-buffered shared vectors. G = 16 (256
 // threads, up to 10 x 10 tiles) keeps the per-thread work of a step high and
-// the number of warps that repeat the pivot arithmetic low; G = 32 covers
-// p <= 192 with smaller tiles.
+// the number of warps that repeat the pivot arithmetic low; G = 20 covers
+// p <= 200.
 template <int T, int G>
-__global__ void __launch_bounds__(G * G, 1)
-noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
-                    double* __restrict__ S, int* status) {
+__device__ __forceinline__ void noise_gj_reg_body(const double* __restrict__ R, int p,
+                                                  float* __restrict__ Ainv,
+                                                  double* __restrict__ S, int* status) {
     pdl_wait();
     pdl_trigger();
     __shared__ float s_inv[G * T];
@@ -137,6 +136,14 @@ noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ain
         }
     }
 }
+
+template <int T, int G>
+__global__ void __launch_bounds__(G * G, 1)
+noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
+                    double* __restrict__ S, int* status) {
+    noise_gj_reg_body<T, G>(R, p, Ainv, S, status);
+}
+
 
 // Shared-memory Gauss-Jordan for p > 192 (same arithmetic, matrix in smem).
 __global__ void __launch_bounds__(kLA, 1)
@@ -858,9 +865,12 @@ size_t noise_ws_bytes(int p) {
            align_up((size_t)p * sizeof(double), kAlign);
 }
 
+// A 20 x 20 thread grid with 10 x 10 register tiles (400 threads) covers
+// p <= 200; larger p use the shared-memory kernel.
+constexpr int kGj20Max = 200;
+
 size_t noise_smem_bytes(int p) {
-    const int T = (p + 31) / 32;
-    return T <= kMaxRegT ? 0 : ((size_t)p * p + 2 * p) * sizeof(float);
+    return p <= kGj20Max ? 0 : ((size_t)p * p + 2 * p) * sizeof(float);
 }
 
 hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* sigma,
@@ -868,7 +878,7 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
     float* Ainv = reinterpret_cast<float*>(ws);
     double* Sd = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) +
                                            align_up((size_t)p * p * sizeof(float), kAlign));
-    const int T16 = (p + 15) / 16, T32 = (p + 31) / 32;
+    const int T16 = (p + 15) / 16;
     if (T16 <= 10) {
         switch (T16) {
 #define HYDE_GJ16(TV) \
@@ -879,13 +889,11 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
 #undef HYDE_GJ16
             default: return HYDE_ERR_SHAPE;
         }
-    } else if (T32 <= kMaxRegT) {
-        switch (T32) {
-            case 6:
-                launch_pdl(noise_gj_reg_kernel<6, 32>, 1, kLA, 0, s, R, p, Ainv, Sd, status);
-                break;
-            default: return HYDE_ERR_SHAPE;   // p in (160, 192] has T32 = 6
-        }
+    } else if (p <= kGj20Max) {
+        // 400 threads take registers in whole 4-warp groups (512 threads' worth), so the
+        // 10 x 10 tile gets 128 registers and spills a little: still far ahead of the
+        // shared-memory kernel
+        launch_pdl(noise_gj_reg_kernel<10, 20>, 1, 400, 0, s, R, p, Ainv, Sd, status);
     } else {
         size_t smem = noise_smem_bytes(p);
         if (ensure_smem_limit((const void*)noise_gj_smem_kernel, (int)smem) != cudaSuccess)
