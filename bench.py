@@ -221,7 +221,9 @@ def run_gb300(args) -> None:
             "bf16x3_all": api.PREC_BF16X3_ALL}[args.precision]
     h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev, precision=prec)
     lib = _lib.load()
-    launches_per_step = lib.hyde_hyres_kernel_launches(h.params)
+    launches_per_step = lib.hyde_hyres_kernel_launches(p, H, W, h.params)
+    if launches_per_step < 0:
+        raise RuntimeError("hyde_hyres_kernel_launches rejected the workload")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 

@@ -347,10 +347,12 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
                                        int n_slots, cudaEvent_t* events,
                                        cudaStream_t stream);
 
-/* Number of kernels one hyde_hyres_denoise call launches (10 + 2 * levels;
- * the two memsets that clear the workspace header and R are not counted),
- * or -1 for bad params. */
-int hyde_hyres_kernel_launches(const hyde_hyres_params* params);
+/* Number of kernels one hyde_hyres_denoise call launches on a p x H x W
+ * cube: 10 + 2 * (DWT launches), a DWT launch per level, except that the
+ * coarse levels run fused in one launch (18 at 349 x 1905, 5 levels); the
+ * two memsets that clear the workspace header and R are not counted. -1
+ * for bad params or shapes. */
+int hyde_hyres_kernel_launches(int p, int H, int W, const hyde_hyres_params* params);
 
 #ifdef __cplusplus
 }

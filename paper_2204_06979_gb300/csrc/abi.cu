@@ -10,16 +10,21 @@
 namespace hyde {
 
 thread_local bool tl_pdl = true;
+thread_local int tl_sm_cap = 0;
 
 int device_sm_count() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     static int cache[64] = {0};
-    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
     int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (dev >= 0 && dev < 64) cache[dev] = v;
-    return v;
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) {
+        v = cache[dev];
+    } else {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        if (dev >= 0 && dev < 64) cache[dev] = v;
+    }
+    return tl_sm_cap > 0 && tl_sm_cap < v ? tl_sm_cap : v;
 }
 
 cudaError_t ensure_smem_limit(const void* func, int bytes) {
@@ -571,6 +576,15 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H, i
 }
 
 // ------------------------------------------------------- sliding windows
+// SMs a window's multi-block kernels are sized for. The one-block kernels
+// (Gauss-Jordan, eigensolver, each with most of an SM's shared memory) carry
+// most of the window form's GPU time; grids sized for all SMs leave them no
+// free SM. Measured on the 2048 x 2048 x 200 scene (512 windows, 64 slots):
+// 46.0 ms per scene uncapped, 41.0 at 38 SMs, 37.5 at 10, 37.8 at 6, 41.6
+// at 4, 58.3 at 2.
+constexpr int kWindowSmCap = 10;
+static int window_sm_cap() { return kWindowSmCap; }
+
 static hyde_status window_valid(const hyde_window& wn, int H, int W) {
     if (wn.h < 1 || wn.w < 1 || wn.y0 < 0 || wn.x0 < 0 || wn.y0 + wn.h > H || wn.x0 + wn.w > W)
         return HYDE_ERR_SHAPE;
@@ -609,6 +623,7 @@ hyde_status hyde_windows_workspace_size(int p, int H, int W, const hyde_window* 
                                         const hyde_hyres_params* params, int n_slots,
                                         size_t* bytes) {
     if (!win || !bytes || n_win < 1 || n_slots < 1) return HYDE_ERR_INVALID_ARG;
+    const SmCap sm_cap(window_sm_cap());
     for (int k = 0; k < n_win; ++k) {
         hyde_status st = window_valid(win[k], H, W);
         if (st != HYDE_OK) return st;
@@ -629,6 +644,7 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H, i
                                        cudaEvent_t* events, cudaStream_t stream) {
     if (!Y || !X || Y == X || !win || !streams || !events || n_win < 1 || n_slots < 1)
         return HYDE_ERR_INVALID_ARG;
+    const SmCap sm_cap(window_sm_cap());   // also around the workspace query below
     size_t need = 0;
     hyde_status st = hyde_windows_workspace_size(p, H, W, win, n_win, params, n_slots, &need);
     if (st != HYDE_OK) return st;
@@ -666,10 +682,14 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H, i
     return HYDE_OK;
 }
 
-int hyde_hyres_kernel_launches(const hyde_hyres_params* params) {
-    if (!params || params->levels < 1 || params->levels > kMaxLevels) return -1;
-    // gram 2, noise 2, eig 1, weights 1, projection 1, DWT L, SURE 2, IDWT L, back 1
-    return 10 + 2 * params->levels;
+int hyde_hyres_kernel_launches(int p, int H, int W, const hyde_hyres_params* params) {
+    if (!params || params->levels < 1 || params->levels > kMaxLevels || p < 1) return -1;
+    int Hp, Wp;
+    if (!padded(H, W, params->levels, &Hp, &Wp)) return -1;
+    // gram 2, noise 2, eig 1, weights 1, projection 1, DWT, SURE 2, IDWT, back 1
+    // (the workspace carve keeps the DWT buffers 16-byte aligned, so the
+    // coarse levels always run fused where the shape allows)
+    return 10 + 2 * dwt_launches(Hp, Wp, params->levels);
 }
 
 }  // extern "C"

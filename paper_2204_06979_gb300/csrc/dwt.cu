@@ -617,6 +617,11 @@ static int tail_first_level(int Hp, int Wp, int levels) {
     return levels + 1;
 }
 
+int dwt_launches(int Hp, int Wp, int levels) {
+    const int lo = tail_first_level(Hp, Wp, levels);
+    return lo <= levels ? lo : levels;   // lo - 1 single levels and the fused tail
+}
+
 static inline bool aligned16(const void* p) {
     return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
 }

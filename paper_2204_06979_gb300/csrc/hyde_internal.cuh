@@ -114,6 +114,17 @@ struct PdlOff {
     ~PdlOff() { tl_pdl = prev; }
 };
 
+// Grids are sized from device_sm_count(); while an SmCap guard is alive on a
+// host thread that count is capped, which the sliding-window form uses so
+// that each window's multi-block kernels leave SMs free for the one-block
+// kernels of the other windows.
+extern thread_local int tl_sm_cap;
+struct SmCap {
+    int prev;
+    explicit SmCap(int cap) : prev(tl_sm_cap) { tl_sm_cap = cap; }
+    ~SmCap() { tl_sm_cap = prev; }
+};
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, Args&&... args) {
@@ -203,7 +214,9 @@ struct DwtSrc {
     int ld;
     int hv, wv;
 };
-size_t dwt_scratch_floats(int Hp, int Wp);   // per image, both ping-pong halves
+size_t dwt_scratch_floats(int Hp, int Wp);
+// kernel launches of launch_dwt2 / launch_idwt2 on a padded Hp x Wp image (aligned buffers)
+int dwt_launches(int Hp, int Wp, int levels);   // per image, both ping-pong halves
 hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp,
                         int Wp, int levels, float* scratch, cudaStream_t s);
 // Synthesis with optional soft threshold of detail coefficients at *lam
