@@ -483,7 +483,7 @@ def run_form(args) -> None:
         def step_eager():
             # every cube's forward and backward on its own stream
             scale.grad.zero_()
-            Xh = api.hyres_scaled_batch(Ys, scale, models, streams)
+            Xh = api.hyres_scaled_batch(Ys, scale, models, streams, sm_cap=args.sm_cap)
             loss = sum(torch.mean((X_ - Xc) ** 2) for X_, Xc in zip(Xh, Xs))
             loss.backward()
 
@@ -576,6 +576,9 @@ def main() -> None:
     ap.add_argument("--form", choices=("plain", "windows", "diff"), default="plain",
                     help="plain: the headline workload; windows / diff: secondary forms")
     ap.add_argument("--slots", type=int, default=64, help="window slots (--form windows)")
+    ap.add_argument("--sm-cap", type=int, default=None,
+                    help="--form diff: SMs each cube's grids are sized for (0: all; "
+                         "default: the batch API's choice)")
     ap.add_argument("--precision", choices=("fp32", "bf16x3", "bf16x3_all"), default="fp32",
                     help="fp32: plain form (headline); bf16x3: Gram on the tensor cores; "
                          "bf16x3_all: the projections there too")

@@ -347,6 +347,13 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
                                        int n_slots, cudaEvent_t* events,
                                        cudaStream_t stream);
 
+/* Caps, for the calling host thread, the SM count that the launchers size
+ * their grids from (0 removes the cap); returns the previous cap. For many
+ * small pipelines on concurrent streams: multi-block kernels sized for
+ * every SM keep the one-block kernels of the other streams from finding a
+ * free SM. A workspace sized without the cap stays large enough. */
+int hyde_set_grid_sm_cap(int sms);
+
 /* Number of kernels one hyde_hyres_denoise call launches on a p x H x W
  * cube: 10 + 2 * (DWT launches), a DWT launch per level, except that the
  * coarse levels run fused in one launch (18 at 349 x 1905, 5 levels); the

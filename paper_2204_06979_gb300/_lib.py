@@ -65,6 +65,7 @@ SIGNATURES = {
                                          ctypes.POINTER(HydeParams), c_vp, c_vp, c_size, c_vp,
                                          c_vp]),
     "hyde_hyres_kernel_launches": (c_int, [c_int, c_int, c_int, ctypes.POINTER(HydeParams)]),
+    "hyde_set_grid_sm_cap": (c_int, [c_int]),
     "hyde_hyres_denoise_scaled": (c_int, [c_vp, c_vp, c_int, c_int, c_int,
                                           ctypes.POINTER(HydeParams), c_vp, c_vp, c_vp, c_size,
                                           c_vp]),

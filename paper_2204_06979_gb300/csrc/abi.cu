@@ -682,6 +682,12 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H, i
     return HYDE_OK;
 }
 
+int hyde_set_grid_sm_cap(int sms) {
+    const int prev = tl_sm_cap;
+    tl_sm_cap = sms > 0 ? sms : 0;
+    return prev;
+}
+
 int hyde_hyres_kernel_launches(int p, int H, int W, const hyde_hyres_params* params) {
     if (!params || params->levels < 1 || params->levels > kMaxLevels || p < 1) return -1;
     int Hp, Wp;
