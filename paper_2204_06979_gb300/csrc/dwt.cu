@@ -8,13 +8,12 @@
 // giving LL (top-left), the row-detail band (top-right), the column-detail
 // band (bottom-left) and the diagonal band. LL is recursed on.
 //
-// Analysis of an already padded image runs as a persistent pipeline (tiles of
-// 16 x 64 coefficients per band, the next tile streamed into shared memory
-// with cp.async while the current one is filtered, float4 filter passes).
-// The first analysis level of an unpadded image (read through the symmetric
-// reflection) and every synthesis level use one tile per block (16 x 32
-// coefficients; the analysis reads a 34 x 66 input tile, the +2 halo wrapping
-// periodically). Details go straight to their Mallat position in the
+// Every analysis level runs as a persistent pipeline (tiles of 16 x 64
+// coefficients per band, the next tile streamed into shared memory with
+// cp.async while the current one is filtered, float4 filter passes); the
+// first level of an unpadded image reads through the symmetric extension.
+// Synthesis levels use one tile per block (16 x 32 coefficients) or the
+// register form below. Details go straight to their Mallat position in the
 // coefficient image; LL goes to a compact ping-pong buffer (or, at the last
 // level, into the coefficient image), so no level reads what another block
 // of the same launch writes. (A pipelined synthesis with the same structure
@@ -26,7 +25,6 @@ namespace hyde {
 namespace {
 
 constexpr int TH = 16, TW = 32;            // coefficient tile per subband
-constexpr int IH = 2 * TH + 2, IW = 2 * TW + 2;
 constexpr int kThreads = 256;
 
 // v in [0, m + tile) -> v mod m, with the division only for tiny images
@@ -36,78 +34,11 @@ __device__ __forceinline__ int wrap(int v, int m) {
     return v < m ? v : v % m;
 }
 
-template <bool REFLECT>
-__global__ void __launch_bounds__(kThreads)
-dwt_level_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int hv,
-                 int wv, int h, int w, float* __restrict__ coef, long long coef_bs,
-                 int coef_ld, float* __restrict__ ll, long long ll_bs, int ll_ld) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ float in[IH][IW + 1];
-    __shared__ float ra[IH][TW + 1];
-    __shared__ float rd[IH][TW + 1];
-    const int b = blockIdx.z;
-    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-    const int hh = h >> 1, wh = w >> 1;
-    const float* s = src + (long long)b * src_bs;
-    // one warp per input row; the periodic wrap is a subtraction except on
-    // images smaller than a tile
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // fixed trip counts (rows wid + 8 rr, columns lane + 32 cc), unrolled, so
-    // that all of a thread's loads are in flight before the first store
-    constexpr int kRowSteps = (IH + kThreads / 32 - 1) / (kThreads / 32);
-    constexpr int kColSteps = (IW + 31) / 32;
-#pragma unroll
-    for (int rr = 0; rr < kRowSteps; ++rr) {
-        const int r = wid + rr * (kThreads / 32);
-        if (r < IH) {
-            int y = wrap(2 * ty0 + r, h);
-            if (REFLECT && y >= hv) y = 2 * hv - 2 - y;
-            const float* row = s + (long long)y * src_ld;
-#pragma unroll
-            for (int cc = 0; cc < kColSteps; ++cc) {
-                const int c = lane + 32 * cc;
-                if (c < IW) {
-                    int x = wrap(2 * tx0 + c, w);
-                    if (REFLECT && x >= wv) x = 2 * wv - 2 - x;
-                    in[r][c] = __ldg(row + x);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < IH * TW; e += kThreads) {
-        const int r = e / TW, k = e % TW;
-        const float x0 = in[r][2 * k], x1 = in[r][2 * k + 1];
-        const float x2 = in[r][2 * k + 2], x3 = in[r][2 * k + 3];
-        ra[r][k] = kH0 * x0 + kH1 * x1 + kH2 * x2 + kH3 * x3;
-        rd[r][k] = kG0 * x0 + kG1 * x1 + kG2 * x2 + kG3 * x3;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < TH * TW; e += kThreads) {
-        const int j = e / TW, k = e % TW;
-        const int J = ty0 + j, K = tx0 + k;
-        if (J >= hh || K >= wh) continue;
-        const float a0 = ra[2 * j][k], a1 = ra[2 * j + 1][k];
-        const float a2 = ra[2 * j + 2][k], a3 = ra[2 * j + 3][k];
-        const float d0 = rd[2 * j][k], d1 = rd[2 * j + 1][k];
-        const float d2 = rd[2 * j + 2][k], d3 = rd[2 * j + 3][k];
-        const float LL = kH0 * a0 + kH1 * a1 + kH2 * a2 + kH3 * a3;
-        const float LH = kG0 * a0 + kG1 * a1 + kG2 * a2 + kG3 * a3;   // column detail
-        const float HL = kH0 * d0 + kH1 * d1 + kH2 * d2 + kH3 * d3;   // row detail
-        const float HH = kG0 * d0 + kG1 * d1 + kG2 * d2 + kG3 * d3;
-        float* cb = coef + (long long)b * coef_bs;
-        ll[(long long)b * ll_bs + (long long)J * ll_ld + K] = LL;
-        cb[(long long)J * coef_ld + wh + K] = HL;
-        cb[(long long)(hh + J) * coef_ld + K] = LH;
-        cb[(long long)(hh + J) * coef_ld + wh + K] = HH;
-    }
-}
-
 // --------------------------------------------------------------------------
-// Analysis level for a source that is already padded (no reflection), as a
-// persistent pipeline: block (g, image) walks tiles g, g + G, ... of one
-// image, 16 x 64 coefficients per subband each, from a 34 x 132 input tile.
+// Analysis level as a persistent pipeline: block (g, image) walks tiles
+// g, g + G, ... of one image, 16 x 64 coefficients per subband each, from a
+// 34 x 132 input tile (rows and columns past the valid hv x wv source are
+// read through the whole-sample symmetric extension).
 // The next tile streams into the other half of a double buffer with cp.async
 // (16-byte copies where the row is 16-byte aligned and the chunk does not
 // reach the image edge, 4-byte copies with the periodic wrap elsewhere)
@@ -133,9 +64,9 @@ template <int N>
 __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 __global__ void __launch_bounds__(kFThreads)
-dwt_level_pipe_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int h, int w,
-                      float* __restrict__ coef, long long coef_bs, int coef_ld,
-                      float* __restrict__ ll, long long ll_bs, int ll_ld) {
+dwt_level_pipe_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int hv,
+                      int wv, int h, int w, float* __restrict__ coef, long long coef_bs,
+                      int coef_ld, float* __restrict__ ll, long long ll_bs, int ll_ld) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ float4 fsm4[];
@@ -160,15 +91,20 @@ dwt_level_pipe_kernel(const float* __restrict__ src, long long src_bs, int src_l
         float* in = inb + buf * FIH * FIW;
         for (int e = tid; e < FIH * (FIW / 4); e += kFThreads) {
             const int r = e / (FIW / 4), cq = e - r * (FIW / 4);
-            const int y = wrap(2 * ty0 + r, h);
+            int y = wrap(2 * ty0 + r, h);
+            if (y >= hv) y = 2 * hv - 2 - y;   // symmetric extension of an unpadded source
             const float* row = S + (long long)y * src_ld;
             const int x0 = 2 * tx0 + 4 * cq;
             float* d = in + r * FIW + 4 * cq;
-            if (vin && x0 + 3 < w) {
+            if (vin && x0 + 3 < wv) {
                 cpa16(d, row + x0);
             } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) cpa4(d + u, row + wrap(x0 + u, w));
+                for (int u = 0; u < 4; ++u) {
+                    int x = wrap(x0 + u, w);
+                    if (x >= wv) x = 2 * wv - 2 - x;
+                    cpa4(d + u, row + x);
+                }
             }
         }
     };
@@ -662,19 +598,14 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
         int lld;
         if (lev == levels) { lp = coef; lbs = cbs; lld = Wp; }
         else { lp = ll_buf(scratch, batch, Hp, Wp, lev, &lbs); lld = w / 2; }
-        dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
-        if (hv < h || wv < w) {
-            launch_pdl(dwt_level_kernel<true>, grid, kThreads, 0, s, sp, sbs, sld, hv, wv, h, w,
-                       coef, cbs, Wp, lp, lbs, lld);
-        } else {
-            // padded source: the pipelined kernel, a few tiles per block
-            const int ntiles = ((w / 2 + FTW - 1) / FTW) * ((h / 2 + FTH - 1) / FTH);
-            int G = (pipe_per_sm * sms + batch - 1) / batch;
-            if (G > ntiles) G = ntiles;
-            if (G < 1) G = 1;
-            launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s, sp, sbs,
-                       sld, h, w, coef, cbs, Wp, lp, lbs, lld);
-        }
+        // the pipelined kernel, a few tiles per block; an unpadded source
+        // (level 1 of hyde_dwt2) is read through the symmetric extension
+        const int ntiles = ((w / 2 + FTW - 1) / FTW) * ((h / 2 + FTH - 1) / FTH);
+        int G = (pipe_per_sm * sms + batch - 1) / batch;
+        if (G > ntiles) G = ntiles;
+        if (G < 1) G = 1;
+        launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s, sp, sbs, sld,
+                   hv, wv, h, w, coef, cbs, Wp, lp, lbs, lld);
     }
     if (lo <= levels) {
         long long bs;
