@@ -64,6 +64,15 @@ def test_kernel_launch_count(lib):
     assert lib.hyde_hyres_kernel_launches(32, 64, 64, None) == -1
 
 
+def test_grid_sm_cap_setter(lib):
+    """hyde_set_grid_sm_cap returns the previous cap; 0 (or less) removes it."""
+    prev = lib.hyde_set_grid_sm_cap(10)
+    assert prev == 0
+    assert lib.hyde_set_grid_sm_cap(19) == 10
+    assert lib.hyde_set_grid_sm_cap(-3) == 19
+    assert lib.hyde_set_grid_sm_cap(0) == 0
+
+
 def test_bad_arguments_rejected_on_host(lib):
     from paper_2204_06979_gb300._lib import HydeParams
     sz = ctypes.c_size_t()
