@@ -155,7 +155,7 @@ def _oracle_threads() -> int:
     return os.cpu_count() or 1
 
 
-def oracle_sample_rate(cube, cols: int, runs: int) -> dict:
+def oracle_sample_rate(cube, cols: int, runs: int, lambda_mode: str = "shared") -> dict:
     """Time the FP64 oracle on the first ``cols`` columns of the cube."""
     import oracle as O
     w = WORKLOAD
@@ -164,7 +164,7 @@ def oracle_sample_rate(cube, cols: int, runs: int) -> dict:
     ts = []
     for _ in range(runs):
         t0 = time.perf_counter()
-        O.hyres(Ys, w["levels"], w["r_max"], w["n_lambda"])
+        O.hyres(Ys, w["levels"], w["r_max"], w["n_lambda"], lambda_mode=lambda_mode)
         ts.append(time.perf_counter() - t0)
     return dict(value=vox / 1e6 / statistics.mean(ts), times=ts, voxels=vox,
                 sample=f"oracle on the {w['H']}x{cols}x{w['p']} column slice "
@@ -219,7 +219,10 @@ def run_gb300(args) -> None:
     Xd = torch.empty_like(Yd)
     prec = {"fp32": api.PREC_FP32, "bf16x3": api.PREC_BF16X3,
             "bf16x3_all": api.PREC_BF16X3_ALL}[args.precision]
-    h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev, precision=prec)
+    lmode = {"shared": api.LAMBDA_SHARED,
+             "per_component": api.LAMBDA_PER_COMPONENT}[args.lambda_mode]
+    h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev, precision=prec,
+                  lambda_mode=lmode)
     lib = _lib.load()
     launches_per_step = lib.hyde_hyres_kernel_launches(p, H, W, h.params)
     if launches_per_step < 0:
@@ -371,7 +374,8 @@ def run_gb300(args) -> None:
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample_rate(cube, cols=args.cpu_cols, runs=args.cpu_runs)
+        s = oracle_sample_rate(cube, cols=args.cpu_cols, runs=args.cpu_runs,
+                               lambda_mode=args.lambda_mode)
         cpu = {"value": round(s["value"], 3), "unit": UNIT, "cores": _oracle_threads(),
                "kind": "oracle", "sample": s["sample"]}
 
@@ -384,6 +388,9 @@ def run_gb300(args) -> None:
             cfg["precision"] = ("bf16x3_all (Gram, projection and back-projection on tcgen05, "
                                 "split-BF16 compensated)")
             cfg["workload"] += ", precision form (all contractions on the tensor cores)"
+        if args.lambda_mode == "per_component":
+            cfg["lambda_mode"] = "per_component (one SURE threshold per kept component)"
+            cfg["workload"] += ", per-component thresholds"
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -582,6 +589,9 @@ def main() -> None:
     ap.add_argument("--precision", choices=("fp32", "bf16x3", "bf16x3_all"), default="fp32",
                     help="fp32: plain form (headline); bf16x3: Gram on the tensor cores; "
                          "bf16x3_all: the projections there too")
+    ap.add_argument("--lambda-mode", choices=("shared", "per_component"), default="shared",
+                    help="shared: one SURE threshold for every kept component (headline); "
+                         "per_component: each kept component at its own threshold")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3

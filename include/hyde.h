@@ -70,6 +70,19 @@ typedef enum {
                               flop/B, where the FP32 forms measure faster)   */
 } hyde_precision;
 
+/* How the SURE selection (Sec. 2.1, "parameter-free") assigns thresholds.
+ * The paper leaves open whether the kept components share one threshold. */
+typedef enum {
+    HYDE_LAMBDA_SHARED = 0,        /* one lambda_{k*} for every kept component:
+                                      (r*, k*) = argmin over the (r, k) table */
+    HYDE_LAMBDA_PER_COMPONENT = 1  /* component i thresholded at its own
+                                      lambda_{k_i}, k_i = argmin_k S_i(lambda_k)
+                                      (first minimum); r* = argmin_r U(r) with
+                                      U(r) = sum_{i<=r} S_i(lambda_{k_i})
+                                             + sum_{r<i<=r_max} S_i(inf)
+                                      (first minimum)                         */
+} hyde_lambda_mode;
+
 /* Parameters of one HyRes run. */
 typedef struct {
     int wavelet;    /* number of vanishing moments of the Daubechies filter;
@@ -78,7 +91,10 @@ typedef struct {
     int r_max;      /* largest rank tried, 1..min(p, 32)                    */
     int n_lambda;   /* K threshold candidates, 2..256; 64 is the default    */
     int precision;  /* hyde_precision                                       */
-    int reserved[3];/* must be zero                                         */
+    int lambda_mode;/* hyde_lambda_mode; HYDE_LAMBDA_SHARED is the default,
+                       and the only mode of the scaled (differentiation)
+                       entry points                                         */
+    int reserved[2];/* must be zero                                         */
 } hyde_hyres_params;
 
 /* Outcome of one HyRes run, written by the device into caller memory. */
@@ -105,6 +121,10 @@ typedef struct {
     size_t sure_inf;   /* double[r_max]  SURE of dropping component i        */
     size_t sure_total; /* double[r_max][K] total SURE of rank r=i+1, lambda_k */
     size_t status;     /* int            device status word                  */
+    size_t lam_comp;   /* float[r_max][levels] threshold that each component's
+                          detail bands of each level were soft-thresholded at
+                          (HYDE_LAMBDA_PER_COMPONENT only: row i < r* holds
+                          lambda_{k_i} in every column, the other rows 0)    */
 } hyde_ws_layout;
 
 /* Human-readable name of a status code (static storage). */
@@ -218,7 +238,11 @@ hyde_status hyde_sure_table(const float* coef, int batch, int Hp, int Wp,
  * Rank r* in 1..r_max and threshold lambda_{k*} minimise the total SURE
  *   T(r, k) = sum_{i<=r} S_i(lambda_k) + sum_{r<i<=r_max} S_i(inf)
  * (ties: smallest r, then smallest k). info (device) receives the choice
- * and the device status; NULL is allowed.
+ * and the device status; NULL is allowed. With lambda_mode
+ * HYDE_LAMBDA_PER_COMPONENT each kept component i gets its own lambda_{k_i}
+ * (see hyde_lambda_mode); info then holds r*, k_0 and lambda_{k_0} of the
+ * first component, sure_min = U(r*) and sure_gap from the runner-up rank,
+ * and the workspace's lam_comp table holds every component's threshold.
  */
 hyde_status hyde_workspace_size(int p, int H, int W,
                                 const hyde_hyres_params* params,

@@ -22,7 +22,8 @@ cited HyRes source. The stages written out here, in the order they run, are:
 Readings where the paper is silent (kept identical in the CUDA path):
 periodic DWT boundary; whole-sample symmetric padding at the bottom/right to
 multiples of 2**L, cropped after the inverse transform; the LL band is never
-thresholded; one lambda shared by all kept components; lambda grid
+thresholded; one lambda shared by all kept components (one per component
+as a variant); lambda grid
 ``k * sqrt(2 ln N) / (K - 1)``; ties go to the smallest rank, then the smallest
 lambda; regression without intercept or ridge; uncentred Gram matrix.
 
@@ -286,19 +287,42 @@ def select_rank_lambda(S, S_inf):
     return r_star + 1, k_star, T, gap
 
 
+def select_rank_lambda_per_component(S, S_inf):
+    """Stage 8 with one threshold per kept component (a reading the paper
+    leaves open, Sec. 2.1): component ``i`` takes ``k_i``, the first
+    minimiser of its own ``S_i(lambda_k)``; the rank minimises
+    ``U[r-1] = sum_{i<=r} S_i(lambda_{k_i}) + sum_{r<i<=r_max} S_i(inf)``
+    (first minimum). Returns ``(r*, k[r_max], U, gap)`` with ``gap`` the
+    relative distance of the runner-up rank's ``U`` to the minimum."""
+    S = np.asarray(S, dtype=np.float64)
+    r_max = S.shape[0]
+    k = np.argmin(S, axis=1)
+    best = S[np.arange(r_max), k]
+    U = np.array([np.sum(best[: r + 1]) + np.sum(S_inf[r + 1:]) for r in range(r_max)])
+    r_star = int(np.argmin(U)) + 1
+    vals = np.sort(U)
+    gap = (vals[1] - vals[0]) / max(abs(vals[0]), 1e-300) if vals.size > 1 else np.inf
+    return r_star, k, U, gap
+
+
 # --------------------------------------------------------------------------
 # The whole path
 # --------------------------------------------------------------------------
 
 def hyres(Y, levels, r_max, n_lambda=64, *, sigma=None, V=None, rank=None,
-          lam=None):
+          lam=None, lambda_mode="shared"):
     """Run stages 1-10 on ``Y`` (``float[p][H][W]``).
 
     Optional overrides (for checks of single stages): ``sigma`` (skip stage 2),
     ``V`` (``p x r_max`` basis, skip stage 4), ``rank`` and ``lam`` (skip
-    stage 8). Returns a dict with the estimate ``X`` (``float64[p][H][W]``)
-    and every intermediate.
+    stage 8). ``lambda_mode``: ``"shared"`` (one threshold for every kept
+    component) or ``"per_component"`` (``select_rank_lambda_per_component``;
+    ``lam`` may then be a sequence of per-component thresholds). Returns a
+    dict with the estimate ``X`` (``float64[p][H][W]``) and every
+    intermediate; ``lam_comp`` holds the threshold of each kept component.
     """
+    if lambda_mode not in ("shared", "per_component"):
+        raise ValueError("lambda_mode must be 'shared' or 'per_component'")
     Y = np.asarray(Y)
     p, H, W = Y.shape
     n = H * W
@@ -322,17 +346,29 @@ def hyres(Y, levels, r_max, n_lambda=64, *, sigma=None, V=None, rank=None,
     S, S_inf = sure_table(C, levels, lams)                      # stage 7
     r_star, k_star, T, gap = select_rank_lambda(S, S_inf)       # stage 8
     lam_star = lams[k_star]
+    extra = {}
+    if lambda_mode == "per_component":
+        r_star, k_comp, U, gap = select_rank_lambda_per_component(S, S_inf)
+        k_star, lam_star = int(k_comp[0]), lams[k_comp[0]]
+        lam_comp = lams[k_comp[:r_star]]
+        extra = dict(k_comp=k_comp, U=U)
     if rank is not None:
         r_star, k_star = int(rank), -1
-        lam_star = float(lam)
+        lam_star = lam
+        lam_comp = np.broadcast_to(np.asarray(lam, dtype=np.float64), (r_star,))
+    if lambda_mode == "shared":
+        lam_star = float(lam_star)
+        lam_comp = np.full(r_star, lam_star)
     mask = _detail_mask(Hp, Wp, levels)
     Ch = C[:r_star].copy()
-    Ch[:, mask] = soft_threshold(Ch[:, mask], lam_star)         # stage 9
+    for i in range(r_star):                                     # stage 9
+        Ch[i][mask] = soft_threshold(Ch[i][mask], lam_comp[i])
     Zh = idwt2(Ch, levels)[:, :H, :W].reshape(r_star, n)
     Xh = sigma[:, None] * (V[:, :r_star] @ Zh)                  # stage 10
     return dict(X=Xh.reshape(p, H, W), rank=r_star, k=k_star, lam=lam_star,
+                lam_comp=np.array(lam_comp, dtype=np.float64),
                 sigma=sigma, R=R, Rw=Rw, evals=evals, V=V, C=C, S=S,
-                S_inf=S_inf, T=T, gap=gap, lams=lams)
+                S_inf=S_inf, T=T, gap=gap, lams=lams, **extra)
 
 
 # --------------------------------------------------------------------------

@@ -22,8 +22,8 @@ c_size_p = ctypes.POINTER(ctypes.c_size_t)
 
 class HydeParams(ctypes.Structure):
     _fields_ = [("wavelet", c_int), ("levels", c_int), ("r_max", c_int),
-                ("n_lambda", c_int), ("precision", c_int),
-                ("reserved", c_int * 3)]
+                ("n_lambda", c_int), ("precision", c_int), ("lambda_mode", c_int),
+                ("reserved", c_int * 2)]
 
 
 class HydeWindow(ctypes.Structure):
@@ -33,7 +33,7 @@ class HydeWindow(ctypes.Structure):
 class HydeWsLayout(ctypes.Structure):
     _fields_ = [(name, c_size) for name in
                 ("total", "R", "sigma", "evals", "V", "coef", "sure", "sure_inf",
-                 "sure_total", "status")]
+                 "sure_total", "status", "lam_comp")]
 
 
 INFO_BYTES = 40   # hyde_hyres_info: 4 x int32 + 3 x float64

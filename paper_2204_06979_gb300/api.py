@@ -19,6 +19,8 @@ HYDE_OK = 0
 PREC_FP32 = 0
 PREC_BF16X3 = 2       # Gram on the tensor cores (split-BF16)
 PREC_BF16X3_ALL = 3   # Gram, projection and back-projection on the tensor cores
+LAMBDA_SHARED = 0         # one SURE threshold for every kept component
+LAMBDA_PER_COMPONENT = 1  # each kept component at its own SURE threshold
 
 
 class HydeError(RuntimeError):
@@ -59,13 +61,15 @@ def padded_shape(H: int, W: int, levels: int) -> tuple[int, int]:
     return -(-H // q) * q, -(-W // q) * q
 
 
-def params(levels: int, r_max: int, n_lambda: int = 64, precision: int = PREC_FP32) -> HydeParams:
+def params(levels: int, r_max: int, n_lambda: int = 64, precision: int = PREC_FP32,
+           lambda_mode: int = LAMBDA_SHARED) -> HydeParams:
     p = HydeParams()
     p.wavelet = 2
     p.levels = levels
     p.r_max = r_max
     p.n_lambda = n_lambda
     p.precision = precision
+    p.lambda_mode = lambda_mode
     return p
 
 
@@ -184,10 +188,10 @@ class HyRes:
     stream."""
 
     def __init__(self, p: int, H: int, W: int, levels: int, r_max: int, n_lambda: int = 64,
-                 device="cuda", precision: int = PREC_FP32):
+                 device="cuda", precision: int = PREC_FP32, lambda_mode: int = LAMBDA_SHARED):
         self.lib = _lib.load()
         self.shape = (p, H, W)
-        self.params = params(levels, r_max, n_lambda, precision)
+        self.params = params(levels, r_max, n_lambda, precision, lambda_mode)
         sz = ctypes.c_size_t()
         _check(self.lib.hyde_workspace_size(p, H, W, ctypes.byref(self.params), ctypes.byref(sz)),
                "hyde_workspace_size")
@@ -270,15 +274,18 @@ class HyRes:
             S_inf=self._view(L.sure_inf, r, torch.float64),
             T=self._view(L.sure_total, r * K, torch.float64).view(r, K),
             status=self._view(L.status, 1, torch.int32),
+            lam_comp=self._view(L.lam_comp, r * self.params.levels,
+                                torch.float32).view(r, self.params.levels),
         )
 
 
 def hyres_denoise(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64,
-                  precision: int = PREC_FP32):
+                  precision: int = PREC_FP32, lambda_mode: int = LAMBDA_SHARED):
     """One-shot HyRes on ``Y[p, H, W]``; returns ``(X, info dict)``
     (synchronises the current stream to read the info record)."""
     p, H, W = Y.shape
-    h = HyRes(p, H, W, levels, r_max, n_lambda, device=Y.device, precision=precision)
+    h = HyRes(p, H, W, levels, r_max, n_lambda, device=Y.device, precision=precision,
+              lambda_mode=lambda_mode)
     X = h(Y)
     return X, h.result_info()
 
@@ -476,11 +483,12 @@ class HyResWindows:
     ``__call__`` enqueues the whole scene on the current stream;
     ``capture``/``replay`` record it once into a CUDA graph and relaunch it."""
 
-    def __init__(self, p, H, W, table, levels, r_max, n_lambda=64, n_slots=64, device="cuda"):
+    def __init__(self, p, H, W, table, levels, r_max, n_lambda=64, n_slots=64, device="cuda",
+                 lambda_mode: int = LAMBDA_SHARED):
         from ._lib import HydeWindow
         self.lib = _lib.load()
         self.shape = (p, H, W)
-        self.params = params(levels, r_max, n_lambda)
+        self.params = params(levels, r_max, n_lambda, lambda_mode=lambda_mode)
         self.device = torch.device(device)
         rows = [tuple(int(v) for v in r) for r in table]
         self.n_win = len(rows)

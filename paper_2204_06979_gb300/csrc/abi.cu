@@ -87,7 +87,9 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     if (pr->precision != HYDE_PREC_FP32 && pr->precision != HYDE_PREC_BF16X3 &&
         pr->precision != HYDE_PREC_BF16X3_ALL)
         return HYDE_ERR_INVALID_ARG;
-    if (pr->reserved[0] || pr->reserved[1] || pr->reserved[2]) return HYDE_ERR_INVALID_ARG;
+    if (pr->lambda_mode != HYDE_LAMBDA_SHARED && pr->lambda_mode != HYDE_LAMBDA_PER_COMPONENT)
+        return HYDE_ERR_INVALID_ARG;
+    if (pr->reserved[0] || pr->reserved[1]) return HYDE_ERR_INVALID_ARG;
     if (p < 2 || p > kMaxBandsGram) return HYDE_ERR_SHAPE;
     if (pr->r_max < 1 || pr->r_max > kMaxRank || pr->r_max > p) return HYDE_ERR_SHAPE;
     if (pr->n_lambda < 2 || pr->n_lambda > kMaxLambda) return HYDE_ERR_SHAPE;
@@ -128,6 +130,7 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.pub.sure = c.take((size_t)r * K * sizeof(double));
     l.pub.sure_inf = c.take((size_t)r * sizeof(double));
     l.pub.sure_total = c.take((size_t)r * K * sizeof(double));
+    l.pub.lam_comp = c.take((size_t)r * pr->levels * sizeof(float));
     l.sint = c.take((size_t)2 * r * K * sizeof(long long));
     l.P = c.take((size_t)p * l.RM * sizeof(float));
     l.Q = c.take((size_t)p * l.RM * sizeof(float));
@@ -345,6 +348,9 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
                                  void* ws, size_t ws_bytes, cudaStream_t stream,
                                  cudaEvent_t* ev, const float* scale = nullptr) {
     if (!Y || !X || Y == X) return HYDE_ERR_INVALID_ARG;
+    // the scaled forms multiply one shared lambda by their scales
+    const bool per_comp = params && params->lambda_mode == HYDE_LAMBDA_PER_COMPONENT;
+    if (per_comp && scale) return HYDE_ERR_INVALID_ARG;
     HyresLayout L;
     hyde_status st = hyres_layout(p, H, W, params, &L);
     if (st != HYDE_OK) return st;
@@ -403,13 +409,15 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     const long long N_det = L.N - (long long)(L.Hp >> lev) * (L.Wp >> lev);
     const double delta = sqrt(2.0 * log((double)L.N)) / (K - 1);
     HYDE_TRY(launch_sure_hist(coef, r, L.Hp, L.Wp, lev, K, delta, sb, stream));
+    float* lam_comp = per_comp ? at<float>(ws, L.pub.lam_comp) : nullptr;
     HYDE_TRY(launch_sure_select(sb, r, K, L.N, N_det, delta, at<double>(ws, L.pub.sure),
                                 at<double>(ws, L.pub.sure_inf), at<double>(ws, L.pub.sure_total),
-                                info, rank_dev, lam_dev, status, stream));
+                                info, rank_dev, lam_dev, status, stream, lam_comp, lev));
     HYDE_TRY(stage());
-    // 9. soft threshold + inverse DWT of the kept components (into zp, H x W)
+    // 9. soft threshold + inverse DWT of the kept components (into zp, H x W);
+    // per-component thresholds are lam_comp[i][l] times *lam_dev = 1
     HYDE_TRY(launch_idwt2(coef, zp, r, L.Hp, L.Wp, H, W, lev, scratch, lam_dev, rank_dev, stream,
-                          scale, lev));
+                          per_comp ? lam_comp : scale, lev));
     HYDE_TRY(stage());
     // 10. back-projection and un-whitening
     if (tc_proj)
@@ -521,6 +529,7 @@ static hyde_status back_layout(const HyresLayout& L, int r, int levels, BackLayo
 hyde_status hyde_backward_workspace_size(int p, int H, int W, const hyde_hyres_params* params,
                                          size_t* bytes) {
     if (!bytes) return HYDE_ERR_INVALID_ARG;
+    if (params && params->lambda_mode != HYDE_LAMBDA_SHARED) return HYDE_ERR_INVALID_ARG;
     HyresLayout L;
     hyde_status st = hyres_layout(p, H, W, params, &L);
     if (st != HYDE_OK) return st;
@@ -537,6 +546,7 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H, i
                                 cudaStream_t stream) {
     if (!Y || !scale || !dscale || (loss != 0 && loss != 1)) return HYDE_ERR_INVALID_ARG;
     if (loss == 0 && !dX) return HYDE_ERR_INVALID_ARG;
+    if (params && params->lambda_mode != HYDE_LAMBDA_SHARED) return HYDE_ERR_INVALID_ARG;
     HyresLayout L;
     hyde_status st = hyres_layout(p, H, W, params, &L);
     if (st != HYDE_OK) return st;
@@ -690,6 +700,9 @@ int hyde_set_grid_sm_cap(int sms) {
 
 int hyde_hyres_kernel_launches(int p, int H, int W, const hyde_hyres_params* params) {
     if (!params || params->levels < 1 || params->levels > kMaxLevels || p < 1) return -1;
+    if (params->lambda_mode != HYDE_LAMBDA_SHARED &&
+        params->lambda_mode != HYDE_LAMBDA_PER_COMPONENT)
+        return -1;
     int Hp, Wp;
     if (!padded(H, W, params->levels, &Hp, &Wp)) return -1;
     // gram 2, noise 2, eig 1, weights 1, projection 1, DWT, SURE 2, IDWT, back 1

@@ -265,12 +265,16 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp,
                              int levels, int K, double delta,
                              const SureBufs& b, cudaStream_t s);
 // Builds S, S_inf (and, when T != NULL, the (rank, lambda) table plus the
-// selection written to info/rank_out/lam_out).
+// selection written to info/rank_out/lam_out). With lam_comp != NULL (and T
+// != NULL) the selection takes one threshold per component instead: the
+// rank comes from the per-component minima, *lam_out = 1 and
+// lam_comp[i][l] (float[batch][levels]) holds component i's threshold.
 hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
                                long long N_det, double delta, double* S,
                                double* S_inf, double* T,
                                hyde_hyres_info* info, int* rank_out,
                                double* lam_out, const int* status,
-                               cudaStream_t s);
+                               cudaStream_t s, float* lam_comp = nullptr,
+                               int levels = 0);
 
 }  // namespace hyde

@@ -185,6 +185,14 @@ sure_table_kernel(const unsigned int* __restrict__ counts, const double* __restr
 // forms every T with a few FP64 operations spread over the block, and finds
 // the first minimum in row-major (rank, lambda) order and the runner-up on
 // order-preserving integer keys.
+//
+// Per-component thresholds (one lambda per kept component): before the
+// prefix, one warp per component takes the first minimum of row i of S (the
+// same FP64 expression as the table), k_i; then
+//   U(r) = sum_{i<=r} S_i(lambda_{k_i}) + sum_{i>r} S_inf[i]
+// is accumulated over r in FP64 by one thread (at most 32 terms) and its
+// first minimum gives the rank. The thresholds go to lam_comp[i][level] for
+// the inverse transform, which multiplies them by *lam_out = 1.
 constexpr int kSelThreads = 256;
 
 __device__ __forceinline__ long long ord_key(double v) {
@@ -230,11 +238,14 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
                    long long N_det, double delta, double* __restrict__ S,
                    double* __restrict__ S_inf, double* __restrict__ T, long long* sint,
                    unsigned int* done, hyde_hyres_info* info, int* rank_out, double* lam_out,
-                   const int* status) {
+                   const int* status, float* lam_comp, int levels) {
     pdl_wait();
     pdl_trigger();
     __shared__ long long wc[kSelThreads / 32], wq[kSelThreads / 32];
     __shared__ double tail[kMaxRank], sinf[kMaxRank];
+    __shared__ double cmin[kMaxRank];   // per-component minimum S_i(lambda_{k_i})
+    __shared__ int ck[kMaxRank];        // its k_i
+    __shared__ int s_rank;
     __shared__ double lam2[kMaxLambda];
     __shared__ long long wm1[kSelThreads / 32], wm2[kSelThreads / 32];
     __shared__ int wi1[kSelThreads / 32];
@@ -280,6 +291,24 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
         lam2[k] = lam * lam;
     }
     __syncthreads();
+    if (lam_comp) {   // per-component first minimum over the rows of S (not yet prefixed)
+        for (int i = wid; i < batch; i += nw) {
+            long long m = 0x7fffffffffffffffLL;
+            int kb = 0x7fffffff;
+            for (int k = lane; k < K; k += 32) {   // ascending k: strict < keeps the first
+                const long long kv = ord_key(fma(lam2[k], (double)PB[i * K + k],
+                                                 (double)PA[i * K + k] * (1.0 / 65536.0)));
+                if (kv < m) { m = kv; kb = k; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long om = __shfl_xor_sync(0xffffffffu, m, o);
+                const int ok = __shfl_xor_sync(0xffffffffu, kb, o);
+                if (om < m || (om == m && ok < kb)) { m = om; kb = ok; }
+            }
+            if (lane == 0) { cmin[i] = key_value(m); ck[i] = kb; }
+        }
+        __syncthreads();
+    }
     if (t < batch) {   // tail[r] = sum_{i > r} S_inf[i], added from i = batch - 1 down
         double acc = 0.0;
         for (int r = batch - 1; r > t; --r) acc += sinf[r];
@@ -323,10 +352,29 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
             }
         }
         const int tot = batch * K;
-        const int r = i1 / K, k = i1 % K;
-        const double v1 = key_value(m1), v2 = key_value(m2);
+        int r = i1 / K, k = i1 % K;
+        double v1 = key_value(m1), v2 = key_value(m2), scale = k * delta;
+        int cand = tot;
+        if (lam_comp) {   // U(r): first minimum over r and the runner-up
+            double acc = 0.0, u1 = 0.0, u2 = 0.0;
+            int rb = 0;
+            for (int q = 0; q < batch; ++q) {
+                acc += cmin[q];
+                const double u = acc + tail[q];
+                if (q == 0) { u1 = u; u2 = u; }
+                else if (u < u1) { u2 = (q == 1) ? u1 : fmin(u2, u1); u1 = u; rb = q; }
+                else u2 = (q == 1) ? u : fmin(u2, u);
+            }
+            r = rb;
+            k = ck[0];
+            v1 = u1;
+            v2 = u2;
+            scale = 1.0;
+            cand = batch;
+        }
+        s_rank = r;
         if (rank_out) *rank_out = r + 1;
-        if (lam_out) *lam_out = k * delta;
+        if (lam_out) *lam_out = scale;
         if (info) {
             info->status = status ? *status : 0;
             info->rank = r + 1;
@@ -334,7 +382,15 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
             info->reserved = 0;
             info->lambda = k * delta;
             info->sure_min = v1;
-            info->sure_gap = (tot > 1) ? (v2 - v1) / fmax(fabs(v1), 1e-300) : 0.0;
+            info->sure_gap = (cand > 1) ? (v2 - v1) / fmax(fabs(v1), 1e-300) : 0.0;
+        }
+    }
+    if (lam_comp) {   // thresholds of the kept components, 0 for the dropped ones
+        __syncthreads();
+        const int rk = s_rank;
+        for (int e = t; e < batch * levels; e += kSelThreads) {
+            const int i = e / levels;
+            lam_comp[e] = i <= rk ? (float)(ck[i] * delta) : 0.f;
         }
     }
 }
@@ -386,19 +442,21 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int l
 hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
                                long long N_det, double delta, double* S, double* S_inf,
                                double* T, hyde_hyres_info* info, int* rank_out,
-                               double* lam_out, const int* status, cudaStream_t s) {
+                               double* lam_out, const int* status, cudaStream_t s,
+                               float* lam_comp, int levels) {
     if (T == nullptr) {   // the tables only
         launch_pdl(sure_table_kernel, (batch + 7) / 8, 256, 0, s, b.counts, b.sums, b.sum_all,
                    batch, K, N, N_det, delta, S, S_inf);
     } else {
         if (batch > kMaxRank || K > kSelThreads || b.done == nullptr || b.sint == nullptr)
             return HYDE_ERR_SHAPE;
+        if (lam_comp && levels < 1) return HYDE_ERR_INVALID_ARG;
         const size_t smem = (size_t)2 * batch * K * sizeof(long long);
         if (ensure_smem_limit((const void*)sure_select_kernel, (int)smem) != cudaSuccess)
             return HYDE_ERR_CUDA;
         launch_pdl(sure_select_kernel, batch, kSelThreads, smem, s, b.counts, b.sums,
                    b.sum_all, batch, K, N, N_det, delta, S, S_inf, T, b.sint, b.done, info,
-                   rank_out, lam_out, status);
+                   rank_out, lam_out, status, lam_comp, levels);
     }
     return cuda_status(cudaGetLastError());
 }

@@ -101,6 +101,9 @@ def test_bad_arguments_rejected_on_host(lib):
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
     p.reserved[0] = 0
     assert lib.hyde_workspace_size(1, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 2
+    p.lambda_mode = 2
+    assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
+    p.lambda_mode = 0
     assert lib.hyde_eig_sym_top(None, 4, 2, None, None, None, None) == 1
 
 
@@ -110,3 +113,18 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_LIB", None)
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def test_lambda_mode_params(lib):
+    """Per-component thresholds are rejected, before any device query, by the
+    scaled (differentiation) entry points, and an unknown mode by every
+    entry point."""
+    from paper_2204_06979_gb300 import api
+    comp = api.params(3, 8, 64, lambda_mode=api.LAMBDA_PER_COMPONENT)
+    bad = api.params(3, 8, 64, lambda_mode=5)
+    sz = ctypes.c_size_t()
+    assert lib.hyde_backward_workspace_size(32, 64, 64, ctypes.byref(comp), ctypes.byref(sz)) == 1
+    assert lib.hyde_hyres_denoise_scaled(1, 2, 32, 64, 64, ctypes.byref(comp), 3, None, 4,
+                                         1 << 30, None) == 1
+    assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(bad), ctypes.byref(sz)) == 1
+    assert lib.hyde_hyres_kernel_launches(32, 64, 64, ctypes.byref(bad)) == -1

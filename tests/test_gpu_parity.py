@@ -221,6 +221,76 @@ def test_hyres_rejects_bad_shapes(hyde):
         hyde.HyRes(32, 3, 64, 3, 8)     # padding longer than the image
 
 
+# ------------------------------------------- per-component thresholds
+
+def _check_hyres_per_component(hyde, Y, L, r_max, K=64):
+    """One threshold per kept component. The S table on the GPU may differ
+    from the oracle's by a coefficient counted on the other side of a grid
+    point (bound of test_sure_table_matches_oracle), so where the oracle's
+    choice of k_i (or of the rank) is that close to a runner-up the GPU may
+    take the runner-up: its choice must then be a minimiser of the oracle's
+    table within that bound, and its estimate must match the oracle run at
+    the GPU's choice. Where the choice is clear it must be identical."""
+    o = O.hyres(Y, L, r_max, K, lambda_mode="per_component")
+    p, H, W = Y.shape
+    h = hyde.HyRes(p, H, W, L, r_max, K, lambda_mode=hyde.LAMBDA_PER_COMPONENT)
+    X = h(_t(Y)).cpu().numpy()
+    info = h.result_info()
+    lam_comp = h.intermediates()["lam_comp"].cpu().numpy().astype(np.float64)
+    assert info["status"] == 0
+    r = info["rank"]
+    assert np.all(lam_comp[r:] == 0.0) and np.all(lam_comp[:r] == lam_comp[:r, :1])
+    lams = o["lams"]
+    k_gpu = np.rint(lam_comp[:r, 0] / lams[1]).astype(int)
+    assert np.allclose(lam_comp[:r, 0], lams[k_gpu], rtol=1e-6, atol=0)
+    assert info["lambda_index"] == k_gpu[0]
+    S, S_inf = o["S"], o["S_inf"]
+    tol = 2.0 * (4.0 + 1e-6 * np.max(np.abs(S)))
+    for i in range(r):
+        clear = np.all(np.delete(S[i], o["k_comp"][i]) > S[i, o["k_comp"][i]] + tol)
+        if clear:
+            assert k_gpu[i] == o["k_comp"][i], (i, k_gpu[i], o["k_comp"][i])
+        else:
+            assert S[i, k_gpu[i]] <= S[i].min() + tol
+    U_gpu = S[np.arange(r), k_gpu].sum() + S_inf[r:].sum()
+    assert U_gpu <= o["U"].min() + r_max * tol
+    if np.all(np.delete(o["U"], o["rank"] - 1) > o["U"].min() + r_max * tol):
+        assert r == o["rank"]
+    if r == o["rank"] and np.array_equal(k_gpu, o["k_comp"][:r]):
+        ref = o["X"]
+    else:
+        ref = O.hyres(Y, L, r_max, K, rank=r, lam=lams[k_gpu], lambda_mode="per_component")["X"]
+    err = O.rel_l2(X, ref)
+    assert err < REL_L2_PATH, err
+    return o, info, k_gpu
+
+
+def test_hyres_per_component_c0(hyde):
+    c = make_cube(64, 64, 32, m=4, seed=1)
+    o, info, k_gpu = _check_hyres_per_component(hyde, c["Y"], 2, 8)
+    assert info["rank"] == 4
+    assert abs(info["sure_min"] - o["U"].min()) < 1e-4 * abs(o["U"].min()) + 8 * 8.0
+
+
+@pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
+    (77, 131, 24, 3, 3, 6, 64, 31),     # ragged: padded to 80 x 136
+    (128, 128, 64, 8, 4, 16, 64, 5),
+    (40, 52, 12, 2, 2, 12, 16, 32),     # r_max = p, small K
+    (30, 30, 6, 2, 1, 1, 2, 33),        # r_max = 1, K = 2, one level
+])
+def test_hyres_per_component_shapes(hyde, H, W, p, m, L, r, K, seed):
+    c = make_cube(H, W, p, m=m, seed=seed)
+    _check_hyres_per_component(hyde, c["Y"], L, r, K)
+
+
+def test_hyres_scaled_rejects_per_component(hyde):
+    g = hyde.HyResGrad(32, 64, 64, 2, 8)
+    g.params.lambda_mode = hyde.LAMBDA_PER_COMPONENT
+    s = torch.ones(8, 2, dtype=torch.float32, device="cuda")
+    with pytest.raises(hyde.HydeError):
+        g.forward_scaled(_t(make_cube(64, 64, 32, m=4, seed=1)["Y"]), s)
+
+
 # ------------------------------------------------------ host cube stream
 
 @pytest.mark.parametrize("count", [1, 3, 4])

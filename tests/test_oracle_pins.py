@@ -299,7 +299,90 @@ def test_selection_tie_break_and_layout():
     assert (r, k) == (1, 1) and gap == 0.0
 
 
+def test_per_component_selection_brute_force():
+    """One threshold per kept component: over every rank r and every
+    assignment (k_1..k_r) of grid indices, the minimum total SURE
+    sum_{i<=r} S_i(k_i) + sum_{i>r} S_i(inf) is the one the selection
+    returns, at the rank and indices it returns."""
+    import itertools
+    rng = np.random.default_rng(7)
+    for trial in range(40):
+        r_max, K = 3, 4
+        S = rng.normal(size=(r_max, K)) * 3.0
+        S_inf = rng.normal(size=r_max) * 3.0
+        best, arg = np.inf, None
+        for r in range(1, r_max + 1):
+            for ks in itertools.product(range(K), repeat=r):
+                v = sum(S[i, ks[i]] for i in range(r)) + S_inf[r:].sum()
+                if v < best:
+                    best, arg = v, (r, ks)
+        r_star, k, U, gap = O.select_rank_lambda_per_component(S, S_inf)
+        assert r_star == arg[0]
+        assert tuple(int(x) for x in k[:r_star]) == arg[1]
+        assert abs(U[r_star - 1] - best) < 1e-12 and abs(U.min() - best) < 1e-12
+        assert gap >= 0.0
+        # never above the best shared-threshold total
+        assert U.min() <= O.sure_rank_lambda(S, S_inf).min() + 1e-12
+
+
+def test_per_component_selection_hand_case_and_ties():
+    S = np.array([[5.0, 3.0, 3.0], [1.0, 1.0, 2.0]])
+    S_inf = np.array([4.0, 0.0])
+    r, k, U, gap = O.select_rank_lambda_per_component(S, S_inf)
+    # k = [1, 0] (first minimum of each row); U = [3 + 0, 3 + 1]
+    assert list(k) == [1, 0] and np.array_equal(U, [3.0, 4.0])
+    assert r == 1 and abs(gap - 1.0 / 3.0) < 1e-15
+    # equal totals: the smaller rank wins, gap 0
+    r, k, U, gap = O.select_rank_lambda_per_component(
+        np.array([[2.0, 1.0], [0.0, 0.5]]), np.array([1.0, 0.0]))
+    assert np.array_equal(U, [1.0, 1.0]) and r == 1 and gap == 0.0
+
+
+def test_per_component_reduces_to_shared_when_curves_are_shifts():
+    """If every component's SURE curve is one curve plus a constant, all
+    components share the minimising index and each rank's per-component
+    total is the row minimum of the shared (r, k) table."""
+    rng = np.random.default_rng(8)
+    f = rng.normal(size=9)
+    S = f[None, :] + rng.normal(size=(5, 1)) * 4.0
+    S_inf = rng.normal(size=5) * 4.0
+    T = O.sure_rank_lambda(S, S_inf)
+    r, k, U, _ = O.select_rank_lambda_per_component(S, S_inf)
+    r_sh, k_sh, _, _ = O.select_rank_lambda(S, S_inf)
+    assert np.allclose(U, T.min(axis=1), rtol=0, atol=1e-12)
+    assert r == r_sh and np.all(k == k_sh)
+
+
 # ---------------------------------------------------------------- whole path
+
+def test_per_component_path_is_sum_of_shared_path_increments():
+    """Components enter the estimate independently (the DWT, the
+    threshold and the back-projection act per component and are linear in
+    the kept set), so the per-component estimate is the sum over kept
+    components i of [shared path at rank i+1, lambda_{k_i}] minus [shared
+    path at rank i, lambda_{k_i}], each run of the shared-threshold path."""
+    c = make_cube(48, 40, 16, m=4, seed=24)
+    o = O.hyres(c["Y"], 2, 8, lambda_mode="per_component")
+    r = o["rank"]
+    assert r >= 2 and len(o["lam_comp"]) == r
+    assert np.array_equal(o["lam_comp"], o["lams"][o["k_comp"][:r]])
+    acc = np.zeros_like(o["X"])
+    for i in range(r):
+        lam = float(o["lam_comp"][i])
+        acc += O.hyres(c["Y"], 2, 8, rank=i + 1, lam=lam)["X"]
+        if i > 0:
+            acc -= O.hyres(c["Y"], 2, 8, rank=i, lam=lam)["X"]
+    assert O.rel_l2(o["X"], acc) < 1e-12
+    # the per-component risk estimate is at most the shared one
+    assert o["U"].min() <= o["T"].min() + 1e-9 * abs(o["T"].min())
+
+
+def test_per_component_c0_keeps_planted_rank():
+    c = make_cube(64, 64, 32, m=4, seed=1)
+    o = O.hyres(c["Y"], 2, 8, lambda_mode="per_component")
+    assert o["rank"] == 4
+    assert O.psnr(c["X"], o["X"]) > O.psnr(c["X"], c["Y"]) + 10.0
+
 
 def test_full_rank_zero_lambda_is_identity():
     c = make_cube(30, 45, 10, m=3, seed=21)  # padded to 32 x 48 at L=3
