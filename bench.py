@@ -155,7 +155,8 @@ def _oracle_threads() -> int:
     return os.cpu_count() or 1
 
 
-def oracle_sample_rate(cube, cols: int, runs: int, lambda_mode: str = "shared") -> dict:
+def oracle_sample_rate(cube, cols: int, runs: int, lambda_mode: str = "shared",
+                       threshold_ll: bool = False) -> dict:
     """Time the FP64 oracle on the first ``cols`` columns of the cube."""
     import oracle as O
     w = WORKLOAD
@@ -164,7 +165,8 @@ def oracle_sample_rate(cube, cols: int, runs: int, lambda_mode: str = "shared") 
     ts = []
     for _ in range(runs):
         t0 = time.perf_counter()
-        O.hyres(Ys, w["levels"], w["r_max"], w["n_lambda"], lambda_mode=lambda_mode)
+        O.hyres(Ys, w["levels"], w["r_max"], w["n_lambda"], lambda_mode=lambda_mode,
+                threshold_ll=threshold_ll)
         ts.append(time.perf_counter() - t0)
     return dict(value=vox / 1e6 / statistics.mean(ts), times=ts, voxels=vox,
                 sample=f"oracle on the {w['H']}x{cols}x{w['p']} column slice "
@@ -222,7 +224,7 @@ def run_gb300(args) -> None:
     lmode = {"shared": api.LAMBDA_SHARED,
              "per_component": api.LAMBDA_PER_COMPONENT}[args.lambda_mode]
     h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev, precision=prec,
-                  lambda_mode=lmode)
+                  lambda_mode=lmode, threshold_ll=args.threshold_ll)
     lib = _lib.load()
     launches_per_step = lib.hyde_hyres_kernel_launches(p, H, W, h.params)
     if launches_per_step < 0:
@@ -375,7 +377,7 @@ def run_gb300(args) -> None:
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample_rate(cube, cols=args.cpu_cols, runs=args.cpu_runs,
-                               lambda_mode=args.lambda_mode)
+                               lambda_mode=args.lambda_mode, threshold_ll=args.threshold_ll)
         cpu = {"value": round(s["value"], 3), "unit": UNIT, "cores": _oracle_threads(),
                "kind": "oracle", "sample": s["sample"]}
 
@@ -391,6 +393,9 @@ def run_gb300(args) -> None:
         if args.lambda_mode == "per_component":
             cfg["lambda_mode"] = "per_component (one SURE threshold per kept component)"
             cfg["workload"] += ", per-component thresholds"
+        if args.threshold_ll:
+            cfg["threshold_ll"] = True
+            cfg["workload"] += ", final LL band thresholded too"
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -592,6 +597,8 @@ def main() -> None:
     ap.add_argument("--lambda-mode", choices=("shared", "per_component"), default="shared",
                     help="shared: one SURE threshold for every kept component (headline); "
                          "per_component: each kept component at its own threshold")
+    ap.add_argument("--threshold-ll", action="store_true",
+                    help="soft-threshold (and count in SURE) the final LL band too")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3

@@ -94,7 +94,12 @@ typedef struct {
     int lambda_mode;/* hyde_lambda_mode; HYDE_LAMBDA_SHARED is the default,
                        and the only mode of the scaled (differentiation)
                        entry points                                         */
-    int reserved[2];/* must be zero                                         */
+    int threshold_ll;/* 0 (default): the final LL band is kept as is and
+                       each of its coefficients adds 1 to SURE; 1: it is
+                       soft-thresholded (at the component's threshold) and
+                       counted in SURE like the detail bands. The paper
+                       leaves this open; 0 only for the scaled entry points */
+    int reserved;   /* must be zero                                         */
 } hyde_hyres_params;
 
 /* Outcome of one HyRes run, written by the device into caller memory. */
@@ -243,6 +248,8 @@ hyde_status hyde_sure_table(const float* coef, int batch, int Hp, int Wp,
  * (see hyde_lambda_mode); info then holds r*, k_0 and lambda_{k_0} of the
  * first component, sure_min = U(r*) and sure_gap from the runner-up rank,
  * and the workspace's lam_comp table holds every component's threshold.
+ * With threshold_ll = 1 the sums and counts of S run over all N
+ * coefficients and the final LL band is thresholded as well.
  */
 hyde_status hyde_workspace_size(int p, int H, int W,
                                 const hyde_hyres_params* params,

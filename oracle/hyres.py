@@ -22,8 +22,8 @@ cited HyRes source. The stages written out here, in the order they run, are:
 Readings where the paper is silent (kept identical in the CUDA path):
 periodic DWT boundary; whole-sample symmetric padding at the bottom/right to
 multiples of 2**L, cropped after the inverse transform; the LL band is never
-thresholded; one lambda shared by all kept components (one per component
-as a variant); lambda grid
+thresholded (thresholded too as a variant); one lambda shared by all kept
+components (one per component as a variant); lambda grid
 ``k * sqrt(2 ln N) / (K - 1)``; ties go to the smallest rank, then the smallest
 lambda; regression without intercept or ridge; uncentred Gram matrix.
 
@@ -233,25 +233,30 @@ def lambda_grid(N, K):
     return np.arange(K, dtype=np.float64) * (lam_max / (K - 1))
 
 
-def _detail_mask(Hp, Wp, levels):
+def _detail_mask(Hp, Wp, levels, threshold_ll=False):
+    """Coefficients that are thresholded: the detail bands, and with
+    ``threshold_ll`` the final LL band too."""
     m = np.ones((Hp, Wp), dtype=bool)
-    m[: Hp >> levels, : Wp >> levels] = False
+    if not threshold_ll:
+        m[: Hp >> levels, : Wp >> levels] = False
     return m
 
 
-def sure_table(C, levels, lams):
+def sure_table(C, levels, lams, threshold_ll=False):
     """Stage 7: SURE of each component ``C[i]`` (whitened, unit noise).
 
     For soft-thresholding the detail coefficients at ``lambda`` and keeping LL:
     ``S_i(lambda) = N - 2 #{detail: |c| <= lambda}
                     + sum_detail min(c^2, lambda^2)``
-    (each LL coefficient, kept as is, contributes 1). For dropping the
-    component (estimate zero): ``S_i(inf) = sum_all c^2 - N``. Evaluated by
-    direct comparison against every candidate. Returns ``(S[r][K], S_inf[r])``.
+    (each LL coefficient, kept as is, contributes 1). With ``threshold_ll``
+    (the variant that thresholds every coefficient) the counts and sums run
+    over all N coefficients. For dropping the component (estimate zero):
+    ``S_i(inf) = sum_all c^2 - N``. Evaluated by direct comparison against
+    every candidate. Returns ``(S[r][K], S_inf[r])``.
     """
     r, Hp, Wp = C.shape
     N = Hp * Wp
-    mask = _detail_mask(Hp, Wp, levels)
+    mask = _detail_mask(Hp, Wp, levels, threshold_ll)
     S = np.empty((r, len(lams)))
     S_inf = np.empty(r)
     for i in range(r):
@@ -310,14 +315,16 @@ def select_rank_lambda_per_component(S, S_inf):
 # --------------------------------------------------------------------------
 
 def hyres(Y, levels, r_max, n_lambda=64, *, sigma=None, V=None, rank=None,
-          lam=None, lambda_mode="shared"):
+          lam=None, lambda_mode="shared", threshold_ll=False):
     """Run stages 1-10 on ``Y`` (``float[p][H][W]``).
 
     Optional overrides (for checks of single stages): ``sigma`` (skip stage 2),
     ``V`` (``p x r_max`` basis, skip stage 4), ``rank`` and ``lam`` (skip
     stage 8). ``lambda_mode``: ``"shared"`` (one threshold for every kept
     component) or ``"per_component"`` (``select_rank_lambda_per_component``;
-    ``lam`` may then be a sequence of per-component thresholds). Returns a
+    ``lam`` may then be a sequence of per-component thresholds).
+    ``threshold_ll``: the final LL band is thresholded (and counted in SURE)
+    like the detail bands, instead of kept. Returns a
     dict with the estimate ``X`` (``float64[p][H][W]``) and every
     intermediate; ``lam_comp`` holds the threshold of each kept component.
     """
@@ -343,7 +350,7 @@ def hyres(Y, levels, r_max, n_lambda=64, *, sigma=None, V=None, rank=None,
     C = dwt2(pad_symmetric(Z.reshape(r_max, H, W), Hp, Wp), levels)  # stage 6
     N = Hp * Wp
     lams = lambda_grid(N, n_lambda)
-    S, S_inf = sure_table(C, levels, lams)                      # stage 7
+    S, S_inf = sure_table(C, levels, lams, threshold_ll)        # stage 7
     r_star, k_star, T, gap = select_rank_lambda(S, S_inf)       # stage 8
     lam_star = lams[k_star]
     extra = {}
@@ -359,7 +366,7 @@ def hyres(Y, levels, r_max, n_lambda=64, *, sigma=None, V=None, rank=None,
     if lambda_mode == "shared":
         lam_star = float(lam_star)
         lam_comp = np.full(r_star, lam_star)
-    mask = _detail_mask(Hp, Wp, levels)
+    mask = _detail_mask(Hp, Wp, levels, threshold_ll)
     Ch = C[:r_star].copy()
     for i in range(r_star):                                     # stage 9
         Ch[i][mask] = soft_threshold(Ch[i][mask], lam_comp[i])

@@ -23,7 +23,7 @@ c_size_p = ctypes.POINTER(ctypes.c_size_t)
 class HydeParams(ctypes.Structure):
     _fields_ = [("wavelet", c_int), ("levels", c_int), ("r_max", c_int),
                 ("n_lambda", c_int), ("precision", c_int), ("lambda_mode", c_int),
-                ("reserved", c_int * 2)]
+                ("threshold_ll", c_int), ("reserved", c_int)]
 
 
 class HydeWindow(ctypes.Structure):

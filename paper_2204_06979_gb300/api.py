@@ -62,7 +62,7 @@ def padded_shape(H: int, W: int, levels: int) -> tuple[int, int]:
 
 
 def params(levels: int, r_max: int, n_lambda: int = 64, precision: int = PREC_FP32,
-           lambda_mode: int = LAMBDA_SHARED) -> HydeParams:
+           lambda_mode: int = LAMBDA_SHARED, threshold_ll: bool = False) -> HydeParams:
     p = HydeParams()
     p.wavelet = 2
     p.levels = levels
@@ -70,6 +70,7 @@ def params(levels: int, r_max: int, n_lambda: int = 64, precision: int = PREC_FP
     p.n_lambda = n_lambda
     p.precision = precision
     p.lambda_mode = lambda_mode
+    p.threshold_ll = int(bool(threshold_ll))
     return p
 
 
@@ -188,10 +189,11 @@ class HyRes:
     stream."""
 
     def __init__(self, p: int, H: int, W: int, levels: int, r_max: int, n_lambda: int = 64,
-                 device="cuda", precision: int = PREC_FP32, lambda_mode: int = LAMBDA_SHARED):
+                 device="cuda", precision: int = PREC_FP32, lambda_mode: int = LAMBDA_SHARED,
+                 threshold_ll: bool = False):
         self.lib = _lib.load()
         self.shape = (p, H, W)
-        self.params = params(levels, r_max, n_lambda, precision, lambda_mode)
+        self.params = params(levels, r_max, n_lambda, precision, lambda_mode, threshold_ll)
         sz = ctypes.c_size_t()
         _check(self.lib.hyde_workspace_size(p, H, W, ctypes.byref(self.params), ctypes.byref(sz)),
                "hyde_workspace_size")
@@ -280,12 +282,13 @@ class HyRes:
 
 
 def hyres_denoise(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64,
-                  precision: int = PREC_FP32, lambda_mode: int = LAMBDA_SHARED):
+                  precision: int = PREC_FP32, lambda_mode: int = LAMBDA_SHARED,
+                  threshold_ll: bool = False):
     """One-shot HyRes on ``Y[p, H, W]``; returns ``(X, info dict)``
     (synchronises the current stream to read the info record)."""
     p, H, W = Y.shape
     h = HyRes(p, H, W, levels, r_max, n_lambda, device=Y.device, precision=precision,
-              lambda_mode=lambda_mode)
+              lambda_mode=lambda_mode, threshold_ll=threshold_ll)
     X = h(Y)
     return X, h.result_info()
 
@@ -484,11 +487,12 @@ class HyResWindows:
     ``capture``/``replay`` record it once into a CUDA graph and relaunch it."""
 
     def __init__(self, p, H, W, table, levels, r_max, n_lambda=64, n_slots=64, device="cuda",
-                 lambda_mode: int = LAMBDA_SHARED):
+                 lambda_mode: int = LAMBDA_SHARED, threshold_ll: bool = False):
         from ._lib import HydeWindow
         self.lib = _lib.load()
         self.shape = (p, H, W)
-        self.params = params(levels, r_max, n_lambda, lambda_mode=lambda_mode)
+        self.params = params(levels, r_max, n_lambda, lambda_mode=lambda_mode,
+                             threshold_ll=threshold_ll)
         self.device = torch.device(device)
         rows = [tuple(int(v) for v in r) for r in table]
         self.n_win = len(rows)

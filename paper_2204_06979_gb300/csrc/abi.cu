@@ -89,7 +89,8 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
         return HYDE_ERR_INVALID_ARG;
     if (pr->lambda_mode != HYDE_LAMBDA_SHARED && pr->lambda_mode != HYDE_LAMBDA_PER_COMPONENT)
         return HYDE_ERR_INVALID_ARG;
-    if (pr->reserved[0] || pr->reserved[1]) return HYDE_ERR_INVALID_ARG;
+    if (pr->threshold_ll != 0 && pr->threshold_ll != 1) return HYDE_ERR_INVALID_ARG;
+    if (pr->reserved) return HYDE_ERR_INVALID_ARG;
     if (p < 2 || p > kMaxBandsGram) return HYDE_ERR_SHAPE;
     if (pr->r_max < 1 || pr->r_max > kMaxRank || pr->r_max > p) return HYDE_ERR_SHAPE;
     if (pr->n_lambda < 2 || pr->n_lambda > kMaxLambda) return HYDE_ERR_SHAPE;
@@ -348,9 +349,10 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
                                  void* ws, size_t ws_bytes, cudaStream_t stream,
                                  cudaEvent_t* ev, const float* scale = nullptr) {
     if (!Y || !X || Y == X) return HYDE_ERR_INVALID_ARG;
-    // the scaled forms multiply one shared lambda by their scales
+    // the scaled forms multiply one shared lambda by their detail-level scales
     const bool per_comp = params && params->lambda_mode == HYDE_LAMBDA_PER_COMPONENT;
-    if (per_comp && scale) return HYDE_ERR_INVALID_ARG;
+    const bool all_coef = params && params->threshold_ll == 1;
+    if ((per_comp || all_coef) && scale) return HYDE_ERR_INVALID_ARG;
     HyresLayout L;
     hyde_status st = hyres_layout(p, H, W, params, &L);
     if (st != HYDE_OK) return st;
@@ -406,9 +408,10 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     HYDE_TRY(launch_dwt2(src, coef, r, L.Hp, L.Wp, lev, scratch, stream));
     HYDE_TRY(stage());
     // 7-8. SURE table and (rank, lambda) selection
-    const long long N_det = L.N - (long long)(L.Hp >> lev) * (L.Wp >> lev);
+    const long long N_det =
+        all_coef ? L.N : L.N - (long long)(L.Hp >> lev) * (L.Wp >> lev);
     const double delta = sqrt(2.0 * log((double)L.N)) / (K - 1);
-    HYDE_TRY(launch_sure_hist(coef, r, L.Hp, L.Wp, lev, K, delta, sb, stream));
+    HYDE_TRY(launch_sure_hist(coef, r, L.Hp, L.Wp, lev, K, delta, sb, stream, all_coef));
     float* lam_comp = per_comp ? at<float>(ws, L.pub.lam_comp) : nullptr;
     HYDE_TRY(launch_sure_select(sb, r, K, L.N, N_det, delta, at<double>(ws, L.pub.sure),
                                 at<double>(ws, L.pub.sure_inf), at<double>(ws, L.pub.sure_total),
@@ -417,7 +420,7 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     // 9. soft threshold + inverse DWT of the kept components (into zp, H x W);
     // per-component thresholds are lam_comp[i][l] times *lam_dev = 1
     HYDE_TRY(launch_idwt2(coef, zp, r, L.Hp, L.Wp, H, W, lev, scratch, lam_dev, rank_dev, stream,
-                          per_comp ? lam_comp : scale, lev));
+                          per_comp ? lam_comp : scale, lev, all_coef));
     HYDE_TRY(stage());
     // 10. back-projection and un-whitening
     if (tc_proj)
@@ -529,7 +532,8 @@ static hyde_status back_layout(const HyresLayout& L, int r, int levels, BackLayo
 hyde_status hyde_backward_workspace_size(int p, int H, int W, const hyde_hyres_params* params,
                                          size_t* bytes) {
     if (!bytes) return HYDE_ERR_INVALID_ARG;
-    if (params && params->lambda_mode != HYDE_LAMBDA_SHARED) return HYDE_ERR_INVALID_ARG;
+    if (params && (params->lambda_mode != HYDE_LAMBDA_SHARED || params->threshold_ll != 0))
+        return HYDE_ERR_INVALID_ARG;
     HyresLayout L;
     hyde_status st = hyres_layout(p, H, W, params, &L);
     if (st != HYDE_OK) return st;
@@ -546,7 +550,8 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H, i
                                 cudaStream_t stream) {
     if (!Y || !scale || !dscale || (loss != 0 && loss != 1)) return HYDE_ERR_INVALID_ARG;
     if (loss == 0 && !dX) return HYDE_ERR_INVALID_ARG;
-    if (params && params->lambda_mode != HYDE_LAMBDA_SHARED) return HYDE_ERR_INVALID_ARG;
+    if (params && (params->lambda_mode != HYDE_LAMBDA_SHARED || params->threshold_ll != 0))
+        return HYDE_ERR_INVALID_ARG;
     HyresLayout L;
     hyde_status st = hyres_layout(p, H, W, params, &L);
     if (st != HYDE_OK) return st;
@@ -703,6 +708,7 @@ int hyde_hyres_kernel_launches(int p, int H, int W, const hyde_hyres_params* par
     if (params->lambda_mode != HYDE_LAMBDA_SHARED &&
         params->lambda_mode != HYDE_LAMBDA_PER_COMPONENT)
         return -1;
+    if (params->threshold_ll != 0 && params->threshold_ll != 1) return -1;
     int Hp, Wp;
     if (!padded(H, W, params->levels, &Hp, &Wp)) return -1;
     // gram 2, noise 2, eig 1, weights 1, projection 1, DWT, SURE 2, IDWT, back 1

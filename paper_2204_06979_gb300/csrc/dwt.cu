@@ -196,7 +196,8 @@ idwt_level_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
                   const float* __restrict__ coef, long long coef_bs, int coef_ld, int h,
                   int w, const double* __restrict__ lam, const float* __restrict__ scale,
                   int scale_ld, int lev, const int* __restrict__ rank,
-                  float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo) {
+                  float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo,
+                  int llt) {
     pdl_wait();
     pdl_trigger();
     __shared__ float sLL[TH + 1][TW + 2], sLH[TH + 1][TW + 2];
@@ -219,7 +220,8 @@ idwt_level_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_ld,
         const int j = e / (TW + 1), k = e % (TW + 1);
         const int J = ty0 + j == 0 ? hh - 1 : wrap(ty0 + j - 1, hh);
         const int K = tx0 + k == 0 ? wh - 1 : wrap(tx0 + k - 1, wh);
-        sLL[j][k] = L[(long long)J * ll_ld + K];
+        const float ll = L[(long long)J * ll_ld + K];
+        sLL[j][k] = llt ? soft(ll, lv) : ll;
         const float hl = C[(long long)J * coef_ld + wh + K];
         const float lh = C[(long long)(hh + J) * coef_ld + K];
         const float hhv = C[(long long)(hh + J) * coef_ld + wh + K];
@@ -282,10 +284,12 @@ __device__ __forceinline__ float4 soft4(float4 v, float lam) {
 // One (strip, run) unit of the register-form synthesis for the calling warp.
 // L is the LL band (global memory when LLG, else shared memory), C the
 // component's coefficient image; st0/st1 the warp's staging rows (used when
-// !vout).
+// !vout). llt: the LL band is soft-thresholded at lv too (the final LL band
+// in the variant that thresholds every coefficient).
 template <bool LLG, int ROWS>
 __device__ __forceinline__ void syn_unit(const float* L, int ll_ld, const float* __restrict__ C,
-                                         int coef_ld, int hh, int wh, float lv, int strip,
+                                         int coef_ld, int hh, int wh, float lv, bool llt,
+                                         int strip,
                                          int run, float* O, int out_ld, int ho, int wo,
                                          bool vout, float4* st0, float4* st1, int lane) {
     const int k0 = strip * 128 + 4 * lane;
@@ -302,12 +306,14 @@ __device__ __forceinline__ void syn_unit(const float* L, int ll_ld, const float*
         const long long rl = (long long)J * ll_ld, rt = (long long)J * coef_ld,
                         rb = (long long)(hh + J) * coef_ld;
         v[0] = ldl4(rl + kc);
+        if (llt) v[0] = soft4(v[0], lv);
         v[1] = soft4(__ldg(reinterpret_cast<const float4*>(C + rb + kc)), lv);
         v[2] = soft4(__ldg(reinterpret_cast<const float4*>(C + rt + wh + kc)), lv);
         v[3] = soft4(__ldg(reinterpret_cast<const float4*>(C + rb + wh + kc)), lv);
         float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
         if (lane == 0) {
             e0 = ldl1(rl + km1);
+            if (llt) e0 = soft(e0, lv);
             e1 = soft(__ldg(C + rb + km1), lv);
             e2 = soft(__ldg(C + rt + wh + km1), lv);
             e3 = soft(__ldg(C + rb + wh + km1), lv);
@@ -393,7 +399,7 @@ idwt_level_vec_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_l
                       int w, const double* __restrict__ lam, const float* __restrict__ scale,
                       int scale_ld, int lev, const int* __restrict__ rank,
                       float* __restrict__ out, long long out_bs, int out_ld, int ho, int wo,
-                      int vout) {
+                      int vout, int llt) {
     pdl_wait();
     pdl_trigger();
     __shared__ float4 stage4[kSynWarps][2][64];   // two output rows of 256 floats per warp
@@ -408,7 +414,8 @@ idwt_level_vec_kernel(const float* __restrict__ llsrc, long long ll_bs, int ll_l
     const int u = blockIdx.x * kSynWarps + wid;
     if (u >= nstrips * nruns) return;   // whole warp
     syn_unit<true, kSynRows>(llsrc + (long long)b * ll_bs, ll_ld,
-                             coef + (long long)b * coef_bs, coef_ld, hh, wh, lv, u % nstrips,
+                             coef + (long long)b * coef_bs, coef_ld, hh, wh, lv, llt != 0,
+                             u % nstrips,
                              u / nstrips, out + (long long)b * out_bs, out_ld, ho, wo, vout != 0,
                              stage4[wid][0], stage4[wid][1], lane);
 }
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(kTailSynThreads, 1)
 idwt_tail_kernel(const float* __restrict__ coef, long long coef_bs, int coef_ld, int Hp, int Wp,
                  int lo, int hi, const double* __restrict__ lam, const float* __restrict__ scale,
                  int scale_ld, const int* __restrict__ rank, float* __restrict__ out,
-                 long long out_bs) {
+                 long long out_bs, int llt) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ float4 tail4[];
@@ -514,11 +521,11 @@ idwt_tail_kernel(const float* __restrict__ coef, long long coef_bs, int coef_ld,
         const int units = nstrips * hh;   // one coefficient row per unit: more warps busy
         for (int u = wid; u < units; u += kTailSynThreads / 32) {
             if (l == hi)
-                syn_unit<true, 1>(C, coef_ld, C, coef_ld, hh, wh, lv, u % nstrips, u / nstrips, O, w,
-                               h, w, true, nullptr, nullptr, lane);
+                syn_unit<true, 1>(C, coef_ld, C, coef_ld, hh, wh, lv, llt != 0, u % nstrips,
+                                  u / nstrips, O, w, h, w, true, nullptr, nullptr, lane);
             else
                 syn_unit<false, 1>(((l + 1 - lo) & 1) ? A : B, wh, C, coef_ld, hh, wh, lv,
-                                u % nstrips, u / nstrips, O, w, h, w, true, nullptr, nullptr,
+                                false, u % nstrips, u / nstrips, O, w, h, w, true, nullptr, nullptr,
                                 lane);
         }
         __syncthreads();
@@ -622,7 +629,8 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
 
 hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int Wp, int H,
                          int W, int levels, float* scratch, const double* lam,
-                         const int* rank, cudaStream_t s, const float* scale, int scale_ld) {
+                         const int* rank, cudaStream_t s, const float* scale, int scale_ld,
+                         bool ll_thr) {
     const long long cbs = (long long)Hp * Wp;
     int lo = tail_first_level(Hp, Wp, levels);
     if (lo <= levels) {
@@ -635,7 +643,7 @@ hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int W
             if (ensure_smem_limit((const void*)idwt_tail_kernel, (int)smem) != cudaSuccess)
                 return HYDE_ERR_CUDA;
             launch_pdl(idwt_tail_kernel, batch, kTailSynThreads, smem, s, coef, cbs, Wp, Hp, Wp, lo,
-                       levels, lam, scale, scale_ld, rank, tout, bs);
+                       levels, lam, scale, scale_ld, rank, tout, bs, ll_thr ? 1 : 0);
         }
     }
     for (int lev = (lo <= levels ? lo - 1 : levels); lev >= 1; --lev) {
@@ -669,12 +677,13 @@ hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp, int W
             const dim3 vgrid((unsigned)((units + kSynWarps - 1) / kSynWarps), batch);
             launch_pdl(idwt_level_vec_kernel, vgrid, kSynThreads, 0, s, lp, lbs, lld, coef, cbs,
                        Wp, h, w, lam, scale, scale_ld, lev, rank, op, obs, old, ho, wo,
-                       vout ? 1 : 0);
+                       vout ? 1 : 0, (ll_thr && lev == levels) ? 1 : 0);
             continue;
         }
         dim3 grid((w / 2 + TW - 1) / TW, (h / 2 + TH - 1) / TH, batch);
         launch_pdl(idwt_level_kernel, grid, kThreads, 0, s, lp, lbs, lld, coef, cbs, Wp, h, w,
-                   lam, scale, scale_ld, lev, rank, op, obs, old, ho, wo);
+                   lam, scale, scale_ld, lev, rank, op, obs, old, ho, wo,
+                   (ll_thr && lev == levels) ? 1 : 0);
     }
     return cuda_status(cudaGetLastError());
 }

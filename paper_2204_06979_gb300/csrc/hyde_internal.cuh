@@ -221,11 +221,13 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp,
                         int Wp, int levels, float* scratch, cudaStream_t s);
 // Synthesis with optional soft threshold of detail coefficients at *lam
 // (times scale[image * scale_ld + level - 1] when scale != NULL) and an
-// optional rank limit (*rank images are processed; NULL = all).
+// optional rank limit (*rank images are processed; NULL = all). ll_thr: the
+// final LL band is thresholded too, at the last level's threshold.
 hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp,
                          int Wp, int H, int W, int levels, float* scratch,
                          const double* lam, const int* rank, cudaStream_t s,
-                         const float* scale = nullptr, int scale_ld = 0);
+                         const float* scale = nullptr, int scale_ld = 0,
+                         bool ll_thr = false);
 
 // ------------------------------------------------- differentiation form
 // acc[i][l] (double, zeroed by the caller) += per-(component, level) sums over
@@ -261,9 +263,11 @@ struct SureBufs {
     long long* sint;        // [2][batch][K] integer prefix rows (selection kernel)
 };
 size_t sure_accum_bytes(int batch, int K);
+// all_coef: every coefficient is binned (the final LL band too)
 hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp,
                              int levels, int K, double delta,
-                             const SureBufs& b, cudaStream_t s);
+                             const SureBufs& b, cudaStream_t s,
+                             bool all_coef = false);
 // Builds S, S_inf (and, when T != NULL, the (rank, lambda) table plus the
 // selection written to info/rank_out/lam_out). With lam_comp != NULL (and T
 // != NULL) the selection takes one threshold per component instead: the

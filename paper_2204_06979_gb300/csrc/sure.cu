@@ -404,7 +404,7 @@ size_t sure_accum_bytes(int batch, int K) {
 }
 
 hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int levels, int K,
-                             double delta, const SureBufs& b, cudaStream_t s) {
+                             double delta, const SureBufs& b, cudaStream_t s, bool all_coef) {
     const int sms = device_sm_count();
     if (sms <= 0) return HYDE_ERR_CUDA;
     if (K < 1 || !(delta > 0.0)) return HYDE_ERR_INVALID_ARG;
@@ -433,9 +433,11 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int l
     if (ensure_smem_limit((const void*)sure_hist_kernel, (int)smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
     dim3 grid(per_comp, batch);
-    launch_pdl(sure_hist_kernel, grid, kHistThreads, smem, s, coef, Hp, Wp, Hp >> levels,
-               Wp >> levels, K, inv_delta, (float)std::ldexp(1.0, sh), std::ldexp(1.0, -sh),
-               (int)rows, b.counts, b.sums, b.sum_all);
+    // an empty excluded band (0 x 0) bins every coefficient
+    const int hl = all_coef ? 0 : Hp >> levels, wl = all_coef ? 0 : Wp >> levels;
+    launch_pdl(sure_hist_kernel, grid, kHistThreads, smem, s, coef, Hp, Wp, hl, wl, K, inv_delta,
+               (float)std::ldexp(1.0, sh), std::ldexp(1.0, -sh), (int)rows, b.counts, b.sums,
+               b.sum_all);
     return cuda_status(cudaGetLastError());
 }
 

@@ -97,9 +97,12 @@ def test_bad_arguments_rejected_on_host(lib):
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 2
     p.r_max, p.n_lambda = 8, 1
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 2
-    p.n_lambda, p.reserved[0] = 64, 1
+    p.n_lambda, p.reserved = 64, 1
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
-    p.reserved[0] = 0
+    p.reserved = 0
+    p.threshold_ll = 2
+    assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
+    p.threshold_ll = 0
     assert lib.hyde_workspace_size(1, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 2
     p.lambda_mode = 2
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
@@ -116,9 +119,9 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
 
 
 def test_lambda_mode_params(lib):
-    """Per-component thresholds are rejected, before any device query, by the
-    scaled (differentiation) entry points, and an unknown mode by every
-    entry point."""
+    """Per-component thresholds and the thresholded LL band are rejected,
+    before any device query, by the scaled (differentiation) entry points,
+    and an unknown mode by every entry point."""
     from paper_2204_06979_gb300 import api
     comp = api.params(3, 8, 64, lambda_mode=api.LAMBDA_PER_COMPONENT)
     bad = api.params(3, 8, 64, lambda_mode=5)
@@ -128,3 +131,8 @@ def test_lambda_mode_params(lib):
                                          1 << 30, None) == 1
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(bad), ctypes.byref(sz)) == 1
     assert lib.hyde_hyres_kernel_launches(32, 64, 64, ctypes.byref(bad)) == -1
+    # the final LL band thresholded too: likewise only outside the scaled forms
+    ll = api.params(3, 8, 64, threshold_ll=True)
+    assert lib.hyde_backward_workspace_size(32, 64, 64, ctypes.byref(ll), ctypes.byref(sz)) == 1
+    assert lib.hyde_hyres_denoise_scaled(1, 2, 32, 64, 64, ctypes.byref(ll), 3, None, 4,
+                                         1 << 30, None) == 1

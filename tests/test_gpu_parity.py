@@ -151,10 +151,10 @@ def test_sure_table_matches_oracle(hyde):
 
 # ------------------------------------------------------------ whole path
 
-def _check_hyres(hyde, Y, L, r_max, K=64, tol=REL_L2_PATH):
-    o = O.hyres(Y, L, r_max, K)
+def _check_hyres(hyde, Y, L, r_max, K=64, tol=REL_L2_PATH, threshold_ll=False):
+    o = O.hyres(Y, L, r_max, K, threshold_ll=threshold_ll)
     p, H, W = Y.shape
-    h = hyde.HyRes(p, H, W, L, r_max, K)
+    h = hyde.HyRes(p, H, W, L, r_max, K, threshold_ll=threshold_ll)
     X = h(_t(Y)).cpu().numpy()
     info = h.result_info()
     mid = h.intermediates()
@@ -223,7 +223,7 @@ def test_hyres_rejects_bad_shapes(hyde):
 
 # ------------------------------------------- per-component thresholds
 
-def _check_hyres_per_component(hyde, Y, L, r_max, K=64):
+def _check_hyres_per_component(hyde, Y, L, r_max, K=64, threshold_ll=False):
     """One threshold per kept component. The S table on the GPU may differ
     from the oracle's by a coefficient counted on the other side of a grid
     point (bound of test_sure_table_matches_oracle), so where the oracle's
@@ -231,9 +231,10 @@ def _check_hyres_per_component(hyde, Y, L, r_max, K=64):
     take the runner-up: its choice must then be a minimiser of the oracle's
     table within that bound, and its estimate must match the oracle run at
     the GPU's choice. Where the choice is clear it must be identical."""
-    o = O.hyres(Y, L, r_max, K, lambda_mode="per_component")
+    o = O.hyres(Y, L, r_max, K, lambda_mode="per_component", threshold_ll=threshold_ll)
     p, H, W = Y.shape
-    h = hyde.HyRes(p, H, W, L, r_max, K, lambda_mode=hyde.LAMBDA_PER_COMPONENT)
+    h = hyde.HyRes(p, H, W, L, r_max, K, lambda_mode=hyde.LAMBDA_PER_COMPONENT,
+                   threshold_ll=threshold_ll)
     X = h(_t(Y)).cpu().numpy()
     info = h.result_info()
     lam_comp = h.intermediates()["lam_comp"].cpu().numpy().astype(np.float64)
@@ -259,7 +260,8 @@ def _check_hyres_per_component(hyde, Y, L, r_max, K=64):
     if r == o["rank"] and np.array_equal(k_gpu, o["k_comp"][:r]):
         ref = o["X"]
     else:
-        ref = O.hyres(Y, L, r_max, K, rank=r, lam=lams[k_gpu], lambda_mode="per_component")["X"]
+        ref = O.hyres(Y, L, r_max, K, rank=r, lam=lams[k_gpu], lambda_mode="per_component",
+                      threshold_ll=threshold_ll)["X"]
     err = O.rel_l2(X, ref)
     assert err < REL_L2_PATH, err
     return o, info, k_gpu
@@ -281,6 +283,26 @@ def test_hyres_per_component_c0(hyde):
 def test_hyres_per_component_shapes(hyde, H, W, p, m, L, r, K, seed):
     c = make_cube(H, W, p, m=m, seed=seed)
     _check_hyres_per_component(hyde, c["Y"], L, r, K)
+
+
+# ------------------------------------- final LL band thresholded too
+
+@pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
+    (64, 64, 32, 4, 2, 8, 64, 1),       # C0: level 2 (with the LL band) in the fused tail
+    (77, 131, 24, 3, 3, 6, 64, 31),     # ragged: the scalar level kernel takes the LL band
+    (40, 48, 12, 2, 1, 12, 16, 32),     # one level, float4 rows: the register-form kernel
+    (349, 256, 144, 12, 5, 20, 64, 2),  # full-cube rows: levels 3-5 fused
+    (30, 30, 6, 2, 1, 1, 2, 33),        # one level, unaligned rows, r_max = 1, K = 2
+])
+def test_hyres_threshold_ll(hyde, H, W, p, m, L, r, K, seed):
+    """Every coefficient thresholded (and counted in SURE), the LL band too,
+    with the shared threshold and with one per component."""
+    c = make_cube(H, W, p, m=m, seed=seed)
+    o, X, info, mid = _check_hyres(hyde, c["Y"], L, r, K, threshold_ll=True)
+    # the variant changes the table: it is not the default one
+    o0 = O.hyres(c["Y"], L, r, K)
+    assert not np.allclose(o["S"], o0["S"])
+    _check_hyres_per_component(hyde, c["Y"], L, r, K, threshold_ll=True)
 
 
 def test_hyres_scaled_rejects_per_component(hyde):

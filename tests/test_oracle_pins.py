@@ -241,11 +241,12 @@ def test_noise_recovers_planted_sigma():
 
 # ---------------------------------------------------------------- SURE
 
-def test_sure_is_unbiased_monte_carlo():
+@pytest.mark.parametrize("threshold_ll", [False, True])
+def test_sure_is_unbiased_monte_carlo(threshold_ll):
     """With the basis and noise levels fixed independently of the noise,
-    SURE(r, lambda) is an unbiased estimate of the whitened squared error.
-    64 noise draws; every (r, k) cell within 4.5 standard errors and 90 %
-    within 2.5."""
+    SURE(r, lambda) is an unbiased estimate of the whitened squared error,
+    with the LL band kept or thresholded too. 64 noise draws; every (r, k)
+    cell within 4.5 standard errors and 90 % within 2.5."""
     H, W, p, L, K = 32, 32, 12, 2, 16
     base = make_cube(H, W, p, m=3, seed=11)
     Xc = base["X"].astype(np.float64)
@@ -255,13 +256,14 @@ def test_sure_is_unbiased_monte_carlo():
     rng = np.random.default_rng(12345)
     lams = O.lambda_grid(H * W, K)
     det_mask = np.ones((H, W), bool)
-    det_mask[: H >> L, : W >> L] = False
+    if not threshold_ll:
+        det_mask[: H >> L, : W >> L] = False
     C_clean = O.dwt2((V.T @ Xw).reshape(p, H, W), L)
     sure_vals, loss_vals = [], []
     for _ in range(64):
         Yw = Xw + rng.standard_normal(Xw.shape)
         C = O.dwt2((V.T @ Yw).reshape(p, H, W), L)
-        S, S_inf = O.sure_table(C, L, lams)
+        S, S_inf = O.sure_table(C, L, lams, threshold_ll)
         T = O.sure_rank_lambda(S, S_inf)
         loss = np.empty_like(T)
         for r in range(1, p + 1):
@@ -288,6 +290,35 @@ def test_sure_single_component_closed_form():
     # lam = 3: 4 - 2*3 + (0.25 + 4 + 2.25) = 4.5
     assert np.allclose(S[0], [4.0, 4.25, 4.5], atol=1e-15)
     assert abs(S_inf[0] - (25 + 0.25 + 4 + 2.25 - 4)) < 1e-14
+
+
+def test_sure_threshold_all_closed_form():
+    """The hand case above with the LL coefficient thresholded too."""
+    C = np.zeros((1, 2, 2))
+    C[0] = [[5.0, 0.5], [-2.0, 1.5]]
+    S, S_inf = O.sure_table(C, 1, np.array([0.0, 1.0, 3.0]), threshold_ll=True)
+    # lam = 1: 4 - 2*1 + (1 + 0.25 + 1 + 1) = 5.25
+    # lam = 3: 4 - 2*3 + (9 + 0.25 + 4 + 2.25) = 13.5
+    assert np.allclose(S[0], [4.0, 5.25, 13.5], atol=1e-15)
+    assert abs(S_inf[0] - (25 + 0.25 + 4 + 2.25 - 4)) < 1e-14
+
+
+@pytest.mark.parametrize("threshold_ll", [False, True])
+def test_full_rank_residual_is_clipped_energy(threshold_ll):
+    """At full rank on an unpadded cube (sides multiples of 2^L) the
+    whitening, the eigenbasis and the DWT are invertible and the last two
+    orthogonal, so the whitened residual energy of the estimate is the energy
+    the soft threshold removes: sum over the thresholded coefficients of
+    min(|c|, lambda)^2 (the LL band among them only with threshold_ll)."""
+    c = make_cube(32, 48, 10, m=3, seed=25)
+    lam = 1.3
+    o = O.hyres(c["Y"], 3, 10, rank=10, lam=lam, threshold_ll=threshold_ll)
+    Rw = (c["Y"].astype(np.float64) - o["X"]) / o["sigma"][:, None, None]
+    C = o["C"]
+    clipped = np.minimum(np.abs(C), lam) ** 2
+    if not threshold_ll:
+        clipped[:, : 32 >> 3, : 48 >> 3] = 0.0
+    assert abs(np.sum(Rw ** 2) / np.sum(clipped) - 1.0) < 1e-10
 
 
 def test_selection_tie_break_and_layout():
