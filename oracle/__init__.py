@@ -14,7 +14,8 @@ from .hyres import (  # noqa: F401
     db2_filters, gram, noise_est_regression, noise_est_schur, noise_est_lstsq,
     whiten_gram, eig_desc, padded_shape, pad_symmetric, dwt2, idwt2,
     soft_threshold, lambda_grid, sure_table, sure_rank_lambda,
-    select_rank_lambda, select_rank_lambda_per_component, hyres,
+    select_rank_lambda, select_rank_lambda_per_component, sure_table_levels,
+    select_rank_lambda_per_level, hyres,
     rel_l2, psnr, sam, level_map, hyres_scaled, hyres_scaled_grad, mse_loss,
     sure_loss_scaled,
 )

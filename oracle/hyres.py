@@ -270,6 +270,38 @@ def sure_table(C, levels, lams, threshold_ll=False):
     return S, S_inf
 
 
+def _level_groups(Hp, Wp, levels, threshold_ll):
+    """Group (1..L) of every Mallat position for per-level thresholds: the
+    detail bands of level l; the final LL band is group 0 (kept), or joins
+    group L when it is thresholded too."""
+    lev = level_map(Hp, Wp, levels)
+    if threshold_ll:
+        lev[lev == 0] = levels
+    return lev
+
+
+def sure_table_levels(C, levels, lams, threshold_ll=False):
+    """Stage 7 split by level: for component ``i`` and group ``l`` (the
+    detail coefficients of level l, plus the final LL band in group L with
+    ``threshold_ll``), the SURE of soft-thresholding that group at
+    ``lambda``: ``S_il(lambda) = N_l - 2 #{group: |c| <= lambda}
+    + sum_group min(c^2, lambda^2)``, N_l the group's size. A component
+    thresholded at ``lambda_l`` on group l has SURE ``n_kept + sum_l
+    S_il(lambda_l)``, n_kept the number of coefficients kept as they are
+    (the LL band unless ``threshold_ll``). Returns ``float[r][L][K]``."""
+    r, Hp, Wp = C.shape
+    lev = _level_groups(Hp, Wp, levels, threshold_ll)
+    out = np.empty((r, levels, len(lams)))
+    for i in range(r):
+        for l in range(1, levels + 1):
+            g = np.abs(C[i][lev == l])
+            g2 = g * g
+            for k, lam in enumerate(lams):
+                out[i, l - 1, k] = (g.size - 2.0 * np.count_nonzero(g <= lam)
+                                    + np.sum(np.minimum(g2, lam * lam)))
+    return out
+
+
 def sure_rank_lambda(S, S_inf):
     """Total SURE of keeping components ``1..r`` thresholded at ``lambda_k``
     and dropping ``r+1..r_max``: ``T[r-1][k] = sum_{i<=r} S_i(lambda_k) +
@@ -310,6 +342,24 @@ def select_rank_lambda_per_component(S, S_inf):
     return r_star, k, U, gap
 
 
+def select_rank_lambda_per_level(S_lev, S_inf, n_kept):
+    """Stage 8 with one threshold per kept component and level: group
+    ``(i, l)`` takes ``k_il``, the first minimiser of ``S_il(lambda_k)``;
+    component ``i`` then has SURE ``S*_i = n_kept + sum_l S_il(lambda_{k_il})``
+    and the rank minimises ``U[r-1] = sum_{i<=r} S*_i + sum_{r<i<=r_max}
+    S_i(inf)`` (first minimum). Returns ``(r*, k[r_max][L], U, gap)``."""
+    S_lev = np.asarray(S_lev, dtype=np.float64)
+    r_max = S_lev.shape[0]
+    k = np.argmin(S_lev, axis=2)
+    best = np.take_along_axis(S_lev, k[:, :, None], axis=2)[:, :, 0]
+    comp = n_kept + best.sum(axis=1)
+    U = np.array([np.sum(comp[: r + 1]) + np.sum(S_inf[r + 1:]) for r in range(r_max)])
+    r_star = int(np.argmin(U)) + 1
+    vals = np.sort(U)
+    gap = (vals[1] - vals[0]) / max(abs(vals[0]), 1e-300) if vals.size > 1 else np.inf
+    return r_star, k, U, gap
+
+
 # --------------------------------------------------------------------------
 # The whole path
 # --------------------------------------------------------------------------
@@ -321,15 +371,18 @@ def hyres(Y, levels, r_max, n_lambda=64, *, sigma=None, V=None, rank=None,
     Optional overrides (for checks of single stages): ``sigma`` (skip stage 2),
     ``V`` (``p x r_max`` basis, skip stage 4), ``rank`` and ``lam`` (skip
     stage 8). ``lambda_mode``: ``"shared"`` (one threshold for every kept
-    component) or ``"per_component"`` (``select_rank_lambda_per_component``;
-    ``lam`` may then be a sequence of per-component thresholds).
+    component), ``"per_component"`` (``select_rank_lambda_per_component``;
+    ``lam`` may then be a sequence of per-component thresholds) or
+    ``"per_level"`` (``select_rank_lambda_per_level``; ``lam`` may then be a
+    ``[rank][levels]`` table).
     ``threshold_ll``: the final LL band is thresholded (and counted in SURE)
     like the detail bands, instead of kept. Returns a
     dict with the estimate ``X`` (``float64[p][H][W]``) and every
-    intermediate; ``lam_comp`` holds the threshold of each kept component.
+    intermediate; ``lam_comp`` holds the threshold of each kept component
+    (``[rank][levels]`` in the per-level mode).
     """
-    if lambda_mode not in ("shared", "per_component"):
-        raise ValueError("lambda_mode must be 'shared' or 'per_component'")
+    if lambda_mode not in ("shared", "per_component", "per_level"):
+        raise ValueError("lambda_mode must be 'shared', 'per_component' or 'per_level'")
     Y = np.asarray(Y)
     p, H, W = Y.shape
     n = H * W
@@ -359,17 +412,32 @@ def hyres(Y, levels, r_max, n_lambda=64, *, sigma=None, V=None, rank=None,
         k_star, lam_star = int(k_comp[0]), lams[k_comp[0]]
         lam_comp = lams[k_comp[:r_star]]
         extra = dict(k_comp=k_comp, U=U)
+    if lambda_mode == "per_level":
+        n_kept = 0 if threshold_ll else (Hp >> levels) * (Wp >> levels)
+        S_lev = sure_table_levels(C, levels, lams, threshold_ll)
+        r_star, k_lev, U, gap = select_rank_lambda_per_level(S_lev, S_inf, n_kept)
+        k_star, lam_star = int(k_lev[0, 0]), lams[k_lev[0, 0]]
+        lam_comp = lams[k_lev[:r_star]]
+        extra = dict(k_lev=k_lev, U=U, S_lev=S_lev)
     if rank is not None:
         r_star, k_star = int(rank), -1
         lam_star = lam
-        lam_comp = np.broadcast_to(np.asarray(lam, dtype=np.float64), (r_star,))
+        shape = (r_star, levels) if lambda_mode == "per_level" else (r_star,)
+        lam_comp = np.broadcast_to(np.asarray(lam, dtype=np.float64), shape)
     if lambda_mode == "shared":
         lam_star = float(lam_star)
         lam_comp = np.full(r_star, lam_star)
-    mask = _detail_mask(Hp, Wp, levels, threshold_ll)
+    # threshold of component i on level l (the LL band: group 0, kept, or
+    # group L with threshold_ll)
+    lam_il = np.asarray(lam_comp, dtype=np.float64)
+    if lam_il.ndim == 1:
+        lam_il = np.repeat(lam_il[:, None], levels, axis=1)
+    groups = _level_groups(Hp, Wp, levels, threshold_ll)
     Ch = C[:r_star].copy()
     for i in range(r_star):                                     # stage 9
-        Ch[i][mask] = soft_threshold(Ch[i][mask], lam_comp[i])
+        for l in range(1, levels + 1):
+            sel = groups == l
+            Ch[i][sel] = soft_threshold(Ch[i][sel], lam_il[i, l - 1])
     Zh = idwt2(Ch, levels)[:, :H, :W].reshape(r_star, n)
     Xh = sigma[:, None] * (V[:, :r_star] @ Zh)                  # stage 10
     return dict(X=Xh.reshape(p, H, W), rank=r_star, k=k_star, lam=lam_star,

@@ -384,7 +384,135 @@ def test_per_component_reduces_to_shared_when_curves_are_shifts():
     assert r == r_sh and np.all(k == k_sh)
 
 
+@pytest.mark.parametrize("threshold_ll", [False, True])
+def test_sure_levels_sum_to_component_table(threshold_ll):
+    """At one threshold for every level the groups add up to the
+    component's SURE: n_kept + sum_l S_il(lambda) = S_i(lambda)."""
+    rng = np.random.default_rng(9)
+    C = rng.normal(size=(3, 24, 40)) * 2.0
+    lams = O.lambda_grid(24 * 40, 8)
+    S, _ = O.sure_table(C, 3, lams, threshold_ll)
+    S_lev = O.sure_table_levels(C, 3, lams, threshold_ll)
+    n_kept = 0 if threshold_ll else 3 * 5
+    assert np.allclose(n_kept + S_lev.sum(axis=1), S, rtol=0, atol=1e-9)
+
+
+def test_sure_levels_single_level_image():
+    """Only the three level-2 rectangles of a 32 x 48, L = 3 layout (cut
+    here by hand) hold nonzero values: the other groups contain zeros only,
+    so S_il = N_l - 2 N_l = -3 (H/2^l)(W/2^l); group 2 is the direct
+    formula on the hand-cut values."""
+    Hp, Wp, L = 32, 48, 3
+    rng = np.random.default_rng(10)
+    C = np.zeros((1, Hp, Wp))
+    h1, w1, h2, w2 = Hp >> 1, Wp >> 1, Hp >> 2, Wp >> 2
+    vals = []
+    for ys, xs in ((slice(0, h2), slice(w2, w1)), (slice(h2, h1), slice(0, w2)),
+                   (slice(h2, h1), slice(w2, w1))):
+        block = rng.normal(size=(h2, w2)) * 3.0
+        C[0, ys, xs] = block
+        vals.append(block.ravel())
+    vals = np.abs(np.concatenate(vals))
+    lams = np.array([0.0, 0.5, 1.7, 4.0])
+    S_lev = O.sure_table_levels(C, L, lams)
+    for l in (1, 3):
+        assert np.all(S_lev[0, l - 1] == -3.0 * (Hp >> l) * (Wp >> l))
+    want = [vals.size - 2.0 * np.sum(vals <= t) + np.sum(np.minimum(vals ** 2, t * t))
+            for t in lams]
+    assert np.allclose(S_lev[0, 1], want, rtol=0, atol=1e-10)
+
+
+def test_per_level_selection_brute_force():
+    """Over every rank and every assignment of grid indices to the kept
+    (component, level) groups, the minimum total SURE is the one the
+    per-level selection returns."""
+    import itertools
+    rng = np.random.default_rng(11)
+    for trial in range(25):
+        r_max, L, K, n_kept = 2, 2, 3, 5.0
+        S_lev = rng.normal(size=(r_max, L, K)) * 3.0
+        S_inf = rng.normal(size=r_max) * 6.0
+        best, arg = np.inf, None
+        for r in range(1, r_max + 1):
+            for ks in itertools.product(range(K), repeat=r * L):
+                v = sum(n_kept + sum(S_lev[i, l, ks[i * L + l]] for l in range(L))
+                        for i in range(r)) + S_inf[r:].sum()
+                if v < best:
+                    best, arg = v, (r, ks)
+        r_star, k, U, gap = O.select_rank_lambda_per_level(S_lev, S_inf, n_kept)
+        assert r_star == arg[0]
+        assert tuple(int(x) for x in k[:r_star].ravel()) == arg[1]
+        assert abs(U.min() - best) < 1e-12 and gap >= 0.0
+
+
+@pytest.mark.parametrize("threshold_ll", [False, True])
+def test_sure_levels_unbiased_monte_carlo(threshold_ll):
+    """With a fixed threshold for each (component, level) the sum of the
+    group SUREs estimates the whitened squared error without bias (the
+    loss thresholds the level rectangles cut by hand)."""
+    H, W, p, L, K = 32, 32, 6, 2, 8
+    base = make_cube(H, W, p, m=2, seed=13)
+    Xw = base["X"].astype(np.float64).reshape(p, -1) / base["sigma"][:, None]
+    _, V = O.eig_desc(Xw @ Xw.T)
+    lams = O.lambda_grid(H * W, K)
+    rng = np.random.default_rng(14)
+    kk = rng.integers(0, K, size=(p, L))
+    grp = np.ones((H, W), dtype=int)
+    grp[: H >> 1, : W >> 1] = 2
+    grp[: H >> 2, : W >> 2] = 2 if threshold_ll else 0
+    n_kept = 0 if threshold_ll else (H >> 2) * (W >> 2)
+    C_clean = O.dwt2((V.T @ Xw).reshape(p, H, W), L)
+    diffs = []
+    for _ in range(64):
+        C = O.dwt2((V.T @ (Xw + rng.standard_normal(Xw.shape))).reshape(p, H, W), L)
+        S_lev = O.sure_table_levels(C, L, lams, threshold_ll)
+        sure = sum(n_kept + sum(S_lev[i, l, kk[i, l]] for l in range(L)) for i in range(p))
+        Ch = C.copy()
+        for i in range(p):
+            for l in (1, 2):
+                m = grp == l
+                Ch[i][m] = O.soft_threshold(Ch[i][m], lams[kk[i, l - 1]])
+        diffs.append(sure - np.sum((Ch - C_clean) ** 2))
+    diffs = np.array(diffs)
+    z = diffs.mean() / (diffs.std(ddof=1) / np.sqrt(diffs.size))
+    assert abs(z) < 4.0
+
+
 # ---------------------------------------------------------------- whole path
+
+@pytest.mark.parametrize("threshold_ll", [False, True])
+def test_full_rank_residual_per_level_thresholds(threshold_ll):
+    """Per-level thresholds at full rank on an unpadded cube: the whitened
+    residual energy is sum_{i,l} sum_{group l} min(|c|, lambda_il)^2."""
+    c = make_cube(32, 48, 10, m=3, seed=26)
+    lam = np.linspace(0.4, 2.2, 10 * 3).reshape(10, 3)
+    o = O.hyres(c["Y"], 3, 10, rank=10, lam=lam, lambda_mode="per_level",
+                threshold_ll=threshold_ll)
+    Rw = (c["Y"].astype(np.float64) - o["X"]) / o["sigma"][:, None, None]
+    C = o["C"]
+    grp = np.zeros((32, 48), dtype=int)
+    for l in (1, 2, 3):
+        grp[: 32 >> (l - 1), : 48 >> (l - 1)] = l
+    grp[: 32 >> 3, : 48 >> 3] = 3 if threshold_ll else 0
+    clipped = 0.0
+    for i in range(10):
+        for l in (1, 2, 3):
+            v = np.abs(C[i][grp == l])
+            clipped += np.sum(np.minimum(v, lam[i, l - 1]) ** 2)
+    assert abs(np.sum(Rw ** 2) / clipped - 1.0) < 1e-10
+
+
+def test_per_level_c0_nested_choices():
+    """Per-level choices contain the per-component ones, which contain the
+    shared one: the minimum SURE can only go down; the planted rank holds."""
+    c = make_cube(64, 64, 32, m=4, seed=1)
+    o = O.hyres(c["Y"], 2, 8, lambda_mode="per_level")
+    oc = O.hyres(c["Y"], 2, 8, lambda_mode="per_component")
+    assert o["rank"] == 4
+    assert o["U"].min() <= oc["U"].min() + 1e-9 <= o["T"].min() + 2e-9
+    assert o["lam_comp"].shape == (4, 2)
+    assert O.psnr(c["X"], o["X"]) > O.psnr(c["X"], c["Y"]) + 10.0
+
 
 def test_per_component_path_is_sum_of_shared_path_increments():
     """Components enter the estimate independently (the DWT, the
