@@ -221,8 +221,8 @@ def run_gb300(args) -> None:
     Xd = torch.empty_like(Yd)
     prec = {"fp32": api.PREC_FP32, "bf16x3": api.PREC_BF16X3,
             "bf16x3_all": api.PREC_BF16X3_ALL}[args.precision]
-    lmode = {"shared": api.LAMBDA_SHARED,
-             "per_component": api.LAMBDA_PER_COMPONENT}[args.lambda_mode]
+    lmode = {"shared": api.LAMBDA_SHARED, "per_component": api.LAMBDA_PER_COMPONENT,
+             "per_level": api.LAMBDA_PER_LEVEL}[args.lambda_mode]
     h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev, precision=prec,
                   lambda_mode=lmode, threshold_ll=args.threshold_ll)
     lib = _lib.load()
@@ -393,6 +393,9 @@ def run_gb300(args) -> None:
         if args.lambda_mode == "per_component":
             cfg["lambda_mode"] = "per_component (one SURE threshold per kept component)"
             cfg["workload"] += ", per-component thresholds"
+        elif args.lambda_mode == "per_level":
+            cfg["lambda_mode"] = "per_level (one SURE threshold per kept component and level)"
+            cfg["workload"] += ", per-level thresholds"
         if args.threshold_ll:
             cfg["threshold_ll"] = True
             cfg["workload"] += ", final LL band thresholded too"
@@ -594,9 +597,11 @@ def main() -> None:
     ap.add_argument("--precision", choices=("fp32", "bf16x3", "bf16x3_all"), default="fp32",
                     help="fp32: plain form (headline); bf16x3: Gram on the tensor cores; "
                          "bf16x3_all: the projections there too")
-    ap.add_argument("--lambda-mode", choices=("shared", "per_component"), default="shared",
+    ap.add_argument("--lambda-mode", choices=("shared", "per_component", "per_level"),
+                    default="shared",
                     help="shared: one SURE threshold for every kept component (headline); "
-                         "per_component: each kept component at its own threshold")
+                         "per_component: each kept component at its own threshold; "
+                         "per_level: each kept component and level at its own threshold")
     ap.add_argument("--threshold-ll", action="store_true",
                     help="soft-threshold (and count in SURE) the final LL band too")
     args = ap.parse_args()

@@ -75,12 +75,21 @@ typedef enum {
 typedef enum {
     HYDE_LAMBDA_SHARED = 0,        /* one lambda_{k*} for every kept component:
                                       (r*, k*) = argmin over the (r, k) table */
-    HYDE_LAMBDA_PER_COMPONENT = 1  /* component i thresholded at its own
+    HYDE_LAMBDA_PER_COMPONENT = 1, /* component i thresholded at its own
                                       lambda_{k_i}, k_i = argmin_k S_i(lambda_k)
                                       (first minimum); r* = argmin_r U(r) with
                                       U(r) = sum_{i<=r} S_i(lambda_{k_i})
                                              + sum_{r<i<=r_max} S_i(inf)
                                       (first minimum)                         */
+    HYDE_LAMBDA_PER_LEVEL = 2      /* the detail bands of level l of component
+                                      i thresholded at their own lambda_{k_il},
+                                      k_il = argmin_k S_il(lambda_k), S_il the
+                                      SURE of that group alone (the final LL
+                                      band joins group L when threshold_ll);
+                                      S*_i = (kept coefficients) + sum_l
+                                      S_il(lambda_{k_il}) replaces S_i above.
+                                      Needs 256 * levels * n_lambda bytes of
+                                      shared memory <= 200 KiB                */
 } hyde_lambda_mode;
 
 /* Parameters of one HyRes run. */
@@ -122,14 +131,19 @@ typedef struct {
     size_t evals;      /* double[r_max]  leading eigenvalues of D^-1 R D^-1  */
     size_t V;          /* double[p][r_max] eigenvectors, row b = band b      */
     size_t coef;       /* float[r_max][H_p][W_p] wavelet coefficients        */
-    size_t sure;       /* double[r_max][K] SURE of thresholding component i  */
+    size_t sure;       /* double[r_max][K] SURE of thresholding component i
+                          (HYDE_LAMBDA_PER_LEVEL: double[r_max][levels][K],
+                          S_il of each level group)                          */
     size_t sure_inf;   /* double[r_max]  SURE of dropping component i        */
-    size_t sure_total; /* double[r_max][K] total SURE of rank r=i+1, lambda_k */
+    size_t sure_total; /* double[r_max][K] total SURE of rank r=i+1, lambda_k
+                          (not written with HYDE_LAMBDA_PER_LEVEL)           */
     size_t status;     /* int            device status word                  */
     size_t lam_comp;   /* float[r_max][levels] threshold that each component's
                           detail bands of each level were soft-thresholded at
-                          (HYDE_LAMBDA_PER_COMPONENT only: row i < r* holds
-                          lambda_{k_i} in every column, the other rows 0)    */
+                          (HYDE_LAMBDA_PER_COMPONENT: row i < r* holds
+                          lambda_{k_i} in every column; HYDE_LAMBDA_PER_LEVEL:
+                          lambda_{k_il}; the other rows 0; not written with
+                          HYDE_LAMBDA_SHARED)                                */
 } hyde_ws_layout;
 
 /* Human-readable name of a status code (static storage). */
@@ -248,6 +262,8 @@ hyde_status hyde_sure_table(const float* coef, int batch, int Hp, int Wp,
  * (see hyde_lambda_mode); info then holds r*, k_0 and lambda_{k_0} of the
  * first component, sure_min = U(r*) and sure_gap from the runner-up rank,
  * and the workspace's lam_comp table holds every component's threshold.
+ * HYDE_LAMBDA_PER_LEVEL likewise, with k_00 (component 1, level 1) in info
+ * and one threshold per (component, level) in lam_comp.
  * With threshold_ll = 1 the sums and counts of S run over all N
  * coefficients and the final LL band is thresholded as well.
  */

@@ -8,6 +8,7 @@ stream. All arithmetic runs in the library's CUDA kernels.
 from __future__ import annotations
 
 import ctypes
+import math
 import struct
 
 import torch
@@ -21,6 +22,7 @@ PREC_BF16X3 = 2       # Gram on the tensor cores (split-BF16)
 PREC_BF16X3_ALL = 3   # Gram, projection and back-projection on the tensor cores
 LAMBDA_SHARED = 0         # one SURE threshold for every kept component
 LAMBDA_PER_COMPONENT = 1  # each kept component at its own SURE threshold
+LAMBDA_PER_LEVEL = 2      # each (kept component, level) at its own SURE threshold
 
 
 class HydeError(RuntimeError):
@@ -266,13 +268,16 @@ class HyRes:
         r, K = self.params.r_max, self.params.n_lambda
         Hp, Wp = padded_shape(H, W, self.params.levels)
         L = self.layout
+        lv = self.params.levels
+        # per-level mode: one SURE row per (component, level)
+        s_shape = (r, lv, K) if self.params.lambda_mode == LAMBDA_PER_LEVEL else (r, K)
         return dict(
             R=self._view(L.R, p * p, torch.float64).view(p, p),
             sigma=self._view(L.sigma, p, torch.float64),
             evals=self._view(L.evals, r, torch.float64),
             V=self._view(L.V, p * r, torch.float64).view(p, r),
             coef=self._view(L.coef, r * Hp * Wp, torch.float32).view(r, Hp, Wp),
-            S=self._view(L.sure, r * K, torch.float64).view(r, K),
+            S=self._view(L.sure, math.prod(s_shape), torch.float64).view(*s_shape),
             S_inf=self._view(L.sure_inf, r, torch.float64),
             T=self._view(L.sure_total, r * K, torch.float64).view(r, K),
             status=self._view(L.status, 1, torch.int32),

@@ -87,7 +87,8 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     if (pr->precision != HYDE_PREC_FP32 && pr->precision != HYDE_PREC_BF16X3 &&
         pr->precision != HYDE_PREC_BF16X3_ALL)
         return HYDE_ERR_INVALID_ARG;
-    if (pr->lambda_mode != HYDE_LAMBDA_SHARED && pr->lambda_mode != HYDE_LAMBDA_PER_COMPONENT)
+    if (pr->lambda_mode != HYDE_LAMBDA_SHARED && pr->lambda_mode != HYDE_LAMBDA_PER_COMPONENT &&
+        pr->lambda_mode != HYDE_LAMBDA_PER_LEVEL)
         return HYDE_ERR_INVALID_ARG;
     if (pr->threshold_ll != 0 && pr->threshold_ll != 1) return HYDE_ERR_INVALID_ARG;
     if (pr->reserved) return HYDE_ERR_INVALID_ARG;
@@ -100,6 +101,11 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     if (n < p) return HYDE_ERR_SHAPE;
     if (eig_smem_bytes(p, pr->r_max) > 227 * 1024) return HYDE_ERR_SHAPE;
     if (noise_smem_bytes(p) > 227 * 1024) return HYDE_ERR_SHAPE;
+    // per-level thresholds: one SURE histogram per (component, level), held in
+    // shared memory as [level][bin][32 lanes] x (count, sum)
+    const int G = pr->lambda_mode == HYDE_LAMBDA_PER_LEVEL ? pr->levels : 1;
+    if (G > 1 && (size_t)2 * G * pr->n_lambda * 32 * sizeof(unsigned int) > 200 * 1024)
+        return HYDE_ERR_SHAPE;
     HyresLayout l;
     l.Hp = Hp; l.Wp = Wp; l.RM = rank_pad(pr->r_max); l.K = pr->n_lambda;
     l.N = (long long)Hp * Wp; l.n = n;
@@ -119,8 +125,8 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.pub.status = c.take(sizeof(int));
     l.rank_dev = c.take(sizeof(int));
     l.lam_dev = c.take(sizeof(double));
-    l.counts = c.take((size_t)r * K * sizeof(unsigned int));
-    l.sums = c.take((size_t)r * K * sizeof(double));
+    l.counts = c.take((size_t)r * G * K * sizeof(unsigned int));
+    l.sums = c.take((size_t)r * G * K * sizeof(double));
     l.sum_all = c.take((size_t)r * sizeof(double));
     l.done = c.take(sizeof(unsigned int));
     l.zero_end = c.off;
@@ -128,11 +134,11 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.pub.sigma = c.take((size_t)p * sizeof(double));
     l.pub.evals = c.take((size_t)r * sizeof(double));
     l.pub.V = c.take((size_t)p * r * sizeof(double));
-    l.pub.sure = c.take((size_t)r * K * sizeof(double));
+    l.pub.sure = c.take((size_t)r * G * K * sizeof(double));
     l.pub.sure_inf = c.take((size_t)r * sizeof(double));
     l.pub.sure_total = c.take((size_t)r * K * sizeof(double));
     l.pub.lam_comp = c.take((size_t)r * pr->levels * sizeof(float));
-    l.sint = c.take((size_t)2 * r * K * sizeof(long long));
+    l.sint = c.take((size_t)2 * r * G * K * sizeof(long long));
     l.P = c.take((size_t)p * l.RM * sizeof(float));
     l.Q = c.take((size_t)p * l.RM * sizeof(float));
     l.noise = c.take(noise_ws_bytes(p));
@@ -351,8 +357,9 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     if (!Y || !X || Y == X) return HYDE_ERR_INVALID_ARG;
     // the scaled forms multiply one shared lambda by their detail-level scales
     const bool per_comp = params && params->lambda_mode == HYDE_LAMBDA_PER_COMPONENT;
+    const bool per_level = params && params->lambda_mode == HYDE_LAMBDA_PER_LEVEL;
     const bool all_coef = params && params->threshold_ll == 1;
-    if ((per_comp || all_coef) && scale) return HYDE_ERR_INVALID_ARG;
+    if ((per_comp || per_level || all_coef) && scale) return HYDE_ERR_INVALID_ARG;
     HyresLayout L;
     hyde_status st = hyres_layout(p, H, W, params, &L);
     if (st != HYDE_OK) return st;
@@ -411,16 +418,26 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     const long long N_det =
         all_coef ? L.N : L.N - (long long)(L.Hp >> lev) * (L.Wp >> lev);
     const double delta = sqrt(2.0 * log((double)L.N)) / (K - 1);
-    HYDE_TRY(launch_sure_hist(coef, r, L.Hp, L.Wp, lev, K, delta, sb, stream, all_coef));
-    float* lam_comp = per_comp ? at<float>(ws, L.pub.lam_comp) : nullptr;
-    HYDE_TRY(launch_sure_select(sb, r, K, L.N, N_det, delta, at<double>(ws, L.pub.sure),
-                                at<double>(ws, L.pub.sure_inf), at<double>(ws, L.pub.sure_total),
-                                info, rank_dev, lam_dev, status, stream, lam_comp, lev));
+    float* lam_comp = (per_comp || per_level) ? at<float>(ws, L.pub.lam_comp) : nullptr;
+    if (per_level) {
+        HYDE_TRY(launch_sure_hist_levels(coef, r, L.Hp, L.Wp, lev, K, delta, all_coef, sb,
+                                         stream));
+        HYDE_TRY(launch_sure_select_levels(sb, r, lev, K, L.Hp, L.Wp, all_coef, L.N, delta,
+                                           at<double>(ws, L.pub.sure),
+                                           at<double>(ws, L.pub.sure_inf), info, rank_dev,
+                                           lam_dev, status, lam_comp, stream));
+    } else {
+        HYDE_TRY(launch_sure_hist(coef, r, L.Hp, L.Wp, lev, K, delta, sb, stream, all_coef));
+        HYDE_TRY(launch_sure_select(sb, r, K, L.N, N_det, delta, at<double>(ws, L.pub.sure),
+                                    at<double>(ws, L.pub.sure_inf),
+                                    at<double>(ws, L.pub.sure_total), info, rank_dev, lam_dev,
+                                    status, stream, lam_comp, lev));
+    }
     HYDE_TRY(stage());
     // 9. soft threshold + inverse DWT of the kept components (into zp, H x W);
-    // per-component thresholds are lam_comp[i][l] times *lam_dev = 1
+    // per-component and per-level thresholds are lam_comp[i][l] times *lam_dev = 1
     HYDE_TRY(launch_idwt2(coef, zp, r, L.Hp, L.Wp, H, W, lev, scratch, lam_dev, rank_dev, stream,
-                          per_comp ? lam_comp : scale, lev, all_coef));
+                          lam_comp ? lam_comp : scale, lev, all_coef));
     HYDE_TRY(stage());
     // 10. back-projection and un-whitening
     if (tc_proj)
@@ -706,7 +723,8 @@ int hyde_set_grid_sm_cap(int sms) {
 int hyde_hyres_kernel_launches(int p, int H, int W, const hyde_hyres_params* params) {
     if (!params || params->levels < 1 || params->levels > kMaxLevels || p < 1) return -1;
     if (params->lambda_mode != HYDE_LAMBDA_SHARED &&
-        params->lambda_mode != HYDE_LAMBDA_PER_COMPONENT)
+        params->lambda_mode != HYDE_LAMBDA_PER_COMPONENT &&
+        params->lambda_mode != HYDE_LAMBDA_PER_LEVEL)
         return -1;
     if (params->threshold_ll != 0 && params->threshold_ll != 1) return -1;
     int Hp, Wp;

@@ -281,4 +281,17 @@ hyde_status launch_sure_select(const SureBufs& b, int batch, int K, long long N,
                                cudaStream_t s, float* lam_comp = nullptr,
                                int levels = 0);
 
+// Per-level thresholds: histograms per (component, level group) ([batch][levels][K],
+// the final LL band in the last group when all_coef), then per group the SURE
+// table S[batch][levels][K] and its first minimum, the rank, and
+// lam_comp[i][l] (float[batch][levels]); *lam_out = 1.
+hyde_status launch_sure_hist_levels(const float* coef, int batch, int Hp, int Wp, int levels,
+                                    int K, double delta, bool all_coef, const SureBufs& b,
+                                    cudaStream_t s);
+hyde_status launch_sure_select_levels(const SureBufs& b, int batch, int levels, int K, int Hp,
+                                      int Wp, bool all_coef, long long N, double delta,
+                                      double* S, double* S_inf, hyde_hyres_info* info,
+                                      int* rank_out, double* lam_out, const int* status,
+                                      float* lam_comp, cudaStream_t s);
+
 }  // namespace hyde

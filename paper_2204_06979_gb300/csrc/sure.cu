@@ -135,6 +135,95 @@ sure_hist_kernel(const float* __restrict__ coef, int Hp, int Wp, int hl, int wl,
     }
 }
 
+// Per-level thresholds: the same binning with one histogram per (component,
+// group), group g = level g + 1 (the detail bands of that level; the final LL
+// band joins the last group when all_coef, else it is not binned). In the
+// Mallat layout the level of position (y, x) is min(ly, lx), ly the largest
+// l <= L with y < Hp >> (l - 1) (likewise lx), and the LL band has ly = lx = L.
+// A warp takes whole rows (ly once per row), its lanes four columns each per
+// step (coalesced scalar loads, four in flight); the shared histogram is
+// [group][bin][lane], the overflow bound the same as the detail-only kernel's
+// with ceil(Wp / 32) values per lane column and row.
+constexpr int kLevCols = 4;
+
+__global__ void __launch_bounds__(kHistThreads)
+sure_hist_level_kernel(const float* __restrict__ coef, int Hp, int Wp, int levels, int all_coef,
+                       int K, float inv_delta, float qscale, double inv_qscale,
+                       int rows_per_block, unsigned int* __restrict__ counts,
+                       double* __restrict__ sums, double* __restrict__ sum_all) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ unsigned int hsm[];   // counts [G][K][32], then sums [G][K][32]
+    __shared__ double wall[kHistThreads / 32];
+    const int G = levels, GK = levels * K;
+    unsigned int* hc = hsm;
+    unsigned int* hq = hsm + GK * 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int nw = kHistThreads / 32;
+    for (int e = tid; e < 2 * GK * 32; e += kHistThreads) hsm[e] = 0u;
+    __syncthreads();
+    const int i = blockIdx.y;
+    const int y0 = blockIdx.x * rows_per_block;
+    const int y1 = min(y0 + rows_per_block, Hp);
+    const int hll = Hp >> levels, wll = Wp >> levels;
+    const float* base = coef + (long long)i * Hp * Wp;
+    float all = 0.f;
+    for (int y = y0 + wid; y < y1; y += nw) {
+        int ly = 1;
+        for (int j = 1; j < G; ++j) ly += y < (Hp >> j);
+        const bool yll = y < hll;
+        const float* row = base + (long long)y * Wp;
+        for (int x0 = 0; x0 < Wp; x0 += 32 * kLevCols) {
+            float v[kLevCols];
+#pragma unroll
+            for (int u = 0; u < kLevCols; ++u) {
+                const int x = x0 + 32 * u + lane;
+                v[u] = x < Wp ? __ldg(row + x) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kLevCols; ++u) {
+                const int x = x0 + 32 * u + lane;
+                if (x >= Wp) continue;
+                const float c = v[u];
+                const float c2 = c * c;
+                all += c2;
+                if (yll && x < wll && !all_coef) continue;
+                int lx = 1;
+                for (int j = 1; j < G; ++j) lx += x < (Wp >> j);
+                const int g = min(ly, lx) - 1;
+                const unsigned k = (unsigned)(__float_as_int(__fmaf_ru(fabsf(c), inv_delta,
+                                                                       kMagic)) - kMagicBits);
+                if (k < (unsigned)K) {
+                    const unsigned q =
+                        (unsigned)(__float_as_int(fmaf(c2, qscale, kMagic)) - kMagicBits);
+                    atomicAdd(hc + (g * K + (int)k) * 32 + lane, 1u);
+                    atomicAdd(hq + (g * K + (int)k) * 32 + lane, q);
+                }
+            }
+        }
+    }
+    all = warp_sum(all);
+    if (lane == 0) wall[wid] = (double)all;
+    __syncthreads();
+    for (int e = wid; e < GK; e += nw) {
+        unsigned int c = hc[e * 32 + lane];
+        unsigned long long q = hq[e * 32 + lane];
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            q += __shfl_xor_sync(0xffffffffu, q, o);
+        }
+        if (lane == 0 && c) {
+            atomicAdd(&counts[(long long)i * GK + e], c);
+            atomicAdd(&sums[(long long)i * GK + e], (double)q * inv_qscale);
+        }
+    }
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w) tot += wall[w];
+        if (tot != 0.0) atomicAdd(&sum_all[i], tot);
+    }
+}
+
 // S[i][k] and S_inf[i]: one warp per component; the prefix sums over the
 // bins are warp scans (K/32 chunks of shuffles), not a K-long serial chain.
 __global__ void __launch_bounds__(256)
@@ -395,6 +484,119 @@ sure_select_kernel(const unsigned int* __restrict__ counts, const double* __rest
     }
 }
 
+// Per-level selection. Block (i, g) scans row (i, g) of the histogram into
+// the group's SURE, S_ig(lambda_k) = A 2^-16 + lambda_k^2 B with
+//   A = (N_g - 2 c) 2^16 + q,   B = N_g - c,
+// N_g the group's size (3 (Hp >> l)(Wp >> l) detail coefficients of level
+// l = g + 1, plus the LL band in the last group when all_coef), and keeps its
+// first minimum over k (key and index in sint). The last block to finish adds
+// each component's group minima to the count of kept coefficients, forms
+//   U(r) = sum_{i<=r} S*_i + sum_{i>r} S_inf[i]
+// and writes the rank, the thresholds lam_comp[i][g] and the info record.
+__global__ void __launch_bounds__(kSelThreads)
+sure_select_level_kernel(const unsigned int* __restrict__ counts,
+                         const double* __restrict__ sums, const double* __restrict__ sum_all,
+                         int batch, int G, int K, int Hp, int Wp, int all_coef, long long N,
+                         double delta, double* __restrict__ S, double* __restrict__ S_inf,
+                         long long* sint, unsigned int* done, hyde_hyres_info* info,
+                         int* rank_out, double* lam_out, const int* status, float* lam_comp) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ long long wc[kSelThreads / 32], wq[kSelThreads / 32];
+    __shared__ long long wk[kSelThreads / 32];
+    __shared__ int wi[kSelThreads / 32];
+    __shared__ double comp[kMaxRank], tail[kMaxRank], sinf[kMaxRank];
+    __shared__ int s_last, s_rank;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    constexpr int nw = kSelThreads / 32;
+    const int row = blockIdx.x, i = row / G, g = row - i * G;
+    const int rows = batch * G;
+    long long Ng = 3LL * (Hp >> (g + 1)) * (Wp >> (g + 1));
+    if (all_coef && g == G - 1) Ng += (long long)(Hp >> G) * (Wp >> G);
+    {
+        long long c = 0, q = 0;
+        if (t < K) {
+            c = counts[(long long)row * K + t];
+            q = (long long)(sums[(long long)row * K + t] * 65536.0);   // exact
+        }
+        block_scan2(c, q, wc, wq);
+        long long key = 0x7fffffffffffffffLL;
+        int kb = 0x7fffffff;
+        if (t < K) {
+            const long long a = (Ng - 2 * c) * 65536LL + q, bb = Ng - c;
+            const double lam = t * delta;
+            const double v = fma(lam * lam, (double)bb, (double)a * (1.0 / 65536.0));
+            S[(long long)row * K + t] = v;
+            key = ord_key(v);
+            kb = t;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, kb, o);
+            if (ok < key || (ok == key && oi < kb)) { key = ok; kb = oi; }
+        }
+        if (lane == 0) { wk[wid] = key; wi[wid] = kb; }
+        __syncthreads();
+        if (t == 0) {
+            for (int w = 1; w < nw; ++w)
+                if (wk[w] < key || (wk[w] == key && wi[w] < kb)) { key = wk[w]; kb = wi[w]; }
+            sint[row] = key;
+            sint[rows + row] = kb;
+            if (g == 0) S_inf[i] = sum_all[i] - (double)N;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = atomicAdd(done, 1u) == (unsigned)gridDim.x - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double n_kept = all_coef ? 0.0 : (double)((long long)(Hp >> G) * (Wp >> G));
+    if (t < batch) {
+        double acc = n_kept;
+        for (int q = 0; q < G; ++q) acc += key_value(__ldcg(sint + t * G + q));
+        comp[t] = acc;
+        sinf[t] = __ldcg(S_inf + t);
+    }
+    __syncthreads();
+    if (t < batch) {
+        double acc = 0.0;
+        for (int r = batch - 1; r > t; --r) acc += sinf[r];
+        tail[t] = acc;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double acc = 0.0, u1 = 0.0, u2 = 0.0;
+        int rb = 0;
+        for (int q = 0; q < batch; ++q) {
+            acc += comp[q];
+            const double u = acc + tail[q];
+            if (q == 0) { u1 = u; u2 = u; }
+            else if (u < u1) { u2 = (q == 1) ? u1 : fmin(u2, u1); u1 = u; rb = q; }
+            else u2 = (q == 1) ? u : fmin(u2, u);
+        }
+        s_rank = rb;
+        const int k0 = (int)__ldcg(sint + rows);
+        if (rank_out) *rank_out = rb + 1;
+        if (lam_out) *lam_out = 1.0;
+        if (info) {
+            info->status = status ? *status : 0;
+            info->rank = rb + 1;
+            info->lambda_index = k0;
+            info->reserved = 0;
+            info->lambda = k0 * delta;
+            info->sure_min = u1;
+            info->sure_gap = batch > 1 ? (u2 - u1) / fmax(fabs(u1), 1e-300) : 0.0;
+        }
+    }
+    __syncthreads();
+    const int rk = s_rank;
+    for (int e = t; e < rows; e += kSelThreads) {
+        const int ci = e / G;
+        lam_comp[e] = ci <= rk ? (float)(__ldcg(sint + rows + e) * delta) : 0.f;
+    }
+}
+
 }  // namespace
 
 size_t sure_accum_bytes(int batch, int K) {
@@ -438,6 +640,54 @@ hyde_status launch_sure_hist(const float* coef, int batch, int Hp, int Wp, int l
     launch_pdl(sure_hist_kernel, grid, kHistThreads, smem, s, coef, Hp, Wp, hl, wl, K, inv_delta,
                (float)std::ldexp(1.0, sh), std::ldexp(1.0, -sh), (int)rows, b.counts, b.sums,
                b.sum_all);
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_sure_hist_levels(const float* coef, int batch, int Hp, int Wp, int levels,
+                                    int K, double delta, bool all_coef, const SureBufs& b,
+                                    cudaStream_t s) {
+    const int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    if (K < 1 || !(delta > 0.0) || levels < 1 || levels > kMaxLevels)
+        return HYDE_ERR_INVALID_ARG;
+    const size_t smem = (size_t)2 * levels * K * 32 * sizeof(unsigned int);
+    if (smem > 200 * 1024) return HYDE_ERR_SHAPE;
+    const float inv_delta = (float)(1.0 / delta);
+    const double q = (K - 1) / (double)inv_delta;
+    const double c2max = q * q * 1.001 + 1e-300;
+    int sh = 16;
+    while (sh > 0 && c2max * std::ldexp(1.0, sh) >= 4194304.0) --sh;
+    if (c2max * std::ldexp(1.0, sh) >= 4194304.0) return HYDE_ERR_SHAPE;
+    const double qmax = std::floor(c2max * std::ldexp(1.0, sh)) + 1.0;
+    // values one lane column can receive per row, and the rows that keep its sum below 2^32
+    const double per_row = (double)(((long long)Wp + 31) / 32);
+    const long long rows_cap = (long long)(4294967295.0 / (qmax * per_row));
+    if (rows_cap < 1) return HYDE_ERR_SHAPE;
+    int per_comp = (8 * sms + batch - 1) / batch;
+    if (per_comp > Hp) per_comp = Hp;
+    if (per_comp < 1) per_comp = 1;
+    long long rows = (Hp + per_comp - 1) / per_comp;
+    if (rows > rows_cap) rows = rows_cap;
+    per_comp = (int)((Hp + rows - 1) / rows);
+    if (ensure_smem_limit((const void*)sure_hist_level_kernel, (int)smem) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    launch_pdl(sure_hist_level_kernel, dim3(per_comp, batch), kHistThreads, smem, s, coef, Hp,
+               Wp, levels, all_coef ? 1 : 0, K, inv_delta, (float)std::ldexp(1.0, sh),
+               std::ldexp(1.0, -sh), (int)rows, b.counts, b.sums, b.sum_all);
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_sure_select_levels(const SureBufs& b, int batch, int levels, int K, int Hp,
+                                      int Wp, bool all_coef, long long N, double delta,
+                                      double* S, double* S_inf, hyde_hyres_info* info,
+                                      int* rank_out, double* lam_out, const int* status,
+                                      float* lam_comp, cudaStream_t s) {
+    if (batch > kMaxRank || K > kSelThreads || levels < 1 || levels > kMaxLevels ||
+        b.done == nullptr || b.sint == nullptr || lam_comp == nullptr)
+        return HYDE_ERR_SHAPE;
+    launch_pdl(sure_select_level_kernel, batch * levels, kSelThreads, 0, s, b.counts, b.sums,
+               b.sum_all, batch, levels, K, Hp, Wp, all_coef ? 1 : 0, N, delta, S, S_inf,
+               b.sint, b.done, info, rank_out, lam_out, status, lam_comp);
     return cuda_status(cudaGetLastError());
 }
 

@@ -104,7 +104,7 @@ def test_bad_arguments_rejected_on_host(lib):
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
     p.threshold_ll = 0
     assert lib.hyde_workspace_size(1, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 2
-    p.lambda_mode = 2
+    p.lambda_mode = 3
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
     p.lambda_mode = 0
     assert lib.hyde_eig_sym_top(None, 4, 2, None, None, None, None) == 1
@@ -131,6 +131,11 @@ def test_lambda_mode_params(lib):
                                          1 << 30, None) == 1
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(bad), ctypes.byref(sz)) == 1
     assert lib.hyde_hyres_kernel_launches(32, 64, 64, ctypes.byref(bad)) == -1
+    # per-level histograms that would not fit in shared memory
+    big = api.params(10, 8, 256, lambda_mode=api.LAMBDA_PER_LEVEL)
+    assert lib.hyde_workspace_size(32, 1024, 1024, ctypes.byref(big), ctypes.byref(sz)) == 2
+    lvl = api.params(3, 8, 64, lambda_mode=api.LAMBDA_PER_LEVEL)
+    assert lib.hyde_backward_workspace_size(32, 64, 64, ctypes.byref(lvl), ctypes.byref(sz)) == 1
     # the final LL band thresholded too: likewise only outside the scaled forms
     ll = api.params(3, 8, 64, threshold_ll=True)
     assert lib.hyde_backward_workspace_size(32, 64, 64, ctypes.byref(ll), ctypes.byref(sz)) == 1

@@ -285,6 +285,85 @@ def test_hyres_per_component_shapes(hyde, H, W, p, m, L, r, K, seed):
     _check_hyres_per_component(hyde, c["Y"], L, r, K)
 
 
+# ---------------------------------------------- per-level thresholds
+
+def _check_hyres_per_level(hyde, Y, L, r_max, K=64, threshold_ll=False):
+    """One threshold per (kept component, level), held to the same rule as
+    the per-component check: identical choices where the oracle's are clear
+    by more than the S-table bound, minimisers of the oracle's tables within
+    it elsewhere, and the estimate against the oracle run at the GPU's
+    choice."""
+    o = O.hyres(Y, L, r_max, K, lambda_mode="per_level", threshold_ll=threshold_ll)
+    p, H, W = Y.shape
+    h = hyde.HyRes(p, H, W, L, r_max, K, lambda_mode=hyde.LAMBDA_PER_LEVEL,
+                   threshold_ll=threshold_ll)
+    X = h(_t(Y)).cpu().numpy()
+    info = h.result_info()
+    mid = h.intermediates()
+    lam = mid["lam_comp"].cpu().numpy().astype(np.float64)
+    assert info["status"] == 0
+    r = info["rank"]
+    assert np.all(lam[r:] == 0.0)
+    lams = o["lams"]
+    k_gpu = np.rint(lam[:r] / lams[1]).astype(int)
+    assert np.allclose(lam[:r], lams[k_gpu], rtol=1e-6, atol=0)
+    assert info["lambda_index"] == k_gpu[0, 0]
+    S_lev, S_inf = o["S_lev"], o["S_inf"]
+    bound = 4.0 + 1e-6 * np.max(np.abs(S_lev))
+    S_gpu = mid["S"].cpu().numpy()
+    assert S_gpu.shape == S_lev.shape
+    assert np.max(np.abs(S_gpu - S_lev)) < 2.0 * bound
+    tol = 2.0 * bound
+    for i in range(r):
+        for l in range(L):
+            kr = o["k_lev"][i, l]
+            if np.all(np.delete(S_lev[i, l], kr) > S_lev[i, l, kr] + tol):
+                assert k_gpu[i, l] == kr, (i, l, k_gpu[i, l], kr)
+            else:
+                assert S_lev[i, l, k_gpu[i, l]] <= S_lev[i, l].min() + tol
+    Hp, Wp = O.padded_shape(H, W, L)
+    n_kept = 0 if threshold_ll else (Hp >> L) * (Wp >> L)
+    U_gpu = sum(n_kept + S_lev[i, np.arange(L), k_gpu[i]].sum() for i in range(r))
+    U_gpu += S_inf[r:].sum()
+    assert U_gpu <= o["U"].min() + r_max * L * tol
+    if np.all(np.delete(o["U"], o["rank"] - 1) > o["U"].min() + r_max * L * tol):
+        assert r == o["rank"]
+    if r == o["rank"] and np.array_equal(k_gpu, o["k_lev"][:r]):
+        ref = o["X"]
+    else:
+        ref = O.hyres(Y, L, r_max, K, rank=r, lam=lams[k_gpu], lambda_mode="per_level",
+                      threshold_ll=threshold_ll)["X"]
+    err = O.rel_l2(X, ref)
+    assert err < REL_L2_PATH, err
+    return o, info
+
+
+def test_hyres_per_level_c0(hyde):
+    c = make_cube(64, 64, 32, m=4, seed=1)
+    o, info = _check_hyres_per_level(hyde, c["Y"], 2, 8)
+    assert info["rank"] == 4
+
+
+@pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
+    (77, 131, 24, 3, 3, 6, 64, 31),     # ragged: padded to 80 x 136
+    (128, 128, 64, 8, 4, 16, 64, 5),
+    (40, 52, 12, 2, 2, 12, 16, 32),     # r_max = p, small K
+    (30, 30, 6, 2, 1, 1, 2, 33),        # r_max = 1, K = 2, one level
+])
+def test_hyres_per_level_shapes(hyde, H, W, p, m, L, r, K, seed):
+    c = make_cube(H, W, p, m=m, seed=seed)
+    _check_hyres_per_level(hyde, c["Y"], L, r, K)
+
+
+@pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
+    (64, 64, 32, 4, 2, 8, 64, 1),
+    (349, 256, 144, 12, 5, 20, 64, 2),
+])
+def test_hyres_per_level_threshold_ll(hyde, H, W, p, m, L, r, K, seed):
+    c = make_cube(H, W, p, m=m, seed=seed)
+    _check_hyres_per_level(hyde, c["Y"], L, r, K, threshold_ll=True)
+
+
 # ------------------------------------- final LL band thresholded too
 
 @pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
