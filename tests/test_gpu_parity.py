@@ -312,7 +312,11 @@ def _check_hyres_per_level(hyde, Y, L, r_max, K=64, threshold_ll=False):
     bound = 4.0 + 1e-6 * np.max(np.abs(S_lev))
     S_gpu = mid["S"].cpu().numpy()
     assert S_gpu.shape == S_lev.shape
-    assert np.max(np.abs(S_gpu - S_lev)) < 2.0 * bound
+    # kept components only: past the planted rank the components lie in the
+    # near-degenerate noise cluster, whose split into single eigenvectors
+    # float32 and float64 solvers make differently (a float32 eigenbasis
+    # alone moves those rows by 2-4 at 128 x 128 x 64)
+    assert np.max(np.abs(S_gpu[:r] - S_lev[:r])) < 2.0 * bound
     tol = 2.0 * bound
     for i in range(r):
         for l in range(L):
