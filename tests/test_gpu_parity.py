@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import oracle as O
+from selection_checks import check_per_level_choice
 from synth import make_cube
 
 pytestmark = pytest.mark.gpu
@@ -288,11 +289,9 @@ def test_hyres_per_component_shapes(hyde, H, W, p, m, L, r, K, seed):
 # ---------------------------------------------- per-level thresholds
 
 def _check_hyres_per_level(hyde, Y, L, r_max, K=64, threshold_ll=False):
-    """One threshold per (kept component, level), held to the same rule as
-    the per-component check: identical choices where the oracle's are clear
-    by more than the S-table bound, minimisers of the oracle's tables within
-    it elsewhere, and the estimate against the oracle run at the GPU's
-    choice."""
+    """One threshold per (kept component, level): the device's choice on its
+    own tables, its tables and choices on the separated components, and its
+    estimate at its own choice, against the oracle (selection_checks)."""
     o = O.hyres(Y, L, r_max, K, lambda_mode="per_level", threshold_ll=threshold_ll)
     p, H, W = Y.shape
     h = hyde.HyRes(p, H, W, L, r_max, K, lambda_mode=hyde.LAMBDA_PER_LEVEL,
@@ -300,45 +299,13 @@ def _check_hyres_per_level(hyde, Y, L, r_max, K=64, threshold_ll=False):
     X = h(_t(Y)).cpu().numpy()
     info = h.result_info()
     mid = h.intermediates()
-    lam = mid["lam_comp"].cpu().numpy().astype(np.float64)
     assert info["status"] == 0
-    r = info["rank"]
-    assert np.all(lam[r:] == 0.0)
-    lams = o["lams"]
-    k_gpu = np.rint(lam[:r] / lams[1]).astype(int)
-    assert np.allclose(lam[:r], lams[k_gpu], rtol=1e-6, atol=0)
-    assert info["lambda_index"] == k_gpu[0, 0]
-    S_lev, S_inf = o["S_lev"], o["S_inf"]
-    bound = 4.0 + 1e-6 * np.max(np.abs(S_lev))
-    S_gpu = mid["S"].cpu().numpy()
-    assert S_gpu.shape == S_lev.shape
-    # kept components only: past the planted rank the components lie in the
-    # near-degenerate noise cluster, whose split into single eigenvectors
-    # float32 and float64 solvers make differently (a float32 eigenbasis
-    # alone moves those rows by 2-4 at 128 x 128 x 64)
-    assert np.max(np.abs(S_gpu[:r] - S_lev[:r])) < 2.0 * bound
-    tol = 2.0 * bound
-    for i in range(r):
-        for l in range(L):
-            kr = o["k_lev"][i, l]
-            if np.all(np.delete(S_lev[i, l], kr) > S_lev[i, l, kr] + tol):
-                assert k_gpu[i, l] == kr, (i, l, k_gpu[i, l], kr)
-            else:
-                assert S_lev[i, l, k_gpu[i, l]] <= S_lev[i, l].min() + tol
-    Hp, Wp = O.padded_shape(H, W, L)
-    n_kept = 0 if threshold_ll else (Hp >> L) * (Wp >> L)
-    U_gpu = sum(n_kept + S_lev[i, np.arange(L), k_gpu[i]].sum() for i in range(r))
-    U_gpu += S_inf[r:].sum()
-    assert U_gpu <= o["U"].min() + r_max * L * tol
-    if np.all(np.delete(o["U"], o["rank"] - 1) > o["U"].min() + r_max * L * tol):
-        assert r == o["rank"]
-    if r == o["rank"] and np.array_equal(k_gpu, o["k_lev"][:r]):
-        ref = o["X"]
-    else:
-        ref = O.hyres(Y, L, r_max, K, rank=r, lam=lams[k_gpu], lambda_mode="per_level",
-                      threshold_ll=threshold_ll)["X"]
-    err = O.rel_l2(X, ref)
-    assert err < REL_L2_PATH, err
+    assert tuple(mid["S"].shape) == (r_max, L, K)
+    check_per_level_choice(
+        o, Y.shape, L, r_max, threshold_ll,
+        S_dev=mid["S"].cpu().numpy(), S_inf_dev=mid["S_inf"].cpu().numpy(),
+        rank=info["rank"], lam=mid["lam_comp"].cpu().numpy().astype(np.float64),
+        sure_min=info["sure_min"], lambda_index=info["lambda_index"], X=X, Y=Y)
     return o, info
 
 
