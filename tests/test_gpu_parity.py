@@ -286,55 +286,6 @@ def test_hyres_per_component_shapes(hyde, H, W, p, m, L, r, K, seed):
     _check_hyres_per_component(hyde, c["Y"], L, r, K)
 
 
-# ---------------------------------------------- per-level thresholds
-
-def _check_hyres_per_level(hyde, Y, L, r_max, K=64, threshold_ll=False):
-    """One threshold per (kept component, level): the device's choice on its
-    own tables, its tables and choices on the separated components, and its
-    estimate at its own choice, against the oracle (selection_checks)."""
-    o = O.hyres(Y, L, r_max, K, lambda_mode="per_level", threshold_ll=threshold_ll)
-    p, H, W = Y.shape
-    h = hyde.HyRes(p, H, W, L, r_max, K, lambda_mode=hyde.LAMBDA_PER_LEVEL,
-                   threshold_ll=threshold_ll)
-    X = h(_t(Y)).cpu().numpy()
-    info = h.result_info()
-    mid = h.intermediates()
-    assert info["status"] == 0
-    assert tuple(mid["S"].shape) == (r_max, L, K)
-    check_per_level_choice(
-        o, Y.shape, L, r_max, threshold_ll,
-        S_dev=mid["S"].cpu().numpy(), S_inf_dev=mid["S_inf"].cpu().numpy(),
-        rank=info["rank"], lam=mid["lam_comp"].cpu().numpy().astype(np.float64),
-        sure_min=info["sure_min"], lambda_index=info["lambda_index"], X=X, Y=Y)
-    return o, info
-
-
-def test_hyres_per_level_c0(hyde):
-    c = make_cube(64, 64, 32, m=4, seed=1)
-    o, info = _check_hyres_per_level(hyde, c["Y"], 2, 8)
-    assert info["rank"] == 4
-
-
-@pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
-    (77, 131, 24, 3, 3, 6, 64, 31),     # ragged: padded to 80 x 136
-    (128, 128, 64, 8, 4, 16, 64, 5),
-    (40, 52, 12, 2, 2, 12, 16, 32),     # r_max = p, small K
-    (30, 30, 6, 2, 1, 1, 2, 33),        # r_max = 1, K = 2, one level
-])
-def test_hyres_per_level_shapes(hyde, H, W, p, m, L, r, K, seed):
-    c = make_cube(H, W, p, m=m, seed=seed)
-    _check_hyres_per_level(hyde, c["Y"], L, r, K)
-
-
-@pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
-    (64, 64, 32, 4, 2, 8, 64, 1),
-    (349, 256, 144, 12, 5, 20, 64, 2),
-])
-def test_hyres_per_level_threshold_ll(hyde, H, W, p, m, L, r, K, seed):
-    c = make_cube(H, W, p, m=m, seed=seed)
-    _check_hyres_per_level(hyde, c["Y"], L, r, K, threshold_ll=True)
-
-
 # ------------------------------------- final LL band thresholded too
 
 @pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
@@ -388,3 +339,52 @@ def test_denoise_host_stream_matches_device_calls(hyde, count):
         info = hyde.parse_info(infos[s * nb:(s + 1) * nb])
         assert info["status"] == 0
         assert (info["rank"], info["lambda_index"]) == choices[s]
+
+
+# ---------------------------------------------- per-level thresholds
+
+def _check_hyres_per_level(hyde, Y, L, r_max, K=64, threshold_ll=False):
+    """One threshold per (kept component, level): the device's choice on its
+    own tables, its tables and choices on the separated components, and its
+    estimate at its own choice, against the oracle (selection_checks)."""
+    o = O.hyres(Y, L, r_max, K, lambda_mode="per_level", threshold_ll=threshold_ll)
+    p, H, W = Y.shape
+    h = hyde.HyRes(p, H, W, L, r_max, K, lambda_mode=hyde.LAMBDA_PER_LEVEL,
+                   threshold_ll=threshold_ll)
+    X = h(_t(Y)).cpu().numpy()
+    info = h.result_info()
+    mid = h.intermediates()
+    assert info["status"] == 0
+    assert tuple(mid["S"].shape) == (r_max, L, K)
+    check_per_level_choice(
+        o, Y.shape, L, r_max, threshold_ll, coef_dev=mid["coef"].cpu().numpy(),
+        S_dev=mid["S"].cpu().numpy(), S_inf_dev=mid["S_inf"].cpu().numpy(),
+        rank=info["rank"], lam=mid["lam_comp"].cpu().numpy().astype(np.float64),
+        sure_min=info["sure_min"], lambda_index=info["lambda_index"], X=X, Y=Y)
+    return o, info
+
+
+def test_hyres_per_level_c0(hyde):
+    c = make_cube(64, 64, 32, m=4, seed=1)
+    o, info = _check_hyres_per_level(hyde, c["Y"], 2, 8)
+    assert info["rank"] == 4
+
+
+@pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
+    (77, 131, 24, 3, 3, 6, 64, 31),     # ragged: padded to 80 x 136
+    (128, 128, 64, 8, 4, 16, 64, 5),
+    (40, 52, 12, 2, 2, 12, 16, 32),     # r_max = p, small K
+    (30, 30, 6, 2, 1, 1, 2, 33),        # r_max = 1, K = 2, one level
+])
+def test_hyres_per_level_shapes(hyde, H, W, p, m, L, r, K, seed):
+    c = make_cube(H, W, p, m=m, seed=seed)
+    _check_hyres_per_level(hyde, c["Y"], L, r, K)
+
+
+@pytest.mark.parametrize("H,W,p,m,L,r,K,seed", [
+    (64, 64, 32, 4, 2, 8, 64, 1),
+    (349, 256, 144, 12, 5, 20, 64, 2),
+])
+def test_hyres_per_level_threshold_ll(hyde, H, W, p, m, L, r, K, seed):
+    c = make_cube(H, W, p, m=m, seed=seed)
+    _check_hyres_per_level(hyde, c["Y"], L, r, K, threshold_ll=True)

@@ -38,7 +38,8 @@ def _device_args(d, c):
     r = d["rank"]
     lam = np.zeros((c["r_max"], c["L"]))
     lam[:r] = d["lam_comp"].astype(np.float32)
-    return dict(S_dev=d["S_lev"].copy(), S_inf_dev=d["S_inf"].copy(), rank=r, lam=lam,
+    return dict(coef_dev=d["C"].astype(np.float32), S_dev=d["S_lev"].copy(),
+                S_inf_dev=d["S_inf"].copy(), rank=r, lam=lam,
                 sure_min=float(d["U"].min()), lambda_index=int(d["k_lev"][0, 0]),
                 X=d["X"].copy())
 
@@ -76,9 +77,15 @@ def test_checks_reject_planted_mistakes(case):
     bad["lambda_index"] = (k00 + 7) % K
     with pytest.raises(AssertionError):
         _check(c, Y, o, bad)
-    # a table row of a separated component off by a dropped term
+    # a table row off by a dropped term, in a leading and in a cluster component
+    for i in (0, c["r_max"] - 1):
+        bad = dict(base, S_dev=base["S_dev"].copy())
+        bad["S_dev"][i, c["L"] - 1] += 12.0
+        with pytest.raises(AssertionError):
+            _check(c, Y, o, bad)
+    # coefficients of one level binned into the next level's group
     bad = dict(base, S_dev=base["S_dev"].copy())
-    bad["S_dev"][0, 0] += 12.0
+    bad["S_dev"][:, [0, 1]] = bad["S_dev"][:, [1, 0]]
     with pytest.raises(AssertionError):
         _check(c, Y, o, bad)
     # an estimate off by 2e-3 (relative), above both tolerances
