@@ -326,7 +326,10 @@ hyde_status hyde_hyres_denoise_timed(const float* Y, float* X, int p, int H,
  * at level l are soft-thresholded at lambda* * scale[i][l].
  * scale: float[r_max][levels] device (row i = component i, rows >= r*
  * unused). Otherwise identical to hyde_hyres_denoise, including the
- * workspace, which the backward then reads.
+ * workspace, which the backward then reads. params must have lambda_mode
+ * HYDE_LAMBDA_SHARED and threshold_ll 0 (HYDE_ERR_INVALID_ARG otherwise,
+ * before any device work): the scales multiply one shared lambda* on the
+ * detail bands. The same holds for the backward and its workspace query.
  */
 hyde_status hyde_hyres_denoise_scaled(const float* Y, float* X, int p, int H,
                                       int W, const hyde_hyres_params* params,
