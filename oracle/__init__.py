@@ -19,3 +19,4 @@ from .hyres import (  # noqa: F401
     rel_l2, psnr, sam, level_map, hyres_scaled, hyres_scaled_grad, mse_loss,
     sure_loss_scaled,
 )
+from .hysime import hysime, hysime_noise, hysime_select  # noqa: F401,E402

@@ -678,3 +678,79 @@ def test_sure_loss_gradient_continuous_part():
     o1 = O.hyres_scaled(c["Y"], levels, r_max, np.ones((16, levels)))
     v1, _ = O.sure_loss_scaled(o1, levels, np.ones((16, levels)))
     assert abs(v1 - np.sum(o1["S"][: o1["rank"], o1["k"]])) < 1e-6 * abs(v1)
+
+
+# ---------------------------------------------------------------- HySime
+
+def test_hysime_correlations_closed_form_from_inverse_gram():
+    """The regression residual of band b is Y q_b / q_bb (q_b the b-th column
+    of Q = (Y^T Y)^-1), so with R = Y^T Y and D_Q = diag(Q):
+    R_n = D_Q^-1 Q D_Q^-1 / n, Y^T W = D_Q^-1 and
+    R_x = (R - 2 D_Q^-1 + D_Q^-1 Q D_Q^-1) / n: a route through the Gram
+    matrix alone, against the oracle's per-band least squares on the data."""
+    c = make_cube(40, 36, 12, m=3, seed=27)
+    h = O.hysime(c["Y"])
+    Yf = c["Y"].reshape(12, -1).astype(np.float64).T
+    n = Yf.shape[0]
+    R = Yf.T @ Yf
+    Q = np.linalg.inv(R)
+    Di = np.diag(1.0 / np.diag(Q))
+    Rn = Di @ Q @ Di / n
+    Rx = (R - 2.0 * Di + Di @ Q @ Di) / n
+    assert np.allclose(h["Ry"], R / n, rtol=1e-12, atol=0)
+    assert np.max(np.abs(h["Rn"] - Rn)) < 1e-9 * np.max(np.abs(Rn))
+    assert np.max(np.abs(h["Rx"] - Rx)) < 1e-9 * np.max(np.abs(Rx))
+
+
+def test_hysime_selection_minimises_subspace_error_brute_force():
+    """Over every subset S of the eigenvectors, the projection error
+    tr((I - P_S) R_y) + 2 tr(P_S R_n) (P_S the projector on S) is smallest
+    for the set HySime keeps, {i : delta_i < 0}."""
+    import itertools
+    rng = np.random.default_rng(15)
+    for trial in range(20):
+        p = 6
+        A = rng.normal(size=(p, p))
+        Ry = A @ A.T + 0.1 * np.eye(p)
+        B = rng.normal(size=(p, p)) * 0.5
+        Rn = B @ B.T + 0.05 * np.eye(p)
+        _, E = np.linalg.eigh(rng.normal(size=(p, p)) + rng.normal(size=(p, p)).T)
+        k, idx, delta = O.hysime_select(E, Ry, Rn)
+        best, arg = np.inf, None
+        for size in range(p + 1):
+            for S in itertools.combinations(range(p), size):
+                P = E[:, list(S)] @ E[:, list(S)].T
+                cost = np.trace((np.eye(p) - P) @ Ry) + 2.0 * np.trace(P @ Rn)
+                if cost < best - 1e-12:
+                    best, arg = cost, set(S)
+        assert set(int(i) for i in idx) == arg and k == len(arg)
+        assert np.all(np.diff(delta[idx]) >= 0)
+
+
+@pytest.mark.parametrize("m,snr", [(3, 30.0), (5, 30.0), (4, 10.0)])
+def test_hysime_recovers_planted_dimension(m, snr):
+    c = make_cube(64, 64, 32, m=m, snr_db=snr, seed=7)
+    h = O.hysime(c["Y"])
+    assert h["k"] == m
+    # the subspace holds the clean cube: its projection keeps > 99.9 % of it
+    Xf = c["X"].reshape(32, -1).astype(np.float64)
+    P = h["E"] @ h["E"].T
+    assert np.linalg.norm(P @ Xf) / np.linalg.norm(Xf) > 0.999
+
+
+def test_hysime_white_noise_has_no_signal_subspace():
+    Z = np.random.default_rng(16).standard_normal((16, 64, 64)).astype(np.float32)
+    assert O.hysime(Z)["k"] == 0
+
+
+def test_hysime_scale_and_band_permutation():
+    c = make_cube(48, 48, 20, m=4, snr_db=25.0, seed=28)
+    Y = c["Y"].astype(np.float64)
+    h = O.hysime(Y)
+    h2 = O.hysime(2.5 * Y)
+    assert h2["k"] == h["k"] and np.allclose(np.abs(h2["E"]), np.abs(h["E"]), atol=1e-8)
+    perm = np.random.default_rng(1).permutation(20)
+    h3 = O.hysime(Y[perm])
+    assert h3["k"] == h["k"]
+    P, P3 = h["E"] @ h["E"].T, h3["E"] @ h3["E"].T
+    assert np.allclose(P3, P[np.ix_(perm, perm)], atol=1e-8)
