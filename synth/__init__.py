@@ -1,8 +1,8 @@
 """Seeded synthetic hyperspectral inputs shared by the tests, the benchmark and
 the oracle checks.
 
-This package draws random numbers and builds clean cubes, noisy cubes and
-window tables. It holds none of the denoiser's arithmetic (no regression, no
+This package draws random numbers and builds clean cubes, noisy cubes,
+window tables and the mixed-noise kinds of ``synth.noise``. It holds none of the denoiser's arithmetic (no regression, no
 Gram, no wavelet, no threshold), so both the CUDA path and the FP64 oracle can
 consume its output without sharing any of the method's code.
 """
