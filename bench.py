@@ -175,16 +175,37 @@ def oracle_sample_rate(cube, cols: int, runs: int, lambda_mode: str = "shared",
 
 # --------------------------------------------------------------- bench
 
-def _dist_setup(n_gpus: int):
+def _dist_setup(n_gpus: int, backend: str = "nccl"):
+    """Rank layout from the launcher's environment; a process group (one
+    rank per GPU, NCCL) when there is more than one rank."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
         return dist, world, rank, local
     return None, 1, 0, local
+
+
+def _max_over_ranks(dist, values, device):
+    """Element-wise maximum over the ranks of each rank's own timings: the
+    job takes as long as its slowest rank."""
+    vals = [float(v) for v in values]
+    if dist is None:
+        return vals
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def _job_rate(world: int, units_per_step: float, steps: int, total_ms: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank
+    processes ``units_per_step`` in each of ``steps`` steps (weak scaling, no
+    exchange between ranks) within the slowest rank's ``total_ms``."""
+    return world * units_per_step * steps / (total_ms / 1e3) / 1e6
 
 
 def _stage_bytes(r_star: int) -> dict:
@@ -257,13 +278,9 @@ def run_gb300(args) -> None:
         barrier()
     wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(dist, [sum(step_ms)], dev)[0]
     ms_per_step = total_ms / args.steps
-    value = world * voxels * args.steps / (total_ms / 1e3) / 1e6
+    value = _job_rate(world, voxels, args.steps, total_ms)
 
     # ---- per-stage timing through the timed entry point (same launches)
     nst = _lib.N_STAGES
@@ -367,12 +384,9 @@ def run_gb300(args) -> None:
     s1.record(stream)
     barrier()
     serial_ms = s0.elapsed_time(s1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms, serial_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms, serial_ms = float(t[0].item()), float(t[1].item())
-    e2e_value = world * voxels * args.steps / (e2e_ms / 1e3) / 1e6
-    e2e_serial = world * voxels * args.steps / (serial_ms / 1e3) / 1e6
+    e2e_ms, serial_ms = _max_over_ranks(dist, [e2e_ms, serial_ms], dev)
+    e2e_value = _job_rate(world, voxels, args.steps, e2e_ms)
+    e2e_serial = _job_rate(world, voxels, args.steps, serial_ms)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
