@@ -141,3 +141,69 @@ def test_lambda_mode_params(lib):
     assert lib.hyde_backward_workspace_size(32, 64, 64, ctypes.byref(ll), ctypes.byref(sz)) == 1
     assert lib.hyde_hyres_denoise_scaled(1, 2, 32, 64, 64, ctypes.byref(ll), 3, None, 4,
                                          1 << 30, None) == 1
+
+
+def test_remaining_entry_points_reject_bad_arguments_on_host(lib):
+    """Every entry point not covered above rejects null pointers, bad sizes
+    and bad shapes before any device query (status codes: 1 invalid
+    argument, 2 unsupported shape)."""
+    from paper_2204_06979_gb300 import api
+    from paper_2204_06979_gb300._lib import HydeWindow, HydeWsLayout
+    sz = ctypes.c_size_t()
+    prm = api.params(2, 8, 64)
+    # Gram workspace: no output, an unknown precision
+    assert lib.hyde_gram_workspace_size(32, 4096, 0, None) == 1
+    assert lib.hyde_gram_workspace_size(32, 4096, 1, ctypes.byref(sz)) == 1
+    assert lib.hyde_gram_workspace_size(32, 0, 2, ctypes.byref(sz)) == 2
+    # allocation-free Gram: null pointers; its scratch size is a constant
+    assert lib.hyde_gram_noalloc(None, 32, 4096, None, None) == 1
+    assert lib.hyde_gram_noalloc_scratch_bytes() == 16 * 1024 * 1024
+    # noise workspace: no output, one band, fewer pixels than bands
+    assert lib.hyde_noise_est_workspace_size(32, 64, 64, None) == 1
+    assert lib.hyde_noise_est_workspace_size(1, 64, 64, ctypes.byref(sz)) == 2
+    assert lib.hyde_noise_est_workspace_size(32, 4, 4, ctypes.byref(sz)) == 2
+    # layout query: no output, bad params
+    lay = HydeWsLayout()
+    assert lib.hyde_workspace_layout(32, 64, 64, ctypes.byref(prm), None) == 1
+    bad = api.params(2, 8, 64)
+    bad.wavelet = 4
+    assert lib.hyde_workspace_layout(32, 64, 64, ctypes.byref(bad), ctypes.byref(lay)) == 1
+    # timed entry point without its events
+    assert lib.hyde_hyres_denoise_timed(1, 2, 32, 64, 64, ctypes.byref(prm), None, 3, 1 << 20,
+                                        None, None) == 1
+    # host cube stream: no cubes, missing device buffers or events
+    ptrs4 = (ctypes.c_void_p * 4)(1, 2, 3, 4)
+    evs7 = (ctypes.c_void_p * 7)(*range(1, 8))
+    ys = (ctypes.c_void_p * 1)(5)
+    xs = (ctypes.c_void_p * 1)(6)
+    args = (ys, xs, None)
+    tail = (32, 64, 64, ctypes.byref(prm))
+    assert lib.hyde_hyres_denoise_host(*args, 0, *tail, ptrs4, 7, 8, 1 << 20, None, None,
+                                       None, evs7) == 1
+    holes = (ctypes.c_void_p * 4)(1, 2, None, 4)
+    assert lib.hyde_hyres_denoise_host(*args, 1, *tail, holes, 7, 8, 1 << 20, None, None,
+                                       None, evs7) == 1
+    ev_holes = (ctypes.c_void_p * 7)(1, 2, 3, None, 5, 6, 7)
+    assert lib.hyde_hyres_denoise_host(*args, 1, *tail, ptrs4, 7, 8, 1 << 20, None, None,
+                                       None, ev_holes) == 1
+    # windows: none, one outside the scene, a core outside its window
+    ok = HydeWindow(0, 0, 32, 32, 8, 8, 16, 16)
+    out = HydeWindow(40, 0, 32, 32, 48, 8, 16, 16)
+    core = HydeWindow(0, 0, 32, 32, 24, 8, 16, 16)
+    one = lambda w: (HydeWindow * 1)(w)
+    assert lib.hyde_windows_workspace_size(8, 64, 64, one(ok), 0, ctypes.byref(prm), 4,
+                                           ctypes.byref(sz)) == 1
+    assert lib.hyde_windows_workspace_size(8, 64, 64, one(out), 1, ctypes.byref(prm), 4,
+                                           ctypes.byref(sz)) == 2
+    assert lib.hyde_windows_workspace_size(8, 64, 64, one(core), 1, ctypes.byref(prm), 4,
+                                           ctypes.byref(sz)) == 2
+    streams = (ctypes.c_void_p * 1)(9)
+    assert lib.hyde_hyres_denoise_windows(1, 1, 8, 64, 64, one(ok), 1, ctypes.byref(prm), None,
+                                          3, 1 << 20, streams, 1, evs7, None) == 1
+    assert lib.hyde_hyres_denoise_windows(1, 2, 8, 64, 64, one(ok), 1, ctypes.byref(prm), None,
+                                          3, 1 << 20, None, 1, evs7, None) == 1
+    # backward: unknown loss, the MSE loss without its adjoint input
+    assert lib.hyde_hyres_backward(1, 2, 32, 64, 64, ctypes.byref(prm), 3, 2, 4, None, 5,
+                                   1 << 20, 6, 1 << 20, None) == 1
+    assert lib.hyde_hyres_backward(1, None, 32, 64, 64, ctypes.byref(prm), 3, 0, 4, None, 5,
+                                   1 << 20, 6, 1 << 20, None) == 1
