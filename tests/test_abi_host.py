@@ -207,3 +207,24 @@ def test_remaining_entry_points_reject_bad_arguments_on_host(lib):
                                    1 << 20, 6, 1 << 20, None) == 1
     assert lib.hyde_hyres_backward(1, None, 32, 64, 64, ctypes.byref(prm), 3, 0, 4, None, 5,
                                    1 << 20, 6, 1 << 20, None) == 1
+
+
+@pytest.mark.parametrize("p,H,W,levels,r_max,K,code", [
+    (32, 0, 64, 2, 8, 64, 2),      # empty image
+    (32, 64, -1, 2, 8, 64, 2),     # negative side
+    (1, 64, 64, 2, 1, 64, 2),      # one band: nothing to regress on
+    (257, 64, 64, 2, 8, 64, 2),    # more bands than the Gram kernel takes
+    (32, 64, 64, 2, 0, 64, 2),     # rank 0
+    (32, 64, 64, 2, 33, 64, 2),    # rank above one warp per eigenpair
+    (8, 64, 64, 2, 9, 64, 2),      # rank above the band count
+    (32, 64, 64, 2, 8, 257, 2),    # more threshold candidates than the table holds
+    (32, 64, 64, 0, 8, 64, 2),     # no DWT level
+    (32, 64, 64, 11, 8, 64, 2),    # more levels than supported
+    (32, 3, 64, 3, 8, 64, 2),      # padding (3 -> 8) longer than the image allows
+    (32, 4, 4, 1, 8, 64, 2),       # fewer pixels than bands
+])
+def test_degenerate_shapes_rejected_on_host(lib, p, H, W, levels, r_max, K, code):
+    from paper_2204_06979_gb300 import api
+    sz = ctypes.c_size_t()
+    prm = api.params(levels, r_max, K)
+    assert lib.hyde_workspace_size(p, H, W, ctypes.byref(prm), ctypes.byref(sz)) == code
