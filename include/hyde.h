@@ -202,6 +202,31 @@ hyde_status hyde_noise_est(const float* Y, int p, int H, int W, double* sigma,
                            int* status, void* ws, size_t ws_bytes,
                            cudaStream_t stream);
 
+/* ----------------------------------------------------------------- HySime
+ * Signal-subspace identification (Sec. 2.1: the subspace step the paper
+ * ships for FastHyDe and runs on GPUs; Bioucas-Dias and Nascimento, 2008).
+ * The noise is each band's least-squares residual on all the other bands
+ * (as in hyde_noise_est); R_y, R_n and R_x are the data, noise and signal
+ * correlation matrices (uncentred, over n); the subspace holds the
+ * eigenvectors e of R_x with delta = -e^T R_y e + 2 e^T R_n e < 0. Only
+ * the Gram matrix touches the data: with Q = (Y^T Y)^-1 and D = diag(Q),
+ * R_n = D^-1 Q D^-1 / n and R_x = (Y^T Y - 2 D^-1 + D^-1 Q D^-1) / n.
+ * Y: float[p][n] band-major device, 2 <= p <= 256, n >= p. r_max: the
+ * candidates, the leading eigenvectors of R_x, 1..min(p, 32) (the published
+ * method ranks all p; eigenvectors past the leading ones carry the least
+ * signal). Outputs (device): *k; idx int[r_max], the kept candidates in
+ * ascending delta, then -1; E double[p][r_max], the candidates (column c,
+ * descending eigenvalue; row b = band b); delta, evals double[r_max].
+ * status: device int the caller zeroes (HYDE_ERR_NUMERIC for a singular or
+ * non-finite matrix). Workspace: hyde_hysime_workspace_size.
+ */
+hyde_status hyde_hysime_workspace_size(int p, long long n, int r_max,
+                                       size_t* bytes);
+hyde_status hyde_hysime(const float* Y, int p, long long n, int r_max, int* k,
+                        int* idx, double* E, double* delta, double* evals,
+                        int* status, void* ws, size_t ws_bytes,
+                        cudaStream_t stream);
+
 /* ----------------------------------------------------------- eigenvectors
  * Leading r eigenpairs of a symmetric positive semi-definite p x p matrix A
  * (double, row-major): the spectral subspace of the low-rank model

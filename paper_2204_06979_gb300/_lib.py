@@ -50,6 +50,9 @@ SIGNATURES = {
     "hyde_noise_est_workspace_size": (c_int, [c_int, c_int, c_int, c_size_p]),
     "hyde_noise_est": (c_int, [c_vp, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_size, c_vp]),
     "hyde_eig_sym_top": (c_int, [c_vp, c_int, c_int, c_vp, c_vp, c_vp, c_vp]),
+    "hyde_hysime_workspace_size": (c_int, [c_int, c_ll, c_int, c_size_p]),
+    "hyde_hysime": (c_int, [c_vp, c_int, c_ll, c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                            c_vp, c_size, c_vp]),
     "hyde_dwt_workspace_size": (c_int, [c_int, c_int, c_int, c_int, c_size_p]),
     "hyde_dwt2": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_int, c_vp, c_size, c_vp]),
     "hyde_idwt2": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_int, c_vp, c_size, c_vp]),

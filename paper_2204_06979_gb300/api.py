@@ -130,6 +130,36 @@ def eig_sym_top(A: torch.Tensor, r: int) -> tuple[torch.Tensor, torch.Tensor, to
     return evals, V, status
 
 
+def hysime(Y: torch.Tensor, r_max: int = 32) -> dict:
+    """HySime subspace identification of ``Y`` (``[p, H, W]`` or ``[p, n]``,
+    float32, CUDA) with the ``min(r_max, p, 32)`` leading eigenvectors of the
+    signal correlation as candidates. Synchronises to read the dimension;
+    returns ``k``, ``E`` (``p x k``, the kept eigenvectors in ascending
+    delta), ``idx``, and all candidates' ``V``, ``delta`` and ``evals``."""
+    Y = _cuda_f32(Y, "Y")
+    lib = _lib.load()
+    p = Y.shape[0]
+    n = Y.numel() // p
+    r = min(r_max, p, 32)
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_hysime_workspace_size(p, n, r, ctypes.byref(sz)), "hyde_hysime_workspace_size")
+    ws = _workspace(sz.value, Y.device)
+    dev = Y.device
+    k = torch.zeros(1, dtype=torch.int32, device=dev)
+    idx = torch.empty(r, dtype=torch.int32, device=dev)
+    V = torch.empty(p, r, dtype=torch.float64, device=dev)
+    delta = torch.empty(r, dtype=torch.float64, device=dev)
+    evals = torch.empty(r, dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(lib.hyde_hysime(_ptr(Y), p, n, r, _ptr(k), _ptr(idx), _ptr(V), _ptr(delta),
+                           _ptr(evals), _ptr(status), _ptr(ws), ws.numel(), _stream()),
+           "hyde_hysime")
+    kk = int(k.item())
+    keep = idx[:kk].long()
+    return dict(k=kk, E=V[:, keep], idx=keep, V=V, delta=delta, evals=evals,
+                status=int(status.item()))
+
+
 def dwt2(x: torch.Tensor, levels: int) -> torch.Tensor:
     """Periodic db2 analysis of ``x[B, H, W]`` -> Mallat ``coef[B, Hp, Wp]``."""
     lib = _lib.load()

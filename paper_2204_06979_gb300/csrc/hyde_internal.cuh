@@ -177,6 +177,10 @@ size_t noise_ws_bytes(int p);
 hyde_status launch_noise_from_gram(const double* R, int p, long long n,
                                    double* sigma, void* ws, int* status,
                                    cudaStream_t s);
+// Q = R^-1 (double[p][p], column b refined in double by one Newton step
+// from the float Gauss-Jordan inverse; ws as for launch_noise_from_gram).
+hyde_status launch_inverse_from_gram(const double* R, int p, void* ws, double* Q, int* status,
+                                     cudaStream_t s);
 size_t eig_smem_bytes(int p, int r);
 size_t noise_smem_bytes(int p);   // dynamic smem of the Gauss-Jordan kernel (0 = registers)
 hyde_status launch_eig_top(const double* A, const double* wsig, int p,

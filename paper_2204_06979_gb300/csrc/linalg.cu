@@ -853,6 +853,48 @@ __global__ void weights_kernel(const double* __restrict__ V, const double* __res
     }
 }
 
+// --------------------------------------------------------------------------
+// Full inverse (block b): column b of Q = R^-1 in double from the float
+// inverse X0 = S^-1 As^-1 S^-1 by one Newton step X0 (2I - R X0): with
+// x = column b of X0 and u = R x, q_b = 2 x - X0 u. One warp per row, lanes
+// over the columns, double sums.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+inverse_refine_kernel(const double* __restrict__ R, const float* __restrict__ Ainv,
+                      const double* __restrict__ S, int p, double* __restrict__ Q,
+                      int* status) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ double xs[];   // x [p], u [p], 1/S [p]
+    double* us = xs + p;
+    double* is = xs + 2 * p;
+    const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    constexpr int nw = 256 / 32;
+    for (int i = t; i < p; i += blockDim.x) is[i] = 1.0 / S[i];
+    __syncthreads();
+    for (int i = t; i < p; i += blockDim.x)
+        xs[i] = (double)Ainv[(long long)i * p + b] * is[i] * is[b];
+    __syncthreads();
+    for (int i = w; i < p; i += nw) {
+        double acc = 0.0;
+        for (int j = lane; j < p; j += 32) acc = fma(__ldg(R + (long long)i * p + j), xs[j], acc);
+        acc = warp_sum_d(acc);
+        if (lane == 0) us[i] = acc;
+    }
+    __syncthreads();
+    for (int i = w; i < p; i += nw) {
+        double acc = 0.0;
+        for (int j = lane; j < p; j += 32)
+            acc = fma((double)Ainv[(long long)i * p + j] * is[j], us[j], acc);
+        acc = warp_sum_d(acc) * is[i];
+        if (lane == 0) {
+            const double v = 2.0 * xs[i] - acc;
+            if (!isfinite(v)) set_status(status, HYDE_ERR_NUMERIC);
+            Q[(long long)i * p + b] = v;
+        }
+    }
+}
+
 size_t eig_fast_bytes(int p, int r) {
     return ((size_t)p * (p + 1) + 7 * (size_t)p + 64 + 32 + 32 + 3 * (size_t)p * r) *
            sizeof(float);
@@ -873,8 +915,11 @@ size_t noise_smem_bytes(int p) {
     return p <= kGj20Max ? 0 : ((size_t)p * p + 2 * p) * sizeof(float);
 }
 
-hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* sigma,
-                                   void* ws, int* status, cudaStream_t s) {
+// The float inverse of the scaled Gram matrix into ws (Ainv, then the
+// scales S): a register-tile Gauss-Jordan kernel for p <= 200, the
+// shared-memory kernel above.
+static hyde_status launch_gj_inverse(const double* R, int p, void* ws, int* status,
+                                     cudaStream_t s) {
     float* Ainv = reinterpret_cast<float*>(ws);
     double* Sd = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) +
                                            align_up((size_t)p * p * sizeof(float), kAlign));
@@ -900,7 +945,29 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* 
             return HYDE_ERR_SHAPE;
         launch_pdl(noise_gj_smem_kernel, 1, kLA, smem, s, R, p, Ainv, Sd, status);
     }
+    return HYDE_OK;
+}
+
+hyde_status launch_noise_from_gram(const double* R, int p, long long n, double* sigma,
+                                   void* ws, int* status, cudaStream_t s) {
+    const float* Ainv = reinterpret_cast<const float*>(ws);
+    const double* Sd = reinterpret_cast<const double*>(
+        reinterpret_cast<const char*>(ws) + align_up((size_t)p * p * sizeof(float), kAlign));
+    hyde_status st = launch_gj_inverse(R, p, ws, status, s);
+    if (st != HYDE_OK) return st;
     launch_pdl(noise_refine_kernel, p, 256, p * sizeof(double), s, R, Ainv, Sd, p, n, sigma,
+               status);
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_inverse_from_gram(const double* R, int p, void* ws, double* Q, int* status,
+                                     cudaStream_t s) {
+    const float* Ainv = reinterpret_cast<const float*>(ws);
+    const double* Sd = reinterpret_cast<const double*>(
+        reinterpret_cast<const char*>(ws) + align_up((size_t)p * p * sizeof(float), kAlign));
+    hyde_status st = launch_gj_inverse(R, p, ws, status, s);
+    if (st != HYDE_OK) return st;
+    launch_pdl(inverse_refine_kernel, p, 256, 3 * p * sizeof(double), s, R, Ainv, Sd, p, Q,
                status);
     return cuda_status(cudaGetLastError());
 }

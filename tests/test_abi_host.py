@@ -228,3 +228,18 @@ def test_degenerate_shapes_rejected_on_host(lib, p, H, W, levels, r_max, K, code
     sz = ctypes.c_size_t()
     prm = api.params(levels, r_max, K)
     assert lib.hyde_workspace_size(p, H, W, ctypes.byref(prm), ctypes.byref(sz)) == code
+
+
+def test_hysime_rejects_bad_arguments_on_host(lib):
+    """HySime's shape and pointer checks come before any device query."""
+    sz = ctypes.c_size_t()
+    assert lib.hyde_hysime_workspace_size(32, 4096, 8, None) == 1
+    assert lib.hyde_hysime_workspace_size(1, 4096, 1, ctypes.byref(sz)) == 2      # one band
+    assert lib.hyde_hysime_workspace_size(257, 4096, 8, ctypes.byref(sz)) == 2    # too many
+    assert lib.hyde_hysime_workspace_size(32, 16, 8, ctypes.byref(sz)) == 2       # n < p
+    assert lib.hyde_hysime_workspace_size(32, 4096, 0, ctypes.byref(sz)) == 2     # no candidate
+    assert lib.hyde_hysime_workspace_size(32, 4096, 33, ctypes.byref(sz)) == 2    # above 32
+    assert lib.hyde_hysime_workspace_size(8, 4096, 9, ctypes.byref(sz)) == 2      # above p
+    assert lib.hyde_hysime(None, 32, 4096, 8, 1, 2, 3, 4, 5, None, 6, 1 << 20, None) == 1
+    assert lib.hyde_hysime(1, 32, 4096, 8, 1, None, 3, 4, 5, None, 6, 1 << 20, None) == 1
+    assert lib.hyde_hysime(1, 32, 16, 8, 1, 2, 3, 4, 5, None, 6, 1 << 20, None) == 2
