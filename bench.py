@@ -224,6 +224,170 @@ def _stage_bytes(r_star: int) -> dict:
     }
 
 
+def _step_stats(ms) -> dict:
+    """Per-step device times: mean (what value and ms_per_step use), median,
+    and the olympic mean (the extremes dropped, the paper's protocol)."""
+    srt = sorted(ms)
+    oly = srt[1:-1] if len(srt) > 2 else srt
+    return {"mean": round(statistics.mean(ms), 4), "median": round(statistics.median(ms), 4),
+            "olympic": round(statistics.mean(oly), 4), "min": round(srt[0], 4),
+            "max": round(srt[-1], 4), "n": len(ms)}
+
+
+def _parity_full_cube(cube, X, info) -> dict:
+    """The FP64 oracle on the whole timed cube, once: relative L2 error of
+    the timed output, the largest per-band error, and whether the (rank,
+    lambda) choice is the oracle's."""
+    import numpy as np
+    import oracle as O
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    o = O.hyres(cube["Y"], w["levels"], w["r_max"], w["n_lambda"])
+    secs = time.perf_counter() - t0
+    Xg = X.cpu().numpy().astype(np.float64)
+    p = Xg.shape[0]
+    d = (Xg - o["X"]).reshape(p, -1)
+    band = np.linalg.norm(d, axis=1) / np.linalg.norm(o["X"].reshape(p, -1), axis=1)
+    return {"rel_l2": float(O.rel_l2(Xg, o["X"])), "max_band_rel_l2": float(band.max()),
+            "rank": int(info["rank"]), "lambda_index": int(info["lambda_index"]),
+            "oracle_rank": int(o["rank"]), "oracle_lambda_index": int(o["k"]),
+            "identical_choice": bool(int(info["rank"]) == int(o["rank"]) and
+                                     int(info["lambda_index"]) == int(o["k"])),
+            "oracle_sure_gap": float(o["gap"]), "oracle_seconds": round(secs, 2),
+            "psnr_gain_db": float(O.psnr(cube["X"], Xg) - O.psnr(cube["X"], cube["Y"]))}
+
+
+def _time_form(fn, args, flush, stream, voxels) -> dict:
+    """Per-step CUDA events around fn() with the clocks sampled meanwhile."""
+    clocks = ClockSampler(torch_device_index())
+    with clocks:
+        ms = _timed_steps(fn, args.form_steps, 3, flush, stream)
+    total = float(sum(ms))
+    return {"ms": round(total / len(ms), 4), "step_ms": _step_stats(ms),
+            "Mvoxel/s": round(voxels * len(ms) / (total / 1e3) / 1e6, 1),
+            "clocks": clocks.summary()}
+
+
+def torch_device_index() -> int:
+    import torch
+    return torch.cuda.current_device()
+
+
+def _form_precision(args, dev, cube, flush, stream) -> dict:
+    """The benchmark cube with the Gram matrix on the tensor cores (split-BF16
+    compensated products), with its error against the FP64 oracle's Gram
+    matrix and output."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2204_06979_gb300 import api
+    w = WORKLOAD
+    p, H, W = w["p"], w["H"], w["W"]
+    Y = torch.from_numpy(cube["Y"]).to(dev)
+    X = torch.empty_like(Y)
+    h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev,
+                  precision=api.PREC_BF16X3)
+    out = _time_form(lambda: h(Y, X), args, flush, stream, p * H * W)
+    torch.cuda.synchronize(dev)
+    info = h.result_info()
+    mid = h.intermediates()
+    Rg = mid["R"].cpu().numpy()
+    R = O.gram(cube["Y"])
+    o = O.hyres(cube["Y"], w["levels"], w["r_max"], w["n_lambda"])
+    Xg = X.cpu().numpy().astype(np.float64)
+    d = np.sqrt(np.outer(np.diag(R), np.diag(R)))
+    out.update({
+        "precision": "bf16x3 (Gram on tcgen05, split-BF16 compensated, FP32 accumulation)",
+        "errors_vs_fp64_oracle": {
+            "gram_max_rel": float(np.max(np.abs(Rg - R) / d)),
+            "sigma_max_rel": float(np.max(np.abs(mid["sigma"].cpu().numpy() / o["sigma"] - 1))),
+            "output_rel_l2": float(O.rel_l2(Xg, o["X"])),
+            "psnr_delta_db": float(O.psnr(cube["X"], Xg) - O.psnr(cube["X"], o["X"])),
+            "identical_choice": bool((info["rank"], info["lambda_index"]) ==
+                                     (o["rank"], o["k"]))}})
+    return out
+
+
+def _form_per_level(args, dev, cube, flush, stream) -> dict:
+    """The benchmark cube with one SURE threshold per kept component and
+    level."""
+    import torch
+    from paper_2204_06979_gb300 import api
+    w = WORKLOAD
+    p, H, W = w["p"], w["H"], w["W"]
+    Y = torch.from_numpy(cube["Y"]).to(dev)
+    X = torch.empty_like(Y)
+    h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev,
+                  lambda_mode=api.LAMBDA_PER_LEVEL)
+    out = _time_form(lambda: h(Y, X), args, flush, stream, p * H * W)
+    info = h.result_info()
+    out.update({"rank": info["rank"], "status": info["status"],
+                "workload": "349x1905x144 cube, one threshold per (kept component, level)"})
+    return out
+
+
+def _form_diff(args, dev, cube, flush, stream) -> dict:
+    """Differentiation form: 16 cubes 128 x 128 x 64, forward with learnable
+    per-(component, level) threshold scales and the hand-written backward of
+    an MSE-to-clean loss, one captured CUDA graph per training step."""
+    import torch
+    from paper_2204_06979_gb300 import api
+    from synth import make_cube
+    B, H, W, p, L, r = 16, 128, 128, 64, 4, 16
+    cubes = [make_cube(H, W, p, m=8, seed=5 + b) for b in range(B)]
+    Ys = [torch.from_numpy(cb["Y"]).to(dev) for cb in cubes]
+    Xs = [torch.from_numpy(cb["X"]).to(dev) for cb in cubes]
+    models = [api.HyResGrad(p, H, W, L, r, device=dev) for _ in range(B)]
+    streams = [torch.cuda.Stream(dev) for _ in range(B)]
+    scale = torch.ones((p, L), dtype=torch.float32, device=dev, requires_grad=True)
+
+    def step_eager():
+        scale.grad.zero_()
+        Xh = api.hyres_scaled_batch(Ys, scale, models, streams)
+        loss = sum(torch.mean((X_ - Xc) ** 2) for X_, Xc in zip(Xh, Xs))
+        loss.backward()
+
+    scale.grad = torch.zeros_like(scale)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step_eager()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_eager()
+    out = _time_form(graph.replay, args, flush, stream, B * p * H * W)
+    out.update({"workload": "16 cubes 128x128x64, db2 L=4, r<=16, forward + backward, "
+                            "MSE-to-clean loss, one CUDA graph per training step",
+                "grad_norm": float(scale.grad.norm())})
+    return out
+
+
+def _form_windows(args, dev, cube, flush, stream) -> dict:
+    """Batched sliding-window form: a 2048 x 2048 x 200 scene in 512 uneven
+    windows, one captured CUDA graph per scene."""
+    import torch
+    from paper_2204_06979_gb300 import api
+    from synth import make_scene, make_window_table
+    H = W = 2048
+    p, L, r = 200, 3, 20
+    T = make_window_table(H, W, depth=9, context=16, min_side=32, max_side=224, seed=4)
+    sc = make_scene(H, W, p, T, m=12, seed=4)
+    Y = torch.from_numpy(sc["Y"]).to(dev)
+    del sc
+    X = torch.zeros_like(Y)
+    win = api.HyResWindows(p, H, W, T, L, r, n_slots=64, device=dev)
+    win.capture(Y, X)
+    out = _time_form(win.replay, args, flush, stream, p * H * W)
+    infos = win.infos()
+    out.update({"workload": "2048x2048x200 scene, 512 windows (sides 48..256, 16-px context), "
+                            "per-core SNR U[5,20] dB, db2 L=3, r<=20, one CUDA graph per scene",
+                "statuses_ok": int(sum(i["status"] == 0 for i in infos)),
+                "windows": len(T)})
+    return out
+
+
 def run_gb300(args) -> None:
     import numpy as np
     import torch
@@ -281,6 +445,8 @@ def run_gb300(args) -> None:
     total_ms = _max_over_ranks(dist, [sum(step_ms)], dev)[0]
     ms_per_step = total_ms / args.steps
     value = _job_rate(world, voxels, args.steps, total_ms)
+    step_stats = _step_stats(step_ms)
+    X_timed = Xd.clone() if rank == 0 else None
 
     # ---- per-stage timing through the timed entry point (same launches)
     nst = _lib.N_STAGES
@@ -388,6 +554,22 @@ def run_gb300(args) -> None:
     e2e_value = _job_rate(world, voxels, args.steps, e2e_ms)
     e2e_serial = _job_rate(world, voxels, args.steps, serial_ms)
 
+    # ---- parity of the timed output against the FP64 oracle on the whole cube
+    parity = None
+    if rank == 0 and world == 1 and not args.no_parity:
+        parity = _parity_full_cube(cube, X_timed, info)
+
+    # ---- the other forms, each on its own workload (rank 0 of a 1-GPU run)
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        forms = {}
+        for name, fn in (("precision_bf16x3", _form_precision), ("per_level", _form_per_level),
+                         ("diff", _form_diff), ("windows", _form_windows)):
+            try:
+                forms[name] = fn(args, dev, cube, flush, stream)
+            except Exception as exc:   # a failing form is reported, not hidden
+                forms[name] = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample_rate(cube, cols=args.cpu_cols, runs=args.cpu_runs,
@@ -429,6 +611,9 @@ def run_gb300(args) -> None:
                             "while cube s is denoised",
                     "serial_value": round(e2e_serial, 1)},
             "gpu_launches": int(launches_per_step * args.steps),
+            "step_ms": step_stats,
+            "parity": parity,
+            "forms": forms,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
             "selection": {"rank": r_star, "lambda_index": info["lambda_index"],
@@ -602,6 +787,12 @@ def main() -> None:
                     help="columns of the cube in the CPU oracle sample")
     ap.add_argument("--cpu-runs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the FP64 oracle run on the whole timed cube")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision, per-level, differentiation and window forms")
+    ap.add_argument("--form-steps", type=int, default=5,
+                    help="timed steps of each secondary form in the plain run")
     ap.add_argument("--form", choices=("plain", "windows", "diff"), default="plain",
                     help="plain: the headline workload; windows / diff: secondary forms")
     ap.add_argument("--slots", type=int, default=64, help="window slots (--form windows)")

@@ -176,9 +176,12 @@ hyde_status hyde_gram(const float* Y, int p, long long n, int precision,
  * 16 MiB array in device global memory (hyde_gram_noalloc_scratch_bytes)
  * that every GPU loading the library holds until the process exits. The
  * grid is capped so the partials fit (fewer blocks for large p, never
- * fewer than one); p > 256 is rejected with HYDE_ERR_SHAPE. The first call
- * on each device looks up the array's device address (cudaGetSymbolAddress,
- * no allocation), so make that first call before any stream capture. All
+ * fewer than one); p > 256 is rejected with HYDE_ERR_SHAPE. Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, no allocation), so the address stays right after
+ * the caller resets the device; the first call on a device also loads the
+ * library's device code there, so make that first call before any stream
+ * capture. All
  * calls share the one array: calls that can overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * Calls no cudaMalloc, cudaFree or allocating library routine.
@@ -218,7 +221,11 @@ hyde_status hyde_noise_est(const float* Y, int p, int H, int W, double* sigma,
  * ascending delta, then -1; E double[p][r_max], the candidates (column c,
  * descending eigenvalue; row b = band b); delta, evals double[r_max].
  * status: device int the caller zeroes (HYDE_ERR_NUMERIC for a singular or
- * non-finite matrix). Workspace: hyde_hysime_workspace_size.
+ * non-finite matrix, or a refined inverse with a diagonal entry that is not
+ * positive). Workspace: hyde_hysime_workspace_size.
+ * When k == r_max < p every candidate lowered the error: the subspace may
+ * be larger than the candidates cover, and k is then only a lower bound
+ * (call again with a larger r_max, at most 32).
  */
 hyde_status hyde_hysime_workspace_size(int p, long long n, int r_max,
                                        size_t* bytes);
@@ -428,6 +435,17 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
  * every SM keep the one-block kernels of the other streams from finding a
  * free SM. A workspace sized without the cap stays large enough. */
 int hyde_set_grid_sm_cap(int sms);
+
+/* Sets, for the calling host thread, the time limit of the bounded
+ * mbarrier waits in the main loop of the tensor-core Gram kernel (0
+ * restores the default of one second); returns the previous setting. When a
+ * wait runs out the kernel stops its loop, writes HYDE_ERR_TIMEOUT to the
+ * status word of the call (hyde_hyres_info.status for the whole path),
+ * waits at most one second more for its own tensor-core work in flight,
+ * frees its tensor memory and returns; its Gram output is then zero and the
+ * CUDA context stays usable. Meant for testing that path: the default suits
+ * every supported size. (No counterpart in the paper.) */
+unsigned long long hyde_set_wait_limit_ns(unsigned long long ns);
 
 /* Number of kernels one hyde_hyres_denoise call launches on a p x H x W
  * cube: 10 + 2 * (DWT launches), a DWT launch per level, except that the

@@ -69,6 +69,7 @@ SIGNATURES = {
                                          c_vp]),
     "hyde_hyres_kernel_launches": (c_int, [c_int, c_int, c_int, ctypes.POINTER(HydeParams)]),
     "hyde_set_grid_sm_cap": (c_int, [c_int]),
+    "hyde_set_wait_limit_ns": (ctypes.c_ulonglong, [ctypes.c_ulonglong]),
     "hyde_hyres_denoise_scaled": (c_int, [c_vp, c_vp, c_int, c_int, c_int,
                                           ctypes.POINTER(HydeParams), c_vp, c_vp, c_vp, c_size,
                                           c_vp]),

@@ -135,7 +135,9 @@ def hysime(Y: torch.Tensor, r_max: int = 32) -> dict:
     float32, CUDA) with the ``min(r_max, p, 32)`` leading eigenvectors of the
     signal correlation as candidates. Synchronises to read the dimension;
     returns ``k``, ``E`` (``p x k``, the kept eigenvectors in ascending
-    delta), ``idx``, and all candidates' ``V``, ``delta`` and ``evals``."""
+    delta), ``idx``, all candidates' ``V``, ``delta`` and ``evals``, and
+    ``saturated`` (every candidate kept while there are fewer candidates
+    than bands: ``k`` is then only a lower bound)."""
     Y = _cuda_f32(Y, "Y")
     lib = _lib.load()
     p = Y.shape[0]
@@ -156,8 +158,10 @@ def hysime(Y: torch.Tensor, r_max: int = 32) -> dict:
            "hyde_hysime")
     kk = int(k.item())
     keep = idx[:kk].long()
+    # every candidate kept with fewer candidates than bands: k is a lower bound
+    saturated = kk == r and r < p
     return dict(k=kk, E=V[:, keep], idx=keep, V=V, delta=delta, evals=evals,
-                status=int(status.item()))
+                status=int(status.item()), saturated=saturated)
 
 
 def dwt2(x: torch.Tensor, levels: int) -> torch.Tensor:

@@ -11,6 +11,7 @@ namespace hyde {
 
 thread_local bool tl_pdl = true;
 thread_local int tl_sm_cap = 0;
+thread_local unsigned long long tl_wait_ns = 0;
 
 int device_sm_count() {
     int dev = 0;
@@ -721,6 +722,12 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H, i
 int hyde_set_grid_sm_cap(int sms) {
     const int prev = tl_sm_cap;
     tl_sm_cap = sms > 0 ? sms : 0;
+    return prev;
+}
+
+unsigned long long hyde_set_wait_limit_ns(unsigned long long ns) {
+    const unsigned long long prev = tl_wait_ns;
+    tl_wait_ns = ns;
     return prev;
 }
 

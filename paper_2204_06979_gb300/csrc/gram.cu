@@ -11,7 +11,6 @@
 // all 32 banks. Each block writes its float
 // partial; a second kernel sums the partials in double and mirrors the
 // triangle.
-#include <mutex>
 
 #include "hyde_internal.cuh"
 
@@ -387,30 +386,23 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& g,
 // global memory, reserved when the module is loaded onto a GPU and held by
 // every GPU that loads the library until the process exits. Host code cannot
 // use the array's name as a device pointer (it names a host-side shadow), so
-// the device address is looked up once per device with that device current.
+// its device address is looked up with the caller's device current. The
+// lookup is repeated on every call (it allocates nothing and is cheap once
+// the module is loaded): a cached address would go stale when the caller
+// resets the device and the module is loaded again elsewhere.
 // --------------------------------------------------------------------------
 namespace hyde {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_gram_scratch[kNoAllocScratchBytes];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 hyde_status gram_scratch_for_current_device(float** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HYDE_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* addr = nullptr;
-        if (cudaGetSymbolAddress(&addr, g_gram_scratch) != cudaSuccess || !addr)
-            return HYDE_ERR_CUDA;
-        g_scratch_addr[dev] = addr;
-    }
-    *out = reinterpret_cast<float*>(g_scratch_addr[dev]);
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_gram_scratch) != cudaSuccess || !addr)
+        return HYDE_ERR_CUDA;
+    *out = reinterpret_cast<float*>(addr);
     return HYDE_OK;
 }
 

@@ -42,6 +42,7 @@ struct TcPlan {
     int tmem_cols; // allocated TMEM columns
     int stages;    // shared-memory stages (<= kTcMaxStages)
     size_t stage_bytes, smem;
+    unsigned long long wait_ns;   // limit of the main-loop mbarrier waits
 };
 
 // Producer warps 0..7 convert; warp 8 issues the MMAs. Each producer thread
@@ -160,7 +161,7 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
             if (it >= S) {
                 // the MMAs that last read this stage (iteration it - S) are done
                 const uint32_t par = (uint32_t)((it / S - 1) & 1);
-                if (!mbar_wait_bounded(smem_u32(&empty_bar[s]), par)) *abort_v = 1;
+                if (!mbar_wait_bounded(smem_u32(&empty_bar[s]), par, P.wait_ns)) *abort_v = 1;
             }
             if (*abort_v) break;
             uint8_t* st = gbase + (size_t)s * P.stage_bytes;
@@ -182,7 +183,7 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
         long long issued = 0;
         for (long long it = 0; it < iters; ++it) {
             const int s = (int)(it % S);
-            if (!mbar_wait_bounded(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1))) {
+            if (!mbar_wait_bounded(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), P.wait_ns)) {
                 *abort_v = 1;
                 break;
             }
@@ -209,11 +210,13 @@ gram_tc_kernel(const float* __restrict__ Y, int p, long long n, TcPlan P,
             umma_commit(smem_u32(&empty_bar[s]));
             issued = it + 1;
         }
-        // MMAs complete in order: the last commit covers all of them (bounded)
+        // MMAs complete in order: the last commit covers all of them (bounded,
+        // never by less than one second, however short the main-loop limit)
         if (issued > 0) {
             const long long last = issued - 1;
             if (!mbar_wait_bounded(smem_u32(&empty_bar[(int)(last % S)]),
-                                   (uint32_t)((last / S) & 1)))
+                                   (uint32_t)((last / S) & 1),
+                                   P.wait_ns > kWaitNs ? P.wait_ns : kWaitNs))
                 *abort_v = 1;
         }
     }
@@ -313,7 +316,8 @@ hyde_status gram_tc_partial_bytes(int p, size_t* bytes) {
 hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, double* R,
                            int* status, cudaStream_t s) {
     if (p < 1 || p > kMaxBandsGram || n < 1) return HYDE_ERR_SHAPE;
-    const TcPlan P = tc_plan(p);
+    TcPlan P = tc_plan(p);
+    P.wait_ns = wait_limit_ns();
     if (P.stages < 2 || P.smem > 227 * 1024 || P.tmem_cols > 512) return HYDE_ERR_SHAPE;
     const int sms = device_sm_count();
     if (sms <= 0) return HYDE_ERR_CUDA;

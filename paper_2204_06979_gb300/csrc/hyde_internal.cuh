@@ -119,6 +119,14 @@ struct PdlOff {
 // that each window's multi-block kernels leave SMs free for the one-block
 // kernels of the other windows.
 extern thread_local int tl_sm_cap;
+
+// Time limit of the bounded mbarrier waits in the main loop of the
+// tensor-core Gram kernel, for kernels launched from this host thread
+// (0: the default, one second). A shorter limit exists to exercise the
+// timeout path; see hyde_set_wait_limit_ns.
+extern thread_local unsigned long long tl_wait_ns;
+inline unsigned long long wait_limit_ns() { return tl_wait_ns ? tl_wait_ns : 1000000000ull; }
+
 struct SmCap {
     int prev;
     explicit SmCap(int cap) : prev(tl_sm_cap) { tl_sm_cap = cap; }

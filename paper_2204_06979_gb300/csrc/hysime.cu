@@ -21,17 +21,23 @@
 namespace hyde {
 namespace {
 
-// R_n and R_x from R and Q (Q symmetrised), one element per thread.
+// R_n and R_x from R and Q (Q symmetrised), one element per thread. The
+// diagonal of the inverse of a positive definite matrix is positive; a
+// refined inverse whose diagonal is not (a singular or badly conditioned
+// Gram matrix) is reported as HYDE_ERR_NUMERIC.
 __global__ void __launch_bounds__(256)
 hysime_form_kernel(const double* __restrict__ R, const double* __restrict__ Q, int p,
-                   double inv_n, double* __restrict__ Rn, double* __restrict__ Rx) {
+                   double inv_n, double* __restrict__ Rn, double* __restrict__ Rx,
+                   int* status) {
     pdl_wait();
     pdl_trigger();
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)p * p) return;
     const int i = (int)(e / p), j = (int)(e - (long long)i * p);
     const double qs = 0.5 * (Q[(long long)i * p + j] + Q[(long long)j * p + i]);
-    const double di = 1.0 / Q[(long long)i * p + i], dj = 1.0 / Q[(long long)j * p + j];
+    const double qii = Q[(long long)i * p + i], qjj = Q[(long long)j * p + j];
+    if (i == j && !(qii > 0.0 && isfinite(qii))) set_status(status, HYDE_ERR_NUMERIC);
+    const double di = 1.0 / qii, dj = 1.0 / qjj;
     const double rn = di * qs * dj;
     Rn[e] = rn * inv_n;
     Rx[e] = (R[e] - (i == j ? 2.0 * di : 0.0) + rn) * inv_n;
@@ -173,7 +179,7 @@ extern "C" hyde_status hyde_hysime(const float* Y, int p, long long n, int r_max
     if (st != HYDE_OK) return st;
     const long long pp = (long long)p * p;
     launch_pdl(hysime_form_kernel, (unsigned)((pp + 255) / 256), 256, 0, stream, R, Q, p, inv_n,
-               Rn, Rx);
+               Rn, Rx, status);
     st = launch_eig_top(Rx, nullptr, p, r_max, evals, E, status, stream);
     if (st != HYDE_OK) return st;
     launch_pdl(hysime_delta_kernel, r_max, kHsThreads, 0, stream, R, Rn, E, p, r_max, inv_n,

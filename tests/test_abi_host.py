@@ -243,3 +243,12 @@ def test_hysime_rejects_bad_arguments_on_host(lib):
     assert lib.hyde_hysime(None, 32, 4096, 8, 1, 2, 3, 4, 5, None, 6, 1 << 20, None) == 1
     assert lib.hyde_hysime(1, 32, 4096, 8, 1, None, 3, 4, 5, None, 6, 1 << 20, None) == 1
     assert lib.hyde_hysime(1, 32, 16, 8, 1, 2, 3, 4, 5, None, 6, 1 << 20, None) == 2
+
+
+def test_wait_limit_setter_round_trip(lib):
+    """hyde_set_wait_limit_ns returns the previous limit; 0 is the default
+    (one second)."""
+    prev = lib.hyde_set_wait_limit_ns(1234)
+    assert prev == 0
+    assert lib.hyde_set_wait_limit_ns(0) == 1234
+    assert lib.hyde_set_wait_limit_ns(0) == 0

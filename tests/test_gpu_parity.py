@@ -135,6 +135,55 @@ def test_eig_matches_oracle(hyde, cfg):
     assert np.max(res) < 1e-5
 
 
+@pytest.mark.parametrize("H,W,p,m,seed,r", [
+    (349, 1905, 144, 12, 2, 20),    # the benchmark cube's whitened Gram matrix
+    (88, 48, 200, 12, 4, 20),       # a small sliding window: n ~ 21 p
+    (128, 128, 200, 12, 6, 20),     # a large sliding window
+])
+def test_eig_at_size(hyde, H, W, p, m, seed, r):
+    """The eigensolver on the whitened Gram matrices it meets on the
+    benchmark cube (p = 144) and on sliding windows (p = 200), fed the
+    oracle's FP64 matrix. Bounds of a float32 solver, with u = 2^-24 and e_0
+    the largest eigenvalue: eigenvalues and residuals ||A v - e v|| within
+    p u e_0; an eigenvector within sin(angle) <= 2 p u / g + 1e-6 of the
+    oracle's, g its gap to the neighbouring eigenvalues relative to e_0; the
+    leading invariant subspace up to the largest relative gap g* inside the
+    top r (signal against noise) within 2 p u / g* as a projector. (LAPACK's
+    float32 solver meets each bound with a factor of 10 or more to spare on
+    these three matrices.)"""
+    c = make_cube(H, W, p, m=m, seed=seed)
+    R = O.gram(c["Y"])
+    Rw = O.whiten_gram(R, O.noise_est_regression(R, H * W))
+    e_ref, V_ref = O.eig_desc(Rw)
+    evals, V, status = hyde.eig_sym_top(_t(Rw), r)
+    assert int(status.item()) == 0
+    evals = evals.cpu().numpy()
+    V = V.cpu().numpy()
+    e0, pu = e_ref[0], p * 2.0 ** -24
+    assert np.max(np.abs(evals - e_ref[:r])) < pu * e0, np.max(np.abs(evals - e_ref[:r])) / e0
+    assert np.max(np.abs(V.T @ V - np.eye(r))) < 1e-5
+    res = np.linalg.norm(Rw @ V - V * evals, axis=0) / e0
+    assert np.max(res) < pu, np.max(res)
+    g = np.abs(np.diff(e_ref[: r + 1])) / e0
+    for i in range(r):
+        gap = min(g[i], g[i - 1] if i > 0 else np.inf)
+        assert _sin_angle(V[:, i], V_ref[:, i]) <= 2 * pu / gap + 1e-6, (i, gap)
+    s = int(np.argmax(g[: r - 1])) + 1          # leading block 0..s-1
+    P = V[:, :s] @ V[:, :s].T
+    Pr = V_ref[:, :s] @ V_ref[:, :s].T
+    assert np.linalg.norm(P - Pr, 2) <= 2 * pu / g[s - 1], (s, g[s - 1])
+    # the sign rule: the entry of largest magnitude is positive
+    piv = np.argmax(np.abs(V), axis=0)
+    assert np.all(V[piv, np.arange(r)] > 0)
+
+
+def _sin_angle(v, w):
+    """Sine of the angle between the lines through v and w."""
+    v = v / np.linalg.norm(v)
+    w = w / np.linalg.norm(w)
+    return float(np.linalg.norm(v - (v @ w) * w))
+
+
 # ------------------------------------------------------------------- SURE
 
 def test_sure_table_matches_oracle(hyde):
@@ -164,7 +213,29 @@ def _check_hyres(hyde, Y, L, r_max, K=64, tol=REL_L2_PATH, threshold_ll=False):
     assert np.max(np.abs(mid["sigma"].cpu().numpy() / o["sigma"] - 1)) < 2e-5
     err = O.rel_l2(X, o["X"])
     assert err < tol, err
+    _check_per_band(X, o["X"], 10 * tol)
     return o, X, info, mid
+
+
+def _check_per_band(X, ref, tol):
+    """Per-band relative L2 error and per-band largest absolute error
+    (relative to the band's largest magnitude), so that a defect confined to
+    a few rows or columns of some bands (the cropped padding at the bottom
+    and right edges, one band's weights) cannot hide inside the whole-cube
+    norm."""
+    p = ref.shape[0]
+    d = (np.asarray(X, dtype=np.float64) - ref).reshape(p, -1)
+    r = ref.reshape(p, -1)
+    per_band = np.linalg.norm(d, axis=1) / np.linalg.norm(r, axis=1)
+    assert np.max(per_band) < tol, (int(np.argmax(per_band)), float(np.max(per_band)))
+    peak = np.max(np.abs(d), axis=1) / np.max(np.abs(r), axis=1)
+    assert np.max(peak) < tol, (int(np.argmax(peak)), float(np.max(peak)))
+    # the last row and column (where the symmetric padding is cropped) alone
+    H, W = ref.shape[1], ref.shape[2]
+    Xa = np.asarray(X, dtype=np.float64)
+    for sl in ((slice(None), H - 1, slice(None)), (slice(None), slice(None), W - 1)):
+        e = np.linalg.norm(Xa[sl] - ref[sl]) / np.linalg.norm(ref[sl])
+        assert e < tol, e
 
 
 def test_hyres_c0(hyde):

@@ -52,8 +52,11 @@ def test_windows_small_scene_full_parity(hyde):
 def test_windows_full_scene_sampled(hyde):
     """2048 x 2048 x 200 scene, 512 windows of sides 48..256 with 16-px
     context, per-core SNR U[5, 20] dB, db2 with 3 levels, r <= 20; the whole
-    scene through the captured graph, six windows checked against the oracle
-    (the smallest, the largest and four drawn at random)."""
+    scene through the captured graph. Every pixel of the scene must be
+    written (the output starts as NaN) and finite; 18 windows are checked
+    against the oracle (the smallest, the largest, window 16 and 15 drawn at
+    random), one by one and together as a relative L2 error over their
+    cores."""
     H = W = 2048
     p, L, r = 200, 3, 20
     T = make_window_table(H, W, depth=9, context=16, min_side=32, max_side=224, seed=4)
@@ -62,18 +65,25 @@ def test_windows_full_scene_sampled(hyde):
     X = torch.zeros_like(Y)
     win = hyde.HyResWindows(p, H, W, T, L, r, n_slots=64)
     win.capture(Y, X)
-    X.zero_()
+    X.fill_(float("nan"))
     win.replay()
     torch.cuda.synchronize()
     infos = win.infos()
     assert all(i["status"] == 0 for i in infos)
+    # the cores tile the scene: every pixel written, none left NaN or Inf
+    assert bool(torch.isfinite(X).all())
     areas = T[:, 2] * T[:, 3]
     rng = np.random.default_rng(0)
     picks = {int(np.argmin(areas)), int(np.argmax(areas))}
-    picks |= set(int(k) for k in rng.choice(len(T), size=4, replace=False))
     picks.add(16)   # 88 x 48 px x 200 bands: SURE keeps all r_max components
+    rest = [k for k in range(len(T)) if k not in picks]
+    picks |= set(int(k) for k in rng.choice(rest, size=15, replace=False))
+    num = den = 0.0
     for k in sorted(picks):
-        _check_window(sc["Y"], T[k], L, r, infos[k], X, k)
+        got, ref = _check_window(sc["Y"], T[k], L, r, infos[k], X, k)
+        num += float(np.sum((got.astype(np.float64) - ref) ** 2))
+        den += float(np.sum(ref ** 2))
+    assert np.sqrt(num / den) < 1e-3
 
 
 def _check_window(Y, row, L, r, info, X, k):
@@ -102,3 +112,4 @@ def _check_window(Y, row, L, r, info, X, k):
         ref = o2["X"][:, cy - y0:cy - y0 + ch, cx - x0:cx - x0 + cw]
     tol = 1e-3 if choice[0] == r else 1e-5
     assert O.rel_l2(got, ref) < tol, (k, O.rel_l2(got, ref))
+    return got, ref

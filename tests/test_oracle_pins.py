@@ -754,3 +754,76 @@ def test_hysime_scale_and_band_permutation():
     assert h3["k"] == h["k"]
     P, P3 = h["E"] @ h["E"].T, h3["E"] @ h3["E"].T
     assert np.allclose(P3, P[np.ix_(perm, perm)], atol=1e-8)
+
+
+# ---------------------------------------------------------------- lambda grid
+
+def test_lambda_grid_golden_values():
+    """Grid points against decimal values worked out at 40 digits
+    (tests/golden/lambda_grid.txt): N = 675,840 is the padded pixel count of
+    the 349 x 1905 cube at five levels (352 x 1920), N = 4096 the 64 x 64
+    cube's. A log10 in place of ln, a missing factor 2 or a K in place of
+    K - 1 each miss these by far more than the tolerance."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "lambda_grid.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 5
+    for N, K, k, val in rows:
+        lams = O.lambda_grid(int(N), int(K))
+        assert lams.shape == (int(K),)
+        assert abs(lams[int(k)] - float(val)) < 4e-15 * float(val)
+
+
+def test_lambda_grid_top_is_universal_threshold():
+    """The top point lambda_max satisfies N exp(-lambda_max^2 / 2) = 1, the
+    defining property of the universal threshold (N times the Gaussian tail
+    density ratio at lambda_max is one); lambda_0 = 0 and the grid is
+    uniform."""
+    for N in (2, 17, 4096, 675840, 10 ** 9):
+        lams = O.lambda_grid(N, 64)
+        assert lams[0] == 0.0
+        assert abs(N * np.exp(-lams[-1] ** 2 / 2.0) - 1.0) < 1e-12
+        d = np.diff(lams)
+        assert np.max(np.abs(d - d[0])) < 1e-14 * lams[-1]
+    assert O.lambda_grid(4096, 2).tolist() == [0.0, O.lambda_grid(4096, 64)[-1]]
+
+
+# ---------------------------------------------------------------- metrics
+
+def test_rel_l2_hand_case_and_operand_order():
+    """||est - ref|| / ||ref||: ref = (3, 4) has norm 5; est = (3, 5.25)
+    differs by 1.25 -> 0.25. With est = (6, 8) the error norm is 5 -> 1.0,
+    and the swapped call divides by ||(6, 8)|| = 10 -> 0.5, so the
+    denominator is the second argument."""
+    ref = np.array([[3.0, 4.0]])
+    assert abs(O.rel_l2(np.array([[3.0, 5.25]]), ref) - 0.25) < 1e-15
+    assert abs(O.rel_l2(np.array([[6.0, 8.0]]), ref) - 1.0) < 1e-15
+    assert abs(O.rel_l2(ref, np.array([[6.0, 8.0]])) - 0.5) < 1e-15
+    assert O.rel_l2(ref, ref) == 0.0
+
+
+def test_psnr_hand_case():
+    """Two bands of two pixels. Band 0: clean (1, 2), estimate (1, 1): MSE
+    1/2, peak 2 -> 10 log10(4 / 0.5) = 30 log10 2. Band 1: clean (3, 4),
+    estimate (3, 5): MSE 1/2, peak 4 -> 10 log10(16 / 0.5) = 50 log10 2.
+    Mean over bands 40 log10 2 = 12.0412 dB. The peak comes from the clean
+    band: taking it from the estimate (1 and 5) gives another value, and so
+    does one MSE over the whole cube."""
+    clean = np.array([[1.0, 2.0], [3.0, 4.0]])
+    est = np.array([[1.0, 1.0], [3.0, 5.0]])
+    log2 = 0.30102999566398119521373889472449302676818988146211   # log10(2)
+    assert abs(O.psnr(clean, est) - 40.0 * log2) < 1e-13
+    # three-axis input [p][H][W] reads the same
+    assert abs(O.psnr(clean.reshape(2, 1, 2), est.reshape(2, 1, 2)) - 40.0 * log2) < 1e-13
+
+
+def test_sam_hand_case():
+    """Pixel 0: clean (1, 0), estimate (1, 1) -> angle pi/4. Pixel 1: clean
+    (0, 1), estimate (0, 2) -> angle 0 (scale does not matter). Mean pi/8.
+    The layout is [band][pixel]: the transposed reading pairs (1, 0) with
+    (1, 0) and (0, 1) with (1, 2) and gives a different mean."""
+    clean = np.array([[1.0, 0.0], [0.0, 1.0]])
+    est = np.array([[1.0, 0.0], [1.0, 2.0]])
+    assert abs(O.sam(clean, est) - np.pi / 8.0) < 1e-15
+    assert abs(O.sam(clean.T, est.T) - np.pi / 8.0) > 1e-3
+    assert O.sam(clean, 3.0 * clean) == 0.0

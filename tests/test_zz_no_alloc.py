@@ -1,4 +1,5 @@
-"""The allocation-free Gram entry point against the regular one.
+"""The allocation-free Gram entry point against the regular one and the
+FP64 oracle.
 
 ``hyde_gram_noalloc`` serves callers that cannot hand the library a
 workspace because they may not allocate device memory themselves: code
@@ -16,6 +17,8 @@ import ctypes
 import numpy as np
 import pytest
 import torch
+
+import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +45,7 @@ def test_gram_noalloc_matches_workspace_gram_twice(p, H, W):
     Y = torch.from_numpy((rng.standard_normal((p, H, W)) + 0.25).astype(np.float32)).cuda()
     n = H * W
     ref = _gram_via_workspace(lib, Y, p, n).cpu().numpy()
+    exact = O.gram(Y.cpu().numpy())
     stream = torch.cuda.current_stream().cuda_stream
     for _ in range(2):   # the shared array keeps the previous call's contents
         R = torch.full((p, p), np.nan, dtype=torch.float64, device="cuda")
@@ -50,6 +54,8 @@ def test_gram_noalloc_matches_workspace_gram_twice(p, H, W):
         assert np.all(np.isfinite(got))
         # same tolerance as the Gram parity tests: float partial sums
         assert np.max(np.abs(got - ref)) < 2e-6 * np.max(np.abs(ref))
+        # and the same bound against the FP64 oracle's Y^T Y
+        assert np.max(np.abs(got - exact)) < 2e-6 * np.max(np.abs(exact))
 
 
 def test_gram_noalloc_rejects_bad_arguments():
