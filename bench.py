@@ -56,6 +56,17 @@ NCU_TRAFFIC: dict = {
 }
 
 
+def _tf32_gram_flops(n: int, p: int) -> float:
+    """Tensor-core flops of the split-TF32 Gram as issued: per pixel, the
+    principal block (M = 128 rows, N = 32/64/128 columns) twice, and for p >
+    128 the two 128 x (p' - 128) blocks three times each (p' = p rounded up
+    to 16)."""
+    Np = -(-p // 16) * 16
+    Na = 32 if p <= 32 else 64 if p <= 64 else 128
+    nb = max(Np - 128, 0)
+    return 2.0 * n * 128 * (2 * Na + 6 * nb)
+
+
 def _small_dense_flops(stage: str, p: int, r: int) -> float:
     """Algorithmic flops of the single-block stages: Householder
     tridiagonalisation 4p^3/3 + back-transformation of r vectors 4p^2 r
@@ -273,10 +284,16 @@ def torch_device_index() -> int:
     return torch.cuda.current_device()
 
 
-def _form_precision(args, dev, cube, flush, stream) -> dict:
+def _form_precision_tf32(args, dev, cube, flush, stream) -> dict:
+    """The benchmark cube with the Gram matrix on the tensor cores (split-TF32
+    compensated products, FP32-accurate)."""
+    return _form_precision(args, dev, cube, flush, stream, tf32=True)
+
+
+def _form_precision(args, dev, cube, flush, stream, tf32: bool = False) -> dict:
     """The benchmark cube with the Gram matrix on the tensor cores (split-BF16
-    compensated products), with its error against the FP64 oracle's Gram
-    matrix and output."""
+    compensated products, or split-TF32 with tf32), with its error against
+    the FP64 oracle's Gram matrix and output."""
     import numpy as np
     import torch
     import oracle as O
@@ -286,7 +303,7 @@ def _form_precision(args, dev, cube, flush, stream) -> dict:
     Y = torch.from_numpy(cube["Y"]).to(dev)
     X = torch.empty_like(Y)
     h = api.HyRes(p, H, W, w["levels"], w["r_max"], w["n_lambda"], device=dev,
-                  precision=api.PREC_BF16X3)
+                  precision=api.PREC_TF32X3 if tf32 else api.PREC_BF16X3)
     out = _time_form(lambda: h(Y, X), args, flush, stream, p * H * W)
     torch.cuda.synchronize(dev)
     info = h.result_info()
@@ -297,7 +314,9 @@ def _form_precision(args, dev, cube, flush, stream) -> dict:
     Xg = X.cpu().numpy().astype(np.float64)
     d = np.sqrt(np.outer(np.diag(R), np.diag(R)))
     out.update({
-        "precision": "bf16x3 (Gram on tcgen05, split-BF16 compensated, FP32 accumulation)",
+        "precision": ("tf32x3 (Gram on tcgen05, split-TF32 compensated, TMEM windows of 64 "
+                      "pixels added in FP32 registers)" if tf32 else
+                      "bf16x3 (Gram on tcgen05, split-BF16 compensated, FP32 accumulation)"),
         "errors_vs_fp64_oracle": {
             "gram_max_rel": float(np.max(np.abs(Rg - R) / d)),
             "sigma_max_rel": float(np.max(np.abs(mid["sigma"].cpu().numpy() / o["sigma"] - 1))),
@@ -404,7 +423,7 @@ def run_gb300(args) -> None:
     voxels = p * n
     Yd = torch.from_numpy(cube["Y"]).to(dev)
     Xd = torch.empty_like(Yd)
-    prec = {"fp32": api.PREC_FP32, "bf16x3": api.PREC_BF16X3,
+    prec = {"fp32": api.PREC_FP32, "tf32x3": api.PREC_TF32X3, "bf16x3": api.PREC_BF16X3,
             "bf16x3_all": api.PREC_BF16X3_ALL}[args.precision]
     lmode = {"shared": api.LAMBDA_SHARED, "per_component": api.LAMBDA_PER_COMPONENT,
              "per_level": api.LAMBDA_PER_LEVEL}[args.lambda_mode]
@@ -476,7 +495,24 @@ def run_gb300(args) -> None:
     peaks = _measured_peaks()
     sbytes = _stage_bytes(r_star)
     dominant = max(stage_avg, key=stage_avg.get)
-    if dominant == "gram" and args.precision != "fp32":
+    if dominant == "gram" and args.precision == "tf32x3":
+        # tf32 MMA work per pixel: the principal 128-band block twice (H H^T and
+        # H (2L)^T), the other band blocks three times; tensor peak for tf32 is
+        # half the measured bf16 rate
+        flops = _tf32_gram_flops(n, p)
+        tc_peak = peaks["bf16_tflops"] / 2
+        achieved = flops / (stage_avg["gram"] / 1e3) / 1e12
+        bts = sbytes["gram"]
+        roofline = {"kernel": "gram_tf32 (tcgen05 split-TF32, TMA) + reduce", "bound": "hbm",
+                    "achieved": bts / (stage_avg["gram"] / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": bts / (stage_avg["gram"] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                    "peak_source": peaks["source"],
+                    "algorithmic": f"{bts} bytes per launch (4 B per voxel read)",
+                    "tensor": {"achieved_tflops": achieved, "peak_tflops": tc_peak,
+                               "frac": achieved / tc_peak,
+                               "peak_source": "measured bf16 burst / 2 (tf32 rate)",
+                               "flops": flops}}
+    elif dominant == "gram" and args.precision != "fp32":
         flops = 3 * 2 * n * p * p   # three bf16 products per entry (hi hi, hi lo, lo hi)
         tc_peak = peaks["bf16_tflops"]
         achieved = flops / (stage_avg["gram"] / 1e3) / 1e12
@@ -563,7 +599,8 @@ def run_gb300(args) -> None:
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:
         forms = {}
-        for name, fn in (("precision_bf16x3", _form_precision), ("per_level", _form_per_level),
+        for name, fn in (("precision_tf32x3", _form_precision_tf32),
+                         ("precision_bf16x3", _form_precision), ("per_level", _form_per_level),
                          ("diff", _form_diff), ("windows", _form_windows)):
             try:
                 forms[name] = fn(args, dev, cube, flush, stream)
@@ -579,7 +616,10 @@ def run_gb300(args) -> None:
 
     if rank == 0:
         cfg = _config(world)
-        if args.precision == "bf16x3":
+        if args.precision == "tf32x3":
+            cfg["precision"] = "tf32x3 (Gram on tcgen05, split-TF32 compensated, FP32-accurate)"
+            cfg["workload"] += ", Gram on the tensor cores (split-TF32)"
+        elif args.precision == "bf16x3":
             cfg["precision"] = "bf16x3 (Gram on tcgen05, split-BF16 compensated)"
             cfg["workload"] += ", precision form"
         elif args.precision == "bf16x3_all":
@@ -599,7 +639,7 @@ def run_gb300(args) -> None:
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16x3+f32",
+            "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32"}.get(args.precision, "bf16x3+f32"),
             "data": "synthetic", "config": cfg,
             "roofline": roofline,
             "stages": hbm_stages | {k: {"ms": round(v, 4)} for k, v in stage_avg.items()
@@ -799,9 +839,11 @@ def main() -> None:
     ap.add_argument("--sm-cap", type=int, default=None,
                     help="--form diff: SMs each cube's grids are sized for (0: all; "
                          "default: the batch API's choice)")
-    ap.add_argument("--precision", choices=("fp32", "bf16x3", "bf16x3_all"), default="fp32",
-                    help="fp32: plain form (headline); bf16x3: Gram on the tensor cores; "
-                         "bf16x3_all: the projections there too")
+    ap.add_argument("--precision", choices=("fp32", "tf32x3", "bf16x3", "bf16x3_all"),
+                    default="fp32",
+                    help="fp32: plain form (headline); tf32x3: Gram on the tensor cores, "
+                         "split-TF32 (FP32-accurate); bf16x3: Gram on the tensor cores, "
+                         "split-BF16; bf16x3_all: the projections there too")
     ap.add_argument("--lambda-mode", choices=("shared", "per_component", "per_level"),
                     default="shared",
                     help="shared: one SURE threshold for every kept component (headline); "

@@ -58,7 +58,15 @@ typedef enum {
 
 typedef enum {
     HYDE_PREC_FP32 = 0,    /* plain FP32 SIMT arithmetic                      */
-    HYDE_PREC_TF32X3 = 1,  /* reserved (rejected): split-TF32 contractions    */
+    HYDE_PREC_TF32X3 = 1,  /* Gram matrix on the tensor cores, FP32-accurate:
+                              each float is split into tf32 hi (rounded) +
+                              lo = y - hi and y_a y_b is taken as
+                              hi hi + hi lo + lo hi (tcgen05.mma kind::tf32,
+                              TMEM windows of 64 pixels added into FP32
+                              registers, double across SMs); needs p a
+                              multiple of 4 and <= 160 and a 16-byte aligned
+                              cube (HYDE_ERR_SHAPE / INVALID_ARG otherwise);
+                              the other stages as in HYDE_PREC_FP32          */
     HYDE_PREC_BF16X3 = 2,  /* Gram matrix on the tensor cores: each float is
                               split into bf16 hi + lo and y_a y_b is taken as
                               hi hi + hi lo + lo hi (tcgen05.mma, FP32
@@ -157,8 +165,10 @@ int hyde_version(void);
  * pixel-by-band matrix; the spectral statistics of the low-rank model
  * (Sec. 2.1, "low-rank"). Y is float[p][n] band-major (ld = n); R is
  * double[p][p] row-major, full symmetric. Per-block float partial sums are
- * combined in double. precision: HYDE_PREC_FP32 (FP32 FMA) or
- * HYDE_PREC_BF16X3 (split-BF16 products on the tensor cores).
+ * combined in double. precision: HYDE_PREC_FP32 (FP32 FMA), HYDE_PREC_TF32X3
+ * (split-TF32 products on the tensor cores, FP32-accurate; p a multiple of 4,
+ * p <= 160, Y 16-byte aligned) or HYDE_PREC_BF16X3 (split-BF16 products on
+ * the tensor cores).
  */
 hyde_status hyde_gram_workspace_size(int p, long long n, int precision,
                                      size_t* bytes);
@@ -437,7 +447,7 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
 int hyde_set_grid_sm_cap(int sms);
 
 /* Sets, for the calling host thread, the time limit of the bounded
- * mbarrier waits in the main loop of the tensor-core Gram kernel (0
+ * mbarrier waits in the main loop of the tensor-core Gram kernels (0
  * restores the default of one second); returns the previous setting. When a
  * wait runs out the kernel stops its loop, writes HYDE_ERR_TIMEOUT to the
  * status word of the call (hyde_hyres_info.status for the whole path),

@@ -18,6 +18,7 @@ from ._lib import HydeParams, HydeWsLayout, INFO_BYTES, INFO_FORMAT
 
 HYDE_OK = 0
 PREC_FP32 = 0
+PREC_TF32X3 = 1       # Gram on the tensor cores (split-TF32, FP32-accurate)
 PREC_BF16X3 = 2       # Gram on the tensor cores (split-BF16)
 PREC_BF16X3_ALL = 3   # Gram, projection and back-projection on the tensor cores
 LAMBDA_SHARED = 0         # one SURE threshold for every kept component
@@ -84,7 +85,8 @@ def version() -> int:
 
 def gram(Y: torch.Tensor, precision: int = PREC_FP32) -> torch.Tensor:
     """R = Y^T Y of a cube ``Y[p, ...]`` (float32, CUDA) as float64 ``[p, p]``
-    (``precision`` PREC_FP32, or PREC_BF16X3 for the tensor-core form)."""
+    (``precision`` PREC_FP32; PREC_TF32X3 or PREC_BF16X3 for the tensor-core
+    forms)."""
     lib = _lib.load()
     Y = _cuda_f32(Y, "Y")
     p = Y.shape[0]

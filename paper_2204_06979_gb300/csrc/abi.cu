@@ -90,7 +90,7 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     if (!pr) return HYDE_ERR_INVALID_ARG;
     if (pr->wavelet != 2) return HYDE_ERR_INVALID_ARG;
     if (pr->precision != HYDE_PREC_FP32 && pr->precision != HYDE_PREC_BF16X3 &&
-        pr->precision != HYDE_PREC_BF16X3_ALL)
+        pr->precision != HYDE_PREC_BF16X3_ALL && pr->precision != HYDE_PREC_TF32X3)
         return HYDE_ERR_INVALID_ARG;
     if (pr->lambda_mode != HYDE_LAMBDA_SHARED && pr->lambda_mode != HYDE_LAMBDA_PER_COMPONENT &&
         pr->lambda_mode != HYDE_LAMBDA_PER_LEVEL)
@@ -116,7 +116,8 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.N = (long long)Hp * Wp; l.n = n;
     hyde_status st = gram_plan(p, n, &l.gram);
     if (st != HYDE_OK) return st;
-    if (pr->precision != HYDE_PREC_FP32) {   // split-BF16 Gram on the tensor cores
+    if (pr->precision == HYDE_PREC_TF32X3 && !gram_tf32_shape_ok(p, n)) return HYDE_ERR_SHAPE;
+    if (pr->precision != HYDE_PREC_FP32) {   // split-BF16 or split-TF32 Gram on the tensor cores
         size_t tcb = 0;
         st = gram_tc_partial_bytes(p, &tcb);
         if (st != HYDE_OK) return st;
@@ -187,8 +188,9 @@ int hyde_version(void) { return 100; }
 // ------------------------------------------------------------------ Gram
 hyde_status hyde_gram_workspace_size(int p, long long n, int precision, size_t* bytes) {
     if (!bytes) return HYDE_ERR_INVALID_ARG;
-    if (precision == HYDE_PREC_BF16X3) {
+    if (precision == HYDE_PREC_BF16X3 || precision == HYDE_PREC_TF32X3) {
         if (n < 1) return HYDE_ERR_SHAPE;
+        if (precision == HYDE_PREC_TF32X3 && !gram_tf32_shape_ok(p, n)) return HYDE_ERR_SHAPE;
         size_t b = 0;
         hyde_status st = gram_tc_partial_bytes(p, &b);
         if (st != HYDE_OK) return st;
@@ -212,6 +214,10 @@ hyde_status hyde_gram(const float* Y, int p, long long n, int precision, double*
     if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return HYDE_ERR_WORKSPACE;
     if (precision == HYDE_PREC_BF16X3)
         return launch_gram_tc(Y, p, n, reinterpret_cast<float*>(ws), R, nullptr, stream);
+    if (precision == HYDE_PREC_TF32X3) {
+        if (!aligned(Y, 16)) return HYDE_ERR_INVALID_ARG;
+        return launch_gram_tf32(Y, p, n, reinterpret_cast<float*>(ws), R, nullptr, stream);
+    }
     GramPlan g;
     gram_plan(p, n, &g);
     return launch_gram(Y, p, n, g, reinterpret_cast<float*>(ws), R, nullptr, stream);
@@ -395,7 +401,9 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
         cudaSuccess)
         return HYDE_ERR_CUDA;
     // 1. Gram matrix (float SIMT, or split-BF16 on the tensor cores)
-    if (params->precision != HYDE_PREC_FP32)
+    if (params->precision == HYDE_PREC_TF32X3)
+        HYDE_TRY(launch_gram_tf32(Y, p, L.n, at<float>(ws, L.partials), R, status, stream));
+    else if (params->precision != HYDE_PREC_FP32)
         HYDE_TRY(launch_gram_tc(Y, p, L.n, at<float>(ws, L.partials), R, status, stream));
     else
         HYDE_TRY(launch_gram(Y, p, L.n, L.gram, at<float>(ws, L.partials), R, status, stream));

@@ -177,6 +177,14 @@ hyde_status launch_gram(const float* Y, int p, long long n, const GramPlan& plan
 // Split-BF16 (hi*hi + hi*lo + lo*hi) Gram on the tensor cores (tcgen05.mma,
 // accumulators in TMEM); per-SM float partials p x p, summed in double.
 hyde_status gram_tc_partial_bytes(int p, size_t* bytes);
+// Split-TF32 (hi*hi + hi*lo + lo*hi) Gram on the tensor cores, FP32-accurate:
+// TMA loads, TMEM windows of 64 pixels drained into FP32 registers. Needs p a
+// multiple of 4, 4 <= p <= 160 and Y 16-byte aligned; partials as for
+// launch_gram_tc (gram_tc_partial_bytes).
+bool gram_tf32_shape_ok(int p, long long n);
+bool gram_tf32_supported(const float* Y, int p, long long n);
+hyde_status launch_gram_tf32(const float* Y, int p, long long n, float* partials, double* R,
+                             int* status, cudaStream_t s);
 hyde_status launch_gram_tc(const float* Y, int p, long long n, float* partials, double* R,
                            int* status, cudaStream_t s);
 

@@ -153,8 +153,12 @@ def test_remaining_entry_points_reject_bad_arguments_on_host(lib):
     prm = api.params(2, 8, 64)
     # Gram workspace: no output, an unknown precision
     assert lib.hyde_gram_workspace_size(32, 4096, 0, None) == 1
-    assert lib.hyde_gram_workspace_size(32, 4096, 1, ctypes.byref(sz)) == 1
+    assert lib.hyde_gram_workspace_size(32, 4096, 9, ctypes.byref(sz)) == 1
     assert lib.hyde_gram_workspace_size(32, 0, 2, ctypes.byref(sz)) == 2
+    # split-TF32 Gram: p a multiple of 4 and at most 160, checked before any device query
+    assert lib.hyde_gram_workspace_size(37, 4096, 1, ctypes.byref(sz)) == 2
+    assert lib.hyde_gram_workspace_size(164, 4096, 1, ctypes.byref(sz)) == 2
+    assert lib.hyde_gram_workspace_size(32, 0, 1, ctypes.byref(sz)) == 2
     # allocation-free Gram: null pointers; its scratch size is a constant
     assert lib.hyde_gram_noalloc(None, 32, 4096, None, None) == 1
     assert lib.hyde_gram_noalloc_scratch_bytes() == 16 * 1024 * 1024

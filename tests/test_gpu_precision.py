@@ -1,5 +1,6 @@
-"""GPU parity of the precision form: the Gram matrix on the tensor cores with
-split-BF16 compensated products (hi*hi + hi*lo + lo*hi, FP32 accumulation in
+"""GPU parity of the precision forms: the Gram matrix on the tensor cores with
+split-TF32 compensated products (FP32-accurate, held to the FP32 path's
+bars), and with split-BF16 compensated products (hi*hi + hi*lo + lo*hi, FP32 accumulation in
 TMEM, double across SMs), everything else as in the FP32 path; and of the
 all-tensor-core variant, which also takes the projection and back-projection
 as split-BF16 products. Held to the precision form's bar: relative error
@@ -73,3 +74,64 @@ def test_precision_form_against_oracle(hyde, cfg, mode):
     assert dpsnr <= 0.05
     if o["gap"] > 1e-3:
         assert info["rank"] == o["rank"]
+
+
+# ------------------------------------------------------ split-TF32 Gram
+
+@pytest.mark.parametrize("p,H,W", [(32, 64, 64), (144, 97, 131), (128, 40, 40), (160, 33, 65),
+                                   (4, 17, 3), (64, 2, 1001), (24, 77, 131)])
+def test_tf32_gram_matches_oracle(hyde, p, H, W):
+    """Split-TF32 Gram against the FP64 oracle, to the bound of the FP32
+    path's Gram (2e-6 of sqrt(R_ii R_jj)): products exact to 2^-21, at most
+    16 tensor-core additions per TMEM window, windows added in FP32
+    registers, CTAs in double. Odd pixel counts exercise the shifted TMA
+    boxes; p = 160 the second band block."""
+    rng = np.random.default_rng(p + H)
+    Y = (rng.standard_normal((p, H, W)) + 0.5).astype(np.float32)
+    ref = O.gram(Y)
+    got = hyde.gram(_t(Y), precision=hyde.PREC_TF32X3).cpu().numpy()
+    assert np.array_equal(got, got.T)
+    scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    err = np.max(np.abs(got - ref) / scale)
+    assert err < 2e-6, err
+
+
+def test_tf32_gram_full_c1(hyde):
+    c = make_cube(349, 1905, 144, m=12, seed=2)
+    ref = O.gram(c["Y"])
+    got = hyde.gram(_t(c["Y"]), precision=hyde.PREC_TF32X3).cpu().numpy()
+    err = np.max(np.abs(got - ref) / np.sqrt(np.outer(np.diag(ref), np.diag(ref))))
+    print(f"tf32x3 Gram at 349x1905x144: {err:.2e} of sqrt(R_ii R_jj)")
+    assert err < 2e-6, err
+
+
+def test_tf32_gram_rejects_unsupported_shapes(hyde):
+    Y = torch.zeros((37, 100), dtype=torch.float32, device="cuda")
+    with pytest.raises(hyde.HydeError):
+        hyde.gram(Y, precision=hyde.PREC_TF32X3)
+    Y = torch.zeros((168, 100), dtype=torch.float32, device="cuda")
+    with pytest.raises(hyde.HydeError):
+        hyde.gram(Y, precision=hyde.PREC_TF32X3)
+
+
+@pytest.mark.parametrize("cfg", ["c0", "c1", "ragged"])
+def test_tf32_form_matches_oracle_like_fp32(hyde, cfg):
+    """The whole path with the split-TF32 Gram, held to the FP32 path's bars:
+    identical (rank, lambda) and relative L2 error <= 1e-5."""
+    shapes = {"c0": (64, 64, 32, 4, 1, 2, 8), "c1": (349, 1905, 144, 12, 2, 5, 20),
+              "ragged": (77, 131, 24, 3, 31, 3, 6)}
+    H, W, p, m, seed, L, r = shapes[cfg]
+    c = make_cube(H, W, p, m=m, seed=seed)
+    o = O.hyres(c["Y"], L, r)
+    h = hyde.HyRes(p, H, W, L, r, precision=hyde.PREC_TF32X3)
+    X = h(_t(c["Y"])).cpu().numpy()
+    info = h.result_info()
+    mid = h.intermediates()
+    assert info["status"] == 0
+    R = mid["R"].cpu().numpy()
+    gram_err = np.max(np.abs(R - o["R"]) / np.sqrt(np.outer(np.diag(o["R"]), np.diag(o["R"]))))
+    out_err = O.rel_l2(X, o["X"])
+    print(f"{cfg} tf32x3: gram {gram_err:.2e} output {out_err:.2e}")
+    assert gram_err < 2e-6
+    assert (info["rank"], info["lambda_index"]) == (o["rank"], o["k"])
+    assert out_err < 1e-5

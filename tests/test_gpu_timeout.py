@@ -1,9 +1,11 @@
-"""The bounded waits of the tensor-core Gram kernel run out, on purpose.
+"""The bounded waits of the tensor-core Gram kernels run out, on purpose.
 
-Every mbarrier wait inside the tcgen05 Gram kernel is bounded in time. Here
+Every mbarrier wait inside the tcgen05 Gram kernels (split-BF16 and
+split-TF32) is bounded in time. Here
 the limit of its main-loop waits is set to 1 ns (``hyde_set_wait_limit_ns``),
 so the tensor-core issuer gives up at its first wait, before the loaders have
-filled a stage, and the loaders give up when a stage is never released. The
+filled a stage, and the loaders (and, in the split-TF32 kernel, the TMA
+warp and the TMEM drain warps) give up when a stage is never released. The
 kernel must then report HYDE_ERR_TIMEOUT through the device status word,
 leave its output zero, free its tensor memory and return, and the CUDA
 context must stay usable: with the default limit restored the same call
@@ -21,13 +23,15 @@ from synth import make_cube
 pytestmark = pytest.mark.gpu
 
 
-def test_tensor_core_gram_timeout_is_reported_and_recovers(hyde):
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_tensor_core_gram_timeout_is_reported_and_recovers(hyde, prec):
     from paper_2204_06979_gb300 import _lib
     lib = _lib.load()
     c = make_cube(349, 256, 144, m=12, seed=2)
     Y = torch.from_numpy(c["Y"]).cuda()
     p, H, W = c["Y"].shape
-    h = hyde.HyRes(p, H, W, 5, 20, precision=hyde.PREC_BF16X3)
+    precision = hyde.PREC_BF16X3 if prec == "bf16x3" else hyde.PREC_TF32X3
+    h = hyde.HyRes(p, H, W, 5, 20, precision=precision)
     prev = lib.hyde_set_wait_limit_ns(1)
     try:
         h(Y)
