@@ -317,7 +317,8 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
     float* sym = reinterpret_cast<float*>(gbase + op_area);
     float* out = partials + (long long)blockIdx.x * p * p;
     if (drain) {
-        if (ok) {
+        // sym holds Na rows: TMEM lanes Na..127 are padding bands (zero)
+        if (ok && row < Na) {
 #pragma unroll
             for (int c = 0; c < NAH; ++c) sym[row * lda + half * NAH + c] = accA[c];
         }
