@@ -5,11 +5,12 @@
 //
 // Every float y is split into hi = tf32(y) (rounded to nearest) and
 // lo = y - hi (exact in float; the tensor core reads its leading 11 bits,
-// a relative error of 2^-21 of y). The product y_a y_b is taken as
-// hi_a hi_b + hi_a lo_b + lo_a hi_b; the dropped lo_a lo_b is ~2^-22 y_a y_b.
-// On the principal 128 x 128 block the two cross terms come from one product
-// by symmetry: with D = H H^T + H (2L)^T, R = (D + D^T) / 2. The block of
-// bands >= 128 (p <= 160) takes the three products directly.
+// a relative error of 2^-22 of y). The product y_a y_b is taken as
+// hi_a hi_b + hi_a lo_b + lo_a hi_b; the dropped lo_a lo_b is ~2^-24 y_a y_b.
+// Tiles: bands [0, 128) against all Np bands (Np = p rounded to 16; one MMA
+// of N = Np per product), and for p > 128 the corner [Np - 128, Np) against
+// [128, Np) (N = Np - 128). Each MMA reads its whole A operand (128 rows)
+// from shared memory, so few wide MMAs keep the operand traffic low.
 //
 // Data path, one CTA per SM over a contiguous range of 32-pixel chunks:
 //  * a TMA warp loads each chunk into a ring of raw stages. Y is [p][n] with
@@ -19,16 +20,17 @@
 //    box must be a multiple of 4 floats, so band class j is loaded from
 //    x0 - s_j, s_j = (j n) mod 4, in a 36-pixel box;
 //  * four converter warps read the raw boxes at the offset s_j, round hi,
-//    form 2 lo and store both into the 128-byte-swizzled K-major tiles the
+//    form lo and store both into the 128-byte-swizzled K-major tiles the
 //    UMMA descriptors expect (bands as rows, 32 pixels per 128-byte row);
 //  * one thread issues tcgen05.mma kind::tf32 into TMEM accumulators that
 //    are double buffered over windows of two chunks (64 pixels);
 //  * eight drain warps add each finished window into FP32 registers
-//    (tcgen05.ld), so that no TMEM accumulator sums more than 16 tensor-core
+//    (tcgen05.ld), so that no TMEM accumulator sums more than 24 tensor-core
 //    additions (the tensor cores' FP32 accumulation loses ~2^-25 relative per
-//    addition, which over the ~4.4k pixels of a CTA would exceed FP32 accuracy).
-// Each CTA writes its float partial (the principal block symmetrised through
-// shared memory); a second kernel sums the partials in double.
+//    addition, which over the ~4.4k pixels of a CTA would exceed FP32
+//    accuracy).
+// Each CTA writes its float partial; a second kernel sums the partials in
+// double in a fixed order.
 //
 // Every mbarrier wait is bounded in time: a timeout sets HYDE_ERR_TIMEOUT and
 // every role winds down, waiting (bounded) for its own TMA loads and MMAs in
@@ -45,17 +47,20 @@ constexpr int kK = 32;              // pixels per chunk: one 128-byte row of fp3
 constexpr int kKBox = kK + 4;       // pixels per TMA box (room for the shift s_j)
 constexpr int kOpStages = 2;
 constexpr int kMaxRaw = 8;
-constexpr int kWin = 2;             // chunks per TMEM accumulation window
+#ifndef HYDE_TF32_WIN
+#define HYDE_TF32_WIN 2
+#endif
+constexpr int kWin = HYDE_TF32_WIN; // chunks per TMEM accumulation window
 constexpr int kTmaWarp = 0, kMmaWarp = 1, kCvtWarp0 = 2, kCvtWarps = 4;
 constexpr int kDrainWarp0 = kCvtWarp0 + kCvtWarps, kDrainWarps = 8;
 constexpr int kT32Threads = (kDrainWarp0 + kDrainWarps) * 32;
 constexpr int kMaxP = 160;          // bands of the tensor-core Gram
 
 struct T32Plan {
-    int p, Np, Na, nb, rows, q4;
+    int p, Np, NT, NC, rows, q4;
     int raw_stages;
     uint32_t box_bytes, raw_stage_bytes, op_bytes;
-    int buf_cols, tmem_cols;
+    int colT, buf_cols, tmem_cols;
     size_t smem;
     unsigned long long wait_ns;
 };
@@ -64,12 +69,15 @@ __device__ __forceinline__ float tf32_rn(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-template <int NAH, int NBX>
+// NT: columns of the top tile (all bands rounded to 16, or 32/64/128 for
+// p <= 128); NC: columns of the corner tile (0 if p <= 128); H0: columns the
+// first half of the drain warps accumulates (the second half takes the rest
+// of the top tile and the corner, H0 as well).
+template <int NT, int NC, int H0>
 __global__ void __launch_bounds__(kT32Threads, 1)
 gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan P,
                  float* __restrict__ partials, int* status) {
     pdl_wait();
-    pdl_trigger();
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t raw_full[kMaxRaw], raw_empty[kMaxRaw];
     __shared__ uint64_t op_full[kOpStages], op_empty[kOpStages];
@@ -80,7 +88,7 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
     const uint32_t s0 = smem_u32(smem_raw);
     const uint32_t base = (s0 + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - s0);
-    // op stage o: hi tile at base + 2 o op_bytes, 2 lo tile op_bytes after it;
+    // op stage o: hi tile at base + 2 o op_bytes, lo tile op_bytes after it;
     // then the raw stages
     const uint32_t op_area = 2u * kOpStages * P.op_bytes;
     const uint32_t rawb = base + op_area;
@@ -157,12 +165,11 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ MMA issue (1 thread)
         if (lane == 0) {
-            const uint32_t idA = idesc_tf32(128, P.Na);
-            const uint32_t idB = idesc_tf32(128, NBX > 0 ? NBX : 16);
+            const uint32_t idT = idesc_tf32(128, NT);
+            const uint32_t idC = idesc_tf32(128, NC > 0 ? NC : 16);
             const uint32_t bo = 128u * 128u;                       // row 128 of a tile
             const uint32_t co = (uint32_t)(P.Np - 128) * 128u;     // row Np - 128
-            const uint32_t colB1 = (uint32_t)P.Na, colB2 = colB1 + NBX;
-            const uint32_t colC1 = colB2 + NBX, colC2 = colC1 + NBX;
+            const uint32_t colT = (uint32_t)P.colT;
             long long issued = 0;
             for (long long it = 0; it < iters; ++it) {
                 if (*abort_v) break;
@@ -189,17 +196,15 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
                 for (int kk = 0; kk < kK / 8; ++kk) {
                     const uint32_t ko = (uint32_t)kk * 32u;   // 8 tf32 along K
                     const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
-                    umma_tf32(d, sw128_desc(hi + ko), sw128_desc(hi + ko), idA, acc);
-                    umma_tf32(d, sw128_desc(hi + ko), sw128_desc(lo + ko), idA, 1u);
-                    if (NBX > 0) {
-                        // bands [0,128) x [128,Np): hi hi and (hi lo2 + lo2 hi)
-                        umma_tf32(d + colB1, sw128_desc(hi + ko), sw128_desc(hi + bo + ko), idB, acc);
-                        umma_tf32(d + colB2, sw128_desc(hi + ko), sw128_desc(lo + bo + ko), idB, acc);
-                        umma_tf32(d + colB2, sw128_desc(lo + ko), sw128_desc(hi + bo + ko), idB, 1u);
+                    // bands [0,128) x [0,NT): hi hi + hi lo + lo hi
+                    umma_tf32(d + colT, sw128_desc(hi + ko), sw128_desc(hi + ko), idT, acc);
+                    umma_tf32(d + colT, sw128_desc(hi + ko), sw128_desc(lo + ko), idT, 1u);
+                    umma_tf32(d + colT, sw128_desc(lo + ko), sw128_desc(hi + ko), idT, 1u);
+                    if (NC > 0) {
                         // bands [Np-128,Np) x [128,Np)
-                        umma_tf32(d + colC1, sw128_desc(hi + co + ko), sw128_desc(hi + bo + ko), idB, acc);
-                        umma_tf32(d + colC2, sw128_desc(hi + co + ko), sw128_desc(lo + bo + ko), idB, acc);
-                        umma_tf32(d + colC2, sw128_desc(lo + co + ko), sw128_desc(hi + bo + ko), idB, 1u);
+                        umma_tf32(d, sw128_desc(hi + co + ko), sw128_desc(hi + bo + ko), idC, acc);
+                        umma_tf32(d, sw128_desc(hi + co + ko), sw128_desc(lo + bo + ko), idC, 1u);
+                        umma_tf32(d, sw128_desc(lo + co + ko), sw128_desc(hi + bo + ko), idC, 1u);
                     }
                 }
                 umma_commit(smem_u32(&op_empty[o]));
@@ -214,7 +219,7 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
                 *abort_v = 1;
         }
     } else if (warp < kDrainWarp0) {
-        // ------------------------------------------- split into hi and 2 lo
+        // ------------------------------------------------ split into hi and lo
         const int ct = tid - kCvtWarp0 * 32;
         for (long long it = 0; it < iters; ++it) {
             if (*abort_v) break;
@@ -243,7 +248,7 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
                 for (int e = 0; e < 4; ++e) {
                     v[e] = (4 * k4 + e < valid) ? src[e] : 0.f;
                     h[e] = tf32_rn(v[e]);
-                    l[e] = 2.0f * (v[e] - h[e]);
+                    l[e] = v[e] - h[e];
                 }
                 const uint32_t off = (uint32_t)b * 128u + ((uint32_t)(k4 ^ (b & 7)) << 4);
                 *reinterpret_cast<float4*>(hi_t + off) = make_float4(h[0], h[1], h[2], h[3]);
@@ -256,17 +261,22 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
     }
 
     // ---------------------------------------------- drain warps (and output)
+    // A drain thread owns TMEM lane `row` and H0 columns in blocks of 16:
+    // half 0 the top tile's columns [0, H0); half 1 the top tile's columns
+    // [H0, NT), then the corner's [0, NC). Block k maps to TMEM column tcol(k)
+    // and to the partial's (band, column) (orow(k), ocol(k)).
     const int dw = warp - kDrainWarp0;
     const bool drain = dw >= 0;
     const int quad = warp & 3, half = drain ? dw >> 2 : 0;
     const int row = 32 * quad + lane;                     // TMEM lane
     const uint32_t lane_addr = (uint32_t)(32 * quad) << 16;
-    float accA[NAH];
-    float accX[NBX > 0 ? NBX : 1];
+    constexpr int T1 = NT - H0;                           // top columns of half 1
+    auto tcol = [&](int k) -> int {
+        return half == 0 ? P.colT + 16 * k : (16 * k < T1 ? P.colT + H0 + 16 * k : 16 * k - T1);
+    };
+    float acc[H0];
 #pragma unroll
-    for (int c = 0; c < NAH; ++c) accA[c] = 0.f;
-#pragma unroll
-    for (int c = 0; c < (NBX > 0 ? NBX : 1); ++c) accX[c] = 0.f;
+    for (int c = 0; c < H0; ++c) acc[c] = 0.f;
     if (drain) {
         for (long long w = 0; w < nwin; ++w) {
             if (*abort_v) break;
@@ -279,28 +289,12 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
             tc_fence_after();
             const uint32_t t0 = tmem + lane_addr + (uint32_t)b * (uint32_t)P.buf_cols;
 #pragma unroll
-            for (int c = 0; c < NAH; c += 16) {
+            for (int k = 0; k < H0 / 16; ++k) {
                 uint32_t r[16];
-                tmem_ld16_nowait(t0 + (uint32_t)(half * NAH + c), r);
+                tmem_ld16_nowait(t0 + (uint32_t)tcol(k), r);
                 tmem_wait_ld();
 #pragma unroll
-                for (int e = 0; e < 16; ++e) accA[c + e] += __uint_as_float(r[e]);
-            }
-            if (NBX > 0) {
-                // half 0: the [0,128) x [128,Np) block, half 1: [Np-128,Np) x [128,Np)
-                const uint32_t x1 = (uint32_t)P.Na + (uint32_t)(half * 2 * NBX);
-#pragma unroll
-                for (int c = 0; c < NBX; c += 16) {
-                    uint32_t r1[16];
-                    tmem_ld16_nowait(t0 + x1 + (uint32_t)c, r1);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) accX[c + e] += __uint_as_float(r1[e]);
-                    tmem_ld16_nowait(t0 + x1 + (uint32_t)(NBX + c), r1);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) accX[c + e] += 0.5f * __uint_as_float(r1[e]);
-                }
+                for (int e = 0; e < 16; ++e) acc[16 * k + e] += __uint_as_float(r[e]);
             }
             tc_fence_before();
             mbar_arrive(smem_u32(&acc_empty[b]));
@@ -310,40 +304,26 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
     __syncthreads();
     const bool ok = iters > 0 && !abort_s;
     if (abort_s && tid == 0) set_status(status, HYDE_ERR_TIMEOUT);
-    // The principal block through shared memory (the raw stages are idle now:
-    // every TMA load has landed): sym[i][j] = D[i][j], then (D + D^T) / 2.
-    const int p = P.p, Na = P.Na;
-    const int lda = Na + 1;
-    float* sym = reinterpret_cast<float*>(gbase + op_area);
+    const int p = P.p;
     float* out = partials + (long long)blockIdx.x * p * p;
-    if (drain) {
-        // sym holds Na rows: TMEM lanes Na..127 are padding bands (zero)
-        if (ok && row < Na) {
+    if (!ok) {
+        for (int e = tid; e < p * p; e += kT32Threads) out[e] = 0.f;
+    } else if (drain) {
+        // top tile: lane = band (< 128); corner: lane -> band Np - 128 + lane
 #pragma unroll
-            for (int c = 0; c < NAH; ++c) sym[row * lda + half * NAH + c] = accA[c];
-        }
-        if (NBX > 0) {
-            if (half == 0 && row < p) {
+        for (int k = 0; k < H0 / 16; ++k) {
+            const bool corner = half == 1 && 16 * k >= T1;
+            const int orow = corner ? P.Np - 128 + row : row;
+            const int ocol = half == 0 ? 16 * k : (corner ? 128 + 16 * k - T1 : H0 + 16 * k);
+            if (orow < p && (!corner || orow >= 128)) {
 #pragma unroll
-                for (int c = 0; c < NBX; ++c)
-                    if (128 + c < p) out[(long long)row * p + 128 + c] = ok ? accX[c] : 0.f;
-            } else if (half == 1) {
-                const int band = P.Np - 128 + row;
-                if (band >= 128 && band < p) {
-#pragma unroll
-                    for (int c = 0; c < NBX; ++c)
-                        if (128 + c < p) out[(long long)band * p + 128 + c] = ok ? accX[c] : 0.f;
-                }
+                for (int e = 0; e < 16; ++e)
+                    if (ocol + e < p) out[(long long)orow * p + ocol + e] = acc[16 * k + e];
             }
         }
     }
-    __syncthreads();
-    const int m = p < 128 ? p : 128;
-    for (int e = tid; e < m * m; e += kT32Threads) {
-        const int i = e / m, j = e - i * m;
-        // after a timeout a late TMA write may still land in sym: write zeros
-        if (j >= i) out[(long long)i * p + j] = ok ? 0.5f * (sym[i * lda + j] + sym[j * lda + i]) : 0.f;
-    }
+    // the reduction may start once every CTA has written its partial
+    pdl_trigger();
     tc_fence_before();
     __syncthreads();
     if (warp == kMmaWarp) {
@@ -353,30 +333,44 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
     }
 }
 
-// R[i][j] = R[j][i] = sum over CTAs of partial[i][j] (i <= j), in double, in
-// a fixed order: one thread per element of the upper triangle.
-__global__ void gram_tf32_reduce_kernel(const float* __restrict__ partials, int nblocks, int p,
-                                        double* __restrict__ R, int* status) {
+// R[i][j] = R[j][i] = sum over CTAs of partial[i][j] (i <= j) in double, in
+// a fixed order: a block takes 32 consecutive elements, warp w sums the
+// partials of CTAs w, w + 8, ... (coalesced rows of 32 floats), and thread
+// t < 32 adds the eight warp sums in warp order. Entries of the lower
+// triangle of a CTA's partial are not read.
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(kRedWarps * 32)
+gram_tf32_reduce_kernel(const float* __restrict__ partials, int nblocks, int p,
+                        double* __restrict__ R, int* status) {
     pdl_wait();
     pdl_trigger();
+    __shared__ double part[kRedWarps][32];
     const long long tot = (long long)p * p;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= tot) return;
-    const int i = (int)(e / p), j = (int)(e - (long long)i * p);
-    if (j < i) return;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int b = 0;
-    for (; b + 4 <= nblocks; b += 4) {
-        s0 += (double)__ldg(partials + (long long)b * tot + e);
-        s1 += (double)__ldg(partials + (long long)(b + 1) * tot + e);
-        s2 += (double)__ldg(partials + (long long)(b + 2) * tot + e);
-        s3 += (double)__ldg(partials + (long long)(b + 3) * tot + e);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long e = (long long)blockIdx.x * 32 + lane;
+    double s0 = 0.0, s1 = 0.0;
+    if (e < tot) {
+        int b = w;
+        for (; b + kRedWarps < nblocks; b += 2 * kRedWarps) {
+            s0 += (double)__ldg(partials + (long long)b * tot + e);
+            s1 += (double)__ldg(partials + (long long)(b + kRedWarps) * tot + e);
+        }
+        if (b < nblocks) s0 += (double)__ldg(partials + (long long)b * tot + e);
     }
-    for (; b < nblocks; ++b) s0 += (double)__ldg(partials + (long long)b * tot + e);
-    const double s = (s0 + s1) + (s2 + s3);
-    if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
-    R[(long long)i * p + j] = s;
-    R[(long long)j * p + i] = s;
+    part[w][lane] = s0 + s1;
+    __syncthreads();
+    if (w == 0 && e < tot) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < kRedWarps; ++q) s += part[q][lane];
+        const int i = (int)(e / p), j = (int)(e - (long long)i * p);
+        if (j >= i) {
+            if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
+            R[(long long)i * p + j] = s;
+            R[(long long)j * p + i] = s;
+        }
+    }
 }
 
 // cuTensorMapEncodeTiled from the driver through the runtime (no link
@@ -406,25 +400,25 @@ bool t32_plan(int p, long long n, T32Plan* out) {
     T32Plan P = {};
     P.p = p;
     P.Np = (p + 15) / 16 * 16;
-    P.Na = p <= 32 ? 32 : p <= 64 ? 64 : 128;
-    P.nb = P.Np > 128 ? P.Np - 128 : 0;
+    P.NT = P.Np > 128 ? P.Np : (p <= 32 ? 32 : p <= 64 ? 64 : 128);
+    P.NC = P.Np > 128 ? P.Np - 128 : 0;
     P.rows = P.Np > 128 ? P.Np : 128;
     P.q4 = p / 4;
     P.box_bytes = (uint32_t)align_up((size_t)P.q4 * kKBox * 4, 128);
     P.raw_stage_bytes = 4u * P.box_bytes;
     P.op_bytes = (uint32_t)P.rows * 128u;
-    P.buf_cols = P.Na + 4 * P.nb;
+    // TMEM per buffer: the corner at column 0 (32 columns reserved), the top
+    // tile after it; rounded to 32 columns
+    P.colT = P.NC > 0 ? 32 : 0;
+    P.buf_cols = (int)align_up((size_t)(P.colT + P.NT), 32);
     const int need = 2 * P.buf_cols;
-    P.tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
     if (need > 512) return false;
+    P.tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
     const size_t room = 227 * 1024 - 1024 - 512;   // alignment slack, static shared memory
     const size_t op_area = 2u * kOpStages * P.op_bytes;
     if (op_area + 2 * P.raw_stage_bytes > room) return false;
-    int rs = (int)((room - op_area) / P.raw_stage_bytes);
+    const int rs = (int)((room - op_area) / P.raw_stage_bytes);
     P.raw_stages = rs > kMaxRaw ? kMaxRaw : rs;
-    // the symmetrisation buffer reuses the raw stages
-    if ((size_t)P.raw_stages * P.raw_stage_bytes < (size_t)P.Na * (P.Na + 1) * sizeof(float))
-        return false;
     P.smem = 1024 + op_area + (size_t)P.raw_stages * P.raw_stage_bytes;
     *out = P;
     return true;
@@ -469,15 +463,18 @@ hyde_status launch_gram_tf32(const float* Y, int p, long long n, float* partials
         return HYDE_OK;
     };
     hyde_status st;
-    if (P.nb == 0)
-        st = P.Na == 32 ? go(gram_tf32_kernel<16, 0>)
-           : P.Na == 64 ? go(gram_tf32_kernel<32, 0>) : go(gram_tf32_kernel<64, 0>);
-    else
-        st = P.nb == 16 ? go(gram_tf32_kernel<64, 16>) : go(gram_tf32_kernel<64, 32>);
+    switch (P.NT) {
+        case 32: st = go(gram_tf32_kernel<32, 0, 16>); break;
+        case 64: st = go(gram_tf32_kernel<64, 0, 32>); break;
+        case 128: st = go(gram_tf32_kernel<128, 0, 64>); break;
+        case 144: st = go(gram_tf32_kernel<144, 16, 80>); break;
+        case 160: st = go(gram_tf32_kernel<160, 32, 96>); break;
+        default: return HYDE_ERR_SHAPE;
+    }
     if (st != HYDE_OK) return st;
     const long long tot = (long long)p * p;
-    launch_pdl(gram_tf32_reduce_kernel, (unsigned)((tot + 255) / 256), 256, 0, s, partials,
-               blocks, p, R, status);
+    launch_pdl(gram_tf32_reduce_kernel, (unsigned)((tot + 31) / 32), kRedWarps * 32, 0, s,
+               partials, blocks, p, R, status);
     return cuda_status(cudaGetLastError());
 }
 
