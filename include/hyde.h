@@ -57,7 +57,13 @@ typedef enum {
 } hyde_status;
 
 typedef enum {
-    HYDE_PREC_FP32 = 0,    /* plain FP32 SIMT arithmetic                      */
+    HYDE_PREC_FP32 = 0,    /* FP32-accurate arithmetic: the whole-path calls
+                              take the Gram matrix as in HYDE_PREC_TF32X3
+                              when its conditions hold (p a multiple of 4,
+                              p <= 160, cube 16-byte aligned) and as FP32
+                              SIMT products otherwise; every other stage in
+                              FP32 SIMT. hyde_gram with this value is always
+                              the SIMT kernel                                 */
     HYDE_PREC_TF32X3 = 1,  /* Gram matrix on the tensor cores, FP32-accurate:
                               each float is split into tf32 hi (rounded) +
                               lo = y - hi and y_a y_b is taken as

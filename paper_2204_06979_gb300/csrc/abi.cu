@@ -122,6 +122,14 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
         st = gram_tc_partial_bytes(p, &tcb);
         if (st != HYDE_OK) return st;
         l.gram.partial_bytes = tcb;
+    } else if (gram_tf32_shape_ok(p, n)) {
+        // the FP32 path takes the split-TF32 Gram when the cube is 16-byte
+        // aligned (known only at the call) and the SIMT kernel otherwise:
+        // room for either's partials
+        size_t tcb = 0;
+        st = gram_tc_partial_bytes(p, &tcb);
+        if (st != HYDE_OK) return st;
+        if (tcb > l.gram.partial_bytes) l.gram.partial_bytes = tcb;
     }
     const int r = pr->r_max, K = pr->n_lambda;
     Carver c;
@@ -400,8 +408,11 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     if (cudaMemsetAsync(at<char>(ws, L.zero_begin), 0, L.zero_end - L.zero_begin, stream) !=
         cudaSuccess)
         return HYDE_ERR_CUDA;
-    // 1. Gram matrix (float SIMT, or split-BF16 on the tensor cores)
-    if (params->precision == HYDE_PREC_TF32X3)
+    // 1. Gram matrix: split-TF32 on the tensor cores (FP32-accurate; the FP32
+    // path's choice whenever the shape and alignment allow), split-BF16, or
+    // float SIMT
+    if (params->precision == HYDE_PREC_TF32X3 ||
+        (params->precision == HYDE_PREC_FP32 && gram_tf32_supported(Y, p, L.n)))
         HYDE_TRY(launch_gram_tf32(Y, p, L.n, at<float>(ws, L.partials), R, status, stream));
     else if (params->precision != HYDE_PREC_FP32)
         HYDE_TRY(launch_gram_tc(Y, p, L.n, at<float>(ws, L.partials), R, status, stream));
