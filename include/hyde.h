@@ -255,12 +255,18 @@ hyde_status hyde_hysime(const float* Y, int p, long long n, int r_max, int* k,
  * (double, row-major): the spectral subspace of the low-rank model
  * (Sec. 2.1). evals (double[r]) are in descending order; V is double[p][r]
  * (column i = eigenvector i); the entry of largest magnitude of each
- * eigenvector is positive. Householder tridiagonalisation, multisection for
- * the eigenvalues, twisted-factorisation eigenvectors and a Gram-Schmidt
- * pass, all in float in one thread block. status as above.
+ * eigenvector is positive. In float: Householder tridiagonalisation in one
+ * thread block; then one block per eigenpair (multisection for the
+ * eigenvalue, twisted-factorisation eigenvector, back-transformation); then
+ * a Gram-Schmidt pass (twice) over the r vectors. status as above.
+ * 2 <= p <= 256 (about 208 at r = 32, shared-memory bound), 1 <= r <=
+ * min(p, 32); ws: hyde_eig_workspace_size bytes (the reflectors and the
+ * unnormalised vectors travel between the kernels there).
  */
+hyde_status hyde_eig_workspace_size(int p, int r, size_t* bytes);
 hyde_status hyde_eig_sym_top(const double* A, int p, int r, double* evals,
-                             double* V, int* status, cudaStream_t stream);
+                             double* V, int* status, void* ws, size_t ws_bytes,
+                             cudaStream_t stream);
 
 /* -------------------------------------------------------------------- DWT
  * L-level separable 2D periodic db2 analysis of a batch of images.

@@ -49,7 +49,8 @@ SIGNATURES = {
     "hyde_gram_noalloc": (c_int, [c_vp, c_int, c_ll, c_vp, c_vp]),
     "hyde_noise_est_workspace_size": (c_int, [c_int, c_int, c_int, c_size_p]),
     "hyde_noise_est": (c_int, [c_vp, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_size, c_vp]),
-    "hyde_eig_sym_top": (c_int, [c_vp, c_int, c_int, c_vp, c_vp, c_vp, c_vp]),
+    "hyde_eig_workspace_size": (c_int, [c_int, c_int, c_size_p]),
+    "hyde_eig_sym_top": (c_int, [c_vp, c_int, c_int, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "hyde_hysime_workspace_size": (c_int, [c_int, c_ll, c_int, c_size_p]),
     "hyde_hysime": (c_int, [c_vp, c_int, c_ll, c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                             c_vp, c_size, c_vp]),

@@ -124,11 +124,14 @@ def eig_sym_top(A: torch.Tensor, r: int) -> tuple[torch.Tensor, torch.Tensor, to
         raise ValueError("A must be a float64 CUDA tensor")
     A = A.contiguous()
     p = A.shape[0]
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_eig_workspace_size(p, r, ctypes.byref(sz)), "hyde_eig_workspace_size")
+    ws = _workspace(sz.value, A.device)
     evals = torch.empty(r, dtype=torch.float64, device=A.device)
     V = torch.empty((p, r), dtype=torch.float64, device=A.device)
     status = torch.zeros(1, dtype=torch.int32, device=A.device)
-    _check(lib.hyde_eig_sym_top(_ptr(A), p, r, _ptr(evals), _ptr(V), _ptr(status), _stream()),
-           "hyde_eig_sym_top")
+    _check(lib.hyde_eig_sym_top(_ptr(A), p, r, _ptr(evals), _ptr(V), _ptr(status), _ptr(ws),
+                                ws.numel(), _stream()), "hyde_eig_sym_top")
     return evals, V, status
 
 

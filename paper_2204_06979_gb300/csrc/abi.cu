@@ -81,7 +81,7 @@ struct HyresLayout {
     long long N, n;
     GramPlan gram;
     hyde_ws_layout pub;
-    size_t rank_dev, lam_dev, counts, sums, sum_all, done, sint, P, Q, noise, partials, zp,
+    size_t rank_dev, lam_dev, counts, sums, sum_all, done, sint, P, Q, noise, eig, partials, zp,
         scratch;
     size_t zero_begin, zero_end;
 };
@@ -156,6 +156,7 @@ hyde_status hyres_layout(int p, int H, int W, const hyde_hyres_params* pr, Hyres
     l.P = c.take((size_t)p * l.RM * sizeof(float));
     l.Q = c.take((size_t)p * l.RM * sizeof(float));
     l.noise = c.take(noise_ws_bytes(p));
+    l.eig = c.take(eig_ws_bytes(p, r));
     l.partials = c.take(l.gram.partial_bytes);
     l.zp = c.take((size_t)r * l.N * sizeof(float));
     l.pub.coef = c.take((size_t)r * l.N * sizeof(float));
@@ -266,11 +267,22 @@ hyde_status hyde_noise_est(const float* Y, int p, int H, int W, double* sigma, i
 }
 
 // ----------------------------------------------------------- eigenvectors
+hyde_status hyde_eig_workspace_size(int p, int r, size_t* bytes) {
+    if (!bytes) return HYDE_ERR_INVALID_ARG;
+    if (p < 2 || r < 1 || r > p || r > kMaxRank || p > kMaxBandsGram) return HYDE_ERR_SHAPE;
+    if (eig_smem_bytes(p, r) > 227 * 1024) return HYDE_ERR_SHAPE;
+    *bytes = align_up(eig_ws_bytes(p, r), kAlign);
+    return HYDE_OK;
+}
+
 hyde_status hyde_eig_sym_top(const double* A, int p, int r, double* evals, double* V,
-                             int* status, cudaStream_t stream) {
+                             int* status, void* ws, size_t ws_bytes, cudaStream_t stream) {
     if (!A || !evals || !V) return HYDE_ERR_INVALID_ARG;
-    if (p < 1 || r < 1 || r > p || r > kMaxRank) return HYDE_ERR_SHAPE;
-    return launch_eig_top(A, nullptr, p, r, evals, V, status, stream);
+    size_t need = 0;
+    hyde_status st = hyde_eig_workspace_size(p, r, &need);
+    if (st != HYDE_OK) return st;
+    if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return HYDE_ERR_WORKSPACE;
+    return launch_eig_top(A, nullptr, p, r, evals, V, ws, status, stream);
 }
 
 // -------------------------------------------------------------------- DWT
@@ -423,7 +435,7 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     HYDE_TRY(launch_noise_from_gram(R, p, L.n, sigma, at<void>(ws, L.noise), status, stream));
     HYDE_TRY(stage());
     // 3-4. whitened Gram matrix, leading eigenpairs, float weights
-    HYDE_TRY(launch_eig_top(R, sigma, p, r, evals, V, status, stream));
+    HYDE_TRY(launch_eig_top(R, sigma, p, r, evals, V, at<void>(ws, L.eig), status, stream));
     HYDE_TRY(launch_weights(V, sigma, p, r, L.RM, P, Q, stream));
     HYDE_TRY(stage());
     // 5. projection into padded component images

@@ -197,10 +197,13 @@ hyde_status launch_noise_from_gram(const double* R, int p, long long n,
 // from the float Gauss-Jordan inverse; ws as for launch_noise_from_gram).
 hyde_status launch_inverse_from_gram(const double* R, int p, void* ws, double* Q, int* status,
                                      cudaStream_t s);
-size_t eig_smem_bytes(int p, int r);
+size_t eig_smem_bytes(int p, int r);   // largest dynamic smem of the three eig kernels
+size_t eig_ws_bytes(int p, int r);     // workspace of launch_eig_top (16-byte aligned)
 size_t noise_smem_bytes(int p);   // dynamic smem of the Gauss-Jordan kernel (0 = registers)
+// Leading r eigenpairs (descending) of A, whitened on load by wsig (NULL: no
+// whitening): evals double[r], V double[p][r]; ws holds eig_ws_bytes(p, r).
 hyde_status launch_eig_top(const double* A, const double* wsig, int p,
-                           int r, double* evals, double* V, int* status,
+                           int r, double* evals, double* V, void* ws, int* status,
                            cudaStream_t s);
 // P[b][i] = V[b][i] / sigma_b and Q[b][i] = V[b][i] * sigma_b (float,
 // row stride ldw, zero for i >= r)

@@ -105,7 +105,7 @@ hysime_delta_kernel(const double* __restrict__ R, const double* __restrict__ Rn,
 
 struct HysimeLayout {
     GramPlan gram;
-    size_t done, partials, R, noise, Q, Rn, Rx, total;
+    size_t done, partials, R, noise, Q, Rn, Rx, eig, total;
 };
 
 hyde_status hysime_layout(int p, long long n, int r, HysimeLayout* L) {
@@ -130,6 +130,7 @@ hyde_status hysime_layout(int p, long long n, int r, HysimeLayout* L) {
     l.Q = take(pp);
     l.Rn = take(pp);
     l.Rx = take(pp);
+    l.eig = take(eig_ws_bytes(p, r));
     l.total = off;
     *L = l;
     return HYDE_OK;
@@ -180,7 +181,7 @@ extern "C" hyde_status hyde_hysime(const float* Y, int p, long long n, int r_max
     const long long pp = (long long)p * p;
     launch_pdl(hysime_form_kernel, (unsigned)((pp + 255) / 256), 256, 0, stream, R, Q, p, inv_n,
                Rn, Rx, status);
-    st = launch_eig_top(Rx, nullptr, p, r_max, evals, E, status, stream);
+    st = launch_eig_top(Rx, nullptr, p, r_max, evals, E, at<void>(ws, L.eig), status, stream);
     if (st != HYDE_OK) return st;
     launch_pdl(hysime_delta_kernel, r_max, kHsThreads, 0, stream, R, Rn, E, p, r_max, inv_n,
                delta, at<unsigned int>(ws, L.done), k, idx, status);

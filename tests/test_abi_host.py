@@ -107,7 +107,17 @@ def test_bad_arguments_rejected_on_host(lib):
     p.lambda_mode = 3
     assert lib.hyde_workspace_size(32, 64, 64, ctypes.byref(p), ctypes.byref(sz)) == 1
     p.lambda_mode = 0
-    assert lib.hyde_eig_sym_top(None, 4, 2, None, None, None, None) == 1
+    assert lib.hyde_eig_sym_top(None, 4, 2, None, None, None, None, 0, None) == 1
+    sz = ctypes.c_size_t()
+    assert lib.hyde_eig_workspace_size(4, 2, None) == 1
+    assert lib.hyde_eig_workspace_size(1, 1, ctypes.byref(sz)) == 2     # one band
+    assert lib.hyde_eig_workspace_size(8, 9, ctypes.byref(sz)) == 2     # r > p
+    assert lib.hyde_eig_workspace_size(64, 33, ctypes.byref(sz)) == 2   # r > 32
+    assert lib.hyde_eig_workspace_size(144, 20, ctypes.byref(sz)) == 0
+    assert sz.value >= (144 * 144 + 20 * 144) * 4
+    # a workspace that is missing or too small is refused before any launch
+    assert lib.hyde_eig_sym_top(1, 144, 20, 1, 1, None, None, 0, None) == 7
+    assert lib.hyde_eig_sym_top(1, 144, 20, 1, 1, None, 256, 1024, None) == 7
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
