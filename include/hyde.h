@@ -258,7 +258,8 @@ hyde_status hyde_hysime(const float* Y, int p, long long n, int r_max, int* k,
  * eigenvector is positive. In float: Householder tridiagonalisation in one
  * thread block; then one block per eigenpair (multisection for the
  * eigenvalue, twisted-factorisation eigenvector, back-transformation); then
- * a Gram-Schmidt pass (twice) over the r vectors. status as above.
+ * Cholesky QR (twice) of the r vectors in descending order (Gram-Schmidt
+ * in exact arithmetic). status as above.
  * 2 <= p <= 256 (about 208 at r = 32, shared-memory bound), 1 <= r <=
  * min(p, 32); ws: hyde_eig_workspace_size bytes (the reflectors and the
  * unnormalised vectors travel between the kernels there).

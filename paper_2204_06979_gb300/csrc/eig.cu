@@ -13,10 +13,10 @@
 //     rounds reach float resolution), the eigenvector of T from a twisted
 //     factorisation at it, and its back-transformation by the reflectors
 //     (read into shared memory), one warp.
-//  3. eig_orth_kernel (one block): classical Gram-Schmidt, twice, over the r
-//     vectors in descending order (orthogonality inside clusters of close
-//     eigenvalues), the sign rule (largest-magnitude entry positive), and the
-//     write-out in double.
+//  3. eig_orth_kernel (one block): Cholesky QR, twice, of the r vectors in
+//     descending order (Gram-Schmidt in that order; orthogonality inside
+//     clusters of close eigenvalues), the sign rule (largest-magnitude entry
+//     positive), and the write-out in double.
 // The p-step Householder recurrence is the only part bound to one SM; the
 // per-eigenpair work runs on r SMs at once.
 #include <float.h>
@@ -109,6 +109,9 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
                                            float x, float pivmin) {
     float q = d[0] - x;
     int c = q < 0.f;
+    // unrolled so that the shared-memory loads of later steps issue ahead of
+    // the dependent chain through q
+#pragma unroll 8
     for (int i = 1; i < p; ++i) {
         if (fabsf(q) < pivmin) q = -pivmin;
         q = (d[i] - x) - __fdividef(e2[i - 1], q);
@@ -424,13 +427,16 @@ eig_pair_kernel(EigWs G, int p, int* status) {
         cpair[i] = G.cpair[i];
         if (!isfinite(di) || !isfinite(ei)) set_status(status, HYDE_ERR_NUMERIC);
     }
-    // the reflectors, for the back-transformation at the end (float4 copies;
-    // p - 2 rows of p floats)
+    // the reflectors, for the back-transformation at the end: asynchronous
+    // 16-byte copies (p - 2 rows of p floats) that land while the
+    // multisection runs
     {
         const int nv = (p - 2) * p;
-        const float4* src = reinterpret_cast<const float4*>(G.refl);
-        float4* dst = reinterpret_cast<float4*>(refl);
-        for (int i = t; i < nv / 4; i += kPairThreads) dst[i] = src[i];
+        for (int i = t; i < nv / 4; i += kPairThreads)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(refl + 4 * i)),
+                         "l"(G.refl + 4 * i));
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
         for (int i = (nv / 4) * 4 + t; i < nv; i += kPairThreads) refl[i] = G.refl[i];
     }
     __syncthreads();
@@ -475,6 +481,8 @@ eig_pair_kernel(EigWs G, int p, int* status) {
         if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi))) break;
     }
     const float lam = 0.5f * (lo + hi);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();   // every thread's reflector copies are visible
     if (wid != 0) return;
     // twisted factorisation at lam: L D L^T from the top in lane 0, U D U^T
     // from the bottom in lane 1, in lockstep
@@ -486,6 +494,7 @@ eig_pair_kernel(EigWs G, int p, int* status) {
         float qv = d[i] - lam;
         if (fabsf(qv) < pivmin) qv = -pivmin;
         D[i] = qv;
+#pragma unroll 4
         for (int s2 = 1; s2 < p; ++s2) {
             i += step;
             const float ee = e2[fwd ? i - 1 : i];
@@ -517,6 +526,7 @@ eig_pair_kernel(EigWs G, int p, int* status) {
         if (up) z[kt] = 1.0f;
         int i = kt;
         float zz = 1.0f;
+#pragma unroll 4
         for (int s2 = 0; s2 < steps; ++s2) {
             if (s2 < len) {
                 i += up ? -1 : 1;
@@ -589,8 +599,14 @@ eig_pair_kernel(EigWs G, int p, int* status) {
 }
 
 // --------------------------------------------------------------------------
-// 3. Classical Gram-Schmidt, two passes, over the r vectors in descending
-// order; sign rule; write-out in double.
+// 3. Orthonormalisation of the r vectors (rows of X, descending eigenvalue)
+// by Cholesky QR, twice: G = X X^T, G = L L^T, X <- L^-1 X. In exact
+// arithmetic this is Gram-Schmidt in the same order (row i becomes a
+// combination of rows 0..i); the second pass removes the first pass's
+// rounding (vectors of well-separated eigenvalues are orthogonal to ~u
+// already, those of close ones to ~u / gap). A pivot that is not positive
+// (two vectors equal to rounding) is floored at 1e-12 G_kk. Then the sign rule and
+// the write-out in double.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(kLA, 1)
 eig_orth_kernel(EigWs G, int p, int r, double* __restrict__ evals, double* __restrict__ V) {
@@ -598,41 +614,60 @@ eig_orth_kernel(EigWs G, int p, int r, double* __restrict__ evals, double* __res
     pdl_trigger();
     extern __shared__ float sm[];
     float* X = sm;                // [r][p]
-    __shared__ float dots[32];
+    __shared__ float Gm[32][33];  // X X^T, then L (lower triangle)
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    for (int i = t; i < r * p; i += blockDim.x) X[i] = G.X[i];
+    constexpr int nw = kLA / 32;
+    for (int i = t; i < r * p; i += kLA) X[i] = G.X[i];
     __syncthreads();
-    for (int j = 1; j < r; ++j) {
-        float* xj = X + j * p;
-        for (int pass = 0; pass < 2; ++pass) {
-            if (wid < j) {
-                const float* xi = X + wid * p;
-                float dt = 0.f;
-                for (int i = lane; i < p; i += 32) dt = fmaf(xi[i], xj[i], dt);
-                dt = warp_sum(dt);
-                if (lane == 0) dots[wid] = dt;
-            }
-            __syncthreads();
-            for (int i = t; i < p; i += blockDim.x) {
-                float acc = xj[i];
-                for (int q2 = 0; q2 < j; ++q2) acc = fmaf(-dots[q2], X[q2 * p + i], acc);
-                xj[i] = acc;
-            }
-            __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        // upper triangle of X X^T, one warp per entry
+        for (int e = wid; e < r * r; e += nw) {
+            const int i = e / r, j = e - i * r;
+            if (j < i) continue;
+            const float* xi = X + i * p;
+            const float* xj = X + j * p;
+            float dt = 0.f;
+            for (int k = lane; k < p; k += 32) dt = fmaf(xi[k], xj[k], dt);
+            dt = warp_sum(dt);
+            if (lane == 0) Gm[i][j] = dt;
         }
+        __syncthreads();
+        // Cholesky by warp 0: column k at step k, lane i holds row i
         if (wid == 0) {
-            float ss = 0.f;
-            for (int i = lane; i < p; i += 32) ss = fmaf(xj[i], xj[i], ss);
-            ss = warp_sum(ss);
-            const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
-            for (int i = lane; i < p; i += 32) xj[i] *= inv;
+            for (int k = 0; k < r; ++k) {
+                float lkk = 0.f;
+                if (lane == k) {
+                    float v = Gm[k][k];
+                    for (int m = 0; m < k; ++m) v = fmaf(-Gm[k][m], Gm[k][m], v);
+                    const float floor_ = 1e-12f * Gm[k][k];
+                    lkk = sqrtf(v > floor_ ? v : (floor_ > 0.f ? floor_ : 1e-30f));
+                    Gm[k][k] = lkk;
+                }
+                lkk = __shfl_sync(0xffffffffu, lkk, k);
+                if (lane > k && lane < r) {
+                    float v = Gm[k][lane];                       // G[k][i], i = lane
+                    for (int m = 0; m < k; ++m) v = fmaf(-Gm[lane][m], Gm[k][m], v);
+                    Gm[lane][k] = v / lkk;                       // L[i][k]
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // X <- L^-1 X, one column of X per thread (forward substitution; the
+        // solved entries are read back from shared memory)
+        for (int e = t; e < p; e += kLA) {
+            for (int i = 0; i < r; ++i) {
+                float v = X[i * p + e];
+                for (int m = 0; m < i; ++m) v = fmaf(-Gm[i][m], X[m * p + e], v);
+                X[i * p + e] = v / Gm[i][i];
+            }
         }
         __syncthreads();
     }
     // sign rule (largest-magnitude entry positive; first such index), one
     // warp per vector
     const float scale = G.scale[0];
-    for (int c = wid; c < r; c += blockDim.x / 32) {
+    for (int c = wid; c < r; c += nw) {
         const float* xc = X + c * p;
         float best = -1.f;
         int bi = 0;
