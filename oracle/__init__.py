@@ -20,3 +20,6 @@ from .hyres import (  # noqa: F401
     sure_loss_scaled,
 )
 from .hysime import hysime, hysime_noise, hysime_select  # noqa: F401,E402
+from .hyminor import (  # noqa: F401,E402
+    hyminor, tvl1_split_bregman, tvl1_objective,
+)
