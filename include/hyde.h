@@ -418,6 +418,31 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H,
                                 size_t fws_bytes, void* bws, size_t bws_bytes,
                                 cudaStream_t stream);
 
+/* ---------------------------------------------------------------- HyMiNoR
+ * Mixed Gaussian and sparse noise reduction built on HyRes (Sec. 2.1: after
+ * HyRes removes the Gaussian noise, an l1-l1 problem solved by a modified
+ * split-Bregman iteration removes the remaining sparse noise). The paper
+ * states neither; this library's reading: G = HyRes(Y) (params as for
+ * hyde_hyres_denoise, info receives its choice); per band image the problem
+ *   min_x ||G/s - x||_1 + lam (||Dx x||_1 + ||Dy x||_1),  s = max |G|,
+ * Dx, Dy periodic forward differences along rows and columns; split Bregman
+ * on A = G/s - x, Bx = Dx x, By = Dy x with penalty mu (thresholds 1/mu and
+ * lam/mu), from x = G/s and zero splitting variables, the x-subproblem
+ * (5 x - sum of the 4 neighbours = rhs) solved by two Jacobi sweeps from
+ * the current x, `iters` iterations; X = s x. Defaults in the binding:
+ * lam = 1, mu = 10, iters = 50. Y, X: float[p][H][W] device, X may not
+ * alias Y. lam >= 0, mu > 0 (HYDE_ERR_INVALID_ARG otherwise), 1 <= iters
+ * <= 100000. Workspace: hyde_hyminor_workspace_size (the HyRes workspace
+ * plus nine cube-sized float buffers: G and two sets of iteration state).
+ */
+hyde_status hyde_hyminor_workspace_size(int p, int H, int W,
+                                        const hyde_hyres_params* params,
+                                        size_t* bytes);
+hyde_status hyde_hyminor(const float* Y, float* X, int p, int H, int W,
+                         const hyde_hyres_params* params, float lam, float mu,
+                         int iters, hyde_hyres_info* info, void* ws,
+                         size_t ws_bytes, cudaStream_t stream);
+
 /* ------------------------------------------------------- sliding windows
  * Batched form: the scene Y (float[p][H][W]) is cut into windows, each
  * denoised with its own noise levels, subspace, rank and threshold, and X

@@ -70,6 +70,10 @@ SIGNATURES = {
                                          c_vp]),
     "hyde_hyres_kernel_launches": (c_int, [c_int, c_int, c_int, ctypes.POINTER(HydeParams)]),
     "hyde_set_grid_sm_cap": (c_int, [c_int]),
+    "hyde_hyminor_workspace_size": (c_int, [c_int, c_int, c_int, ctypes.POINTER(HydeParams),
+                                            c_size_p]),
+    "hyde_hyminor": (c_int, [c_vp, c_vp, c_int, c_int, c_int, ctypes.POINTER(HydeParams),
+                             ctypes.c_float, ctypes.c_float, c_int, c_vp, c_vp, c_size, c_vp]),
     "hyde_set_wait_limit_ns": (ctypes.c_ulonglong, [ctypes.c_ulonglong]),
     "hyde_hyres_denoise_scaled": (c_int, [c_vp, c_vp, c_int, c_int, c_int,
                                           ctypes.POINTER(HydeParams), c_vp, c_vp, c_vp, c_size,

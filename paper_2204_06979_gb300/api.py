@@ -339,6 +339,27 @@ def hyres_denoise(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64,
 
 # ------------------------------------------------------ differentiation form
 
+def hyminor(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64, lam: float = 1.0,
+            mu: float = 10.0, iters: int = 50, precision: int = PREC_FP32
+            ) -> tuple[torch.Tensor, dict]:
+    """HyMiNoR of ``Y[p, H, W]`` (``hyde_hyminor``): HyRes, then the l1-l1
+    sparse-noise stage. Returns ``(X, info)`` (info: HyRes's choice)."""
+    lib = _lib.load()
+    Y = _cuda_f32(Y, "Y")
+    p, H, W = Y.shape
+    prm = params(levels, r_max, n_lambda, precision)
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_hyminor_workspace_size(p, H, W, ctypes.byref(prm), ctypes.byref(sz)),
+           "hyde_hyminor_workspace_size")
+    ws = _workspace(sz.value, Y.device)
+    X = torch.empty_like(Y)
+    info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=Y.device)
+    _check(lib.hyde_hyminor(_ptr(Y), _ptr(X), p, H, W, ctypes.byref(prm), float(lam), float(mu),
+                            int(iters), _ptr(info), _ptr(ws), ws.numel(), _stream()),
+           "hyde_hyminor")
+    return X, parse_info(info)
+
+
 def _scale_rows(scale: torch.Tensor, r_max: int, levels: int) -> torch.Tensor:
     if not scale.is_cuda or scale.dtype != torch.float32 or scale.dim() != 2:
         raise ValueError("scale must be a float32 CUDA matrix [rows >= r_max, levels]")

@@ -266,3 +266,18 @@ def test_wait_limit_setter_round_trip(lib):
     assert prev == 0
     assert lib.hyde_set_wait_limit_ns(0) == 1234
     assert lib.hyde_set_wait_limit_ns(0) == 0
+
+
+def test_hyminor_rejects_bad_arguments_on_host(lib):
+    """hyde_hyminor refuses null pointers, a negative lambda, a non-positive
+    mu and an iteration count outside 1..100000 before touching the device."""
+    from paper_2204_06979_gb300 import api
+    prm = api.params(2, 8, 64)
+    P = ctypes.byref(prm)
+    assert lib.hyde_hyminor(None, 1, 8, 64, 64, P, 1.0, 10.0, 50, None, None, 0, None) == 1
+    assert lib.hyde_hyminor(1, 1, 8, 64, 64, None, 1.0, 10.0, 50, None, None, 0, None) == 1
+    assert lib.hyde_hyminor(1, 1, 8, 64, 64, P, -1.0, 10.0, 50, None, None, 0, None) == 1
+    assert lib.hyde_hyminor(1, 1, 8, 64, 64, P, 1.0, 0.0, 50, None, None, 0, None) == 1
+    assert lib.hyde_hyminor(1, 1, 8, 64, 64, P, 1.0, float("nan"), 50, None, None, 0, None) == 1
+    assert lib.hyde_hyminor(1, 1, 8, 64, 64, P, 1.0, 10.0, 0, None, None, 0, None) == 2
+    assert lib.hyde_hyminor_workspace_size(8, 64, 64, P, None) == 1
