@@ -67,7 +67,15 @@ struct TvOut {
 };
 
 // One split-Bregman iteration on tile (blockIdx.x, blockIdx.y) of band
-// blockIdx.z. first: the state is x = h and t = ux = uy = 0 (not read).
+// blockIdx.z (32 x 8 threads: threadIdx.x runs along the image rows).
+// first: the state is x = h and t = ux = uy = 0 (not read).
+__device__ __forceinline__ int wrap_near(int i, int n) {
+    // the halo reaches at most three pixels past an edge; tiny images wrap
+    // more than once
+    if (i >= 0 && i < n) return i;
+    return wrap(i, n);
+}
+
 __global__ void __launch_bounds__(kTvThreads)
 tvl1_iter_kernel(const float* __restrict__ h, TvState in, TvOut out, int H, int W,
                  const unsigned int* __restrict__ smax, float inv_mu, float lam_inv_mu,
@@ -81,65 +89,84 @@ tvl1_iter_kernel(const float* __restrict__ h, TvState in, TvOut out, int H, int 
     __shared__ float s_rhs[N1][N1 + 1];       // rhs at (y0-1+r, x0-1+c)
     __shared__ float s_x1[N1][N1 + 1];        // x1 at (y0-1+r, x0-1+c)
     __shared__ float s_x2[N2][N2 + 1];        // x2 at (y0+r, x0+c)
-    const int t = threadIdx.x;
+    __shared__ int s_col[N0];                 // wrapped columns x0-2 .. x0+kTs+2
+    __shared__ int s_row[N0];                 // wrapped rows y0-2 .. y0+kTs+2 (times W)
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int y0 = blockIdx.y * kTs, x0 = blockIdx.x * kTs;
     const long long off = (long long)blockIdx.z * H * W;
     const float s = __uint_as_float(*smax);
     const float tA = s * inv_mu, tB = s * lam_inv_mu;
     const float* hb = h + off;
     const float* xb = (first ? h : in.x) + off;
+    const float* tb = in.t + off;
+    const float* uxb = in.ux + off;
+    const float* uyb = in.uy + off;
+    const int lin = ty * 32 + tx;
+    for (int i = lin; i < N0; i += kTvThreads) {
+        s_col[i] = wrap_near(x0 - 2 + i, W);
+        s_row[i] = wrap_near(y0 - 2 + i, H) * W;
+    }
+    __syncthreads();
 
-    for (int e = t; e < N0 * N0; e += kTvThreads) {
-        const int r = e / N0, c = e - r * N0;
-        s_x0[r][c] = __ldg(xb + (long long)wrap(y0 - 2 + r, H) * W + wrap(x0 - 2 + c, W));
+    for (int r = ty; r < N0; r += 8) {
+        const float* row = xb + s_row[r];
+        for (int c = tx; c < N0; c += 32) s_x0[r][c] = __ldg(row + s_col[c]);
     }
-    for (int e = t; e < N1 * (kTs + 4); e += kTvThreads) {
-        const int r = e / (kTs + 4), c = e - r * (kTs + 4);
-        float w = 0.f;
-        if (!first) {
-            const float u = __ldg(in.ux + off + (long long)wrap(y0 - 1 + r, H) * W +
-                                  wrap(x0 - 2 + c, W));
-            w = u - 2.0f * clipf(u, tB);
+    for (int r = ty; r < N1; r += 8) {           // wx rows y0-1.., columns x0-2..
+        const int gr = s_row[r + 1];
+        for (int c = tx; c < kTs + 4; c += 32) {
+            float w = 0.f;
+            if (!first) {
+                const float u = __ldg(uxb + gr + s_col[c]);
+                w = u - 2.0f * clipf(u, tB);
+            }
+            s_wx[r][c] = w;
         }
-        s_wx[r][c] = w;
     }
-    for (int e = t; e < (kTs + 4) * N1; e += kTvThreads) {
-        const int r = e / N1, c = e - r * N1;
-        float w = 0.f;
-        if (!first) {
-            const float u = __ldg(in.uy + off + (long long)wrap(y0 - 2 + r, H) * W +
-                                  wrap(x0 - 1 + c, W));
-            w = u - 2.0f * clipf(u, tB);
+    for (int r = ty; r < kTs + 4; r += 8) {      // wy rows y0-2.., columns x0-1..
+        const int gr = s_row[r];
+        for (int c = tx; c < N1; c += 32) {
+            float w = 0.f;
+            if (!first) {
+                const float u = __ldg(uyb + gr + s_col[c + 1]);
+                w = u - 2.0f * clipf(u, tB);
+            }
+            s_wy[r][c] = w;
         }
-        s_wy[r][c] = w;
     }
     __syncthreads();
     // right-hand side and the first Jacobi sweep on the (kTs + 3)^2 region
-    for (int e = t; e < N1 * N1; e += kTvThreads) {
-        const int r = e / N1, c = e - r * N1;
-        const long long g = (long long)wrap(y0 - 1 + r, H) * W + wrap(x0 - 1 + c, W);
-        float tv = first ? 0.f : __ldg(in.t + off + g);
-        const float rhs = __ldg(hb + g) - tv + 2.0f * clipf(tv, tA) +
-                          (s_wx[r][c] - s_wx[r][c + 1]) + (s_wy[r][c] - s_wy[r + 1][c]);
-        s_rhs[r][c] = rhs;
-        const float nb = s_x0[r][c + 1] + s_x0[r + 2][c + 1] + s_x0[r + 1][c] + s_x0[r + 1][c + 2];
-        s_x1[r][c] = (rhs + nb) * 0.2f;
+    for (int r = ty; r < N1; r += 8) {
+        const int gr = s_row[r + 1];
+        for (int c = tx; c < N1; c += 32) {
+            const int g = gr + s_col[c + 1];
+            const float tv = first ? 0.f : __ldg(tb + g);
+            const float rhs = __ldg(hb + g) - tv + 2.0f * clipf(tv, tA) +
+                              (s_wx[r][c] - s_wx[r][c + 1]) + (s_wy[r][c] - s_wy[r + 1][c]);
+            s_rhs[r][c] = rhs;
+            const float nb =
+                s_x0[r][c + 1] + s_x0[r + 2][c + 1] + s_x0[r + 1][c] + s_x0[r + 1][c + 2];
+            s_x1[r][c] = (rhs + nb) * 0.2f;
+        }
     }
     __syncthreads();
     // second sweep on the (kTs + 1)^2 region
-    for (int e = t; e < N2 * N2; e += kTvThreads) {
-        const int r = e / N2, c = e - r * N2;
-        const float nb = s_x1[r][c + 1] + s_x1[r + 2][c + 1] + s_x1[r + 1][c] + s_x1[r + 1][c + 2];
-        s_x2[r][c] = (s_rhs[r + 1][c + 1] + nb) * 0.2f;
+    for (int r = ty; r < N2; r += 8) {
+        for (int c = tx; c < N2; c += 32) {
+            const float nb =
+                s_x1[r][c + 1] + s_x1[r + 2][c + 1] + s_x1[r + 1][c] + s_x1[r + 1][c + 2];
+            s_x2[r][c] = (s_rhs[r + 1][c + 1] + nb) * 0.2f;
+        }
     }
     __syncthreads();
-    // the tile's new state
-    for (int e = t; e < kTs * kTs; e += kTvThreads) {
-        const int r = e / kTs, c = e - r * kTs;
-        const int gy = y0 + r, gx = x0 + c;
-        if (gy >= H || gx >= W) continue;
+    // the tile's new state (coalesced rows of 32)
+    const int gx = x0 + tx;
+    if (gx >= W) return;
+    for (int r = ty; r < kTs; r += 8) {
+        const int gy = y0 + r;
+        if (gy >= H) break;
         const long long g = off + (long long)gy * W + gx;
-        const float x2 = s_x2[r][c];
+        const float x2 = s_x2[r][tx];
         float tv = 0.f, uxv = 0.f, uyv = 0.f;
         if (!first) {
             tv = __ldg(in.t + g);
@@ -148,8 +175,8 @@ tvl1_iter_kernel(const float* __restrict__ h, TvState in, TvOut out, int H, int 
         }
         out.x[g] = x2;
         out.t[g] = __ldg(h + g) - x2 + clipf(tv, tA);
-        out.ux[g] = (s_x2[r][c + 1] - x2) + clipf(uxv, tB);
-        out.uy[g] = (s_x2[r + 1][c] - x2) + clipf(uyv, tB);
+        out.ux[g] = (s_x2[r][tx + 1] - x2) + clipf(uxv, tB);
+        out.uy[g] = (s_x2[r + 1][tx] - x2) + clipf(uyv, tB);
     }
 }
 
@@ -202,6 +229,7 @@ extern "C" hyde_status hyde_hyminor(const float* Y, float* X, int p, int H, int 
     if (!Y || !X || !params) return HYDE_ERR_INVALID_ARG;
     if (!(lam >= 0.f) || !(mu > 0.f) || !isfinite(lam) || !isfinite(mu)) return HYDE_ERR_INVALID_ARG;
     if (iters < 1 || iters > 100000) return HYDE_ERR_SHAPE;
+    if ((long long)H * W > 0x7fffffffLL) return HYDE_ERR_SHAPE;   // one band image in int
     HmLayout L;
     hyde_status st = hm_layout(p, H, W, params, &L);
     if (st != HYDE_OK) return st;
@@ -229,7 +257,8 @@ extern "C" hyde_status hyde_hyminor(const float* Y, float* X, int p, int H, int 
         TvOut out{k == iters - 1 ? X : at<float>(ws, L.state[dst][0]),
                   at<float>(ws, L.state[dst][1]), at<float>(ws, L.state[dst][2]),
                   at<float>(ws, L.state[dst][3])};
-        launch_pdl(tvl1_iter_kernel, grid, kTvThreads, 0, stream, (const float*)G, in, out, H, W,
+        launch_pdl(tvl1_iter_kernel, grid, dim3(32, kTvThreads / 32), 0, stream, (const float*)G,
+                   in, out, H, W,
                    (const unsigned int*)smax, 1.0f / mu, lam / mu, k == 0 ? 1 : 0);
     }
     return cuda_status(cudaGetLastError());
