@@ -169,18 +169,15 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
     pdl_wait();
     pdl_trigger();
     extern __shared__ float sm[];
-    // even leading dimension >= p + 1: rows 8-byte aligned for the paired
-    // column accesses, and the column index p a padding slot inside each row
-    const int lda = (p + 2) & ~1;
-    const int pe = (p + 1) & ~1;       // even vector length
+    const int lda = p + 1;
     float* q = sm;
     float* A = q;    q += p * lda;
-    float* tauv = q; q += pe;
-    float* dv = q;   q += pe;
-    float* ev = q;   q += pe;
-    float* e2v = q;  q += pe;
-    float* vf = q;   q += pe;     // reflector buffer 0, full length
-    float* pvv = q;  q += 2 * pe; // p = tau A v, then reflector buffer 1
+    float* tauv = q; q += p;
+    float* dv = q;   q += p;
+    float* ev = q;   q += p;
+    float* e2v = q;  q += p;
+    float* vf = q;   q += p;     // reflector buffer 0, full length
+    float* pvv = q;  q += 2 * p; // p = tau A v, then reflector buffer 1
     float* red = q;  q += 64;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 
@@ -221,17 +218,13 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
     // the trailing matrix applies update k and accumulates p' = A' v_{k+1} of
     // step k+1 from the new values (row sums by a reduce-scatter). Two
     // barriers per step, one read and one write of each trailing element.
-    // Lane l owns the column pairs (64 b + 2 l, 64 b + 2 l + 1): one 64-bit
-    // load and store and three paired FMAs (fma.rn.f32x2) per two elements;
-    // pair blocks left of column k+1 hold v = w = 0 and are skipped.
     float* const scv = vf;           // reflector scales (vf is free after the load)
     float* const cvec = e2v;         // updated column k+1 (e2v is filled by the tail)
     constexpr int NA = (32 * NB + NW - 1) / NW;   // trailing rows per warp
-    constexpr int NB2 = (NB + 1) / 2;             // 64-column pair blocks
     if (wid < NW) {
     // prologue: reflector 0 (scalars in every warp) and p_0 = tau_0 A v_0
     float tau_k = 0.f, sc_k = 0.f;
-    float2 vreg[NB2];
+    float vreg[NB];
     if (p >= 3) {
         float ss = 0.f;
         for (int i = 2 + lane; i < p; i += 32) { const float x = A[i * lda]; ss = fmaf(x, x, ss); }
@@ -240,10 +233,7 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
         hh_scalars(A, lda, 0, ss, tau_k, sc_k, beta);
         if (t == 0) { tauv[0] = tau_k; scv[0] = sc_k; dv[0] = A[0]; ev[0] = beta; }
 #pragma unroll
-        for (int b = 0; b < NB2; ++b) {
-            const int j = 64 * b + 2 * lane;
-            vreg[b] = make_float2(hh_coef(A, lda, p, 0, sc_k, j), hh_coef(A, lda, p, 0, sc_k, j + 1));
-        }
+        for (int b = 0; b < NB; ++b) vreg[b] = hh_coef(A, lda, p, 0, sc_k, lane + 32 * b);
         const int i0 = 1 + ((wid - 1) & (NW - 1));
         float sacc[NA];
 #pragma unroll
@@ -252,16 +242,11 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
             sacc[a] = 0.f;
             if (i < p) {
                 const float* row = A + i * lda;
-                float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-                for (int b = 0; b < NB2; ++b) {
-                    const int j = 64 * b + 2 * lane;
-                    if (j < p) {
-                        const float2 x = *reinterpret_cast<const float2*>(row + j);
-                        fma_f32x2(s0, s1, x.x, x.y, vreg[b].x, vreg[b].y);
-                    }
+                for (int b = 0; b < NB; ++b) {
+                    const int j = lane + 32 * b;
+                    if (j < p) sacc[a] = fmaf(row[j], vreg[b], sacc[a]);
                 }
-                sacc[a] = s0 + s1;
             }
         }
         int a_own;
@@ -271,27 +256,22 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
     }
     bar_sync_warps<NW>();
     for (int k = 0; k + 2 < p; ++k) {
-        const float* pc = pvv + (k & 1) * pe;
-        float* pn = pvv + ((k + 1) & 1) * pe;
+        const float* pc = pvv + (k & 1) * p;
+        float* pn = pvv + ((k + 1) & 1) * p;
         const bool has_next = k + 4 <= p;
-        const int bmin = (k + 1) >> 6;     // pair blocks b < bmin: columns <= k, no update
         // K = tau/2 v^T p and w = p - K v (v_k, p_k nonzero on rows > k)
-        float2 pj[NB2];
-        float kp0 = 0.f, kp1 = 0.f;
+        float pj[NB];
+        float kp = 0.f;
 #pragma unroll
-        for (int b = 0; b < NB2; ++b) {
-            const int j = 64 * b + 2 * lane;
-            pj[b].x = (j > k && j < p) ? pc[j] : 0.f;
-            pj[b].y = (j + 1 > k && j + 1 < p) ? pc[j + 1] : 0.f;
-            fma_f32x2(kp0, kp1, vreg[b].x, vreg[b].y, pj[b].x, pj[b].y);
+        for (int b = 0; b < NB; ++b) {
+            const int j = lane + 32 * b;
+            pj[b] = (j > k && j < p) ? pc[j] : 0.f;
+            kp = fmaf(vreg[b], pj[b], kp);
         }
-        const float K = 0.5f * tau_k * warp_sum(kp0 + kp1);
-        float2 wreg[NB2];
+        const float K = 0.5f * tau_k * warp_sum(kp);
+        float wreg[NB];
 #pragma unroll
-        for (int b = 0; b < NB2; ++b) {
-            wreg[b] = pj[b];
-            fma_f32x2(wreg[b].x, wreg[b].y, -K, -K, vreg[b].x, vreg[b].y);
-        }
+        for (int b = 0; b < NB; ++b) wreg[b] = fmaf(-K, vreg[b], pj[b]);
         const int i0 = k + 1 + ((wid - (k + 1)) & (NW - 1));
         // column k+1 by warp 0 alone (lane l: rows k+1+l+32b), written to
         // cvec (A keeps the old values: the sweep updates the column in
@@ -315,7 +295,7 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
         }
         bar_sync_warps<NW>();
         float tau_n = 0.f, sc_n = 0.f;
-        float2 vn[NB2];
+        float vn[NB];
         if (has_next) {
             float beta;
             hh_scalars_of(cvec[k + 2], red[32], tau_n, sc_n, beta);
@@ -324,20 +304,18 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
                 dv[k + 1] = cvec[k + 1]; ev[k + 1] = beta;
             }
 #pragma unroll
-            for (int b = 0; b < NB2; ++b) {
-                const int j = 64 * b + 2 * lane;
-                vn[b].x = j == k + 2 ? 1.0f : ((j > k + 2 && j < p) ? cvec[j] * sc_n : 0.f);
-                vn[b].y = j + 1 == k + 2 ? 1.0f
-                                         : ((j + 1 > k + 2 && j + 1 < p) ? cvec[j + 1] * sc_n : 0.f);
+            for (int b = 0; b < NB; ++b) {
+                const int j = lane + 32 * b;
+                vn[b] = j == k + 2 ? 1.0f : ((j > k + 2 && j < p) ? cvec[j] * sc_n : 0.f);
             }
         } else {
 #pragma unroll
-            for (int b = 0; b < NB2; ++b) vn[b] = make_float2(0.f, 0.f);
+            for (int b = 0; b < NB; ++b) vn[b] = 0.f;
         }
-        // fused sweep: update k on rows > k+1; accumulate p' rows. Column
-        // k+1 gets the same value warp 0 put in cvec; columns <= k are left
-        // alone (v = w = 0 there); the pair (p-1, p) writes the padding slot
-        // p back unchanged (v = w = 0 at p).
+        // fused sweep: update k on rows > k+1, columns > k+1; accumulate p' rows
+        // Columns j <= k have v = w = 0 and are rewritten unchanged; column
+        // k+1 gets the same value warp 0 put in cvec; only the last column
+        // block can reach past p (p > 32 (NB - 1)).
         float sacc[NA];
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
@@ -346,19 +324,15 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
             if (i > k + 1 && i < p) {
                 float* row = A + i * lda;
                 const float vi = row[k] * sc_k, wi = fmaf(-K, vi, pc[i]);
-                float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-                for (int b = 0; b < NB2; ++b) {
-                    const int j = 64 * b + 2 * lane;
-                    if (b >= bmin && (b < NB2 - 1 || j < p)) {
-                        float2 x = *reinterpret_cast<const float2*>(row + j);
-                        fma_f32x2(x.x, x.y, -wi, -wi, vreg[b].x, vreg[b].y);
-                        fma_f32x2(x.x, x.y, -vi, -vi, wreg[b].x, wreg[b].y);
-                        *reinterpret_cast<float2*>(row + j) = x;
-                        fma_f32x2(s0, s1, x.x, x.y, vn[b].x, vn[b].y);
+                for (int b = 0; b < NB; ++b) {
+                    const int j = lane + 32 * b;
+                    if (b < NB - 1 || j < p) {
+                        const float x = fmaf(-vi, wreg[b], fmaf(-wi, vreg[b], row[j]));
+                        row[j] = x;
+                        sacc[a] = fmaf(x, vn[b], sacc[a]);
                     }
                 }
-                sacc[a] = s0 + s1;
             }
         }
         if (has_next) {
@@ -371,7 +345,7 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
         tau_k = tau_n;
         sc_k = sc_n;
 #pragma unroll
-        for (int b = 0; b < NB2; ++b) vreg[b] = vn[b];
+        for (int b = 0; b < NB; ++b) vreg[b] = vn[b];
         bar_sync_warps<NW>();
     }
     }   // wid < NW
@@ -710,10 +684,7 @@ eig_orth_kernel(EigWs G, int p, int r, double* __restrict__ evals, double* __res
     }
 }
 
-size_t eig_tridiag_bytes(int p) {
-    const size_t lda = (size_t)((p + 2) & ~1), pe = (size_t)((p + 1) & ~1);
-    return ((size_t)p * lda + 7 * pe + 64) * sizeof(float);
-}
+size_t eig_tridiag_bytes(int p) { return ((size_t)p * (p + 1) + 7 * (size_t)p + 64) * sizeof(float); }
 size_t eig_pair_bytes(int p) { return ((size_t)8 * p + (size_t)(p - 2 > 0 ? p - 2 : 0) * p) * sizeof(float); }
 
 }  // namespace
