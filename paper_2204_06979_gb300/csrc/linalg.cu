@@ -40,9 +40,8 @@ constexpr float kPivotFloor = 2e-6f;
 // T x T tile of rows ty T.. and columns tx T.. in registers. A step costs T^2
 // FMAs and 2T shared loads per thread plus one barrier; the pivot row and
 // column are published through double-buffered shared vectors. G = 16 (256
-// threads, up to 10 x 10 tiles) keeps the per-thread work of a step high and
-// the number of warps that repeat the pivot arithmetic low; G = 20 covers
-// p <= 200.
+// threads, up to 13 x 13 tiles: p <= 208) keeps the per-thread work of a step
+// high and the number of warps that repeat the pivot arithmetic low.
 template <int T, int G>
 __device__ __forceinline__ void noise_gj_reg_body(const double* __restrict__ R, int p,
                                                   float* __restrict__ Ainv,
@@ -139,7 +138,7 @@ noise_gj_reg_kernel(const double* __restrict__ R, int p, float* __restrict__ Ain
 }
 
 
-// Shared-memory Gauss-Jordan for p > 192 (same arithmetic, matrix in smem).
+// Shared-memory Gauss-Jordan for p > 208 (same arithmetic, matrix in smem).
 __global__ void __launch_bounds__(kLA, 1)
 noise_gj_smem_kernel(const double* __restrict__ R, int p, float* __restrict__ Ainv,
                      double* __restrict__ S, int* status) {
@@ -319,16 +318,19 @@ size_t noise_ws_bytes(int p) {
            align_up((size_t)p * sizeof(double), kAlign);
 }
 
-// A 20 x 20 thread grid with 10 x 10 register tiles (400 threads) covers
-// p <= 200; larger p use the shared-memory kernel.
-constexpr int kGj20Max = 200;
+// A 16 x 16 thread grid with T x T register tiles covers p <= 16 T; T <= 13
+// (p <= 208) stays in registers without spilling (244 at T = 13, one block
+// of 256 threads). A 20 x 20 grid of 10 x 10 tiles measured 259 against
+// 217 us at p = 200 (it spills at 400 threads). Larger p use the
+// shared-memory kernel.
+constexpr int kGjRegMax = 208;
 
 size_t noise_smem_bytes(int p) {
-    return p <= kGj20Max ? 0 : ((size_t)p * p + 2 * p) * sizeof(float);
+    return p <= kGjRegMax ? 0 : ((size_t)p * p + 2 * p) * sizeof(float);
 }
 
 // The float inverse of the scaled Gram matrix into ws (Ainv, then the
-// scales S): a register-tile Gauss-Jordan kernel for p <= 200, the
+// scales S): a register-tile Gauss-Jordan kernel for p <= 208, the
 // shared-memory kernel above.
 static hyde_status launch_gj_inverse(const double* R, int p, void* ws, int* status,
                                      cudaStream_t s) {
@@ -336,21 +338,17 @@ static hyde_status launch_gj_inverse(const double* R, int p, void* ws, int* stat
     double* Sd = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) +
                                            align_up((size_t)p * p * sizeof(float), kAlign));
     const int T16 = (p + 15) / 16;
-    if (T16 <= 10) {
+    if (p <= kGjRegMax) {
         switch (T16) {
 #define HYDE_GJ16(TV) \
     case TV: launch_pdl(noise_gj_reg_kernel<TV, 16>, 1, 256, 0, s, R, p, Ainv, Sd, status); \
         break;
             HYDE_GJ16(1) HYDE_GJ16(2) HYDE_GJ16(3) HYDE_GJ16(4) HYDE_GJ16(5)
             HYDE_GJ16(6) HYDE_GJ16(7) HYDE_GJ16(8) HYDE_GJ16(9) HYDE_GJ16(10)
+            HYDE_GJ16(11) HYDE_GJ16(12) HYDE_GJ16(13)
 #undef HYDE_GJ16
             default: return HYDE_ERR_SHAPE;
         }
-    } else if (p <= kGj20Max) {
-        // 400 threads take registers in whole 4-warp groups (512 threads' worth), so the
-        // 10 x 10 tile gets 128 registers and spills a little: still far ahead of the
-        // shared-memory kernel
-        launch_pdl(noise_gj_reg_kernel<10, 20>, 1, 400, 0, s, R, p, Ainv, Sd, status);
     } else {
         size_t smem = noise_smem_bytes(p);
         if (ensure_smem_limit((const void*)noise_gj_smem_kernel, (int)smem) != cudaSuccess)
