@@ -85,8 +85,8 @@ def test_gram_full_c1(hyde):
 @pytest.mark.parametrize("H,W,p,m,seed", [
     (64, 64, 32, 4, 1), (128, 128, 64, 8, 5), (45, 70, 24, 3, 9),
     (60, 64, 150, 5, 11),    # 16 x 16 threads, 10 x 10 register tiles
-    (60, 66, 176, 5, 12),    # 20 x 20 threads, 10 x 10 tiles (p <= 200)
-    (64, 72, 200, 6, 13),    # the same at p = 200 (the sliding-window scenes)
+    (60, 66, 176, 5, 12),    # 16 x 16 threads, 11 x 11 tiles
+    (64, 72, 200, 6, 13),    # 13 x 13 tiles at p = 200 (the sliding-window scenes)
     (64, 80, 230, 6, 14),    # shared-memory kernel
 ])
 def test_noise_est_matches_oracle(hyde, H, W, p, m, seed):
