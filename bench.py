@@ -42,17 +42,14 @@ FP32_SM_PEAK_TFLOPS = 128 * 2 * 2.070e9 / 1e12         # one SM, for single-bloc
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # dominant kernel, from one ncu capture of the 349 x 1905 x 144 cube; keyed by
 # (stage, precision). profiles/ holds the capture summaries; an entry is
-# removed when its kernel changes.
+# removed when its kernel changes (the eigensolver has no current capture).
 NCU_TRAFFIC: dict = {
-    # gram_partial84 385.70 + 3.25 MB, gram_reduce 6.83 MB
-    ("gram", "fp32"): 395.78e6,
+    # gram_tf32 387.44 + 4.57 MB (profiles/gram_tf32_349x1905x144.md)
+    ("gram", "fp32"): 392.01e6,
+    ("gram", "tf32x3"): 392.01e6,
     # gram_tc 385.77 + 3.68 MB, gram_tc_reduce 8.42 MB
     ("gram", "bf16x3"): 397.87e6,
     ("gram", "bf16x3_all"): 397.87e6,
-    # eig_fast (one thread block) 0.24 MB
-    ("eig", "fp32"): 0.24e6,
-    ("eig", "bf16x3"): 0.24e6,
-    ("eig", "bf16x3_all"): 0.24e6,
 }
 
 
@@ -530,7 +527,7 @@ def run_gb300(args) -> None:
     peaks = _measured_peaks()
     sbytes = _stage_bytes(r_star)
     dominant = max(stage_avg, key=stage_avg.get)
-    if dominant == "gram" and args.precision == "tf32x3":
+    if dominant == "gram" and args.precision in ("tf32x3", "fp32") and p % 4 == 0 and p <= 160:
         # tf32 MMA work per pixel: the principal 128-band block twice (H H^T and
         # H (2L)^T), the other band blocks three times; tensor peak for tf32 is
         # half the measured bf16 rate
