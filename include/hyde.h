@@ -496,10 +496,11 @@ int hyde_set_grid_sm_cap(int sms);
 unsigned long long hyde_set_wait_limit_ns(unsigned long long ns);
 
 /* Number of kernels one hyde_hyres_denoise call launches on a p x H x W
- * cube: 10 + 2 * (DWT launches), a DWT launch per level, except that the
- * coarse levels run fused in one launch (18 at 349 x 1905, 5 levels); the
- * two memsets that clear the workspace header and R are not counted. -1
- * for bad params or shapes. */
+ * cube: 12 + 2 * (DWT launches), a DWT launch per level, except that the
+ * coarse levels run fused in one launch (20 at 349 x 1905, 5 levels). The
+ * memsets are not counted: one clears the workspace header, and the SIMT
+ * and split-BF16 Gram clear R before their reduction (the split-TF32 Gram
+ * writes R whole). -1 for bad params or shapes. */
 int hyde_hyres_kernel_launches(int p, int H, int W, const hyde_hyres_params* params);
 
 #ifdef __cplusplus

@@ -771,10 +771,11 @@ int hyde_hyres_kernel_launches(int p, int H, int W, const hyde_hyres_params* par
     if (params->threshold_ll != 0 && params->threshold_ll != 1) return -1;
     int Hp, Wp;
     if (!padded(H, W, params->levels, &Hp, &Wp)) return -1;
-    // gram 2, noise 2, eig 1, weights 1, projection 1, DWT, SURE 2, IDWT, back 1
-    // (the workspace carve keeps the DWT buffers 16-byte aligned, so the
-    // coarse levels always run fused where the shape allows)
-    return 10 + 2 * dwt_launches(Hp, Wp, params->levels);
+    // gram 2, noise 2, eig 3 (tridiagonalisation, eigenpairs, orthonormalisation),
+    // weights 1, projection 1, DWT, SURE 2, IDWT, back 1 (the workspace carve
+    // keeps the DWT buffers 16-byte aligned, so the coarse levels always run
+    // fused where the shape allows)
+    return 12 + 2 * dwt_launches(Hp, Wp, params->levels);
 }
 
 }  // extern "C"

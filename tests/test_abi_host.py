@@ -48,7 +48,7 @@ def test_status_strings_and_version(lib):
 
 
 def test_kernel_launch_count(lib):
-    """The launch count the benchmark reports: gram 2, noise 2, eig 1,
+    """The launch count the benchmark reports: gram 2, noise 2, eig 3,
     weights 1, projection 1, SURE 2, back-projection 1, and per direction one
     DWT launch per level except that the coarse levels (those whose LL band
     has at most 12288 values, when the quarter-width stays a multiple of 4)
@@ -57,9 +57,9 @@ def test_kernel_launch_count(lib):
     def count(p, H, W, L, r):
         prm = api.params(L, r)
         return lib.hyde_hyres_kernel_launches(p, H, W, ctypes.byref(prm))
-    assert count(144, 349, 1905, 5, 20) == 10 + 2 * 4   # levels 1-3, then 4-5 fused
-    assert count(32, 64, 64, 2, 8) == 10 + 2 * 2       # level 1, then 2 fused
-    assert count(24, 77, 131, 3, 6) == 10 + 2 * 3      # 136 / 8 = 17: no fused tail
+    assert count(144, 349, 1905, 5, 20) == 12 + 2 * 4   # levels 1-3, then 4-5 fused
+    assert count(32, 64, 64, 2, 8) == 12 + 2 * 2       # level 1, then 2 fused
+    assert count(24, 77, 131, 3, 6) == 12 + 2 * 3      # 136 / 8 = 17: no fused tail
     assert count(32, 64, 64, 11, 8) == -1
     assert lib.hyde_hyres_kernel_launches(32, 64, 64, None) == -1
 

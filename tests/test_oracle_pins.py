@@ -922,3 +922,26 @@ def test_hyminor_scale_equivariant_and_cleans_sparse_noise():
     Ys, _ = N.stripes(c["Y"], 8, band_fraction=0.3, amplitude=1.0, seed=2)
     o3 = O.hyminor(Ys, 2, 6)
     assert O.rel_l2(o3["X"], c["X"]) < 0.9 * O.rel_l2(o3["G"], c["X"])
+
+
+# ---------------------------------------------------------------- Gram matrix
+
+def test_gram_hand_case_and_brute_force():
+    """R = Y^T Y with pixels as rows and bands as columns, input [band][H][W].
+    Hand case: bands (1, 2, 3) and (4, 5, 6) over three pixels give
+    R = [[14, 32], [32, 77]]. A transposed reading (pixels as columns) would
+    give a 3 x 3 matrix. Brute force: a triple loop over bands and pixels on
+    a small random cube, exact in float64 for small integer entries."""
+    Y = np.array([[[1.0, 2.0, 3.0]], [[4.0, 5.0, 6.0]]], dtype=np.float32)   # p=2, H=1, W=3
+    assert O.gram(Y).tolist() == [[14.0, 32.0], [32.0, 77.0]]
+    rng = np.random.default_rng(5)
+    Y = rng.integers(-8, 9, size=(5, 3, 4)).astype(np.float32)
+    R = O.gram(Y)
+    p = Y.shape[0]
+    for a in range(p):
+        for b in range(p):
+            s = 0.0
+            for y in range(3):
+                for x in range(4):
+                    s += float(Y[a, y, x]) * float(Y[b, y, x])
+            assert R[a, b] == s
