@@ -55,16 +55,7 @@ inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 inline int rank_pad(int r) { return (r + 3) / 4 * 4; }   // weights row stride: r rounded up to 4
 
-bool padded(int H, int W, int levels, int* Hp, int* Wp) {
-    if (levels < 1 || levels > kMaxLevels || H < 1 || W < 1) return false;
-    const int q = 1 << levels;
-    const long long hp = ((long long)H + q - 1) / q * q, wp = ((long long)W + q - 1) / q * q;
-    if (hp > (1 << 30) || wp > (1 << 30)) return false;
-    if (hp - H > H - 1 || wp - W > W - 1) return false;
-    *Hp = (int)hp;
-    *Wp = (int)wp;
-    return true;
-}
+bool padded(int H, int W, int levels, int* Hp, int* Wp) { return padded_dims(H, W, levels, Hp, Wp); }
 
 // Bump allocator over the caller's workspace (offsets only).
 struct Carver {

@@ -231,6 +231,20 @@ hyde_status launch_backproject_tc(const float* Zh, long long n, const float* Q, 
 // ------------------------------------------------------------------ DWT
 // Source of the first analysis level: the image is read at (y, x) of the
 // padded domain through whole-sample symmetric reflection at hv, wv.
+// Padded sides for an L-level transform: multiples of 2^L that whole-sample
+// symmetric extension can reach (at most H - 1 rows and W - 1 columns
+// added); false for unsupported shapes.
+inline bool padded_dims(int H, int W, int levels, int* Hp, int* Wp) {
+    if (levels < 1 || levels > kMaxLevels || H < 1 || W < 1) return false;
+    const int q = 1 << levels;
+    const long long hp = ((long long)H + q - 1) / q * q, wp = ((long long)W + q - 1) / q * q;
+    if (hp > (1 << 30) || wp > (1 << 30)) return false;
+    if (hp - H > H - 1 || wp - W > W - 1) return false;
+    *Hp = (int)hp;
+    *Wp = (int)wp;
+    return true;
+}
+
 struct DwtSrc {
     const float* ptr;
     long long bstride;
