@@ -418,6 +418,33 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H,
                                 size_t fws_bytes, void* bws, size_t bws_bytes,
                                 cudaStream_t stream);
 
+/* ----------------------------------------------------------------- FORPDN
+ * First-order spectral roughness penalty denoising (Sec. 2.1: a full-rank,
+ * wavelet-based method for additive Gaussian noise; the paper states no
+ * more). Reading: every band image is padded (whole-sample symmetric) and
+ * transformed by the L-level periodic db2 DWT; the coefficient positions
+ * form L + 1 groups (group 0 the final LL band, group l the detail positions
+ * of level l); in group g every position's spectrum c (its p band
+ * coefficients) becomes (I + lam_g D^T D)^-1 c, D the first difference
+ * along the bands; lam_g is the first minimiser over the grid lam_0 = 0,
+ * lam_m = 10^(-3 + 7 (m - 1) / (n_lambda - 2)) of Stein's unbiased risk
+ * estimate under independent band noise of variance sigma_b^2 (the
+ * regression noise estimate of the HyRes stage); the inverse DWT, cropped,
+ * is written to X.
+ * Y, X: float[p][H][W], device, may not alias. 2 <= p <= 256, H W >= p,
+ * 1 <= levels <= 10 (sides padded as for hyde_hyres_denoise),
+ * 2 <= n_lambda <= 256. info (device int[levels + 2], or NULL): info[0] the
+ * status seen on the device (HYDE_OK if none), info[1 + g] the chosen grid
+ * index of group g. sure (device double[levels + 1][n_lambda], or NULL):
+ * the SURE table. ws: hyde_forpdn_workspace_size bytes, 256-byte aligned.
+ * Asynchronous on stream; no host synchronisation.
+ */
+hyde_status hyde_forpdn_workspace_size(int p, int H, int W, int levels, int n_lambda,
+                                       size_t* bytes);
+hyde_status hyde_forpdn(const float* Y, float* X, int p, int H, int W, int levels,
+                        int n_lambda, int* info, double* sure, void* ws, size_t ws_bytes,
+                        cudaStream_t stream);
+
 /* ---------------------------------------------------------------- HyMiNoR
  * Mixed Gaussian and sparse noise reduction built on HyRes (Sec. 2.1: after
  * HyRes removes the Gaussian noise, an l1-l1 problem solved by a modified

@@ -73,10 +73,12 @@ def sure_group(G, N, sigma2, lam):
     return float(np.trace(M @ G @ M) + 2.0 * N * np.sum(sigma2 * np.diag(S)) - N * np.sum(sigma2))
 
 
-def forpdn(Y, levels, n_lambda=64, sigma=None):
+def forpdn(Y, levels, n_lambda=64, sigma=None, k=None):
     """FORPDN on ``Y`` (``float[p][H][W]``). Returns a dict with ``X`` (float64
     cube), ``sigma``, the SURE table ``S`` [L + 1][K] (group 0 = LL), the
-    chosen grid indices ``k`` [L + 1] and thresholds ``lam`` [L + 1]."""
+    chosen grid indices ``k`` [L + 1] and thresholds ``lam`` [L + 1]. ``k``
+    given (one grid index per group) replaces the SURE choice: the estimate
+    at another choice, for comparisons near ties."""
     Y = np.asarray(Y, dtype=np.float64)
     p, H, W = Y.shape
     n = H * W
@@ -97,7 +99,7 @@ def forpdn(Y, levels, n_lambda=64, sigma=None):
         G = Cg.T @ Cg
         for m, lam in enumerate(lams):
             S_tab[g, m] = sure_group(G, N, sigma2, lam)
-        k_sel[g] = int(np.argmin(S_tab[g]))    # first minimiser
+        k_sel[g] = int(np.argmin(S_tab[g])) if k is None else int(k[g])   # first minimiser
         F[:, mask] = (Cg @ smoother(p, lams[k_sel[g]])).T
     X = np.stack([idwt2(F[b], levels)[:H, :W] for b in range(p)])
     return dict(X=X, sigma=np.asarray(sigma, dtype=np.float64), S=S_tab, k=k_sel,

@@ -360,6 +360,27 @@ def hyminor(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64, lam: f
     return X, parse_info(info)
 
 
+def forpdn(Y: torch.Tensor, levels: int, n_lambda: int = 64) -> tuple[torch.Tensor, dict]:
+    """FORPDN of ``Y[p, H, W]`` (``hyde_forpdn``): per wavelet-level group,
+    spectral smoothing (I + lam D^T D)^-1 with lam chosen by SURE. Returns
+    ``(X, info)`` with info's ``status``, the chosen grid index per group
+    (``k``, group 0 = the final LL band) and the SURE table (``sure``)."""
+    lib = _lib.load()
+    Y = _cuda_f32(Y, "Y")
+    p, H, W = Y.shape
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_forpdn_workspace_size(p, H, W, levels, n_lambda, ctypes.byref(sz)),
+           "hyde_forpdn_workspace_size")
+    ws = _workspace(sz.value, Y.device)
+    X = torch.empty_like(Y)
+    info = torch.zeros(levels + 2, dtype=torch.int32, device=Y.device)
+    sure = torch.zeros((levels + 1, n_lambda), dtype=torch.float64, device=Y.device)
+    _check(lib.hyde_forpdn(_ptr(Y), _ptr(X), p, H, W, levels, n_lambda, _ptr(info), _ptr(sure),
+                           _ptr(ws), ws.numel(), _stream()), "hyde_forpdn")
+    inf = info.cpu().tolist()
+    return X, {"status": inf[0], "k": inf[1:], "sure": sure}
+
+
 def _scale_rows(scale: torch.Tensor, r_max: int, levels: int) -> torch.Tensor:
     if not scale.is_cuda or scale.dtype != torch.float32 or scale.dim() != 2:
         raise ValueError("scale must be a float32 CUDA matrix [rows >= r_max, levels]")
