@@ -415,6 +415,38 @@ def _form_hyminor(args, dev, cube, flush, stream) -> dict:
     return out
 
 
+def _form_forpdn(args, dev, cube, flush, stream) -> dict:
+    """FORPDN on the benchmark cube (five levels, 64-point grid), with its
+    error against the FP64 oracle on the whole cube and whether every
+    group's smoothing choice is the oracle's."""
+    import importlib
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2204_06979_gb300 import api
+    F = importlib.import_module("oracle.forpdn")
+    w = WORKLOAD
+    Y = torch.from_numpy(cube["Y"]).to(dev)
+    state = {}
+
+    def step():
+        state["X"], state["info"] = api.forpdn(Y, w["levels"])
+
+    out = _time_form(step, args, flush, stream, cube["Y"].size)
+    torch.cuda.synchronize(dev)
+    out.update({"workload": "349x1905x144 cube, db2 L=5, six groups (LL, levels 1-5), "
+                            "64-point smoothing grid",
+                "k": state["info"]["k"],
+                "note": "time includes the workspace allocation of each call"})
+    if not args.no_parity:
+        ref = F.forpdn(cube["Y"], w["levels"])
+        got = state["X"].cpu().numpy()
+        out.update({"rel_l2_vs_oracle": float(O.rel_l2(got, ref["X"])),
+                    "identical_choice": bool(list(ref["k"]) == list(state["info"]["k"])),
+                    "psnr_gain_db": float(O.psnr(cube["X"], got) - O.psnr(cube["X"], cube["Y"]))})
+    return out
+
+
 def _form_windows(args, dev, cube, flush, stream) -> dict:
     """Batched sliding-window form: a 2048 x 2048 x 200 scene in 512 uneven
     windows, one captured CUDA graph per scene."""
@@ -634,7 +666,7 @@ def run_gb300(args) -> None:
         for name, fn in (("precision_tf32x3", _form_precision_tf32),
                          ("precision_bf16x3", _form_precision), ("per_level", _form_per_level),
                          ("diff", _form_diff), ("hyminor", _form_hyminor),
-                         ("windows", _form_windows)):
+                         ("forpdn", _form_forpdn), ("windows", _form_windows)):
             try:
                 forms[name] = fn(args, dev, cube, flush, stream)
             except Exception as exc:   # a failing form is reported, not hidden

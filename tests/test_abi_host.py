@@ -281,3 +281,16 @@ def test_hyminor_rejects_bad_arguments_on_host(lib):
     assert lib.hyde_hyminor(1, 1, 8, 64, 64, P, 1.0, float("nan"), 50, None, None, 0, None) == 1
     assert lib.hyde_hyminor(1, 1, 8, 64, 64, P, 1.0, 10.0, 0, None, None, 0, None) == 2
     assert lib.hyde_hyminor_workspace_size(8, 64, 64, P, None) == 1
+
+
+def test_forpdn_rejects_bad_shapes_on_host(lib):
+    """hyde_forpdn_workspace_size checks its shape arguments on the host."""
+    sz = ctypes.c_size_t()
+    lib.hyde_forpdn_workspace_size.argtypes = [ctypes.c_int] * 5 + [ctypes.POINTER(ctypes.c_size_t)]
+    assert lib.hyde_forpdn_workspace_size(8, 64, 64, 2, 64, None) == 1     # no output pointer
+    assert lib.hyde_forpdn_workspace_size(1, 64, 64, 2, 64, ctypes.byref(sz)) == 2    # one band
+    assert lib.hyde_forpdn_workspace_size(300, 64, 64, 2, 64, ctypes.byref(sz)) == 2  # p > 256
+    assert lib.hyde_forpdn_workspace_size(8, 64, 64, 0, 64, ctypes.byref(sz)) == 2    # no level
+    assert lib.hyde_forpdn_workspace_size(8, 64, 64, 2, 1, ctypes.byref(sz)) == 2     # K < 2
+    assert lib.hyde_forpdn_workspace_size(8, 64, 64, 2, 300, ctypes.byref(sz)) == 2   # K > 256
+    assert lib.hyde_forpdn_workspace_size(8, 2, 2, 1, 64, ctypes.byref(sz)) == 2      # n < p
