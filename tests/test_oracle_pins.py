@@ -1025,3 +1025,61 @@ def test_forpdn_denoises_and_respects_symmetries():
     # group sizes cover the padded image once
     lev = O.level_map(64, 64, 2)
     assert sum(int(np.sum(lev == g)) for g in range(3)) == 64 * 64
+
+
+# ---------------------------------------------------------------- WSRRR
+
+def _wsrrr():
+    import importlib
+    return importlib.import_module("oracle.wsrrr")
+
+
+def test_wsrrr_zero_iterations_is_hyres_and_objective_decreases():
+    """No V-step leaves HyRes's estimate; each half-step is an exact block
+    minimisation, so the objective never increases (C0 and a cube with
+    padded sides)."""
+    Wm = _wsrrr()
+    for (H, W, p, m, seed, L, r) in [(64, 64, 32, 4, 1, 2, 8), (50, 45, 24, 3, 9, 3, 6)]:
+        c = make_cube(H, W, p, m=m, seed=seed)
+        g = O.hyres(c["Y"], L, r)
+        o0 = Wm.wsrrr(c["Y"], L, r, iters=0, hy=g)
+        assert O.rel_l2(o0["X"], g["X"]) < 1e-12
+        o = Wm.wsrrr(c["Y"], L, r, iters=6, hy=g)
+        d = np.diff(o["J"])
+        assert np.all(d <= 1e-12 * abs(o["J"][0])), d
+        assert o["J"][-1] < o["J"][0]
+
+
+def test_wsrrr_without_threshold_keeps_the_eigenvectors():
+    """lam = 0 on an unpadded cube: B = W2^T Yw V, so Yw^T W2 B = (Yw^T Yw) V
+    = V Lambda for eigenvectors V, whose polar factor is V itself."""
+    Wm = _wsrrr()
+    c = make_cube(64, 64, 32, m=4, seed=1)
+    g = O.hyres(c["Y"], 2, 8, rank=5, lam=0.0)
+    o = Wm.wsrrr(c["Y"], 2, 8, iters=3, hy=g)
+    assert np.max(np.abs(o["V"] - g["V"][:, :5])) < 1e-10
+
+
+def test_wsrrr_polar_factor_solves_procrustes():
+    """polar(M) maximises tr(V^T M) over matrices with orthonormal columns:
+    the maximum is the sum of M's singular values, and no random orthonormal
+    V exceeds it."""
+    Wm = _wsrrr()
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((12, 4)) @ np.diag([5.0, 2.0, 1.0, 0.1])
+    P = Wm.polar(M)
+    assert np.max(np.abs(P.T @ P - np.eye(4))) < 1e-13
+    best = np.trace(P.T @ M)
+    assert abs(best - np.sum(np.linalg.svd(M, compute_uv=False))) < 1e-12
+    for _ in range(200):
+        Qr, _ = np.linalg.qr(rng.standard_normal((12, 4)))
+        assert np.trace(Qr.T @ M) <= best + 1e-12
+
+
+def test_wsrrr_scale_equivariant():
+    Wm = _wsrrr()
+    c = make_cube(48, 48, 16, m=3, seed=6)
+    o = Wm.wsrrr(c["Y"], 2, 6, iters=3)
+    o4 = Wm.wsrrr(c["Y"] * np.float32(4.0), 2, 6, iters=3)
+    assert o4["rank"] == o["rank"]
+    assert O.rel_l2(o4["X"], 4.0 * o["X"]) < 1e-10
