@@ -447,6 +447,38 @@ def _form_forpdn(args, dev, cube, flush, stream) -> dict:
     return out
 
 
+def _form_wsrrr(args, dev, cube, flush, stream) -> dict:
+    """WSRRR on the benchmark cube: HyRes, then ten cyclic-descent steps
+    (thresholded coefficients, orthogonal Procrustes basis); its error
+    against the FP64 oracle at the same iteration count."""
+    import importlib
+    import torch
+    import oracle as O
+    from paper_2204_06979_gb300 import api
+    Wm = importlib.import_module("oracle.wsrrr")
+    w = WORKLOAD
+    iters = 10
+    Y = torch.from_numpy(cube["Y"]).to(dev)
+    state = {}
+
+    def step():
+        state["X"], state["info"] = api.wsrrr(Y, w["levels"], w["r_max"], w["n_lambda"],
+                                              iters=iters)
+
+    out = _time_form(step, args, flush, stream, cube["Y"].size)
+    torch.cuda.synchronize(dev)
+    out.update({"workload": "349x1905x144 cube, db2 L=5, r<=20: HyRes, then 10 WSRRR steps",
+                "rank": state["info"]["rank"],
+                "note": "time includes the workspace allocation of each call"})
+    if not args.no_parity:
+        ref = Wm.wsrrr(cube["Y"], w["levels"], w["r_max"], w["n_lambda"], iters=iters)
+        got = state["X"].cpu().numpy()
+        out.update({"rel_l2_vs_oracle": float(O.rel_l2(got, ref["X"])),
+                    "objective_first_last": [float(ref["J"][0]), float(ref["J"][-1])],
+                    "psnr_gain_db": float(O.psnr(cube["X"], got) - O.psnr(cube["X"], cube["Y"]))})
+    return out
+
+
 def _form_windows(args, dev, cube, flush, stream) -> dict:
     """Batched sliding-window form: a 2048 x 2048 x 200 scene in 512 uneven
     windows, one captured CUDA graph per scene."""
@@ -666,7 +698,8 @@ def run_gb300(args) -> None:
         for name, fn in (("precision_tf32x3", _form_precision_tf32),
                          ("precision_bf16x3", _form_precision), ("per_level", _form_per_level),
                          ("diff", _form_diff), ("hyminor", _form_hyminor),
-                         ("forpdn", _form_forpdn), ("windows", _form_windows)):
+                         ("forpdn", _form_forpdn), ("wsrrr", _form_wsrrr),
+                         ("windows", _form_windows)):
             try:
                 forms[name] = fn(args, dev, cube, flush, stream)
             except Exception as exc:   # a failing form is reported, not hidden

@@ -445,6 +445,33 @@ hyde_status hyde_forpdn(const float* Y, float* X, int p, int H, int W, int level
                         int n_lambda, int* info, double* sure, void* ws, size_t ws_bytes,
                         cudaStream_t stream);
 
+/* ------------------------------------------------------------------ WSRRR
+ * Wavelet-based sparse reduced-rank regression (Sec. 2.1: a low-rank,
+ * wavelet-based method for Gaussian noise that also extracts features; the
+ * paper states no more). Reading: on the whitened cube Yw (the bands
+ * divided by the HyRes noise estimate, padded by whole-sample symmetric
+ * extension, one row per padded pixel) the model Yw ~ W2 B V^T (W2 the
+ * orthogonal L-level db2 synthesis of r component images, B their wavelet
+ * coefficients, V^T V = I) and the objective
+ * 1/2 ||Yw - W2 B V^T||^2 + lambda |B without the final LL band|_1,
+ * decreased by cyclic descent from HyRes's basis, rank r* and threshold
+ * lambda*: iters times B <- soft(W2^T Yw V, lambda) (the HyRes projection,
+ * analysis and thresholded synthesis), V <- polar(Yw^T W2 B) (orthogonal
+ * Procrustes, in double); then a last B-step. X = sigma_b (W2 B V^T),
+ * cropped; iters = 0 gives HyRes's estimate.
+ * params as for hyde_hyres_denoise with lambda_mode HYDE_LAMBDA_SHARED,
+ * threshold_ll 0, precision HYDE_PREC_FP32 or HYDE_PREC_TF32X3, r_max <= 32;
+ * 0 <= iters <= 1000. info: HyRes's choice (r*, lambda index) and the
+ * device status. features (device float[r_max][H_p][W_p], or NULL): the
+ * final component images W2 B on the padded domain (rows >= r* zero).
+ * ws: hyde_wsrrr_workspace_size bytes, 256-byte aligned. Asynchronous.
+ */
+hyde_status hyde_wsrrr_workspace_size(int p, int H, int W, const hyde_hyres_params* params,
+                                      size_t* bytes);
+hyde_status hyde_wsrrr(const float* Y, float* X, int p, int H, int W,
+                       const hyde_hyres_params* params, int iters, hyde_hyres_info* info,
+                       float* features, void* ws, size_t ws_bytes, cudaStream_t stream);
+
 /* ---------------------------------------------------------------- HyMiNoR
  * Mixed Gaussian and sparse noise reduction built on HyRes (Sec. 2.1: after
  * HyRes removes the Gaussian noise, an l1-l1 problem solved by a modified

@@ -70,6 +70,10 @@ SIGNATURES = {
                                          c_vp]),
     "hyde_hyres_kernel_launches": (c_int, [c_int, c_int, c_int, ctypes.POINTER(HydeParams)]),
     "hyde_set_grid_sm_cap": (c_int, [c_int]),
+    "hyde_wsrrr_workspace_size": (c_int, [c_int, c_int, c_int, ctypes.POINTER(HydeParams),
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+    "hyde_wsrrr": (c_int, [c_vp, c_vp, c_int, c_int, c_int, ctypes.POINTER(HydeParams), c_int,
+                           c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),
     "hyde_forpdn_workspace_size": (c_int, [c_int, c_int, c_int, c_int, c_int,
                                            ctypes.POINTER(ctypes.c_size_t)]),
     "hyde_forpdn": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_int, c_vp, c_vp, c_vp,

@@ -360,6 +360,34 @@ def hyminor(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64, lam: f
     return X, parse_info(info)
 
 
+def wsrrr(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64, iters: int = 10,
+          precision: int = PREC_FP32, features: bool = False
+          ) -> tuple[torch.Tensor, dict] | tuple[torch.Tensor, dict, torch.Tensor]:
+    """WSRRR of ``Y[p, H, W]`` (``hyde_wsrrr``): HyRes, then ``iters`` cyclic
+    descent steps on the sparse reduced-rank model. Returns ``(X, info)``
+    (info: HyRes's choice), and with ``features`` also the component images
+    ``F[r_max, H_p, W_p]`` (rows past the rank zero)."""
+    lib = _lib.load()
+    Y = _cuda_f32(Y, "Y")
+    p, H, W = Y.shape
+    prm = params(levels, r_max, n_lambda, precision)
+    sz = ctypes.c_size_t()
+    _check(lib.hyde_wsrrr_workspace_size(p, H, W, ctypes.byref(prm), ctypes.byref(sz)),
+           "hyde_wsrrr_workspace_size")
+    ws = _workspace(sz.value, Y.device)
+    X = torch.empty_like(Y)
+    info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=Y.device)
+    F = None
+    if features:
+        Hp, Wp = padded_shape(H, W, levels)
+        F = torch.empty((r_max, Hp, Wp), dtype=torch.float32, device=Y.device)
+    _check(lib.hyde_wsrrr(_ptr(Y), _ptr(X), p, H, W, ctypes.byref(prm), int(iters), _ptr(info),
+                          _ptr(F), _ptr(ws), ws.numel(), _stream()), "hyde_wsrrr")
+    if features:
+        return X, parse_info(info), F
+    return X, parse_info(info)
+
+
 def forpdn(Y: torch.Tensor, levels: int, n_lambda: int = 64) -> tuple[torch.Tensor, dict]:
     """FORPDN of ``Y[p, H, W]`` (``hyde_forpdn``): per wavelet-level group,
     spectral smoothing (I + lam D^T D)^-1 with lam chosen by SURE. Returns

@@ -482,6 +482,108 @@ hyde_status hyde_hyres_denoise(const float* Y, float* X, int p, int H, int W,
     return hyres_enqueue(Y, X, p, H, W, params, info, ws, ws_bytes, stream, nullptr);
 }
 
+// ------------------------------------------------------------------ WSRRR
+static hyde_status wsrrr_check(const hyde_hyres_params* params) {
+    if (!params) return HYDE_ERR_INVALID_ARG;
+    if (params->lambda_mode != HYDE_LAMBDA_SHARED || params->threshold_ll != 0)
+        return HYDE_ERR_INVALID_ARG;
+    if (params->precision != HYDE_PREC_FP32 && params->precision != HYDE_PREC_TF32X3)
+        return HYDE_ERR_INVALID_ARG;
+    if (params->r_max > 32) return HYDE_ERR_SHAPE;
+    return HYDE_OK;
+}
+
+struct WsrrrExtra {
+    size_t hy, M, partials, total;
+    int nblocks;
+};
+
+static hyde_status wsrrr_layout(int p, int H, int W, const hyde_hyres_params* params,
+                                HyresLayout* L, WsrrrExtra* E) {
+    hyde_status st = wsrrr_check(params);
+    if (st != HYDE_OK) return st;
+    st = hyres_layout(p, H, W, params, L);
+    if (st != HYDE_OK) return st;
+    const int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    E->nblocks = 2 * sms;
+    Carver c;
+    E->hy = c.take(L->pub.total);
+    E->M = c.take((size_t)p * params->r_max * sizeof(double));
+    E->partials = c.take(wsrrr_cross_partial_bytes(p, params->r_max, E->nblocks));
+    E->total = c.off;
+    return HYDE_OK;
+}
+
+hyde_status hyde_wsrrr_workspace_size(int p, int H, int W, const hyde_hyres_params* params,
+                                      size_t* bytes) {
+    if (!bytes) return HYDE_ERR_INVALID_ARG;
+    HyresLayout L;
+    WsrrrExtra E;
+    const hyde_status st = wsrrr_layout(p, H, W, params, &L, &E);
+    if (st != HYDE_OK) return st;
+    *bytes = E.total;
+    return HYDE_OK;
+}
+
+hyde_status hyde_wsrrr(const float* Y, float* X, int p, int H, int W,
+                       const hyde_hyres_params* params, int iters, hyde_hyres_info* info,
+                       float* features, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!Y || !X || Y == X) return HYDE_ERR_INVALID_ARG;
+    if (iters < 0 || iters > 1000) return HYDE_ERR_SHAPE;
+    HyresLayout L;
+    WsrrrExtra E;
+    hyde_status st = wsrrr_layout(p, H, W, params, &L, &E);
+    if (st != HYDE_OK) return st;
+    if (!ws || !aligned(ws, kAlign) || ws_bytes < E.total) return HYDE_ERR_WORKSPACE;
+    void* hws = at<void>(ws, E.hy);
+    // HyRes: noise estimate, subspace, rank r* and threshold lambda*
+    st = hyres_enqueue(Y, X, p, H, W, params, info, hws, L.pub.total, stream, nullptr);
+    if (st != HYDE_OK) return st;
+    if (iters == 0 && !features) return HYDE_OK;
+    const int r = params->r_max, lev = params->levels;
+    int* status = at<int>(hws, L.pub.status);
+    int* rank_dev = at<int>(hws, L.rank_dev);
+    double* lam_dev = at<double>(hws, L.lam_dev);
+    double* sigma = at<double>(hws, L.pub.sigma);
+    double* V = at<double>(hws, L.pub.V);
+    float* P = at<float>(hws, L.P);
+    float* Q = at<float>(hws, L.Q);
+    float* zp = at<float>(hws, L.zp);
+    float* coef = at<float>(hws, L.pub.coef);
+    float* scratch = at<float>(hws, L.scratch);
+    double* M = at<double>(ws, E.M);
+    const DwtSrc src{zp, L.N, L.Wp, L.Hp, L.Wp};
+#define HYDE_TRY(x) do { hyde_status s_ = (x); if (s_ != HYDE_OK) return s_; } while (0)
+    // B-step: coefficients of the projected whitened cube, thresholded
+    auto bstep = [&]() -> hyde_status {
+        HYDE_TRY(launch_weights(V, sigma, p, r, L.RM, P, Q, stream));
+        HYDE_TRY(launch_project_pad(Y, p, H, W, P, r, L.RM, zp, L.Hp, L.Wp, stream));
+        return launch_dwt2(src, coef, r, L.Hp, L.Wp, lev, scratch, stream);
+    };
+    for (int it = 0; it < iters; ++it) {
+        HYDE_TRY(bstep());
+        // component images W2 B on the padded domain (no crop)
+        HYDE_TRY(launch_idwt2(coef, zp, r, L.Hp, L.Wp, L.Hp, L.Wp, lev, scratch, lam_dev,
+                              rank_dev, stream));
+        // V-step: the orthogonal Procrustes basis of Yw^T W2 B
+        HYDE_TRY(launch_wsrrr_cross(Y, p, H, W, zp, r, L.Hp, L.Wp, rank_dev, sigma,
+                                    at<float>(ws, E.partials), E.nblocks, M, r, status, stream));
+        HYDE_TRY(launch_wsrrr_polar(M, p, r, rank_dev, V, r, status, stream));
+    }
+    HYDE_TRY(bstep());
+    if (features) {
+        if (cudaMemsetAsync(features, 0, (size_t)r * L.N * sizeof(float), stream) != cudaSuccess)
+            return HYDE_ERR_CUDA;
+        HYDE_TRY(launch_idwt2(coef, features, r, L.Hp, L.Wp, L.Hp, L.Wp, lev, scratch, lam_dev,
+                              rank_dev, stream));
+    }
+    HYDE_TRY(launch_idwt2(coef, zp, r, L.Hp, L.Wp, H, W, lev, scratch, lam_dev, rank_dev, stream));
+    HYDE_TRY(launch_backproject(zp, L.n, Q, p, r, L.RM, rank_dev, X, stream));
+#undef HYDE_TRY
+    return cuda_status(cudaGetLastError());
+}
+
 hyde_status hyde_hyres_denoise_host(const float* const* Y_host, float* const* X_host,
                                     hyde_hyres_info* info_host, int count, int p, int H,
                                     int W, const hyde_hyres_params* params,

@@ -266,6 +266,21 @@ hyde_status launch_idwt2(const float* coef, float* out, int batch, int Hp,
                          const float* scale = nullptr, int scale_ld = 0,
                          bool ll_thr = false);
 
+// ------------------------------------------------------------------ WSRRR
+// M (double [p][ldm]) = Yw^T Xr over the padded pixels (Yw = the cube read
+// through the symmetric extension, divided by sigma_b; Xr = the first
+// *rank_dev of the RM padded component images); partials: nblocks x p x RM
+// floats (wsrrr_cross_partial_bytes).
+hyde_status launch_wsrrr_cross(const float* Y, int p, int H, int W, const float* Xr, int RM,
+                               int Hp, int Wp, const int* rank_dev, const double* sigma,
+                               float* partials, int nblocks, double* M, int ldm, int* status,
+                               cudaStream_t s);
+size_t wsrrr_cross_partial_bytes(int p, int RM, int nblocks);
+// V[:, :r] (double [p][ldv]) = the orthonormal polar factor of M[:, :r],
+// r = *rank_dev <= 32, in double.
+hyde_status launch_wsrrr_polar(const double* M, int p, int ldm, const int* rank_dev, double* V,
+                               int ldv, int* status, cudaStream_t s);
+
 // ------------------------------------------------- differentiation form
 // acc[i][l] (double, zeroed by the caller) += per-(component, level) sums over
 // the detail coefficients of components i < *rank:
