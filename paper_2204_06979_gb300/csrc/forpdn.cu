@@ -249,71 +249,105 @@ forpdn_energy_kernel(const double* __restrict__ Gg, const double* __restrict__ s
 // of the tridiagonal I + lam D^T D at it (diagonal 1 + lam deg_b, deg = 1 at
 // the ends and 2 inside; off-diagonal -lam): m_0 = a_0,
 // m_b = a_b - lam^2 / m_{b-1}, stored as inv_b = 1 / m_b and
-// cp_b = -lam / m_b.
+// cp_b = -lam / m_b. Four threads share a grid point (k split four ways,
+// fixed combination order); each term's factors are formed in float (their
+// relative error, ~1e-7, is far below the table's use) and accumulated in
+// double. The factorisation runs in double (for large lam the system's
+// condition number, ~1 + 4 lam, amplifies float rounding in the pivots),
+// with reciprocals from a float seed and two Newton-Raphson steps
+// r <- r (2 - x r) (each squares the relative error, ~6e-8 -> ~4e-15 ->
+// double rounding) in place of double divisions.
+constexpr int kSelParts = 4;
+
+__device__ __forceinline__ double rcp_newton(double x) {
+    double r = (double)(1.0f / (float)x);
+    r = r * fma(-x, r, 2.0);
+    r = r * fma(-x, r, 2.0);
+    return r;
+}
+
 __global__ void __launch_bounds__(256)
 forpdn_select_kernel(const double* __restrict__ E, const double* __restrict__ sigma, int p,
                      int K, FpGeom G, double* __restrict__ sure, int* __restrict__ kidx,
                      float* __restrict__ tables, int* status, int* info) {
     pdl_wait();
     pdl_trigger();
-    __shared__ double mu[256], Ek[256], Ak[256];
+    __shared__ float mu[256];
+    __shared__ double Ek[256], Ak[256];
     __shared__ double S[256];
+    __shared__ double part[256];
     __shared__ double s_sig2;
     const int g = blockIdx.x, t = threadIdx.x, ng = G.ngroups;
     for (int k = t; k < p; k += blockDim.x) {
-        const double s = sinpi((double)k / (2.0 * p));
-        mu[k] = 4.0 * s * s;
+        const double sn = sinpi((double)k / (2.0 * p));
+        mu[k] = (float)(4.0 * sn * sn);
         Ek[k] = E[(long long)g * p + k];
         Ak[k] = E[(long long)ng * p + k];
     }
-    if (t == 0) {
+    if (t < 32) {
         double s2 = 0.0;
-        for (int b = 0; b < p; ++b) s2 = fma(sigma[b], sigma[b], s2);
-        s_sig2 = s2;
+        for (int b = t; b < p; b += 32) s2 = fma(sigma[b], sigma[b], s2);
+        s2 = warp_sum_d(s2);
+        if (t == 0) s_sig2 = s2;
     }
     __syncthreads();
     double npos = 0.0;
     for (int r = 0; r < G.nrect[g]; ++r) npos += (double)G.rect[g][r].h * G.rect[g][r].w;
-    for (int m = t; m < K; m += blockDim.x) {
-        const double lam = m == 0 ? 0.0 : exp10(-3.0 + 7.0 * (m - 1) / (double)(K > 2 ? K - 2 : 1));
+    for (int m0 = 0; m0 < K; m0 += 256 / kSelParts) {
+        const int m = m0 + t / kSelParts, part_id = t % kSelParts;
         double s = 0.0;
-        for (int k = 0; k < p; ++k) {
-            const double den = 1.0 + lam * mu[k];
-            const double f = lam * mu[k] / den;
-            s += f * f * Ek[k] + 2.0 * npos * Ak[k] / den;
+        if (m < K) {
+            const float lam = m == 0 ? 0.f
+                                     : (float)exp10(-3.0 + 7.0 * (m - 1) / (double)(K > 2 ? K - 2 : 1));
+            for (int k = part_id; k < p; k += kSelParts) {
+                const float den = fmaf(lam, mu[k], 1.0f);
+                const float iden = 1.0f / den;
+                const float f = lam * mu[k] * iden;
+                s = fma((double)(f * f), Ek[k], s);
+                s = fma(2.0 * npos * (double)iden, Ak[k], s);
+            }
         }
-        s -= npos * s_sig2;
-        S[m] = s;
-        if (!isfinite(s)) set_status(status, HYDE_ERR_NUMERIC);
-        sure[(long long)g * K + m] = s;
+        part[t] = s;
+        __syncthreads();
+        if (part_id == 0 && m < K) {
+            const double tot = ((part[t] + part[t + 1]) + (part[t + 2] + part[t + 3])) - npos * s_sig2;
+            S[m] = tot;
+            if (!isfinite(tot)) set_status(status, HYDE_ERR_NUMERIC);
+            sure[(long long)g * K + m] = tot;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (t == 0) {
         int best = 0;
         for (int m = 1; m < K; ++m)
             if (S[m] < S[best]) best = m;
         kidx[g] = best;
         if (info) info[1 + g] = best;
-        const double lam = best == 0 ? 0.0 : exp10(-3.0 + 7.0 * (best - 1) / (double)(K > 2 ? K - 2 : 1));
+        const double lam = best == 0 ? 0.0
+                                     : exp10(-3.0 + 7.0 * (best - 1) / (double)(K > 2 ? K - 2 : 1));
         float* inv = tables + (long long)g * (2 * p + 1);
         float* cpv = inv + p;
-        double mprev = 1.0;
+        double imprev = 1.0;
         for (int b = 0; b < p; ++b) {
             const double deg = p == 1 ? 0.0 : ((b == 0 || b == p - 1) ? 1.0 : 2.0);
-            const double a = 1.0 + lam * deg;
-            const double m = b == 0 ? a : a - lam * lam / mprev;
-            inv[b] = (float)(1.0 / m);
-            cpv[b] = (float)(-lam / m);
-            mprev = m;
+            const double a = fma(lam, deg, 1.0);
+            const double m = b == 0 ? a : fma(-lam * lam, imprev, a);
+            const double im = rcp_newton(m);
+            inv[b] = (float)im;
+            cpv[b] = (float)(-lam * im);
+            imprev = im;
         }
         inv[2 * p] = (float)lam;
     }
 }
 
-// One thread per Mallat position: its group, then the tridiagonal solve in
-// place (forward values d_b = (c_b + lam d_{b-1}) / m_b in shared memory,
-// then x_b = d_b - cp_b x_{b+1}). Positions are consecutive within a row, so
-// every band's loads and stores are coalesced.
+// A block of kSmoothThreads consecutive Mallat positions: their spectra
+// (p band rows of kSmoothThreads floats) are copied into shared memory with
+// 16-byte cp.async; one thread per position finds its group and solves the
+// tridiagonal system there (forward values d_b = (c_b + lam d_{b-1}) / m_b,
+// then x_b = d_b - cp_b x_{b+1}, in place); the block writes the rows back
+// with 16-byte stores. The plane Hp Wp and the block's first position are
+// multiples of 4, so every 16-byte piece is wholly inside or outside.
 __global__ void __launch_bounds__(kSmoothThreads)
 forpdn_smooth_kernel(float* __restrict__ C, int p, int Hp, int Wp, int levels,
                      const float* __restrict__ tables) {
@@ -321,38 +355,56 @@ forpdn_smooth_kernel(float* __restrict__ C, int p, int Hp, int Wp, int levels,
     pdl_trigger();
     extern __shared__ float fsm[];
     const int ng = levels + 1;
+    const int ntab = (ng * (2 * p + 1) + 3) & ~3;
     float* tab = fsm;                          // [ng][2 p + 1]
-    float* dsm = fsm + ng * (2 * p + 1);       // [p][kSmoothThreads]
+    float* dsm = fsm + ntab;                   // [p][kSmoothThreads], 16-byte aligned
     const int t = threadIdx.x;
-    for (int i = t; i < ng * (2 * p + 1); i += kSmoothThreads) tab[i] = tables[i];
-    __syncthreads();
     const long long plane = (long long)Hp * Wp;
-    const long long q = (long long)blockIdx.x * kSmoothThreads + t;
-    if (q >= plane) return;
-    const int y = (int)(q / Wp), x = (int)(q - (long long)y * Wp);
-    int ly = 0, lx = 0;
-    for (int j = 1; j <= levels; ++j) {
-        if (y < (Hp >> j)) ly = j;
-        if (x < (Wp >> j)) lx = j;
+    const long long q0 = (long long)blockIdx.x * kSmoothThreads;
+    constexpr int Q4 = kSmoothThreads / 4;
+    for (int e = t; e < p * Q4; e += kSmoothThreads) {
+        const int b = e / Q4, k4 = e - b * Q4;
+        const long long q = q0 + 4 * k4;
+        const bool ok = q < plane;
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dsm + b * kSmoothThreads + 4 * k4);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d),
+                     "l"(C + (long long)b * plane + (ok ? q : 0)), "r"(ok ? 16 : 0));
     }
-    const int m = ly < lx ? ly : lx;
-    const int g = m == levels ? 0 : m + 1;
-    const float* inv = tab + g * (2 * p + 1);
-    const float* cpv = inv + p;
-    const float lam = inv[2 * p];
-    float* cq = C + q;
-    float d = 0.f;
-#pragma unroll 8
-    for (int b = 0; b < p; ++b) {
-        const float c = cq[(long long)b * plane];
-        d = fmaf(lam, d, c) * inv[b];
-        dsm[b * kSmoothThreads + t] = d;
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int i = t; i < ng * (2 * p + 1); i += kSmoothThreads) tab[i] = tables[i];
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const long long q = q0 + t;
+    if (q < plane) {
+        const int y = (int)(q / Wp), x = (int)(q - (long long)y * Wp);
+        int ly = 0, lx = 0;
+        for (int j = 1; j <= levels; ++j) {
+            if (y < (Hp >> j)) ly = j;
+            if (x < (Wp >> j)) lx = j;
+        }
+        const int m = ly < lx ? ly : lx;
+        const int g = m == levels ? 0 : m + 1;
+        const float* inv = tab + g * (2 * p + 1);
+        const float* cpv = inv + p;
+        const float lam = inv[2 * p];
+        float d = 0.f;
+        for (int b = 0; b < p; ++b) {
+            d = fmaf(lam, d, dsm[b * kSmoothThreads + t]) * inv[b];
+            dsm[b * kSmoothThreads + t] = d;
+        }
+        float xv = d;
+        for (int b = p - 2; b >= 0; --b) {
+            xv = fmaf(-cpv[b], xv, dsm[b * kSmoothThreads + t]);
+            dsm[b * kSmoothThreads + t] = xv;
+        }
     }
-    float xv = d;
-    cq[(long long)(p - 1) * plane] = xv;
-    for (int b = p - 2; b >= 0; --b) {
-        xv = fmaf(-cpv[b], xv, dsm[b * kSmoothThreads + t]);
-        cq[(long long)b * plane] = xv;
+    __syncthreads();
+    for (int e = t; e < p * Q4; e += kSmoothThreads) {
+        const int b = e / Q4, k4 = e - b * Q4;
+        const long long qq = q0 + 4 * k4;
+        if (qq < plane)
+            *reinterpret_cast<float4*>(C + (long long)b * plane + qq) =
+                *reinterpret_cast<const float4*>(dsm + b * kSmoothThreads + 4 * k4);
     }
 }
 
@@ -430,7 +482,8 @@ hyde_status fp_layout(int p, int H, int W, int levels, int K, FpLayout* out) {
     L.threads = (L.ntiles < 128 ? 128 : (L.ntiles + 31) / 32 * 32);
     if (L.threads > kFpMaxThreads) return HYDE_ERR_SHAPE;
     L.smem_gram = (size_t)FSTAGES * L.PT * 8 * FKC * sizeof(float);
-    L.smem_smooth = ((size_t)G.ngroups * (2 * p + 1) + (size_t)p * kSmoothThreads) * sizeof(float);
+    L.smem_smooth = ((size_t)((G.ngroups * (2 * p + 1) + 3) & ~3) + (size_t)p * kSmoothThreads) *
+                    sizeof(float);
     if (L.smem_gram > 227 * 1024 || L.smem_smooth > 227 * 1024) return HYDE_ERR_SHAPE;
     size_t off = 0;
     auto take = [&](size_t bytes) {

@@ -17,7 +17,8 @@
 //  * wsrrr_polar_kernel (one block, double): G = M^T M, its Cholesky factor
 //    L (M = Q1 L^T), Q1 by triangular solves, the polar factor U of L^T by
 //    the scaled Newton iteration X <- (g X + X^-T / g) / 2 (Gauss-Jordan
-//    inverses with partial pivoting, at most 40 iterations), V = Q1 U.
+//    inverses with partial pivoting; stops once an update is below 1e-12 of
+//    X, at most 40 iterations), V = Q1 U.
 #include <float.h>
 
 #include "hyde_internal.cuh"
@@ -285,10 +286,11 @@ wsrrr_polar_kernel(const double* __restrict__ M, int p, int ldm, const int* __re
         }
         __syncthreads();
         const double g = sqrt(sqrt(s_ni / s_nx));      // (|X^-1|_F / |X|_F)^(1/2)
+        const double ginv = 1.0 / g;
         double dd = 0.0, nn = 0.0;
         for (int e = t; e < r * r; e += kPolarThreads) {
             const int i = e / r, j = e - i * r;
-            const double xn = 0.5 * (g * X[i][j] + Xi[j][i] / g);
+            const double xn = 0.5 * (g * X[i][j] + Xi[j][i] * ginv);
             const double d = xn - X[i][j];
             dd = fma(d, d, dd);
             nn = fma(xn, xn, nn);
@@ -310,7 +312,7 @@ wsrrr_polar_kernel(const double* __restrict__ M, int p, int ldm, const int* __re
         if (t == 0) {
             double a = 0.0;
             for (int w = 0; w < kPolarThreads / 32; ++w) a += s_red[w];
-            s_stop = s_nx <= 1e-30 * a ? 1 : 0;
+            s_stop = s_nx <= 1e-24 * a ? 1 : 0;   // |update| <= 1e-12 |X|: quadratic convergence
         }
         for (int e = t; e < r * r; e += kPolarThreads) {
             const int i = e / r, j = e - i * r;
@@ -320,12 +322,15 @@ wsrrr_polar_kernel(const double* __restrict__ M, int p, int ldm, const int* __re
         if (s_stop) break;
     }
     // V = Q1 U with Q1 = M L^-T (row b: forward substitution with L)
+    __shared__ double s_dinv[kMaxR];
+    for (int i = t; i < r; i += kPolarThreads) s_dinv[i] = 1.0 / Gm[i][i];
+    __syncthreads();
     for (int b = t; b < p; b += kPolarThreads) {
         double q[kMaxR];
         for (int i = 0; i < r; ++i) {
             double v = M[(long long)b * ldm + i];
             for (int j = 0; j < i; ++j) v = fma(-q[j], Gm[i][j], v);
-            q[i] = v / Gm[i][i];
+            q[i] = v * s_dinv[i];
         }
         for (int j = 0; j < r; ++j) {
             double v = 0.0;
