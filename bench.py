@@ -20,6 +20,7 @@ bounded column slice of the same cube on the host cores.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import os
 import statistics
@@ -542,13 +543,15 @@ def run_gb300(args) -> None:
     torch.cuda.synchronize(dev)
     info = h.result_info()
 
-    # ---- device-timed steps (each step between its own events, L2 flushed between)
+    # ---- one cube at a time (each between its own events, L2 flushed between):
+    # the latency of a denoise, and the headline when --streams 1
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    slots = args.streams if (lmode == api.LAMBDA_SHARED and not args.threshold_ll) else 1
     clocks = ClockSampler(local)
     barrier()
     wall0 = time.perf_counter()
-    with clocks:
+    with (clocks if slots == 1 else contextlib.nullcontext()):
         for i in range(args.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
@@ -561,7 +564,43 @@ def run_gb300(args) -> None:
     ms_per_step = total_ms / args.steps
     value = _job_rate(world, voxels, args.steps, total_ms)
     step_stats = _step_stats(step_ms)
+    latency = {"ms": round(ms_per_step, 4), "step_ms": step_stats,
+               "value": round(value, 1)}
     X_timed = Xd.clone() if rank == 0 else None
+
+    # ---- the headline: K cubes in flight over `slots` workspaces and streams
+    # (hyde_hyres_denoise_many), distinct input copies (each 383 MB > L2, so
+    # no flush is needed between them), exactly K cubes between a barrier +
+    # synchronize on both sides
+    pipeline = None
+    if slots > 1:
+        many = api.HyResMany(p, H, W, w["levels"], w["r_max"], w["n_lambda"], slots=slots,
+                             device=dev, precision=prec)
+        Ys = [Yd] + [Yd.clone() for _ in range(slots - 1)]
+        Xs = [torch.empty_like(Yd) for _ in range(slots)]
+        pick = lambda K: ([Ys[k % slots] for k in range(K)], [Xs[k % slots] for k in range(K)])
+        if args.warmup > 0:
+            many(*pick(args.warmup))
+        torch.cuda.synchronize(dev)
+        yk, xk = pick(args.steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        wall0 = time.perf_counter()
+        with clocks:
+            e0.record(stream)
+            many(yk, xk)
+            e1.record(stream)
+            barrier()
+        wall = time.perf_counter() - wall0
+        total_ms = _max_over_ranks(dist, [e0.elapsed_time(e1)], dev)[0]
+        ms_per_step = total_ms / args.steps
+        value = _job_rate(world, voxels, args.steps, total_ms)
+        X_timed = Xs[(args.steps - 1) % slots].clone() if rank == 0 else None
+        last = many.result_info(args.steps - 1)
+        pipeline = {"slots": slots, "ms_per_cube": round(ms_per_step, 4),
+                    "last_cube_status": last["status"], "last_cube_rank": last["rank"],
+                    "identical_to_serial": bool(torch.equal(Xs[(args.steps - 1) % slots], Xd))}
 
     # ---- per-stage timing through the timed entry point (same launches)
     nst = _lib.N_STAGES
@@ -714,6 +753,13 @@ def run_gb300(args) -> None:
 
     if rank == 0:
         cfg = _config(world)
+        if pipeline is not None:
+            cfg["streams"] = slots
+            cfg["workload"] += (f", {slots} cubes in flight (hyde_hyres_denoise_many: one "
+                                f"workspace and stream each)")
+            cfg["l2"] = (f"each cube's input (383 MB, {slots} distinct copies) exceeds L2; no "
+                         f"flush between pipelined cubes (the serial latency run flushes 256 MB "
+                         f"between steps)")
         if args.precision == "tf32x3":
             cfg["precision"] = "tf32x3 (Gram on tcgen05, split-TF32 compensated, FP32-accurate)"
             cfg["workload"] += ", Gram on the tensor cores (split-TF32)"
@@ -749,7 +795,9 @@ def run_gb300(args) -> None:
                             "while cube s is denoised",
                     "serial_value": round(e2e_serial, 1)},
             "gpu_launches": int(launches_per_step * args.steps),
-            "step_ms": step_stats,
+            "step_ms": step_stats if pipeline is None else None,
+            "latency": latency,
+            "pipeline": pipeline,
             "parity": parity,
             "forms": forms,
             "clocks": clocks.summary(),
@@ -919,6 +967,9 @@ def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--streams", type=int, default=3,
+                    help="cubes in flight for the headline (hyde_hyres_denoise_many); 1 = one "
+                         "cube at a time")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
     ap.add_argument("--cpu-cols", type=int, default=384,

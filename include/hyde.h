@@ -418,6 +418,25 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H,
                                 size_t fws_bytes, void* bws, size_t bws_bytes,
                                 cudaStream_t stream);
 
+/* ------------------------------------------------------ several cubes at once
+ * Denoises count independent cubes (Y[k] -> X[k], device pointers in host
+ * arrays; each cube as hyde_hyres_denoise with the same shape and params)
+ * over `slots` workspaces (1..16; ws[s], each hyde_workspace_size bytes,
+ * 256-byte aligned): cube k runs on slot_streams[k % slots] with ws[k % slots],
+ * so the cubes of different slots overlap on the GPU. Per cube, a third of
+ * the work is single-block (the noise inverse and the eigensolver) and leaves
+ * most SMs idle; another cube's bandwidth-bound stages fill them. The slot
+ * streams are forked from `stream` (events[0]) and joined back to it
+ * (events[1 + s]): work enqueued on `stream` afterwards sees every X[k].
+ * info: device array of count records, or NULL. Cubes of the same slot run
+ * in order on its stream. Asynchronous; no host synchronisation.
+ */
+hyde_status hyde_hyres_denoise_many(const float* const* Y, float* const* X, int count, int p,
+                                    int H, int W, const hyde_hyres_params* params,
+                                    hyde_hyres_info* info, void* const* ws, size_t ws_bytes,
+                                    int slots, cudaStream_t stream,
+                                    const cudaStream_t* slot_streams, const cudaEvent_t* events);
+
 /* ----------------------------------------------------------------- FORPDN
  * First-order spectral roughness penalty denoising (Sec. 2.1: a full-rank,
  * wavelet-based method for additive Gaussian noise; the paper states no

@@ -98,6 +98,9 @@ SIGNATURES = {
     "hyde_hyres_denoise_host": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int,
                                         ctypes.POINTER(HydeParams), c_vp, c_vp, c_vp, c_size,
                                         c_vp, c_vp, c_vp, c_vp]),
+    "hyde_hyres_denoise_many": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int,
+                                        ctypes.POINTER(HydeParams), c_vp, c_vp, c_size, c_int,
+                                        c_vp, c_vp, c_vp]),
 }
 
 N_STAGES = 8

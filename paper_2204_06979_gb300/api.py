@@ -325,6 +325,61 @@ class HyRes:
         )
 
 
+class HyResMany:
+    """Several cubes of one shape at once (``hyde_hyres_denoise_many``): ``slots``
+    workspaces, each with its own stream, forked from and joined to the
+    current stream; cube k runs in slot k % slots, so one cube's
+    single-block stages overlap another's bandwidth-bound ones."""
+
+    def __init__(self, p: int, H: int, W: int, levels: int, r_max: int, n_lambda: int = 64,
+                 slots: int = 3, device="cuda", precision: int = PREC_FP32):
+        self.lib = _lib.load()
+        self.shape = (p, H, W)
+        self.params = params(levels, r_max, n_lambda, precision)
+        sz = ctypes.c_size_t()
+        _check(self.lib.hyde_workspace_size(p, H, W, ctypes.byref(self.params), ctypes.byref(sz)),
+               "hyde_workspace_size")
+        self.device = torch.device(device)
+        self.slots = int(slots)
+        self.ws = [_workspace(sz.value, self.device) for _ in range(self.slots)]
+        self.ws_bytes = sz.value
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.slots)]
+        self.events = [torch.cuda.Event() for _ in range(self.slots + 1)]
+        cur = torch.cuda.current_stream(self.device)
+        for e in self.events:   # torch creates the CUDA event on first record
+            e.record(cur)
+        self.info = None
+
+    def __call__(self, Ys, Xs) -> None:
+        """Enqueues ``Ys[k] -> Xs[k]`` for every k on the current stream's
+        timeline (returns at once)."""
+        count = len(Ys)
+        if count != len(Xs) or count < 1:
+            raise ValueError("need as many outputs as inputs")
+        for Y, X in zip(Ys, Xs):
+            if tuple(Y.shape) != self.shape or tuple(X.shape) != self.shape:
+                raise ValueError("every cube must have the shape the plan was made for")
+            _cuda_f32(Y, "Y")
+            _cuda_f32(X, "X")
+        if self.info is None or self.info.numel() != count * INFO_BYTES:
+            self.info = torch.zeros(count * INFO_BYTES, dtype=torch.uint8, device=self.device)
+        p, H, W = self.shape
+        yp = (ctypes.c_void_p * count)(*[Y.data_ptr() for Y in Ys])
+        xp = (ctypes.c_void_p * count)(*[X.data_ptr() for X in Xs])
+        wp = (ctypes.c_void_p * self.slots)(*[w.data_ptr() for w in self.ws])
+        sp = (ctypes.c_void_p * self.slots)(*[s.cuda_stream for s in self.streams])
+        ep = (ctypes.c_void_p * (self.slots + 1))(*[e.cuda_event for e in self.events])
+        _check(self.lib.hyde_hyres_denoise_many(yp, xp, count, p, H, W, ctypes.byref(self.params),
+                                                self.info.data_ptr(), wp, self.ws_bytes,
+                                                self.slots, _stream(), sp, ep),
+               "hyde_hyres_denoise_many")
+
+    def result_info(self, k: int) -> dict:
+        """The info record of cube k of the last call (synchronises)."""
+        torch.cuda.current_stream(self.device).synchronize()
+        return parse_info(self.info[k * INFO_BYTES:(k + 1) * INFO_BYTES])
+
+
 def hyres_denoise(Y: torch.Tensor, levels: int, r_max: int, n_lambda: int = 64,
                   precision: int = PREC_FP32, lambda_mode: int = LAMBDA_SHARED,
                   threshold_ll: bool = False):

@@ -482,6 +482,38 @@ hyde_status hyde_hyres_denoise(const float* Y, float* X, int p, int H, int W,
     return hyres_enqueue(Y, X, p, H, W, params, info, ws, ws_bytes, stream, nullptr);
 }
 
+// ------------------------------------------------------- several cubes at once
+hyde_status hyde_hyres_denoise_many(const float* const* Y, float* const* X, int count, int p,
+                                    int H, int W, const hyde_hyres_params* params,
+                                    hyde_hyres_info* info, void* const* ws, size_t ws_bytes,
+                                    int slots, cudaStream_t stream,
+                                    const cudaStream_t* slot_streams, const cudaEvent_t* events) {
+    if (!Y || !X || !ws || !slot_streams || !events || !params) return HYDE_ERR_INVALID_ARG;
+    if (count < 1 || slots < 1 || slots > 16) return HYDE_ERR_INVALID_ARG;
+    for (int k = 0; k < count; ++k)
+        if (!Y[k] || !X[k] || Y[k] == X[k]) return HYDE_ERR_INVALID_ARG;
+    for (int s = 0; s < slots; ++s)
+        if (!ws[s] || !slot_streams[s] || !events[1 + s]) return HYDE_ERR_INVALID_ARG;
+    if (!events[0]) return HYDE_ERR_INVALID_ARG;
+    const int used = count < slots ? count : slots;
+    // fork the slot streams from the caller's stream
+    if (cudaEventRecord(events[0], stream) != cudaSuccess) return HYDE_ERR_CUDA;
+    for (int s = 0; s < used; ++s)
+        if (cudaStreamWaitEvent(slot_streams[s], events[0], 0) != cudaSuccess) return HYDE_ERR_CUDA;
+    for (int k = 0; k < count; ++k) {
+        const int s = k % slots;
+        const hyde_status st = hyres_enqueue(Y[k], X[k], p, H, W, params, info ? info + k : nullptr,
+                                             ws[s], ws_bytes, slot_streams[s], nullptr);
+        if (st != HYDE_OK) return st;
+    }
+    // join them back
+    for (int s = 0; s < used; ++s) {
+        if (cudaEventRecord(events[1 + s], slot_streams[s]) != cudaSuccess) return HYDE_ERR_CUDA;
+        if (cudaStreamWaitEvent(stream, events[1 + s], 0) != cudaSuccess) return HYDE_ERR_CUDA;
+    }
+    return HYDE_OK;
+}
+
 // ------------------------------------------------------------------ WSRRR
 static hyde_status wsrrr_check(const hyde_hyres_params* params) {
     if (!params) return HYDE_ERR_INVALID_ARG;
