@@ -550,6 +550,47 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
                                        int n_slots, cudaEvent_t* events,
                                        cudaStream_t stream);
 
+/* ----------------------------------------------- batched sliding windows
+ * The same form with one launch per stage over all windows (Sec. 2.2.2:
+ * the tiles of a large scene, each denoised on its own by HyRes, Sec. 2.1):
+ * the Gram matrices of all windows on the tensor cores (split-TF32, the
+ * windows read in place from the scene), a one-block Gauss-Jordan and
+ * eigensolver per window, the projection, the DWT, SURE and its selection,
+ * the thresholded inverse DWT and the back-projection of the cores, each a
+ * single launch over every window (13 kernels for the whole scene).
+ *
+ * Differences from hyde_hyres_denoise on the window's cube: sigma comes from
+ * the float Gauss-Jordan inverse without the FP64 Newton step (that step is
+ * p^3 double FMAs per window; its effect on a window's output is ~1e-5
+ * relative at p = 200), and only the shared-lambda mode with the LL band
+ * kept (lambda_mode HYDE_LAMBDA_SHARED, threshold_ll 0) and the FP32 or
+ * HYDE_PREC_TF32X3 precision (both the split-TF32 Gram) are supported.
+ *
+ * A plan holds the window table and the layout of the workspace. Create it
+ * once per table (host only; copies win), query its workspace size, and run
+ * it any number of times; every call first copies the plan's tables (held in
+ * page-locked host memory) into the workspace on `stream`, so a call can be
+ * captured into a CUDA graph and replayed while the plan lives. Limits:
+ * 1 <= p <= 208, W a multiple of 4, every window's x0 a multiple of 4 and
+ * its padded sides (multiples of 2^levels) shorter than twice its sides,
+ * at most 65535 windows; HYDE_ERR_SHAPE otherwise (hyde_hyres_denoise_windows
+ * takes any table). Y (16-byte aligned) and X: float[p][H][W] device, X may
+ * not alias Y; info (device, may be NULL): one record per window.
+ */
+typedef struct hyde_windows_plan_s* hyde_windows_plan;
+
+hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win,
+                                     int n_win, const hyde_hyres_params* params,
+                                     hyde_windows_plan* plan);
+hyde_status hyde_windows_plan_workspace_size(hyde_windows_plan plan, size_t* bytes);
+/* Kernels one hyde_hyres_denoise_windows_batched call launches (-1 if NULL). */
+int hyde_windows_plan_kernel_launches(hyde_windows_plan plan);
+hyde_status hyde_windows_plan_destroy(hyde_windows_plan plan);
+hyde_status hyde_hyres_denoise_windows_batched(const float* Y, float* X,
+                                               hyde_windows_plan plan,
+                                               hyde_hyres_info* info, void* ws,
+                                               size_t ws_bytes, cudaStream_t stream);
+
 /* Caps, for the calling host thread, the SM count that the launchers size
  * their grids from (0 removes the cap); returns the previous cap. For many
  * small pipelines on concurrent streams: multi-block kernels sized for

@@ -95,6 +95,12 @@ SIGNATURES = {
     "hyde_hyres_denoise_windows": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_vp, c_int,
                                            ctypes.POINTER(HydeParams), c_vp, c_vp, c_size, c_vp,
                                            c_int, c_vp, c_vp]),
+    "hyde_windows_plan_create": (c_int, [c_int, c_int, c_int, c_vp, c_int,
+                                         ctypes.POINTER(HydeParams), ctypes.POINTER(c_vp)]),
+    "hyde_windows_plan_workspace_size": (c_int, [c_vp, c_size_p]),
+    "hyde_windows_plan_kernel_launches": (c_int, [c_vp]),
+    "hyde_windows_plan_destroy": (c_int, [c_vp]),
+    "hyde_hyres_denoise_windows_batched": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "hyde_hyres_denoise_host": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int,
                                         ctypes.POINTER(HydeParams), c_vp, c_vp, c_vp, c_size,
                                         c_vp, c_vp, c_vp, c_vp]),

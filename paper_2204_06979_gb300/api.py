@@ -648,6 +648,69 @@ def hyres_sure_loss(Y: torch.Tensor, scale: torch.Tensor, model: HyResGrad) -> t
 
 # ------------------------------------------------------- sliding windows
 
+class HyResWindowsBatched:
+    """Sliding-window HyRes with one launch per stage over all windows
+    (``hyde_hyres_denoise_windows_batched``): a plan built once from the
+    window table (``int32[n][8]``, as for ``HyResWindows``), its workspace and
+    per-window info records. ``__call__`` enqueues the scene on the current
+    stream; ``capture``/``replay`` record it into a CUDA graph."""
+
+    def __init__(self, p, H, W, table, levels, r_max, n_lambda=64, device="cuda",
+                 precision: int = PREC_FP32):
+        from ._lib import HydeWindow
+        self.lib = _lib.load()
+        self.shape = (p, H, W)
+        self.params = params(levels, r_max, n_lambda, precision=precision)
+        self.device = torch.device(device)
+        rows = [tuple(int(v) for v in r) for r in table]
+        self.n_win = len(rows)
+        win = (HydeWindow * self.n_win)(*[HydeWindow(*r) for r in rows])
+        self.plan = ctypes.c_void_p()
+        _check(self.lib.hyde_windows_plan_create(p, H, W, win, self.n_win,
+                                                 ctypes.byref(self.params),
+                                                 ctypes.byref(self.plan)),
+               "hyde_windows_plan_create")
+        sz = ctypes.c_size_t()
+        _check(self.lib.hyde_windows_plan_workspace_size(self.plan, ctypes.byref(sz)),
+               "hyde_windows_plan_workspace_size")
+        self.ws = _workspace(sz.value, self.device)
+        self.info = torch.zeros(self.n_win * INFO_BYTES, dtype=torch.uint8, device=self.device)
+        self.kernel_launches = self.lib.hyde_windows_plan_kernel_launches(self.plan)
+        self.graph = None
+
+    def __del__(self):
+        plan = getattr(self, "plan", None)
+        if plan is not None and plan.value:
+            self.lib.hyde_windows_plan_destroy(plan)
+            self.plan = None
+
+    def __call__(self, Y: torch.Tensor, X: torch.Tensor | None = None) -> torch.Tensor:
+        Y = _cuda_f32(Y, "Y")
+        if tuple(Y.shape) != self.shape:
+            raise ValueError(f"expected a scene of shape {self.shape}")
+        if X is None:
+            X = torch.empty_like(Y)
+        _check(self.lib.hyde_hyres_denoise_windows_batched(
+            _ptr(Y), _ptr(X), self.plan, _ptr(self.info), _ptr(self.ws), self.ws.numel(),
+            _stream()), "hyde_hyres_denoise_windows_batched")
+        return X
+
+    def capture(self, Y: torch.Tensor, X: torch.Tensor) -> None:
+        """Record one scene denoise (reading Y, writing X) into a CUDA graph."""
+        self(Y, X)
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            self(Y, X)
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+    def infos(self) -> list[dict]:
+        raw = self.info.cpu()
+        return [parse_info(raw[k * INFO_BYTES:(k + 1) * INFO_BYTES]) for k in range(self.n_win)]
+
+
 class HyResWindows:
     """Sliding-window HyRes over a scene of fixed shape and window table
     (``int32[n][8]``: window y0, x0, h, w and core y0, x0, h, w). Owns the

@@ -63,6 +63,14 @@ __host__ __device__ inline EigWs eig_ws_carve(float* base, int p) {
     return w;
 }
 
+// Window blockIdx.y of a batched call: every workspace pointer moves by the
+// window's stride (floats); one-window launches have gridDim.y = 1.
+__device__ __forceinline__ EigWs eig_ws_window(EigWs w, long long off) {
+    w.refl += off; w.tau += off; w.d += off; w.e += off;
+    w.scale += off; w.lam += off; w.X += off;
+    return w;
+}
+
 // Barrier among warps 0..NW-1 only (named barrier 1); the other warps of the
 // block do not take part and wait at the next __syncthreads.
 template <int NW>
@@ -234,9 +242,16 @@ __device__ __forceinline__ void tri_sweep(int b0, float* A, int lda, int p, int 
 template <int NB, int NW>
 __global__ void __launch_bounds__(kLA, 1)
 eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p,
-                   EigWs G, int* status) {
+                   EigWs G, int* status, long long wst) {
     pdl_wait();
     pdl_trigger();
+    if (blockIdx.y) {
+        const int wi = blockIdx.y;
+        Ain += (long long)wi * p * p;
+        if (wsig) wsig += (long long)wi * p;
+        G = eig_ws_window(G, wi * wst);
+        if (status) status += wi;
+    }
     extern __shared__ float sm[];
     const int lda = p + 1;
     float* q = sm;
@@ -554,9 +569,16 @@ __device__ __forceinline__ float refl_entry(const float* refl, int p, const floa
 template <int NB>
 __global__ void __launch_bounds__(kRegThreads, 1)
 eig_tridiag_reg_kernel(const double* __restrict__ Ain, const double* __restrict__ wsig, int p,
-                       EigWs G, int* status) {
+                       EigWs G, int* status, long long wst) {
     pdl_wait();
     pdl_trigger();
+    if (blockIdx.y) {
+        const int wi = blockIdx.y;
+        Ain += (long long)wi * p * p;
+        if (wsig) wsig += (long long)wi * p;
+        G = eig_ws_window(G, wi * wst);
+        if (status) status += wi;
+    }
     constexpr int NA = 2 * NB;                 // rows per warp: i = wid + 16 a < 32 NB
     extern __shared__ float sm[];
     float* q = sm;
@@ -763,9 +785,13 @@ size_t eig_tridiag_reg_bytes(int p) { return ((size_t)p * p + 9 * (size_t)p) * s
 // --------------------------------------------------------------------------
 template <int NB>
 __global__ void __launch_bounds__(kPairThreads)
-eig_pair_kernel(EigWs G, int p, int* status) {
+eig_pair_kernel(EigWs G, int p, int* status, long long wst) {
     pdl_wait();
     pdl_trigger();
+    if (blockIdx.y) {
+        G = eig_ws_window(G, blockIdx.y * wst);
+        if (status) status += blockIdx.y;
+    }
     extern __shared__ float sm[];
     float* d = sm;
     float* e = d + p;
@@ -1034,9 +1060,16 @@ eig_pair_kernel(EigWs G, int p, int* status) {
 constexpr int kOrthThreads = 512;
 
 __global__ void __launch_bounds__(kOrthThreads, 1)
-eig_orth_kernel(EigWs G, int p, int r, double* __restrict__ evals, double* __restrict__ V) {
+eig_orth_kernel(EigWs G, int p, int r, double* __restrict__ evals, double* __restrict__ V,
+                long long wst) {
     pdl_wait();
     pdl_trigger();
+    if (blockIdx.y) {
+        const int wi = blockIdx.y;
+        G = eig_ws_window(G, wi * wst);
+        evals += (long long)wi * r;
+        V += (long long)wi * p * r;
+    }
     extern __shared__ float sm[];
     const int ldx = p | 1;
     float* X = sm;                // [r][ldx]
@@ -1135,18 +1168,20 @@ size_t eig_ws_bytes(int p, int r) {
 // shared-memory form above.
 template <int NB>
 hyde_status launch_tridiag(const double* A, const double* wsig, int p, EigWs G, int* status,
-                           cudaStream_t s) {
+                           int n_win, long long wst, cudaStream_t s) {
     if constexpr (NB <= kRegMaxNB) {
         const size_t sr = eig_tridiag_reg_bytes(p);
         if (ensure_smem_limit((const void*)eig_tridiag_reg_kernel<NB>, (int)sr) != cudaSuccess)
             return HYDE_ERR_SHAPE;
-        launch_pdl(eig_tridiag_reg_kernel<NB>, 1, kRegThreads, sr, s, A, wsig, p, G, status);
+        launch_pdl(eig_tridiag_reg_kernel<NB>, dim3(1, n_win), kRegThreads, sr, s, A, wsig, p, G,
+                   status, wst);
     } else {
         const size_t st = eig_tridiag_bytes(p);
         if (ensure_smem_limit((const void*)eig_tridiag_kernel<NB, kEigWarps>, (int)st) !=
             cudaSuccess)
             return HYDE_ERR_SHAPE;
-        launch_pdl(eig_tridiag_kernel<NB, kEigWarps>, 1, kLA, st, s, A, wsig, p, G, status);
+        launch_pdl(eig_tridiag_kernel<NB, kEigWarps>, dim3(1, n_win), kLA, st, s, A, wsig, p, G,
+                   status, wst);
     }
     return HYDE_OK;
 }
@@ -1157,20 +1192,27 @@ size_t eig_smem_bytes(int p, int r) {
     return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 
-hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, double* evals,
-                           double* V, void* ws, int* status, cudaStream_t s) {
-    if (r > 32 || r < 1 || r > p || p > 256 || p < 2 || !ws) return HYDE_ERR_SHAPE;
+// n_win windows (block row y = window): window w reads A + w p^2, wsig + w p,
+// the workspace at ws + w ws_stride bytes and writes evals + w r, V + w p r,
+// status + w.
+static hyde_status eig_top(const double* A, const double* wsig, int p, int r, double* evals,
+                           double* V, void* ws, size_t ws_stride, int* status, int n_win,
+                           cudaStream_t s) {
+    if (r > 32 || r < 1 || r > p || p > 256 || p < 2 || !ws || n_win < 1 || n_win > 65535)
+        return HYDE_ERR_SHAPE;
     if (eig_smem_bytes(p, r) > 227 * 1024) return HYDE_ERR_SHAPE;
+    if (n_win > 1 && (ws_stride % 16) != 0) return HYDE_ERR_SHAPE;
+    const long long wst = (long long)(ws_stride / sizeof(float));
     const EigWs G = eig_ws_carve(reinterpret_cast<float*>(ws), p);
     const size_t sp = eig_pair_bytes(p), so = (size_t)r * (p | 1) * sizeof(float);
     const int NB = (p + 31) / 32;
     switch (NB) {
 #define HYDE_EIG(NBV)                                                                              \
     case NBV:                                                                                      \
-        if (launch_tridiag<NBV>(A, wsig, p, G, status, s) != HYDE_OK ||                           \
+        if (launch_tridiag<NBV>(A, wsig, p, G, status, n_win, wst, s) != HYDE_OK ||               \
             ensure_smem_limit((const void*)eig_pair_kernel<NBV>, (int)sp) != cudaSuccess)          \
             return HYDE_ERR_SHAPE;                                                                 \
-        launch_pdl(eig_pair_kernel<NBV>, r, kPairThreads, sp, s, G, p, status);                   \
+        launch_pdl(eig_pair_kernel<NBV>, dim3(r, n_win), kPairThreads, sp, s, G, p, status, wst); \
         break;
         HYDE_EIG(1) HYDE_EIG(2) HYDE_EIG(3) HYDE_EIG(4)
         HYDE_EIG(5) HYDE_EIG(6) HYDE_EIG(7) HYDE_EIG(8)
@@ -1179,8 +1221,19 @@ hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, do
     }
     if (ensure_smem_limit((const void*)eig_orth_kernel, (int)so) != cudaSuccess)
         return HYDE_ERR_SHAPE;
-    launch_pdl(eig_orth_kernel, 1, kOrthThreads, so, s, G, p, r, evals, V);
+    launch_pdl(eig_orth_kernel, dim3(1, n_win), kOrthThreads, so, s, G, p, r, evals, V, wst);
     return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_eig_top(const double* A, const double* wsig, int p, int r, double* evals,
+                           double* V, void* ws, int* status, cudaStream_t s) {
+    return eig_top(A, wsig, p, r, evals, V, ws, 0, status, 1, s);
+}
+
+hyde_status launch_eig_top_batched(const double* A, const double* wsig, int p, int r,
+                                   double* evals, double* V, void* ws, size_t ws_stride,
+                                   int* status, int n_win, cudaStream_t s) {
+    return eig_top(A, wsig, p, r, evals, V, ws, ws_stride, status, n_win, s);
 }
 
 }  // namespace hyde

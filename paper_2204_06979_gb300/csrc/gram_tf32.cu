@@ -39,6 +39,7 @@
 
 #include "hyde_internal.cuh"
 #include "tc_common.cuh"
+#include "tmap.cuh"
 
 namespace hyde {
 namespace {
@@ -373,28 +374,6 @@ gram_tf32_reduce_kernel(const float* __restrict__ partials, int nblocks, int p,
     }
 }
 
-// cuTensorMapEncodeTiled from the driver through the runtime (no link
-// against the driver library); looked up once.
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(f);
-    }
-    return fn;
-}
-
 bool t32_plan(int p, long long n, T32Plan* out) {
     if (p < 4 || p > kMaxP || (p & 3) != 0 || n < 1 || 4 * n > 0x7fffffffLL) return false;
     T32Plan P = {};
@@ -425,6 +404,23 @@ bool t32_plan(int p, long long n, T32Plan* out) {
 }
 
 }  // namespace
+
+// cuTensorMapEncodeTiled from the driver through the runtime (no link
+// against the driver library); looked up once.
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
 
 bool gram_tf32_shape_ok(int p, long long n) {
     T32Plan P;

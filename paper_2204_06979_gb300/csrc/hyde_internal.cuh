@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <utility>
+#include <vector>
 
 #include "../../include/hyde.h"
 
@@ -305,6 +306,79 @@ hyde_status launch_gather_window(const float* Y, int H, int W, int y0, int x0, i
 hyde_status launch_scatter_core(const float* cube, int h, int w, int y0, int x0, int cy0,
                                 int cx0, int ch, int cw, int p, int H, int W, float* X,
                                 cudaStream_t s);
+
+// ------------------------------------------- batched sliding windows
+// One window of a batched call as its kernels see it (a device table). The
+// window's r_max component images (padded Hp x Wp) start at float offset
+// `img` of the component and coefficient buffers, its DWT scratch at `scr`.
+struct WinDesc {
+    int y0, x0, h, w;         // window in scene pixels
+    int cy0, cx0, ch, cw;     // its core, in scene pixels
+    int Hp, Wp;               // padded component images
+    int sh, pad_;             // SURE fixed-point unit 2^-sh
+    long long img;
+    long long scr;
+    double delta;             // SURE grid step sqrt(2 ln N) / (K - 1), N = Hp Wp
+};
+
+// Floats of DWT scratch per component image of N = Hp Wp values (the LL
+// bands of two consecutive levels, rounded to 16 bytes).
+__host__ __device__ inline long long win_scratch_stride(long long N) {
+    return (N / 4 + N / 16 + 3) & ~3LL;
+}
+
+// Pieces of the window Gram matrices: CTA g of the tensor-core kernel takes
+// pieces[pbeg[g] .. pbeg[g + 1]) = (window, first chunk, end chunk, partial
+// slot); window w's partials are slots wslot0[w] .. wslot0[w + 1] (role 0,
+// rows < 128) and wslot1 (role 1, bands >= 128, p > 128 only).
+struct WinGramLayout {
+    int G0, G1, nslot0, nslot1;
+    size_t part0_floats, part1_floats;
+    std::vector<int4> pieces;
+    std::vector<int> pbeg, wslot0, wslot1;
+};
+// geo[w] = (y0, x0, h, w); every x0 must be a multiple of 4
+bool win_gram_supported(int p, int W, const float* Y);
+hyde_status win_gram_layout(int p, const int4* geo, int n_win, int sms, WinGramLayout* L);
+hyde_status launch_win_gram(const float* Y, int p, int H, int W, const int4* pieces,
+                            const int* pbeg, const int4* geo, const int* wslot0,
+                            const int* wslot1, int n_win, int G0, int G1, float* part0,
+                            float* part1, double* R, int* status, cudaStream_t s);
+// Noise levels of every window from its Gram matrix (R [n_win][p][p]): the
+// float Gauss-Jordan inverse of the scaled matrix, sigma_b^2 = S_b^2 /
+// (n_w [As^-1]_bb); scratch Ainv float [n_win][p][p], S double [n_win][p].
+hyde_status launch_win_noise(const double* R, int p, int n_win, const WinDesc* desc,
+                             double* sigma, float* Ainv, double* S, int* status,
+                             cudaStream_t s);
+// Leading eigenpairs of every window's whitened Gram matrix (strides: one
+// window's R, sigma, eigensolver workspace, evals, V, status).
+hyde_status launch_eig_top_batched(const double* A, const double* wsig, int p, int r,
+                                   double* evals, double* V, void* ws, size_t ws_stride,
+                                   int* status, int n_win, cudaStream_t s);
+hyde_status launch_weights_batched(const double* V, const double* sigma, int p, int r, int ldw,
+                                   float* P, float* Q, int n_win, cudaStream_t s);
+// The stages after the weights (windows_batched.cu): projection into the
+// padded component images, DWT, SURE tables and selection, thresholded
+// inverse DWT, back-projection of the cores into X.
+// tstart[w] .. tstart[w + 1]: window w's tiles of kWinProjTile padded pixels
+// (projection) or kWinBackTile core pixels (back-projection), n_tiles in all.
+constexpr int kWinProjTile = 2048;
+constexpr int kWinBackTile = 2048;
+hyde_status launch_win_project(const float* Y, int p, int H, int W, const WinDesc* desc,
+                               const int* tstart, int n_win, int n_tiles, const float* P, int r,
+                               int ldw, float* Zp, cudaStream_t s);
+hyde_status launch_win_dwt(const float* Zp, float* coef, float* scratch, const WinDesc* desc,
+                           int n_win, int r, int levels, cudaStream_t s);
+hyde_status launch_win_sure(const float* coef, const WinDesc* desc, int n_win, int r,
+                            int levels, int K, unsigned int* counts, double* sums,
+                            double* sum_all, int* rank, double* lam, hyde_hyres_info* info,
+                            int* status, cudaStream_t s);
+hyde_status launch_win_idwt(const float* coef, float* Zh, float* scratch, const WinDesc* desc,
+                            int n_win, int r, int levels, const int* rank, const double* lam,
+                            cudaStream_t s);
+hyde_status launch_win_backproject(const float* Zh, const WinDesc* desc, const int* tstart,
+                                   int n_win, int n_tiles, const float* Q, int p, int ldw,
+                                   const int* rank, int H, int W, float* X, cudaStream_t s);
 
 // ----------------------------------------------------------------- SURE
 struct SureBufs {

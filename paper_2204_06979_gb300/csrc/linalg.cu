@@ -259,12 +259,50 @@ __global__ void weights_kernel(const double* __restrict__ V, const double* __res
                                float* __restrict__ Q) {
     pdl_wait();
     pdl_trigger();
+    // window blockIdx.y of a batched call (one window: gridDim.y = 1)
+    const int wi = blockIdx.y;
+    V += (long long)wi * p * r;
+    sigma += (long long)wi * p;
+    P += (long long)wi * p * ldw;
+    Q += (long long)wi * p * ldw;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * ldw;
          e += gridDim.x * blockDim.x) {
         int b = e / ldw, i = e % ldw;
         double v = i < r ? V[(long long)b * r + i] : 0.0;
         P[e] = (float)(v / sigma[b]);
         Q[e] = (float)(v * sigma[b]);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Noise levels of the windows of a batched sliding-window call, one window
+// per block: the register Gauss-Jordan inverse of the window's scaled Gram
+// matrix, then sigma_b = S_b / sqrt(n_w [As^-1]_bb) (n_w the window's
+// pixels) straight from the float inverse. The FP64 Newton step of the
+// one-cube path costs p^3 double FMAs per window, which over hundreds of
+// windows would take longer than the whole batched call; without it sigma
+// carries the float inverse's error (~1e-5 relative at p = 200).
+// --------------------------------------------------------------------------
+template <int T, int G>
+__global__ void __launch_bounds__(G * G, 1)
+win_noise_kernel(const double* __restrict__ R, int p, const WinDesc* __restrict__ desc,
+                 double* __restrict__ sigma, float* __restrict__ Ainv, double* __restrict__ S,
+                 int* status) {
+    const int w = blockIdx.x;
+    const long long pp = (long long)p * p;
+    float* Aw = Ainv + w * pp;
+    double* Sw = S + (long long)w * p;
+    noise_gj_reg_body<T, G>(R + w * pp, p, Aw, Sw, status + w);
+    __syncthreads();   // the block's global writes of Aw and Sw are visible to it
+    const double n = (double)desc[w].h * (double)desc[w].w;
+    for (int b = threadIdx.x; b < p; b += G * G) {
+        const double a = (double)Aw[(long long)b * p + b];
+        double s2 = Sw[b] * Sw[b] / (n * a);
+        if (!(a > 0.0) || !isfinite(s2) || !(s2 > 0.0)) {
+            set_status(status + w, HYDE_ERR_NUMERIC);
+            s2 = 1.0;
+        }
+        sigma[(long long)w * p + b] = sqrt(s2);
     }
 }
 
@@ -379,6 +417,33 @@ hyde_status launch_inverse_from_gram(const double* R, int p, void* ws, double* Q
     if (st != HYDE_OK) return st;
     launch_pdl(inverse_refine_kernel, p, 256, 3 * p * sizeof(double), s, R, Ainv, Sd, p, Q,
                status);
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_win_noise(const double* R, int p, int n_win, const WinDesc* desc,
+                             double* sigma, float* Ainv, double* S, int* status,
+                             cudaStream_t s) {
+    if (p < 1 || p > kGjRegMax || n_win < 1) return HYDE_ERR_SHAPE;
+    switch ((p + 15) / 16) {
+#define HYDE_WGJ(TV)                                                                            \
+    case TV:                                                                                    \
+        launch_pdl(win_noise_kernel<TV, 16>, n_win, 256, 0, s, R, p, desc, sigma, Ainv, S,      \
+                   status);                                                                     \
+        break;
+        HYDE_WGJ(1) HYDE_WGJ(2) HYDE_WGJ(3) HYDE_WGJ(4) HYDE_WGJ(5)
+        HYDE_WGJ(6) HYDE_WGJ(7) HYDE_WGJ(8) HYDE_WGJ(9) HYDE_WGJ(10)
+        HYDE_WGJ(11) HYDE_WGJ(12) HYDE_WGJ(13)
+#undef HYDE_WGJ
+        default: return HYDE_ERR_SHAPE;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_weights_batched(const double* V, const double* sigma, int p, int r, int ldw,
+                                   float* P, float* Q, int n_win, cudaStream_t s) {
+    int tot = p * ldw;
+    launch_pdl(weights_kernel, dim3((tot + 255) / 256, n_win), 256, 0, s, V, sigma, p, r, ldw,
+               P, Q);
     return cuda_status(cudaGetLastError());
 }
 

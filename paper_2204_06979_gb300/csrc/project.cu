@@ -183,6 +183,154 @@ backproject_kernel(const float* __restrict__ Zh, long long n, const float* __res
     }
 }
 
+// --------------------------------------------------------------------------
+// Batched sliding windows: one block per tile of one window (the window of
+// tile t is found by bisection of the tile table), the window's weights in
+// shared memory, the window read in place from the scene (row stride W, band
+// stride H W).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int window_of_tile(const int* __restrict__ tstart, int n_win, int t) {
+    int lo = 0, hi = n_win;   // tstart[lo] <= t < tstart[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(tstart + mid) <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Padded component images of a window: Zp[img + i Hp Wp + y Wp + x] for
+// i < r, with whole-sample reflection of the window at its bottom and right.
+template <int RM>
+__global__ void __launch_bounds__(kThreads)
+win_project_kernel(const float* __restrict__ Y, int p, int H, int W,
+                   const WinDesc* __restrict__ desc, const int* __restrict__ tstart, int n_win,
+                   const float* __restrict__ P, int r, float* __restrict__ Zp) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ float4 Ps4[];
+    float* Ps = reinterpret_cast<float*>(Ps4);
+    const int t = blockIdx.x;
+    const int wi = window_of_tile(tstart, n_win, t);
+    const WinDesc d = desc[wi];
+    const float* Pw = P + (long long)wi * p * RM;
+    for (int e = threadIdx.x; e < p * RM; e += kThreads) Ps[e] = Pw[e];
+    __syncthreads();
+    const int N = d.Hp * d.Wp;
+    const long long bs = (long long)H * W;
+    const float* Yw = Y + (long long)d.y0 * W + d.x0;
+    float* Zw = Zp + d.img;
+    const int t0 = (t - __ldg(tstart + wi)) * kWinProjTile;
+    const int t1 = min(t0 + kWinProjTile, N);
+    for (int base = t0; base < t1; base += kThreads * kPix) {
+        int src[kPix];
+        bool live[kPix];
+#pragma unroll
+        for (int u = 0; u < kPix; ++u) {
+            const int pix = base + threadIdx.x + u * kThreads;
+            live[u] = pix < t1;
+            int y = live[u] ? pix / d.Wp : 0;
+            int x = live[u] ? pix - y * d.Wp : 0;
+            if (y >= d.h) y = 2 * d.h - 2 - y;
+            if (x >= d.w) x = 2 * d.w - 2 - x;
+            src[u] = y * W + x;
+        }
+        float acc[kPix][RM];
+#pragma unroll
+        for (int u = 0; u < kPix; ++u)
+#pragma unroll
+            for (int i = 0; i < RM; ++i) acc[u][i] = 0.f;
+        int b = 0;
+        for (; b + kBandGroup <= p; b += kBandGroup) {
+            float v[kBandGroup][kPix];
+#pragma unroll
+            for (int g = 0; g < kBandGroup; ++g)
+#pragma unroll
+                for (int u = 0; u < kPix; ++u)
+                    v[g][u] = __ldg(Yw + (long long)(b + g) * bs + src[u]);
+#pragma unroll
+            for (int g = 0; g < kBandGroup; ++g)
+                project_fma<RM>(acc, v[g], Ps4 + (b + g) * (RM / 4));
+        }
+        for (; b < p; ++b) {
+            float vt[kPix];
+#pragma unroll
+            for (int u = 0; u < kPix; ++u) vt[u] = __ldg(Yw + (long long)b * bs + src[u]);
+            project_fma<RM>(acc, vt, Ps4 + b * (RM / 4));
+        }
+#pragma unroll
+        for (int u = 0; u < kPix; ++u) {
+            if (!live[u]) continue;
+            const int pix = base + threadIdx.x + u * kThreads;
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+                if (i < r) Zw[(long long)i * N + pix] = acc[u][i];
+        }
+    }
+}
+
+// X at the window's core pixels: X_b = sum_{i < r*} Q[b][i] Zh_i, Zh the
+// window's synthesised component images (Hp x Wp, window coordinates).
+template <int R, int RM>
+__device__ __forceinline__ void win_backproject_pixel(const float* __restrict__ Zh, int N, int zpix,
+                                                      const float4* __restrict__ Qs4, int p, int r,
+                                                      long long bs, float* __restrict__ X) {
+    float z[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) z[i] = (i < r) ? __ldg(Zh + (long long)i * N + zpix) : 0.f;
+    for (int b = 0; b < p; ++b) {
+        const float4* w4 = Qs4 + b * (RM / 4);
+        float x = 0.f;
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q) {
+            const float4 w = w4[q];
+            x = fmaf(z[4 * q + 0], w.x, x);
+            x = fmaf(z[4 * q + 1], w.y, x);
+            x = fmaf(z[4 * q + 2], w.z, x);
+            x = fmaf(z[4 * q + 3], w.w, x);
+        }
+        X[(long long)b * bs] = x;
+    }
+}
+
+template <int RM>
+__global__ void __launch_bounds__(kBpThreads)
+win_backproject_kernel(const float* __restrict__ Zh, const WinDesc* __restrict__ desc,
+                       const int* __restrict__ tstart, int n_win, const float* __restrict__ Q,
+                       int p, const int* __restrict__ rank, int H, int W,
+                       float* __restrict__ X) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ float4 Qs4[];
+    float* Qs = reinterpret_cast<float*>(Qs4);
+    const int t = blockIdx.x;
+    const int wi = window_of_tile(tstart, n_win, t);
+    const WinDesc d = desc[wi];
+    const float* Qw = Q + (long long)wi * p * RM;
+    for (int e = threadIdx.x; e < p * RM; e += kBpThreads) Qs[e] = Qw[e];
+    __syncthreads();
+    const int r = min(rank[wi], RM);
+    const int groups = (r + 3) / 4;
+    const int N = d.Hp * d.Wp, n = d.ch * d.cw;
+    const long long bs = (long long)H * W;
+    const float* Zw = Zh + d.img;
+    const int t0 = (t - __ldg(tstart + wi)) * kWinBackTile;
+    const int t1 = min(t0 + kWinBackTile, n);
+    for (int c = t0 + threadIdx.x; c < t1; c += kBpThreads) {
+        const int yy = c / d.cw, xx = c - yy * d.cw;
+        const int zpix = (d.cy0 - d.y0 + yy) * d.Wp + (d.cx0 - d.x0 + xx);
+        float* Xp = X + (long long)(d.cy0 + yy) * W + (d.cx0 + xx);
+        switch (groups) {
+#define HYDE_WBP_CASE(G) \
+    case G: if (4 * G <= RM) win_backproject_pixel<4 * G, RM>(Zw, N, zpix, Qs4, p, r, bs, Xp); break;
+            HYDE_WBP_CASE(1) HYDE_WBP_CASE(2) HYDE_WBP_CASE(3) HYDE_WBP_CASE(4)
+            HYDE_WBP_CASE(5) HYDE_WBP_CASE(6) HYDE_WBP_CASE(7) HYDE_WBP_CASE(8)
+#undef HYDE_WBP_CASE
+            default: break;
+        }
+    }
+}
+
 // Grid of a grid-stride kernel: the blocks that fit on the device at once
 // (occupancy of this kernel at this shared-memory size), fewer if the work
 // has fewer tiles; small tiles (256 pixels) keep the last wave short.
@@ -240,6 +388,49 @@ hyde_status launch_backproject(const float* Zh, long long n, const float* Q, int
         HYDE_BACK(4) HYDE_BACK(8) HYDE_BACK(12) HYDE_BACK(16)
         HYDE_BACK(20) HYDE_BACK(24) HYDE_BACK(28) HYDE_BACK(32)
 #undef HYDE_BACK
+        default: return HYDE_ERR_INVALID_ARG;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_win_project(const float* Y, int p, int H, int W, const WinDesc* desc,
+                               const int* tstart, int n_win, int n_tiles, const float* P, int r,
+                               int ldw, float* Zp, cudaStream_t s) {
+    const size_t smem = (size_t)p * ldw * sizeof(float);
+    if (smem > 227 * 1024 || n_tiles < 1) return HYDE_ERR_SHAPE;
+    switch (ldw) {
+#define HYDE_WPROJ(RMV)                                                                         \
+    case RMV:                                                                                   \
+        if (ensure_smem_limit((const void*)win_project_kernel<RMV>, (int)smem) != cudaSuccess)  \
+            return HYDE_ERR_CUDA;                                                               \
+        launch_pdl(win_project_kernel<RMV>, n_tiles, kThreads, smem, s, Y, p, H, W, desc, tstart, \
+                   n_win, P, r, Zp);                                                            \
+        break;
+        HYDE_WPROJ(4) HYDE_WPROJ(8) HYDE_WPROJ(12) HYDE_WPROJ(16)
+        HYDE_WPROJ(20) HYDE_WPROJ(24) HYDE_WPROJ(28) HYDE_WPROJ(32)
+#undef HYDE_WPROJ
+        default: return HYDE_ERR_INVALID_ARG;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+hyde_status launch_win_backproject(const float* Zh, const WinDesc* desc, const int* tstart,
+                                   int n_win, int n_tiles, const float* Q, int p, int ldw,
+                                   const int* rank, int H, int W, float* X, cudaStream_t s) {
+    const size_t smem = (size_t)p * ldw * sizeof(float);
+    if (smem > 227 * 1024 || n_tiles < 1) return HYDE_ERR_SHAPE;
+    switch (ldw) {
+#define HYDE_WBACK(RMV)                                                                         \
+    case RMV:                                                                                   \
+        if (ensure_smem_limit((const void*)win_backproject_kernel<RMV>, (int)smem) !=           \
+            cudaSuccess)                                                                        \
+            return HYDE_ERR_CUDA;                                                               \
+        launch_pdl(win_backproject_kernel<RMV>, n_tiles, kBpThreads, smem, s, Zh, desc, tstart, \
+                   n_win, Q, p, rank, H, W, X);                                                 \
+        break;
+        HYDE_WBACK(4) HYDE_WBACK(8) HYDE_WBACK(12) HYDE_WBACK(16)
+        HYDE_WBACK(20) HYDE_WBACK(24) HYDE_WBACK(28) HYDE_WBACK(32)
+#undef HYDE_WBACK
         default: return HYDE_ERR_INVALID_ARG;
     }
     return cuda_status(cudaGetLastError());

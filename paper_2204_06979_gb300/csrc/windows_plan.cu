@@ -1,0 +1,249 @@
+// Plan and entry point of the batched sliding-window form (arXiv 2204.06979:
+// the tiles of a large scene each denoised by HyRes, Sec. 2.2.2 and 2.1).
+//
+// The plan turns the host window table into device tables (one WinDesc per
+// window, the Gram pieces, the tile tables of the projections) and a
+// workspace layout. It keeps the tables in page-locked host memory; each call
+// copies them into the workspace on the caller's stream and then launches
+// every stage once over all windows, so that a call is one capturable
+// sequence of 13 kernels whatever the number of windows.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "hyde_internal.cuh"
+
+using namespace hyde;
+
+struct hyde_windows_plan_s {
+    int p, H, W, n_win, r, L, K, RM;
+    int G0, G1, proj_tiles, back_tiles;
+    void* host;              // page-locked copy of the tables
+    size_t tables;           // their bytes (the head of the workspace)
+    // workspace offsets
+    size_t desc, geo, pieces, pbeg, wslot0, wslot1, tproj, tback;
+    size_t status, R, sigma, Ainv, S, eig, eig_stride, evals, V, P, Q;
+    size_t zp, coef, scr, counts, sums, sum_all, rank, lam, part0, part1, total;
+};
+
+namespace {
+
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off += align_up(bytes, kAlign);
+        return o;
+    }
+};
+
+hyde_status window_ok(const hyde_window& wn, int H, int W) {
+    if (wn.h < 1 || wn.w < 1 || wn.y0 < 0 || wn.x0 < 0 || wn.y0 + wn.h > H || wn.x0 + wn.w > W)
+        return HYDE_ERR_SHAPE;
+    if (wn.ch < 1 || wn.cw < 1 || wn.cy0 < wn.y0 || wn.cx0 < wn.x0 ||
+        wn.cy0 + wn.ch > wn.y0 + wn.h || wn.cx0 + wn.cw > wn.x0 + wn.w)
+        return HYDE_ERR_SHAPE;
+    return HYDE_OK;
+}
+
+// Fixed-point unit 2^-sh of the window SURE histogram: rn(c^2 2^sh) < 2^22
+// for every binned coefficient (|c| <= (K - 1) delta, with margin), and one
+// lane column (N / 32 values in a block over N coefficients) below 2^32.
+bool sure_shift(long long N, int K, double delta, int* sh_out) {
+    const float inv_delta = (float)(1.0 / delta);
+    const double q = (K - 1) / (double)inv_delta;
+    const double c2max = q * q * 1.001 + 1e-300;
+    const double per_col = (double)((N + 31) / 32);
+    for (int sh = 16; sh >= 0; --sh) {
+        const double sc = ldexp(1.0, sh);
+        if (c2max * sc >= 4194304.0) continue;
+        const double qmax = floor(c2max * sc) + 1.0;
+        if (qmax * per_col < 4294967295.0) {
+            *sh_out = sh;
+            return true;
+        }
+    }
+    return false;
+}
+
+template <typename T>
+T* at(void* base, size_t off) {
+    return reinterpret_cast<T*>(reinterpret_cast<char*>(base) + off);
+}
+
+}  // namespace
+
+extern "C" {
+
+hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win, int n_win,
+                                     const hyde_hyres_params* params, hyde_windows_plan* out) {
+    if (!win || !params || !out || n_win < 1) return HYDE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (params->wavelet != 2 || params->levels < 1 || params->levels > kMaxLevels ||
+        params->r_max < 1 || params->r_max > kMaxRank || params->r_max > p ||
+        params->n_lambda < 2 || params->n_lambda > 256)
+        return HYDE_ERR_INVALID_ARG;
+    if ((params->precision != HYDE_PREC_FP32 && params->precision != HYDE_PREC_TF32X3) ||
+        params->lambda_mode != HYDE_LAMBDA_SHARED || params->threshold_ll != 0)
+        return HYDE_ERR_INVALID_ARG;
+    if (n_win > 65535 || p < 1 || p > 208 || H < 1 || W < 1 || (W % 4) != 0)
+        return HYDE_ERR_SHAPE;
+    const int r = params->r_max, L = params->levels, K = params->n_lambda;
+    std::vector<WinDesc> D(n_win);
+    std::vector<int4> geo(n_win);
+    std::vector<int> tproj(n_win + 1, 0), tback(n_win + 1, 0);
+    long long img = 0, scr = 0;
+    for (int k = 0; k < n_win; ++k) {
+        const hyde_window& wn = win[k];
+        hyde_status st = window_ok(wn, H, W);
+        if (st != HYDE_OK) return st;
+        int Hp, Wp;
+        if ((wn.x0 % 4) != 0 || !padded_dims(wn.h, wn.w, L, &Hp, &Wp)) return HYDE_ERR_SHAPE;
+        const long long N = (long long)Hp * Wp;
+        if (N > (1LL << 30)) return HYDE_ERR_SHAPE;
+        WinDesc d = {};
+        d.y0 = wn.y0; d.x0 = wn.x0; d.h = wn.h; d.w = wn.w;
+        d.cy0 = wn.cy0; d.cx0 = wn.cx0; d.ch = wn.ch; d.cw = wn.cw;
+        d.Hp = Hp; d.Wp = Wp;
+        d.img = img;
+        d.scr = scr;
+        d.delta = sqrt(2.0 * log((double)N)) / (K - 1);
+        if (!sure_shift(N, K, d.delta, &d.sh)) return HYDE_ERR_SHAPE;
+        img += (long long)align_up((size_t)(r * N), 64);
+        scr += (long long)align_up((size_t)(r * win_scratch_stride(N)), 64);
+        D[k] = d;
+        geo[k] = make_int4(wn.y0, wn.x0, wn.h, wn.w);
+        tproj[k + 1] = tproj[k] + (int)((N + kWinProjTile - 1) / kWinProjTile);
+        tback[k + 1] =
+            tback[k] + (int)(((long long)wn.ch * wn.cw + kWinBackTile - 1) / kWinBackTile);
+    }
+    const int sms = device_sm_count();
+    if (sms <= 0) return HYDE_ERR_CUDA;
+    WinGramLayout G;
+    hyde_status st = win_gram_layout(p, geo.data(), n_win, sms, &G);
+    if (st != HYDE_OK) return st;
+
+    hyde_windows_plan_s* P = new hyde_windows_plan_s();
+    P->p = p; P->H = H; P->W = W; P->n_win = n_win; P->r = r; P->L = L; P->K = K;
+    P->RM = (r + 3) / 4 * 4;
+    P->G0 = G.G0; P->G1 = G.G1;
+    P->proj_tiles = tproj[n_win];
+    P->back_tiles = tback[n_win];
+    const size_t n = (size_t)n_win, pp = (size_t)p * p;
+    Carve c;
+    P->desc = c.take(n * sizeof(WinDesc));
+    P->geo = c.take(n * sizeof(int4));
+    P->pieces = c.take(G.pieces.size() * sizeof(int4));
+    P->pbeg = c.take(G.pbeg.size() * sizeof(int));
+    P->wslot0 = c.take((n + 1) * sizeof(int));
+    P->wslot1 = c.take((n + 1) * sizeof(int));
+    P->tproj = c.take((n + 1) * sizeof(int));
+    P->tback = c.take((n + 1) * sizeof(int));
+    P->tables = c.off;
+    P->status = c.take((n + 1) * sizeof(int));
+    P->R = c.take(n * pp * sizeof(double));
+    P->sigma = c.take(n * p * sizeof(double));
+    P->Ainv = c.take(n * pp * sizeof(float));
+    P->S = c.take(n * p * sizeof(double));
+    P->eig_stride = align_up(eig_ws_bytes(p, r), kAlign);
+    P->eig = c.take(n * P->eig_stride);
+    P->evals = c.take(n * r * sizeof(double));
+    P->V = c.take(n * p * r * sizeof(double));
+    P->P = c.take(n * p * P->RM * sizeof(float));
+    P->Q = c.take(n * p * P->RM * sizeof(float));
+    P->zp = c.take((size_t)img * sizeof(float));
+    P->coef = c.take((size_t)img * sizeof(float));
+    P->scr = c.take((size_t)(scr > 0 ? scr : 4) * sizeof(float));
+    P->counts = c.take(n * r * K * sizeof(unsigned int));
+    P->sums = c.take(n * r * K * sizeof(double));
+    P->sum_all = c.take(n * r * sizeof(double));
+    P->rank = c.take(n * sizeof(int));
+    P->lam = c.take(n * sizeof(double));
+    P->part0 = c.take((G.part0_floats > 0 ? G.part0_floats : 4) * sizeof(float));
+    P->part1 = c.take((G.part1_floats > 0 ? G.part1_floats : 4) * sizeof(float));
+    P->total = c.off;
+
+    if (cudaMallocHost(&P->host, P->tables) != cudaSuccess) {
+        delete P;
+        return HYDE_ERR_CUDA;
+    }
+    memset(P->host, 0, P->tables);
+    memcpy(at<char>(P->host, P->desc), D.data(), n * sizeof(WinDesc));
+    memcpy(at<char>(P->host, P->geo), geo.data(), n * sizeof(int4));
+    if (!G.pieces.empty())
+        memcpy(at<char>(P->host, P->pieces), G.pieces.data(), G.pieces.size() * sizeof(int4));
+    memcpy(at<char>(P->host, P->pbeg), G.pbeg.data(), G.pbeg.size() * sizeof(int));
+    memcpy(at<char>(P->host, P->wslot0), G.wslot0.data(), (n + 1) * sizeof(int));
+    memcpy(at<char>(P->host, P->wslot1), G.wslot1.data(), (n + 1) * sizeof(int));
+    memcpy(at<char>(P->host, P->tproj), tproj.data(), (n + 1) * sizeof(int));
+    memcpy(at<char>(P->host, P->tback), tback.data(), (n + 1) * sizeof(int));
+    *out = P;
+    return HYDE_OK;
+}
+
+hyde_status hyde_windows_plan_workspace_size(hyde_windows_plan plan, size_t* bytes) {
+    if (!plan || !bytes) return HYDE_ERR_INVALID_ARG;
+    *bytes = plan->total;
+    return HYDE_OK;
+}
+
+int hyde_windows_plan_kernel_launches(hyde_windows_plan plan) {
+    // Gram 2, noise 1, eigensolver 3, weights 1, projection 1, DWT 1,
+    // SURE 2, inverse DWT 1, back-projection 1
+    return plan ? 13 : -1;
+}
+
+hyde_status hyde_windows_plan_destroy(hyde_windows_plan plan) {
+    if (!plan) return HYDE_ERR_INVALID_ARG;
+    if (plan->host) cudaFreeHost(plan->host);
+    delete plan;
+    return HYDE_OK;
+}
+
+hyde_status hyde_hyres_denoise_windows_batched(const float* Y, float* X, hyde_windows_plan P,
+                                               hyde_hyres_info* info, void* ws,
+                                               size_t ws_bytes, cudaStream_t s) {
+    if (!Y || !X || Y == X || !P) return HYDE_ERR_INVALID_ARG;
+    if (((uintptr_t)Y % 16) != 0 || ((uintptr_t)X % 4) != 0) return HYDE_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < P->total) return HYDE_ERR_WORKSPACE;
+    const int p = P->p, n = P->n_win, r = P->r;
+    const WinDesc* desc = at<WinDesc>(ws, P->desc);
+    int* status = at<int>(ws, P->status);
+    float* zp = at<float>(ws, P->zp);
+    float* coef = at<float>(ws, P->coef);
+    float* scr = at<float>(ws, P->scr);
+    int* rank = at<int>(ws, P->rank);
+    double* lam = at<double>(ws, P->lam);
+    double* R = at<double>(ws, P->R);
+    double* sigma = at<double>(ws, P->sigma);
+    double* V = at<double>(ws, P->V);
+    float* Pw = at<float>(ws, P->P);
+    float* Qw = at<float>(ws, P->Q);
+#define HYDE_TRY(x) do { hyde_status s_ = (x); if (s_ != HYDE_OK) return s_; } while (0)
+    if (cudaMemcpyAsync(ws, P->host, P->tables, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, (size_t)(n + 1) * sizeof(int), s) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    HYDE_TRY(launch_win_gram(Y, p, P->H, P->W, at<int4>(ws, P->pieces), at<int>(ws, P->pbeg),
+                             at<int4>(ws, P->geo), at<int>(ws, P->wslot0),
+                             at<int>(ws, P->wslot1), n, P->G0, P->G1, at<float>(ws, P->part0),
+                             at<float>(ws, P->part1), R, status + n, s));
+    HYDE_TRY(launch_win_noise(R, p, n, desc, sigma, at<float>(ws, P->Ainv), at<double>(ws, P->S),
+                              status, s));
+    HYDE_TRY(launch_eig_top_batched(R, sigma, p, r, at<double>(ws, P->evals), V,
+                                    at<void>(ws, P->eig), P->eig_stride, status, n, s));
+    HYDE_TRY(launch_weights_batched(V, sigma, p, r, P->RM, Pw, Qw, n, s));
+    HYDE_TRY(launch_win_project(Y, p, P->H, P->W, desc, at<int>(ws, P->tproj), n, P->proj_tiles,
+                                Pw, r, P->RM, zp, s));
+    HYDE_TRY(launch_win_dwt(zp, coef, scr, desc, n, r, P->L, s));
+    HYDE_TRY(launch_win_sure(coef, desc, n, r, P->L, P->K, at<unsigned int>(ws, P->counts),
+                             at<double>(ws, P->sums), at<double>(ws, P->sum_all), rank, lam,
+                             info, status, s));
+    HYDE_TRY(launch_win_idwt(coef, zp, scr, desc, n, r, P->L, rank, lam, s));
+    HYDE_TRY(launch_win_backproject(zp, desc, at<int>(ws, P->tback), n, P->back_tiles, Qw, p,
+                                    P->RM, rank, P->H, P->W, X, s));
+#undef HYDE_TRY
+    return HYDE_OK;
+}
+
+}  // extern "C"

@@ -294,3 +294,34 @@ def test_forpdn_rejects_bad_shapes_on_host(lib):
     assert lib.hyde_forpdn_workspace_size(8, 64, 64, 2, 1, ctypes.byref(sz)) == 2     # K < 2
     assert lib.hyde_forpdn_workspace_size(8, 64, 64, 2, 300, ctypes.byref(sz)) == 2   # K > 256
     assert lib.hyde_forpdn_workspace_size(8, 2, 2, 1, 64, ctypes.byref(sz)) == 2      # n < p
+
+
+def test_windows_plan_rejects_bad_tables_on_host(lib):
+    """hyde_windows_plan_create checks the parameters and every window on the
+    host before it asks for the device."""
+    from paper_2204_06979_gb300 import api
+    from paper_2204_06979_gb300._lib import HydeWindow
+    plan = ctypes.c_void_p()
+
+    def create(p, H, W, rows, prm):
+        win = (HydeWindow * len(rows))(*[HydeWindow(*r) for r in rows])
+        return lib.hyde_windows_plan_create(p, H, W, win, len(rows), ctypes.byref(prm),
+                                            ctypes.byref(plan))
+
+    ok_row = (0, 0, 64, 64, 0, 0, 64, 64)
+    shared = api.params(2, 4, 64)
+    assert lib.hyde_windows_plan_create(8, 64, 64, None, 1, ctypes.byref(shared),
+                                        ctypes.byref(plan)) == 1
+    assert create(8, 64, 64, [ok_row], api.params(2, 4, 64, lambda_mode=api.LAMBDA_PER_LEVEL)) == 1
+    assert create(8, 64, 64, [ok_row], api.params(2, 4, 64, threshold_ll=True)) == 1
+    assert create(8, 64, 64, [ok_row], api.params(2, 4, 64, precision=api.PREC_BF16X3)) == 1
+    assert create(8, 64, 64, [ok_row], api.params(2, 4, 1)) == 1            # K < 2
+    assert create(240, 64, 64, [ok_row], api.params(2, 4, 64)) == 2         # p > 208
+    assert create(8, 64, 62, [(0, 0, 64, 62, 0, 0, 64, 62)], shared) == 2   # W not a multiple of 4
+    assert create(8, 64, 64, [(0, 2, 64, 60, 0, 2, 64, 60)], shared) == 2   # x0 not a multiple of 4
+    assert create(8, 64, 64, [(0, 0, 64, 68, 0, 0, 64, 64)], shared) == 2   # outside the scene
+    assert create(8, 64, 64, [(0, 0, 32, 32, 0, 0, 40, 32)], shared) == 2   # core outside window
+    assert create(8, 64, 64, [(0, 0, 3, 64, 0, 0, 3, 64)], api.params(3, 4, 64)) == 2  # padding
+    assert plan.value is None
+    assert lib.hyde_windows_plan_kernel_launches(None) == -1
+    assert lib.hyde_windows_plan_destroy(None) == 1

@@ -1,0 +1,105 @@
+"""GPU parity of the batched sliding-window form (one launch per stage over
+all windows): every window against the FP64 oracle run on that window alone,
+on small scenes in full (one band role and two band roles of the tensor-core
+Gram, padded and unpadded windows) and on the 2048 x 2048 x 200 scene with
+512 uneven windows on a sample of windows; eager calls against the captured
+graph; every core pixel written."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synth import make_scene, make_window_table
+from test_gpu_windows import _check_window
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(hyde, Y, p, H, W, T, L, r):
+    win = hyde.HyResWindowsBatched(p, H, W, T, L, r)
+    X = torch.full_like(Y, float("nan"))
+    win(Y, X)
+    torch.cuda.synchronize()
+    return win, X
+
+
+@pytest.mark.parametrize("H,W,p,L,r,depth,ctx,mn,mx,seed", [
+    (192, 160, 24, 2, 6, 4, 8, 16, 96, 7),      # p <= 128: one band role
+    (128, 160, 140, 2, 8, 3, 8, 24, 96, 3),     # p > 128: rows [0, 128) and bands [128, 140)
+    (134, 124, 64, 3, 5, 2, 8, 24, 96, 11),     # edge windows of sides not a multiple of 8: padded
+])
+def test_windows_batched_full_parity(hyde, H, W, p, L, r, depth, ctx, mn, mx, seed):
+    T = make_window_table(H, W, depth=depth, context=ctx, min_side=mn, max_side=mx, seed=seed)
+    sc = make_scene(H, W, p, T, m=4, seed=seed)
+    Y = torch.from_numpy(sc["Y"]).cuda()
+    win, X = _run(hyde, Y, p, H, W, T, L, r)
+    assert win.kernel_launches == 13
+    infos = win.infos()
+    assert all(i["status"] == 0 for i in infos)
+    assert bool(torch.isfinite(X).all())   # the cores tile the scene
+    num = den = 0.0
+    for k, row in enumerate(T):
+        got, ref = _check_window(sc["Y"], row, L, r, infos[k], X, k)
+        num += float(np.sum((got.astype(np.float64) - ref) ** 2))
+        den += float(np.sum(ref ** 2))
+        # a per-band bound beside the window's relative L2
+        err_b = np.sqrt(np.sum((got.astype(np.float64) - ref) ** 2, axis=(1, 2)))
+        nrm_b = np.sqrt(np.sum(ref ** 2, axis=(1, 2)))
+        assert np.all(err_b <= 1e-3 * nrm_b + 1e-6 * nrm_b.max()), k
+    # sigma comes from the float inverse without the FP64 Newton step (a
+    # relative error up to ~kappa 2^-24, kappa the condition number of the
+    # scaled Gram matrix), which moves a window's output by up to ~2e-5
+    assert np.sqrt(num / den) < 3e-5
+
+
+def test_windows_batched_graph_replay_and_repeat(hyde):
+    """The captured graph and a second eager call reproduce the first call
+    bit for bit (fixed-order reductions everywhere)."""
+    H, W, p, L, r = 192, 160, 24, 2, 6
+    T = make_window_table(H, W, depth=4, context=8, min_side=16, max_side=96, seed=7)
+    sc = make_scene(H, W, p, T, m=4, seed=9)
+    Y = torch.from_numpy(sc["Y"]).cuda()
+    win, X1 = _run(hyde, Y, p, H, W, T, L, r)
+    X2 = torch.zeros_like(Y)
+    win(Y, X2)
+    X3 = torch.zeros_like(Y)
+    win.capture(Y, X3)
+    X3.zero_()
+    win.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(X1, X2)
+    assert torch.equal(X1, X3)
+
+
+def test_windows_batched_full_scene_sampled(hyde):
+    """2048 x 2048 x 200 scene, 512 windows of sides 48..256 with 16-px
+    context, per-core SNR U[5, 20] dB, db2 with 3 levels, r <= 20, through
+    the captured graph: every pixel written and finite; 18 windows (the
+    smallest, the largest, window 16 and 15 drawn at random) against the
+    oracle, one by one and together."""
+    H = W = 2048
+    p, L, r = 200, 3, 20
+    T = make_window_table(H, W, depth=9, context=16, min_side=32, max_side=224, seed=4)
+    sc = make_scene(H, W, p, T, m=12, seed=4)
+    Y = torch.from_numpy(sc["Y"]).cuda()
+    X = torch.zeros_like(Y)
+    win = hyde.HyResWindowsBatched(p, H, W, T, L, r)
+    win.capture(Y, X)
+    X.fill_(float("nan"))
+    win.replay()
+    torch.cuda.synchronize()
+    infos = win.infos()
+    assert all(i["status"] == 0 for i in infos)
+    assert bool(torch.isfinite(X).all())
+    areas = T[:, 2] * T[:, 3]
+    rng = np.random.default_rng(0)
+    picks = {int(np.argmin(areas)), int(np.argmax(areas)), 16}
+    rest = [k for k in range(len(T)) if k not in picks]
+    picks |= set(int(k) for k in rng.choice(rest, size=15, replace=False))
+    num = den = 0.0
+    for k in sorted(picks):
+        got, ref = _check_window(sc["Y"], T[k], L, r, infos[k], X, k)
+        num += float(np.sum((got.astype(np.float64) - ref) ** 2))
+        den += float(np.sum(ref ** 2))
+    assert np.sqrt(num / den) < 1e-3
