@@ -1043,6 +1043,330 @@ eig_pair_kernel(EigWs G, int p, int* status, long long wst) {
 }
 
 // --------------------------------------------------------------------------
+// 2b. All r eigenpairs of a window in one block (the batched window form,
+// one block per window): warp w takes eigenpairs c = w, w + 8, ... (at most
+// four). Their eigenvalues by multisection with 32 points per round (lane j
+// counts at point j + 1 of 33, the counts of the warp's eigenvalues
+// interleaved in one pass over T), the eigenvectors of T by the twisted
+// factorisation as in eig_pair_kernel, and the back-transformation by the
+// same compact-WY blocks, built once per window by all warps and applied by
+// each warp to its vectors together (one load of a reflector block for all
+// of them). The reflectors are read through L2.
+// --------------------------------------------------------------------------
+constexpr int kAllThreads = 256, kAllWarps = kAllThreads / 32, kMaxPerWarp = 4;
+
+// Sturm counts of T - x_q I for NQ points at once (sturm_count_poly's
+// recurrence and rescaling, one pass over d and e2).
+template <int NQ>
+__device__ __forceinline__ void sturm_counts(const float* d, const float* e2, int p,
+                                             const float (&x)[NQ], int (&c)[NQ]) {
+    float Pm[NQ], P[NQ];
+    bool sg[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        Pm[q] = 1.0f;
+        P[q] = d[0] - x[q];
+        sg[q] = !(P[q] > 0.f);
+        c[q] = sg[q];
+    }
+#pragma unroll 2
+    for (int i = 1; i < p; ++i) {
+        const float ee = e2[i - 1], di = d[i];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float t = ee * Pm[q];
+            const float Pn = fmaf(di - x[q], P[q], -t);
+            const bool sn = Pn < 0.f || (Pn == 0.f && !sg[q]);
+            c[q] += sn != sg[q];
+            sg[q] = sn;
+            Pm[q] = P[q];
+            P[q] = Pn;
+            if (i & 1) {
+                const float m = fmaxf(fabsf(P[q]), fabsf(Pm[q]));
+                const int ex = min((__float_as_int(m) >> 23) & 255, 254);
+                const float sc = __int_as_float((254 - ex) << 23);
+                P[q] *= sc;
+                Pm[q] *= sc;
+            }
+        }
+    }
+}
+
+size_t eig_pairs_all_bytes(int p, int r) {
+    return ((size_t)4 * p + (size_t)3 * kAllWarps * p + (size_t)r * p) * sizeof(float);
+}
+
+#ifndef HYDE_EIG_ALL_MINB
+#define HYDE_EIG_ALL_MINB 2
+#endif
+template <int NB>
+__global__ void __launch_bounds__(kAllThreads, HYDE_EIG_ALL_MINB)
+eig_pairs_all_kernel(EigWs G, int p, int r, int* status, long long wst) {
+    pdl_wait();
+    pdl_trigger();
+    G = eig_ws_window(G, blockIdx.x * wst);
+    if (status) status += blockIdx.x;
+    extern __shared__ float sm[];
+    float* d = sm;
+    float* e = d + p;
+    float* e2 = e + p;
+    float* tau = e2 + p;
+    float* wsc = tau + p;                       // per warp: Dp, Dm, ratios (p each)
+    float* Z = wsc + 3 * kAllWarps * p;         // [r][p] eigenvectors of T
+    __shared__ float s_lo, s_hi, s_pivmin;
+    __shared__ __align__(16) float Tm[kMaxWyBlocks][8][8];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int i = t; i < p; i += kAllThreads) {
+        const float di = G.d[i], ei = G.e[i];
+        d[i] = di;
+        e[i] = ei;
+        e2[i] = ei * ei;
+        tau[i] = G.tau[i];
+        if (!isfinite(di) || !isfinite(ei)) set_status(status, HYDE_ERR_NUMERIC);
+    }
+    __syncthreads();
+    if (wid == 0) {
+        float lo = FLT_MAX, hi = -FLT_MAX, emax = 0.f;
+        for (int i = lane; i < p; i += 32) {
+            const float rad = fabsf(e[i]) + (i > 0 ? fabsf(e[i - 1]) : 0.f);
+            lo = fminf(lo, d[i] - rad);
+            hi = fmaxf(hi, d[i] + rad);
+            emax = fmaxf(emax, e2[i]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        }
+        if (lane == 0) {
+            const float w = hi - lo;
+            s_lo = lo - 1e-6f * fmaxf(w, 1e-30f);
+            s_hi = hi + 1e-6f * fmaxf(w, 1e-30f);
+            s_pivmin = FLT_MIN * fmaxf(1.f, emax);
+        }
+    }
+    __syncthreads();
+    const float pivmin = s_pivmin;
+    // multisection of the warp's eigenvalues (c = wid + 8 k, the (p - c)-th
+    // smallest); each round keeps the one of 33 sub-intervals that holds it
+    float lo[kMaxPerWarp], hi[kMaxPerWarp];
+    bool act[kMaxPerWarp];
+#pragma unroll
+    for (int k = 0; k < kMaxPerWarp; ++k) {
+        lo[k] = s_lo;
+        hi[k] = s_hi;
+        act[k] = wid + kAllWarps * k < r;
+    }
+    for (int it = 0; it < 24; ++it) {   // 24 rounds of 33x exceed float resolution
+        float x[kMaxPerWarp];
+        int cnt[kMaxPerWarp];
+#pragma unroll
+        for (int k = 0; k < kMaxPerWarp; ++k)
+            x[k] = lo[k] + (hi[k] - lo[k]) * (float)(lane + 1) / 33.f;
+        sturm_counts<kMaxPerWarp>(d, e2, p, x, cnt);
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < kMaxPerWarp; ++k) {
+            const int target = p - 1 - (wid + kAllWarps * k);
+            const int nle = __popc(__ballot_sync(0xffffffffu, cnt[k] <= target));
+            if (act[k]) {
+                const float xl = lo[k] + (hi[k] - lo[k]) * (float)nle / 33.f;
+                const float xh = lo[k] + (hi[k] - lo[k]) * (float)(nle + 1) / 33.f;
+                const float nlo = nle > 0 ? xl : lo[k];
+                const float nhi = nle < 32 ? xh : hi[k];
+                if (!(nlo < nhi) || (nhi - nlo) >= (hi[k] - lo[k])) {
+                    act[k] = false;
+                } else {
+                    lo[k] = nlo;
+                    hi[k] = nhi;
+                    if (hi[k] - lo[k] <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo[k]), fabsf(hi[k])))
+                        act[k] = false;
+                }
+            }
+            any |= act[k];
+        }
+        if (!any) break;
+    }
+    // eigenvectors of T by the twisted factorisation, one at a time per warp
+    float* Dp = wsc + 3 * wid * p;
+    float* Dm = Dp + p;
+    float* rat = Dm + p;
+    float lamk[kMaxPerWarp];
+#pragma unroll
+    for (int k = 0; k < kMaxPerWarp; ++k) {
+        lamk[k] = 0.5f * (lo[k] + hi[k]);
+        const int c = wid + kAllWarps * k;
+        if (c >= r) continue;   // warp-uniform
+        const float lam = lamk[k];
+        if (lane < 2) {
+            const bool fwd = lane == 0;
+            float* D = fwd ? Dp : Dm;
+            int i = fwd ? 0 : p - 1;
+            const int step = fwd ? 1 : -1;
+            float qv = d[i] - lam;
+            if (fabsf(qv) < pivmin) qv = -pivmin;
+            D[i] = qv;
+            for (int s2 = 1; s2 < p; ++s2) {
+                i += step;
+                const float ee = e2[fwd ? i - 1 : i];
+                qv = (d[i] - lam) - __fdividef(ee, qv);
+                if (fabsf(qv) < pivmin) qv = -pivmin;
+                D[i] = qv;
+            }
+        }
+        __syncwarp();
+        float best = FLT_MAX;
+        int bi = 0;
+        for (int i = lane; i < p; i += 32) {
+            const float g = fabsf(Dp[i] + Dm[i] - (d[i] - lam));
+            if (g < best) { best = g; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        const int kt = bi;
+        for (int i = lane; i < p; i += 32)
+            rat[i] = i < kt ? -__fdividef(e[i], Dp[i]) : (i > kt ? -__fdividef(e[i - 1], Dm[i]) : 1.0f);
+        __syncwarp();
+        float* z = Z + (size_t)c * p;
+        if (lane < 2) {
+            const bool up = lane == 0;
+            const int len = up ? kt : p - 1 - kt;
+            if (up) z[kt] = 1.0f;
+            int i = kt;
+            float zz = 1.0f;
+            for (int s2 = 0; s2 < len; ++s2) {
+                i += up ? -1 : 1;
+                zz *= rat[i];
+                z[i] = zz;
+            }
+        }
+        __syncwarp();
+    }
+    // compact WY factors of the reflector blocks, by all warps
+    const int nblk = (p - 2 + 7) / 8;
+    for (int blk = wid; blk < nblk; blk += kAllWarps) {
+        const int k0 = 8 * blk;
+        float vq[8][NB];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int i = lane + 32 * b;
+                vq[q][b] = (k0 + q < p - 2 && i < p) ? __ldg(G.refl + (k0 + q) * p + i) : 0.f;
+            }
+        float W[8][8];
+#pragma unroll
+        for (int q = 1; q < 8; ++q)
+#pragma unroll
+            for (int a = 0; a < q; ++a) {
+                float d0 = 0.f;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) d0 = fmaf(vq[a][b], vq[q][b], d0);
+                W[a][q] = d0;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 1; q < 8; ++q)
+#pragma unroll
+                for (int a = 0; a < q; ++a) W[a][q] += __shfl_xor_sync(0xffffffffu, W[a][q], o);
+        float T[8][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float tq = k0 + q < p - 2 ? tau[k0 + q] : 0.f;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) T[a][q] = 0.f;
+            T[q][q] = tq;
+#pragma unroll
+            for (int a = 0; a < q; ++a) {
+                float acc = 0.f;
+#pragma unroll
+                for (int m = a; m < q; ++m) acc = fmaf(T[a][m], W[m][q], acc);
+                T[a][q] = -tq * acc;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (lane == ((8 * a + q) & 31)) Tm[blk][a][q] = T[a][q];
+    }
+    __syncthreads();   // every T block, every z
+    // back-transformation of the warp's vectors: x <- x - V (T (V^T x))
+    const int nv = r > wid ? (r - wid + kAllWarps - 1) / kAllWarps : 0;
+    float x[kMaxPerWarp][NB];
+#pragma unroll
+    for (int k = 0; k < kMaxPerWarp; ++k)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int i = lane + 32 * b;
+            x[k][b] = (k < nv && i < p) ? Z[(size_t)(wid + kAllWarps * k) * p + i] : 0.f;
+        }
+    if (nv > 0) {
+        for (int blk = nblk - 1; blk >= 0; --blk) {
+            const int k0 = 8 * blk;
+            float vq[8][NB];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int i = lane + 32 * b;
+                    vq[q][b] = (k0 + q < p - 2 && i < p) ? __ldg(G.refl + (k0 + q) * p + i) : 0.f;
+                }
+#pragma unroll
+            for (int k = 0; k < kMaxPerWarp; ++k) {
+                if (k >= nv) break;   // warp-uniform
+                float y[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    y[q] = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) y[q] = fmaf(vq[q][b], x[k][b], y[q]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) y[q] += __shfl_xor_sync(0xffffffffu, y[q], o);
+                float u[8];
+#pragma unroll
+                for (int a2 = 0; a2 < 8; ++a2) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int q = a2; q < 8; ++q) acc = fmaf(Tm[blk][a2][q], y[q], acc);
+                    u[a2] = acc;
+                }
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    float xv = x[k][b];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) xv = fmaf(-u[q], vq[q][b], xv);
+                    x[k][b] = xv;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxPerWarp; ++k) {
+        if (k >= nv) break;
+        const int c = wid + kAllWarps * k;
+        float ss = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) ss = fmaf(x[k][b], x[k][b], ss);
+        ss = warp_sum(ss);
+        const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int i = lane + 32 * b;
+            if (i < p) G.X[(size_t)c * p + i] = x[k][b] * inv;
+        }
+        if (lane == 0) G.lam[c] = lamk[k];
+    }
+}
+
+// --------------------------------------------------------------------------
 // 3. Orthonormalisation of the r vectors (rows of X, descending eigenvalue)
 // by Cholesky QR, twice: G = X X^T, G = L L^T, X <- L^-1 X. In exact
 // arithmetic this is Gram-Schmidt in the same order (row i becomes a
@@ -1209,10 +1533,18 @@ static hyde_status eig_top(const double* A, const double* wsig, int p, int r, do
     switch (NB) {
 #define HYDE_EIG(NBV)                                                                              \
     case NBV:                                                                                      \
-        if (launch_tridiag<NBV>(A, wsig, p, G, status, n_win, wst, s) != HYDE_OK ||               \
-            ensure_smem_limit((const void*)eig_pair_kernel<NBV>, (int)sp) != cudaSuccess)          \
+        if (launch_tridiag<NBV>(A, wsig, p, G, status, n_win, wst, s) != HYDE_OK)                 \
             return HYDE_ERR_SHAPE;                                                                 \
-        launch_pdl(eig_pair_kernel<NBV>, dim3(r, n_win), kPairThreads, sp, s, G, p, status, wst); \
+        if (n_win == 1) {                                                                          \
+            if (ensure_smem_limit((const void*)eig_pair_kernel<NBV>, (int)sp) != cudaSuccess)      \
+                return HYDE_ERR_SHAPE;                                                             \
+            launch_pdl(eig_pair_kernel<NBV>, dim3(r, 1), kPairThreads, sp, s, G, p, status, wst);  \
+        } else {                                                                                   \
+            const size_t sa = eig_pairs_all_bytes(p, r);                                           \
+            if (ensure_smem_limit((const void*)eig_pairs_all_kernel<NBV>, (int)sa) != cudaSuccess) \
+                return HYDE_ERR_SHAPE;                                                             \
+            launch_pdl(eig_pairs_all_kernel<NBV>, n_win, kAllThreads, sa, s, G, p, r, status, wst); \
+        }                                                                                          \
         break;
         HYDE_EIG(1) HYDE_EIG(2) HYDE_EIG(3) HYDE_EIG(4)
         HYDE_EIG(5) HYDE_EIG(6) HYDE_EIG(7) HYDE_EIG(8)

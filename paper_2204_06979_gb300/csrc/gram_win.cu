@@ -1,17 +1,20 @@
 // Gram matrices R_w = Y_w^T Y_w of every window of a batched sliding-window
 // call on the 5th-generation tensor cores, split-TF32 (the spectral
 // statistics of HyRes, arXiv 2204.06979 Sec. 2.1, for each tile of a scene
-// that is denoised in tiles, Sec. 2.2.2). The arithmetic is that of the
-// single-cube kernel (gram_tf32.cu): y = hi + lo with hi = tf32_rn(y), the
-// products hi hi + hi lo + lo hi on kind::tf32 MMAs into TMEM windows of two
-// chunks, each window drained into FP32 registers.
+// that is denoised in tiles, Sec. 2.2.2): y = hi + lo, the products
+// hi hi + hi lo + lo hi on kind::tf32 MMAs into TMEM windows of two chunks,
+// each window drained into FP32 registers (as in gram_tf32.cu).
 //
-// What differs is the data path:
+// What differs from the one-cube kernel:
 //  * the windows are read in place from the scene Y [p][H][W] through one
-//    3D tensor map (x, y, band); a chunk is an 8 x 4 pixel block of one
-//    window, loaded as a box {8, 4, bands} that lands as [band][32 pixels],
-//    one 128-byte row per band, and pixels outside the window are zeroed by
-//    the converters (a box may overhang the window or the scene);
+//    3D tensor map (x, y, band); a chunk is 32 consecutive pixels of one
+//    window row, a box {32, 1, bands} that TMA writes with the 128-byte
+//    swizzle, i.e. straight into the K-major operand layout. That raw tile
+//    is the hi operand: the tensor core reads the leading 19 bits of each
+//    float, hi = trunc_tf32(y). The converter warps form only
+//    lo = tf32_rn(y - hi) (exact difference, rounded: 2^-21 |y|) and zero
+//    the pixels past the window's right edge in both tiles. The dropped
+//    lo lo term is below 2^-20 y_a y_b;
 //  * the bands split into two roles so that the accumulators of one CTA fit
 //    its registers for p up to 208: role 0 computes rows [0, 128) of R
 //    against all bands (one MMA of N = round16(p) per product), role 1 the
@@ -22,6 +25,9 @@
 //    range crosses a few window boundaries; each (window, range) piece ends
 //    with the drain warps writing their FP32 sums to the piece's own partial,
 //    and a second kernel adds a window's partials in double in piece order.
+// Measured on the 2048 x 2048 x 200 scene (512 windows): with 8 x 4 pixel
+// chunks and converters writing both hi and lo tiles the kernel took 5.6 ms,
+// the converters busy ~2.7k of the ~3.6k cycles per chunk.
 // Every mbarrier wait is bounded in time; a timeout sets HYDE_ERR_TIMEOUT and
 // every role winds down (waiting, bounded, for its own copies and MMAs in
 // flight) before the CTA frees its TMEM.
@@ -36,13 +42,22 @@ namespace hyde {
 namespace {
 
 constexpr int kK = 32;                 // pixels per chunk
-constexpr int kCx = 8, kCy = 4;        // chunk: 8 columns x 4 rows
+constexpr int kCx = 32, kCy = 1;       // chunk: 32 consecutive pixels of one window row
 constexpr int kOpStages = 2;
 constexpr int kMaxRaw = 8;
 constexpr int kWin = 2;                // chunks per TMEM accumulation window
-constexpr int kTmaWarp = 0, kMmaWarp = 1, kCvtWarp0 = 2, kCvtWarps = 2;
+// Warp roles: warpgroups 0-1 hold the TMA warp, the MMA warp and six
+// converter warps, warpgroups 2-3 the eight drain warps. The drain warps
+// keep up to 112 FP32 sums each; the block is launched with 128 registers
+// per thread, then warpgroups 0-1 release down to kLowRegs and 2-3 take up
+// to kHighRegs (setmaxnreg), which adds up to the launch's 65536 exactly.
+constexpr int kTmaWarp = 0, kMmaWarp = 1, kCvtWarp0 = 2, kCvtWarps = 6;
 constexpr int kDrainWarp0 = kCvtWarp0 + kCvtWarps, kDrainWarps = 8;
 constexpr int kWgThreads = (kDrainWarp0 + kDrainWarps) * 32;
+constexpr int kLaunchRegs = 128, kLowRegs = 64, kHighRegs = 192;
+static_assert(kWgThreads == 512, "four warpgroups");
+static_assert(256 * kLowRegs + 256 * kHighRegs == kWgThreads * kLaunchRegs,
+              "the register split must add up to the launch allocation");
 constexpr int kMaxP = 208;
 
 struct WgRole {
@@ -84,17 +99,20 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
     const uint32_t s0 = smem_u32(smem_raw);
     const uint32_t base = (s0 + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - s0);
-    const uint32_t op_area = 2u * kOpStages * P.op_bytes;
+    // lo tiles (one per op stage), then the raw stages, which are the hi
+    // tiles: TMA writes them in the 128-byte-swizzled K-major layout
+    const uint32_t op_area = (uint32_t)kOpStages * P.op_bytes;
     const uint32_t rawb = base + op_area;
+    const uint32_t all_area = op_area + (uint32_t)P.raw_stages * P.raw_stage_bytes;
     volatile int* abort_v = &abort_s;
     const int RS = P.raw_stages;
 
-    for (uint32_t e = tid; e < op_area / 16; e += kWgThreads)   // rows >= nb stay zero
+    for (uint32_t e = tid; e < all_area / 16; e += kWgThreads)   // rows >= nb stay zero
         reinterpret_cast<uint4*>(gbase)[e] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int q = 0; q < RS; ++q) {
             mbar_init(smem_u32(&raw_full[q]), 1);
-            mbar_init(smem_u32(&raw_empty[q]), kCvtWarps * 32);
+            mbar_init(smem_u32(&raw_empty[q]), 1);   // the MMAs that read the stage
         }
         for (int q = 0; q < kOpStages; ++q) {
             mbar_init(smem_u32(&op_full[q]), kCvtWarps * 32);
@@ -119,6 +137,8 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
 
+    if (warp < kDrainWarp0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kLowRegs));
     if (warp == kTmaWarp) {
         // ------------------------------------------------------ TMA loads
         if (lane == 0) {
@@ -144,7 +164,7 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
                     mbar_arrive_expect_tx(bar, bytes);
                     const int cy = c / nx, cx = c - cy * nx;
                     tma_load_3d(rawb + (uint32_t)s * P.raw_stage_bytes, tmap, g.y + kCx * cx,
-                                g.x + kCy * cy, P.band0, bar);
+                                g.x + kCy * cy, P.band0, bar);   // x0 + 32 cx: 16-byte aligned
                     issued = it + 1;
                 }
             }
@@ -184,7 +204,9 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t hi = base + (uint32_t)o * 2u * P.op_bytes, lo = hi + P.op_bytes;
+                    const int s = (int)(it % P.raw_stages);
+                    const uint32_t hi = rawb + (uint32_t)s * P.raw_stage_bytes;
+                    const uint32_t lo = base + (uint32_t)o * P.op_bytes;
                     const uint32_t d = tmem + (uint32_t)b * (uint32_t)P.buf_cols;
 #pragma unroll
                     for (int kk = 0; kk < kK / 8; ++kk) {
@@ -195,6 +217,7 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
                         umma_tf32(d, sw128_desc(lo + ko), sw128_desc(hi + ko), idT, 1u);
                     }
                     umma_commit(smem_u32(&op_empty[o]));
+                    umma_commit(smem_u32(&raw_empty[s]));
                     if (last) {
                         umma_commit(smem_u32(&acc_full[b]));
                         ++wg;
@@ -209,7 +232,7 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
                                    wait_ns > kWaitNs ? wait_ns : kWaitNs))
                 *abort_v = 1;
         }
-    } else if (warp < kDrainWarp0) {
+    } else {
         // ------------------------------------ split into hi and lo, mask the window
         const int ct = tid - kCvtWarp0 * 32;
         long long it = 0;
@@ -234,36 +257,56 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
                     stop = true;
                     break;
                 }
-                const int cy = c / nx, cx = c - cy * nx;
-                const int rv = min(kCy, g.z - kCy * cy), cv = min(kCx, g.w - kCx * cx);
-                const float* raw = reinterpret_cast<const float*>(
-                    gbase + (op_area + (uint32_t)s * P.raw_stage_bytes));
-                uint8_t* hi_t = gbase + (uint32_t)o * 2u * P.op_bytes;
-                uint8_t* lo_t = hi_t + P.op_bytes;
-                for (int gi = ct; gi < P.nb * 8; gi += kCvtWarps * 32) {
-                    const int b = gi >> 3, k4 = gi & 7;
-                    const int row = k4 >> 1, col0 = (k4 & 1) * 4;
-                    const float4 v4 = *reinterpret_cast<const float4*>(raw + b * kK + 4 * k4);
-                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-                    float h[4], l[4];
+                const int cx = c % nx;
+                const int cv = min(kCx, g.w - kCx * cx);   // pixels of the chunk in the window
+                uint8_t* raw = gbase + (op_area + (uint32_t)s * P.raw_stage_bytes);
+                uint8_t* lo_t = gbase + (uint32_t)o * P.op_bytes;
+                // lo = tf32_rn(y - trunc(y)) for the pixels of the window; the
+                // tensor core reads hi = trunc(y) from the raw tile itself.
+                // Pixels past the window's right edge are zeroed in both.
+                constexpr int kStep = kCvtWarps * 32, kU = 4;
+                const int nit = P.nb * 8;
+                for (int g0 = ct; g0 < nit; g0 += kU * kStep) {
+                    float4 v4[kU];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float v = (row < rv && col0 + e < cv) ? vv[e] : 0.f;
-                        h[e] = tf32_rn(v);
-                        l[e] = v - h[e];
+                    for (int u = 0; u < kU; ++u) {
+                        const int gi = g0 + u * kStep;
+                        const int b = gi >> 3, k4 = gi & 7;
+                        const uint32_t off = (uint32_t)b * 128u + ((uint32_t)(k4 ^ (b & 7)) << 4);
+                        v4[u] = gi < nit ? *reinterpret_cast<const float4*>(raw + off)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    const uint32_t off = (uint32_t)b * 128u + ((uint32_t)(k4 ^ (b & 7)) << 4);
-                    *reinterpret_cast<float4*>(hi_t + off) = make_float4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<float4*>(lo_t + off) = make_float4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int gi = g0 + u * kStep;
+                        if (gi >= nit) break;
+                        const int b = gi >> 3, k4 = gi & 7;
+                        const uint32_t off = (uint32_t)b * 128u + ((uint32_t)(k4 ^ (b & 7)) << 4);
+                        float vv[4] = {v4[u].x, v4[u].y, v4[u].z, v4[u].w};
+                        const bool edge = 4 * k4 + 4 > cv;
+                        if (edge) {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (4 * k4 + e >= cv) vv[e] = 0.f;
+                            *reinterpret_cast<float4*>(raw + off) =
+                                make_float4(vv[0], vv[1], vv[2], vv[3]);
+                        }
+                        float l[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            l[e] = tf32_rn(vv[e] - __uint_as_float(__float_as_uint(vv[e]) & 0xFFFFE000u));
+                        *reinterpret_cast<float4*>(lo_t + off) = make_float4(l[0], l[1], l[2], l[3]);
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(smem_u32(&op_full[o]));
-                mbar_arrive(smem_u32(&raw_empty[s]));
             }
         }
+    }
     } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kHighRegs));
         // ---------------------------------------------------- drain warps
-        // Drain group grp (warps 4-7 or 8-11) owns TMEM lane `row` (the
+        // Drain group grp (warps 8-11 or 12-15) owns TMEM lane `row` (the
         // band band0 + row) and the column blocks grp, grp + 2, ...; at the
         // end of a piece it writes its sums to the piece's partial.
         const int dw = warp - kDrainWarp0, grp = dw >> 2;
@@ -392,8 +435,8 @@ bool role_plan(int p, int band0, int nb, int NT, WgRole* r, size_t* smem) {
     R.band0 = band0;
     R.nb = nb;
     R.rows = NT > 128 ? NT : 128;
-    R.op_bytes = (uint32_t)R.rows * 128u;
-    R.raw_stage_bytes = (uint32_t)align_up((size_t)nb * kK * 4, 1024);
+    R.op_bytes = (uint32_t)R.rows * 128u;   // one tile: rows x 32 floats, swizzled
+    R.raw_stage_bytes = R.op_bytes;         // a raw stage is the hi tile of its chunk
     R.buf_cols = (int)align_up((size_t)NT, 32);
     const int need = 2 * R.buf_cols;
     if (need > 512) return false;
@@ -401,7 +444,7 @@ bool role_plan(int p, int band0, int nb, int NT, WgRole* r, size_t* smem) {
     R.out_rows = nb < 128 ? nb : 128;
     R.out_cols = band0 == 0 ? p : nb;
     const size_t room = 227 * 1024 - 1024 - 1024;   // alignment slack, static shared memory
-    const size_t op_area = 2u * kOpStages * R.op_bytes;
+    const size_t op_area = (size_t)kOpStages * R.op_bytes;
     if (op_area + 2 * R.raw_stage_bytes > room) return false;
     const int rs = (int)((room - op_area) / R.raw_stage_bytes);
     R.raw_stages = rs > kMaxRaw ? kMaxRaw : rs;
@@ -433,7 +476,11 @@ hyde_status win_gram_layout(int p, const int4* geo, int n_win, int sms, WinGramL
         if (geo[w].z < 1 || geo[w].w < 1 || (geo[w].y % 4) != 0) return HYDE_ERR_SHAPE;
     const bool two = p > 128;
     // CTAs in proportion to the work per chunk (bands loaded + the MMA's N)
-    const double w0 = (double)p + nt0_of(p), w1 = two ? (double)(p - 128) + (nt0_of(p) - 128) : 0.0;
+#ifndef HYDE_WIN_W1X
+#define HYDE_WIN_W1X 2.2
+#endif
+    const double w0 = (double)p + nt0_of(p),
+                 w1 = two ? HYDE_WIN_W1X * ((double)(p - 128) + (nt0_of(p) - 128)) : 0.0;
     int G0 = two ? (int)(sms * w0 / (w0 + w1) + 0.5) : sms;
     if (G0 < 1) G0 = 1;
     if (two && G0 > sms - 1) G0 = sms - 1;
@@ -505,7 +552,7 @@ hyde_status launch_win_gram(const float* Y, int p, int H, int W, const int4* pie
         const cuuint32_t box[3] = {(cuuint32_t)kCx, (cuuint32_t)kCy, (cuuint32_t)Wp.role[r].nb};
         const cuuint32_t estr[3] = {1, 1, 1};
         if (enc(&tm[r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(Y), dims, strides,
-                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return HYDE_ERR_CUDA;
@@ -513,6 +560,11 @@ hyde_status launch_win_gram(const float* Y, int p, int H, int W, const int4* pie
     if (!two) tm[1] = tm[0];
     auto go = [&](auto kernel) -> hyde_status {
         if (ensure_smem_limit((const void*)kernel, (int)smem) != cudaSuccess) return HYDE_ERR_CUDA;
+        // the setmaxnreg split assumes exactly kLaunchRegs registers per thread at launch
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, (const void*)kernel) != cudaSuccess ||
+            fa.numRegs != kLaunchRegs)
+            return HYDE_ERR_CUDA;
         launch_pdl(kernel, G0 + G1, kWgThreads, smem, s, tm[0], tm[1], pieces, pbeg, geo, Wp,
                    part0, part1, status);
         return HYDE_OK;

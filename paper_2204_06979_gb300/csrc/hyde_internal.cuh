@@ -362,8 +362,8 @@ hyde_status launch_weights_batched(const double* V, const double* sigma, int p, 
 // inverse DWT, back-projection of the cores into X.
 // tstart[w] .. tstart[w + 1]: window w's tiles of kWinProjTile padded pixels
 // (projection) or kWinBackTile core pixels (back-projection), n_tiles in all.
-constexpr int kWinProjTile = 2048;
-constexpr int kWinBackTile = 2048;
+constexpr int kWinProjTile = 512;
+constexpr int kWinBackTile = 1024;
 hyde_status launch_win_project(const float* Y, int p, int H, int W, const WinDesc* desc,
                                const int* tstart, int n_win, int n_tiles, const float* P, int r,
                                int ldw, float* Zp, cudaStream_t s);
