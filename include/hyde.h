@@ -559,12 +559,15 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
  * the thresholded inverse DWT and the back-projection of the cores, each a
  * single launch over every window (13 kernels for the whole scene).
  *
- * Differences from hyde_hyres_denoise on the window's cube: sigma comes from
- * the float Gauss-Jordan inverse without the FP64 Newton step (that step is
- * p^3 double FMAs per window; its effect on a window's output is ~1e-5
- * relative at p = 200), and only the shared-lambda mode with the LL band
- * kept (lambda_mode HYDE_LAMBDA_SHARED, threshold_ll 0) and the FP32 or
- * HYDE_PREC_TF32X3 precision (both the split-TF32 Gram) are supported.
+ * Differences from hyde_hyres_denoise on the window's cube: the Gram matrices
+ * come from a four-term split-BF16 product on the tensor cores (every
+ * product term exact, an unbiased 2^-18 split residual; FP32-accurate like
+ * the split-TF32 kernel), sigma from the float Gauss-Jordan inverse without
+ * the FP64 Newton step (that step is p^3 double FMAs per window; its effect
+ * on a window's output is ~1e-5 relative at p = 200), and only the
+ * shared-lambda mode with the LL band kept (lambda_mode HYDE_LAMBDA_SHARED,
+ * threshold_ll 0) with precision HYDE_PREC_FP32 or HYDE_PREC_TF32X3 (the
+ * same path) is accepted.
  *
  * A plan holds the window table and the layout of the workspace. Create it
  * once per table (host only; copies win), query its workspace size, and run
@@ -586,6 +589,15 @@ hyde_status hyde_windows_plan_workspace_size(hyde_windows_plan plan, size_t* byt
 /* Kernels one hyde_hyres_denoise_windows_batched call launches (-1 if NULL). */
 int hyde_windows_plan_kernel_launches(hyde_windows_plan plan);
 hyde_status hyde_windows_plan_destroy(hyde_windows_plan plan);
+/* Byte offsets of intermediates a batched call leaves in its workspace, for
+ * inspection after the stream has finished: R double[n_win][p][p] (each
+ * window's Gram matrix), sigma double[n_win][p], V double[n_win][p][r_max]. */
+typedef struct {
+    size_t R;
+    size_t sigma;
+    size_t V;
+} hyde_windows_ws_layout;
+hyde_status hyde_windows_plan_layout(hyde_windows_plan plan, hyde_windows_ws_layout* out);
 hyde_status hyde_hyres_denoise_windows_batched(const float* Y, float* X,
                                                hyde_windows_plan plan,
                                                hyde_hyres_info* info, void* ws,

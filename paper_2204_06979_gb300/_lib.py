@@ -30,6 +30,10 @@ class HydeWindow(ctypes.Structure):
     _fields_ = [(name, c_int) for name in ("y0", "x0", "h", "w", "cy0", "cx0", "ch", "cw")]
 
 
+class HydeWindowsWsLayout(ctypes.Structure):
+    _fields_ = [(name, c_size) for name in ("R", "sigma", "V")]
+
+
 class HydeWsLayout(ctypes.Structure):
     _fields_ = [(name, c_size) for name in
                 ("total", "R", "sigma", "evals", "V", "coef", "sure", "sure_inf",
@@ -100,6 +104,7 @@ SIGNATURES = {
     "hyde_windows_plan_workspace_size": (c_int, [c_vp, c_size_p]),
     "hyde_windows_plan_kernel_launches": (c_int, [c_vp]),
     "hyde_windows_plan_destroy": (c_int, [c_vp]),
+    "hyde_windows_plan_layout": (c_int, [c_vp, ctypes.POINTER(HydeWindowsWsLayout)]),
     "hyde_hyres_denoise_windows_batched": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "hyde_hyres_denoise_host": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int,
                                         ctypes.POINTER(HydeParams), c_vp, c_vp, c_vp, c_size,

@@ -710,6 +710,25 @@ class HyResWindowsBatched:
         raw = self.info.cpu()
         return [parse_info(raw[k * INFO_BYTES:(k + 1) * INFO_BYTES]) for k in range(self.n_win)]
 
+    def intermediates(self) -> dict:
+        """Every window's Gram matrix R [n][p][p], noise levels sigma [n][p]
+        and basis V [n][p][r_max] (float64 tensors on the device) from the
+        workspace, after the stream has finished."""
+        from ._lib import HydeWindowsWsLayout
+        lay = HydeWindowsWsLayout()
+        _check(self.lib.hyde_windows_plan_layout(self.plan, ctypes.byref(lay)),
+               "hyde_windows_plan_layout")
+        p = self.shape[0]
+        r = self.params.r_max
+        n = self.n_win
+
+        def view(off, count):
+            return self.ws[off:off + 8 * count].view(torch.float64)
+
+        return {"R": view(lay.R, n * p * p).view(n, p, p),
+                "sigma": view(lay.sigma, n * p).view(n, p),
+                "V": view(lay.V, n * p * r).view(n, p, r)}
+
 
 class HyResWindows:
     """Sliding-window HyRes over a scene of fixed shape and window table

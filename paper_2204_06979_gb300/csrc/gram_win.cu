@@ -1,20 +1,22 @@
 // Gram matrices R_w = Y_w^T Y_w of every window of a batched sliding-window
-// call on the 5th-generation tensor cores, split-TF32 (the spectral
-// statistics of HyRes, arXiv 2204.06979 Sec. 2.1, for each tile of a scene
-// that is denoised in tiles, Sec. 2.2.2): y = hi + lo, the products
-// hi hi + hi lo + lo hi on kind::tf32 MMAs into TMEM windows of two chunks,
-// each window drained into FP32 registers (as in gram_tf32.cu).
+// call on the 5th-generation tensor cores (the spectral statistics of HyRes,
+// arXiv 2204.06979 Sec. 2.1, for each tile of a scene that is denoised in
+// tiles, Sec. 2.2.2), with a four-term split-BF16 product: y = hi + lo + e,
+// hi = bf16_rn(y), lo = bf16_rn(y - hi), |e| <= 2^-18 |y| (unbiased), and
+// y_a y_b ~ hi hi + hi lo + lo hi + lo lo, every term exact in FP32, on
+// kind::f16 MMAs (K = 16 per instruction) into TMEM windows of one 64-pixel
+// chunk, each window drained into FP32 registers. The per-instruction cost
+// of the MMAs, not their arithmetic, bounds this kernel at these shapes:
+// split-TF32 (three products at K = 8) issues 50 % more instructions per
+// pixel and drops the lo lo term.
 //
-// What differs from the one-cube kernel:
+// The data path:
 //  * the windows are read in place from the scene Y [p][H][W] through one
-//    3D tensor map (x, y, band); a chunk is 32 consecutive pixels of one
-//    window row, a box {32, 1, bands} that TMA writes with the 128-byte
-//    swizzle, i.e. straight into the K-major operand layout. That raw tile
-//    is the hi operand: the tensor core reads the leading 19 bits of each
-//    float, hi = trunc_tf32(y). The converter warps form only
-//    lo = tf32_rn(y - hi) (exact difference, rounded: 2^-21 |y|) and zero
-//    the pixels past the window's right edge in both tiles. The dropped
-//    lo lo term is below 2^-20 y_a y_b;
+//    3D tensor map (x, y, band); a chunk is a 32 x 2 pixel block of one
+//    window, a box {32, 2, bands} that lands as [band][64 floats];
+//  * six converter warps split each chunk into the hi and lo tiles in the
+//    128-byte-swizzled K-major layout (one 128-byte row of 64 bf16 per
+//    band), pixels outside the window set to zero;
 //  * the bands split into two roles so that the accumulators of one CTA fit
 //    its registers for p up to 208: role 0 computes rows [0, 128) of R
 //    against all bands (one MMA of N = round16(p) per product), role 1 the
@@ -25,9 +27,10 @@
 //    range crosses a few window boundaries; each (window, range) piece ends
 //    with the drain warps writing their FP32 sums to the piece's own partial,
 //    and a second kernel adds a window's partials in double in piece order.
-// Measured on the 2048 x 2048 x 200 scene (512 windows): with 8 x 4 pixel
-// chunks and converters writing both hi and lo tiles the kernel took 5.6 ms,
-// the converters busy ~2.7k of the ~3.6k cycles per chunk.
+// Measured on the 2048 x 2048 x 200 scene (512 windows): split-TF32 with two
+// converter warps 5.6 ms (the converters busy ~2.7k of ~3.6k cycles per
+// 32-pixel chunk), with six converter warps 3.9 ms (the MMA issue ~115-140
+// cycles per instruction, whatever N).
 // Every mbarrier wait is bounded in time; a timeout sets HYDE_ERR_TIMEOUT and
 // every role winds down (waiting, bounded, for its own copies and MMAs in
 // flight) before the CTA frees its TMEM.
@@ -41,11 +44,11 @@
 namespace hyde {
 namespace {
 
-constexpr int kK = 32;                 // pixels per chunk
-constexpr int kCx = 32, kCy = 1;       // chunk: 32 consecutive pixels of one window row
+constexpr int kK = 64;                 // pixels per chunk: one 128-byte row of bf16
+constexpr int kCx = 32, kCy = 2;       // chunk: 32 x 2 pixels of one window
 constexpr int kOpStages = 2;
 constexpr int kMaxRaw = 8;
-constexpr int kWin = 2;                // chunks per TMEM accumulation window
+constexpr int kWin = 1;                // chunks per TMEM accumulation window (64 pixels)
 // Warp roles: warpgroups 0-1 hold the TMA warp, the MMA warp and six
 // converter warps, warpgroups 2-3 the eight drain warps. The drain warps
 // keep up to 112 FP32 sums each; the block is launched with 128 registers
@@ -75,10 +78,6 @@ struct WgParams {
     unsigned long long wait_ns;
 };
 
-__device__ __forceinline__ float tf32_rn(float x) {
-    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-
 // One CTA of role `R` (NT = the MMA's N). Pieces pbeg[g] .. pbeg[g + 1] - 1
 // of `pieces` (x: window, y, z: chunk range, w: partial slot); geo[window] =
 // (y0, x0, h, w) in scene pixels.
@@ -99,9 +98,9 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
     const uint32_t s0 = smem_u32(smem_raw);
     const uint32_t base = (s0 + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - s0);
-    // lo tiles (one per op stage), then the raw stages, which are the hi
-    // tiles: TMA writes them in the 128-byte-swizzled K-major layout
-    const uint32_t op_area = (uint32_t)kOpStages * P.op_bytes;
+    // op stage o: hi tile at base + 2 o op_bytes, lo tile op_bytes after it;
+    // then the raw stages ([band][64 floats], as TMA writes them)
+    const uint32_t op_area = 2u * kOpStages * P.op_bytes;
     const uint32_t rawb = base + op_area;
     const uint32_t all_area = op_area + (uint32_t)P.raw_stages * P.raw_stage_bytes;
     volatile int* abort_v = &abort_s;
@@ -112,7 +111,7 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
     if (tid == 0) {
         for (int q = 0; q < RS; ++q) {
             mbar_init(smem_u32(&raw_full[q]), 1);
-            mbar_init(smem_u32(&raw_empty[q]), 1);   // the MMAs that read the stage
+            mbar_init(smem_u32(&raw_empty[q]), kCvtWarps * 32);
         }
         for (int q = 0; q < kOpStages; ++q) {
             mbar_init(smem_u32(&op_full[q]), kCvtWarps * 32);
@@ -178,7 +177,7 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ MMA issue (1 thread)
         if (lane == 0) {
-            const uint32_t idT = idesc_tf32(128, NT);
+            const uint32_t idT = idesc_bf16(128, NT);
             long long it = 0, issued = 0, wg = 0;
             bool stop = false;
             for (int q = q0; q < q1 && !stop; ++q) {
@@ -204,20 +203,18 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
                         break;
                     }
                     tc_fence_after();
-                    const int s = (int)(it % P.raw_stages);
-                    const uint32_t hi = rawb + (uint32_t)s * P.raw_stage_bytes;
-                    const uint32_t lo = base + (uint32_t)o * P.op_bytes;
+                    const uint32_t hi = base + (uint32_t)o * 2u * P.op_bytes, lo = hi + P.op_bytes;
                     const uint32_t d = tmem + (uint32_t)b * (uint32_t)P.buf_cols;
 #pragma unroll
-                    for (int kk = 0; kk < kK / 8; ++kk) {
-                        const uint32_t ko = (uint32_t)kk * 32u;   // 8 tf32 along K
+                    for (int kk = 0; kk < kK / 16; ++kk) {
+                        const uint32_t ko = (uint32_t)kk * 32u;   // 16 bf16 along K
                         const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
-                        umma_tf32(d, sw128_desc(hi + ko), sw128_desc(hi + ko), idT, acc);
-                        umma_tf32(d, sw128_desc(hi + ko), sw128_desc(lo + ko), idT, 1u);
-                        umma_tf32(d, sw128_desc(lo + ko), sw128_desc(hi + ko), idT, 1u);
+                        umma_bf16(d, sw128_desc(hi + ko), sw128_desc(hi + ko), idT, acc);
+                        umma_bf16(d, sw128_desc(hi + ko), sw128_desc(lo + ko), idT, 1u);
+                        umma_bf16(d, sw128_desc(lo + ko), sw128_desc(hi + ko), idT, 1u);
+                        umma_bf16(d, sw128_desc(lo + ko), sw128_desc(lo + ko), idT, 1u);
                     }
                     umma_commit(smem_u32(&op_empty[o]));
-                    umma_commit(smem_u32(&raw_empty[s]));
                     if (last) {
                         umma_commit(smem_u32(&acc_full[b]));
                         ++wg;
@@ -257,49 +254,51 @@ __device__ __forceinline__ void win_gram_role(const CUtensorMap* tmap, const int
                     stop = true;
                     break;
                 }
-                const int cx = c % nx;
-                const int cv = min(kCx, g.w - kCx * cx);   // pixels of the chunk in the window
-                uint8_t* raw = gbase + (op_area + (uint32_t)s * P.raw_stage_bytes);
-                uint8_t* lo_t = gbase + (uint32_t)o * P.op_bytes;
-                // lo = tf32_rn(y - trunc(y)) for the pixels of the window; the
-                // tensor core reads hi = trunc(y) from the raw tile itself.
-                // Pixels past the window's right edge are zeroed in both.
-                constexpr int kStep = kCvtWarps * 32, kU = 4;
+                const int cy = c / nx, cx = c - cy * nx;
+                const int rv = min(kCy, g.z - kCy * cy), cv = min(kCx, g.w - kCx * cx);
+                const float* raw = reinterpret_cast<const float*>(
+                    gbase + (op_area + (uint32_t)s * P.raw_stage_bytes));
+                uint8_t* hi_t = gbase + (uint32_t)o * 2u * P.op_bytes;
+                uint8_t* lo_t = hi_t + P.op_bytes;
+                // item (b, k8): pixels 8 k8 .. 8 k8 + 7 of band b (window row
+                // k8 / 4, columns 8 (k8 % 4) ..), one 16-byte chunk of the
+                // swizzled bf16 row in each tile; pixels outside the window
+                // are zero
+                constexpr int kStep = kCvtWarps * 32, kU = 2;
                 const int nit = P.nb * 8;
                 for (int g0 = ct; g0 < nit; g0 += kU * kStep) {
-                    float4 v4[kU];
+                    float4 va[kU], vb[kU];
 #pragma unroll
                     for (int u = 0; u < kU; ++u) {
                         const int gi = g0 + u * kStep;
-                        const int b = gi >> 3, k4 = gi & 7;
-                        const uint32_t off = (uint32_t)b * 128u + ((uint32_t)(k4 ^ (b & 7)) << 4);
-                        v4[u] = gi < nit ? *reinterpret_cast<const float4*>(raw + off)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float* src = raw + (gi < nit ? gi : 0) * 8;
+                        va[u] = *reinterpret_cast<const float4*>(src);
+                        vb[u] = *reinterpret_cast<const float4*>(src + 4);
                     }
 #pragma unroll
                     for (int u = 0; u < kU; ++u) {
                         const int gi = g0 + u * kStep;
                         if (gi >= nit) break;
-                        const int b = gi >> 3, k4 = gi & 7;
-                        const uint32_t off = (uint32_t)b * 128u + ((uint32_t)(k4 ^ (b & 7)) << 4);
-                        float vv[4] = {v4[u].x, v4[u].y, v4[u].z, v4[u].w};
-                        const bool edge = 4 * k4 + 4 > cv;
-                        if (edge) {
+                        const int b = gi >> 3, k8 = gi & 7;
+                        const int row = k8 >> 2, col0 = (k8 & 3) * 8;
+                        float v[8] = {va[u].x, va[u].y, va[u].z, va[u].w,
+                                      vb[u].x, vb[u].y, vb[u].z, vb[u].w};
+                        if (row >= rv || col0 + 8 > cv) {
 #pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (4 * k4 + e >= cv) vv[e] = 0.f;
-                            *reinterpret_cast<float4*>(raw + off) =
-                                make_float4(vv[0], vv[1], vv[2], vv[3]);
+                            for (int e = 0; e < 8; ++e)
+                                if (row >= rv || col0 + e >= cv) v[e] = 0.f;
                         }
-                        float l[4];
+                        uint32_t h[4], l[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            l[e] = tf32_rn(vv[e] - __uint_as_float(__float_as_uint(vv[e]) & 0xFFFFE000u));
-                        *reinterpret_cast<float4*>(lo_t + off) = make_float4(l[0], l[1], l[2], l[3]);
+                        for (int e = 0; e < 4; ++e) split_pair(v[2 * e], v[2 * e + 1], h[e], l[e]);
+                        const uint32_t off = (uint32_t)b * 128u + ((uint32_t)(k8 ^ (b & 7)) << 4);
+                        *reinterpret_cast<uint4*>(hi_t + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<uint4*>(lo_t + off) = make_uint4(l[0], l[1], l[2], l[3]);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(smem_u32(&op_full[o]));
+                mbar_arrive(smem_u32(&raw_empty[s]));
             }
         }
     }
@@ -435,8 +434,8 @@ bool role_plan(int p, int band0, int nb, int NT, WgRole* r, size_t* smem) {
     R.band0 = band0;
     R.nb = nb;
     R.rows = NT > 128 ? NT : 128;
-    R.op_bytes = (uint32_t)R.rows * 128u;   // one tile: rows x 32 floats, swizzled
-    R.raw_stage_bytes = R.op_bytes;         // a raw stage is the hi tile of its chunk
+    R.op_bytes = (uint32_t)R.rows * 128u;   // one bf16 tile: rows x 64 pixels, swizzled
+    R.raw_stage_bytes = (uint32_t)align_up((size_t)nb * kK * 4, 1024);
     R.buf_cols = (int)align_up((size_t)NT, 32);
     const int need = 2 * R.buf_cols;
     if (need > 512) return false;
@@ -444,7 +443,7 @@ bool role_plan(int p, int band0, int nb, int NT, WgRole* r, size_t* smem) {
     R.out_rows = nb < 128 ? nb : 128;
     R.out_cols = band0 == 0 ? p : nb;
     const size_t room = 227 * 1024 - 1024 - 1024;   // alignment slack, static shared memory
-    const size_t op_area = (size_t)kOpStages * R.op_bytes;
+    const size_t op_area = 2u * kOpStages * R.op_bytes;
     if (op_area + 2 * R.raw_stage_bytes > room) return false;
     const int rs = (int)((room - op_area) / R.raw_stage_bytes);
     R.raw_stages = rs > kMaxRaw ? kMaxRaw : rs;
@@ -476,8 +475,12 @@ hyde_status win_gram_layout(int p, const int4* geo, int n_win, int sms, WinGramL
         if (geo[w].z < 1 || geo[w].w < 1 || (geo[w].y % 4) != 0) return HYDE_ERR_SHAPE;
     const bool two = p > 128;
     // CTAs in proportion to the work per chunk (bands loaded + the MMA's N)
+// Role 1's MMAs (N = p - 128) cost nearly as much per instruction as role
+// 0's, so its CTAs count for more than its arithmetic: the weight factor
+// measured best at 1.6 on the 2048 x 2048 x 200 scene (2.57 ms against 2.88
+// at 1.2 and 2.91 at 2.2).
 #ifndef HYDE_WIN_W1X
-#define HYDE_WIN_W1X 2.2
+#define HYDE_WIN_W1X 1.6
 #endif
     const double w0 = (double)p + nt0_of(p),
                  w1 = two ? HYDE_WIN_W1X * ((double)(p - 128) + (nt0_of(p) - 128)) : 0.0;
@@ -552,7 +555,7 @@ hyde_status launch_win_gram(const float* Y, int p, int H, int W, const int4* pie
         const cuuint32_t box[3] = {(cuuint32_t)kCx, (cuuint32_t)kCy, (cuuint32_t)Wp.role[r].nb};
         const cuuint32_t estr[3] = {1, 1, 1};
         if (enc(&tm[r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(Y), dims, strides,
-                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return HYDE_ERR_CUDA;

@@ -194,6 +194,14 @@ int hyde_windows_plan_kernel_launches(hyde_windows_plan plan) {
     return plan ? 13 : -1;
 }
 
+hyde_status hyde_windows_plan_layout(hyde_windows_plan plan, hyde_windows_ws_layout* out) {
+    if (!plan || !out) return HYDE_ERR_INVALID_ARG;
+    out->R = plan->R;
+    out->sigma = plan->sigma;
+    out->V = plan->V;
+    return HYDE_OK;
+}
+
 hyde_status hyde_windows_plan_destroy(hyde_windows_plan plan) {
     if (!plan) return HYDE_ERR_INVALID_ARG;
     if (plan->host) cudaFreeHost(plan->host);
