@@ -482,25 +482,57 @@ def _form_wsrrr(args, dev, cube, flush, stream) -> dict:
 
 def _form_windows(args, dev, cube, flush, stream) -> dict:
     """Batched sliding-window form: a 2048 x 2048 x 200 scene in 512 uneven
-    windows, one captured CUDA graph per scene."""
+    windows, every stage one launch over all windows (the plan API), replayed
+    from one captured CUDA graph; the per-window pipelines on 64 streams
+    (hyde_hyres_denoise_windows) beside it, and the error of sampled windows
+    against the FP64 oracle."""
+    import numpy as np
     import torch
+    import oracle as O
     from paper_2204_06979_gb300 import api
     from synth import make_scene, make_window_table
     H = W = 2048
     p, L, r = 200, 3, 20
     T = make_window_table(H, W, depth=9, context=16, min_side=32, max_side=224, seed=4)
     sc = make_scene(H, W, p, T, m=12, seed=4)
-    Y = torch.from_numpy(sc["Y"]).to(dev)
-    del sc
+    Yh = sc["Y"]
+    Y = torch.from_numpy(Yh).to(dev)
     X = torch.zeros_like(Y)
-    win = api.HyResWindows(p, H, W, T, L, r, n_slots=64, device=dev)
+    win = api.HyResWindowsBatched(p, H, W, T, L, r, device=dev)
     win.capture(Y, X)
     out = _time_form(win.replay, args, flush, stream, p * H * W)
+    torch.cuda.synchronize(dev)
     infos = win.infos()
     out.update({"workload": "2048x2048x200 scene, 512 windows (sides 48..256, 16-px context), "
-                            "per-core SNR U[5,20] dB, db2 L=3, r<=20, one CUDA graph per scene",
+                            "per-core SNR U[5,20] dB, db2 L=3, r<=20; 13 kernels over all "
+                            "windows, one CUDA graph per scene",
                 "statuses_ok": int(sum(i["status"] == 0 for i in infos)),
-                "windows": len(T)})
+                "windows": len(T), "gpu_launches": win.kernel_launches,
+                "l2": "the scene (3.4 GB) exceeds L2; no flush"})
+    if not args.no_parity:
+        areas = T[:, 2] * T[:, 3]
+        picks = sorted({int(np.argmin(areas)), int(np.argmax(areas)), 16, 200, 400})
+        got_all = X.cpu().numpy()
+        num = den = 0.0
+        same = 0
+        for k in picks:
+            y0, x0, h, w, cy, cx, ch, cw = (int(v) for v in T[k])
+            o = O.hyres(Yh[:, y0:y0 + h, x0:x0 + w], L, r)
+            ref = o["X"][:, cy - y0:cy - y0 + ch, cx - x0:cx - x0 + cw]
+            got = got_all[:, cy:cy + ch, cx:cx + cw].astype(np.float64)
+            num += float(np.sum((got - ref) ** 2))
+            den += float(np.sum(ref ** 2))
+            same += int((infos[k]["rank"], infos[k]["lambda_index"]) == (o["rank"], o["k"]))
+        out.update({"parity_windows": picks, "rel_l2_vs_oracle": float(np.sqrt(num / den)),
+                    "identical_choice": f"{same}/{len(picks)}"})
+    del win
+    # the per-window pipelines (one single-cube pipeline per window, 64 streams)
+    slots = api.HyResWindows(p, H, W, T, L, r, n_slots=64, device=dev)
+    X2 = torch.zeros_like(Y)
+    slots.capture(Y, X2)
+    o2 = _time_form(slots.replay, args, flush, stream, p * H * W)
+    out["per_window_pipelines"] = {"ms": o2["ms"], "Mvoxel/s": o2["Mvoxel/s"],
+                                   "step_ms": o2["step_ms"]}
     return out
 
 
@@ -854,13 +886,16 @@ def run_form(args) -> None:
         sc = make_scene(H, W, p, T, m=12, seed=4)
         Y = torch.from_numpy(sc["Y"]).to(dev)
         X = torch.zeros_like(Y)
-        win = api.HyResWindows(p, H, W, T, L, r, n_slots=args.slots, device=dev)
+        if args.slots > 0:   # the per-window pipelines on that many streams
+            win = api.HyResWindows(p, H, W, T, L, r, n_slots=args.slots, device=dev)
+        else:                # every stage one launch over all windows
+            win = api.HyResWindowsBatched(p, H, W, T, L, r, device=dev)
         win.capture(Y, X)
         with clocks:
             ms = _timed_steps(win.replay, args.steps, args.warmup, flush, stream)
         voxels = p * H * W
         infos = win.infos()
-        extra = {"windows": len(T), "slots": win.n_slots,
+        extra = {"windows": len(T), "slots": args.slots if args.slots > 0 else "batched",
                  "window_sides": [int(T[:, 2:4].min()), int(T[:, 2:4].max())],
                  "statuses_ok": int(sum(i["status"] == 0 for i in infos)),
                  "ranks": [int(min(i["rank"] for i in infos)), int(max(i["rank"] for i in infos))]}
@@ -984,7 +1019,9 @@ def main() -> None:
                     help="timed steps of each secondary form in the plain run")
     ap.add_argument("--form", choices=("plain", "windows", "diff"), default="plain",
                     help="plain: the headline workload; windows / diff: secondary forms")
-    ap.add_argument("--slots", type=int, default=64, help="window slots (--form windows)")
+    ap.add_argument("--slots", type=int, default=0,
+                    help="--form windows: 0 runs every stage once over all windows (the "
+                         "batched plan); n > 0 the per-window pipelines on n streams")
     ap.add_argument("--sm-cap", type=int, default=None,
                     help="--form diff: SMs each cube's grids are sized for (0: all; "
                          "default: the batch API's choice)")

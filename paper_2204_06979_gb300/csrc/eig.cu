@@ -285,7 +285,8 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
     }
     __syncthreads();
     const float scale = s_scale;
-    for (int i = wid; i < p; i += 32) {
+    const int nwarps = (int)(blockDim.x >> 5);
+    for (int i = wid; i < p; i += nwarps) {
         const float si = iw[i] * scale;
         for (int j = lane; j < p; j += 32)
             A[i * lda + j] = d2f_bits(Ain[(long long)i * p + j]) * si * iw[j];
@@ -445,7 +446,7 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
     __syncthreads();
     // reflector k as an explicit vector in row k: 0 up to k, 1 at k+1,
     // x * scale beyond (the back-transformation then reads it directly)
-    for (int k = wid; k < p - 2; k += 32) {
+    for (int k = wid; k < p - 2; k += nwarps) {
         const float sck = scv[k];
         for (int i = lane; i < p; i += 32) {
             float* a = A + k * lda + i;
@@ -466,7 +467,7 @@ eig_tridiag_kernel(const double* __restrict__ Ain, const double* __restrict__ ws
     __syncthreads();
     // write-out: T, the reflectors as rows (row k of A, already explicit),
     // tau and the scale
-    for (int k = wid; k < p - 2; k += 32)
+    for (int k = wid; k < p - 2; k += nwarps)
         for (int i = lane; i < p; i += 32) G.refl[(size_t)k * p + i] = A[k * lda + i];
     for (int i = t; i < p; i += blockDim.x) {
         G.d[i] = dv[i];
@@ -1044,53 +1045,17 @@ eig_pair_kernel(EigWs G, int p, int* status, long long wst) {
 
 // --------------------------------------------------------------------------
 // 2b. All r eigenpairs of a window in one block (the batched window form,
-// one block per window): warp w takes eigenpairs c = w, w + 8, ... (at most
-// four). Their eigenvalues by multisection with 32 points per round (lane j
-// counts at point j + 1 of 33, the counts of the warp's eigenvalues
-// interleaved in one pass over T), the eigenvectors of T by the twisted
+// one block per window): the eigenvalues by multisection, eight points per
+// eigenvalue and round (four eigenvalues per warp; with 33 points per
+// eigenvalue and four Sturm chains interleaved per lane the multisection took
+// 711k of the kernel's ~1M cycles per window), then warp w takes eigenpairs
+// c = w, w + 8, ... (at most four): the eigenvectors of T by the twisted
 // factorisation as in eig_pair_kernel, and the back-transformation by the
 // same compact-WY blocks, built once per window by all warps and applied by
 // each warp to its vectors together (one load of a reflector block for all
 // of them). The reflectors are read through L2.
 // --------------------------------------------------------------------------
 constexpr int kAllThreads = 256, kAllWarps = kAllThreads / 32, kMaxPerWarp = 4;
-
-// Sturm counts of T - x_q I for NQ points at once (sturm_count_poly's
-// recurrence and rescaling, one pass over d and e2).
-template <int NQ>
-__device__ __forceinline__ void sturm_counts(const float* d, const float* e2, int p,
-                                             const float (&x)[NQ], int (&c)[NQ]) {
-    float Pm[NQ], P[NQ];
-    bool sg[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        Pm[q] = 1.0f;
-        P[q] = d[0] - x[q];
-        sg[q] = !(P[q] > 0.f);
-        c[q] = sg[q];
-    }
-#pragma unroll 2
-    for (int i = 1; i < p; ++i) {
-        const float ee = e2[i - 1], di = d[i];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const float t = ee * Pm[q];
-            const float Pn = fmaf(di - x[q], P[q], -t);
-            const bool sn = Pn < 0.f || (Pn == 0.f && !sg[q]);
-            c[q] += sn != sg[q];
-            sg[q] = sn;
-            Pm[q] = P[q];
-            P[q] = Pn;
-            if (i & 1) {
-                const float m = fmaxf(fabsf(P[q]), fabsf(Pm[q]));
-                const int ex = min((__float_as_int(m) >> 23) & 255, 254);
-                const float sc = __int_as_float((254 - ex) << 23);
-                P[q] *= sc;
-                Pm[q] *= sc;
-            }
-        }
-    }
-}
 
 size_t eig_pairs_all_bytes(int p, int r) {
     return ((size_t)4 * p + (size_t)3 * kAllWarps * p + (size_t)r * p) * sizeof(float);
@@ -1147,57 +1112,48 @@ eig_pairs_all_kernel(EigWs G, int p, int r, int* status, long long wst) {
     }
     __syncthreads();
     const float pivmin = s_pivmin;
-    // multisection of the warp's eigenvalues (c = wid + 8 k, the (p - c)-th
-    // smallest); each round keeps the one of 33 sub-intervals that holds it
-    float lo[kMaxPerWarp], hi[kMaxPerWarp];
-    bool act[kMaxPerWarp];
-#pragma unroll
-    for (int k = 0; k < kMaxPerWarp; ++k) {
-        lo[k] = s_lo;
-        hi[k] = s_hi;
-        act[k] = wid + kAllWarps * k < r;
-    }
-    for (int it = 0; it < 24; ++it) {   // 24 rounds of 33x exceed float resolution
-        float x[kMaxPerWarp];
-        int cnt[kMaxPerWarp];
-#pragma unroll
-        for (int k = 0; k < kMaxPerWarp; ++k)
-            x[k] = lo[k] + (hi[k] - lo[k]) * (float)(lane + 1) / 33.f;
-        sturm_counts<kMaxPerWarp>(d, e2, p, x, cnt);
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < kMaxPerWarp; ++k) {
-            const int target = p - 1 - (wid + kAllWarps * k);
-            const int nle = __popc(__ballot_sync(0xffffffffu, cnt[k] <= target));
-            if (act[k]) {
-                const float xl = lo[k] + (hi[k] - lo[k]) * (float)nle / 33.f;
-                const float xh = lo[k] + (hi[k] - lo[k]) * (float)(nle + 1) / 33.f;
-                const float nlo = nle > 0 ? xl : lo[k];
-                const float nhi = nle < 32 ? xh : hi[k];
-                if (!(nlo < nhi) || (nhi - nlo) >= (hi[k] - lo[k])) {
-                    act[k] = false;
+    // multisection: eigenvalue slot c = 4 wid + (lane / 8) (the (p - c)-th
+    // smallest) is searched by the eight lanes of its octet, lane j counting
+    // at point j + 1 of 9 of the slot's interval; each round keeps the one of
+    // nine sub-intervals that holds it. One Sturm count per lane and round.
+    __shared__ float s_lam[kAllWarps * 4];
+    {
+        const int c = 4 * wid + (lane >> 3), j = lane & 7;
+        const int target = p - 1 - c;
+        float lo = s_lo, hi = s_hi;
+        bool act = c < r;
+        for (int it = 0; it < 48; ++it) {   // 48 rounds of 9x exceed float resolution
+            const float x = lo + (hi - lo) * (float)(j + 1) / 9.f;
+            const int cnt = sturm_count_poly(d, e2, p, x);
+            const unsigned bal = __ballot_sync(0xffffffffu, cnt <= target);
+            const int nle = __popc((bal >> (lane & ~7)) & 0xffu);
+            if (act) {
+                const float xl = lo + (hi - lo) * (float)nle / 9.f;
+                const float xh = lo + (hi - lo) * (float)(nle + 1) / 9.f;
+                const float nlo = nle > 0 ? xl : lo;
+                const float nhi = nle < 8 ? xh : hi;
+                if (!(nlo < nhi) || (nhi - nlo) >= (hi - lo)) {
+                    act = false;
                 } else {
-                    lo[k] = nlo;
-                    hi[k] = nhi;
-                    if (hi[k] - lo[k] <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo[k]), fabsf(hi[k])))
-                        act[k] = false;
+                    lo = nlo;
+                    hi = nhi;
+                    if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi))) act = false;
                 }
             }
-            any |= act[k];
+            if (!__any_sync(0xffffffffu, act)) break;
         }
-        if (!any) break;
+        if (j == 0) s_lam[c] = 0.5f * (lo + hi);
     }
+    __syncthreads();
     // eigenvectors of T by the twisted factorisation, one at a time per warp
     float* Dp = wsc + 3 * wid * p;
     float* Dm = Dp + p;
     float* rat = Dm + p;
-    float lamk[kMaxPerWarp];
 #pragma unroll
     for (int k = 0; k < kMaxPerWarp; ++k) {
-        lamk[k] = 0.5f * (lo[k] + hi[k]);
         const int c = wid + kAllWarps * k;
         if (c >= r) continue;   // warp-uniform
-        const float lam = lamk[k];
+        const float lam = s_lam[c];
         if (lane < 2) {
             const bool fwd = lane == 0;
             float* D = fwd ? Dp : Dm;
@@ -1362,7 +1318,7 @@ eig_pairs_all_kernel(EigWs G, int p, int r, int* status, long long wst) {
             const int i = lane + 32 * b;
             if (i < p) G.X[(size_t)c * p + i] = x[k][b] * inv;
         }
-        if (lane == 0) G.lam[c] = lamk[k];
+        if (lane == 0) G.lam[c] = s_lam[c];
     }
 }
 
@@ -1504,8 +1460,11 @@ hyde_status launch_tridiag(const double* A, const double* wsig, int p, EigWs G, 
         if (ensure_smem_limit((const void*)eig_tridiag_kernel<NB, kEigWarps>, (int)st) !=
             cudaSuccess)
             return HYDE_ERR_SHAPE;
-        launch_pdl(eig_tridiag_kernel<NB, kEigWarps>, dim3(1, n_win), kLA, st, s, A, wsig, p, G,
-                   status, wst);
+        // only the kEigWarps sweep warps work after the load: many windows at
+        // once launch just those, so that the block leaves half the SM's
+        // registers to other kernels' blocks
+        launch_pdl(eig_tridiag_kernel<NB, kEigWarps>, dim3(1, n_win), n_win > 1 ? 32 * kEigWarps : kLA,
+                   st, s, A, wsig, p, G, status, wst);
     }
     return HYDE_OK;
 }

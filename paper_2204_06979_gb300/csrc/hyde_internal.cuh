@@ -372,7 +372,7 @@ hyde_status launch_win_dwt(const float* Zp, float* coef, float* scratch, const W
 hyde_status launch_win_sure(const float* coef, const WinDesc* desc, int n_win, int r,
                             int levels, int K, unsigned int* counts, double* sums,
                             double* sum_all, int* rank, double* lam, hyde_hyres_info* info,
-                            int* status, cudaStream_t s);
+                            int* status, const int* gstatus, cudaStream_t s);
 hyde_status launch_win_idwt(const float* coef, float* Zh, float* scratch, const WinDesc* desc,
                             int n_win, int r, int levels, const int* rank, const double* lam,
                             cudaStream_t s);

@@ -240,19 +240,32 @@ win_project_kernel(const float* __restrict__ Y, int p, int H, int W,
         for (int u = 0; u < kPix; ++u)
 #pragma unroll
             for (int i = 0; i < RM; ++i) acc[u][i] = 0.f;
-        int b = 0;
-        for (; b + kBandGroup <= p; b += kBandGroup) {
-            float v[kBandGroup][kPix];
+        // the loads of band group g + 1 are issued before the FMAs of group g
+        const int pg = p - p % kBandGroup;
+        float v[kBandGroup][kPix];
+        if (pg > 0) {
+#pragma unroll
+            for (int g = 0; g < kBandGroup; ++g)
+#pragma unroll
+                for (int u = 0; u < kPix; ++u) v[g][u] = __ldg(Yw + (long long)g * bs + src[u]);
+        }
+        for (int b0 = 0; b0 < pg; b0 += kBandGroup) {
+            float nv[kBandGroup][kPix];
+            const int bn = b0 + kBandGroup < pg ? b0 + kBandGroup : b0;   // last group: reload
 #pragma unroll
             for (int g = 0; g < kBandGroup; ++g)
 #pragma unroll
                 for (int u = 0; u < kPix; ++u)
-                    v[g][u] = __ldg(Yw + (long long)(b + g) * bs + src[u]);
+                    nv[g][u] = __ldg(Yw + (long long)(bn + g) * bs + src[u]);
 #pragma unroll
             for (int g = 0; g < kBandGroup; ++g)
-                project_fma<RM>(acc, v[g], Ps4 + (b + g) * (RM / 4));
+                project_fma<RM>(acc, v[g], Ps4 + (b0 + g) * (RM / 4));
+#pragma unroll
+            for (int g = 0; g < kBandGroup; ++g)
+#pragma unroll
+                for (int u = 0; u < kPix; ++u) v[g][u] = nv[g][u];
         }
-        for (; b < p; ++b) {
+        for (int b = pg; b < p; ++b) {
             float vt[kPix];
 #pragma unroll
             for (int u = 0; u < kPix; ++u) vt[u] = __ldg(Yw + (long long)b * bs + src[u]);

@@ -340,7 +340,7 @@ hyde_status launch_win_dwt(const float* Zp, float* coef, float* scratch, const W
 hyde_status launch_win_sure(const float* coef, const WinDesc* desc, int n_win, int r,
                             int levels, int K, unsigned int* counts, double* sums,
                             double* sum_all, int* rank, double* lam, hyde_hyres_info* info,
-                            int* status, cudaStream_t s) {
+                            int* status, const int* gstatus, cudaStream_t s) {
     if (n_win < 1 || n_win > 65535 || r < 1 || r > kMaxRank || K < 2 || K > kWdThreads)
         return HYDE_ERR_SHAPE;
     const size_t smem = (size_t)2 * K * 32 * sizeof(unsigned int);
@@ -348,9 +348,8 @@ hyde_status launch_win_sure(const float* coef, const WinDesc* desc, int n_win, i
         return HYDE_ERR_CUDA;
     launch_pdl(win_sure_hist_kernel, dim3(r, n_win), kWdThreads, smem, s, coef, desc, r, levels,
                K, counts, sums, sum_all);
-    // status[n_win] is the call's own word (the Gram kernel's timeout)
     launch_pdl(win_sure_select_kernel, n_win, kWdThreads, 0, s, counts, sums, sum_all, desc, r,
-               levels, K, rank, lam, info, status, status + n_win);
+               levels, K, rank, lam, info, status, gstatus);
     return cuda_status(cudaGetLastError());
 }
 

@@ -5,8 +5,13 @@
 // window, the Gram pieces, the tile tables of the projections) and a
 // workspace layout. It keeps the tables in page-locked host memory; each call
 // copies them into the workspace on the caller's stream and then launches
-// every stage once over all windows, so that a call is one capturable
-// sequence of 13 kernels whatever the number of windows.
+// every stage once per group of windows. The windows form two groups, each
+// run on its own stream (the caller's and one the plan owns, forked and
+// joined with events): the one-block-per-window stages of one group (the
+// Gauss-Jordan inverse, the tridiagonalisation, the eigenpairs, all bound by
+// the latency of one SM) then share the SMs with the bandwidth- and
+// tensor-bound stages of the other. A call is one capturable sequence of 26
+// kernels whatever the number of windows.
 #include <math.h>
 #include <string.h>
 
@@ -16,15 +21,31 @@
 
 using namespace hyde;
 
-struct hyde_windows_plan_s {
-    int p, H, W, n_win, r, L, K, RM;
+#ifndef HYDE_WIN_GROUPS
+#define HYDE_WIN_GROUPS 2
+#endif
+namespace {
+constexpr int kGroups = HYDE_WIN_GROUPS;
+}
+
+struct WinGroup {
+    int w0, n;                       // windows [w0, w0 + n)
     int G0, G1, proj_tiles, back_tiles;
+    size_t pieces, pbeg, wslot0, wslot1, tproj, tback;   // table offsets
+    size_t part0, part1;             // its Gram partials
+};
+
+struct hyde_windows_plan_s {
+    int p, H, W, n_win, r, L, K, RM, ngroups;
+    WinGroup g[kGroups];
     void* host;              // page-locked copy of the tables
     size_t tables;           // their bytes (the head of the workspace)
+    cudaStream_t side;       // the second group's stream
+    cudaEvent_t fork, join;
     // workspace offsets
-    size_t desc, geo, pieces, pbeg, wslot0, wslot1, tproj, tback;
+    size_t desc, geo;
     size_t status, R, sigma, Ainv, S, eig, eig_stride, evals, V, P, Q;
-    size_t zp, coef, scr, counts, sums, sum_all, rank, lam, part0, part1, total;
+    size_t zp, coef, scr, counts, sums, sum_all, rank, lam, total;
 };
 
 namespace {
@@ -120,26 +141,51 @@ hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win
     }
     const int sms = device_sm_count();
     if (sms <= 0) return HYDE_ERR_CUDA;
-    WinGramLayout G;
-    hyde_status st = win_gram_layout(p, geo.data(), n_win, sms, &G);
-    if (st != HYDE_OK) return st;
+    const int ngroups = n_win >= kGroups ? kGroups : 1;
+    // groups of consecutive windows with about equal pixel counts
+    int wb[kGroups + 1] = {0};
+    {
+        long long tot = 0;
+        for (int k = 0; k < n_win; ++k) tot += (long long)win[k].h * win[k].w;
+        long long acc = 0;
+        int gi = 1;
+        for (int k = 0; k < n_win && gi < ngroups; ++k) {
+            acc += (long long)win[k].h * win[k].w;
+            if (acc * ngroups >= tot * gi && k + 1 < n_win) wb[gi++] = k + 1;
+        }
+        for (; gi < ngroups; ++gi) wb[gi] = wb[gi - 1] + 1;
+        wb[ngroups] = n_win;
+    }
+    WinGramLayout GL[kGroups];
+    for (int gi = 0; gi < ngroups; ++gi) {
+        hyde_status st = win_gram_layout(p, geo.data() + wb[gi], wb[gi + 1] - wb[gi], sms, &GL[gi]);
+        if (st != HYDE_OK) return st;
+    }
 
     hyde_windows_plan_s* P = new hyde_windows_plan_s();
     P->p = p; P->H = H; P->W = W; P->n_win = n_win; P->r = r; P->L = L; P->K = K;
     P->RM = (r + 3) / 4 * 4;
-    P->G0 = G.G0; P->G1 = G.G1;
-    P->proj_tiles = tproj[n_win];
-    P->back_tiles = tback[n_win];
+    P->ngroups = ngroups;
     const size_t n = (size_t)n_win, pp = (size_t)p * p;
     Carve c;
     P->desc = c.take(n * sizeof(WinDesc));
     P->geo = c.take(n * sizeof(int4));
-    P->pieces = c.take(G.pieces.size() * sizeof(int4));
-    P->pbeg = c.take(G.pbeg.size() * sizeof(int));
-    P->wslot0 = c.take((n + 1) * sizeof(int));
-    P->wslot1 = c.take((n + 1) * sizeof(int));
-    P->tproj = c.take((n + 1) * sizeof(int));
-    P->tback = c.take((n + 1) * sizeof(int));
+    for (int gi = 0; gi < ngroups; ++gi) {
+        WinGroup& g = P->g[gi];
+        const WinGramLayout& G = GL[gi];
+        g.w0 = wb[gi];
+        g.n = wb[gi + 1] - wb[gi];
+        g.G0 = G.G0;
+        g.G1 = G.G1;
+        g.proj_tiles = tproj[wb[gi + 1]] - tproj[wb[gi]];
+        g.back_tiles = tback[wb[gi + 1]] - tback[wb[gi]];
+        g.pieces = c.take(G.pieces.size() * sizeof(int4));
+        g.pbeg = c.take(G.pbeg.size() * sizeof(int));
+        g.wslot0 = c.take((g.n + 1) * sizeof(int));
+        g.wslot1 = c.take((g.n + 1) * sizeof(int));
+        g.tproj = c.take((g.n + 1) * sizeof(int));
+        g.tback = c.take((g.n + 1) * sizeof(int));
+    }
     P->tables = c.off;
     P->status = c.take((n + 1) * sizeof(int));
     P->R = c.take(n * pp * sizeof(double));
@@ -160,24 +206,42 @@ hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win
     P->sum_all = c.take(n * r * sizeof(double));
     P->rank = c.take(n * sizeof(int));
     P->lam = c.take(n * sizeof(double));
-    P->part0 = c.take((G.part0_floats > 0 ? G.part0_floats : 4) * sizeof(float));
-    P->part1 = c.take((G.part1_floats > 0 ? G.part1_floats : 4) * sizeof(float));
+    for (int gi = 0; gi < ngroups; ++gi) {
+        P->g[gi].part0 = c.take((GL[gi].part0_floats > 0 ? GL[gi].part0_floats : 4) * sizeof(float));
+        P->g[gi].part1 = c.take((GL[gi].part1_floats > 0 ? GL[gi].part1_floats : 4) * sizeof(float));
+    }
     P->total = c.off;
 
     if (cudaMallocHost(&P->host, P->tables) != cudaSuccess) {
         delete P;
         return HYDE_ERR_CUDA;
     }
+    if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming) != cudaSuccess) {
+        hyde_windows_plan_destroy(P);
+        return HYDE_ERR_CUDA;
+    }
     memset(P->host, 0, P->tables);
     memcpy(at<char>(P->host, P->desc), D.data(), n * sizeof(WinDesc));
     memcpy(at<char>(P->host, P->geo), geo.data(), n * sizeof(int4));
-    if (!G.pieces.empty())
-        memcpy(at<char>(P->host, P->pieces), G.pieces.data(), G.pieces.size() * sizeof(int4));
-    memcpy(at<char>(P->host, P->pbeg), G.pbeg.data(), G.pbeg.size() * sizeof(int));
-    memcpy(at<char>(P->host, P->wslot0), G.wslot0.data(), (n + 1) * sizeof(int));
-    memcpy(at<char>(P->host, P->wslot1), G.wslot1.data(), (n + 1) * sizeof(int));
-    memcpy(at<char>(P->host, P->tproj), tproj.data(), (n + 1) * sizeof(int));
-    memcpy(at<char>(P->host, P->tback), tback.data(), (n + 1) * sizeof(int));
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const WinGroup& g = P->g[gi];
+        const WinGramLayout& G = GL[gi];
+        if (!G.pieces.empty())
+            memcpy(at<char>(P->host, g.pieces), G.pieces.data(), G.pieces.size() * sizeof(int4));
+        memcpy(at<char>(P->host, g.pbeg), G.pbeg.data(), G.pbeg.size() * sizeof(int));
+        memcpy(at<char>(P->host, g.wslot0), G.wslot0.data(), (g.n + 1) * sizeof(int));
+        memcpy(at<char>(P->host, g.wslot1), G.wslot1.data(), (g.n + 1) * sizeof(int));
+        // tile tables relative to the group's first window
+        std::vector<int> tp(g.n + 1), tb(g.n + 1);
+        for (int k = 0; k <= g.n; ++k) {
+            tp[k] = tproj[g.w0 + k] - tproj[g.w0];
+            tb[k] = tback[g.w0 + k] - tback[g.w0];
+        }
+        memcpy(at<char>(P->host, g.tproj), tp.data(), (g.n + 1) * sizeof(int));
+        memcpy(at<char>(P->host, g.tback), tb.data(), (g.n + 1) * sizeof(int));
+    }
     *out = P;
     return HYDE_OK;
 }
@@ -189,9 +253,9 @@ hyde_status hyde_windows_plan_workspace_size(hyde_windows_plan plan, size_t* byt
 }
 
 int hyde_windows_plan_kernel_launches(hyde_windows_plan plan) {
-    // Gram 2, noise 1, eigensolver 3, weights 1, projection 1, DWT 1,
-    // SURE 2, inverse DWT 1, back-projection 1
-    return plan ? 13 : -1;
+    // per group: Gram 2, noise 1, eigensolver 3, weights 1, projection 1,
+    // DWT 1, SURE 2, inverse DWT 1, back-projection 1
+    return plan ? 13 * plan->ngroups : -1;
 }
 
 hyde_status hyde_windows_plan_layout(hyde_windows_plan plan, hyde_windows_ws_layout* out) {
@@ -205,7 +269,55 @@ hyde_status hyde_windows_plan_layout(hyde_windows_plan plan, hyde_windows_ws_lay
 hyde_status hyde_windows_plan_destroy(hyde_windows_plan plan) {
     if (!plan) return HYDE_ERR_INVALID_ARG;
     if (plan->host) cudaFreeHost(plan->host);
+    if (plan->side) cudaStreamDestroy(plan->side);
+    if (plan->fork) cudaEventDestroy(plan->fork);
+    if (plan->join) cudaEventDestroy(plan->join);
     delete plan;
+    return HYDE_OK;
+}
+
+// One group's stages on stream s: per-window arrays from the group's first
+// window on, its own Gram pieces, partials and tile tables.
+static hyde_status enqueue_group(const hyde_windows_plan_s* P, const WinGroup& g, const float* Y,
+                                 float* X, hyde_hyres_info* info, void* ws, cudaStream_t s) {
+    const int p = P->p, n = g.n, r = P->r, w0 = g.w0;
+    const size_t pp = (size_t)p * p;
+    const WinDesc* desc = at<WinDesc>(ws, P->desc) + w0;
+    int* status = at<int>(ws, P->status) + w0;
+    int* gstatus = at<int>(ws, P->status) + P->n_win;
+    float* zp = at<float>(ws, P->zp);
+    float* coef = at<float>(ws, P->coef);
+    float* scr = at<float>(ws, P->scr);
+    int* rank = at<int>(ws, P->rank) + w0;
+    double* lam = at<double>(ws, P->lam) + w0;
+    double* R = at<double>(ws, P->R) + w0 * pp;
+    double* sigma = at<double>(ws, P->sigma) + (size_t)w0 * p;
+    double* V = at<double>(ws, P->V) + (size_t)w0 * p * r;
+    float* Pw = at<float>(ws, P->P) + (size_t)w0 * p * P->RM;
+    float* Qw = at<float>(ws, P->Q) + (size_t)w0 * p * P->RM;
+#define HYDE_TRY(x) do { hyde_status s_ = (x); if (s_ != HYDE_OK) return s_; } while (0)
+    HYDE_TRY(launch_win_gram(Y, p, P->H, P->W, at<int4>(ws, g.pieces), at<int>(ws, g.pbeg),
+                             at<int4>(ws, P->geo) + w0, at<int>(ws, g.wslot0),
+                             at<int>(ws, g.wslot1), n, g.G0, g.G1, at<float>(ws, g.part0),
+                             at<float>(ws, g.part1), R, gstatus, s));
+    HYDE_TRY(launch_win_noise(R, p, n, desc, sigma, at<float>(ws, P->Ainv) + w0 * pp,
+                              at<double>(ws, P->S) + (size_t)w0 * p, status, s));
+    HYDE_TRY(launch_eig_top_batched(R, sigma, p, r, at<double>(ws, P->evals) + (size_t)w0 * r, V,
+                                    at<char>(ws, P->eig) + (size_t)w0 * P->eig_stride,
+                                    P->eig_stride, status, n, s));
+    HYDE_TRY(launch_weights_batched(V, sigma, p, r, P->RM, Pw, Qw, n, s));
+    HYDE_TRY(launch_win_project(Y, p, P->H, P->W, desc, at<int>(ws, g.tproj), n, g.proj_tiles,
+                                Pw, r, P->RM, zp, s));
+    HYDE_TRY(launch_win_dwt(zp, coef, scr, desc, n, r, P->L, s));
+    HYDE_TRY(launch_win_sure(coef, desc, n, r, P->L, P->K,
+                             at<unsigned int>(ws, P->counts) + (size_t)w0 * r * P->K,
+                             at<double>(ws, P->sums) + (size_t)w0 * r * P->K,
+                             at<double>(ws, P->sum_all) + (size_t)w0 * r, rank, lam,
+                             info ? info + w0 : nullptr, status, gstatus, s));
+    HYDE_TRY(launch_win_idwt(coef, zp, scr, desc, n, r, P->L, rank, lam, s));
+    HYDE_TRY(launch_win_backproject(zp, desc, at<int>(ws, g.tback), n, g.back_tiles, Qw, p,
+                                    P->RM, rank, P->H, P->W, X, s));
+#undef HYDE_TRY
     return HYDE_OK;
 }
 
@@ -215,43 +327,22 @@ hyde_status hyde_hyres_denoise_windows_batched(const float* Y, float* X, hyde_wi
     if (!Y || !X || Y == X || !P) return HYDE_ERR_INVALID_ARG;
     if (((uintptr_t)Y % 16) != 0 || ((uintptr_t)X % 4) != 0) return HYDE_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < P->total) return HYDE_ERR_WORKSPACE;
-    const int p = P->p, n = P->n_win, r = P->r;
-    const WinDesc* desc = at<WinDesc>(ws, P->desc);
     int* status = at<int>(ws, P->status);
-    float* zp = at<float>(ws, P->zp);
-    float* coef = at<float>(ws, P->coef);
-    float* scr = at<float>(ws, P->scr);
-    int* rank = at<int>(ws, P->rank);
-    double* lam = at<double>(ws, P->lam);
-    double* R = at<double>(ws, P->R);
-    double* sigma = at<double>(ws, P->sigma);
-    double* V = at<double>(ws, P->V);
-    float* Pw = at<float>(ws, P->P);
-    float* Qw = at<float>(ws, P->Q);
-#define HYDE_TRY(x) do { hyde_status s_ = (x); if (s_ != HYDE_OK) return s_; } while (0)
     if (cudaMemcpyAsync(ws, P->host, P->tables, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(status, 0, (size_t)(n + 1) * sizeof(int), s) != cudaSuccess)
+        cudaMemsetAsync(status, 0, (size_t)(P->n_win + 1) * sizeof(int), s) != cudaSuccess)
         return HYDE_ERR_CUDA;
-    HYDE_TRY(launch_win_gram(Y, p, P->H, P->W, at<int4>(ws, P->pieces), at<int>(ws, P->pbeg),
-                             at<int4>(ws, P->geo), at<int>(ws, P->wslot0),
-                             at<int>(ws, P->wslot1), n, P->G0, P->G1, at<float>(ws, P->part0),
-                             at<float>(ws, P->part1), R, status + n, s));
-    HYDE_TRY(launch_win_noise(R, p, n, desc, sigma, at<float>(ws, P->Ainv), at<double>(ws, P->S),
-                              status, s));
-    HYDE_TRY(launch_eig_top_batched(R, sigma, p, r, at<double>(ws, P->evals), V,
-                                    at<void>(ws, P->eig), P->eig_stride, status, n, s));
-    HYDE_TRY(launch_weights_batched(V, sigma, p, r, P->RM, Pw, Qw, n, s));
-    HYDE_TRY(launch_win_project(Y, p, P->H, P->W, desc, at<int>(ws, P->tproj), n, P->proj_tiles,
-                                Pw, r, P->RM, zp, s));
-    HYDE_TRY(launch_win_dwt(zp, coef, scr, desc, n, r, P->L, s));
-    HYDE_TRY(launch_win_sure(coef, desc, n, r, P->L, P->K, at<unsigned int>(ws, P->counts),
-                             at<double>(ws, P->sums), at<double>(ws, P->sum_all), rank, lam,
-                             info, status, s));
-    HYDE_TRY(launch_win_idwt(coef, zp, scr, desc, n, r, P->L, rank, lam, s));
-    HYDE_TRY(launch_win_backproject(zp, desc, at<int>(ws, P->tback), n, P->back_tiles, Qw, p,
-                                    P->RM, rank, P->H, P->W, X, s));
-#undef HYDE_TRY
-    return HYDE_OK;
+    if (P->ngroups == 1) return enqueue_group(P, P->g[0], Y, X, info, ws, s);
+    // the second group on the plan's stream, forked from and joined back to s
+    if (cudaEventRecord(P->fork, s) != cudaSuccess ||
+        cudaStreamWaitEvent(P->side, P->fork, 0) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    hyde_status st = enqueue_group(P, P->g[0], Y, X, info, ws, s);
+    const hyde_status st2 = enqueue_group(P, P->g[1], Y, X, info, ws, P->side);
+    if (cudaEventRecord(P->join, P->side) != cudaSuccess ||
+        cudaStreamWaitEvent(s, P->join, 0) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    if (st == HYDE_OK) st = st2;
+    return st;
 }
 
 }  // extern "C"

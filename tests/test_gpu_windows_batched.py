@@ -15,6 +15,15 @@ from test_gpu_windows import _check_window
 
 pytestmark = pytest.mark.gpu
 
+# Near-tie tolerance of the SURE table where a window's rank reaches r_max
+# (the top-r_max subspace ends inside the cluster of noise eigenvalues): the
+# batched form sums each window's Gram matrix in a different order than the
+# one-cube path and takes sigma from the float inverse, which moves the
+# eigenvectors inside the cluster. Measured: window 10 of the 192 x 160 x 24
+# scene picks k = 20 (the oracle's choice) or k = 22 depending on the
+# Gram's piece boundaries, whose oracle SURE lies 1.9e-3 above the minimum.
+TIE_TOL = 5e-3
+
 
 def _run(hyde, Y, p, H, W, T, L, r):
     win = hyde.HyResWindowsBatched(p, H, W, T, L, r)
@@ -34,13 +43,13 @@ def test_windows_batched_full_parity(hyde, H, W, p, L, r, depth, ctx, mn, mx, se
     sc = make_scene(H, W, p, T, m=4, seed=seed)
     Y = torch.from_numpy(sc["Y"]).cuda()
     win, X = _run(hyde, Y, p, H, W, T, L, r)
-    assert win.kernel_launches == 13
+    assert win.kernel_launches == 26   # 13 per window group, two groups
     infos = win.infos()
     assert all(i["status"] == 0 for i in infos)
     assert bool(torch.isfinite(X).all())   # the cores tile the scene
     num = den = 0.0
     for k, row in enumerate(T):
-        got, ref = _check_window(sc["Y"], row, L, r, infos[k], X, k)
+        got, ref = _check_window(sc["Y"], row, L, r, infos[k], X, k, tie_tol=TIE_TOL)
         num += float(np.sum((got.astype(np.float64) - ref) ** 2))
         den += float(np.sum(ref ** 2))
         # a per-band bound beside the window's relative L2
@@ -99,7 +108,7 @@ def test_windows_batched_full_scene_sampled(hyde):
     picks |= set(int(k) for k in rng.choice(rest, size=15, replace=False))
     num = den = 0.0
     for k in sorted(picks):
-        got, ref = _check_window(sc["Y"], T[k], L, r, infos[k], X, k)
+        got, ref = _check_window(sc["Y"], T[k], L, r, infos[k], X, k, tie_tol=TIE_TOL)
         num += float(np.sum((got.astype(np.float64) - ref) ** 2))
         den += float(np.sum(ref ** 2))
     assert np.sqrt(num / den) < 1e-3
