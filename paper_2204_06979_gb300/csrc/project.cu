@@ -283,26 +283,36 @@ win_project_kernel(const float* __restrict__ Y, int p, int H, int W,
 }
 
 // X at the window's core pixels: X_b = sum_{i < r*} Q[b][i] Zh_i, Zh the
-// window's synthesised component images (Hp x Wp, window coordinates).
+// window's synthesised component images (Hp x Wp, window coordinates). A
+// thread takes two pixels (c and c + kBpThreads of the tile, so that each
+// store is coalesced): every weight read from shared memory feeds both, in
+// one paired FMA. Measured on the 2048 x 2048 x 200 scene: one pixel per
+// thread 1.15 ms, short-scoreboard (shared-memory) stalls leading.
 template <int R, int RM>
-__device__ __forceinline__ void win_backproject_pixel(const float* __restrict__ Zh, int N, int zpix,
-                                                      const float4* __restrict__ Qs4, int p, int r,
-                                                      long long bs, float* __restrict__ X) {
-    float z[R];
+__device__ __forceinline__ void win_backproject_pair(const float* __restrict__ Zh, int N, int z0,
+                                                     int z1, bool two,
+                                                     const float4* __restrict__ Qs4, int p, int r,
+                                                     long long bs, float* __restrict__ X0,
+                                                     float* __restrict__ X1) {
+    float za[R], zb[R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) z[i] = (i < r) ? __ldg(Zh + (long long)i * N + zpix) : 0.f;
+    for (int i = 0; i < R; ++i) {
+        za[i] = (i < r) ? __ldg(Zh + (long long)i * N + z0) : 0.f;
+        zb[i] = (i < r && two) ? __ldg(Zh + (long long)i * N + z1) : 0.f;
+    }
     for (int b = 0; b < p; ++b) {
         const float4* w4 = Qs4 + b * (RM / 4);
-        float x = 0.f;
+        float xa = 0.f, xb = 0.f;
 #pragma unroll
         for (int q = 0; q < R / 4; ++q) {
             const float4 w = w4[q];
-            x = fmaf(z[4 * q + 0], w.x, x);
-            x = fmaf(z[4 * q + 1], w.y, x);
-            x = fmaf(z[4 * q + 2], w.z, x);
-            x = fmaf(z[4 * q + 3], w.w, x);
+            fma_f32x2(xa, xb, za[4 * q + 0], zb[4 * q + 0], w.x, w.x);
+            fma_f32x2(xa, xb, za[4 * q + 1], zb[4 * q + 1], w.y, w.y);
+            fma_f32x2(xa, xb, za[4 * q + 2], zb[4 * q + 2], w.z, w.z);
+            fma_f32x2(xa, xb, za[4 * q + 3], zb[4 * q + 3], w.w, w.w);
         }
-        X[(long long)b * bs] = x;
+        X0[(long long)b * bs] = xa;
+        if (two) X1[(long long)b * bs] = xb;
     }
 }
 
@@ -329,13 +339,21 @@ win_backproject_kernel(const float* __restrict__ Zh, const WinDesc* __restrict__
     const float* Zw = Zh + d.img;
     const int t0 = (t - __ldg(tstart + wi)) * kWinBackTile;
     const int t1 = min(t0 + kWinBackTile, n);
-    for (int c = t0 + threadIdx.x; c < t1; c += kBpThreads) {
-        const int yy = c / d.cw, xx = c - yy * d.cw;
-        const int zpix = (d.cy0 - d.y0 + yy) * d.Wp + (d.cx0 - d.x0 + xx);
-        float* Xp = X + (long long)(d.cy0 + yy) * W + (d.cx0 + xx);
+    for (int c = t0 + threadIdx.x; c < t1; c += 2 * kBpThreads) {
+        const int c1 = c + kBpThreads;
+        const bool two = c1 < t1;
+        const int y0 = c / d.cw, x0 = c - y0 * d.cw;
+        const int y1 = two ? c1 / d.cw : y0, x1 = two ? c1 - y1 * d.cw : x0;
+        const int z0 = (d.cy0 - d.y0 + y0) * d.Wp + (d.cx0 - d.x0 + x0);
+        const int z1 = (d.cy0 - d.y0 + y1) * d.Wp + (d.cx0 - d.x0 + x1);
+        float* X0 = X + (long long)(d.cy0 + y0) * W + (d.cx0 + x0);
+        float* X1 = X + (long long)(d.cy0 + y1) * W + (d.cx0 + x1);
         switch (groups) {
-#define HYDE_WBP_CASE(G) \
-    case G: if (4 * G <= RM) win_backproject_pixel<4 * G, RM>(Zw, N, zpix, Qs4, p, r, bs, Xp); break;
+#define HYDE_WBP_CASE(G)                                                                          \
+    case G:                                                                                       \
+        if (4 * G <= RM)                                                                          \
+            win_backproject_pair<4 * G, RM>(Zw, N, z0, z1, two, Qs4, p, r, bs, X0, X1);           \
+        break;
             HYDE_WBP_CASE(1) HYDE_WBP_CASE(2) HYDE_WBP_CASE(3) HYDE_WBP_CASE(4)
             HYDE_WBP_CASE(5) HYDE_WBP_CASE(6) HYDE_WBP_CASE(7) HYDE_WBP_CASE(8)
 #undef HYDE_WBP_CASE
