@@ -893,9 +893,11 @@ def run_form(args) -> None:
     peaks = _measured_peaks()
     clocks = ClockSampler(0)
     if args.form == "windows":
-        H = W = 2048
+        H = W = args.win_scene
         p, L, r = 200, 3, 20
-        T = make_window_table(H, W, depth=9, context=16, min_side=32, max_side=224, seed=4)
+        # the 2048 x 2048 scene has 2^9 windows; a quarter of the area, a quarter of them
+        depth = {2048: 9, 1024: 7, 512: 5}[H]
+        T = make_window_table(H, W, depth=depth, context=16, min_side=32, max_side=224, seed=4)
         sc = make_scene(H, W, p, T, m=12, seed=4)
         Y = torch.from_numpy(sc["Y"]).to(dev)
         X = torch.zeros_like(Y)
@@ -916,7 +918,7 @@ def run_form(args) -> None:
         # projection) and write the scene once
         win_vox = int(np.sum(T[:, 2].astype(np.int64) * T[:, 3]) * p)
         alg_bytes = 4 * (2 * win_vox + voxels)
-        workload = ("sliding-window HyRes of a 2048x2048x200 float32 synthetic scene, 512 "
+        workload = (f"sliding-window HyRes of a {H}x{W}x200 float32 synthetic scene, {len(T)} "
                     "uneven windows (sides 48..256, 16-px context), per-core SNR U[5,20] dB, "
                     "db2 L=3, r<=20, K=64, one captured CUDA graph per scene")
     else:
@@ -1032,6 +1034,9 @@ def main() -> None:
                     help="timed steps of each secondary form in the plain run")
     ap.add_argument("--form", choices=("plain", "windows", "diff"), default="plain",
                     help="plain: the headline workload; windows / diff: secondary forms")
+    ap.add_argument("--win-scene", type=int, default=2048, choices=(2048, 1024, 512),
+                    help="--form windows: scene side (2048: the benchmark scene; smaller "
+                         "sides for profiler captures)")
     ap.add_argument("--slots", type=int, default=0,
                     help="--form windows: 0 runs every stage once over all windows (the "
                          "batched plan); n > 0 the per-window pipelines on n streams")
