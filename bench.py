@@ -504,7 +504,7 @@ def _form_windows(args, dev, cube, flush, stream) -> dict:
     torch.cuda.synchronize(dev)
     infos = win.infos()
     out.update({"workload": "2048x2048x200 scene, 512 windows (sides 48..256, 16-px context), "
-                            "per-core SNR U[5,20] dB, db2 L=3, r<=20; 13 kernels over all "
+                            "per-core SNR U[5,20] dB, db2 L=3, r<=20; 24 kernels over all "
                             "windows, one CUDA graph per scene",
                 "statuses_ok": int(sum(i["status"] == 0 for i in infos)),
                 "windows": len(T), "gpu_launches": win.kernel_launches,

@@ -553,11 +553,12 @@ hyde_status hyde_hyres_denoise_windows(const float* Y, float* X, int p, int H,
 /* ----------------------------------------------- batched sliding windows
  * The same form with one launch per stage over all windows (Sec. 2.2.2:
  * the tiles of a large scene, each denoised on its own by HyRes, Sec. 2.1):
- * the Gram matrices of all windows on the tensor cores (split-TF32, the
+ * the Gram matrices of all windows on the tensor cores (split-BF16, the
  * windows read in place from the scene), a one-block Gauss-Jordan and
  * eigensolver per window, the projection, the DWT, SURE and its selection,
  * the thresholded inverse DWT and the back-projection of the cores, each a
- * single launch over every window (13 kernels for the whole scene).
+ * single launch over every window (12 kernels per group of windows; the
+ * windows form two groups, each run on its own stream, so 24 for a scene).
  *
  * Differences from hyde_hyres_denoise on the window's cube: the Gram matrices
  * come from a four-term split-BF16 product on the tensor cores (every

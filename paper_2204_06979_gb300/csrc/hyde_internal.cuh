@@ -367,12 +367,14 @@ constexpr int kWinBackTile = 1024;
 hyde_status launch_win_project(const float* Y, int p, int H, int W, const WinDesc* desc,
                                const int* tstart, int n_win, int n_tiles, const float* P, int r,
                                int ldw, float* Zp, cudaStream_t s);
+// DWT of every kept component with the SURE histogram rows formed on the way
 hyde_status launch_win_dwt(const float* Zp, float* coef, float* scratch, const WinDesc* desc,
-                           int n_win, int r, int levels, cudaStream_t s);
-hyde_status launch_win_sure(const float* coef, const WinDesc* desc, int n_win, int r,
-                            int levels, int K, unsigned int* counts, double* sums,
-                            double* sum_all, int* rank, double* lam, hyde_hyres_info* info,
-                            int* status, const int* gstatus, cudaStream_t s);
+                           int n_win, int r, int levels, int K, unsigned int* counts,
+                           double* sums, double* sum_all, cudaStream_t s);
+hyde_status launch_win_sure(const WinDesc* desc, int n_win, int r, int levels, int K,
+                            const unsigned int* counts, const double* sums,
+                            const double* sum_all, int* rank, double* lam, hyde_hyres_info* info,
+                            const int* status, const int* gstatus, cudaStream_t s);
 hyde_status launch_win_idwt(const float* coef, float* Zh, float* scratch, const WinDesc* desc,
                             int n_win, int r, int levels, const int* rank, const double* lam,
                             cudaStream_t s);

@@ -7,8 +7,8 @@
 //    component image, level after level inside the block (the LL band of a
 //    level goes to the block's scratch in global memory, read back through L2
 //    by the next level after a barrier);
-//  * win_sure_hist_kernel: the SURE histogram of the component's detail
-//    coefficients on the grid lambda_k = k delta (counts and 2^-sh fixed-point
+//    the detail coefficients go straight into the component's SURE
+//    histogram on the grid lambda_k = k delta (counts and 2^-sh fixed-point
 //    sums of c^2 per bin, exact integers, so the table does not depend on the
 //    order of the additions), written as row i of the window's table;
 //  * win_sure_select_kernel (one block per window): the integer-prefixed
@@ -31,18 +31,52 @@ __device__ __forceinline__ float softf(float c, float lam) {
     return copysignf(fmaxf(fabsf(c) - lam, 0.f), c);
 }
 
+// SURE histogram: bin k collects the detail coefficients with
+// (k - 1) delta < |c| <= k delta (bin 0: c = 0); the bin and rn(c^2 2^sh)
+// each come from one FMA onto 1.5 * 2^23 (exact below 2^22), into a
+// [bin][lane] shared histogram (lane l of every warp hits bank l). The plan
+// picks sh so that no lane column can overflow 32 bits.
+constexpr float kMagic = 12582912.f;   // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+
 // Analysis of component i of window w: levels 1..L. Level l reads its input
 // (h x w, the padded image at l = 1, else LL_{l-1} from scratch) and writes
 // the three detail bands to their Mallat positions of the coefficient image
 // (row stride Wp) and LL_l to scratch (half A for odd l, B for even l) or,
-// at l = L, into the coefficient image.
+// at l = L, into the coefficient image. Every detail coefficient goes into
+// the component's SURE histogram as it is formed (the final LL band only
+// into the sum of squares), so the coefficients are not read again for SURE
+// (a separate histogram kernel over the 512-window scene took 0.33 ms).
 __global__ void __launch_bounds__(kWdThreads)
 win_dwt_kernel(const float* __restrict__ Zp, float* __restrict__ coef,
-               float* __restrict__ scratch, const WinDesc* __restrict__ desc, int levels) {
+               float* __restrict__ scratch, const WinDesc* __restrict__ desc, int levels,
+               int r, int K, unsigned int* __restrict__ counts, double* __restrict__ sums,
+               double* __restrict__ sum_all) {
     pdl_wait();
     pdl_trigger();
+    extern __shared__ unsigned int whsm[];   // counts [K][32], then sums [K][32]
+    __shared__ double wall[kWdThreads / 32];
+    unsigned int* hc = whsm;
+    unsigned int* hq = whsm + K * 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int e = tid; e < 2 * K * 32; e += kWdThreads) whsm[e] = 0u;
     const int i = blockIdx.x, wi = blockIdx.y;
     const WinDesc d = desc[wi];
+    const float inv_delta = (float)(1.0 / d.delta);
+    const float qscale = ldexpf(1.0f, d.sh);
+    float all = 0.f;
+    auto bin = [&](float c) {
+        const float c2 = c * c;
+        all += c2;
+        const unsigned k =
+            (unsigned)(__float_as_int(__fmaf_ru(fabsf(c), inv_delta, kMagic)) - kMagicBits);
+        if (k < (unsigned)K) {
+            const unsigned q = (unsigned)(__float_as_int(fmaf(c2, qscale, kMagic)) - kMagicBits);
+            atomicAdd(hc + k * 32 + lane, 1u);
+            atomicAdd(hq + k * 32 + lane, q);
+        }
+    };
+    __syncthreads();
     const int N = d.Hp * d.Wp;
     const float* img = Zp + d.img + (long long)i * N;
     float* C = coef + d.img + (long long)i * N;
@@ -54,8 +88,8 @@ win_dwt_kernel(const float* __restrict__ Zp, float* __restrict__ coef,
         float* ll = l == levels ? C : ((l & 1) ? A : B);
         const int ll_ld = l == levels ? d.Wp : wh;
         for (int e = threadIdx.x; e < hh * wh; e += kWdThreads) {
-            const int J = e / wh, K = e - J * wh;
-            const int x0 = 2 * K, x2 = (2 * K + 2 >= w) ? 2 * K + 2 - w : 2 * K + 2;
+            const int J = e / wh, Kc = e - J * wh;
+            const int x0 = 2 * Kc, x2 = (2 * Kc + 2 >= w) ? 2 * Kc + 2 - w : 2 * Kc + 2;
             float a[4], dd[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
@@ -75,57 +109,20 @@ win_dwt_kernel(const float* __restrict__ Zp, float* __restrict__ coef,
             }
             float* pt = C + (long long)J * d.Wp;
             float* pb = C + (long long)(hh + J) * d.Wp;
-            pt[wh + K] = kH0 * dd[0] + kH1 * dd[1] + kH2 * dd[2] + kH3 * dd[3];   // row detail
-            pb[K] = kG0 * a[0] + kG1 * a[1] + kG2 * a[2] + kG3 * a[3];           // column detail
-            pb[wh + K] = kG0 * dd[0] + kG1 * dd[1] + kG2 * dd[2] + kG3 * dd[3];
-            ll[(long long)J * ll_ld + K] = kH0 * a[0] + kH1 * a[1] + kH2 * a[2] + kH3 * a[3];
+            const float hl = kH0 * dd[0] + kH1 * dd[1] + kH2 * dd[2] + kH3 * dd[3];   // row detail
+            const float lh = kG0 * a[0] + kG1 * a[1] + kG2 * a[2] + kG3 * a[3];       // column detail
+            const float hhv = kG0 * dd[0] + kG1 * dd[1] + kG2 * dd[2] + kG3 * dd[3];
+            const float llv = kH0 * a[0] + kH1 * a[1] + kH2 * a[2] + kH3 * a[3];
+            pt[wh + Kc] = hl;
+            pb[Kc] = lh;
+            pb[wh + Kc] = hhv;
+            ll[(long long)J * ll_ld + Kc] = llv;
+            bin(hl);
+            bin(lh);
+            bin(hhv);
+            if (l == levels) all += llv * llv;   // kept, not binned
         }
         __syncthreads();
-    }
-}
-
-// SURE histogram of component i of window w. Bin k collects the detail
-// coefficients with (k - 1) delta < |c| <= k delta (bin 0: c = 0): the bin
-// and rn(c^2 2^sh) each come from one FMA onto 1.5 * 2^23 (exact below
-// 2^22), into a [bin][lane] shared histogram (lane l of every warp hits bank
-// l). The plan picks sh so that no lane column can overflow 32 bits.
-constexpr float kMagic = 12582912.f;   // 1.5 * 2^23
-constexpr int kMagicBits = 0x4B400000;
-
-__global__ void __launch_bounds__(kWdThreads)
-win_sure_hist_kernel(const float* __restrict__ coef, const WinDesc* __restrict__ desc, int r,
-                     int levels, int K, unsigned int* __restrict__ counts,
-                     double* __restrict__ sums, double* __restrict__ sum_all) {
-    pdl_wait();
-    pdl_trigger();
-    extern __shared__ unsigned int whsm[];   // counts [K][32], then sums [K][32]
-    __shared__ double wall[kWdThreads / 32];
-    unsigned int* hc = whsm;
-    unsigned int* hq = whsm + K * 32;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int i = blockIdx.x, wi = blockIdx.y;
-    const WinDesc d = desc[wi];
-    for (int e = tid; e < 2 * K * 32; e += kWdThreads) whsm[e] = 0u;
-    __syncthreads();
-    const float inv_delta = (float)(1.0 / d.delta);
-    const float qscale = ldexpf(1.0f, d.sh);
-    const int hl = d.Hp >> levels, wl = d.Wp >> levels;
-    const int N = d.Hp * d.Wp;
-    const float* C = coef + d.img + (long long)i * N;
-    float all = 0.f;
-    for (int e = tid; e < N; e += kWdThreads) {
-        const float c = __ldg(C + e);
-        const float c2 = c * c;
-        all += c2;
-        const int y = e / d.Wp, x = e - y * d.Wp;
-        if (y < hl && x < wl) continue;   // the final LL band is kept, not binned
-        const unsigned k =
-            (unsigned)(__float_as_int(__fmaf_ru(fabsf(c), inv_delta, kMagic)) - kMagicBits);
-        if (k < (unsigned)K) {
-            const unsigned q = (unsigned)(__float_as_int(fmaf(c2, qscale, kMagic)) - kMagicBits);
-            atomicAdd(hc + k * 32 + lane, 1u);
-            atomicAdd(hq + k * 32 + lane, q);
-        }
     }
     all = warp_sum(all);
     if (lane == 0) wall[wid] = (double)all;
@@ -150,6 +147,7 @@ win_sure_hist_kernel(const float* __restrict__ coef, const WinDesc* __restrict__
         sum_all[(long long)wi * r + i] = tot;
     }
 }
+
 
 __device__ __forceinline__ long long ord_key(double v) {
     const long long bits = __double_as_longlong(v);
@@ -331,23 +329,24 @@ win_idwt_kernel(const float* __restrict__ coef, float* __restrict__ Zh,
 }  // namespace
 
 hyde_status launch_win_dwt(const float* Zp, float* coef, float* scratch, const WinDesc* desc,
-                           int n_win, int r, int levels, cudaStream_t s) {
-    if (n_win < 1 || n_win > 65535 || r < 1 || levels < 1) return HYDE_ERR_SHAPE;
-    launch_pdl(win_dwt_kernel, dim3(r, n_win), kWdThreads, 0, s, Zp, coef, scratch, desc, levels);
+                           int n_win, int r, int levels, int K, unsigned int* counts,
+                           double* sums, double* sum_all, cudaStream_t s) {
+    if (n_win < 1 || n_win > 65535 || r < 1 || levels < 1 || K < 2 || K > kWdThreads)
+        return HYDE_ERR_SHAPE;
+    const size_t smem = (size_t)2 * K * 32 * sizeof(unsigned int);
+    if (ensure_smem_limit((const void*)win_dwt_kernel, (int)smem) != cudaSuccess)
+        return HYDE_ERR_CUDA;
+    launch_pdl(win_dwt_kernel, dim3(r, n_win), kWdThreads, smem, s, Zp, coef, scratch, desc,
+               levels, r, K, counts, sums, sum_all);
     return cuda_status(cudaGetLastError());
 }
 
-hyde_status launch_win_sure(const float* coef, const WinDesc* desc, int n_win, int r,
-                            int levels, int K, unsigned int* counts, double* sums,
-                            double* sum_all, int* rank, double* lam, hyde_hyres_info* info,
-                            int* status, const int* gstatus, cudaStream_t s) {
+hyde_status launch_win_sure(const WinDesc* desc, int n_win, int r, int levels, int K,
+                            const unsigned int* counts, const double* sums,
+                            const double* sum_all, int* rank, double* lam, hyde_hyres_info* info,
+                            const int* status, const int* gstatus, cudaStream_t s) {
     if (n_win < 1 || n_win > 65535 || r < 1 || r > kMaxRank || K < 2 || K > kWdThreads)
         return HYDE_ERR_SHAPE;
-    const size_t smem = (size_t)2 * K * 32 * sizeof(unsigned int);
-    if (ensure_smem_limit((const void*)win_sure_hist_kernel, (int)smem) != cudaSuccess)
-        return HYDE_ERR_CUDA;
-    launch_pdl(win_sure_hist_kernel, dim3(r, n_win), kWdThreads, smem, s, coef, desc, r, levels,
-               K, counts, sums, sum_all);
     launch_pdl(win_sure_select_kernel, n_win, kWdThreads, 0, s, counts, sums, sum_all, desc, r,
                levels, K, rank, lam, info, status, gstatus);
     return cuda_status(cudaGetLastError());

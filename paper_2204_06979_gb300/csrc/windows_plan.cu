@@ -10,7 +10,7 @@
 // joined with events): the one-block-per-window stages of one group (the
 // Gauss-Jordan inverse, the tridiagonalisation, the eigenpairs, all bound by
 // the latency of one SM) then share the SMs with the bandwidth- and
-// tensor-bound stages of the other. A call is one capturable sequence of 26
+// tensor-bound stages of the other. A call is one capturable sequence of 24
 // kernels whatever the number of windows.
 #include <math.h>
 #include <string.h>
@@ -254,8 +254,9 @@ hyde_status hyde_windows_plan_workspace_size(hyde_windows_plan plan, size_t* byt
 
 int hyde_windows_plan_kernel_launches(hyde_windows_plan plan) {
     // per group: Gram 2, noise 1, eigensolver 3, weights 1, projection 1,
-    // DWT 1, SURE 2, inverse DWT 1, back-projection 1
-    return plan ? 13 * plan->ngroups : -1;
+    // DWT with the SURE histogram 1, SURE selection 1, inverse DWT 1,
+    // back-projection 1
+    return plan ? 12 * plan->ngroups : -1;
 }
 
 hyde_status hyde_windows_plan_layout(hyde_windows_plan plan, hyde_windows_ws_layout* out) {
@@ -308,11 +309,11 @@ static hyde_status enqueue_group(const hyde_windows_plan_s* P, const WinGroup& g
     HYDE_TRY(launch_weights_batched(V, sigma, p, r, P->RM, Pw, Qw, n, s));
     HYDE_TRY(launch_win_project(Y, p, P->H, P->W, desc, at<int>(ws, g.tproj), n, g.proj_tiles,
                                 Pw, r, P->RM, zp, s));
-    HYDE_TRY(launch_win_dwt(zp, coef, scr, desc, n, r, P->L, s));
-    HYDE_TRY(launch_win_sure(coef, desc, n, r, P->L, P->K,
-                             at<unsigned int>(ws, P->counts) + (size_t)w0 * r * P->K,
-                             at<double>(ws, P->sums) + (size_t)w0 * r * P->K,
-                             at<double>(ws, P->sum_all) + (size_t)w0 * r, rank, lam,
+    unsigned int* counts = at<unsigned int>(ws, P->counts) + (size_t)w0 * r * P->K;
+    double* sums = at<double>(ws, P->sums) + (size_t)w0 * r * P->K;
+    double* sum_all = at<double>(ws, P->sum_all) + (size_t)w0 * r;
+    HYDE_TRY(launch_win_dwt(zp, coef, scr, desc, n, r, P->L, P->K, counts, sums, sum_all, s));
+    HYDE_TRY(launch_win_sure(desc, n, r, P->L, P->K, counts, sums, sum_all, rank, lam,
                              info ? info + w0 : nullptr, status, gstatus, s));
     HYDE_TRY(launch_win_idwt(coef, zp, scr, desc, n, r, P->L, rank, lam, s));
     HYDE_TRY(launch_win_backproject(zp, desc, at<int>(ws, g.tback), n, g.back_tiles, Qw, p,

@@ -43,7 +43,7 @@ def test_windows_batched_full_parity(hyde, H, W, p, L, r, depth, ctx, mn, mx, se
     sc = make_scene(H, W, p, T, m=4, seed=seed)
     Y = torch.from_numpy(sc["Y"]).cuda()
     win, X = _run(hyde, Y, p, H, W, T, L, r)
-    assert win.kernel_launches == 26   # 13 per window group, two groups
+    assert win.kernel_launches == 24   # 12 per window group, two groups
     infos = win.infos()
     assert all(i["status"] == 0 for i in infos)
     assert bool(torch.isfinite(X).all())   # the cores tile the scene
