@@ -288,8 +288,14 @@ win_idwt_kernel(const float* __restrict__ coef, float* __restrict__ Zh,
         const int lld = l == levels ? d.Wp : wh;
         float* O = l == 1 ? Zh + d.img + (long long)i * N : ((l & 1) ? B : A);
         const int old = l == 1 ? d.Wp : w;
-        for (int e = threadIdx.x; e < hh * wh; e += kWdThreads) {
-            const int j = e / wh, k = e - j * wh;
+        // the finest level writes only the 2 x 2 output blocks that meet the
+        // core (the back-projection reads nothing else); coarser levels all
+        const int jlo = l == 1 ? (d.cy0 - d.y0) >> 1 : 0;
+        const int klo = l == 1 ? (d.cx0 - d.x0) >> 1 : 0;
+        const int jn = l == 1 ? ((d.cy0 - d.y0 + d.ch + 1) >> 1) - jlo : hh;
+        const int kn = l == 1 ? ((d.cx0 - d.x0 + d.cw + 1) >> 1) - klo : wh;
+        for (int e = threadIdx.x; e < jn * kn; e += kWdThreads) {
+            const int j = jlo + e / kn, k = klo + (e - (e / kn) * kn);
             const int jm = j == 0 ? hh - 1 : j - 1, km = k == 0 ? wh - 1 : k - 1;
             auto ll = [&](int y, int x) {
                 return l == levels ? __ldg(L + (long long)y * lld + x)
