@@ -52,9 +52,17 @@ constexpr int kMaxRaw = 8;
 #define HYDE_TF32_WIN 2
 #endif
 constexpr int kWin = HYDE_TF32_WIN; // chunks per TMEM accumulation window
-constexpr int kTmaWarp = 0, kMmaWarp = 1, kCvtWarp0 = 2, kCvtWarps = 4;
+// Warpgroups 0-1: the TMA warp, the MMA warp and six converter warps;
+// warpgroups 2-3: the eight drain warps, which keep up to 96 FP32 sums each.
+// Launched with 128 registers per thread, warpgroups 0-1 release down to 64
+// and 2-3 take up to 192 (setmaxnreg), adding up to the launch's 65536.
+constexpr int kTmaWarp = 0, kMmaWarp = 1, kCvtWarp0 = 2, kCvtWarps = 6;
 constexpr int kDrainWarp0 = kCvtWarp0 + kCvtWarps, kDrainWarps = 8;
 constexpr int kT32Threads = (kDrainWarp0 + kDrainWarps) * 32;
+constexpr int kLaunchRegs = 128, kLowRegs = 64, kHighRegs = 192;
+static_assert(kT32Threads == 512, "four warpgroups");
+static_assert(256 * kLowRegs + 256 * kHighRegs == kT32Threads * kLaunchRegs,
+              "the register split must add up to the launch allocation");
 constexpr int kMaxP = 160;          // bands of the tensor-core Gram
 
 struct T32Plan {
@@ -132,6 +140,8 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
     const long long iters = c1 > c0 ? c1 - c0 : 0;
     const long long nwin = (iters + kWin - 1) / kWin;
 
+    if (warp < kDrainWarp0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kLowRegs));
     if (warp == kTmaWarp) {
         // ------------------------------------------------------ TMA loads
         if (lane == 0) {
@@ -219,7 +229,7 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
                                    P.wait_ns > kWaitNs ? P.wait_ns : kWaitNs))
                 *abort_v = 1;
         }
-    } else if (warp < kDrainWarp0) {
+    } else {
         // ------------------------------------------------ split into hi and lo
         const int ct = tid - kCvtWarp0 * 32;
         for (long long it = 0; it < iters; ++it) {
@@ -260,15 +270,15 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
             mbar_arrive(smem_u32(&raw_empty[s]));
         }
     }
-
+    } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kHighRegs));
     // ---------------------------------------------- drain warps (and output)
     // A drain thread owns TMEM lane `row` and H0 columns in blocks of 16:
     // half 0 the top tile's columns [0, H0); half 1 the top tile's columns
     // [H0, NT), then the corner's [0, NC). Block k maps to TMEM column tcol(k)
     // and to the partial's (band, column) (orow(k), ocol(k)).
     const int dw = warp - kDrainWarp0;
-    const bool drain = dw >= 0;
-    const int quad = warp & 3, half = drain ? dw >> 2 : 0;
+    const int quad = warp & 3, half = dw >> 2;
     const int row = 32 * quad + lane;                     // TMEM lane
     const uint32_t lane_addr = (uint32_t)(32 * quad) << 16;
     constexpr int T1 = NT - H0;                           // top columns of half 1
@@ -278,50 +288,51 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, long long n, T32Plan 
     float acc[H0];
 #pragma unroll
     for (int c = 0; c < H0; ++c) acc[c] = 0.f;
-    if (drain) {
-        for (long long w = 0; w < nwin; ++w) {
-            if (*abort_v) break;
-            const int b = (int)(w & 1);
-            if (!mbar_wait_bounded(smem_u32(&acc_full[b]), (uint32_t)((w / 2) & 1), P.wait_ns)) {
-                *abort_v = 1;
-                break;
-            }
-            __syncwarp();
-            tc_fence_after();
-            const uint32_t t0 = tmem + lane_addr + (uint32_t)b * (uint32_t)P.buf_cols;
-#pragma unroll
-            for (int k = 0; k < H0 / 16; ++k) {
-                uint32_t r[16];
-                tmem_ld16_nowait(t0 + (uint32_t)tcol(k), r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int e = 0; e < 16; ++e) acc[16 * k + e] += __uint_as_float(r[e]);
-            }
-            tc_fence_before();
-            mbar_arrive(smem_u32(&acc_empty[b]));
+    for (long long w = 0; w < nwin; ++w) {
+        if (*abort_v) break;
+        const int b = (int)(w & 1);
+        if (!mbar_wait_bounded(smem_u32(&acc_full[b]), (uint32_t)((w / 2) & 1), P.wait_ns)) {
+            *abort_v = 1;
+            break;
         }
+        __syncwarp();
+        tc_fence_after();
+        const uint32_t t0 = tmem + lane_addr + (uint32_t)b * (uint32_t)P.buf_cols;
+#pragma unroll
+        for (int k = 0; k < H0 / 16; ++k) {
+            uint32_t r[16];
+            tmem_ld16_nowait(t0 + (uint32_t)tcol(k), r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[16 * k + e] += __uint_as_float(r[e]);
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&acc_empty[b]));
+    }
+    // the partial (a CTA without chunks writes zeros); overwritten with zeros
+    // below if any role gave up
+    const int p = P.p;
+    float* out = partials + (long long)blockIdx.x * p * p;
+    // top tile: lane = band (< 128); corner: lane -> band Np - 128 + lane
+#pragma unroll
+    for (int k = 0; k < H0 / 16; ++k) {
+        const bool corner = half == 1 && 16 * k >= T1;
+        const int orow = corner ? P.Np - 128 + row : row;
+        const int ocol = half == 0 ? 16 * k : (corner ? 128 + 16 * k - T1 : H0 + 16 * k);
+        if (orow < p && (!corner || orow >= 128)) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                if (ocol + e < p) out[(long long)orow * p + ocol + e] = acc[16 * k + e];
+        }
+    }
     }
     tc_fence_before();
     __syncthreads();
-    const bool ok = iters > 0 && !abort_s;
-    if (abort_s && tid == 0) set_status(status, HYDE_ERR_TIMEOUT);
-    const int p = P.p;
-    float* out = partials + (long long)blockIdx.x * p * p;
-    if (!ok) {
+    if (abort_s) {
+        if (tid == 0) set_status(status, HYDE_ERR_TIMEOUT);
+        const int p = P.p;
+        float* out = partials + (long long)blockIdx.x * p * p;
         for (int e = tid; e < p * p; e += kT32Threads) out[e] = 0.f;
-    } else if (drain) {
-        // top tile: lane = band (< 128); corner: lane -> band Np - 128 + lane
-#pragma unroll
-        for (int k = 0; k < H0 / 16; ++k) {
-            const bool corner = half == 1 && 16 * k >= T1;
-            const int orow = corner ? P.Np - 128 + row : row;
-            const int ocol = half == 0 ? 16 * k : (corner ? 128 + 16 * k - T1 : H0 + 16 * k);
-            if (orow < p && (!corner || orow >= 128)) {
-#pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    if (ocol + e < p) out[(long long)orow * p + ocol + e] = acc[16 * k + e];
-            }
-        }
     }
     // the reduction may start once every CTA has written its partial
     pdl_trigger();
@@ -454,6 +465,11 @@ hyde_status launch_gram_tf32(const float* Y, int p, long long n, float* partials
     const int blocks = (int)(nchunks < sms ? nchunks : sms);
     auto go = [&](auto kernel) -> hyde_status {
         if (ensure_smem_limit((const void*)kernel, (int)P.smem) != cudaSuccess)
+            return HYDE_ERR_CUDA;
+        // the setmaxnreg split assumes exactly kLaunchRegs registers per thread at launch
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, (const void*)kernel) != cudaSuccess ||
+            fa.numRegs != kLaunchRegs)
             return HYDE_ERR_CUDA;
         launch_pdl(kernel, blocks, kT32Threads, P.smem, s, tmap, n, P, partials, status);
         return HYDE_OK;
