@@ -135,6 +135,42 @@ project_pad_kernel(const float* __restrict__ Y, int p, int H, int W,
     }
 }
 
+// X_b = sum_{i < R} Q[b][i] z_i for two pixels at once (component images of
+// N pixels, pixel z0 written to X0 + b bs, z1 to X1 + b bs): every weight
+// read from shared memory feeds both, in one paired FMA. The window form
+// takes pixels c and c + kBpThreads of a tile, so that each store is
+// coalesced; there one pixel per thread took 1.15 ms on the 2048 x 2048 x 200
+// scene (short-scoreboard stalls on the weights leading) and two 0.79 ms. On
+// the one-cube path (backproject_kernel, 349 x 1905 x 144) the same pairing
+// measured 116 against 110 us, so that kernel keeps one pixel per thread.
+template <int R, int RM>
+__device__ __forceinline__ void backproject_pair(const float* __restrict__ Zh, int N, int z0,
+                                                     int z1, bool two,
+                                                     const float4* __restrict__ Qs4, int p, int r,
+                                                     long long bs, float* __restrict__ X0,
+                                                     float* __restrict__ X1) {
+    float za[R], zb[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        za[i] = (i < r) ? __ldg(Zh + (long long)i * N + z0) : 0.f;
+        zb[i] = (i < r && two) ? __ldg(Zh + (long long)i * N + z1) : 0.f;
+    }
+    for (int b = 0; b < p; ++b) {
+        const float4* w4 = Qs4 + b * (RM / 4);
+        float xa = 0.f, xb = 0.f;
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q) {
+            const float4 w = w4[q];
+            fma_f32x2(xa, xb, za[4 * q + 0], zb[4 * q + 0], w.x, w.x);
+            fma_f32x2(xa, xb, za[4 * q + 1], zb[4 * q + 1], w.y, w.y);
+            fma_f32x2(xa, xb, za[4 * q + 2], zb[4 * q + 2], w.z, w.z);
+            fma_f32x2(xa, xb, za[4 * q + 3], zb[4 * q + 3], w.w, w.w);
+        }
+        X0[(long long)b * bs] = xa;
+        if (two) X1[(long long)b * bs] = xb;
+    }
+}
+
 // X_b = sum_{i < R} Q[b][i] z_i for one pixel, R a multiple of 4 >= r*.
 template <int R, int RM>
 __device__ __forceinline__ void backproject_pixel(const float* __restrict__ Zh, long long n,
@@ -282,40 +318,6 @@ win_project_kernel(const float* __restrict__ Y, int p, int H, int W,
     }
 }
 
-// X at the window's core pixels: X_b = sum_{i < r*} Q[b][i] Zh_i, Zh the
-// window's synthesised component images (Hp x Wp, window coordinates). A
-// thread takes two pixels (c and c + kBpThreads of the tile, so that each
-// store is coalesced): every weight read from shared memory feeds both, in
-// one paired FMA. Measured on the 2048 x 2048 x 200 scene: one pixel per
-// thread 1.15 ms, short-scoreboard (shared-memory) stalls leading.
-template <int R, int RM>
-__device__ __forceinline__ void win_backproject_pair(const float* __restrict__ Zh, int N, int z0,
-                                                     int z1, bool two,
-                                                     const float4* __restrict__ Qs4, int p, int r,
-                                                     long long bs, float* __restrict__ X0,
-                                                     float* __restrict__ X1) {
-    float za[R], zb[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        za[i] = (i < r) ? __ldg(Zh + (long long)i * N + z0) : 0.f;
-        zb[i] = (i < r && two) ? __ldg(Zh + (long long)i * N + z1) : 0.f;
-    }
-    for (int b = 0; b < p; ++b) {
-        const float4* w4 = Qs4 + b * (RM / 4);
-        float xa = 0.f, xb = 0.f;
-#pragma unroll
-        for (int q = 0; q < R / 4; ++q) {
-            const float4 w = w4[q];
-            fma_f32x2(xa, xb, za[4 * q + 0], zb[4 * q + 0], w.x, w.x);
-            fma_f32x2(xa, xb, za[4 * q + 1], zb[4 * q + 1], w.y, w.y);
-            fma_f32x2(xa, xb, za[4 * q + 2], zb[4 * q + 2], w.z, w.z);
-            fma_f32x2(xa, xb, za[4 * q + 3], zb[4 * q + 3], w.w, w.w);
-        }
-        X0[(long long)b * bs] = xa;
-        if (two) X1[(long long)b * bs] = xb;
-    }
-}
-
 template <int RM>
 __global__ void __launch_bounds__(kBpThreads)
 win_backproject_kernel(const float* __restrict__ Zh, const WinDesc* __restrict__ desc,
@@ -352,7 +354,7 @@ win_backproject_kernel(const float* __restrict__ Zh, const WinDesc* __restrict__
 #define HYDE_WBP_CASE(G)                                                                          \
     case G:                                                                                       \
         if (4 * G <= RM)                                                                          \
-            win_backproject_pair<4 * G, RM>(Zw, N, z0, z1, two, Qs4, p, r, bs, X0, X1);           \
+            backproject_pair<4 * G, RM>(Zw, N, z0, z1, two, Qs4, p, r, bs, X0, X1);               \
         break;
             HYDE_WBP_CASE(1) HYDE_WBP_CASE(2) HYDE_WBP_CASE(3) HYDE_WBP_CASE(4)
             HYDE_WBP_CASE(5) HYDE_WBP_CASE(6) HYDE_WBP_CASE(7) HYDE_WBP_CASE(8)
