@@ -45,9 +45,9 @@ FP32_SM_PEAK_TFLOPS = 128 * 2 * 2.070e9 / 1e12         # one SM, for single-bloc
 # (stage, precision). profiles/ holds the capture summaries; an entry is
 # removed when its kernel changes (the eigensolver has no current capture).
 NCU_TRAFFIC: dict = {
-    # gram_tf32 387.44 + 4.57 MB (profiles/gram_tf32_349x1905x144.md)
-    ("gram", "fp32"): 392.01e6,
-    ("gram", "tf32x3"): 392.01e6,
+    # gram_tf32 (six converter warps) 387.22 + 2.97 MB (profiles/gram_tf32_349x1905x144.md)
+    ("gram", "fp32"): 390.19e6,
+    ("gram", "tf32x3"): 390.19e6,
     # gram_tc 385.77 + 3.68 MB, gram_tc_reduce 8.42 MB
     ("gram", "bf16x3"): 397.87e6,
     ("gram", "bf16x3_all"): 397.87e6,
