@@ -499,8 +499,10 @@ def _form_windows(args, dev, cube, flush, stream) -> dict:
     Y = torch.from_numpy(Yh).to(dev)
     X = torch.zeros_like(Y)
     win = api.HyResWindowsBatched(p, H, W, T, L, r, device=dev)
+    tuning = win.autotune(Y, X)   # projection tile and Gram role split, timed on this scene
     win.capture(Y, X)
     out = _time_form(win.replay, args, flush, stream, p * H * W)
+    out["tuning"] = tuning
     torch.cuda.synchronize(dev)
     infos = win.infos()
     out.update({"workload": "2048x2048x200 scene, 512 windows (sides 48..256, 16-px context), "
@@ -903,8 +905,9 @@ def run_form(args) -> None:
         X = torch.zeros_like(Y)
         if args.slots > 0:   # the per-window pipelines on that many streams
             win = api.HyResWindows(p, H, W, T, L, r, n_slots=args.slots, device=dev)
-        else:                # every stage one launch over all windows
+        else:                # every stage one launch over all windows, tuned on the scene
             win = api.HyResWindowsBatched(p, H, W, T, L, r, device=dev)
+            win.autotune(Y, X)
         win.capture(Y, X)
         with clocks:
             ms = _timed_steps(win.replay, args.steps, args.warmup, flush, stream)

@@ -599,6 +599,26 @@ typedef struct {
     size_t V;
 } hyde_windows_ws_layout;
 hyde_status hyde_windows_plan_layout(hyde_windows_plan plan, hyde_windows_ws_layout* out);
+/* Tuning of the batched form: the projection tile (padded pixels per block, a
+ * multiple of 256 up to 4096) and the weight of the window Gram's second band
+ * role when it splits the CTAs between its two roles (p > 128; > 0, up to
+ * 16). The defaults, 256 and 1.6, measured best on the 2048 x 2048 x 200
+ * scene. hyde_windows_plan_autotune times every candidate (tiles 256, 512,
+ * 1024 x weights 1.2, 1.6, 2.0) on the caller's scene with
+ * hyde_hyres_denoise_windows_batched (an untimed call, then the median of
+ * three), keeps the fastest and reports its time in *best_ms (may be NULL);
+ * it synchronizes `stream` and may not run while the stream is being
+ * captured. Change the tuning only while no call of the plan is in flight,
+ * and capture graphs again afterwards: a captured call keeps the grid sizes
+ * of the tuning it was captured with. HYDE_ERR_INVALID_ARG for values out of
+ * range. (No counterpart in the paper.) */
+hyde_status hyde_windows_plan_set_tuning(hyde_windows_plan plan, int proj_tile,
+                                         double gram_role_weight);
+hyde_status hyde_windows_plan_get_tuning(hyde_windows_plan plan, int* proj_tile,
+                                         double* gram_role_weight);
+hyde_status hyde_windows_plan_autotune(hyde_windows_plan plan, const float* Y, float* X,
+                                       void* ws, size_t ws_bytes, cudaStream_t stream,
+                                       float* best_ms);
 hyde_status hyde_hyres_denoise_windows_batched(const float* Y, float* X,
                                                hyde_windows_plan plan,
                                                hyde_hyres_info* info, void* ws,

@@ -105,6 +105,11 @@ SIGNATURES = {
     "hyde_windows_plan_kernel_launches": (c_int, [c_vp]),
     "hyde_windows_plan_destroy": (c_int, [c_vp]),
     "hyde_windows_plan_layout": (c_int, [c_vp, ctypes.POINTER(HydeWindowsWsLayout)]),
+    "hyde_windows_plan_set_tuning": (c_int, [c_vp, c_int, ctypes.c_double]),
+    "hyde_windows_plan_get_tuning": (c_int, [c_vp, ctypes.POINTER(c_int),
+                                             ctypes.POINTER(ctypes.c_double)]),
+    "hyde_windows_plan_autotune": (c_int, [c_vp, c_vp, c_vp, c_vp, c_size, c_vp,
+                                           ctypes.POINTER(ctypes.c_float)]),
     "hyde_hyres_denoise_windows_batched": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "hyde_hyres_denoise_host": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int,
                                         ctypes.POINTER(HydeParams), c_vp, c_vp, c_vp, c_size,

@@ -665,6 +665,7 @@ class HyResWindowsBatched:
         rows = [tuple(int(v) for v in r) for r in table]
         self.n_win = len(rows)
         win = (HydeWindow * self.n_win)(*[HydeWindow(*r) for r in rows])
+        self._table = win
         self.plan = ctypes.c_void_p()
         _check(self.lib.hyde_windows_plan_create(p, H, W, win, self.n_win,
                                                  ctypes.byref(self.params),
@@ -709,6 +710,61 @@ class HyResWindowsBatched:
     def infos(self) -> list[dict]:
         raw = self.info.cpu()
         return [parse_info(raw[k * INFO_BYTES:(k + 1) * INFO_BYTES]) for k in range(self.n_win)]
+
+    def tuning(self) -> dict:
+        """The plan's tuned settings: projection tile and Gram role weight."""
+        tile = ctypes.c_int()
+        w = ctypes.c_double()
+        _check(self.lib.hyde_windows_plan_get_tuning(self.plan, ctypes.byref(tile),
+                                                     ctypes.byref(w)),
+               "hyde_windows_plan_get_tuning")
+        return {"proj_tile": tile.value, "gram_role_weight": w.value}
+
+    def set_tuning(self, proj_tile: int, gram_role_weight: float) -> None:
+        _check(self.lib.hyde_windows_plan_set_tuning(self.plan, int(proj_tile),
+                                                     float(gram_role_weight)),
+               "hyde_windows_plan_set_tuning")
+        self.graph = None   # a captured call keeps the grid sizes it was captured with
+
+    def _cache_key(self) -> str:
+        import hashlib
+        h = hashlib.sha1()
+        h.update(repr((self.shape, self.params.levels, self.params.r_max,
+                       self.params.n_lambda, torch.cuda.get_device_name(self.device))).encode())
+        h.update(bytes(self._table))
+        return h.hexdigest()
+
+    def autotune(self, Y: torch.Tensor, X: torch.Tensor | None = None,
+                 cache: str | None = None) -> dict:
+        """Pick the fastest tuning on this scene (hyde_windows_plan_autotune)
+        and return it with its time. With a cache file (JSON), a setting
+        stored there for the same scene shape, window table, parameters and
+        device is reused instead of timing, and a new result is stored."""
+        import json
+        import os
+        key = self._cache_key()
+        store = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                store = json.load(f)
+            if key in store:
+                t = store[key]
+                self.set_tuning(t["proj_tile"], t["gram_role_weight"])
+                return dict(t, cached=True)
+        Y = _cuda_f32(Y, "Y")
+        if X is None:
+            X = torch.empty_like(Y)
+        ms = ctypes.c_float()
+        _check(self.lib.hyde_windows_plan_autotune(self.plan, _ptr(Y), _ptr(X), _ptr(self.ws),
+                                                   self.ws.numel(), _stream(), ctypes.byref(ms)),
+               "hyde_windows_plan_autotune")
+        self.graph = None
+        t = dict(self.tuning(), ms=ms.value)
+        if cache:
+            store[key] = t
+            with open(cache, "w") as f:
+                json.dump(store, f, indent=1, sort_keys=True)
+        return dict(t, cached=False)
 
     def intermediates(self) -> dict:
         """Every window's Gram matrix R [n][p][p], noise levels sigma [n][p]

@@ -470,23 +470,21 @@ bool win_gram_supported(int p, int W, const float* Y) {
 }
 
 // Host plan of the pieces: the chunks of all windows (window by window, each
-// window's 8 x 4 blocks row by row) cut into G0 equal ranges for role 0 and
-// G1 for role 1.
-hyde_status win_gram_layout(int p, const int4* geo, int n_win, int sms, WinGramLayout* L) {
+// window's 32 x 2 blocks row by row) cut into G0 equal ranges for role 0 and
+// G1 for role 1. CTAs go to the roles in proportion to their work per chunk
+// (bands loaded + the MMA's N), role 1's weighted by w1x: its MMAs
+// (N = p - 128) cost nearly as much per instruction as role 0's, so it
+// needs more CTAs than its arithmetic (the batched plan tunes w1x; 1.6 on
+// the 2048 x 2048 x 200 scene: 2.57 ms against 2.88 at 1.2 and 2.91 at 2.2).
+hyde_status win_gram_layout(int p, const int4* geo, int n_win, int sms, double w1x,
+                            WinGramLayout* L) {
     if (p < 1 || p > kMaxP || n_win < 1 || sms < 1) return HYDE_ERR_SHAPE;
     for (int w = 0; w < n_win; ++w)
         if (geo[w].z < 1 || geo[w].w < 1 || (geo[w].y % 4) != 0) return HYDE_ERR_SHAPE;
     const bool two = p > 128;
-    // CTAs in proportion to the work per chunk (bands loaded + the MMA's N)
-// Role 1's MMAs (N = p - 128) cost nearly as much per instruction as role
-// 0's, so its CTAs count for more than its arithmetic: the weight factor
-// measured best at 1.6 on the 2048 x 2048 x 200 scene (2.57 ms against 2.88
-// at 1.2 and 2.91 at 2.2).
-#ifndef HYDE_WIN_W1X
-#define HYDE_WIN_W1X 1.6
-#endif
+    if (!(w1x > 0.0)) return HYDE_ERR_INVALID_ARG;
     const double w0 = (double)p + nt0_of(p),
-                 w1 = two ? HYDE_WIN_W1X * ((double)(p - 128) + (nt0_of(p) - 128)) : 0.0;
+                 w1 = two ? w1x * ((double)(p - 128) + (nt0_of(p) - 128)) : 0.0;
     int G0 = two ? (int)(sms * w0 / (w0 + w1) + 0.5) : sms;
     if (G0 < 1) G0 = 1;
     if (two && G0 > sms - 1) G0 = sms - 1;

@@ -339,7 +339,8 @@ struct WinGramLayout {
 };
 // geo[w] = (y0, x0, h, w); every x0 must be a multiple of 4
 bool win_gram_supported(int p, int W, const float* Y);
-hyde_status win_gram_layout(int p, const int4* geo, int n_win, int sms, WinGramLayout* L);
+hyde_status win_gram_layout(int p, const int4* geo, int n_win, int sms, double w1x,
+                            WinGramLayout* L);
 hyde_status launch_win_gram(const float* Y, int p, int H, int W, const int4* pieces,
                             const int* pbeg, const int4* geo, const int* wslot0,
                             const int* wslot1, int n_win, int G0, int G1, float* part0,
@@ -360,16 +361,16 @@ hyde_status launch_weights_batched(const double* V, const double* sigma, int p, 
 // The stages after the weights (windows_batched.cu): projection into the
 // padded component images, DWT, SURE tables and selection, thresholded
 // inverse DWT, back-projection of the cores into X.
-// tstart[w] .. tstart[w + 1]: window w's tiles of kWinProjTile padded pixels
-// (projection) or kWinBackTile core pixels (back-projection), n_tiles in all.
-// Measured on the 2048 x 2048 x 200 scene (whole call): projection tiles of
-// 1024 / 512 / 256 pixels 8.81 / 8.71 / 8.61 ms; back-projection tiles of
-// 512 / 1024 / 2048 core pixels 8.71 / 8.71 / 8.73 ms.
-constexpr int kWinProjTile = 256;
+// tstart[w] .. tstart[w + 1]: window w's tiles of `tile` padded pixels
+// (projection; a multiple of 256, tuned by the batched plan) or kWinBackTile
+// core pixels (back-projection), n_tiles in all. Measured on the 2048 x 2048
+// x 200 scene (whole call): projection tiles of 1024 / 512 / 256 pixels
+// 8.81 / 8.71 / 8.61 ms; back-projection tiles of 512 / 1024 / 2048 core
+// pixels 8.71 / 8.71 / 8.73 ms.
 constexpr int kWinBackTile = 1024;
 hyde_status launch_win_project(const float* Y, int p, int H, int W, const WinDesc* desc,
-                               const int* tstart, int n_win, int n_tiles, const float* P, int r,
-                               int ldw, float* Zp, cudaStream_t s);
+                               const int* tstart, int n_win, int n_tiles, int tile,
+                               const float* P, int r, int ldw, float* Zp, cudaStream_t s);
 // DWT of every kept component with the SURE histogram rows formed on the way
 hyde_status launch_win_dwt(const float* Zp, float* coef, float* scratch, const WinDesc* desc,
                            int n_win, int r, int levels, int K, unsigned int* counts,

@@ -241,7 +241,7 @@ template <int RM>
 __global__ void __launch_bounds__(kThreads)
 win_project_kernel(const float* __restrict__ Y, int p, int H, int W,
                    const WinDesc* __restrict__ desc, const int* __restrict__ tstart, int n_win,
-                   const float* __restrict__ P, int r, float* __restrict__ Zp) {
+                   int tile, const float* __restrict__ P, int r, float* __restrict__ Zp) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ float4 Ps4[];
@@ -256,8 +256,8 @@ win_project_kernel(const float* __restrict__ Y, int p, int H, int W,
     const long long bs = (long long)H * W;
     const float* Yw = Y + (long long)d.y0 * W + d.x0;
     float* Zw = Zp + d.img;
-    const int t0 = (t - __ldg(tstart + wi)) * kWinProjTile;
-    const int t1 = min(t0 + kWinProjTile, N);
+    const int t0 = (t - __ldg(tstart + wi)) * tile;
+    const int t1 = min(t0 + tile, N);
     for (int base = t0; base < t1; base += kThreads * kPix) {
         int src[kPix];
         bool live[kPix];
@@ -427,17 +427,17 @@ hyde_status launch_backproject(const float* Zh, long long n, const float* Q, int
 }
 
 hyde_status launch_win_project(const float* Y, int p, int H, int W, const WinDesc* desc,
-                               const int* tstart, int n_win, int n_tiles, const float* P, int r,
-                               int ldw, float* Zp, cudaStream_t s) {
+                               const int* tstart, int n_win, int n_tiles, int tile,
+                               const float* P, int r, int ldw, float* Zp, cudaStream_t s) {
     const size_t smem = (size_t)p * ldw * sizeof(float);
-    if (smem > 227 * 1024 || n_tiles < 1) return HYDE_ERR_SHAPE;
+    if (smem > 227 * 1024 || n_tiles < 1 || tile < 256 || (tile % 256) != 0) return HYDE_ERR_SHAPE;
     switch (ldw) {
 #define HYDE_WPROJ(RMV)                                                                         \
     case RMV:                                                                                   \
         if (ensure_smem_limit((const void*)win_project_kernel<RMV>, (int)smem) != cudaSuccess)  \
             return HYDE_ERR_CUDA;                                                               \
         launch_pdl(win_project_kernel<RMV>, n_tiles, kThreads, smem, s, Y, p, H, W, desc, tstart, \
-                   n_win, P, r, Zp);                                                            \
+                   n_win, tile, P, r, Zp);                                                      \
         break;
         HYDE_WPROJ(4) HYDE_WPROJ(8) HYDE_WPROJ(12) HYDE_WPROJ(16)
         HYDE_WPROJ(20) HYDE_WPROJ(24) HYDE_WPROJ(28) HYDE_WPROJ(32)

@@ -36,7 +36,12 @@ struct WinGroup {
 };
 
 struct hyde_windows_plan_s {
-    int p, H, W, n_win, r, L, K, RM, ngroups;
+    int p, H, W, n_win, r, L, K, RM, ngroups, sms;
+    int proj_tile;           // tuned: projection tile (padded pixels)
+    double w1x;              // tuned: weight of the Gram's second band role
+    std::vector<int4> geo_v;             // (y0, x0, h, w) per window
+    std::vector<long long> npad;         // padded pixels per window
+    std::vector<int> tback_v;            // back-projection tile prefix
     WinGroup g[kGroups];
     void* host;              // page-locked copy of the tables
     size_t tables;           // their bytes (the head of the workspace)
@@ -95,6 +100,43 @@ T* at(void* base, size_t off) {
 
 }  // namespace
 
+// The tables that depend on the tuned parameters (the Gram pieces and CTA
+// split of each group, the projection tile tables), written into the plan's
+// page-locked copy. The workspace is carved for every setting at once.
+static hyde_status fill_tables(hyde_windows_plan_s* P, int tile, double w1x) {
+    if (tile < 256 || tile > 4096 || (tile % 256) != 0 || !(w1x > 0.0) || w1x > 16.0)
+        return HYDE_ERR_INVALID_ARG;
+    for (int gi = 0; gi < P->ngroups; ++gi) {
+        WinGroup& g = P->g[gi];
+        WinGramLayout G;
+        const hyde_status st = win_gram_layout(P->p, P->geo_v.data() + g.w0, g.n, P->sms, w1x, &G);
+        if (st != HYDE_OK) return st;
+        // the carve holds at most sms + n pieces per role and sms + 1 CTA starts
+        if (G.pieces.size() > (size_t)2 * (P->sms + g.n) || G.pbeg.size() > (size_t)P->sms + 1)
+            return HYDE_ERR_SHAPE;
+        g.G0 = G.G0;
+        g.G1 = G.G1;
+        std::vector<int> tp(g.n + 1, 0), tb(g.n + 1, 0);
+        for (int k = 0; k < g.n; ++k) {
+            tp[k + 1] = tp[k] + (int)((P->npad[g.w0 + k] + tile - 1) / tile);
+            tb[k + 1] = P->tback_v[g.w0 + k + 1] - P->tback_v[g.w0];
+        }
+        g.proj_tiles = tp[g.n];
+        g.back_tiles = tb[g.n];
+        memset(at<char>(P->host, g.pieces), 0, (size_t)2 * (P->sms + g.n) * sizeof(int4));
+        if (!G.pieces.empty())
+            memcpy(at<char>(P->host, g.pieces), G.pieces.data(), G.pieces.size() * sizeof(int4));
+        memcpy(at<char>(P->host, g.pbeg), G.pbeg.data(), G.pbeg.size() * sizeof(int));
+        memcpy(at<char>(P->host, g.wslot0), G.wslot0.data(), (g.n + 1) * sizeof(int));
+        memcpy(at<char>(P->host, g.wslot1), G.wslot1.data(), (g.n + 1) * sizeof(int));
+        memcpy(at<char>(P->host, g.tproj), tp.data(), (g.n + 1) * sizeof(int));
+        memcpy(at<char>(P->host, g.tback), tb.data(), (g.n + 1) * sizeof(int));
+    }
+    P->proj_tile = tile;
+    P->w1x = w1x;
+    return HYDE_OK;
+}
+
 extern "C" {
 
 hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win, int n_win,
@@ -113,7 +155,7 @@ hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win
     const int r = params->r_max, L = params->levels, K = params->n_lambda;
     std::vector<WinDesc> D(n_win);
     std::vector<int4> geo(n_win);
-    std::vector<int> tproj(n_win + 1, 0), tback(n_win + 1, 0);
+    std::vector<int> tback(n_win + 1, 0);
     long long img = 0, scr = 0;
     for (int k = 0; k < n_win; ++k) {
         const hyde_window& wn = win[k];
@@ -135,7 +177,6 @@ hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win
         scr += (long long)align_up((size_t)(r * win_scratch_stride(N)), 64);
         D[k] = d;
         geo[k] = make_int4(wn.y0, wn.x0, wn.h, wn.w);
-        tproj[k + 1] = tproj[k] + (int)((N + kWinProjTile - 1) / kWinProjTile);
         tback[k + 1] =
             tback[k] + (int)(((long long)wn.ch * wn.cw + kWinBackTile - 1) / kWinBackTile);
     }
@@ -156,31 +197,27 @@ hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win
         for (; gi < ngroups; ++gi) wb[gi] = wb[gi - 1] + 1;
         wb[ngroups] = n_win;
     }
-    WinGramLayout GL[kGroups];
-    for (int gi = 0; gi < ngroups; ++gi) {
-        hyde_status st = win_gram_layout(p, geo.data() + wb[gi], wb[gi + 1] - wb[gi], sms, &GL[gi]);
-        if (st != HYDE_OK) return st;
-    }
 
     hyde_windows_plan_s* P = new hyde_windows_plan_s();
     P->p = p; P->H = H; P->W = W; P->n_win = n_win; P->r = r; P->L = L; P->K = K;
     P->RM = (r + 3) / 4 * 4;
     P->ngroups = ngroups;
+    P->sms = sms;
+    P->geo_v = geo;
+    P->npad.resize(n_win);
+    for (int k = 0; k < n_win; ++k) P->npad[k] = (long long)D[k].Hp * D[k].Wp;
+    P->tback_v = tback;
     const size_t n = (size_t)n_win, pp = (size_t)p * p;
+    const size_t rows0 = (size_t)(p < 128 ? p : 128), rows1 = (size_t)(p > 128 ? p - 128 : 0);
     Carve c;
     P->desc = c.take(n * sizeof(WinDesc));
     P->geo = c.take(n * sizeof(int4));
     for (int gi = 0; gi < ngroups; ++gi) {
         WinGroup& g = P->g[gi];
-        const WinGramLayout& G = GL[gi];
         g.w0 = wb[gi];
         g.n = wb[gi + 1] - wb[gi];
-        g.G0 = G.G0;
-        g.G1 = G.G1;
-        g.proj_tiles = tproj[wb[gi + 1]] - tproj[wb[gi]];
-        g.back_tiles = tback[wb[gi + 1]] - tback[wb[gi]];
-        g.pieces = c.take(G.pieces.size() * sizeof(int4));
-        g.pbeg = c.take(G.pbeg.size() * sizeof(int));
+        g.pieces = c.take((size_t)2 * (sms + g.n) * sizeof(int4));
+        g.pbeg = c.take((size_t)(sms + 1) * sizeof(int));
         g.wslot0 = c.take((g.n + 1) * sizeof(int));
         g.wslot1 = c.take((g.n + 1) * sizeof(int));
         g.tproj = c.take((g.n + 1) * sizeof(int));
@@ -207,13 +244,16 @@ hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win
     P->rank = c.take(n * sizeof(int));
     P->lam = c.take(n * sizeof(double));
     for (int gi = 0; gi < ngroups; ++gi) {
-        P->g[gi].part0 = c.take((GL[gi].part0_floats > 0 ? GL[gi].part0_floats : 4) * sizeof(float));
-        P->g[gi].part1 = c.take((GL[gi].part1_floats > 0 ? GL[gi].part1_floats : 4) * sizeof(float));
+        // a role's pieces: at most one per CTA plus one per window boundary
+        const size_t slots = (size_t)sms + P->g[gi].n;
+        P->g[gi].part0 = c.take((slots * rows0 * p > 0 ? slots * rows0 * p : 4) * sizeof(float));
+        P->g[gi].part1 = c.take((slots * rows1 * rows1 > 0 ? slots * rows1 * rows1 : 4) * sizeof(float));
     }
     P->total = c.off;
 
     if (cudaMallocHost(&P->host, P->tables) != cudaSuccess) {
-        delete P;
+        P->host = nullptr;
+        hyde_windows_plan_destroy(P);
         return HYDE_ERR_CUDA;
     }
     if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -225,22 +265,11 @@ hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win
     memset(P->host, 0, P->tables);
     memcpy(at<char>(P->host, P->desc), D.data(), n * sizeof(WinDesc));
     memcpy(at<char>(P->host, P->geo), geo.data(), n * sizeof(int4));
-    for (int gi = 0; gi < ngroups; ++gi) {
-        const WinGroup& g = P->g[gi];
-        const WinGramLayout& G = GL[gi];
-        if (!G.pieces.empty())
-            memcpy(at<char>(P->host, g.pieces), G.pieces.data(), G.pieces.size() * sizeof(int4));
-        memcpy(at<char>(P->host, g.pbeg), G.pbeg.data(), G.pbeg.size() * sizeof(int));
-        memcpy(at<char>(P->host, g.wslot0), G.wslot0.data(), (g.n + 1) * sizeof(int));
-        memcpy(at<char>(P->host, g.wslot1), G.wslot1.data(), (g.n + 1) * sizeof(int));
-        // tile tables relative to the group's first window
-        std::vector<int> tp(g.n + 1), tb(g.n + 1);
-        for (int k = 0; k <= g.n; ++k) {
-            tp[k] = tproj[g.w0 + k] - tproj[g.w0];
-            tb[k] = tback[g.w0 + k] - tback[g.w0];
-        }
-        memcpy(at<char>(P->host, g.tproj), tp.data(), (g.n + 1) * sizeof(int));
-        memcpy(at<char>(P->host, g.tback), tb.data(), (g.n + 1) * sizeof(int));
+    // defaults: the settings measured best on the 2048 x 2048 x 200 scene
+    const hyde_status st = fill_tables(P, 256, 1.6);
+    if (st != HYDE_OK) {
+        hyde_windows_plan_destroy(P);
+        return st;
     }
     *out = P;
     return HYDE_OK;
@@ -257,6 +286,20 @@ int hyde_windows_plan_kernel_launches(hyde_windows_plan plan) {
     // DWT with the SURE histogram 1, SURE selection 1, inverse DWT 1,
     // back-projection 1
     return plan ? 12 * plan->ngroups : -1;
+}
+
+hyde_status hyde_windows_plan_set_tuning(hyde_windows_plan plan, int proj_tile,
+                                         double gram_role_weight) {
+    if (!plan) return HYDE_ERR_INVALID_ARG;
+    return fill_tables(plan, proj_tile, gram_role_weight);
+}
+
+hyde_status hyde_windows_plan_get_tuning(hyde_windows_plan plan, int* proj_tile,
+                                         double* gram_role_weight) {
+    if (!plan || !proj_tile || !gram_role_weight) return HYDE_ERR_INVALID_ARG;
+    *proj_tile = plan->proj_tile;
+    *gram_role_weight = plan->w1x;
+    return HYDE_OK;
 }
 
 hyde_status hyde_windows_plan_layout(hyde_windows_plan plan, hyde_windows_ws_layout* out) {
@@ -308,7 +351,7 @@ static hyde_status enqueue_group(const hyde_windows_plan_s* P, const WinGroup& g
                                     P->eig_stride, status, n, s));
     HYDE_TRY(launch_weights_batched(V, sigma, p, r, P->RM, Pw, Qw, n, s));
     HYDE_TRY(launch_win_project(Y, p, P->H, P->W, desc, at<int>(ws, g.tproj), n, g.proj_tiles,
-                                Pw, r, P->RM, zp, s));
+                                P->proj_tile, Pw, r, P->RM, zp, s));
     unsigned int* counts = at<unsigned int>(ws, P->counts) + (size_t)w0 * r * P->K;
     double* sums = at<double>(ws, P->sums) + (size_t)w0 * r * P->K;
     double* sum_all = at<double>(ws, P->sum_all) + (size_t)w0 * r;
@@ -344,6 +387,67 @@ hyde_status hyde_hyres_denoise_windows_batched(const float* Y, float* X, hyde_wi
         return HYDE_ERR_CUDA;
     if (st == HYDE_OK) st = st2;
     return st;
+}
+
+// Times every candidate setting on the caller's scene (one untimed call,
+// then the median of three, CUDA events on `stream`) and keeps the fastest.
+hyde_status hyde_windows_plan_autotune(hyde_windows_plan P, const float* Y, float* X, void* ws,
+                                       size_t ws_bytes, cudaStream_t stream, float* best_ms) {
+    if (!P) return HYDE_ERR_INVALID_ARG;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return HYDE_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return HYDE_ERR_INVALID_ARG;
+    static const int kTiles[] = {256, 512, 1024};
+    static const double kWeights[] = {1.2, 1.6, 2.0};
+    const int nw = P->p > 128 ? 3 : 1;   // the weight only splits two band roles
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return HYDE_ERR_CUDA;
+    }
+    const int tile0 = P->proj_tile;
+    const double w0 = P->w1x;
+    int best_tile = tile0;
+    double best_w = w0;
+    float best = -1.f;
+    hyde_status st = HYDE_OK;
+    for (int ti = 0; ti < 3 && st == HYDE_OK; ++ti) {
+        for (int wi = 0; wi < nw && st == HYDE_OK; ++wi) {
+            const double w = nw == 1 ? w0 : kWeights[wi];
+            // the previous setting's calls have finished: its tables may change
+            if (cudaStreamSynchronize(stream) != cudaSuccess) { st = HYDE_ERR_CUDA; break; }
+            st = fill_tables(P, kTiles[ti], w);
+            if (st != HYDE_OK) break;
+            float ms[3];
+            for (int it = 0; it < 4 && st == HYDE_OK; ++it) {
+                if (it > 0 && cudaEventRecord(e0, stream) != cudaSuccess) st = HYDE_ERR_CUDA;
+                if (st == HYDE_OK)
+                    st = hyde_hyres_denoise_windows_batched(Y, X, P, nullptr, ws, ws_bytes, stream);
+                if (st == HYDE_OK && it > 0) {
+                    if (cudaEventRecord(e1, stream) != cudaSuccess ||
+                        cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms[it - 1], e0, e1) != cudaSuccess)
+                        st = HYDE_ERR_CUDA;
+                }
+            }
+            if (st != HYDE_OK) break;
+            float a = ms[0], b = ms[1], c = ms[2];   // median of three
+            const float med = a > b ? (b > c ? b : (a > c ? c : a)) : (a > c ? a : (b > c ? c : b));
+            if (best < 0.f || med < best) {
+                best = med;
+                best_tile = kTiles[ti];
+                best_w = w;
+            }
+        }
+    }
+    cudaStreamSynchronize(stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const hyde_status st2 = fill_tables(P, st == HYDE_OK ? best_tile : tile0,
+                                        st == HYDE_OK ? best_w : w0);
+    if (st != HYDE_OK) return st;
+    if (best_ms) *best_ms = best;
+    return st2;
 }
 
 }  // extern "C"

@@ -325,3 +325,8 @@ def test_windows_plan_rejects_bad_tables_on_host(lib):
     assert plan.value is None
     assert lib.hyde_windows_plan_kernel_launches(None) == -1
     assert lib.hyde_windows_plan_destroy(None) == 1
+    tile = ctypes.c_int()
+    wgt = ctypes.c_double()
+    assert lib.hyde_windows_plan_set_tuning(None, 256, 1.6) == 1
+    assert lib.hyde_windows_plan_get_tuning(None, ctypes.byref(tile), ctypes.byref(wgt)) == 1
+    assert lib.hyde_windows_plan_autotune(None, None, None, None, 0, None, None) == 1

@@ -143,3 +143,36 @@ def test_windows_batched_gram_and_sigma(hyde, H, W, p, depth, seed):
         assert err.max() < 2e-6, (k, err.max())
         s_ref = O.noise_est_regression(R, h * w)
         assert np.max(np.abs(S_all[k] / s_ref - 1)) < 5e-4, k
+
+
+def test_windows_batched_autotune_and_cache(hyde, tmp_path):
+    """The tuner times its candidates on the scene and keeps one of them; the
+    tuned plan still matches the oracle; the cache file hands the same
+    setting to a new plan without timing; out-of-range settings are refused."""
+    H, W, p, L, r = 128, 160, 140, 2, 8
+    T = make_window_table(H, W, depth=3, context=8, min_side=24, max_side=96, seed=3)
+    sc = make_scene(H, W, p, T, m=4, seed=3)
+    Y = torch.from_numpy(sc["Y"]).cuda()
+    win = hyde.HyResWindowsBatched(p, H, W, T, L, r)
+    assert win.tuning() == {"proj_tile": 256, "gram_role_weight": 1.6}
+    cache = str(tmp_path / "tuning.json")
+    t = win.autotune(Y, cache=cache)
+    assert not t["cached"] and t["ms"] > 0
+    assert t["proj_tile"] in (256, 512, 1024) and t["gram_role_weight"] in (1.2, 1.6, 2.0)
+    X = torch.full_like(Y, float("nan"))
+    win(Y, X)
+    torch.cuda.synchronize()
+    infos = win.infos()
+    num = den = 0.0
+    for k, row in enumerate(T):
+        got, ref = _check_window(sc["Y"], row, L, r, infos[k], X, k, tie_tol=TIE_TOL)
+        num += float(np.sum((got.astype(np.float64) - ref) ** 2))
+        den += float(np.sum(ref ** 2))
+    assert np.sqrt(num / den) < 3e-5
+    win2 = hyde.HyResWindowsBatched(p, H, W, T, L, r)
+    t2 = win2.autotune(Y, cache=cache)
+    assert t2["cached"]
+    assert win2.tuning() == {"proj_tile": t["proj_tile"], "gram_role_weight": t["gram_role_weight"]}
+    for bad in ((128, 1.6), (300, 1.6), (256, 0.0), (256, 20.0)):
+        with pytest.raises(RuntimeError):
+            win2.set_tuning(*bad)
