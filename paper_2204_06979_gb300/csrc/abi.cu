@@ -439,7 +439,7 @@ static hyde_status hyres_enqueue(const float* Y, float* X, int p, int H, int W,
     HYDE_TRY(stage());
     // 6. wavelet analysis
     DwtSrc src{zp, L.N, L.Wp, L.Hp, L.Wp};
-    HYDE_TRY(launch_dwt2(src, coef, r, L.Hp, L.Wp, lev, scratch, stream));
+    HYDE_TRY(launch_dwt2(src, coef, r, L.Hp, L.Wp, lev, scratch, stream, status));
     HYDE_TRY(stage());
     // 7-8. SURE table and (rank, lambda) selection
     const long long N_det =
@@ -591,7 +591,7 @@ hyde_status hyde_wsrrr(const float* Y, float* X, int p, int H, int W,
     auto bstep = [&]() -> hyde_status {
         HYDE_TRY(launch_weights(V, sigma, p, r, L.RM, P, Q, stream));
         HYDE_TRY(launch_project_pad(Y, p, H, W, P, r, L.RM, zp, L.Hp, L.Wp, stream));
-        return launch_dwt2(src, coef, r, L.Hp, L.Wp, lev, scratch, stream);
+        return launch_dwt2(src, coef, r, L.Hp, L.Wp, lev, scratch, stream, status);
     };
     for (int it = 0; it < iters; ++it) {
         HYDE_TRY(bstep());

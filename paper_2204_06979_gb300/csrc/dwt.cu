@@ -19,7 +19,12 @@
 // of the same launch writes. (A pipelined synthesis with the same structure
 // as the analysis measured slower on the 20 x 352 x 1920 components: its
 // blocks hold too few tiles to hide the first load.)
+#include <cuda.h>
+#include <string.h>
+
 #include "hyde_internal.cuh"
+#include "tc_common.cuh"
+#include "tmap.cuh"
 
 namespace hyde {
 namespace {
@@ -39,17 +44,26 @@ __device__ __forceinline__ int wrap(int v, int m) {
 // g, g + G, ... of one image, 16 x 64 coefficients per subband each, from a
 // 34 x 132 input tile (rows and columns past the valid hv x wv source are
 // read through the whole-sample symmetric extension).
-// The next tile streams into the other half of a double buffer with cp.async
-// (16-byte copies where the row is 16-byte aligned and the chunk does not
-// reach the image edge, 4-byte copies with the periodic wrap elsewhere)
-// while the current one is filtered: the row pass reads 10 inputs and writes
-// 4 outputs per thread as float4, the column pass forms the four subbands of
-// 4 coefficients per thread and stores them as float4 rows.
+// The next tile streams into the other half of a double buffer while the
+// current one is filtered: the row pass reads 10 inputs and writes 4 outputs
+// per thread as float4, the column pass forms the four subbands of 4
+// coefficients per thread and stores them as float4 rows.
+// Interior tiles (the whole 34 x 132 box inside the valid source) are one
+// TMA copy (a 3D tensor map over width, height and image; x = 2 tx0 is a
+// multiple of 128 floats), completed on the buffer's mbarrier. Tiles that
+// meet the halo (periodic wrap of the padded image, symmetric extension of
+// an unpadded one) are gathered with cp.async instead: 16-byte copies where
+// the row is 16-byte aligned and the chunk stays inside the valid width,
+// 4-byte copies through the wrap and the reflection elsewhere.
 // --------------------------------------------------------------------------
 constexpr int FTH = 16, FTW = 64;           // coefficients per subband per tile
 constexpr int FIH = 2 * FTH + 2;            // input rows
 constexpr int FIW = 2 * FTW + 4;            // input columns (2 FTW + 2 used, multiple of 4)
+constexpr int FIBUF = 4512;                 // buffer stride in floats (FIH FIW rounded to 128 B)
 constexpr int kFThreads = 256;
+constexpr uint32_t kTileBytes = FIH * FIW * sizeof(float);
+static_assert(FIBUF >= FIH * FIW && (FIBUF * sizeof(float)) % 128 == 0, "buffer stride");
+static_assert((FIW * sizeof(float)) % 16 == 0 && FIW <= 256 && FIH <= 256, "TMA box");
 
 __device__ __forceinline__ void cpa16(float* dst, const float* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -64,16 +78,30 @@ template <int N>
 __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 __global__ void __launch_bounds__(kFThreads)
-dwt_level_pipe_kernel(const float* __restrict__ src, long long src_bs, int src_ld, int hv,
+dwt_level_pipe_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma,
+                      unsigned long long wait_ns, int* __restrict__ status,
+                      const float* __restrict__ src, long long src_bs, int src_ld, int hv,
                       int wv, int h, int w, float* __restrict__ coef, long long coef_bs,
                       int coef_ld, float* __restrict__ ll, long long ll_bs, int ll_ld) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ float4 fsm4[];
-    float* inb = reinterpret_cast<float*>(fsm4);     // [2][FIH][FIW]
-    float* ra = inb + 2 * FIH * FIW;                  // [FIH][FTW]
+    __shared__ __align__(8) uint64_t full[2];          // TMA completion, one per buffer
+    // the TMA destination wants 128-byte alignment: round the dynamic base up
+    const uint32_t base_s = smem_u32(fsm4);
+    float* inb = reinterpret_cast<float*>(reinterpret_cast<char*>(fsm4) +
+                                          (((base_s + 127u) & ~127u) - base_s));   // [2][FIBUF]
+    float* ra = inb + 2 * FIBUF;                      // [FIH][FTW]
     float* rd = ra + FIH * FTW;                       // [FIH][FTW]
     const int tid = threadIdx.x;
+    if (use_tma && tid == 0) {
+        mbar_init(smem_u32(&full[0]), 1);
+        mbar_init(smem_u32(&full[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
+                     : "memory");
+    }
+    __syncthreads();
     const int b = blockIdx.y, G = gridDim.x;
     const int hh = h >> 1, wh = w >> 1;
     const int tiles_x = (wh + FTW - 1) / FTW, tiles_y = (hh + FTH - 1) / FTH;
@@ -86,9 +114,24 @@ dwt_level_pipe_kernel(const float* __restrict__ src, long long src_bs, int src_l
                       ((reinterpret_cast<uintptr_t>(CB) & 15) == 0) &&
                       ((reinterpret_cast<uintptr_t>(LB) & 15) == 0);
 
+    // tma_pend bit j: the tile in buffer j is a TMA copy not yet waited for;
+    // phase bit j: the parity that buffer j's barrier completes next
+    unsigned tma_pend = 0, phase = 0;
     auto load_tile = [&](int t, int buf) {
         const int ty0 = (t / tiles_x) * FTH, tx0 = (t % tiles_x) * FTW;
-        float* in = inb + buf * FIH * FIW;
+        float* in = inb + buf * FIBUF;
+        if (use_tma && 2 * tx0 + FIW <= wv && 2 * ty0 + FIH <= hv) {
+            if (tid == 0) {
+                // the buffer's last generic reads finished before the block
+                // barrier that precedes this call; order them before the copy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const uint32_t bar = smem_u32(&full[buf]);
+                mbar_arrive_expect_tx(bar, kTileBytes);
+                tma_load_3d(smem_u32(in), &tmap, 2 * tx0, 2 * ty0, b, bar);
+            }
+            tma_pend |= 1u << buf;
+            return;
+        }
         for (int e = tid; e < FIH * (FIW / 4); e += kFThreads) {
             const int r = e / (FIW / 4), cq = e - r * (FIW / 4);
             int y = wrap(2 * ty0 + r, h);
@@ -117,8 +160,29 @@ dwt_level_pipe_kernel(const float* __restrict__ src, long long src_bs, int src_l
         if (t + G < ntiles) load_tile(t + G, buf ^ 1);
         cpa_commit();
         cpa_wait<1>();
-        __syncthreads();   // tile t landed; the previous column pass is done
-        const float* in = inb + buf * FIH * FIW;
+        int late = 0;
+        if (tma_pend & (1u << buf)) {
+            late = !mbar_wait_bounded(smem_u32(&full[buf]), (phase >> buf) & 1u, wait_ns);
+            tma_pend &= ~(1u << buf);
+            phase ^= 1u << buf;
+        }
+        // tile t landed; the previous column pass is done
+        if (__syncthreads_or(late)) {
+            // a copy did not complete in time: report it, let the copies
+            // still in flight land (bounded by the default limit, whatever
+            // the configured one, so that none outlives the block), and stop
+            if (tid == 0) {
+                set_status(status, HYDE_ERR_TIMEOUT);
+                if (late)   // this buffer's copy, whose phase was already passed on
+                    mbar_wait_bounded(smem_u32(&full[buf]), ((phase >> buf) & 1u) ^ 1u, kWaitNs);
+                if (tma_pend & (1u << (buf ^ 1)))
+                    mbar_wait_bounded(smem_u32(&full[buf ^ 1]), (phase >> (buf ^ 1)) & 1u,
+                                      kWaitNs);
+            }
+            cpa_wait<0>();
+            return;
+        }
+        const float* in = inb + buf * FIBUF;
         for (int e = tid; e < FIH * (FTW / 4); e += kFThreads) {
             const int r = e / (FTW / 4), kq = e - r * (FTW / 4);
             const float* ir = in + r * FIW + 8 * kq;
@@ -569,10 +633,33 @@ static inline bool aligned16(const void* p) {
     return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
 }
 
+// Tensor map of the TMA copies of the interior tiles of one analysis level:
+// the source as width x height x image (floats), box FIW x FIH x 1. False
+// (cp.async for every tile) where the layout does not allow it: a base or a
+// row or image stride not a multiple of 16 bytes, a source smaller than the
+// box, or no encoder in the driver.
+static bool dwt_tmap(const float* sp, long long sbs, int sld, int hv, int wv, int batch,
+                     CUtensorMap* tm) {
+    if ((reinterpret_cast<uintptr_t>(sp) & 15) != 0 || (sld & 3) != 0 || (sbs & 3) != 0 ||
+        wv < FIW || hv < FIH || sld < wv || sbs < (long long)sld * hv)
+        return false;
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)wv, (cuuint64_t)hv, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)sld * sizeof(float),
+                                   (cuuint64_t)sbs * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)FIW, (cuuint32_t)FIH, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(sp), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int Wp,
-                        int levels, float* scratch, cudaStream_t s) {
+                        int levels, float* scratch, cudaStream_t s, int* status) {
     const long long cbs = (long long)Hp * Wp;
-    const size_t pipe_smem = (size_t)(2 * FIH * FIW + 2 * FIH * FTW) * sizeof(float);
+    const size_t pipe_smem = (size_t)(2 * FIBUF + 2 * FIH * FTW) * sizeof(float) + 128;
     if (ensure_smem_limit((const void*)dwt_level_pipe_kernel, (int)pipe_smem) != cudaSuccess)
         return HYDE_ERR_CUDA;
     const int sms = device_sm_count();
@@ -611,8 +698,14 @@ hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp, int W
         int G = (pipe_per_sm * sms + batch - 1) / batch;
         if (G > ntiles) G = ntiles;
         if (G < 1) G = 1;
-        launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s, sp, sbs, sld,
-                   hv, wv, h, w, coef, cbs, Wp, lp, lbs, lld);
+        // TMA copies for the interior tiles only where a timeout can be
+        // reported (the caller passed a status word)
+        CUtensorMap tm;
+        memset(&tm, 0, sizeof(tm));
+        const int use_tma = status && dwt_tmap(sp, sbs, sld, hv, wv, batch, &tm) ? 1 : 0;
+        launch_pdl(dwt_level_pipe_kernel, dim3(G, batch), kFThreads, pipe_smem, s, tm, use_tma,
+                   wait_limit_ns(), status, sp, sbs, sld, hv, wv, h, w, coef, cbs, Wp, lp, lbs,
+                   lld);
     }
     if (lo <= levels) {
         long long bs;

@@ -551,7 +551,7 @@ extern "C" hyde_status hyde_forpdn(const float* Y, float* X, int p, int H, int W
     if (st != HYDE_OK) return st;
     // 2. DWT of every band, read through the symmetric extension
     const DwtSrc src{Y, L.n, W, H, W};
-    st = launch_dwt2(src, coef, p, L.Hp, L.Wp, levels, scratch, stream);
+    st = launch_dwt2(src, coef, p, L.Hp, L.Wp, levels, scratch, stream, status);
     if (st != HYDE_OK) return st;
     // 3. Gram matrices of the groups' spectra
     float* gpart = fp_at<float>(ws, L.gpart);

@@ -255,8 +255,12 @@ struct DwtSrc {
 size_t dwt_scratch_floats(int Hp, int Wp);
 // kernel launches of launch_dwt2 / launch_idwt2 on a padded Hp x Wp image (aligned buffers)
 int dwt_launches(int Hp, int Wp, int levels);   // per image, both ping-pong halves
+// status (may be NULL): receives HYDE_ERR_TIMEOUT if a TMA copy of an
+// interior tile does not complete within the wait limit; without it every
+// tile is gathered with cp.async.
 hyde_status launch_dwt2(const DwtSrc& src, float* coef, int batch, int Hp,
-                        int Wp, int levels, float* scratch, cudaStream_t s);
+                        int Wp, int levels, float* scratch, cudaStream_t s,
+                        int* status = nullptr);
 // Synthesis with optional soft threshold of detail coefficients at *lam
 // (times scale[image * scale_ld + level - 1] when scale != NULL) and an
 // optional rank limit (*rank images are processed; NULL = all). ll_thr: the
