@@ -608,6 +608,27 @@ def test_scaled_forward_at_unit_scale_is_hyres():
     assert O.rel_l2(o["X_scaled"], o["X"]) < 1e-13
 
 
+def test_whiten_gram_is_gram_of_whitened_cube_and_mse_hand_case():
+    """R_w = D^-1 R D^-1 equals the Gram matrix of the cube with each band
+    divided by its sigma, formed by a pixel loop (not a matrix product); the
+    MSE of a hand case: two voxels off by 1 and 3 among four give 10 / 4."""
+    rng = np.random.default_rng(61)
+    Y = rng.integers(-4, 5, size=(3, 2, 5)).astype(np.float64)
+    sigma = np.array([0.5, 2.0, 4.0])
+    Yw = Y / sigma[:, None, None]
+    want = np.zeros((3, 3))
+    for yy in range(2):
+        for xx in range(5):
+            v = Yw[:, yy, xx]
+            for i in range(3):
+                for j in range(3):
+                    want[i, j] += v[i] * v[j]
+    assert np.allclose(O.whiten_gram(O.gram(Y), sigma), want, rtol=1e-14, atol=0)
+    Xh = np.array([[[1.0, 2.0], [3.0, 4.0]]])
+    Xc = np.array([[[0.0, 2.0], [3.0, 7.0]]])
+    assert O.mse_loss(Xh, Xc) == 10.0 / 4.0
+
+
 def test_level_map_counts():
     lev = O.level_map(32, 48, 3)
     assert np.count_nonzero(lev == 0) == 4 * 6
