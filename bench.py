@@ -1020,7 +1020,7 @@ def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--streams", type=int, default=3,
+    ap.add_argument("--streams", type=int, default=4,
                     help="cubes in flight for the headline (hyde_hyres_denoise_many); 1 = one "
                          "cube at a time")
     ap.add_argument("--warmup", type=int, default=5)

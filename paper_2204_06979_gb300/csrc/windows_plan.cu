@@ -45,8 +45,8 @@ struct hyde_windows_plan_s {
     WinGroup g[kGroups];
     void* host;              // page-locked copy of the tables
     size_t tables;           // their bytes (the head of the workspace)
-    cudaStream_t side;       // the second group's stream
-    cudaEvent_t fork, join;
+    cudaStream_t side[kGroups - 1];      // the streams of groups 1, 2, ...
+    cudaEvent_t fork, join[kGroups - 1];
     // workspace offsets
     size_t desc, geo;
     size_t status, R, sigma, Ainv, S, eig, eig_stride, evals, V, P, Q;
@@ -256,9 +256,11 @@ hyde_status hyde_windows_plan_create(int p, int H, int W, const hyde_window* win
         hyde_windows_plan_destroy(P);
         return HYDE_ERR_CUDA;
     }
-    if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming) != cudaSuccess) {
+    bool made = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int gi = 0; made && gi + 1 < kGroups; ++gi)
+        made = cudaStreamCreateWithFlags(&P->side[gi], cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&P->join[gi], cudaEventDisableTiming) == cudaSuccess;
+    if (!made) {
         hyde_windows_plan_destroy(P);
         return HYDE_ERR_CUDA;
     }
@@ -313,9 +315,11 @@ hyde_status hyde_windows_plan_layout(hyde_windows_plan plan, hyde_windows_ws_lay
 hyde_status hyde_windows_plan_destroy(hyde_windows_plan plan) {
     if (!plan) return HYDE_ERR_INVALID_ARG;
     if (plan->host) cudaFreeHost(plan->host);
-    if (plan->side) cudaStreamDestroy(plan->side);
+    for (int gi = 0; gi + 1 < kGroups; ++gi) {
+        if (plan->side[gi]) cudaStreamDestroy(plan->side[gi]);
+        if (plan->join[gi]) cudaEventDestroy(plan->join[gi]);
+    }
     if (plan->fork) cudaEventDestroy(plan->fork);
-    if (plan->join) cudaEventDestroy(plan->join);
     delete plan;
     return HYDE_OK;
 }
@@ -376,16 +380,18 @@ hyde_status hyde_hyres_denoise_windows_batched(const float* Y, float* X, hyde_wi
         cudaMemsetAsync(status, 0, (size_t)(P->n_win + 1) * sizeof(int), s) != cudaSuccess)
         return HYDE_ERR_CUDA;
     if (P->ngroups == 1) return enqueue_group(P, P->g[0], Y, X, info, ws, s);
-    // the second group on the plan's stream, forked from and joined back to s
-    if (cudaEventRecord(P->fork, s) != cudaSuccess ||
-        cudaStreamWaitEvent(P->side, P->fork, 0) != cudaSuccess)
-        return HYDE_ERR_CUDA;
+    // groups 1, 2, ... on the plan's streams, forked from and joined back to s
+    if (cudaEventRecord(P->fork, s) != cudaSuccess) return HYDE_ERR_CUDA;
+    for (int gi = 1; gi < P->ngroups; ++gi)
+        if (cudaStreamWaitEvent(P->side[gi - 1], P->fork, 0) != cudaSuccess) return HYDE_ERR_CUDA;
     hyde_status st = enqueue_group(P, P->g[0], Y, X, info, ws, s);
-    const hyde_status st2 = enqueue_group(P, P->g[1], Y, X, info, ws, P->side);
-    if (cudaEventRecord(P->join, P->side) != cudaSuccess ||
-        cudaStreamWaitEvent(s, P->join, 0) != cudaSuccess)
-        return HYDE_ERR_CUDA;
-    if (st == HYDE_OK) st = st2;
+    for (int gi = 1; gi < P->ngroups; ++gi) {
+        const hyde_status sg = enqueue_group(P, P->g[gi], Y, X, info, ws, P->side[gi - 1]);
+        if (st == HYDE_OK) st = sg;
+        if (cudaEventRecord(P->join[gi - 1], P->side[gi - 1]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, P->join[gi - 1], 0) != cudaSuccess)
+            return HYDE_ERR_CUDA;
+    }
     return st;
 }
 

@@ -13,7 +13,7 @@ from synth import make_cube
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("count,slots", [(5, 3), (2, 3), (4, 1)])
+@pytest.mark.parametrize("count,slots", [(5, 3), (2, 3), (4, 1), (6, 4)])
 def test_many_cubes_equal_one_at_a_time(hyde, count, slots):
     H, W, p, L, r = 77, 131, 24, 3, 6
     cubes = [make_cube(H, W, p, m=3, seed=40 + k)["Y"] for k in range(count)]
