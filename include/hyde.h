@@ -279,7 +279,9 @@ hyde_status hyde_eig_sym_top(const double* A, int p, int r, double* evals,
  * One level: a_k = sum_m h_m x[(2k+m) mod M], d_k = sum_m g_m x[(2k+m) mod M]
  * along rows, then along columns, g_m = (-1)^m h_{3-m}.
  * hyde_idwt2 is the exact transpose (the inverse of the periodic transform)
- * followed by cropping to H x W. wavelet must be 2.
+ * followed by cropping to H x W. wavelet must be 2. These two calls have no
+ * status word, so their tiles are gathered with cp.async only; inside the
+ * HyRes path the interior tiles of each analysis level are TMA copies.
  */
 hyde_status hyde_dwt_workspace_size(int batch, int H, int W, int levels,
                                     size_t* bytes);
@@ -638,7 +640,11 @@ int hyde_set_grid_sm_cap(int sms);
  * status word of the call (hyde_hyres_info.status for the whole path),
  * waits at most one second more for its own tensor-core work in flight,
  * frees its tensor memory and returns; its Gram output is then zero and the
- * CUDA context stays usable. Meant for testing that path: the default suits
+ * CUDA context stays usable. The same limit bounds the waits for the TMA
+ * copies of the wavelet analysis inside the HyRes, WSRRR and FORPDN calls:
+ * a block whose copy runs out writes HYDE_ERR_TIMEOUT, lets its copies in
+ * flight land (at most one second) and stops, leaving its tiles of the
+ * coefficients unwritten. Meant for testing those paths: the default suits
  * every supported size. (No counterpart in the paper.) */
 unsigned long long hyde_set_wait_limit_ns(unsigned long long ns);
 
