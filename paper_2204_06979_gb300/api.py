@@ -329,10 +329,11 @@ class HyResMany:
     """Several cubes of one shape at once (``hyde_hyres_denoise_many``): ``slots``
     workspaces, each with its own stream, forked from and joined to the
     current stream; cube k runs in slot k % slots, so one cube's
-    single-block stages overlap another's bandwidth-bound ones."""
+    single-block stages overlap another's bandwidth-bound ones (four slots
+    measured fastest of one to four on a 349 x 1905 x 144 cube)."""
 
     def __init__(self, p: int, H: int, W: int, levels: int, r_max: int, n_lambda: int = 64,
-                 slots: int = 3, device="cuda", precision: int = PREC_FP32):
+                 slots: int = 4, device="cuda", precision: int = PREC_FP32):
         self.lib = _lib.load()
         self.shape = (p, H, W)
         self.params = params(levels, r_max, n_lambda, precision)
