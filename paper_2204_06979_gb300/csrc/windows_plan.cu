@@ -26,6 +26,8 @@ using namespace hyde;
 #endif
 namespace {
 constexpr int kGroups = HYDE_WIN_GROUPS;
+static_assert(kGroups >= 1, "at least one window group");
+constexpr int kSideSlots = kGroups > 1 ? kGroups - 1 : 1;
 }
 
 struct WinGroup {
@@ -45,8 +47,8 @@ struct hyde_windows_plan_s {
     WinGroup g[kGroups];
     void* host;              // page-locked copy of the tables
     size_t tables;           // their bytes (the head of the workspace)
-    cudaStream_t side[kGroups - 1];      // the streams of groups 1, 2, ...
-    cudaEvent_t fork, join[kGroups - 1];
+    cudaStream_t side[kSideSlots];       // the streams of groups 1, 2, ...
+    cudaEvent_t fork, join[kSideSlots];
     // workspace offsets
     size_t desc, geo;
     size_t status, R, sigma, Ainv, S, eig, eig_stride, evals, V, P, Q;
