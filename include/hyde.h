@@ -431,7 +431,9 @@ hyde_status hyde_hyres_backward(const float* Y, const float* dX, int p, int H,
  * streams are forked from `stream` (events[0]) and joined back to it
  * (events[1 + s]): work enqueued on `stream` afterwards sees every X[k].
  * info: device array of count records, or NULL. Cubes of the same slot run
- * in order on its stream. Asynchronous; no host synchronisation.
+ * in order on its stream. Asynchronous; no host synchronisation. On a
+ * 349 x 1905 x 144 cube four slots measured fastest of one to four (0.54 ms
+ * per cube against 0.88 ms one at a time). (No counterpart in the paper.)
  */
 hyde_status hyde_hyres_denoise_many(const float* const* Y, float* const* X, int count, int p,
                                     int H, int W, const hyde_hyres_params* params,
