@@ -9,9 +9,10 @@
 // band (bottom-left) and the diagonal band. LL is recursed on.
 //
 // Every analysis level runs as a persistent pipeline (tiles of 16 x 64
-// coefficients per band, the next tile streamed into shared memory with
-// cp.async while the current one is filtered, float4 filter passes); the
-// first level of an unpadded image reads through the symmetric extension.
+// coefficients per band, the next tile streamed into shared memory while the
+// current one is filtered: one TMA copy for an interior tile, cp.async
+// through the halo; float4 filter passes); the first level of an unpadded
+// image reads through the symmetric extension.
 // Synthesis levels use one tile per block (16 x 32 coefficients) or the
 // register form below. Details go straight to their Mallat position in the
 // coefficient image; LL goes to a compact ping-pong buffer (or, at the last
